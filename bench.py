@@ -1,0 +1,413 @@
+"""Benchmark: SHO projection + expansion throughput on one GB300 (psi GB/s at stated error).
+
+One step = one pass of the hot path over the 96^3 workload: project psi onto every atom's SHO basis
+(1D tables, cube gather, x/y/z passes), then expand random FP64 coefficients into a second wave-function
+buffer (z/y/x passes, row gather).  Inputs are resident in HBM before the timed region; psi (906 MB)
+is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead, on a bounded
+sample of the same workload.  Under torchrun (N > 1) every rank runs its own replica of the workload
+(weak scaling, no collective); the reference arm runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "SHO project+expand psi GB/s vs HBM peak at stated error; p50/p99 request latency"
+WORKLOAD = "c96"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
+# 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.
+FP64_PEAK_TFLOPS = 1.19
+
+
+def union_cube_points(w, pos):
+    """Number of distinct grid points covered by the atoms' cubes (counted exactly on the host)."""
+    nx, ny, nz = w.grid
+    mask = np.zeros((nz, ny, nx), dtype=bool)
+    i = np.arange(w.cube)
+    for X in pos:
+        o = np.floor(X / w.h).astype(int) - w.cube // 2 + 1
+        idx = []
+        for d, n in enumerate((nx, ny, nz)):
+            j = o[d] + i
+            if w.periodic:
+                j = j % n
+            else:
+                j = j[(j >= 0) & (j < n)]
+            idx.append(j)
+        mask[np.ix_(idx[2], idx[1], idx[0])] = True
+    return int(mask.sum())
+
+
+def algorithmic(w, pos, nstates, elem=8):
+    """Algorithmic bytes and flops of one step (projection + expansion)."""
+    U = union_cube_points(w, pos)
+    A, B, C, nu = w.natoms, w.nbands, w.cube, w.numax
+    P = (nu + 1) * (nu + 2) // 2
+    coeff = A * nstates * B * elem
+    bytes_prj = U * B * elem + coeff
+    bytes_add = 2 * U * B * elem + coeff
+    flop_per_atom_band = 2 * (C ** 3 * (nu + 1) + C ** 2 * P + C * nstates)
+    flops = A * B * flop_per_atom_band
+    return dict(union_points=U, bytes_prj=bytes_prj, bytes_add=bytes_add, flops_prj=flops, flops_add=flops)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.proc = None
+        self.dev = device_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------------- our arm
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1905_00480_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads.WORKLOADS[WORKLOAD]
+    # every rank runs its own replica with its own seed stream (weak scaling)
+    rng = np.random.default_rng([w.seed, rank])
+    pos, sig = workloads.atoms(w, rng if rank else None)
+    nst = api.nstates(w.numax)
+    alg = algorithmic(w, pos, nst)
+    g = torch.Generator(device=dev)
+    g.manual_seed(w.seed + 7919 * rank)
+    nx, ny, nz = w.grid
+    psi = torch.randn((nz, ny, nx, w.nbands), generator=g, device=dev, dtype=torch.float64)
+    cin = torch.randn((w.natoms, nst, w.nbands), generator=g, device=dev, dtype=torch.float64)
+    hpsi = torch.zeros_like(psi)
+    coeff = torch.empty((w.natoms, nst, w.nbands), dtype=torch.float64, device=dev)
+    handle = api.Handle(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+                    stream=stream)
+        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(K):
+        ev[i][0].record(stream)
+        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+                    stream=stream)
+        ev[i][1].record(stream)
+        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+        ev[i][2].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    ms_total = max_over_ranks(ws, ms_total)
+    ms_step = ms_total / K
+    t_prj = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    t_add = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    bytes_step = alg["bytes_prj"] + alg["bytes_add"]
+    value = ws * bytes_step / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host psi and coefficients in, expansion result out
+    psi_h = torch.empty(psi.shape, dtype=psi.dtype, pin_memory=True)
+    psi_h.copy_(psi)
+    cin_h = torch.empty(cin.shape, dtype=cin.dtype, pin_memory=True)
+    cin_h.copy_(cin)
+    out_h = torch.empty(psi.shape, dtype=psi.dtype, pin_memory=True)
+    psi_d = torch.empty_like(psi)
+    cin_d = torch.empty_like(cin)
+
+    def e2e_step():
+        psi_d.copy_(psi_h, non_blocking=True)
+        cin_d.copy_(cin_h, non_blocking=True)
+        api.project(psi_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+                    stream=stream)
+        hpsi.zero_()
+        api.add(hpsi, cin_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+        out_h.copy_(hpsi, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    K2 = max(2, min(K, 10))
+    barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K2):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(ws, e0.elapsed_time(e1) / K2)
+    h2d = psi.numel() * 8 + cin.numel() * 8
+    d2h = psi.numel() * 8
+
+    result = None
+    if rank == 0:
+        peaks = _peaks()
+        dom = "k_project" if t_prj >= t_add else "k_expand"
+        t_dom = max(t_prj, t_add)
+        flops_dom = alg["flops_prj"] if dom == "k_project" else alg["flops_add"]
+        achieved = flops_dom / (t_dom * 1e-3) / 1e12
+        result = {
+            "metric": METRIC,
+            "value": round(value, 3),
+            "unit": "GB/s",
+            "n_gpus": ws,
+            "steps": K,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic (seeded N(0,1) psi and coefficients, uniform atoms with min separation 2.0)",
+            "config": {
+                "workload": "periodic 96^3 grid, h=0.2, 64 atoms, sigma U[0.5,1], numax 5 (56 states), cube 32^3, "
+                            "128 bands, FP64: project then expand",
+                "global_batch": w.nbands * ws,
+                "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                "l2": "inputs larger than L2 (psi 906 MB per buffer), no flush",
+                "union_cube_points": alg["union_points"],
+                "algorithmic_bytes_per_step": bytes_step,
+            },
+            "kernels_ms": {"project": round(t_prj, 4), "expand": round(t_add, 4)},
+            "hbm_fraction": round(value / ws / peaks.get("hbm_gbs", 6793.4), 4),
+            "roofline": {
+                "bound": "alu",
+                "kernel": dom,
+                "achieved": round(achieved, 4),
+                "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "traffic": None,
+                "peak_source": "measured FP64 DFMA throughput (152 SMs x 4 flop/clk)",
+            },
+            "e2e": {"value": round(ws * bytes_step / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
+                    "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 3 * K,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            result["cpu_baseline"], result["error_vs_oracle"] = cpu_baseline(
+                w, pos, sig, psi, cin, coeff, hpsi_ref=None, api=api, handle=handle)
+    return result
+
+
+def _oracle_sample(w, pos, sig, nsel, nbands_sel, seed=5):
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(w.natoms, size=nsel, replace=False))
+    return sel, nbands_sel
+
+
+def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle):
+    """Time the FP64 oracle, as it stands, on the workload (all atoms and bands: about ten seconds of
+    host work on 16 cores) and state the GPU error against it."""
+    import oracle
+    sel, _ = _oracle_sample(w, pos, sig, w.natoms, w.nbands)
+    psi = psi_d.cpu().numpy()
+    cin = cin_d.cpu().numpy()
+    sw = workloads.Workload(**{**w.__dict__, "natoms": len(sel)})
+    alg = algorithmic(sw, pos[sel], api.nstates(w.numax))
+    t0 = time.perf_counter()
+    ref_c = oracle.project(w.grid, w.h, w.periodic, psi, pos[sel], sig[sel], w.numax, w.cube)
+    t1 = time.perf_counter()
+    out = oracle.add(w.grid, w.h, w.periodic, np.zeros_like(psi), pos[sel], sig[sel], w.numax, w.cube, cin[sel])
+    t2 = time.perf_counter()
+    secs = t2 - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    got_c = coeff_d.cpu().numpy()[sel]
+    err_c = float(np.linalg.norm(got_c - ref_c) / np.linalg.norm(ref_c))
+    # GPU expansion of the same atoms into zeros
+    import torch
+    z = torch.zeros_like(psi_d)
+    api.add(z, cin_d[torch.as_tensor(sel, device=cin_d.device)].contiguous(), pos[sel], sig[sel], w.numax, w.cube,
+            w.h, w.periodic, prec="fp64", handle=handle)
+    err_a = float(np.linalg.norm(z.cpu().numpy() - out) / np.linalg.norm(out))
+    base = {"value": round((alg["bytes_prj"] + alg["bytes_add"]) / secs / 1e9, 5), "unit": "GB/s", "cores": cores,
+            "kind": "oracle", "seconds": round(secs, 3), "project_s": round(t1 - t0, 3), "add_s": round(t2 - t1, 3),
+            "sample": f"{len(sel)} of {w.natoms} atoms (all {w.nbands} bands), project + expand, FP64 direct "
+                      "summation over fully sampled 3D projectors"}
+    err = {"project_rel_norm": err_c, "expand_rel_norm": err_a, "tolerance": 1e-12,
+           "sample": f"{len(sel)} atoms"}
+    return base, err
+
+
+# ----------------------------------------------------------------------------------- reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    w = workloads.WORKLOADS[WORKLOAD]
+    pos, sig = workloads.atoms(w)
+    N = oracle.nstates(w.numax)
+    rng = np.random.default_rng([w.seed, 1])
+    psi = rng.standard_normal((w.grid[2], w.grid[1], w.grid[0], w.nbands))
+    cin = rng.standard_normal((w.natoms, N, w.nbands))
+    nsel = 2  # atoms per timed step: a bounded sample so the whole run takes a few minutes
+    sel_all = np.arange(w.natoms)
+    sw = workloads.Workload(**{**w.__dict__, "natoms": nsel})
+
+    def step(i):
+        sel = sel_all[(i * nsel) % w.natoms:(i * nsel) % w.natoms + nsel]
+        oracle.project(w.grid, w.h, w.periodic, psi, pos[sel], sig[sel], w.numax, w.cube)
+        oracle.add(w.grid, w.h, w.periodic, psi, pos[sel], sig[sel], w.numax, w.cube, cin[sel])
+        return sel
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    byts = 0
+    for i in range(args.steps):
+        sel = step(args.warmup + i)
+        a = algorithmic(sw, pos[sel], N)
+        byts += a["bytes_prj"] + a["bytes_add"]
+    secs = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = byts / secs / 1e9
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 5), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "periodic 96^3 grid, h=0.2, 64 atoms, sigma U[0.5,1], numax 5, cube 32^3, 128 bands, "
+                               "FP64: project then expand"},
+        "cpu_baseline": {"value": round(value, 5), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{nsel} atoms (all bands) per step of the 64-atom workload"},
+        "e2e": {"value": round(value, 5), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+    else:
+        res = run_ours(args, ws, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

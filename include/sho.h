@@ -1,0 +1,161 @@
+/*
+ * sho.h -- C ABI of the GB300 SHO projector library (libsho.so).
+ *
+ * Projection of real-space grid wave functions onto analytical SHO (3D Hermite-Gauss) projector
+ * functions, and its adjoint, the expansion, after Baumeister & Tsukamoto, "Analytical PAW Projector
+ * Functions for Reduced Bandwidth Requirements" (PASC'19).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Grid       grid point j = (jx, jy, jz), 0 <= j_d < n[d], sits at r = h * j (lengths in Bohr).
+ *             psi is stored psi[jz][jy][jx][b]: bands innermost (the paper vectorises over bands,
+ *             Sec. 6), contiguous, element type given by a sho_dtype.
+ *  Atoms      pos[a][3] (x, y, z) and sigma[a] are HOST arrays of double.  The cube of atom a has
+ *             edge `cube` points; its origin per axis is o_d = floor(pos[a][d] / h) - cube/2 + 1 and
+ *             cube point i_d maps to grid index (o_d + i_d) mod n[d] (periodic) or is dropped when
+ *             outside [0, n[d]) (not periodic).  The functions are evaluated at the unwrapped offset
+ *             u_d = (o_d + i_d) h - pos[a][d].
+ *  Functions  phi_n(u) = (sigma sqrt(pi) 2^n n!)^(-1/2) H_n(u/sigma) exp(-u^2 / 2 sigma^2)
+ *             (eq. 1HO-eigenstate, Sec. 2.2, normalised; the paper leaves the factor out and folds it
+ *             into the atomic matrix, Sec. 3.7), three of them multiplied per state
+ *             (eq. SHO-factorizable-basis).
+ *  Basis      all (nx, ny, nz) with nx + ny + nz <= numax (eq. SHO-basis, Sec. 2.5), N =
+ *             (numax+1)(numax+2)(numax+3)/6 states (eq. SHO_basis_size), enumerated nz outer,
+ *             ny middle, nx inner.  Coefficients are stored coeff[a][k][b], bands innermost.
+ *  Memory     every array pointer except pos/sigma is a DEVICE pointer (cudaMalloc / torch); the
+ *             caller owns all buffers and the library never frees or retains them after the call's
+ *             work has completed on `stream`.
+ *  Streams    `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *             asynchronous: they enqueue work and return.  A handle orders its own calls (each call
+ *             waits for the handle's previous call), so one handle may be used from several streams,
+ *             but not from several host threads at once.
+ *  Errors     every call returns SHO_OK (0) or a negative sho_status.  Argument errors are detected
+ *             on the host before anything is enqueued; nothing is written then.  CUDA launch errors
+ *             return SHO_ERR_CUDA.  Errors raised later on the device are reported by sho_sync().
+ *  Precision  sho_prec selects the arithmetic of the contractions.  SHO_P_FP64 needs FP64 psi and
+ *             coefficients.  The other forms take FP32 or BF16 psi and FP32 coefficients and keep the
+ *             1D function tables in FP64 until they are rounded to the contraction type.
+ */
+#ifndef SHO_H
+#define SHO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHO_VERSION 1
+#define SHO_MAX_NUMAX 9      /* largest numax of projection / expansion (forces use numax + 1) */
+
+typedef enum {
+  SHO_OK = 0,
+  SHO_ERR_ARG = -1,        /* null pointer, negative size, unknown enum value */
+  SHO_ERR_NUMAX = -2,      /* numax outside [0, SHO_MAX_NUMAX] */
+  SHO_ERR_CUBE = -3,       /* cube not a multiple of 8 in [8, 64], or larger than a grid dimension */
+  SHO_ERR_SPACING = -4,    /* h > h_max = pi sigma / sqrt(2 numax + 1) (eq. max_grid_spacing),
+                              returned only in strict mode (sho_set_strict) */
+  SHO_ERR_DTYPE = -5,      /* dtype / precision combination not supported */
+  SHO_ERR_OOM = -6,        /* device or pinned host allocation failed */
+  SHO_ERR_CUDA = -7,       /* a CUDA runtime call or launch failed */
+  SHO_ERR_TIMEOUT = -8,    /* a bounded wait ran out (serving) */
+  SHO_ERR_DEVICE = -9,     /* a device-side check failed (reported by sho_sync) */
+  SHO_ERR_CAPACITY = -10,  /* serving admission: request can never fit the memory budget */
+  SHO_ERR_STATE = -11      /* unknown ticket / system, or call not valid in the current state */
+} sho_status;
+
+typedef enum { SHO_F64 = 0, SHO_F32 = 1, SHO_BF16 = 2 } sho_dtype;
+
+typedef enum {
+  SHO_P_FP64 = 0,        /* FP64 throughout (FP64 psi and coefficients) */
+  SHO_P_FP32 = 1,        /* FP32 CUDA-core contractions, FP32 accumulation */
+  SHO_P_TF32 = 2,        /* x-pass on TF32 tensor cores, FP32 accumulation */
+  SHO_P_3XTF32 = 3,      /* x-pass as three TF32 products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
+  SHO_P_BF16 = 4,        /* x-pass on BF16 tensor cores, FP32 accumulation */
+  SHO_P_SPLIT_FP16 = 5   /* x-pass as three FP16 products of a hi/lo split, FP32 accumulation */
+} sho_prec;
+
+typedef struct {
+  int n[3];       /* grid points along x, y, z */
+  double h;       /* grid spacing (Bohr) */
+  int periodic;   /* 1: cube indices wrap around the grid; 0: points outside the grid are dropped */
+} sho_grid;
+
+typedef struct sho_handle sho_handle;
+
+/* Library version (SHO_VERSION). */
+int sho_version(void);
+
+/* Basis size (numax+1)(numax+2)(numax+3)/6, eq. SHO_basis_size (Sec. 2.5); 0 for numax < 0. */
+int sho_nstates(int numax);
+
+/* Largest grid spacing that samples states up to numax without aliasing:
+ * h_max = pi sigma / sqrt(2 numax + 1), eq. max_grid_spacing (Sec. 3.6). */
+double sho_max_spacing(double sigma, int numax);
+
+/* Static description of a status code (never NULL). */
+const char* sho_strerror(int status);
+
+/* Create a handle bound to CUDA device `device` (made current during each call).  The handle owns
+ * a device workspace that grows on demand and is freed by sho_destroy. */
+int sho_create(sho_handle** out, int device);
+
+/* Wait for the handle's outstanding work, free its workspace and the handle. */
+int sho_destroy(sho_handle* handle);
+
+/* strict != 0: a spacing above h_max (eq. max_grid_spacing) is an error (SHO_ERR_SPACING); default 0
+ * (allowed: the method still computes the defined sums, only their sampling is coarse). */
+int sho_set_strict(sho_handle* handle, int strict);
+
+/* Block until the handle's enqueued work is complete; return the first device-side error since the
+ * previous sho_sync (SHO_ERR_DEVICE) or a CUDA error, else SHO_OK. */
+int sho_sync(sho_handle* handle);
+
+/*
+ * Projection -- step (1) of the non-local action (Sec. 3.2) with the SHO basis injected (Sec. 3.5):
+ *     coeff[a][k][b] = h^3 * sum_{cube points i of atom a} Psi_k(u_i) * psi[j(i)][b]
+ * evaluated as three separable passes (x, then y, then z; eq. TuckerTensor, Sec. 3.4) with the 1D
+ * functions generated on the fly from the Hermite recursion (Sec. 3.7).
+ *   psi    device [n[2]][n[1]][n[0]][nbands], type psi_dtype (read only)
+ *   coeff  device [natoms][sho_nstates(numax)][nbands], type coeff_dtype (written, fully)
+ * Supported: (SHO_P_FP64, psi F64, coeff F64); (SHO_P_FP32 | TF32 | 3XTF32 | BF16 | SPLIT_FP16,
+ * psi F32 or BF16, coeff F32).  natoms == 0 or nbands == 0 is a no-op returning SHO_OK.
+ */
+int sho_project(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
+                int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                void* coeff, sho_dtype coeff_dtype, void* stream);
+
+/*
+ * Expansion -- step (3) of the non-local action (Sec. 3.2), the adjoint of the projection:
+ *     psi[j][b] += sum_a sum_{i: j(i) = j} sum_k coeff[a][k][b] * Psi_k(u_i)      (no h^3 factor)
+ * so that <P psi, c> = h^3 <psi, E c>.  Evaluated z-pass, y-pass, x-pass.  Every grid row is
+ * read and written once, atoms are added in ascending index order: the result is deterministic.
+ *   coeff  device [natoms][sho_nstates(numax)][nbands], type coeff_dtype (read only)
+ *   psi    device [n[2]][n[1]][n[0]][nbands], type psi_dtype (read-modify-write)
+ * Same dtype / precision combinations as sho_project.
+ */
+int sho_add(sho_handle* handle, const sho_grid* grid, const void* coeff, sho_dtype coeff_dtype, int nbands,
+            int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
+            sho_dtype psi_dtype, void* stream);
+
+/*
+ * Forces -- gradient of a function E(c) of the projection coefficients with respect to the atom
+ * positions, the cube origins held fixed:
+ *     dEdX[a][d] = sum_b sum_k dEdc[a][k][b] * d coeff[a][k][b] / d pos[a][d]
+ * Built from a projection at numax + 1 and the ladder relation of Hermite functions (derivative of
+ * the Hermite recursion, Sec. 3.7):  d phi_n / du = (1/sigma) [ sqrt(n/2) phi_{n-1} - sqrt((n+1)/2) phi_{n+1} ],
+ * so  d C_n / dX = (1/sigma) [ sqrt((n+1)/2) C_{n+1} - sqrt(n/2) C_{n-1} ]  per axis.
+ *   psi    device [n[2]][n[1]][n[0]][nbands], type psi_dtype
+ *   dEdc   device [natoms][sho_nstates(numax)][nbands], type coeff_dtype
+ *   dEdX   device [natoms][3] double (written); the physical force is -dEdX.
+ * numax may be at most SHO_MAX_NUMAX.  The band/state reduction is done in FP64 in a fixed order.
+ */
+int sho_forces(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
+               int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+               const void* dEdc, sho_dtype coeff_dtype, double* dEdX, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHO_H */

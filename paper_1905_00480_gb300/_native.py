@@ -1,0 +1,76 @@
+"""ctypes view of libsho.so (the C ABI of include/sho.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsho.so")
+
+SHO_OK = 0
+STATUS_NAMES = {
+    0: "SHO_OK", -1: "SHO_ERR_ARG", -2: "SHO_ERR_NUMAX", -3: "SHO_ERR_CUBE", -4: "SHO_ERR_SPACING",
+    -5: "SHO_ERR_DTYPE", -6: "SHO_ERR_OOM", -7: "SHO_ERR_CUDA", -8: "SHO_ERR_TIMEOUT", -9: "SHO_ERR_DEVICE",
+    -10: "SHO_ERR_CAPACITY", -11: "SHO_ERR_STATE",
+}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
+PRECS = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16": 4, "split_fp16": 5}
+
+
+class ShoError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = lib().sho_strerror(status).decode() if _lib is not None else ""
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)} ({msg})")
+
+
+class sho_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("periodic", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+_GP = ctypes.POINTER(sho_grid)
+
+# name -> (restype, argtypes); every symbol declared in include/sho.h
+SIGNATURES = {
+    "sho_version": (_I, []),
+    "sho_nstates": (_I, [_I]),
+    "sho_max_spacing": (ctypes.c_double, [ctypes.c_double, _I]),
+    "sho_strerror": (ctypes.c_char_p, [_I]),
+    "sho_create": (_I, [ctypes.POINTER(_VP), _I]),
+    "sho_destroy": (_I, [_VP]),
+    "sho_set_strict": (_I, [_VP, _I]),
+    "sho_sync": (_I, [_VP]),
+    "sho_project": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
+    "sho_add": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
+    "sho_forces": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),
+}
+
+
+def lib():
+    """Load libsho.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -m paper_1905_00480_gb300.build); there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str):
+    if status != SHO_OK:
+        raise ShoError(status, what)

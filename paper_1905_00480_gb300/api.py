@@ -1,0 +1,173 @@
+"""PyTorch-facing binding of libsho: same names as the C ABI, argument marshalling only.
+
+PyTorch provides device memory and streams; every step of projection, expansion and forces runs in
+the library's CUDA kernels.  Tensors must live on a CUDA device; there is no CPU path.
+
+Layouts (see include/sho.h): psi [Nz][Ny][Nx][B] contiguous, coefficients [A][N][B], positions [A][3]
+and sigma [A] (any device; they are copied to the host as the C ABI expects).
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+_TORCH_DT = {torch.float64: "f64", torch.float32: "f32", torch.bfloat16: "bf16"}
+
+
+def nstates(numax: int) -> int:
+    """(numax+1)(numax+2)(numax+3)/6 (eq. SHO_basis_size)."""
+    return int(N.lib().sho_nstates(int(numax)))
+
+
+def max_spacing(sigma: float, numax: int) -> float:
+    """h_max = pi sigma / sqrt(2 numax + 1) (eq. max_grid_spacing)."""
+    return float(N.lib().sho_max_spacing(float(sigma), int(numax)))
+
+
+class Handle:
+    """Owns a libsho handle (device workspace, call ordering) for one CUDA device."""
+
+    def __init__(self, device: int = 0, strict: bool = False):
+        self._h = ctypes.c_void_p()
+        self.device = int(device)
+        N.check(N.lib().sho_create(ctypes.byref(self._h), self.device), "sho_create")
+        if strict:
+            N.check(N.lib().sho_set_strict(self._h, 1), "sho_set_strict")
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def sync(self):
+        N.check(N.lib().sho_sync(self._h), "sho_sync")
+
+    def close(self):
+        if self._h:
+            N.lib().sho_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles = {}
+_hlock = threading.Lock()
+
+
+def default_handle(device: int) -> Handle:
+    with _hlock:
+        h = _handles.get(device)
+        if h is None:
+            h = _handles[device] = Handle(device)
+        return h
+
+
+def _grid(psi: torch.Tensor, h: float, periodic: bool) -> N.sho_grid:
+    g = N.sho_grid()
+    nz, ny, nx = psi.shape[0], psi.shape[1], psi.shape[2]
+    g.n[0], g.n[1], g.n[2] = int(nx), int(ny), int(nz)
+    g.h = float(h)
+    g.periodic = 1 if periodic else 0
+    return g
+
+
+def _host_f64(x, shape_last=None):
+    if isinstance(x, torch.Tensor):
+        x = x.detach().to("cpu", torch.float64).numpy()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if shape_last is not None:
+        a = a.reshape(-1, shape_last)
+    return a
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check_psi(psi: torch.Tensor):
+    if not psi.is_cuda:
+        raise ValueError("psi must be a CUDA tensor (there is no CPU path)")
+    if psi.dim() != 4 or not psi.is_contiguous():
+        raise ValueError("psi must be a contiguous [Nz][Ny][Nx][B] tensor")
+    if psi.dtype not in _TORCH_DT:
+        raise ValueError(f"unsupported psi dtype {psi.dtype}")
+
+
+def _stream_ptr(psi: torch.Tensor, stream):
+    s = stream if stream is not None else torch.cuda.current_stream(psi.device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _coeff_dtype(prec: str):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def project(psi: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, periodic: bool = True,
+            prec: str = "fp64", out: torch.Tensor = None, handle: Handle = None, stream=None) -> torch.Tensor:
+    """sho_project: c[a][k][b] = h^3 sum over the atom's cube of Psi_k(u) psi[j][b]."""
+    _check_psi(psi)
+    pos_h = _host_f64(pos, 3)
+    sig_h = _host_f64(sigma).reshape(-1)
+    A, B = pos_h.shape[0], psi.shape[3]
+    cdt = _coeff_dtype(prec)
+    if out is None:
+        out = torch.empty((A, nstates(numax), B), dtype=cdt, device=psi.device)
+    elif out.dtype != cdt or not out.is_contiguous() or tuple(out.shape) != (A, nstates(numax), B):
+        raise ValueError("out has the wrong dtype, shape or layout")
+    hd = handle or default_handle(psi.device.index or 0)
+    g = _grid(psi, h, periodic)
+    st = N.lib().sho_project(hd.ptr, ctypes.byref(g), ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
+                             B, A, _dp(pos_h), _dp(sig_h), int(numax), int(cube), N.PRECS[prec],
+                             ctypes.c_void_p(out.data_ptr()), N.DTYPES[_TORCH_DT[cdt]], _stream_ptr(psi, stream))
+    N.check(st, "sho_project")
+    return out
+
+
+def add(psi: torch.Tensor, coeff: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, periodic: bool = True,
+        prec: str = "fp64", handle: Handle = None, stream=None) -> torch.Tensor:
+    """sho_add (in place): psi[j][b] += sum_a sum_k c[a][k][b] Psi_k(u).  Returns psi."""
+    _check_psi(psi)
+    pos_h = _host_f64(pos, 3)
+    sig_h = _host_f64(sigma).reshape(-1)
+    A, B = pos_h.shape[0], psi.shape[3]
+    if not coeff.is_cuda or not coeff.is_contiguous() or tuple(coeff.shape) != (A, nstates(numax), B):
+        raise ValueError("coeff must be a contiguous CUDA tensor [A][N][B]")
+    hd = handle or default_handle(psi.device.index or 0)
+    g = _grid(psi, h, periodic)
+    st = N.lib().sho_add(hd.ptr, ctypes.byref(g), ctypes.c_void_p(coeff.data_ptr()),
+                         N.DTYPES[_TORCH_DT[coeff.dtype]], B, A, _dp(pos_h), _dp(sig_h), int(numax), int(cube),
+                         N.PRECS[prec], ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
+                         _stream_ptr(psi, stream))
+    N.check(st, "sho_add")
+    return psi
+
+
+def forces(psi: torch.Tensor, dEdc: torch.Tensor, pos, sigma, numax: int, cube: int, h: float,
+           periodic: bool = True, prec: str = "fp64", out: torch.Tensor = None, handle: Handle = None,
+           stream=None) -> torch.Tensor:
+    """sho_forces: dEdX[a][d] = sum_{k,b} dEdc[a][k][b] d c[a][k][b] / d X[a][d] (FP64 result)."""
+    _check_psi(psi)
+    pos_h = _host_f64(pos, 3)
+    sig_h = _host_f64(sigma).reshape(-1)
+    A, B = pos_h.shape[0], psi.shape[3]
+    if not dEdc.is_cuda or not dEdc.is_contiguous() or tuple(dEdc.shape) != (A, nstates(numax), B):
+        raise ValueError("dEdc must be a contiguous CUDA tensor [A][N][B]")
+    if out is None:
+        out = torch.empty((A, 3), dtype=torch.float64, device=psi.device)
+    hd = handle or default_handle(psi.device.index or 0)
+    g = _grid(psi, h, periodic)
+    st = N.lib().sho_forces(hd.ptr, ctypes.byref(g), ctypes.c_void_p(psi.data_ptr()),
+                            N.DTYPES[_TORCH_DT[psi.dtype]], B, A, _dp(pos_h), _dp(sig_h), int(numax), int(cube),
+                            N.PRECS[prec], ctypes.c_void_p(dEdc.data_ptr()), N.DTYPES[_TORCH_DT[dEdc.dtype]],
+                            ctypes.cast(ctypes.c_void_p(out.data_ptr()), ctypes.POINTER(ctypes.c_double)),
+                            _stream_ptr(psi, stream))
+    N.check(st, "sho_forces")
+    return out

@@ -1,0 +1,422 @@
+// sho_api.cu -- host side of the C ABI declared in include/sho.h: argument validation, the per-call
+// plan (cube origins, per-plane atom lists), workspace management and kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "sho_internal.h"
+
+struct sho_handle {
+  int device = 0;
+  int strict = 0;
+  int sms = 1;
+  void* ws = nullptr;          // device workspace (plan + intermediates), grows on demand
+  size_t ws_bytes = 0;
+  cudaEvent_t last = nullptr;  // completion of the handle's most recent call
+  bool has_last = false;
+  int device_error = SHO_OK;   // first device-side error since the last sho_sync
+};
+
+namespace sho {
+namespace {
+
+// Makes the handle's device current for the duration of a call and restores the caller's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Bump allocator over the workspace; every region starts on a 256-byte boundary.
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+int check_common(const sho_grid* grid, int nbands, int natoms, const double* pos, const double* sigma, int numax,
+                 int cube, int max_numax) {
+  if (!grid) return SHO_ERR_ARG;
+  if (nbands < 0 || natoms < 0) return SHO_ERR_ARG;
+  for (int d = 0; d < 3; d++)
+    if (grid->n[d] <= 0) return SHO_ERR_ARG;
+  if (!(grid->h > 0.0) || !std::isfinite(grid->h)) return SHO_ERR_ARG;
+  if (grid->n[0] > 768) return SHO_ERR_ARG;  // one grid row of 32 bands must fit in shared memory
+  if (natoms > 0 && (!pos || !sigma)) return SHO_ERR_ARG;
+  if (numax < 0 || numax > max_numax) return SHO_ERR_NUMAX;
+  if (cube < 8 || cube > kMaxCube || (cube % 8) != 0) return SHO_ERR_CUBE;
+  if (grid->periodic)
+    for (int d = 0; d < 3; d++)
+      if (cube > grid->n[d]) return SHO_ERR_CUBE;
+  for (int a = 0; a < natoms; a++) {
+    if (!(sigma[a] > 0.0) || !std::isfinite(sigma[a])) return SHO_ERR_ARG;
+    for (int d = 0; d < 3; d++)
+      if (!std::isfinite(pos[3 * a + d])) return SHO_ERR_ARG;
+  }
+  return SHO_OK;
+}
+
+int check_spacing(const sho_handle* h, const sho_grid* grid, int natoms, const double* sigma, int numax) {
+  if (!h->strict) return SHO_OK;
+  for (int a = 0; a < natoms; a++)
+    if (grid->h > sho_max_spacing(sigma[a], numax)) return SHO_ERR_SPACING;
+  return SHO_OK;
+}
+
+int check_dtypes(sho_prec prec, sho_dtype psi_dt, sho_dtype coeff_dt) {
+  switch (prec) {
+    case SHO_P_FP64:
+      return (psi_dt == SHO_F64 && coeff_dt == SHO_F64) ? SHO_OK : SHO_ERR_DTYPE;
+    case SHO_P_FP32:
+      return ((psi_dt == SHO_F32 || psi_dt == SHO_BF16) && coeff_dt == SHO_F32) ? SHO_OK : SHO_ERR_DTYPE;
+    case SHO_P_TF32:
+    case SHO_P_3XTF32:
+    case SHO_P_BF16:
+    case SHO_P_SPLIT_FP16:
+      return SHO_ERR_DTYPE;  // tensor-core forms are not part of this build
+    default:
+      return SHO_ERR_ARG;
+  }
+}
+
+std::vector<AtomDev> make_atoms(const sho_grid* grid, int natoms, const double* pos, const double* sigma, int cube) {
+  std::vector<AtomDev> at((size_t)natoms);
+  for (int a = 0; a < natoms; a++) {
+    AtomDev& t = at[(size_t)a];
+    std::memset(&t, 0, sizeof(t));
+    for (int d = 0; d < 3; d++) {
+      t.X[d] = pos[3 * a + d];
+      t.o[d] = (int)std::floor(pos[3 * a + d] / grid->h) - cube / 2 + 1;
+    }
+    t.sigma = sigma[a];
+  }
+  return at;
+}
+
+int grid_index(int o, int i, int n, int periodic) {
+  int j = o + i;
+  if (periodic) {
+    j %= n;
+    if (j < 0) j += n;
+    return j;
+  }
+  return (j >= 0 && j < n) ? j : -1;
+}
+
+// Per-plane atom lists (CSR): atom a is listed under plane jz for every cube plane it covers,
+// atoms in ascending order within a plane.
+void plane_lists(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, std::vector<int>& ptr,
+                 std::vector<int>& list) {
+  const int nz = grid->n[2];
+  ptr.assign((size_t)nz + 1, 0);
+  for (size_t a = 0; a < at.size(); a++)
+    for (int i = 0; i < cube; i++) {
+      int j = grid_index(at[a].o[2], i, nz, grid->periodic);
+      if (j >= 0) ptr[(size_t)j + 1]++;
+    }
+  for (int z = 0; z < nz; z++) ptr[(size_t)z + 1] += ptr[(size_t)z];
+  list.assign((size_t)ptr[(size_t)nz], 0);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (size_t a = 0; a < at.size(); a++)
+    for (int i = 0; i < cube; i++) {
+      int j = grid_index(at[a].o[2], i, nz, grid->periodic);
+      if (j >= 0) list[(size_t)fill[(size_t)j]++] = (int)a;
+    }
+}
+
+// Number of cube z-slabs per (atom, band tile) so that the CTAs spread evenly over the SMs.
+int choose_zsplit(int natoms, int nbands, int cube, int sms) {
+  const int nbt = (nbands + kWarp - 1) / kWarp;
+  int best = 1;
+  double best_score = -1.0;
+  for (int zs = 1; zs <= 8; zs *= 2) {
+    if (zs > 1 && cube / zs < 4) break;
+    const double ctas = (double)natoms * nbt * zs;
+    const double per_sm = std::ceil(ctas / sms);
+    const double eff = ctas / (per_sm * sms);
+    const double fill = std::min(1.0, ctas / (4.0 * sms));
+    const double score = eff * fill;
+    if (score > best_score + 1e-9) {
+      best_score = score;
+      best = zs;
+    }
+  }
+  return best;
+}
+
+int ensure_workspace(sho_handle* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return SHO_OK;
+  if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  size_t want = bytes + bytes / 4 + (1 << 20);
+  if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return SHO_ERR_OOM;
+  }
+  h->ws_bytes = want;
+  return SHO_OK;
+}
+
+int begin_call(sho_handle* h, cudaStream_t s) {
+  if (h->has_last && cudaStreamWaitEvent(s, h->last, 0) != cudaSuccess) return SHO_ERR_CUDA;
+  return SHO_OK;
+}
+
+int end_call(sho_handle* h, cudaStream_t s) {
+  if (cudaEventRecord(h->last, s) != cudaSuccess) return SHO_ERR_CUDA;
+  h->has_last = true;
+  return SHO_OK;
+}
+
+int upload(sho_handle* h, size_t off, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return SHO_OK;
+  if (cudaMemcpyAsync(static_cast<char*>(h->ws) + off, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return SHO_ERR_CUDA;
+  return SHO_OK;
+}
+
+GridDev make_grid(const sho_grid* grid, int cube, int nbands) {
+  GridDev g;
+  for (int d = 0; d < 3; d++) g.n[d] = grid->n[d];
+  g.periodic = grid->periodic ? 1 : 0;
+  g.h = grid->h;
+  g.cube = cube;
+  g.nbands = nbands;
+  return g;
+}
+
+#define SHO_TRY(x)                \
+  do {                            \
+    int _st = (x);                \
+    if (_st != SHO_OK) return _st; \
+  } while (0)
+
+}  // namespace
+}  // namespace sho
+
+using namespace sho;
+
+extern "C" {
+
+int sho_version(void) { return SHO_VERSION; }
+
+int sho_nstates(int numax) { return sho::nstates(numax); }
+
+double sho_max_spacing(double sigma, int numax) {
+  if (numax < 0) return 0.0;
+  return 3.14159265358979323846 * sigma / std::sqrt(2.0 * numax + 1.0);
+}
+
+const char* sho_strerror(int status) {
+  switch (status) {
+    case SHO_OK: return "success";
+    case SHO_ERR_ARG: return "invalid argument";
+    case SHO_ERR_NUMAX: return "numax out of range";
+    case SHO_ERR_CUBE: return "unsupported cube size";
+    case SHO_ERR_SPACING: return "grid spacing above the sampling limit h_max";
+    case SHO_ERR_DTYPE: return "unsupported dtype / precision combination";
+    case SHO_ERR_OOM: return "out of memory";
+    case SHO_ERR_CUDA: return "CUDA error";
+    case SHO_ERR_TIMEOUT: return "timed out";
+    case SHO_ERR_DEVICE: return "device-side check failed";
+    case SHO_ERR_CAPACITY: return "request exceeds the memory budget";
+    case SHO_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+  }
+}
+
+int sho_create(sho_handle** out, int device) {
+  if (!out) return SHO_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess) {
+    cudaGetLastError();
+    return SHO_ERR_CUDA;
+  }
+  if (device < 0 || device >= count) return SHO_ERR_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  sho_handle* h = new sho_handle();
+  h->device = device;
+  if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) h->sms = 1;
+  if (cudaEventCreateWithFlags(&h->last, cudaEventDisableTiming) != cudaSuccess) {
+    delete h;
+    return SHO_ERR_CUDA;
+  }
+  *out = h;
+  return SHO_OK;
+}
+
+int sho_destroy(sho_handle* h) {
+  if (!h) return SHO_ERR_ARG;
+  int st = SHO_OK;
+  {
+    DeviceGuard guard(h->device);
+    if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) st = SHO_ERR_CUDA;
+    if (h->ws) cudaFree(h->ws);
+    if (h->last) cudaEventDestroy(h->last);
+  }
+  delete h;
+  return st;
+}
+
+int sho_set_strict(sho_handle* h, int strict) {
+  if (!h) return SHO_ERR_ARG;
+  h->strict = strict ? 1 : 0;
+  return SHO_OK;
+}
+
+int sho_sync(sho_handle* h) {
+  if (!h) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+  int e = h->device_error;
+  h->device_error = SHO_OK;
+  return e;
+}
+
+int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
+                const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* coeff,
+                sho_dtype coeff_dtype, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
+  SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
+  SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!psi || !coeff) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  ProjectLaunch L;
+  L.g = make_grid(grid, cube, nbands);
+  L.psi = psi;
+  L.psi_dtype = psi_dtype;
+  L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
+  L.natoms = natoms;
+  L.numax = numax;
+  L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
+  L.coeff = coeff;
+  L.coeff_dtype = coeff_dtype;
+  L.stream = s;
+  if (launch_project(L) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype coeff_dtype, int nbands, int natoms,
+            const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
+            sho_dtype psi_dtype, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
+  SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
+  SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!psi || !coeff) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  std::vector<int> ptr, list;
+  plane_lists(grid, at, cube, ptr, list);
+  const size_t tc = compute_size(coeff_dtype);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  const size_t o_ptr = cv.take(ptr.size() * sizeof(int));
+  const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
+  const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
+  const size_t o_t2 = cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  SHO_TRY(upload(h, o_ptr, ptr.data(), ptr.size() * sizeof(int), s));
+  SHO_TRY(upload(h, o_list, list.data(), list.size() * sizeof(int), s));
+  char* ws = static_cast<char*>(h->ws);
+  ExpandLaunch L;
+  L.g = make_grid(grid, cube, nbands);
+  L.coeff = coeff;
+  L.coeff_dtype = coeff_dtype;
+  L.psi = psi;
+  L.psi_dtype = psi_dtype;
+  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  L.natoms = natoms;
+  L.numax = numax;
+  L.plane_ptr = reinterpret_cast<const int*>(ws + o_ptr);
+  L.plane_atoms = reinterpret_cast<const int*>(ws + o_list);
+  L.tables = ws + o_tab;
+  L.t2 = ws + o_t2;
+  L.stream = s;
+  if (launch_expand(L) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
+               const double* pos, const double* sigma, int numax, int cube, sho_prec prec, const void* dEdc,
+               sho_dtype coeff_dtype, double* dEdX, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
+  SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
+  SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  if (natoms == 0) return SHO_OK;
+  if (!dEdX) return SHO_ERR_ARG;
+  if (nbands > 0 && (!psi || !dEdc)) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (nbands == 0) {
+    SHO_TRY(begin_call(h, s));
+    if (cudaMemsetAsync(dEdX, 0, sizeof(double) * 3 * (size_t)natoms, s) != cudaSuccess) return SHO_ERR_CUDA;
+    return end_call(h, s);
+  }
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  const size_t tc = compute_size(coeff_dtype);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  const size_t o_cp = cv.take((size_t)natoms * nstates(numax + 1) * (size_t)nbands * tc);
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  char* ws = static_cast<char*>(h->ws);
+  ProjectLaunch P;
+  P.g = make_grid(grid, cube, nbands);
+  P.psi = psi;
+  P.psi_dtype = psi_dtype;
+  P.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  P.natoms = natoms;
+  P.numax = numax + 1;
+  P.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
+  P.coeff = ws + o_cp;
+  P.coeff_dtype = coeff_dtype;
+  P.stream = s;
+  if (launch_project(P) != cudaSuccess) return SHO_ERR_CUDA;
+  ForcesLaunch F;
+  F.natoms = natoms;
+  F.numax = numax;
+  F.nbands = nbands;
+  F.atoms = P.atoms;
+  F.cp = ws + o_cp;
+  F.dEdc = dEdc;
+  F.coeff_dtype = coeff_dtype;
+  F.dEdX = dEdX;
+  F.stream = s;
+  if (launch_forces_contract(F) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// sho_expand.cu -- SHO expansion on CUDA cores (FP64 and FP32 forms).
+//
+//   psi[j][b] += sum_a sum_k coeff[a][k][b] Psi_k(u)          (Sec. 3.2 step 3; adjoint of projection)
+//
+// evaluated with the passes of the projection in reverse order (z, then y, then x):
+//   z-pass  T2[a][z][(nx,ny)][b] = sum_nz coeff[a][(nx,ny,nz)][b] phi_nz(z)      C N FMAs per atom-band
+//   y-pass  T1[nx]               = sum_ny T2[(nx,ny)] phi_ny(y)                  C^2 P
+//   x-pass  psi[z][y][x][b]     += sum_nx T1[nx] phi_nx(x)                       C^3 (numax+1)
+//
+// Kernel 1 (one warp per atom and 32-band tile) runs the z-pass and writes the x and y function
+// tables; both go to the handle's workspace.  Kernel 2 is a gather over grid rows: one warp per
+// (grid row (z, y), 32-band tile) loads the row once into shared memory, adds the y- and x-passes of
+// every atom whose cube covers the row in ascending atom order, and writes the row back once.  No
+// atomics: every psi element is written by exactly one warp, in a fixed order (deterministic).
+#include "sho_device.cuh"
+
+namespace sho {
+
+// ------------------------------------------------------------------------------ kernel 1: z-pass
+template <int NU, typename TCo, typename TC>
+__global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
+                                                        const TCo* __restrict__ coeff, TC* __restrict__ tables,
+                                                        TC* __restrict__ t2) {
+  using BS = Basis<NU>;
+  constexpr int NP = BS::NP, P = BS::P, N = BS::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = g.cube;
+  TC* phz = reinterpret_cast<TC*>(smem_raw);  // [NP][C]
+  const int lane = threadIdx.x;
+  const int a = blockIdx.y;
+  const int B = g.nbands;
+  const int b = blockIdx.x * kWarp + lane;
+  const bool bok = b < B;
+  const AtomDev at = atoms[a];
+
+  TC* tx = tables + (size_t)a * 2 * NP * C;  // [NP][C]
+  TC* ty = tx + (size_t)NP * C;              // [NP][C]
+  for (int i = lane; i < C; i += kWarp) {
+    phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
+    if (blockIdx.x == 0) {
+      phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, tx + i, C);
+      phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, ty + i, C);
+    }
+  }
+  __syncwarp();
+  if (!bok) return;
+
+  const TCo* ca = coeff + (size_t)a * N * B + b;
+  TC* out = t2 + (size_t)a * C * P * B + b;
+#pragma unroll
+  for (int ny = 0; ny < NP; ny++) {
+#pragma unroll
+    for (int nx = 0; nx + ny <= NU; nx++) {
+      TC cz[NP];
+#pragma unroll
+      for (int nz = 0; nz < NP; nz++)
+        cz[nz] = (nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * B], (TC)0) : (TC)0;
+      const int p = BS::pair(nx, ny);
+      for (int iz = 0; iz < C; iz++) {
+        TC s = (TC)0;
+#pragma unroll
+        for (int nz = 0; nz + nx + ny <= NU; nz++) s = fma(cz[nz], phz[nz * C + iz], s);
+        out[((size_t)iz * P + p) * B] = s;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ kernel 2: rows
+template <int NU, typename TP, typename TC>
+__global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev* __restrict__ atoms,
+                                                       const int* __restrict__ plane_ptr,
+                                                       const int* __restrict__ plane_atoms,
+                                                       const TC* __restrict__ tables, const TC* __restrict__ t2,
+                                                       TP* __restrict__ psi) {
+  using BS = Basis<NU>;
+  constexpr int NP = BS::NP, P = BS::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* acc = reinterpret_cast<TC*>(smem_raw);  // [Nx][32]
+  const int C = g.cube;
+  const int Nx = g.n[0], Ny = g.n[1];
+  const int lane = threadIdx.x;
+  const int r = blockIdx.x;
+  const int z = r / Ny, y = r - z * Ny;
+  const int B = g.nbands;
+  const int b = blockIdx.y * kWarp + lane;
+  const bool bok = b < B;
+  const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+
+  // Does any atom's cube cover this row?  (Rows outside every cube are not touched at all.)
+  bool any = false;
+  for (int q = q0; q < q1 && !any; q++) {
+    const int oy = atoms[plane_atoms[q]].o[1];
+    int iy = y - oy;
+    if (g.periodic) {
+      iy %= Ny;
+      if (iy < 0) iy += Ny;
+    }
+    any = (iy >= 0 && iy < C);
+  }
+  if (!any) return;
+
+  TP* row = psi + (size_t)r * Nx * B + b;
+  for (int jx = 0; jx < Nx; jx++) acc[jx * kWarp + lane] = bok ? to_real(row[(size_t)jx * B], (TC)0) : (TC)0;
+
+  for (int q = q0; q < q1; q++) {
+    const int a = plane_atoms[q];
+    const AtomDev at = atoms[a];
+    int iy = y - at.o[1], iz = z - at.o[2];
+    if (g.periodic) {
+      iy %= Ny;
+      if (iy < 0) iy += Ny;
+      iz %= g.n[2];
+      if (iz < 0) iz += g.n[2];
+    }
+    if (iy < 0 || iy >= C) continue;
+    const TC* tx = tables + (size_t)a * 2 * NP * C;
+    const TC* ty = tx + (size_t)NP * C;
+    // y-pass (a6, middle pass)
+    const TC* t2a = t2 + ((size_t)a * C + iz) * P * B + b;
+    TC t2r[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) t2r[p] = bok ? t2a[(size_t)p * B] : (TC)0;
+    TC t1[NP];
+#pragma unroll
+    for (int nx = 0; nx < NP; nx++) t1[nx] = (TC)0;
+#pragma unroll
+    for (int ny = 0; ny < NP; ny++) {
+      const TC w = ty[ny * C + iy];
+#pragma unroll
+      for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fma(t2r[BS::pair(nx, ny)], w, t1[nx]);
+    }
+    // x-pass (a6, last pass) into the row accumulator
+    for (int ix = 0; ix < C; ix++) {
+      const int jx = cube_index(at.o[0], ix, Nx, g.periodic);
+      if (jx < 0) continue;
+      TC s = acc[jx * kWarp + lane];
+#pragma unroll
+      for (int nx = 0; nx < NP; nx++) s = fma(t1[nx], tx[nx * C + ix], s);
+      acc[jx * kWarp + lane] = s;
+    }
+  }
+  if (bok)
+    for (int jx = 0; jx < Nx; jx++) row[(size_t)jx * B] = store_cast(acc[jx * kWarp + lane], (TP*)nullptr);
+}
+
+template <int NU, typename TP, typename TCo, typename TC>
+static cudaError_t launch_expand_t(const ExpandLaunch& p) {
+  const int C = p.g.cube;
+  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  {
+    const size_t smem = (size_t)(NU + 1) * C * sizeof(TC);
+    k_expand_zpass<NU, TCo, TC><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+        p.g, p.atoms, static_cast<const TCo*>(p.coeff), static_cast<TC*>(p.tables), static_cast<TC*>(p.t2));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  {
+    auto kern = k_expand_rows<NU, TP, TC>;
+    const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(TC);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(p.g.n[1] * p.g.n[2], nbt), kWarp, smem, p.stream>>>(
+        p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const TC*>(p.tables), static_cast<const TC*>(p.t2),
+        static_cast<TP*>(p.psi));
+    return cudaGetLastError();
+  }
+}
+
+template <int NU>
+static cudaError_t launch_expand_nu(const ExpandLaunch& p) {
+  if (p.coeff_dtype == SHO_F64) {
+    if (p.psi_dtype == SHO_F64) return launch_expand_t<NU, double, double, double>(p);
+    return cudaErrorInvalidValue;
+  }
+  if (p.psi_dtype == SHO_F32) return launch_expand_t<NU, float, float, float>(p);
+  if (p.psi_dtype == SHO_BF16) return launch_expand_t<NU, __nv_bfloat16, float, float>(p);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_expand(const ExpandLaunch& p) {
+  switch (p.numax) {
+    case 0: return launch_expand_nu<0>(p);
+    case 1: return launch_expand_nu<1>(p);
+    case 2: return launch_expand_nu<2>(p);
+    case 3: return launch_expand_nu<3>(p);
+    case 4: return launch_expand_nu<4>(p);
+    case 5: return launch_expand_nu<5>(p);
+    case 6: return launch_expand_nu<6>(p);
+    case 7: return launch_expand_nu<7>(p);
+    case 8: return launch_expand_nu<8>(p);
+    case 9: return launch_expand_nu<9>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sho

@@ -1,0 +1,89 @@
+// sho_internal.h -- structures shared by the host API and the kernels of libsho (not installed).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sho.h"
+
+namespace sho {
+
+constexpr int kMaxCube = 64;      // largest cube edge (points), a multiple of 8
+constexpr int kWarp = 32;         // bands per warp tile
+constexpr int kMaxTableNu = SHO_MAX_NUMAX + 1;  // forces project at numax + 1
+constexpr int kMaxStates = (SHO_MAX_NUMAX + 1) * (SHO_MAX_NUMAX + 2) * (SHO_MAX_NUMAX + 3) / 6;
+
+// Per-atom data uploaded by the host plan: position, width and the integer cube origin
+// o_d = floor(X_d / h) - cube/2 + 1 computed on the host.
+struct AtomDev {
+  double X[3];
+  double sigma;
+  int o[3];
+  int pad;
+};
+static_assert(sizeof(AtomDev) == 48, "AtomDev layout");
+
+// Geometry common to all kernels.
+struct GridDev {
+  int n[3];          // Nx, Ny, Nz
+  int periodic;
+  double h;
+  int cube;
+  int nbands;
+};
+
+enum class Real { F64, F32 };
+
+struct ProjectLaunch {
+  GridDev g;
+  const void* psi;          // [Nz][Ny][Nx][B]
+  sho_dtype psi_dtype;
+  const AtomDev* atoms;     // device [A]
+  int natoms;
+  int numax;
+  int zsplit;               // cube z-planes split over this many CTAs of one cluster
+  void* coeff;              // [A][N][B], FP64 or FP32
+  sho_dtype coeff_dtype;
+  cudaStream_t stream;
+};
+
+struct ExpandLaunch {
+  GridDev g;
+  const void* coeff;        // [A][N][B]
+  sho_dtype coeff_dtype;
+  void* psi;                // [Nz][Ny][Nx][B], read-modify-write
+  sho_dtype psi_dtype;
+  const AtomDev* atoms;     // device [A]
+  int natoms;
+  int numax;
+  const int* plane_ptr;     // [Nz + 1]: atoms whose cube covers plane z are
+  const int* plane_atoms;   //   plane_atoms[plane_ptr[z] .. plane_ptr[z+1]), ascending
+  void* tables;             // workspace [A][2][numax+1][cube] of the compute type (x and y tables)
+  void* t2;                 // workspace [A][cube][P][B] of the compute type (z-pass result)
+  cudaStream_t stream;
+};
+
+struct ForcesLaunch {
+  int natoms;
+  int numax;                // numax of dEdc; cp holds numax + 1
+  int nbands;
+  const AtomDev* atoms;
+  const void* cp;           // [A][N(numax+1)][B], compute type
+  const void* dEdc;         // [A][N(numax)][B], coefficient type
+  sho_dtype coeff_dtype;
+  double* dEdX;             // [A][3]
+  cudaStream_t stream;
+};
+
+// Kernel launchers (return a CUDA error code).
+cudaError_t launch_project(const ProjectLaunch& p);
+cudaError_t launch_expand(const ExpandLaunch& p);
+cudaError_t launch_forces_contract(const ForcesLaunch& p);
+
+// Bytes of compute-type scalars for a dtype.
+inline size_t compute_size(sho_dtype coeff_dtype) { return coeff_dtype == SHO_F64 ? 8 : 4; }
+
+inline int nstates(int nu) { return nu < 0 ? 0 : (nu + 1) * (nu + 2) * (nu + 3) / 6; }
+inline int npairs(int nu) { return nu < 0 ? 0 : (nu + 1) * (nu + 2) / 2; }
+
+}  // namespace sho
