@@ -154,6 +154,35 @@ int sho_forces(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dt
                int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                const void* dEdc, sho_dtype coeff_dtype, double* dEdX, void* stream);
 
+/* Size of the fixed device scratch array of sho_forces_noalloc: 16 MiB. */
+#define SHO_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/*
+ * Allocation-free forces.  The paper has no counterpart to this entry point; it exists for callers
+ * that cannot let a library allocate device memory -- for example an application whose own pool
+ * allocator owns all device memory, a plug-in inside a host program that forbids foreign
+ * allocations, or a process so close to its memory limit that an allocation could fail mid-step.
+ *
+ * It computes what sho_forces computes, with the same arguments minus the handle, on the device that
+ * is current for the calling thread and on `stream`.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch (the per-atom plan and the numax+1 projection) is one file-scope
+ * static device array of SHO_NOALLOC_SCRATCH_BYTES, loaded with the library, which every GPU that
+ * loads libsho.so holds until the process exits.
+ *   limit     ceil256(48 * natoms) + natoms * sho_nstates(numax + 1) * nbands * s <= SHO_NOALLOC_SCRATCH_BYTES,
+ *             s = 8 for SHO_P_FP64 and 4 for SHO_P_FP32; larger problems return SHO_ERR_CAPACITY before
+ *             anything is enqueued.
+ *   set-up    the first call on a device looks up the array's device address once (the device must be
+ *             current, which it is for that call); make that first call before any stream capture.
+ *   sharing   all calls on a device share the array and it keeps the last call's contents; each call
+ *             writes every scratch element before reading it, so nothing needs clearing.  Calls whose
+ *             GPU work overlaps (different streams with no ordering between them) race on the array:
+ *             order them, for instance on one stream.
+ * Precisions: SHO_P_FP64 (psi, dEdc F64) and SHO_P_FP32 (psi F32/BF16, dEdc F32).
+ */
+int sho_forces_noalloc(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
+                       const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                       const void* dEdc, sho_dtype coeff_dtype, double* dEdX, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
