@@ -164,26 +164,32 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workloads.WORKLOADS[WORKLOAD]
+    w = workloads.WORKLOADS[args.workload]
+    if args.bands:
+        w = workloads.Workload(**{**w.__dict__, "nbands": args.bands})
+    prec = args.prec or ("fp64" if w.dtype == "f64" else "fp32")
+    sdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.storage or w.dtype]
+    cdt = torch.float64 if prec == "fp64" else torch.float32
+    elem = torch.tensor([], dtype=sdt).element_size()
     # every rank runs its own replica with its own seed stream (weak scaling)
     rng = np.random.default_rng([w.seed, rank])
     pos, sig = workloads.atoms(w, rng if rank else None)
     nst = api.nstates(w.numax)
-    alg = algorithmic(w, pos, nst)
+    alg = algorithmic(w, pos, nst, elem=elem)
     g = torch.Generator(device=dev)
     g.manual_seed(w.seed + 7919 * rank)
     nx, ny, nz = w.grid
-    psi = torch.randn((nz, ny, nx, w.nbands), generator=g, device=dev, dtype=torch.float64)
-    cin = torch.randn((w.natoms, nst, w.nbands), generator=g, device=dev, dtype=torch.float64)
+    psi = torch.randn((nz, ny, nx, w.nbands), generator=g, device=dev, dtype=torch.float64).to(sdt)
+    cin = torch.randn((w.natoms, nst, w.nbands), generator=g, device=dev, dtype=torch.float64).to(cdt)
     hpsi = torch.zeros_like(psi)
-    coeff = torch.empty((w.natoms, nst, w.nbands), dtype=torch.float64, device=dev)
+    coeff = torch.empty((w.natoms, nst, w.nbands), dtype=cdt, device=dev)
     handle = api.Handle(local)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
                     stream=stream)
-        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -200,10 +206,10 @@ def run_ours(args, ws, rank, local):
     t0.record(stream)
     for i in range(K):
         ev[i][0].record(stream)
-        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
                     stream=stream)
         ev[i][1].record(stream)
-        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle, stream=stream)
         ev[i][2].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -229,10 +235,10 @@ def run_ours(args, ws, rank, local):
     def e2e_step():
         psi_d.copy_(psi_h, non_blocking=True)
         cin_d.copy_(cin_h, non_blocking=True)
-        api.project(psi_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+        api.project(psi_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
                     stream=stream)
         hpsi.zero_()
-        api.add(hpsi, cin_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+        api.add(hpsi, cin_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle, stream=stream)
         out_h.copy_(hpsi, non_blocking=True)
 
     for _ in range(max(1, args.warmup)):
@@ -248,16 +254,30 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(ws, e0.elapsed_time(e1) / K2)
-    h2d = psi.numel() * 8 + cin.numel() * 8
-    d2h = psi.numel() * 8
+    h2d = psi.numel() * psi.element_size() + cin.numel() * cin.element_size()
+    d2h = psi.numel() * psi.element_size()
 
     result = None
     if rank == 0:
         peaks = _peaks()
         dom = "k_project" if t_prj >= t_add else "k_expand"
         t_dom = max(t_prj, t_add)
-        flops_dom = alg["flops_prj"] if dom == "k_project" else alg["flops_add"]
-        achieved = flops_dom / (t_dom * 1e-3) / 1e12
+        if prec == "fp64":
+            flops_dom = alg["flops_prj"] if dom == "k_project" else alg["flops_add"]
+            achieved = flops_dom / (t_dom * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                    "peak_source": "measured FP64 DFMA throughput (152 SMs x 4 flop/clk)"}
+        else:
+            bytes_dom = alg["bytes_prj"] if dom == "k_project" else alg["bytes_add"]
+            achieved = bytes_dom / (t_dom * 1e-3) / 1e9
+            hbm = peaks.get("hbm_gbs", 6793.4)
+            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+        wl = {"c96": "periodic 96^3 grid, h=0.2, 64 atoms, sigma U[0.5,1], numax 5 (56 states), cube 32^3",
+              "c160": "periodic 160^3 grid, h=0.2, 512 atoms, sigma U[0.5,1], numax 7 (120 states), cube 32^3",
+              "c128": "periodic 128^3 grid, h=0.2, 128 atoms, sigma U[0.5,1], numax 5 (56 states), cube 32^3",
+              "tiny": "16^3 grid, h=0.25, 1 atom, numax 3, cube 16"}[args.workload]
         result = {
             "metric": METRIC,
             "value": round(value, 3),
@@ -269,38 +289,164 @@ def run_ours(args, ws, rank, local):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
+                      "split_fp16": "split-f16"}[prec],
             "data": "synthetic (seeded N(0,1) psi and coefficients, uniform atoms with min separation 2.0)",
             "config": {
-                "workload": "periodic 96^3 grid, h=0.2, 64 atoms, sigma U[0.5,1], numax 5 (56 states), cube 32^3, "
-                            "128 bands, FP64: project then expand",
+                "workload": f"{wl}, {w.nbands} bands, psi {args.storage or w.dtype}, {prec} arithmetic: "
+                            "project then expand",
                 "global_batch": w.nbands * ws,
                 "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                "l2": "inputs larger than L2 (psi 906 MB per buffer), no flush",
+                "l2": f"inputs larger than L2 (psi {psi.numel() * psi.element_size() / 1e6:.0f} MB per buffer), "
+                      "no flush",
                 "union_cube_points": alg["union_points"],
                 "algorithmic_bytes_per_step": bytes_step,
             },
             "kernels_ms": {"project": round(t_prj, 4), "expand": round(t_add, 4)},
             "hbm_fraction": round(value / ws / peaks.get("hbm_gbs", 6793.4), 4),
-            "roofline": {
-                "bound": "alu",
-                "kernel": dom,
-                "achieved": round(achieved, 4),
-                "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "traffic": None,
-                "peak_source": "measured FP64 DFMA throughput (152 SMs x 4 flop/clk)",
-            },
+            "roofline": roof,
             "e2e": {"value": round(ws * bytes_step / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                     "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * K,
             "clocks": clk,
         }
+        default_case = args.workload == WORKLOAD and prec == "fp64" and not args.bands
+        if not default_case:
+            args.no_same_gpu_baselines = args.no_precision_forms = args.no_cpu_baseline = True
+        if not args.no_same_gpu_baselines:
+            result["same_gpu_baselines"] = same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream)
+        if not args.no_precision_forms:
+            del hpsi, psi_h, out_h, psi_d, cin_d
+            torch.cuda.empty_cache()
+            result["precision_forms"] = precision_forms(api, handle, stream)
         if not args.no_cpu_baseline and ws == 1:
             result["cpu_baseline"], result["error_vs_oracle"] = cpu_baseline(
                 w, pos, sig, psi, cin, coeff, hpsi_ref=None, api=api, handle=handle)
     return result
+
+
+def _time_steps(stream, fn, warmup=2, steps=5):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream):
+    """The same project + expand step on the same GPU with (1) stored FP64 projector values (the
+    conventional scheme of the paper's comparison, Sec. 6) and (2) the FP32 CUDA-core form."""
+    import torch
+    out = {}
+    bytes_step = alg["bytes_prj"] + alg["bytes_add"]
+    proj = api.usu_build(pos, sig, w.numax, w.cube, w.grid, w.h, w.periodic, device=psi.device.index or 0,
+                         handle=handle, stream=stream)
+    coeff = torch.empty_like(cin)
+    hpsi = torch.zeros_like(psi)
+
+    def usu_step():
+        api.usu_project(psi, proj, pos, sig, w.numax, w.cube, w.h, w.periodic, out=coeff, handle=handle,
+                        stream=stream)
+        api.usu_add(hpsi, cin, proj, pos, sig, w.numax, w.cube, w.h, w.periodic, handle=handle, stream=stream)
+
+    ms = _time_steps(stream, usu_step)
+    out["stored_projector_fp64"] = {"value": round(bytes_step / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+                                    "ms_per_step": round(ms, 4), "projector_bytes": proj.numel() * 8}
+    del proj, hpsi
+    psi32 = psi.float()
+    cin32 = cin.float()
+    c32 = torch.empty(cin.shape, dtype=torch.float32, device=psi.device)
+    h32 = torch.zeros_like(psi32)
+
+    def fp32_step():
+        api.project(psi32, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp32", out=c32, handle=handle,
+                    stream=stream)
+        api.add(h32, cin32, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp32", handle=handle, stream=stream)
+
+    ms32 = _time_steps(stream, fp32_step)
+    bytes32 = bytes_step // 2
+    out["fp32_cuda_cores"] = {"value": round(bytes32 / (ms32 * 1e-3) / 1e9, 3), "unit": "GB/s",
+                              "ms_per_step": round(ms32, 4), "note": "same workload with psi and coefficients in FP32"}
+    del psi32, h32
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_forms(api, handle, stream, modes=("fp32", "tf32", "3xtf32", "bf16", "split_fp16"),
+                    storages=("f32", "bf16"), steps=5):
+    """The 160^3 / 512-atom / numax 7 / 256-band workload in every reduced-precision form: project +
+    expand throughput and the error against the plain FP64 SHO form run on the same GPU on the same
+    storage-rounded psi (norm-wise over all coefficients / the whole expanded grid)."""
+    import torch
+    w = workloads.WORKLOADS["c160"]
+    pos, sig = workloads.atoms(w)
+    nst = api.nstates(w.numax)
+    alg = algorithmic(w, pos, nst, elem=4)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev)
+    g.manual_seed(w.seed)
+    nx, ny, nz = w.grid
+    cin = torch.randn((w.natoms, nst, w.nbands), generator=g, device=dev, dtype=torch.float32)
+    out = {"workload": "periodic 160^3, h=0.2, 512 atoms, numax 7 (120 states), cube 32, 256 bands",
+           "reference": "FP64 SHO form on the same GPU, same storage-rounded psi",
+           "union_cube_points": alg["union_points"], "forms": {}}
+    for st in storages:
+        tdt = torch.float32 if st == "f32" else torch.bfloat16
+        psi = torch.randn((nz, ny, nx, w.nbands), generator=g, device=dev, dtype=torch.float32).to(tdt)
+        # FP64 references of this storage
+        psi64 = psi.double()
+        c_ref = api.project(psi64, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle,
+                            stream=stream)
+        del psi64
+        e_ref = torch.zeros((nz, ny, nx, w.nbands), dtype=torch.float64, device=dev)
+        api.add(e_ref, cin.double(), pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle,
+                stream=stream)
+        elem = 4 if st == "f32" else 2
+        bytes_step = alg["bytes_prj"] * elem // 4 + alg["bytes_add"] * elem // 4
+        coeff = torch.empty((w.natoms, nst, w.nbands), dtype=torch.float32, device=dev)
+        hpsi = torch.zeros_like(psi)
+        for mode in modes:
+            def step():
+                api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=mode, out=coeff, handle=handle,
+                            stream=stream)
+                api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=mode, handle=handle,
+                        stream=stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step()
+            torch.cuda.synchronize()
+            t_prj, t_add = [], []
+            for _ in range(steps):
+                ev[0].record(stream)
+                api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=mode, out=coeff, handle=handle,
+                            stream=stream)
+                ev[1].record(stream)
+                api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=mode, handle=handle,
+                        stream=stream)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                t_prj.append(ev[0].elapsed_time(ev[1]))
+                t_add.append(ev[1].elapsed_time(ev[2]))
+            ms = float(np.median(t_prj) + np.median(t_add))
+            err_c = float(torch.linalg.vector_norm(coeff.double() - c_ref) / torch.linalg.vector_norm(c_ref))
+            hpsi.zero_()
+            api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=mode, handle=handle, stream=stream)
+            err_e = float(torch.linalg.vector_norm(hpsi.double() - e_ref) / torch.linalg.vector_norm(e_ref))
+            gbs = bytes_step / (ms * 1e-3) / 1e9
+            out["forms"][f"{st}/{mode}"] = {
+                "ms_project": round(float(np.median(t_prj)), 4), "ms_expand": round(float(np.median(t_add)), 4),
+                "GB/s": round(gbs, 2), "hbm_frac": round(gbs / _peaks().get("hbm_gbs", 6793.4), 4),
+                "err_project": err_c, "err_expand": err_e}
+            hpsi.zero_()
+        del psi, hpsi, e_ref, c_ref
+        torch.cuda.empty_cache()
+    return out
 
 
 def _oracle_sample(w, pos, sig, nsel, nbands_sel, seed=5):
@@ -394,6 +540,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-same-gpu-baselines", action="store_true")
+    ap.add_argument("--no-precision-forms", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
+    ap.add_argument("--storage", default=None, choices=["f64", "f32", "bf16"])
+    ap.add_argument("--bands", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

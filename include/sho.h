@@ -119,7 +119,9 @@ int sho_sync(sho_handle* handle);
  *   psi    device [n[2]][n[1]][n[0]][nbands], type psi_dtype (read only)
  *   coeff  device [natoms][sho_nstates(numax)][nbands], type coeff_dtype (written, fully)
  * Supported: (SHO_P_FP64, psi F64, coeff F64); (SHO_P_FP32 | TF32 | 3XTF32 | BF16 | SPLIT_FP16,
- * psi F32 or BF16, coeff F32).  natoms == 0 or nbands == 0 is a no-op returning SHO_OK.
+ * psi F32 or BF16, coeff F32).  The tensor-core forms (TF32, 3XTF32, BF16, SPLIT_FP16) need
+ * numax <= 7 (SHO_ERR_NUMAX otherwise; for sho_forces numax + 1 <= 7) and a cube that is a multiple
+ * of 16 (SHO_ERR_CUBE).  natoms == 0 or nbands == 0 is a no-op returning SHO_OK.
  */
 int sho_project(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                 int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
@@ -153,6 +155,26 @@ int sho_add(sho_handle* handle, const sho_grid* grid, const void* coeff, sho_dty
 int sho_forces(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                const void* dEdc, sho_dtype coeff_dtype, double* dEdX, void* stream);
+
+/* ----------------------------------------------------------------------------------------------
+ * Stored-projector FP64 baseline: the conventional scheme the paper measures against ("USU", Sec. 6,
+ * Table 1): projector values sampled once onto each atom's cube and kept in device memory, then
+ * streamed by the projection and expansion.  Same definitions, conventions and results as
+ * sho_project / sho_add in SHO_P_FP64 (up to rounding order); numax <= SHO_USU_MAX_NUMAX (the paper's
+ * Table 1 goes up to 56 coefficients, numax 5).
+ *   proj   device [natoms][cube^3][sho_nstates(numax)] double, cube point index (iz*cube + iy)*cube + ix;
+ *          written by sho_usu_build, read by the other two (caller allocates: 8 * A * C^3 * N bytes).
+ *   psi, coeff as for sho_project / sho_add, FP64 only.  pos / sigma host arrays as above.
+ */
+#define SHO_USU_MAX_NUMAX 5
+int sho_usu_build(sho_handle* handle, const sho_grid* grid, int natoms, const double* pos, const double* sigma,
+                  int numax, int cube, double* proj, void* stream);
+int sho_usu_project(sho_handle* handle, const sho_grid* grid, const double* psi, int nbands, int natoms,
+                    const double* pos, const double* sigma, int numax, int cube, const double* proj,
+                    double* coeff, void* stream);
+int sho_usu_add(sho_handle* handle, const sho_grid* grid, const double* coeff, int nbands, int natoms,
+                const double* pos, const double* sigma, int numax, int cube, const double* proj, double* psi,
+                void* stream);
 
 /* Size of the fixed device scratch array of sho_forces_noalloc: 16 MiB. */
 #define SHO_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)

@@ -83,7 +83,7 @@ int check_dtypes(sho_prec prec, sho_dtype psi_dt, sho_dtype coeff_dt) {
     case SHO_P_3XTF32:
     case SHO_P_BF16:
     case SHO_P_SPLIT_FP16:
-      return SHO_ERR_DTYPE;  // tensor-core forms are not part of this build
+      return ((psi_dt == SHO_F32 || psi_dt == SHO_BF16) && coeff_dt == SHO_F32) ? SHO_OK : SHO_ERR_DTYPE;
     default:
       return SHO_ERR_ARG;
   }
@@ -184,6 +184,15 @@ int upload(sho_handle* h, size_t off, const void* src, size_t bytes, cudaStream_
   if (bytes == 0) return SHO_OK;
   if (cudaMemcpyAsync(static_cast<char*>(h->ws) + off, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return SHO_ERR_CUDA;
+  return SHO_OK;
+}
+
+// Extra limits of the tensor-core forms: numax (of the projection actually run) <= 7 and a cube of
+// whole 16-point MMA steps.
+int check_tc(sho_prec prec, int numax_run, int cube) {
+  if (!is_tc(prec)) return SHO_OK;
+  if (numax_run > kTcMaxNumax) return SHO_ERR_NUMAX;
+  if (cube % 16) return SHO_ERR_CUBE;
   return SHO_OK;
 }
 
@@ -293,6 +302,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
+  SHO_TRY(check_tc(prec, numax, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!psi || !coeff) return SHO_ERR_ARG;
@@ -316,7 +326,8 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
   L.stream = s;
-  if (launch_project(L) != cudaSuccess) return SHO_ERR_CUDA;
+  const cudaError_t e = is_tc(prec) ? launch_project_tc(L, prec) : launch_project(L);
+  if (e != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
 }
 
@@ -326,6 +337,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
+  SHO_TRY(check_tc(prec, numax, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!psi || !coeff) return SHO_ERR_ARG;
@@ -362,7 +374,8 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   L.tables = ws + o_tab;
   L.t2 = ws + o_t2;
   L.stream = s;
-  if (launch_expand(L) != cudaSuccess) return SHO_ERR_CUDA;
+  const cudaError_t e = is_tc(prec) ? launch_expand_tc(L, prec) : launch_expand(L);
+  if (e != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
 }
 
@@ -372,6 +385,7 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
+  SHO_TRY(check_tc(prec, numax + 1, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
   if (natoms == 0) return SHO_OK;
   if (!dEdX) return SHO_ERR_ARG;
@@ -404,7 +418,8 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   P.coeff = ws + o_cp;
   P.coeff_dtype = coeff_dtype;
   P.stream = s;
-  if (launch_project(P) != cudaSuccess) return SHO_ERR_CUDA;
+  const cudaError_t e = is_tc(prec) ? launch_project_tc(P, prec) : launch_project(P);
+  if (e != cudaSuccess) return SHO_ERR_CUDA;
   ForcesLaunch F;
   F.natoms = natoms;
   F.numax = numax;
@@ -416,6 +431,100 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   F.dEdX = dEdX;
   F.stream = s;
   if (launch_forces_contract(F) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+// ------------------------------------------------------------------ stored-projector baseline
+int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double* pos, const double* sigma, int numax,
+                  int cube, double* proj, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, 0, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
+  if (natoms == 0) return SHO_OK;
+  if (!proj) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  UsuLaunch L = {};
+  L.g = make_grid(grid, cube, 0);
+  L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
+  L.natoms = natoms;
+  L.numax = numax;
+  L.proj = proj;
+  L.stream = s;
+  if (launch_usu(0, L) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int nbands, int natoms,
+                    const double* pos, const double* sigma, int numax, int cube, const double* proj, double* coeff,
+                    void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!psi || !proj || !coeff) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  UsuLaunch L = {};
+  L.g = make_grid(grid, cube, nbands);
+  L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
+  L.natoms = natoms;
+  L.numax = numax;
+  L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
+  L.proj = const_cast<double*>(proj);
+  L.psi_in = psi;
+  L.coeff_out = coeff;
+  L.stream = s;
+  if (launch_usu(1, L) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+int sho_usu_add(sho_handle* h, const sho_grid* grid, const double* coeff, int nbands, int natoms, const double* pos,
+                const double* sigma, int numax, int cube, const double* proj, double* psi, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!psi || !proj || !coeff) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  std::vector<int> ptr, list;
+  plane_lists(grid, at, cube, ptr, list);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  const size_t o_ptr = cv.take(ptr.size() * sizeof(int));
+  const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  SHO_TRY(upload(h, o_ptr, ptr.data(), ptr.size() * sizeof(int), s));
+  SHO_TRY(upload(h, o_list, list.data(), list.size() * sizeof(int), s));
+  char* ws = static_cast<char*>(h->ws);
+  UsuLaunch L = {};
+  L.g = make_grid(grid, cube, nbands);
+  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  L.natoms = natoms;
+  L.numax = numax;
+  L.proj = const_cast<double*>(proj);
+  L.coeff_in = coeff;
+  L.psi_out = psi;
+  L.plane_ptr = reinterpret_cast<const int*>(ws + o_ptr);
+  L.plane_atoms = reinterpret_cast<const int*>(ws + o_list);
+  L.stream = s;
+  if (launch_usu(2, L) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
 }
 

@@ -130,14 +130,26 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
 #pragma unroll
       for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fma(t2r[BS::pair(nx, ny)], w, t1[nx]);
     }
-    // x-pass (a6, last pass) into the row accumulator
-    for (int ix = 0; ix < C; ix++) {
-      const int jx = cube_index(at.o[0], ix, Nx, g.periodic);
-      if (jx < 0) continue;
-      TC s = acc[jx * kWarp + lane];
+    // x-pass (a6, last pass) into the row accumulator: eight x points at a time, each chain seeded
+    // with the accumulator value, so eight independent FMA chains are in flight and every point
+    // costs exactly numax+1 FMAs.
+    for (int ix0 = 0; ix0 < C; ix0 += 8) {
+      int jx[8];
+      TC s[8];
 #pragma unroll
-      for (int nx = 0; nx < NP; nx++) s = fma(t1[nx], tx[nx * C + ix], s);
-      acc[jx * kWarp + lane] = s;
+      for (int u = 0; u < 8; u++) {
+        jx[u] = cube_index(at.o[0], ix0 + u, Nx, g.periodic);
+        s[u] = jx[u] >= 0 ? acc[jx[u] * kWarp + lane] : (TC)0;
+      }
+#pragma unroll
+      for (int nx = 0; nx < NP; nx++) {
+        const TC w = t1[nx];
+#pragma unroll
+        for (int u = 0; u < 8; u++) s[u] = fma(w, tx[nx * C + ix0 + u], s[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++)
+        if (jx[u] >= 0) acc[jx[u] * kWarp + lane] = s[u];
     }
   }
   if (bok)
@@ -176,6 +188,29 @@ static cudaError_t launch_expand_nu(const ExpandLaunch& p) {
   if (p.psi_dtype == SHO_F32) return launch_expand_t<NU, float, float, float>(p);
   if (p.psi_dtype == SHO_BF16) return launch_expand_t<NU, __nv_bfloat16, float, float>(p);
   return cudaErrorInvalidValue;
+}
+
+template <int NU>
+static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
+  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float);
+  k_expand_zpass<NU, float, float><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+      p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p) {
+  switch (p.numax) {
+    case 0: return zpass_f32_nu<0>(p);
+    case 1: return zpass_f32_nu<1>(p);
+    case 2: return zpass_f32_nu<2>(p);
+    case 3: return zpass_f32_nu<3>(p);
+    case 4: return zpass_f32_nu<4>(p);
+    case 5: return zpass_f32_nu<5>(p);
+    case 6: return zpass_f32_nu<6>(p);
+    case 7: return zpass_f32_nu<7>(p);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_expand(const ExpandLaunch& p) {

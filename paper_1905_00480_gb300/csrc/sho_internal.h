@@ -75,7 +75,34 @@ struct ForcesLaunch {
   cudaStream_t stream;
 };
 
+// Stored-projector baseline: op 0 = sample projectors, 1 = project, 2 = add.
+struct UsuLaunch {
+  GridDev g;
+  const AtomDev* atoms;
+  int natoms;
+  int numax;
+  int zsplit;
+  double* proj;             // [A][C^3][N] FP64
+  const double* psi_in;     // project: psi
+  double* coeff_out;        // project: coefficients
+  const double* coeff_in;   // add: coefficients
+  double* psi_out;          // add: psi (read-modify-write)
+  const int* plane_ptr;
+  const int* plane_atoms;
+  cudaStream_t stream;
+};
+
 // Kernel launchers (return a CUDA error code).
+cudaError_t launch_usu(int op, const UsuLaunch& p);
+cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
+cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
+cudaError_t launch_expand_tc(const ExpandLaunch& p, sho_prec prec);
+
+constexpr int kTcMaxNumax = 7;  // tensor-core forms: eight 1D functions fill one MMA tile
+
+inline bool is_tc(sho_prec p) {
+  return p == SHO_P_TF32 || p == SHO_P_3XTF32 || p == SHO_P_BF16 || p == SHO_P_SPLIT_FP16;
+}
 cudaError_t launch_project(const ProjectLaunch& p);
 cudaError_t launch_expand(const ExpandLaunch& p);
 cudaError_t launch_forces_contract(const ForcesLaunch& p);

@@ -1,0 +1,203 @@
+// sho_usu.cu -- stored-projector FP64 baseline (the conventional scheme the paper compares with,
+// "USU" in Sec. 6): the projector values Psi_k(u_i) of every atom are sampled once onto its cube and
+// stored in device memory, [A][C^3][N] FP64; projection and expansion then stream them from memory
+// instead of generating the 1D functions on the fly.  Same cube convention, same band-major psi, same
+// deterministic decomposition as the SHO kernels (cluster-reduced z-slabs; row gather), so the two
+// differ only in where the projector values come from.
+#include <cooperative_groups.h>
+
+#include "sho_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sho {
+
+// --------------------------------------------------------------------------------- build
+template <int NU>
+__global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __restrict__ atoms,
+                                                   double* __restrict__ proj) {
+  using BS = Basis<NU>;
+  constexpr int NP = BS::NP, N = BS::N;
+  const int C = g.cube;
+  const long long c3 = (long long)C * C * C;
+  const int a = blockIdx.y;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= c3) return;
+  const AtomDev at = atoms[a];
+  const int ix = (int)(i % C), iy = (int)((i / C) % C), iz = (int)(i / ((long long)C * C));
+  double fx[NP], fy[NP], fz[NP];
+  phi_column(cube_offset(at.o[0], ix, g.h, at.X[0]), at.sigma, NU, fx, 1);
+  phi_column(cube_offset(at.o[1], iy, g.h, at.X[1]), at.sigma, NU, fy, 1);
+  phi_column(cube_offset(at.o[2], iz, g.h, at.X[2]), at.sigma, NU, fz, 1);
+  double* out = proj + ((long long)a * c3 + i) * N;
+  int k = 0;
+#pragma unroll
+  for (int nz = 0; nz < NP; nz++)
+#pragma unroll
+    for (int ny = 0; ny + nz <= NU; ny++)
+#pragma unroll
+      for (int nx = 0; nx + ny + nz <= NU; nx++) out[k++] = fx[nx] * fy[ny] * fz[nz];
+}
+
+// --------------------------------------------------------------------------------- project
+template <int NU>
+__global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* __restrict__ psi,
+                                                       const AtomDev* __restrict__ atoms,
+                                                       const double* __restrict__ proj, int zsplit,
+                                                       double* __restrict__ coeff) {
+  constexpr int N = Basis<NU>::N;
+  __shared__ double acc[N * kWarp];
+  const int C = g.cube;
+  const int lane = threadIdx.x;
+  const int a = blockIdx.z;
+  const int B = g.nbands;
+  const int b = blockIdx.y * kWarp + lane;
+  const bool bok = b < B;
+  const AtomDev at = atoms[a];
+  const long long c3 = (long long)C * C * C;
+  const double* pa = proj + (long long)a * c3 * N;
+  double r[N];
+#pragma unroll
+  for (int k = 0; k < N; k++) r[k] = 0.0;
+  const int chunk = (C + zsplit - 1) / zsplit;
+  const int iz0 = blockIdx.x * chunk, iz1 = min(C, iz0 + chunk);
+  for (int iz = iz0; iz < iz1; iz++) {
+    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
+    if (jz < 0) continue;
+    for (int iy = 0; iy < C; iy++) {
+      const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
+      if (jy < 0) continue;
+      const double* row = psi + ((long long)jz * g.n[1] + jy) * g.n[0] * B + b;
+      for (int ix = 0; ix < C; ix++) {
+        const int jx = cube_index(at.o[0], ix, g.n[0], g.periodic);
+        if (jx < 0) continue;
+        const double v = bok ? row[(long long)jx * B] : 0.0;
+        const double* p = pa + (((long long)iz * C + iy) * C + ix) * N;
+#pragma unroll
+        for (int k = 0; k < N; k++) r[k] = fma(__ldg(p + k), v, r[k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < N; k++) acc[k * kWarp + lane] = r[k];
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  const int rank = (int)cl.block_rank();
+  const double h3 = g.h * g.h * g.h;
+  for (int k = rank; k < N; k += zsplit) {
+    double s = 0.0;
+    for (int q = 0; q < zsplit; q++) s += cl.map_shared_rank(acc, q)[k * kWarp + lane];
+    if (bok) coeff[((long long)a * N + k) * B + b] = s * h3;
+  }
+  cl.sync();
+}
+
+// --------------------------------------------------------------------------------- add (row gather)
+template <int NU>
+__global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __restrict__ atoms,
+                                                   const int* __restrict__ plane_ptr,
+                                                   const int* __restrict__ plane_atoms,
+                                                   const double* __restrict__ proj,
+                                                   const double* __restrict__ coeff, double* __restrict__ psi) {
+  constexpr int N = Basis<NU>::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* acc = reinterpret_cast<double*>(smem_raw);  // [Nx][32]
+  const int C = g.cube;
+  const int Nx = g.n[0], Ny = g.n[1];
+  const int lane = threadIdx.x;
+  const int r = blockIdx.x;
+  const int z = r / Ny, y = r - z * Ny;
+  const int B = g.nbands;
+  const int b = blockIdx.y * kWarp + lane;
+  const bool bok = b < B;
+  const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+  bool any = false;
+  for (int q = q0; q < q1 && !any; q++) {
+    int iy = y - atoms[plane_atoms[q]].o[1];
+    if (g.periodic) {
+      iy %= Ny;
+      if (iy < 0) iy += Ny;
+    }
+    any = (iy >= 0 && iy < C);
+  }
+  if (!any) return;
+  double* row = psi + (long long)r * Nx * B + b;
+  for (int jx = 0; jx < Nx; jx++) acc[jx * kWarp + lane] = bok ? row[(long long)jx * B] : 0.0;
+  const long long c3 = (long long)C * C * C;
+  for (int q = q0; q < q1; q++) {
+    const int a = plane_atoms[q];
+    const AtomDev at = atoms[a];
+    int iy = y - at.o[1], iz = z - at.o[2];
+    if (g.periodic) {
+      iy %= Ny;
+      if (iy < 0) iy += Ny;
+      iz %= g.n[2];
+      if (iz < 0) iz += g.n[2];
+    }
+    if (iy < 0 || iy >= C) continue;
+    double cr[N];
+    const double* ca = coeff + (long long)a * N * B + b;
+#pragma unroll
+    for (int k = 0; k < N; k++) cr[k] = bok ? ca[(long long)k * B] : 0.0;
+    const double* pa = proj + ((long long)a * c3 + ((long long)iz * C + iy) * C) * N;
+    for (int ix = 0; ix < C; ix++) {
+      const int jx = cube_index(at.o[0], ix, Nx, g.periodic);
+      if (jx < 0) continue;
+      const double* p = pa + (long long)ix * N;
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; k++) s = fma(cr[k], __ldg(p + k), s);
+      acc[jx * kWarp + lane] += s;
+    }
+  }
+  if (bok)
+    for (int jx = 0; jx < Nx; jx++) row[(long long)jx * B] = acc[jx * kWarp + lane];
+}
+
+template <int NU>
+static cudaError_t usu_nu(int op, const UsuLaunch& p) {
+  const int C = p.g.cube;
+  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  if (op == 0) {
+    const long long c3 = (long long)C * C * C;
+    k_usu_build<NU><<<dim3((unsigned)((c3 + 127) / 128), p.natoms), 128, 0, p.stream>>>(p.g, p.atoms, p.proj);
+    return cudaGetLastError();
+  }
+  if (op == 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.zsplit, nbt, p.natoms);
+    cfg.blockDim = dim3(kWarp, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = p.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = p.zsplit;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_usu_project<NU>, p.g, p.psi_in, p.atoms, (const double*)p.proj, p.zsplit,
+                              p.coeff_out);
+  }
+  auto kern = k_usu_add<NU>;
+  const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(p.g.n[1] * p.g.n[2], nbt), kWarp, smem, p.stream>>>(p.g, p.atoms, p.plane_ptr, p.plane_atoms, p.proj,
+                                                                  p.coeff_in, p.psi_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_usu(int op, const UsuLaunch& p) {
+  switch (p.numax) {
+    case 0: return usu_nu<0>(op, p);
+    case 1: return usu_nu<1>(op, p);
+    case 2: return usu_nu<2>(op, p);
+    case 3: return usu_nu<3>(op, p);
+    case 4: return usu_nu<4>(op, p);
+    case 5: return usu_nu<5>(op, p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sho

@@ -1,0 +1,100 @@
+"""Differentiation pattern (GPU): E = sum_b sum_{a,n} D[a,n] c[a,n,b]^2 on the 128^3 / 128-atom / numax 5 /
+64-band FP32 workload, forces dE/dX from the hand-written backward of ShoProject, checked against
+(1) the FP64 oracle's analytic forces on sampled atoms and (2) central finite differences with step
+1e-4 of FP64 projections; and dE/dpsi against the expansion identity on a small case."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import rel_max, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+# FP32 forces vs FP64 references: FP32 storage of psi is shared by both sides (the references use the
+# same rounded psi); the FP32 projection at numax+1 carries ~1e-7 relative error per coefficient, the
+# ladder difference of neighbouring coefficients can cancel by ~10x, and E sums 64 bands x 56 states.
+TOL_FORCE_FP32 = 2e-5
+
+
+def _energy(c, D):
+    import torch
+    return (D[:, :, None] * c * c).sum()
+
+
+def test_c128_forces_autograd_vs_oracle_and_fd():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    from paper_1905_00480_gb300.autograd import sho_project
+    w = workloads.WORKLOADS["c128"]
+    pos, sig = workloads.atoms(w)
+    N = oracle.nstates(w.numax)
+    D = torch.from_numpy(workloads.dmatrix_host(w, N)).cuda().float()
+    psi = workloads.psi_device(w)                                   # FP32 [128][128][128][64]
+    X = torch.tensor(pos, dtype=torch.float64, requires_grad=True)
+    c = sho_project(psi, X, torch.from_numpy(sig), w.numax, w.cube, w.h, w.periodic, prec="fp32")
+    E = _energy(c, D)
+    E.backward()
+    F = X.grad.numpy()
+    assert np.all(np.isfinite(F))
+
+    # (1) oracle forces on sampled atoms, with dE/dc = 2 D c (c from the same GPU forward)
+    rng = np.random.default_rng(4)
+    sel = np.sort(rng.choice(w.natoms, size=3, replace=False))
+    psi_h = psi.double().cpu().numpy()
+    dEdc = (2.0 * D[:, :, None] * c.detach()).double().cpu().numpy()
+    ref = oracle.forces(w.grid, w.h, w.periodic, psi_h, pos[sel], sig[sel], w.numax, w.cube, dEdc[sel])
+    assert rel_max(F[sel], ref) <= TOL_FORCE_FP32
+
+    # (2) central differences of E_a(X_a) = sum D c_a^2 with FP64 GPU projections of the FP64 psi
+    psi64 = psi.double()
+    step = 1e-4
+    Dd = D.double()
+    for a in sel:
+        for d in range(3):
+            e = []
+            for sgn in (1.0, -1.0):
+                p = pos[a:a + 1].copy()
+                p[0, d] += sgn * step
+                assert np.floor(p[0, d] / w.h) == np.floor(pos[a, d] / w.h)
+                ca = api.project(psi64, p, sig[a:a + 1], w.numax, w.cube, w.h, w.periodic, prec="fp64")
+                e.append(float((Dd[a][:, None] * ca[0] * ca[0]).sum()))
+            fd = (e[0] - e[1]) / (2 * step)
+            assert abs(F[a, d] - fd) <= TOL_FORCE_FP32 * np.abs(ref).max(), (a, d, F[a, d], fd)
+
+
+def test_fp64_autograd_grad_psi_is_h3_expansion():
+    """dL/dpsi for L = <g, c> equals h^3 E(g); checked against the oracle expansion (FP64)."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300.autograd import sho_project
+    rng = np.random.default_rng(8)
+    grid, h, numax, cube = (32, 28, 36), 0.2, 4, 16
+    pos, sig = workloads.random_atoms(rng, 4, tuple(n * h for n in grid), True, min_sep=1.0)
+    psi_h = rng.standard_normal((36, 28, 32, 5))
+    g = rng.standard_normal((4, oracle.nstates(numax), 5))
+    psi = torch.from_numpy(psi_h).cuda().requires_grad_(True)
+    c = sho_project(psi, pos, torch.from_numpy(sig), numax, cube, h, True, prec="fp64")
+    (c * torch.from_numpy(g).cuda()).sum().backward()
+    ref = h ** 3 * oracle.add(grid, h, True, np.zeros_like(psi_h), pos, sig, numax, cube, g)
+    got = psi.grad.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-12
+
+
+def test_fp64_autograd_forces_vs_oracle():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300.autograd import sho_project
+    rng = np.random.default_rng(9)
+    grid, h, numax, cube = (40, 40, 40), 0.2, 5, 32
+    pos, sig = workloads.random_atoms(rng, 5, tuple(n * h for n in grid), True, min_sep=1.0)
+    psi_h = rng.standard_normal((40, 40, 40, 8))
+    Dm = rng.uniform(-1, 1, size=(5, oracle.nstates(numax)))
+    X = torch.tensor(pos, requires_grad=True)
+    c = sho_project(torch.from_numpy(psi_h).cuda(), X, torch.from_numpy(sig), numax, cube, h, True, prec="fp64")
+    E = (torch.from_numpy(Dm).cuda()[:, :, None] * c * c).sum()
+    E.backward()
+    dEdc = 2.0 * Dm[:, :, None] * c.detach().cpu().numpy()
+    ref = oracle.forces(grid, h, True, psi_h, pos, sig, numax, cube, dEdc)
+    assert rel_max(X.grad.numpy(), ref) <= 1e-12

@@ -1,0 +1,37 @@
+"""Stored-projector FP64 baseline (the paper's "USU" comparison, Sec. 6) against the oracle (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import TOL_FP64, assert_coeff_close, rel_norm, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_usu_matches_oracle(periodic):
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(200)
+    grid, h, numax, cube = (36, 40, 32), 0.2, 5, 16
+    pos, sig = workloads.random_atoms(rng, 5, tuple(n * h for n in grid), periodic, min_sep=1.0)
+    psi = rng.standard_normal((32, 40, 36, 40))
+    c = rng.standard_normal((5, oracle.nstates(numax), 40))
+    proj = api.usu_build(pos, sig, numax, cube, grid, h, periodic)
+    psi_d = torch.from_numpy(psi).cuda()
+    got = api.usu_project(psi_d, proj, pos, sig, numax, cube, h, periodic).cpu().numpy()
+    ref = oracle.project(grid, h, periodic, psi, pos, sig, numax, cube)
+    assert_coeff_close(got, ref, TOL_FP64)
+    api.usu_add(psi_d, torch.from_numpy(c).cuda(), proj, pos, sig, numax, cube, h, periodic)
+    ref2 = oracle.add(grid, h, periodic, psi, pos, sig, numax, cube, c)
+    assert rel_norm(psi_d.cpu().numpy() - psi, ref2 - psi) <= TOL_FP64
+
+
+def test_usu_rejects_large_numax():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api, ShoError
+    with pytest.raises(ShoError):
+        api.usu_build(np.zeros((1, 3)), [1.0], 6, 16, (16, 16, 16), 0.25, True)
