@@ -312,9 +312,13 @@ def run_ours(args, ws, rank, local):
         }
         default_case = args.workload == WORKLOAD and prec == "fp64" and not args.bands
         if not default_case:
-            args.no_same_gpu_baselines = args.no_precision_forms = args.no_cpu_baseline = True
+            args.no_same_gpu_baselines = args.no_precision_forms = args.no_cpu_baseline = args.no_serving = True
         if not args.no_same_gpu_baselines:
             result["same_gpu_baselines"] = same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream)
+        if not args.no_serving:
+            result["serving"] = serving_bench(api)
+            st = result["serving"]["loads"].get("0.8") or next(iter(result["serving"]["loads"].values()))
+            result["p50_ms"], result["p99_ms"] = st["p50_ms"], st["p99_ms"]
         if not args.no_precision_forms:
             del hpsi, psi_h, out_h, psi_d, cin_d
             torch.cuda.empty_cache()
@@ -449,6 +453,72 @@ def precision_forms(api, handle, stream, modes=("fp32", "tf32", "3xtf32", "bf16"
     return out
 
 
+def serving_bench(api, nsys=12, warm=200, measured=1000, loads=(0.5, 0.8, 0.95), slots=4, prec="fp32"):
+    """Poisson stream of project / expand requests (50/50) over heterogeneous device-resident systems
+    (grid 48^3..192^3, 8..1024 atoms, 16..512 bands, numax 3/5/7/9, FP32 psi).  Capacity = completed
+    requests per second of a saturating burst; each offered load rho submits `measured` requests at
+    rate rho * capacity after `warm` warm-up requests.  Latency = submit -> completion as recorded by the
+    server; GB/s = algorithmic psi + coefficient bytes of the completed requests / busy wall time."""
+    import torch
+    from paper_1905_00480_gb300.serve import Server
+    specs = workloads.serving_systems(nsys)
+    srv = Server(torch.cuda.current_device(), budget_bytes=96 << 30, slots=slots)
+    ids = []
+    for sp in specs:
+        rng = np.random.default_rng(sp.seed)
+        L = sp.grid * sp.h
+        pos, sig = workloads.random_atoms(rng, sp.natoms, (L, L, L), True, min_sep=1.0)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(sp.seed)
+        psi = torch.randn((sp.grid, sp.grid, sp.grid, sp.nbands), generator=g, device="cuda", dtype=torch.float32)
+        ids.append(srv.register(psi, pos, sig, sp.numax, sp.cube, sp.h, sp.periodic))
+        del psi
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(SERVE_SEED)
+
+    def draw(n):
+        return [(ids[int(rng.integers(len(ids)))], "project" if rng.random() < 0.5 else "expand") for _ in range(n)]
+
+    def run_burst(reqs):
+        t0 = time.perf_counter()
+        ts = [srv.submit(i, op, prec) for i, op in reqs]
+        for t in ts:
+            srv.wait(t, 600000)
+        return time.perf_counter() - t0
+
+    run_burst(draw(warm))
+    nburst = 400
+    cap = nburst / run_burst(draw(nburst))
+    out = {"systems": [dict(grid=sp.grid, atoms=sp.natoms, bands=sp.nbands, numax=sp.numax) for sp in specs],
+           "slots": slots, "precision": prec, "capacity_rps": round(cap, 2), "warmup_requests": warm,
+           "measured_requests": measured, "loads": {}}
+    for rho in loads:
+        srv.reset_stats()
+        reqs = draw(measured)
+        arrivals = workloads.poisson_arrivals(rng, measured, rho * cap)
+        t0 = time.perf_counter()
+        ts = []
+        for (i, op), ta in zip(reqs, arrivals):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ts.append(srv.submit(i, op, prec))
+        for t in ts:
+            srv.wait(t, 600000)
+        st = srv.stats()
+        out["loads"][str(rho)] = {"offered_rps": round(rho * cap, 2), "p50_ms": round(st["p50_ms"], 3),
+                                  "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3),
+                                  "max_ms": round(st["max_ms"], 3), "completed": st["completed"],
+                                  "failed": st["failed"], "gbs": round(st["gbs"], 2),
+                                  "max_inflight": st["max_inflight"], "peak_gb": round(st["peak_bytes"] / 1e9, 2)}
+    srv.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+SERVE_SEED = 4242
+
+
 def _oracle_sample(w, pos, sig, nsel, nbands_sel, seed=5):
     rng = np.random.default_rng(seed)
     sel = np.sort(rng.choice(w.natoms, size=nsel, replace=False))
@@ -542,6 +612,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-same-gpu-baselines", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "bf16"])

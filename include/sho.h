@@ -176,6 +176,67 @@ int sho_usu_add(sho_handle* handle, const sho_grid* grid, const double* coeff, i
                 const double* pos, const double* sigma, int numax, int cube, const double* proj, double* psi,
                 void* stream);
 
+/* ----------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over device-resident systems.  (The paper applies the
+ * non-local operator inside an iterative eigensolver, Sec. 3.2; serving many independent systems
+ * with one GPU is this library's deployment form of the same two operations.)
+ *
+ * A server owns `slots` execution slots (a CUDA stream and a workspace each) and one scheduler
+ * thread.  Systems are registered once: the server copies psi into device memory it owns and
+ * allocates the coefficients, so both stay resident between requests.  Requests (project: psi ->
+ * coeff; expand: psi += E coeff) are queued by sho_submit and started by the scheduler as soon as a
+ * slot is free, the request's workspace fits the memory budget next to the resident systems and
+ * in-flight workspaces, and no earlier request of the same system is still running (requests of one
+ * system run in submission order; requests of different systems overlap on the device).  Results of
+ * a request do not depend on what else runs: every kernel is deterministic and works on its own
+ * system's buffers.
+ *   budget_bytes  device memory the server may hold: resident systems + slot workspaces.
+ *   errors        sho_system_register returns SHO_ERR_CAPACITY when the system does not fit the
+ *                 budget; sho_submit returns SHO_ERR_CAPACITY when the request could never be admitted
+ *                 and SHO_ERR_STATE for an unknown system; sho_wait returns SHO_ERR_TIMEOUT when the
+ *                 ticket is not complete within timeout_ms (the request keeps running), or the
+ *                 request's own error status.
+ */
+typedef struct sho_server sho_server;
+
+typedef enum { SHO_OP_PROJECT = 0, SHO_OP_EXPAND = 1 } sho_op;
+
+typedef struct {
+  uint64_t submitted;        /* requests accepted by sho_submit */
+  uint64_t completed;        /* requests finished (successfully or not) */
+  uint64_t failed;           /* requests that finished with an error */
+  double p50_ms, p99_ms;     /* latency percentiles (submit -> completion seen by the scheduler) */
+  double mean_ms, max_ms;
+  double busy_seconds;       /* wall time from the first admission to the last completion */
+  double algorithmic_bytes;  /* psi and coefficient bytes of the completed requests */
+  double gbs;                /* algorithmic_bytes / busy_seconds / 1e9 */
+  size_t resident_bytes;     /* device memory of the registered systems */
+  size_t workspace_bytes;    /* device memory of the slot workspaces */
+  size_t peak_bytes;         /* peak of resident + workspace */
+  int max_inflight;          /* most requests running at the same time */
+} sho_server_stats;
+
+int sho_server_create(sho_server** out, int device, size_t budget_bytes, int slots);
+/* Waits (bounded by each request finishing) for running requests, drops queued ones, frees everything. */
+int sho_server_destroy(sho_server* server);
+/* Register a system.  psi: [n[2]][n[1]][n[0]][nbands] of psi_dtype at any address cudaMemcpy accepts
+ * (host or device); it is copied.  Coefficients (FP64 for F64 psi, FP32 otherwise) start at zero. */
+int sho_system_register(sho_server* server, const sho_grid* grid, int nbands, int natoms, const double* pos,
+                        const double* sigma, int numax, int cube, sho_dtype psi_dtype, const void* psi,
+                        int* system_id);
+/* Remove a system once its requests are done (SHO_ERR_STATE while any is queued or running). */
+int sho_system_unregister(sho_server* server, int system_id);
+/* Copy a system's psi and/or coefficients (either pointer may be NULL) to any address cudaMemcpy
+ * accepts, or its coefficients from one; waits for the system's requests to finish first. */
+int sho_system_read(sho_server* server, int system_id, void* psi_out, void* coeff_out);
+int sho_system_write_coeff(sho_server* server, int system_id, const void* coeff_in);
+/* Queue a request; *ticket identifies it for sho_wait. */
+int sho_submit(sho_server* server, int system_id, sho_op op, sho_prec prec, uint64_t* ticket);
+int sho_wait(sho_server* server, uint64_t ticket, int timeout_ms);
+int sho_server_get_stats(sho_server* server, sho_server_stats* stats);
+/* Clear latency records and counters (not the systems). */
+int sho_server_reset_stats(sho_server* server);
+
 /* Size of the fixed device scratch array of sho_forces_noalloc: 16 MiB. */
 #define SHO_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

@@ -29,6 +29,15 @@ class sho_grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("h", ctypes.c_double), ("periodic", ctypes.c_int)]
 
 
+class sho_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("busy_seconds", ctypes.c_double),
+                ("algorithmic_bytes", ctypes.c_double), ("gbs", ctypes.c_double),
+                ("resident_bytes", ctypes.c_size_t), ("workspace_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -54,6 +63,16 @@ SIGNATURES = {
     "sho_usu_build": (_I, [_VP, _GP, _I, _DP, _DP, _I, _I, _VP, _VP]),
     "sho_usu_project": (_I, [_VP, _GP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP, _VP]),
     "sho_usu_add": (_I, [_VP, _GP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP, _VP]),
+    "sho_server_create": (_I, [ctypes.POINTER(_VP), _I, ctypes.c_size_t, _I]),
+    "sho_server_destroy": (_I, [_VP]),
+    "sho_system_register": (_I, [_VP, _GP, _I, _I, _DP, _DP, _I, _I, _I, _VP, ctypes.POINTER(_I)]),
+    "sho_system_unregister": (_I, [_VP, _I]),
+    "sho_system_read": (_I, [_VP, _I, _VP, _VP]),
+    "sho_system_write_coeff": (_I, [_VP, _I, _VP]),
+    "sho_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
+    "sho_wait": (_I, [_VP, ctypes.c_uint64, _I]),
+    "sho_server_get_stats": (_I, [_VP, ctypes.POINTER(sho_server_stats)]),
+    "sho_server_reset_stats": (_I, [_VP]),
 }
 
 

@@ -213,6 +213,40 @@ GridDev make_grid(const sho_grid* grid, int cube, int nbands) {
   } while (0)
 
 }  // namespace
+
+// Workspace a call needs (an upper bound: the per-plane lists are counted as natoms * cube entries).
+size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, int cube, int nbands,
+                       sho_dtype coeff_dtype) {
+  const size_t tc = compute_size(coeff_dtype);
+  Carve cv;
+  cv.take((size_t)natoms * sizeof(AtomDev));
+  if (op == SHO_OP_EXPAND) {
+    cv.take(((size_t)grid->n[2] + 1) * sizeof(int));
+    cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
+    cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
+    cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
+  }
+  return cv.off;
+}
+
+// Grow the handle's workspace to exactly `bytes` (no growth margin) when it is smaller.
+int handle_reserve(sho_handle* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return SHO_OK;
+  DeviceGuard guard(h->device);
+  if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SHO_ERR_OOM;
+  }
+  h->ws_bytes = bytes;
+  return SHO_OK;
+}
+
+size_t handle_workspace(const sho_handle* h) { return h->ws_bytes; }
+
 }  // namespace sho
 
 using namespace sho;

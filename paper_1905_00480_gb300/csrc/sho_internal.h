@@ -98,6 +98,12 @@ cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
 cudaError_t launch_expand_tc(const ExpandLaunch& p, sho_prec prec);
 
+// Host helpers shared with the serving loop (sho_api.cu).
+size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, int cube, int nbands,
+                       sho_dtype coeff_dtype);
+int handle_reserve(sho_handle* h, size_t bytes);
+size_t handle_workspace(const sho_handle* h);
+
 constexpr int kTcMaxNumax = 7;  // tensor-core forms: eight 1D functions fill one MMA tile
 
 inline bool is_tc(sho_prec p) {
