@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "sho_internal.h"
@@ -134,6 +135,35 @@ void plane_lists(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
     }
 }
 
+// Atoms sorted by the Morton code of their cube origins (wrapped into the grid): CTAs launched
+// together then work on nearby cubes and share psi rows through L2.  Only the launch order changes;
+// every atom's coefficients are computed the same way.
+std::vector<int> spatial_order(const sho_grid* grid, const std::vector<AtomDev>& at) {
+  auto spread = [](uint32_t v) {
+    uint64_t x = v & 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+  };
+  std::vector<std::pair<uint64_t, int>> key(at.size());
+  for (size_t a = 0; a < at.size(); a++) {
+    uint32_t c[3];
+    for (int d = 0; d < 3; d++) {
+      int o = at[a].o[d] % grid->n[d];
+      if (o < 0) o += grid->n[d];
+      c[d] = (uint32_t)o;
+    }
+    key[a] = {spread(c[0]) | spread(c[1]) << 1 | spread(c[2]) << 2, (int)a};
+  }
+  std::stable_sort(key.begin(), key.end());
+  std::vector<int> order(at.size());
+  for (size_t i = 0; i < at.size(); i++) order[i] = key[i].second;
+  return order;
+}
+
 // Number of cube z-slabs per (atom, band tile) so that the CTAs spread evenly over the SMs.
 int choose_zsplit(int natoms, int nbands, int cube, int sms) {
   const int nbt = (nbands + kWarp - 1) / kWarp;
@@ -220,11 +250,13 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
   const size_t tc = compute_size(coeff_dtype);
   Carve cv;
   cv.take((size_t)natoms * sizeof(AtomDev));
+  if (op == SHO_OP_PROJECT) cv.take((size_t)natoms * sizeof(int));
   if (op == SHO_OP_EXPAND) {
     cv.take(((size_t)grid->n[2] + 1) * sizeof(int));
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
     cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
     cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
+    cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 4);
   }
   return cv.off;
 }
@@ -344,12 +376,16 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  std::vector<int> order = spatial_order(grid, at);
   Carve cv;
   const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  const size_t o_order = cv.take(order.size() * sizeof(int));
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  SHO_TRY(upload(h, o_order, order.data(), order.size() * sizeof(int), s));
   ProjectLaunch L;
+  L.order = reinterpret_cast<const int*>(static_cast<char*>(h->ws) + o_order);
   L.g = make_grid(grid, cube, nbands);
   L.psi = psi;
   L.psi_dtype = psi_dtype;
@@ -360,7 +396,10 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
   L.stream = s;
-  const cudaError_t e = is_tc(prec) ? launch_project_tc(L, prec) : launch_project(L);
+  const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
+                        : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_project_fp32(L, prec)
+                        : is_tc(prec) ? launch_project_tc(L, prec)
+                        : launch_project(L);
   if (e != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
 }
@@ -388,6 +427,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
   const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
   const size_t o_t2 = cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
+  const size_t o_txm = cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 4);
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
@@ -405,10 +445,16 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   L.numax = numax;
   L.plane_ptr = reinterpret_cast<const int*>(ws + o_ptr);
   L.plane_atoms = reinterpret_cast<const int*>(ws + o_list);
+  L.max_plane = 0;
+  for (size_t z = 0; z + 1 < ptr.size(); z++) L.max_plane = std::max(L.max_plane, ptr[z + 1] - ptr[z]);
   L.tables = ws + o_tab;
   L.t2 = ws + o_t2;
+  L.tables_xmajor = ws + o_txm;
   L.stream = s;
-  const cudaError_t e = is_tc(prec) ? launch_expand_tc(L, prec) : launch_expand(L);
+  const cudaError_t e = prec == SHO_P_FP64 ? launch_expand(L)
+                        : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_expand_fp32(L, prec)
+                        : is_tc(prec) ? launch_expand_tc(L, prec)
+                        : launch_expand(L);
   if (e != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
 }
@@ -433,15 +479,19 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
     return end_call(h, s);
   }
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  std::vector<int> order = spatial_order(grid, at);
   const size_t tc = compute_size(coeff_dtype);
   Carve cv;
   const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  const size_t o_order = cv.take(order.size() * sizeof(int));
   const size_t o_cp = cv.take((size_t)natoms * nstates(numax + 1) * (size_t)nbands * tc);
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  SHO_TRY(upload(h, o_order, order.data(), order.size() * sizeof(int), s));
   char* ws = static_cast<char*>(h->ws);
   ProjectLaunch P;
+  P.order = reinterpret_cast<const int*>(ws + o_order);
   P.g = make_grid(grid, cube, nbands);
   P.psi = psi;
   P.psi_dtype = psi_dtype;
@@ -452,7 +502,10 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   P.coeff = ws + o_cp;
   P.coeff_dtype = coeff_dtype;
   P.stream = s;
-  const cudaError_t e = is_tc(prec) ? launch_project_tc(P, prec) : launch_project(P);
+  const cudaError_t e = prec == SHO_P_FP64 ? launch_project(P)
+                        : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_project_fp32(P, prec)
+                        : is_tc(prec) ? launch_project_tc(P, prec)
+                        : launch_project(P);
   if (e != cudaSuccess) return SHO_ERR_CUDA;
   ForcesLaunch F;
   F.natoms = natoms;

@@ -20,7 +20,7 @@ namespace sho {
 template <int NU, typename TCo, typename TC>
 __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
                                                         const TCo* __restrict__ coeff, TC* __restrict__ tables,
-                                                        TC* __restrict__ t2) {
+                                                        TC* __restrict__ t2, TC* __restrict__ txm) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -40,6 +40,12 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
     if (blockIdx.x == 0) {
       phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, tx + i, C);
       phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, ty + i, C);
+      if (txm) {  // x table again, x-major [C][NPX] with NPX = NP rounded up to 4 (zero padded)
+        constexpr int NPX = (NP + 3) & ~3;
+        TC* row = txm + ((size_t)a * C + i) * NPX;
+        phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, row, 1);
+        for (int n = NP; n < NPX; n++) row[n] = (TC)0;
+      }
     }
   }
   __syncwarp();
@@ -163,7 +169,8 @@ static cudaError_t launch_expand_t(const ExpandLaunch& p) {
   {
     const size_t smem = (size_t)(NU + 1) * C * sizeof(TC);
     k_expand_zpass<NU, TCo, TC><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
-        p.g, p.atoms, static_cast<const TCo*>(p.coeff), static_cast<TC*>(p.tables), static_cast<TC*>(p.t2));
+        p.g, p.atoms, static_cast<const TCo*>(p.coeff), static_cast<TC*>(p.tables), static_cast<TC*>(p.t2),
+        (TC*)nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -195,7 +202,8 @@ static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float);
   k_expand_zpass<NU, float, float><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
-      p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2));
+      p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
+      static_cast<float*>(p.tables_xmajor));
   return cudaGetLastError();
 }
 
@@ -209,6 +217,8 @@ cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p) {
     case 5: return zpass_f32_nu<5>(p);
     case 6: return zpass_f32_nu<6>(p);
     case 7: return zpass_f32_nu<7>(p);
+    case 8: return zpass_f32_nu<8>(p);
+    case 9: return zpass_f32_nu<9>(p);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -42,6 +42,7 @@ struct ProjectLaunch {
   int natoms;
   int numax;
   int zsplit;               // cube z-planes split over this many CTAs of one cluster
+  const int* order = nullptr;  // optional device [A]: atoms in spatial (Morton) order of their cubes
   void* coeff;              // [A][N][B], FP64 or FP32
   sho_dtype coeff_dtype;
   cudaStream_t stream;
@@ -58,8 +59,10 @@ struct ExpandLaunch {
   int numax;
   const int* plane_ptr;     // [Nz + 1]: atoms whose cube covers plane z are
   const int* plane_atoms;   //   plane_atoms[plane_ptr[z] .. plane_ptr[z+1]), ascending
+  int max_plane;            // longest per-plane list
   void* tables;             // workspace [A][2][numax+1][cube] of the compute type (x and y tables)
   void* t2;                 // workspace [A][cube][P][B] of the compute type (z-pass result)
+  void* tables_xmajor = nullptr;  // optional workspace [A][cube][NPX] FP32: x table, x-major
   cudaStream_t stream;
 };
 
@@ -97,6 +100,11 @@ cudaError_t launch_usu(int op, const UsuLaunch& p);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
 cudaError_t launch_expand_tc(const ExpandLaunch& p, sho_prec prec);
+// Streaming FP32-class kernels (cp.async row pipeline / block gather), used when rows of bands are
+// 16-byte aligned (fp32_stream_ok); the CUDA-core / tensor-core row kernels serve the other cases.
+bool fp32_stream_ok(const void* psi, sho_dtype dt, int nbands);
+cudaError_t launch_project_fp32(const ProjectLaunch& p, sho_prec prec);
+cudaError_t launch_expand_fp32(const ExpandLaunch& p, sho_prec prec);
 
 // Host helpers shared with the serving loop (sho_api.cu).
 size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, int cube, int nbands,
