@@ -169,7 +169,7 @@ def run_ours(args, ws, rank, local):
         w = workloads.Workload(**{**w.__dict__, "nbands": args.bands})
     prec = args.prec or ("fp64" if w.dtype == "f64" else "fp32")
     sdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.storage or w.dtype]
-    cdt = torch.float64 if prec == "fp64" else torch.float32
+    cdt = torch.float64 if prec in ("fp64", "ff64") else torch.float32
     elem = torch.tensor([], dtype=sdt).element_size()
     # every rank runs its own replica with its own seed stream (weak scaling)
     rng = np.random.default_rng([w.seed, rank])
@@ -262,7 +262,7 @@ def run_ours(args, ws, rank, local):
         peaks = _peaks()
         dom = "k_project" if t_prj >= t_add else "k_expand"
         t_dom = max(t_prj, t_add)
-        if prec == "fp64":
+        if prec in ("fp64", "ff64"):
             flops_dom = alg["flops_prj"] if dom == "k_project" else alg["flops_add"]
             achieved = flops_dom / (t_dom * 1e-3) / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
@@ -289,7 +289,7 @@ def run_ours(args, ws, rank, local):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
+            "dtype": {"fp64": "f64", "ff64": "f64 storage, f32x2 x-pass", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
                       "split_fp16": "split-f16"}[prec],
             "data": "synthetic (seeded N(0,1) psi and coefficients, uniform atoms with min separation 2.0)",
             "config": {
@@ -614,7 +614,7 @@ def main():
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
+    ap.add_argument("--prec", default=None, choices=["fp64", "ff64", "fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "bf16"])
     ap.add_argument("--bands", type=int, default=0)
     args = ap.parse_args()

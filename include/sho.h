@@ -32,9 +32,9 @@
  *  Errors     every call returns SHO_OK (0) or a negative sho_status.  Argument errors are detected
  *             on the host before anything is enqueued; nothing is written then.  CUDA launch errors
  *             return SHO_ERR_CUDA.  Errors raised later on the device are reported by sho_sync().
- *  Precision  sho_prec selects the arithmetic of the contractions.  SHO_P_FP64 needs FP64 psi and
- *             coefficients.  The other forms take FP32 or BF16 psi and FP32 coefficients and keep the
- *             1D function tables in FP64 until they are rounded to the contraction type.
+ *  Precision  sho_prec selects the arithmetic of the contractions.  SHO_P_FP64 and SHO_P_FF64 need
+ *             FP64 psi and coefficients.  The other forms take FP32 or BF16 psi and FP32 coefficients
+ *             and keep the 1D function tables in FP64 until they are rounded to the contraction type.
  */
 #ifndef SHO_H
 #define SHO_H
@@ -72,7 +72,10 @@ typedef enum {
   SHO_P_TF32 = 2,        /* x-pass on TF32 tensor cores, FP32 accumulation */
   SHO_P_3XTF32 = 3,      /* x-pass as three TF32 products (hi*hi + hi*lo + lo*hi), FP32 accumulation */
   SHO_P_BF16 = 4,        /* x-pass on BF16 tensor cores, FP32 accumulation */
-  SHO_P_SPLIT_FP16 = 5   /* x-pass as three FP16 products of a hi/lo split, FP32 accumulation */
+  SHO_P_SPLIT_FP16 = 5,  /* x-pass as three FP16 products of a hi/lo split, FP32 accumulation */
+  SHO_P_FF64 = 6         /* FP64-accurate: FP64 psi and coefficients, x-pass as float-float
+                            (double-FP32) dot products on the FP32 pipe, y/z passes and accumulation in
+                            FP64; |psi| must lie in the FP32 normal range (smaller values count as 0) */
 } sho_prec;
 
 typedef struct {
@@ -118,7 +121,7 @@ int sho_sync(sho_handle* handle);
  * functions generated on the fly from the Hermite recursion (Sec. 3.7).
  *   psi    device [n[2]][n[1]][n[0]][nbands], type psi_dtype (read only)
  *   coeff  device [natoms][sho_nstates(numax)][nbands], type coeff_dtype (written, fully)
- * Supported: (SHO_P_FP64, psi F64, coeff F64); (SHO_P_FP32 | TF32 | 3XTF32 | BF16 | SPLIT_FP16,
+ * Supported: (SHO_P_FP64 | FF64, psi F64, coeff F64); (SHO_P_FP32 | TF32 | 3XTF32 | BF16 | SPLIT_FP16,
  * psi F32 or BF16, coeff F32).  The tensor-core forms (TF32, 3XTF32, BF16, SPLIT_FP16) need
  * numax <= 7 (SHO_ERR_NUMAX otherwise; for sho_forces numax + 1 <= 7) and a cube that is a multiple
  * of 16 (SHO_ERR_CUBE).  natoms == 0 or nbands == 0 is a no-op returning SHO_OK.

@@ -15,7 +15,7 @@ STATUS_NAMES = {
     -10: "SHO_ERR_CAPACITY", -11: "SHO_ERR_STATE",
 }
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
-PRECS = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16": 4, "split_fp16": 5}
+PRECS = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16": 4, "split_fp16": 5, "ff64": 6}
 
 
 class ShoError(RuntimeError):

@@ -107,7 +107,7 @@ def _stream_ptr(psi: torch.Tensor, stream):
 
 
 def _coeff_dtype(prec: str):
-    return torch.float64 if prec == "fp64" else torch.float32
+    return torch.float64 if prec in ("fp64", "ff64") else torch.float32
 
 
 def project(psi: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, periodic: bool = True,

@@ -77,6 +77,7 @@ int check_spacing(const sho_handle* h, const sho_grid* grid, int natoms, const d
 int check_dtypes(sho_prec prec, sho_dtype psi_dt, sho_dtype coeff_dt) {
   switch (prec) {
     case SHO_P_FP64:
+    case SHO_P_FF64:
       return (psi_dt == SHO_F64 && coeff_dt == SHO_F64) ? SHO_OK : SHO_ERR_DTYPE;
     case SHO_P_FP32:
       return ((psi_dt == SHO_F32 || psi_dt == SHO_BF16) && coeff_dt == SHO_F32) ? SHO_OK : SHO_ERR_DTYPE;
@@ -256,7 +257,7 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
     cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
     cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
-    cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 4);
+    cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 8);
   }
   return cv.off;
 }
@@ -397,6 +398,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   L.coeff_dtype = coeff_dtype;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
+                        : prec == SHO_P_FF64 ? launch_project_ff(L)
                         : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_project_fp32(L, prec)
                         : is_tc(prec) ? launch_project_tc(L, prec)
                         : launch_project(L);
@@ -427,7 +429,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
   const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
   const size_t o_t2 = cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
-  const size_t o_txm = cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 4);
+  const size_t o_txm = cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 8);
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
@@ -452,6 +454,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   L.tables_xmajor = ws + o_txm;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_expand(L)
+                        : prec == SHO_P_FF64 ? launch_expand_ff(L)
                         : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_expand_fp32(L, prec)
                         : is_tc(prec) ? launch_expand_tc(L, prec)
                         : launch_expand(L);
@@ -503,6 +506,7 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   P.coeff_dtype = coeff_dtype;
   P.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(P)
+                        : prec == SHO_P_FF64 ? launch_project_ff(P)
                         : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_project_fp32(P, prec)
                         : is_tc(prec) ? launch_project_tc(P, prec)
                         : launch_project(P);

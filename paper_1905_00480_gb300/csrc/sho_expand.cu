@@ -207,6 +207,32 @@ static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
   return cudaGetLastError();
 }
 
+template <int NU>
+static cudaError_t zpass_f64_nu(const ExpandLaunch& p) {
+  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double);
+  k_expand_zpass<NU, double, double><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+      p.g, p.atoms, static_cast<const double*>(p.coeff), static_cast<double*>(p.tables), static_cast<double*>(p.t2),
+      (double*)nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p) {
+  switch (p.numax) {
+    case 0: return zpass_f64_nu<0>(p);
+    case 1: return zpass_f64_nu<1>(p);
+    case 2: return zpass_f64_nu<2>(p);
+    case 3: return zpass_f64_nu<3>(p);
+    case 4: return zpass_f64_nu<4>(p);
+    case 5: return zpass_f64_nu<5>(p);
+    case 6: return zpass_f64_nu<6>(p);
+    case 7: return zpass_f64_nu<7>(p);
+    case 8: return zpass_f64_nu<8>(p);
+    case 9: return zpass_f64_nu<9>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p) {
   switch (p.numax) {
     case 0: return zpass_f32_nu<0>(p);

@@ -1,0 +1,510 @@
+// sho_ff.cu -- the FP64-accurate form with float-float x-passes (SHO_P_FF64).
+//
+// Same decomposition, cube convention and deterministic reductions as the FP64 kernels
+// (sho_project.cu, sho_expand.cu).  On GB300 the FP64 pipe runs at 1/61 of the FP32 pipe, and the
+// x-pass is 89 % of the FMAs of a projection or expansion (C^3 (numax+1) of C^3 (numax+1) + C^2 P + C N
+// per atom-band).  Here that pass runs as float-float dot products on the FP32 pipe (sho_ff.cuh);
+// the 1D tables are generated in FP64 and split once, and the y- and z-passes, the cluster reduction
+// and the final accumulation into psi stay in FP64.
+//   projection  T1[n] = sum_x psi[x] phi_n(x): psi split into float pairs with integer instructions,
+//               then one float-float dot step per (x, n); T1 is rebuilt in FP64 per grid row.
+//   expansion   the update sum_a sum_n T1_a[n] phi_n(x) of each grid point is accumulated over atoms as
+//               a float pair in registers (block gather over 8-row x 32-point tiles) and added to psi in
+//               FP64 once.
+#include <cooperative_groups.h>
+
+#include "sho_device.cuh"
+#include "sho_ff.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sho {
+
+// ------------------------------------------------------------------------------- projection
+constexpr int kFfStages = 3;   // cp.async ring depth (rows of 32 x points x 32 bands x 8 bytes)
+constexpr int kFfRowBytes = 32 * 8;
+
+__device__ __forceinline__ uint32_t ff_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void ff_cp16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes));
+}
+__device__ __forceinline__ void ff_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void ff_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int NU>
+struct FfProjectSmem {
+  static constexpr int NP = NU + 1, NPX = (NP + 1) & ~1, N = Basis<NU>::N;
+  static constexpr bool ACCR = N <= 56;  // z-pass accumulators in registers up to numax 5
+  __host__ __device__ static size_t ring_bytes(int cube) {
+    const size_t ring = (size_t)kFfStages * cube * kFfRowBytes;
+    const size_t red = (size_t)N * kWarp * sizeof(double);
+    return ACCR ? (ring > red ? ring : red) : ring;
+  }
+  static size_t bytes(int cube) {
+    size_t t = ring_bytes(cube);
+    t += (size_t)cube * NPX * sizeof(float2);                      // x table (pairs), x-major
+    t += 2 * (size_t)NP * cube * sizeof(double);                   // y, z tables (FP64)
+    t += (size_t)cube * sizeof(long long);                         // x offsets
+    t = (t + 15) & ~(size_t)15;
+    if (!ACCR) t += (size_t)N * kWarp * sizeof(double);            // partial coefficients
+    return t;
+  }
+};
+
+template <int NU>
+__global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* __restrict__ psi,
+                                                      const AtomDev* __restrict__ atoms, int zsplit,
+                                                      double* __restrict__ coeff) {
+  using BS = Basis<NU>;
+  using SM = FfProjectSmem<NU>;
+  constexpr int NP = BS::NP, P = BS::P, N = BS::N, NPX = SM::NPX;
+  constexpr bool ACCR = SM::ACCR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = g.cube;
+  unsigned char* ring = smem_raw;
+  const size_t ringb = SM::ring_bytes(C);
+  float2* phx = reinterpret_cast<float2*>(ring + ringb);                     // [C][NPX] pairs
+  double* phy = reinterpret_cast<double*>(phx + (size_t)C * NPX);            // [NP][C]
+  double* phz = phy + (size_t)NP * C;                                        // [NP][C]
+  long long* xoff = reinterpret_cast<long long*>(phz + (size_t)NP * C);      // [C]
+  size_t off = ringb + (size_t)C * NPX * sizeof(float2) + 2 * (size_t)NP * C * sizeof(double) + (size_t)C * 8;
+  off = (off + 15) & ~(size_t)15;
+  double* acc = ACCR ? reinterpret_cast<double*>(ring) : reinterpret_cast<double*>(smem_raw + off);  // [N][32]
+
+  const int lane = threadIdx.x;
+  const int a = blockIdx.z;
+  const int B = g.nbands;
+  const int b0 = blockIdx.y * kWarp;
+  const bool bok = b0 + lane < B;
+  const AtomDev at = atoms[a];
+
+  for (int i = lane; i < C; i += kWarp) {
+    double col[NP];
+    phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, col, 1);
+#pragma unroll
+    for (int n = 0; n < NPX; n++) {
+      const ff f = n < NP ? ff_from_double_exact(col[n]) : ff{0.0f, 0.0f};
+      phx[i * NPX + n] = make_float2(f.hi, f.lo);
+    }
+    phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, phy + i, C);
+    phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
+    const int jx = cube_index(at.o[0], i, g.n[0], g.periodic);
+    xoff[i] = jx < 0 ? -1ll : (long long)jx * B;
+  }
+  double accr[ACCR ? N : 1];
+  if constexpr (ACCR) {
+#pragma unroll
+    for (int k = 0; k < N; k++) accr[k] = 0.0;
+  } else {
+    for (int i = lane; i < N * kWarp; i += kWarp) acc[i] = 0.0;
+  }
+  __syncwarp();
+
+  const int chunk = (C + zsplit - 1) / zsplit;
+  const int iz0 = blockIdx.x * chunk, iz1 = min(C, iz0 + chunk);
+  const int R = max(0, iz1 - iz0) * C;
+  const long long rowlen = (long long)g.n[0] * B;
+  const int valid_bytes = (B - b0) * 8;
+  // 16-byte asynchronous copies need every (grid point, band tile) run of psi to start on a 16-byte
+  // boundary: an even band count and a 16-byte aligned base.  Otherwise the ring is filled with
+  // plain 8-byte loads (same data layout, no overlap of loads and compute).
+  const bool async_ok = ((B & 1) == 0) && (((uintptr_t)psi & 15u) == 0);
+
+  // copies of slab row r (x points x 32 bands) into ring stage r % kFfStages
+  auto issue = [&](int r) {
+    if (r >= R) return;
+    const int iz = iz0 + r / C, iy = r - (r / C) * C;
+    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
+    const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
+    if (jz < 0 || jy < 0) return;
+    const double* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b0;
+    unsigned char* st = ring + (size_t)(r % kFfStages) * C * kFfRowBytes;
+    if (async_ok) {
+      for (int q = lane; q < C * 16; q += kWarp) {  // 16 chunks of 16 bytes per x point
+        const int x = q >> 4, part = q & 15;
+        const long long o = xoff[x];
+        int nb = valid_bytes - part * 16;
+        nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
+        const void* src = (o >= 0 && nb > 0)
+                               ? (const void*)(reinterpret_cast<const unsigned char*>(row + o) + part * 16)
+                               : (const void*)psi;
+        ff_cp16(ff_smem_u32(st + x * kFfRowBytes + part * 16), src, o >= 0 ? nb : 0);
+      }
+    } else {
+      double* sd = reinterpret_cast<double*>(st);
+      for (int x = 0; x < C; x++) {
+        const long long o = xoff[x];
+        sd[x * 32 + lane] = (o >= 0 && bok) ? row[o + lane] : 0.0;
+      }
+    }
+  };
+
+#pragma unroll
+  for (int r = 0; r < kFfStages - 1; r++) {
+    issue(r);
+    ff_commit();
+  }
+  double t2[P];
+#pragma unroll
+  for (int p = 0; p < P; p++) t2[p] = 0.0;
+
+  for (int r = 0; r < R; r++) {
+    ff_wait<kFfStages - 2>();
+    __syncwarp();
+    issue(r + kFfStages - 1);
+    ff_commit();
+    const int iz = iz0 + r / C, iy = r - (r / C) * C;
+    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
+    const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
+    if (jz >= 0 && jy >= 0) {
+      const double* st = reinterpret_cast<const double*>(ring + (size_t)(r % kFfStages) * C * kFfRowBytes);
+      // x-pass (a3) as float-float dot products
+      float S[NP], E[NP];
+#pragma unroll
+      for (int n = 0; n < NP; n++) S[n] = E[n] = 0.0f;
+#pragma unroll 4
+      for (int ix = 0; ix < C; ix++) {
+        const ff pv = ff_from_double(st[ix * 32 + lane]);
+        const float4* f4 = reinterpret_cast<const float4*>(phx + (size_t)ix * NPX);
+#pragma unroll
+        for (int q = 0; q < NPX / 2; q++) {
+          const float4 f = f4[q];
+          if (2 * q < NP) ff_dot_step(S[2 * q], E[2 * q], pv, ff{f.x, f.y});
+          if (2 * q + 1 < NP) ff_dot_step(S[2 * q + 1], E[2 * q + 1], pv, ff{f.z, f.w});
+        }
+      }
+      double t1[NP];
+#pragma unroll
+      for (int n = 0; n < NP; n++) t1[n] = ff_to_double(S[n], E[n]);
+      // y-pass (a4) in FP64
+#pragma unroll
+      for (int ny = 0; ny < NP; ny++) {
+        const double w = phy[ny * C + iy];
+#pragma unroll
+        for (int nx = 0; nx + ny <= NU; nx++) t2[BS::pair(nx, ny)] = fma(t1[nx], w, t2[BS::pair(nx, ny)]);
+      }
+    }
+    __syncwarp();
+    if (iy == C - 1) {
+      // z-pass (a5) in FP64 for the finished plane
+      int k = 0;
+#pragma unroll
+      for (int nz = 0; nz < NP; nz++) {
+        const double w = phz[nz * C + iz];
+#pragma unroll
+        for (int ny = 0; ny + nz <= NU; ny++)
+#pragma unroll
+          for (int nx = 0; nx + ny + nz <= NU; nx++) {
+            if constexpr (ACCR)
+              accr[k] = fma(t2[BS::pair(nx, ny)], w, accr[k]);
+            else
+              acc[k * kWarp + lane] = fma(t2[BS::pair(nx, ny)], w, acc[k * kWarp + lane]);
+            k++;
+          }
+      }
+#pragma unroll
+      for (int p = 0; p < P; p++) t2[p] = 0.0;
+    }
+  }
+  ff_wait<0>();
+  __syncwarp();
+  if constexpr (ACCR) {
+#pragma unroll
+    for (int k = 0; k < N; k++) acc[k * kWarp + lane] = accr[k];
+  }
+
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  const int rank = (int)cl.block_rank();
+  const double h3 = g.h * g.h * g.h;
+  for (int k = rank; k < N; k += zsplit) {
+    double s = 0.0;
+    for (int q = 0; q < zsplit; q++) s += cl.map_shared_rank(acc, q)[k * kWarp + lane];
+    if (bok) coeff[((long long)a * N + k) * B + b0 + lane] = s * h3;
+  }
+  cl.sync();
+}
+
+// ------------------------------------------------------------------------------- expansion
+// x tables of every atom as float pairs, x-major [A][C][NPX], from the FP64 tables [A][2][NP][C].
+template <int NU>
+__global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tables, float2* __restrict__ txff) {
+  constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
+  const long long total = (long long)natoms * cube * NPX;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(i % NPX);
+    const long long ai = i / NPX;
+    const int ix = (int)(ai % cube);
+    const int a = (int)(ai / cube);
+    const ff f = n < NP ? ff_from_double_exact(tables[((long long)a * 2 * NP + n) * cube + ix]) : ff{0.0f, 0.0f};
+    txff[i] = make_float2(f.hi, f.lo);
+  }
+}
+
+// ------------------------------------------------------------------------------- expansion, block gather
+// Tiles of 8 grid rows x 32 x points x 32 bands of one z plane (8 warps, one per row).  For each atom
+// whose cube meets the tile, its z-pass slice T2[a][z][P][32] (FP64), its x table as float pairs
+// [C][NPX] and its y table [NP][C] (FP64) are staged once in shared memory, double-buffered across
+// atoms, and shared by the 8 row-warps.  Each warp keeps the update of its 32 x points as float pairs
+// in registers and adds it to psi in FP64 at the end.  Atoms in ascending order; deterministic.
+constexpr int kFfRows = 8;
+constexpr int kFfXSeg = 32;
+
+template <int NU>
+struct FfBlkSmem {
+  static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 1) & ~1;
+  // bytes of one staging buffer: T2 [P][32] doubles + x pairs [C][NPX] + y [NP][C] doubles
+  __host__ __device__ static size_t buf_bytes(int cube) {
+    return (size_t)P * 32 * 8 + (size_t)cube * NPX * 8 + (size_t)NP * cube * 8;
+  }
+  static size_t bytes(int cube, int max_plane) { return 2 * buf_bytes(cube) + (size_t)(max_plane + 1) * 4; }
+};
+
+template <int NU>
+__global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, const AtomDev* __restrict__ atoms,
+                                                                   const int* __restrict__ plane_ptr,
+                                                                   const int* __restrict__ plane_atoms,
+                                                                   const double* __restrict__ tables,
+                                                                   const float2* __restrict__ txff,
+                                                                   const double* __restrict__ t2,
+                                                                   double* __restrict__ psi) {
+  using BS = Basis<NU>;
+  using SM = FfBlkSmem<NU>;
+  constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = g.cube;
+  const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
+  const size_t bufb = SM::buf_bytes(C);
+  int* slist = reinterpret_cast<int*>(smem_raw + 2 * bufb);
+  __shared__ int wcount[kFfRows];
+  __shared__ int s_nlist;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nseg = (Nx + kFfXSeg - 1) / kFfXSeg, nyb = (Ny + kFfRows - 1) / kFfRows;
+  int bid = blockIdx.x;
+  const int seg = bid % nseg;
+  bid /= nseg;
+  const int yb = bid % nyb;
+  const int z = bid / nyb;
+  const int xs = seg * kFfXSeg;
+  const int y = yb * kFfRows + warp;
+  const bool yok = y < Ny;
+  const int B = g.nbands;
+  const int b0 = blockIdx.y * kWarp;
+  const bool bok = b0 + lane < B;
+  const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+
+  auto meets = [&](const AtomDev& at) {
+    int dy = yb * kFfRows - at.o[1], dx = xs - at.o[0];
+    if (g.periodic) {
+      dy %= Ny;
+      if (dy < 0) dy += Ny;
+      dx %= Nx;
+      if (dx < 0) dx += Nx;
+      return (dy < C || dy + kFfRows > Ny) && (dx < C || dx + kFfXSeg > Nx);
+    }
+    return dy < C && dy + kFfRows > 0 && dx < C && dx + kFfXSeg > 0;
+  };
+
+  // staging with 8-byte asynchronous copies (FP64 rows of an arbitrary band count are 8-byte aligned)
+  auto cp8 = [](void* dst, const void* src, int bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(ff_smem_u32(dst)), "l"(src), "r"(bytes));
+  };
+  auto stage = [&](int a, int buf) {
+    const AtomDev at = atoms[a];
+    int iz = z - at.o[2];
+    if (g.periodic) {
+      iz %= Nz;
+      if (iz < 0) iz += Nz;
+    }
+    unsigned char* dst = smem_raw + (size_t)buf * bufb;
+    double* dt2 = reinterpret_cast<double*>(dst);
+    const double* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
+    for (int q = tid; q < P * 32; q += kFfRows * kWarp) {
+      const int p = q >> 5, bl = q & 31;
+      const bool ok = b0 + bl < B;
+      cp8(dt2 + q, ok ? (const void*)(src_t2 + (size_t)p * B + bl) : (const void*)t2, ok ? 8 : 0);
+    }
+    float2* dx = reinterpret_cast<float2*>(dst + (size_t)P * 32 * 8);
+    const float2* src_x = txff + (size_t)a * C * NPX;
+    for (int q = tid; q < C * NPX; q += kFfRows * kWarp) cp8(dx + q, src_x + q, 8);
+    double* dy = reinterpret_cast<double*>(dst + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
+    const double* src_y = tables + ((size_t)a * 2 + 1) * NP * C;
+    for (int q = tid; q < NP * C; q += kFfRows * kWarp) cp8(dy + q, src_y + q, 8);
+  };
+
+  // the plane's atoms that meet the tile, compacted in ascending order
+  if (tid == 0) s_nlist = 0;
+  __syncthreads();
+  for (int base = q0; base < q1; base += kFfRows * kWarp) {
+    const int q = base + tid;
+    int a = -1;
+    bool m = false;
+    if (q < q1) {
+      a = plane_atoms[q];
+      m = meets(atoms[a]);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) wcount[warp] = __popc(bal);
+    __syncthreads();
+    int off = s_nlist;
+    for (int w = 0; w < warp; w++) off += wcount[w];
+    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = a;
+    __syncthreads();
+    if (tid == 0)
+      for (int w = 0; w < kFfRows; w++) s_nlist += wcount[w];
+    __syncthreads();
+  }
+  const int nlist = s_nlist;
+
+  float uh[kFfXSeg], ul[kFfXSeg];  // update of the 32 x points of this row, as float pairs
+#pragma unroll
+  for (int x = 0; x < kFfXSeg; x++) uh[x] = ul[x] = 0.0f;
+
+  int buf = 0;
+  if (nlist > 0) stage(slist[0], 0);
+  ff_commit();
+  for (int li = 0; li < nlist; li++) {
+    const int a = slist[li];
+    if (li + 1 < nlist) stage(slist[li + 1], buf ^ 1);
+    ff_commit();
+    ff_wait<1>();
+    __syncthreads();
+    const unsigned char* src = smem_raw + (size_t)buf * bufb;
+    const double* t2s = reinterpret_cast<const double*>(src);
+    const float2* txs = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8);
+    const double* tys = reinterpret_cast<const double*>(src + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
+    const AtomDev at = atoms[a];
+    int iy = y - at.o[1];
+    if (g.periodic) {
+      iy %= Ny;
+      if (iy < 0) iy += Ny;
+    }
+    if (yok && iy >= 0 && iy < C) {
+      // y-pass in FP64
+      double t1[NP];
+#pragma unroll
+      for (int n = 0; n < NP; n++) t1[n] = 0.0;
+#pragma unroll
+      for (int ny = 0; ny < NP; ny++) {
+        const double w = tys[ny * C + iy];
+#pragma unroll
+        for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fma(t2s[BS::pair(nx, ny) * 32 + lane], w, t1[nx]);
+      }
+      ff t1f[NP];
+#pragma unroll
+      for (int n = 0; n < NP; n++) t1f[n] = ff_from_double(t1[n]);
+      int dx = xs - at.o[0];
+      if (g.periodic) {
+        dx %= Nx;
+        if (dx < 0) dx += Nx;
+      }
+      // x-pass as float-float dot products into the register update
+#pragma unroll
+      for (int x = 0; x < kFfXSeg; x++) {
+        int ix = dx + x;
+        if (g.periodic && ix >= Nx) ix -= Nx;
+        if (ix >= 0 && ix < C) {
+          float s = 0.0f, c = 0.0f;
+          const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
+#pragma unroll
+          for (int qn = 0; qn < NPX / 2; qn++) {
+            const float4 f = f4[qn];
+            if (2 * qn < NP) ff_dot_step(s, c, t1f[2 * qn], ff{f.x, f.y});
+            if (2 * qn + 1 < NP) ff_dot_step(s, c, t1f[2 * qn + 1], ff{f.z, f.w});
+          }
+          ff_add(uh[x], ul[x], s, c);
+        }
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  ff_wait<0>();
+  if (!yok || !bok || nlist == 0) return;
+  double* rowp = psi + ((size_t)z * Ny + y) * (size_t)Nx * B + b0 + lane;
+#pragma unroll
+  for (int x = 0; x < kFfXSeg; x++)
+    if (xs + x < Nx) rowp[(size_t)(xs + x) * B] += ff_to_double(uh[x], ul[x]);
+}
+
+// ------------------------------------------------------------------------------- launchers
+template <int NU>
+static cudaError_t ff_project_nu(const ProjectLaunch& p) {
+  const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
+  auto kern = k_project_ff<NU>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.zsplit, (p.g.nbands + kWarp - 1) / kWarp, p.natoms);
+  cfg.blockDim = dim3(kWarp, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = p.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = p.zsplit;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit,
+                            static_cast<double*>(p.coeff));
+}
+
+template <int NU>
+static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
+  constexpr int NPX = (NU + 2) & ~1;
+  cudaError_t e = launch_expand_zpass_f64(p);
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)p.natoms * p.g.cube * NPX;
+  k_ff_tables<NU><<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, p.stream>>>(
+      p.natoms, p.g.cube, static_cast<const double*>(p.tables), static_cast<float2*>(p.tables_xmajor));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  auto kern = k_expand_blk_ff<NU>;
+  const size_t smem = FfBlkSmem<NU>::bytes(p.g.cube, p.max_plane);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nseg = (p.g.n[0] + kFfXSeg - 1) / kFfXSeg, nyb = (p.g.n[1] + kFfRows - 1) / kFfRows;
+  kern<<<dim3((unsigned)nseg * nyb * p.g.n[2], (p.g.nbands + kWarp - 1) / kWarp), kFfRows * kWarp, smem, p.stream>>>(
+      p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const double*>(p.tables),
+      static_cast<const float2*>(p.tables_xmajor), static_cast<const double*>(p.t2), static_cast<double*>(p.psi));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_ff(const ProjectLaunch& p) {
+  switch (p.numax) {
+    case 0: return ff_project_nu<0>(p);
+    case 1: return ff_project_nu<1>(p);
+    case 2: return ff_project_nu<2>(p);
+    case 3: return ff_project_nu<3>(p);
+    case 4: return ff_project_nu<4>(p);
+    case 5: return ff_project_nu<5>(p);
+    case 6: return ff_project_nu<6>(p);
+    case 7: return ff_project_nu<7>(p);
+    case 8: return ff_project_nu<8>(p);
+    case 9: return ff_project_nu<9>(p);
+    case 10: return ff_project_nu<10>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_expand_ff(const ExpandLaunch& p) {
+  switch (p.numax) {
+    case 0: return ff_expand_nu<0>(p);
+    case 1: return ff_expand_nu<1>(p);
+    case 2: return ff_expand_nu<2>(p);
+    case 3: return ff_expand_nu<3>(p);
+    case 4: return ff_expand_nu<4>(p);
+    case 5: return ff_expand_nu<5>(p);
+    case 6: return ff_expand_nu<6>(p);
+    case 7: return ff_expand_nu<7>(p);
+    case 8: return ff_expand_nu<8>(p);
+    case 9: return ff_expand_nu<9>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sho

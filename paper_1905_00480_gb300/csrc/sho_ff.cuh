@@ -1,0 +1,97 @@
+// sho_ff.cuh -- float-float ("double-FP32") arithmetic for the FP64-accurate form on the FP32 pipe.
+//
+// A double v is carried as an unevaluated pair (hi, lo) of floats with v ~= hi + lo to about 48
+// significant bits.  Products use the error-free FMA product (Dekker's TwoProduct as restated with a
+// fused multiply-add): p = a*b, e = fma(a, b, -p) gives a*b = p + e exactly.  Sums use Knuth's
+// error-free TwoSum.  A dot product accumulated this way (Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, Algorithm Dot2 extended to pair inputs) is as accurate as if
+// computed in twice the working precision: relative errors of order 2^-48, far inside the 1e-12 bar
+// of the FP64 form, while every instruction runs on the FP32 pipe (61x the FP64 rate on GB300).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sho {
+
+struct ff {
+  float hi, lo;
+};
+
+// Split a double into hi + lo without FP64 instructions: hi takes the sign, exponent and the top 23
+// mantissa bits (truncation), lo the next bits of the remainder (rounded once to float).  Magnitudes
+// outside the float normal range (below 2^-126 or at/above 2^128) are flushed to zero; the FP64-accurate
+// form documents that its inputs must lie inside that range.
+__device__ __forceinline__ ff ff_from_double(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hw = (unsigned int)(b >> 32);
+  const int e = (int)((hw >> 20) & 0x7ff);  // biased double exponent
+  ff r;
+  if (e < 1023 - 126 || e > 1023 + 127) {
+    r.hi = 0.0f;
+    r.lo = 0.0f;
+    return r;
+  }
+  const unsigned int sign = hw & 0x80000000u;
+  const unsigned int mhi = (unsigned int)(b >> 29) & 0x7fffffu;  // mantissa bits 51..29
+  r.hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | mhi);
+  // remainder: mantissa bits 28..0, value m_lo * 2^(e - 1023 - 52)
+  const unsigned int mlo = (unsigned int)b & 0x1fffffffu;
+  const int el = e - 1023 - 52 + 127;  // float exponent of 2^(e-1075)
+  if (mlo == 0u || el < 1) {
+    r.lo = 0.0f;
+  } else {
+    const float scale = __uint_as_float((unsigned int)el << 23);
+    const float m = __uint2float_rn(mlo) * scale;
+    r.lo = sign ? -m : m;
+  }
+  return r;
+}
+
+// Split a double into hi + lo with FP64 arithmetic (for values computed once per table entry).
+__device__ __forceinline__ ff ff_from_double_exact(double v) {
+  ff r;
+  r.hi = __double2float_rn(v);
+  r.lo = __double2float_rn(v - (double)r.hi);
+  return r;
+}
+
+// Exact float -> double widening with integer instructions (no FP64-pipe conversion); zeros and
+// subnormal floats map to 0.
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                  ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// s + c as a double: two exact widenings and one FP64 add.
+__device__ __forceinline__ double ff_to_double(float s, float c) { return f2d_int(s) + f2d_int(c); }
+
+// Accumulate a*b (pairs) into the running dot product (s, c):  s + c += (a.hi + a.lo)(b.hi + b.lo),
+// dropping only a.lo*b.lo.  s carries the error-free sum of the leading products, c the errors and
+// the cross terms.
+__device__ __forceinline__ void ff_dot_step(float& s, float& c, const ff a, const ff b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);           // exact low part of a.hi*b.hi
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float t = s + p;                     // TwoSum(s, p)
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (p - bb);
+  s = t;
+  c += err + e;
+}
+
+// (s, c) += (u, v): add two pair values, error-free on the leading parts.
+__device__ __forceinline__ void ff_add(float& s, float& c, float u, float v) {
+  const float t = s + u;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (u - bb);
+  s = t;
+  c += err + v;
+}
+
+}  // namespace sho

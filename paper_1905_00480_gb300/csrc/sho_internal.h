@@ -98,6 +98,9 @@ struct UsuLaunch {
 // Kernel launchers (return a CUDA error code).
 cudaError_t launch_usu(int op, const UsuLaunch& p);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
+cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
+cudaError_t launch_project_ff(const ProjectLaunch& p);
+cudaError_t launch_expand_ff(const ExpandLaunch& p);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
 cudaError_t launch_expand_tc(const ExpandLaunch& p, sho_prec prec);
 // Streaming FP32-class kernels (cp.async row pipeline / block gather), used when rows of bands are
@@ -123,6 +126,7 @@ cudaError_t launch_forces_contract(const ForcesLaunch& p);
 
 // Bytes of compute-type scalars for a dtype.
 inline size_t compute_size(sho_dtype coeff_dtype) { return coeff_dtype == SHO_F64 ? 8 : 4; }
+inline bool is_f64_form(sho_prec p) { return p == SHO_P_FP64 || p == SHO_P_FF64; }
 
 inline int nstates(int nu) { return nu < 0 ? 0 : (nu + 1) * (nu + 2) * (nu + 3) / 6; }
 inline int npairs(int nu) { return nu < 0 ? 0 : (nu + 1) * (nu + 2) / 2; }

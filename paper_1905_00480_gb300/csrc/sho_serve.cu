@@ -400,7 +400,7 @@ int sho_submit(sho_server* s, int id, sho_op op, sho_prec prec, uint64_t* ticket
   if (it == s->systems.end()) return SHO_ERR_STATE;
   SysRec& sys = it->second;
   const bool f64 = sys.psi_dt == SHO_F64;
-  if ((prec == SHO_P_FP64) != f64) return SHO_ERR_DTYPE;
+  if (sho::is_f64_form(prec) != f64) return SHO_ERR_DTYPE;
   Req r;
   r.sys = id;
   r.op = op;
