@@ -38,6 +38,10 @@ def _peaks():
         return {}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the dominant kernel of the default bench
+# step (k_expand_blk_ff<5>, 96^3 / 64 atoms / 128 bands); valid only while that kernel is unchanged.
+NCU_TRAFFIC = {"k_expand": 951.229440e6 + 846.012160e6}
+
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
 # 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.
 FP64_PEAK_TFLOPS = 1.19
@@ -167,7 +171,7 @@ def run_ours(args, ws, rank, local):
     w = workloads.WORKLOADS[args.workload]
     if args.bands:
         w = workloads.Workload(**{**w.__dict__, "nbands": args.bands})
-    prec = args.prec or ("fp64" if w.dtype == "f64" else "fp32")
+    prec = args.prec or ("ff64" if w.dtype == "f64" else "fp32")
     sdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[args.storage or w.dtype]
     cdt = torch.float64 if prec in ("fp64", "ff64") else torch.float32
     elem = torch.tensor([], dtype=sdt).element_size()
@@ -262,7 +266,7 @@ def run_ours(args, ws, rank, local):
         peaks = _peaks()
         dom = "k_project" if t_prj >= t_add else "k_expand"
         t_dom = max(t_prj, t_add)
-        if prec in ("fp64", "ff64"):
+        if prec == "fp64":
             flops_dom = alg["flops_prj"] if dom == "k_project" else alg["flops_add"]
             achieved = flops_dom / (t_dom * 1e-3) / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
@@ -272,8 +276,10 @@ def run_ours(args, ws, rank, local):
             bytes_dom = alg["bytes_prj"] if dom == "k_project" else alg["bytes_add"]
             achieved = bytes_dom / (t_dom * 1e-3) / 1e9
             hbm = peaks.get("hbm_gbs", 6793.4)
+            traffic = NCU_TRAFFIC.get(dom) if (prec == "ff64" and args.workload == WORKLOAD and not args.bands) else None
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+                    "frac": round(achieved / hbm, 4), "traffic": traffic,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
         wl = {"c96": "periodic 96^3 grid, h=0.2, 64 atoms, sigma U[0.5,1], numax 5 (56 states), cube 32^3",
               "c160": "periodic 160^3 grid, h=0.2, 512 atoms, sigma U[0.5,1], numax 7 (120 states), cube 32^3",
               "c128": "periodic 128^3 grid, h=0.2, 128 atoms, sigma U[0.5,1], numax 5 (56 states), cube 32^3",
@@ -310,7 +316,7 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": 3 * K,
             "clocks": clk,
         }
-        default_case = args.workload == WORKLOAD and prec == "fp64" and not args.bands
+        default_case = args.workload == WORKLOAD and prec == "ff64" and not args.bands
         if not default_case:
             args.no_same_gpu_baselines = args.no_precision_forms = args.no_cpu_baseline = args.no_serving = True
         if not args.no_same_gpu_baselines:
@@ -325,7 +331,7 @@ def run_ours(args, ws, rank, local):
             result["precision_forms"] = precision_forms(api, handle, stream)
         if not args.no_cpu_baseline and ws == 1:
             result["cpu_baseline"], result["error_vs_oracle"] = cpu_baseline(
-                w, pos, sig, psi, cin, coeff, hpsi_ref=None, api=api, handle=handle)
+                w, pos, sig, psi, cin, coeff, hpsi_ref=None, api=api, handle=handle, prec=prec)
     return result
 
 
@@ -363,7 +369,28 @@ def same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream):
     ms = _time_steps(stream, usu_step)
     out["stored_projector_fp64"] = {"value": round(bytes_step / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
                                     "ms_per_step": round(ms, 4), "projector_bytes": proj.numel() * 8}
-    del proj, hpsi
+    del proj
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_prj, t_add = [], []
+    for i in range(8):
+        ev[0].record(stream)
+        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", out=coeff, handle=handle,
+                    stream=stream)
+        ev[1].record(stream)
+        api.add(hpsi, cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec="fp64", handle=handle, stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if i >= 2:
+            t_prj.append(ev[0].elapsed_time(ev[1]))
+            t_add.append(ev[1].elapsed_time(ev[2]))
+    tp, ta = float(np.median(t_prj)), float(np.median(t_add))
+    fl = alg["flops_prj"]
+    out["fp64_dfma"] = {"value": round(bytes_step / ((tp + ta) * 1e-3) / 1e9, 3), "unit": "GB/s",
+                        "ms_per_step": round(tp + ta, 4), "ms_project": round(tp, 4), "ms_expand": round(ta, 4),
+                        "fp64_pipe_frac_project": round(fl / (tp * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                        "fp64_pipe_frac_expand": round(fl / (ta * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                        "note": "native FP64 FMA form (FP64-pipe bound on GB300)"}
+    del hpsi
     psi32 = psi.float()
     cin32 = cin.float()
     c32 = torch.empty(cin.shape, dtype=torch.float32, device=psi.device)
@@ -525,7 +552,7 @@ def _oracle_sample(w, pos, sig, nsel, nbands_sel, seed=5):
     return sel, nbands_sel
 
 
-def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle):
+def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle, prec="ff64"):
     """Time the FP64 oracle, as it stands, on the workload (all atoms and bands: about ten seconds of
     host work on 16 cores) and state the GPU error against it."""
     import oracle
@@ -547,13 +574,13 @@ def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle):
     import torch
     z = torch.zeros_like(psi_d)
     api.add(z, cin_d[torch.as_tensor(sel, device=cin_d.device)].contiguous(), pos[sel], sig[sel], w.numax, w.cube,
-            w.h, w.periodic, prec="fp64", handle=handle)
+            w.h, w.periodic, prec=prec, handle=handle)
     err_a = float(np.linalg.norm(z.cpu().numpy() - out) / np.linalg.norm(out))
     base = {"value": round((alg["bytes_prj"] + alg["bytes_add"]) / secs / 1e9, 5), "unit": "GB/s", "cores": cores,
             "kind": "oracle", "seconds": round(secs, 3), "project_s": round(t1 - t0, 3), "add_s": round(t2 - t1, 3),
             "sample": f"{len(sel)} of {w.natoms} atoms (all {w.nbands} bands), project + expand, FP64 direct "
                       "summation over fully sampled 3D projectors"}
-    err = {"project_rel_norm": err_c, "expand_rel_norm": err_a, "tolerance": 1e-12,
+    err = {"project_rel_norm": err_c, "expand_rel_norm": err_a, "tolerance": 1e-12, "form": prec,
            "sample": f"{len(sel)} atoms"}
     return base, err
 
