@@ -390,6 +390,16 @@ def same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream):
                         "fp64_pipe_frac_project": round(fl / (tp * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
                         "fp64_pipe_frac_expand": round(fl / (ta * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
                         "note": "native FP64 FMA form (FP64-pipe bound on GB300)"}
+    # the full non-local action (project, per-atom D, expand) in the headline form
+    rng = np.random.default_rng(11)
+    Dm = rng.uniform(-1, 1, size=(w.natoms, cin.shape[1], cin.shape[1]))
+    Dm = torch.from_numpy(0.5 * (Dm + Dm.transpose(0, 2, 1))).to(psi.device)
+    hpsi.zero_()
+    msn = _time_steps(stream, lambda: api.apply_nonlocal(psi, hpsi, Dm, pos, sig, w.numax, w.cube, w.h, w.periodic,
+                                                         prec="ff64", handle=handle, stream=stream))
+    out["nonlocal_action_ff64"] = {"value": round(bytes_step / (msn * 1e-3) / 1e9, 3), "unit": "GB/s",
+                                   "ms_per_step": round(msn, 4),
+                                   "note": "hpsi += E D P psi with a random symmetric N x N D per atom"}
     del hpsi
     psi32 = psi.float()
     cin32 = cin.float()

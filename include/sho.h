@@ -159,6 +159,22 @@ int sho_forces(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dt
                int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                const void* dEdc, sho_dtype coeff_dtype, double* dEdX, void* stream);
 
+/*
+ * Non-local action -- the three steps of Sec. 3.2 with the SHO basis injected (Sec. 3.5):
+ *     hpsi[j][b] += sum_a sum_{k,k'} Psi_k(u) D[a][k][k'] c[a][k'][b],   c = projection of psi
+ * i.e. projection, multiplication by the atomic matrix (D = U^T F^T D F U of Sec. 3.5, an N x N matrix
+ * per atom in the Cartesian SHO basis) and expansion.  The projection and the multiplied coefficients
+ * live in the handle's workspace; psi and hpsi may not overlap.
+ *   psi    device [n[2]][n[1]][n[0]][nbands], psi_dtype (read only)
+ *   D      device [natoms][N][N], coefficient type of `prec` (F64 for FP64 / FF64, F32 otherwise),
+ *          row-major D[a][k][k'] with the library's state order
+ *   hpsi   device, same shape and dtype as psi (read-modify-write)
+ * Same precision / dtype rules as sho_project.
+ */
+int sho_apply_nonlocal(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
+                       int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                       const void* D, void* hpsi, void* stream);
+
 /* ----------------------------------------------------------------------------------------------
  * Stored-projector FP64 baseline: the conventional scheme the paper measures against ("USU", Sec. 6,
  * Table 1): projector values sampled once onto each atom's cube and kept in device memory, then

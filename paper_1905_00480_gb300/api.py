@@ -173,6 +173,30 @@ def forces(psi: torch.Tensor, dEdc: torch.Tensor, pos, sigma, numax: int, cube: 
     return out
 
 
+def apply_nonlocal(psi: torch.Tensor, hpsi: torch.Tensor, D: torch.Tensor, pos, sigma, numax: int, cube: int,
+                   h: float, periodic: bool = True, prec: str = "fp64", handle: Handle = None,
+                   stream=None) -> torch.Tensor:
+    """sho_apply_nonlocal (in place on hpsi): hpsi += sum_a |k> D[a][k][k'] <k'|psi>."""
+    _check_psi(psi)
+    _check_psi(hpsi)
+    if hpsi.shape != psi.shape or hpsi.dtype != psi.dtype:
+        raise ValueError("hpsi must match psi in shape and dtype")
+    pos_h = _host_f64(pos, 3)
+    sig_h = _host_f64(sigma).reshape(-1)
+    A, B = pos_h.shape[0], psi.shape[3]
+    Ns = nstates(numax)
+    if not D.is_cuda or not D.is_contiguous() or tuple(D.shape) != (A, Ns, Ns) or D.dtype != _coeff_dtype(prec):
+        raise ValueError("D must be a contiguous CUDA tensor [A][N][N] of the form's coefficient dtype")
+    hd = handle or default_handle(psi.device.index or 0)
+    g = _grid(psi, h, periodic)
+    st = N.lib().sho_apply_nonlocal(hd.ptr, ctypes.byref(g), ctypes.c_void_p(psi.data_ptr()),
+                                    N.DTYPES[_TORCH_DT[psi.dtype]], B, A, _dp(pos_h), _dp(sig_h), int(numax),
+                                    int(cube), N.PRECS[prec], ctypes.c_void_p(D.data_ptr()),
+                                    ctypes.c_void_p(hpsi.data_ptr()), _stream_ptr(psi, stream))
+    N.check(st, "sho_apply_nonlocal")
+    return hpsi
+
+
 # ------------------------------------------------------------------------ stored-projector baseline
 def usu_build(pos, sigma, numax: int, cube: int, grid_shape, h: float, periodic: bool = True, device=0,
               handle: Handle = None, stream=None) -> torch.Tensor:

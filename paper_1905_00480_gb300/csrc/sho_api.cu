@@ -15,6 +15,8 @@ struct sho_handle {
   void* ws = nullptr;          // device workspace (plan + intermediates), grows on demand
   size_t ws_bytes = 0;
   cudaEvent_t last = nullptr;  // completion of the handle's most recent call
+  void* coeff_ws = nullptr;    // coefficient buffers of the non-local action (c and D c)
+  size_t coeff_ws_bytes = 0;
   bool has_last = false;
   int device_error = SHO_OK;   // first device-side error since the last sho_sync
 };
@@ -342,6 +344,7 @@ int sho_destroy(sho_handle* h) {
     DeviceGuard guard(h->device);
     if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) st = SHO_ERR_CUDA;
     if (h->ws) cudaFree(h->ws);
+    if (h->coeff_ws) cudaFree(h->coeff_ws);
     if (h->last) cudaEventDestroy(h->last);
   }
   delete h;
@@ -523,6 +526,47 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   F.stream = s;
   if (launch_forces_contract(F) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
+}
+
+// ------------------------------------------------------------------ non-local action
+int sho_apply_nonlocal(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
+                       int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                       const void* D, void* hpsi, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
+  const sho_dtype cdt = is_f64_form(prec) ? SHO_F64 : SHO_F32;
+  SHO_TRY(check_dtypes(prec, psi_dtype, cdt));
+  SHO_TRY(check_tc(prec, numax, cube));
+  SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!psi || !hpsi || !D || psi == hpsi) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Coefficient buffers: c (projection) and d = D c.  They sit in a second allocation owned by the
+  // handle's workspace growth, ahead of what the nested calls carve, so use a dedicated region: the
+  // workspace is sized for the larger of the nested calls plus both coefficient arrays.
+  const size_t nco = (size_t)natoms * nstates(numax) * (size_t)nbands * compute_size(cdt);
+  const size_t inner = std::max(workspace_bytes(SHO_OP_PROJECT, grid, natoms, numax, cube, nbands, cdt),
+                                workspace_bytes(SHO_OP_EXPAND, grid, natoms, numax, cube, nbands, cdt));
+  SHO_TRY(begin_call(h, s));
+  if (!h->coeff_ws || h->coeff_ws_bytes < 2 * nco) {
+    if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+    if (h->coeff_ws) cudaFree(h->coeff_ws);
+    h->coeff_ws = nullptr;
+    h->coeff_ws_bytes = 0;
+    if (cudaMalloc(&h->coeff_ws, 2 * nco) != cudaSuccess) {
+      cudaGetLastError();
+      return SHO_ERR_OOM;
+    }
+    h->coeff_ws_bytes = 2 * nco;
+  }
+  SHO_TRY(ensure_workspace(h, inner));
+  void* c = h->coeff_ws;
+  void* d = static_cast<char*>(h->coeff_ws) + nco;
+  SHO_TRY(sho_project(h, grid, psi, psi_dtype, nbands, natoms, pos, sigma, numax, cube, prec, c, cdt, stream));
+  if (launch_dmatrix(natoms, nstates(numax), nbands, cdt, D, c, d, s) != cudaSuccess) return SHO_ERR_CUDA;
+  return sho_add(h, grid, d, cdt, nbands, natoms, pos, sigma, numax, cube, prec, hpsi, psi_dtype, stream);
 }
 
 // ------------------------------------------------------------------ stored-projector baseline

@@ -99,6 +99,8 @@ struct UsuLaunch {
 cudaError_t launch_usu(int op, const UsuLaunch& p);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
+cudaError_t launch_dmatrix(int natoms, int nstates, int nbands, sho_dtype dt, const void* D, const void* c, void* d,
+                           cudaStream_t s);
 cudaError_t launch_project_ff(const ProjectLaunch& p);
 cudaError_t launch_expand_ff(const ExpandLaunch& p);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
