@@ -57,6 +57,12 @@ def _compile(nvcc: str, src: str, verbose: bool) -> str:
     obj = os.path.join(OBJ_DIR, f"{base}.{_digest(src)}.o")
     if os.path.exists(obj):
         return obj
+    for old in os.listdir(OBJ_DIR):  # objects of earlier versions of this source
+        if old.startswith(base + ".") and old.endswith(".o"):
+            try:
+                os.remove(os.path.join(OBJ_DIR, old))
+            except OSError:
+                pass
     cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -259,7 +259,7 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
     cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
     cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
-    cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 8);
+    cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 16);
   }
   return cv.off;
 }
@@ -432,7 +432,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
   const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
   const size_t o_t2 = cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
-  const size_t o_txm = cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 8);
+  const size_t o_txm = cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 16);
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));

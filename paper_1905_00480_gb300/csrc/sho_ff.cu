@@ -46,7 +46,8 @@ struct FfProjectSmem {
   static size_t bytes(int cube) {
     size_t t = ring_bytes(cube);
     t += (size_t)cube * NPX * sizeof(float2);                      // x table (pairs), x-major
-    t += 2 * (size_t)NP * cube * sizeof(double);                   // y, z tables (FP64)
+    t += (size_t)NP * cube * sizeof(float2);                       // y table (pairs)
+    t += (size_t)NP * cube * sizeof(double);                       // z table (FP64)
     t += (size_t)cube * sizeof(long long);                         // x offsets
     t = (t + 15) & ~(size_t)15;
     if (!ACCR) t += (size_t)N * kWarp * sizeof(double);            // partial coefficients
@@ -67,10 +68,11 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
   unsigned char* ring = smem_raw;
   const size_t ringb = SM::ring_bytes(C);
   float2* phx = reinterpret_cast<float2*>(ring + ringb);                     // [C][NPX] pairs
-  double* phy = reinterpret_cast<double*>(phx + (size_t)C * NPX);            // [NP][C]
-  double* phz = phy + (size_t)NP * C;                                        // [NP][C]
+  float2* phy = phx + (size_t)C * NPX;                                       // [NP][C] pairs
+  double* phz = reinterpret_cast<double*>(phy + (size_t)NP * C);             // [NP][C]
   long long* xoff = reinterpret_cast<long long*>(phz + (size_t)NP * C);      // [C]
-  size_t off = ringb + (size_t)C * NPX * sizeof(float2) + 2 * (size_t)NP * C * sizeof(double) + (size_t)C * 8;
+  size_t off = ringb + (size_t)C * NPX * sizeof(float2) + (size_t)NP * C * (sizeof(float2) + sizeof(double)) +
+               (size_t)C * 8;
   off = (off + 15) & ~(size_t)15;
   double* acc = ACCR ? reinterpret_cast<double*>(ring) : reinterpret_cast<double*>(smem_raw + off);  // [N][32]
 
@@ -89,7 +91,12 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       const ff f = n < NP ? ff_from_double_exact(col[n]) : ff{0.0f, 0.0f};
       phx[i * NPX + n] = make_float2(f.hi, f.lo);
     }
-    phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, phy + i, C);
+    phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, col, 1);
+#pragma unroll
+    for (int n = 0; n < NP; n++) {
+      const ff f = ff_from_double_exact(col[n]);
+      phy[n * C + i] = make_float2(f.hi, f.lo);
+    }
     phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
     const int jx = cube_index(at.o[0], i, g.n[0], g.periodic);
     xoff[i] = jx < 0 ? -1ll : (long long)jx * B;
@@ -147,9 +154,9 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     issue(r);
     ff_commit();
   }
-  double t2[P];
+  float t2s[P], t2c[P];  // y-pass accumulators of the current plane, float pairs
 #pragma unroll
-  for (int p = 0; p < P; p++) t2[p] = 0.0;
+  for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
 
   for (int r = 0; r < R; r++) {
     ff_wait<kFfStages - 2>();
@@ -176,20 +183,24 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
           if (2 * q + 1 < NP) ff_dot_step(S[2 * q + 1], E[2 * q + 1], pv, ff{f.z, f.w});
         }
       }
-      double t1[NP];
+      ff t1[NP];
 #pragma unroll
-      for (int n = 0; n < NP; n++) t1[n] = ff_to_double(S[n], E[n]);
-      // y-pass (a4) in FP64
+      for (int n = 0; n < NP; n++) t1[n] = ff_norm(S[n], E[n]);
+      // y-pass (a4) as float-float dot steps
 #pragma unroll
       for (int ny = 0; ny < NP; ny++) {
-        const double w = phy[ny * C + iy];
+        const float2 w = phy[ny * C + iy];
 #pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++) t2[BS::pair(nx, ny)] = fma(t1[nx], w, t2[BS::pair(nx, ny)]);
+        for (int nx = 0; nx + ny <= NU; nx++)
+          ff_dot_step(t2s[BS::pair(nx, ny)], t2c[BS::pair(nx, ny)], t1[nx], ff{w.x, w.y});
       }
     }
     __syncwarp();
     if (iy == C - 1) {
       // z-pass (a5) in FP64 for the finished plane
+      double t2[P];
+#pragma unroll
+      for (int p = 0; p < P; p++) t2[p] = ff_to_double(t2s[p], t2c[p]);
       int k = 0;
 #pragma unroll
       for (int nz = 0; nz < NP; nz++) {
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
           }
       }
 #pragma unroll
-      for (int p = 0; p < P; p++) t2[p] = 0.0;
+      for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
     }
   }
   ff_wait<0>();
@@ -229,18 +240,34 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
 }
 
 // ------------------------------------------------------------------------------- expansion
-// x tables of every atom as float pairs, x-major [A][C][NPX], from the FP64 tables [A][2][NP][C].
+// Float-pair copies of the expansion intermediates: the x tables x-major [A][C][NPX], the y tables
+// [A][NP][C] (from the FP64 tables [A][2][NP][C]) and the z-pass result T2 (same layout as the FP64 T2,
+// converted in place: a double and a float pair are both 8 bytes).
 template <int NU>
-__global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tables, float2* __restrict__ txff) {
+__global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tables, float2* __restrict__ txff,
+                            float2* __restrict__ tyff, double* __restrict__ t2, long long t2_count) {
   constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
-  const long long total = (long long)natoms * cube * NPX;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+  const long long nx_total = (long long)natoms * cube * NPX;
+  const long long ny_total = (long long)natoms * NP * cube;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nx_total; i += stride) {
     const int n = (int)(i % NPX);
     const long long ai = i / NPX;
     const int ix = (int)(ai % cube);
     const int a = (int)(ai / cube);
     const ff f = n < NP ? ff_from_double_exact(tables[((long long)a * 2 * NP + n) * cube + ix]) : ff{0.0f, 0.0f};
     txff[i] = make_float2(f.hi, f.lo);
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ny_total; i += stride) {
+    const long long a = i / ((long long)NP * cube);
+    const long long rest = i - a * NP * cube;  // n * cube + iy
+    const ff f = ff_from_double_exact(tables[(a * 2 + 1) * NP * cube + rest]);
+    tyff[i] = make_float2(f.hi, f.lo);
+  }
+  float2* t2f = reinterpret_cast<float2*>(t2);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < t2_count; i += stride) {
+    const ff f = ff_from_double_exact(t2[i]);
+    t2f[i] = make_float2(f.hi, f.lo);
   }
 }
 
@@ -256,20 +283,23 @@ constexpr int kFfXSeg = 32;
 template <int NU>
 struct FfBlkSmem {
   static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 1) & ~1;
-  // bytes of one staging buffer: T2 [P][32] doubles + x pairs [C][NPX] + y [NP][C] doubles
+  // bytes of one staging buffer: T2 [P][32] pairs + x pairs [C][NPX] + y pairs [NP][C]
   __host__ __device__ static size_t buf_bytes(int cube) {
     return (size_t)P * 32 * 8 + (size_t)cube * NPX * 8 + (size_t)NP * cube * 8;
   }
-  static size_t bytes(int cube, int max_plane) { return 2 * buf_bytes(cube) + (size_t)(max_plane + 1) * 4; }
+  // 2 staging buffers + per-warp update accumulators [8 warps][32 x][32 bands] float pairs + atom list
+  static size_t bytes(int cube, int max_plane) {
+    return 2 * buf_bytes(cube) + (size_t)kFfRows * kFfXSeg * kWarp * 8 + (size_t)(max_plane + 1) * 4;
+  }
 };
 
 template <int NU>
 __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, const AtomDev* __restrict__ atoms,
                                                                    const int* __restrict__ plane_ptr,
                                                                    const int* __restrict__ plane_atoms,
-                                                                   const double* __restrict__ tables,
+                                                                   const float2* __restrict__ tyff,
                                                                    const float2* __restrict__ txff,
-                                                                   const double* __restrict__ t2,
+                                                                   const float2* __restrict__ t2,
                                                                    double* __restrict__ psi) {
   using BS = Basis<NU>;
   using SM = FfBlkSmem<NU>;
@@ -278,7 +308,8 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   const int C = g.cube;
   const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
   const size_t bufb = SM::buf_bytes(C);
-  int* slist = reinterpret_cast<int*>(smem_raw + 2 * bufb);
+  float2* accs = reinterpret_cast<float2*>(smem_raw + 2 * bufb);  // [warps][32 x][32 bands]
+  int* slist = reinterpret_cast<int*>(accs + kFfRows * kFfXSeg * kWarp);
   __shared__ int wcount[kFfRows];
   __shared__ int s_nlist;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -320,8 +351,8 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
       if (iz < 0) iz += Nz;
     }
     unsigned char* dst = smem_raw + (size_t)buf * bufb;
-    double* dt2 = reinterpret_cast<double*>(dst);
-    const double* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
+    float2* dt2 = reinterpret_cast<float2*>(dst);
+    const float2* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
     for (int q = tid; q < P * 32; q += kFfRows * kWarp) {
       const int p = q >> 5, bl = q & 31;
       const bool ok = b0 + bl < B;
@@ -330,8 +361,8 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     float2* dx = reinterpret_cast<float2*>(dst + (size_t)P * 32 * 8);
     const float2* src_x = txff + (size_t)a * C * NPX;
     for (int q = tid; q < C * NPX; q += kFfRows * kWarp) cp8(dx + q, src_x + q, 8);
-    double* dy = reinterpret_cast<double*>(dst + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
-    const double* src_y = tables + ((size_t)a * 2 + 1) * NP * C;
+    float2* dy = reinterpret_cast<float2*>(dst + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
+    const float2* src_y = tyff + (size_t)a * NP * C;
     for (int q = tid; q < NP * C; q += kFfRows * kWarp) cp8(dy + q, src_y + q, 8);
   };
 
@@ -359,9 +390,10 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   }
   const int nlist = s_nlist;
 
-  float uh[kFfXSeg], ul[kFfXSeg];  // update of the 32 x points of this row, as float pairs
+  float2* accw = accs + warp * kFfXSeg * kWarp;  // this row's update of the 32 x points, float pairs
 #pragma unroll
-  for (int x = 0; x < kFfXSeg; x++) uh[x] = ul[x] = 0.0f;
+  for (int x = 0; x < kFfXSeg; x++) accw[x * kWarp + lane] = make_float2(0.0f, 0.0f);
+  const int xend = min(kFfXSeg, Nx - xs);       // tile points that exist on the grid
 
   int buf = 0;
   if (nlist > 0) stage(slist[0], 0);
@@ -373,9 +405,9 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     ff_wait<1>();
     __syncthreads();
     const unsigned char* src = smem_raw + (size_t)buf * bufb;
-    const double* t2s = reinterpret_cast<const double*>(src);
+    const float2* t2s = reinterpret_cast<const float2*>(src);
     const float2* txs = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8);
-    const double* tys = reinterpret_cast<const double*>(src + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
+    const float2* tys = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
     const AtomDev at = atoms[a];
     int iy = y - at.o[1];
     if (g.periodic) {
@@ -383,30 +415,46 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
       if (iy < 0) iy += Ny;
     }
     if (yok && iy >= 0 && iy < C) {
-      // y-pass in FP64
-      double t1[NP];
+      // y-pass as float-float dot steps
+      float ys[NP], yc[NP];
 #pragma unroll
-      for (int n = 0; n < NP; n++) t1[n] = 0.0;
+      for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
 #pragma unroll
       for (int ny = 0; ny < NP; ny++) {
-        const double w = tys[ny * C + iy];
+        const float2 w = tys[ny * C + iy];
 #pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fma(t2s[BS::pair(nx, ny) * 32 + lane], w, t1[nx]);
+        for (int nx = 0; nx + ny <= NU; nx++) {
+          const float2 v = t2s[BS::pair(nx, ny) * 32 + lane];
+          ff_dot_step(ys[nx], yc[nx], ff{v.x, v.y}, ff{w.x, w.y});
+        }
       }
       ff t1f[NP];
 #pragma unroll
-      for (int n = 0; n < NP; n++) t1f[n] = ff_from_double(t1[n]);
+      for (int n = 0; n < NP; n++) t1f[n] = ff_norm(ys[n], yc[n]);
       int dx = xs - at.o[0];
       if (g.periodic) {
         dx %= Nx;
         if (dx < 0) dx += Nx;
       }
-      // x-pass as float-float dot products into the register update
-#pragma unroll
-      for (int x = 0; x < kFfXSeg; x++) {
-        int ix = dx + x;
-        if (g.periodic && ix >= Nx) ix -= Nx;
-        if (ix >= 0 && ix < C) {
+      // x-pass as float-float dot products over the tile points inside the cube: one contiguous run
+      // of x (two when the cube wraps around a periodic grid)
+      int r0a, r0b, r1a, r1b;
+      if (g.periodic) {
+        r0a = 0;
+        r0b = dx < C ? min(xend, C - dx) : 0;           // ix = dx + x
+        r1a = Nx - dx;                                  // ix = dx + x - Nx
+        r1b = min(xend, Nx - dx + C);
+      } else {
+        r0a = max(0, -dx);
+        r0b = min(xend, C - dx);
+        r1a = r1b = 0;
+      }
+      for (int run = 0; run < 2; run++) {
+        const int xa = run ? max(r1a, r0b) : r0a, xb = run ? r1b : r0b;
+        const int shift = run ? dx - Nx : dx;
+#pragma unroll 2
+        for (int x = xa; x < xb; x++) {
+          const int ix = x + shift;
           float s = 0.0f, c = 0.0f;
           const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
 #pragma unroll
@@ -415,7 +463,9 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
             if (2 * qn < NP) ff_dot_step(s, c, t1f[2 * qn], ff{f.x, f.y});
             if (2 * qn + 1 < NP) ff_dot_step(s, c, t1f[2 * qn + 1], ff{f.z, f.w});
           }
-          ff_add(uh[x], ul[x], s, c);
+          float2 v = accw[x * kWarp + lane];
+          ff_add(v.x, v.y, s, c);
+          accw[x * kWarp + lane] = v;
         }
       }
     }
@@ -425,9 +475,10 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   ff_wait<0>();
   if (!yok || !bok || nlist == 0) return;
   double* rowp = psi + ((size_t)z * Ny + y) * (size_t)Nx * B + b0 + lane;
-#pragma unroll
-  for (int x = 0; x < kFfXSeg; x++)
-    if (xs + x < Nx) rowp[(size_t)(xs + x) * B] += ff_to_double(uh[x], ul[x]);
+  for (int x = 0; x < xend; x++) {
+    const float2 v = accw[x * kWarp + lane];
+    rowp[(size_t)(xs + x) * B] += ff_to_double(v.x, v.y);
+  }
 }
 
 // ------------------------------------------------------------------------------- launchers
@@ -458,9 +509,13 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   constexpr int NPX = (NU + 2) & ~1;
   cudaError_t e = launch_expand_zpass_f64(p);
   if (e != cudaSuccess) return e;
-  const long long total = (long long)p.natoms * p.g.cube * NPX;
-  k_ff_tables<NU><<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, p.stream>>>(
-      p.natoms, p.g.cube, static_cast<const double*>(p.tables), static_cast<float2*>(p.tables_xmajor));
+  const long long t2_count = (long long)p.natoms * p.g.cube * Basis<NU>::P * p.g.nbands;
+  const long long total = std::max<long long>(t2_count, (long long)p.natoms * p.g.cube * NPX);
+  // y pairs go after the x pairs in the x-major region (sized for [A][C][4 * ceil(NP/4)] doubles)
+  float2* txff = static_cast<float2*>(p.tables_xmajor);
+  float2* tyff = txff + (size_t)p.natoms * p.g.cube * NPX;
+  k_ff_tables<NU><<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, p.stream>>>(
+      p.natoms, p.g.cube, static_cast<const double*>(p.tables), txff, tyff, static_cast<double*>(p.t2), t2_count);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   auto kern = k_expand_blk_ff<NU>;
@@ -469,8 +524,8 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   if (e != cudaSuccess) return e;
   const int nseg = (p.g.n[0] + kFfXSeg - 1) / kFfXSeg, nyb = (p.g.n[1] + kFfRows - 1) / kFfRows;
   kern<<<dim3((unsigned)nseg * nyb * p.g.n[2], (p.g.nbands + kWarp - 1) / kWarp), kFfRows * kWarp, smem, p.stream>>>(
-      p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const double*>(p.tables),
-      static_cast<const float2*>(p.tables_xmajor), static_cast<const double*>(p.t2), static_cast<double*>(p.psi));
+      p.g, p.atoms, p.plane_ptr, p.plane_atoms, tyff, txff, static_cast<const float2*>(p.t2),
+      static_cast<double*>(p.psi));
   return cudaGetLastError();
 }
 

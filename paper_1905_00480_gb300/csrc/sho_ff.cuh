@@ -85,6 +85,15 @@ __device__ __forceinline__ void ff_dot_step(float& s, float& c, const ff a, cons
   c += err + e;
 }
 
+// Renormalise a pair so that |lo| <= ulp(hi)/2 (Fast2Sum; valid because |c| <= |s| here).
+__device__ __forceinline__ ff ff_norm(float s, float c) {
+  const float t = s + c;
+  ff r;
+  r.hi = t;
+  r.lo = c - (t - s);
+  return r;
+}
+
 // (s, c) += (u, v): add two pair values, error-free on the leading parts.
 __device__ __forceinline__ void ff_add(float& s, float& c, float u, float v) {
   const float t = s + u;
