@@ -319,8 +319,11 @@ def run_ours(args, ws, rank, local):
         default_case = args.workload == WORKLOAD and prec == "ff64" and not args.bands
         if not default_case:
             args.no_same_gpu_baselines = args.no_precision_forms = args.no_cpu_baseline = args.no_serving = True
+            args.no_forces = True
         if not args.no_same_gpu_baselines:
             result["same_gpu_baselines"] = same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream)
+        if not args.no_forces:
+            result["forces"] = forces_bench(api, handle, stream)
         if not args.no_serving:
             result["serving"] = serving_bench(api)
             st = result["serving"]["loads"].get("0.8") or next(iter(result["serving"]["loads"].values()))
@@ -556,6 +559,46 @@ def serving_bench(api, nsys=12, warm=200, measured=1000, loads=(0.5, 0.8, 0.95),
 SERVE_SEED = 4242
 
 
+def forces_bench(api, handle, stream, steps=5):
+    """Differentiation workload: periodic 128^3, 128 atoms, numax 5, 64 bands FP32; E = sum D c^2 with
+    D ~ U[-1,1].  Times one forward (projection) + backward (forces and dE/dpsi = h^3 E(2 D c)) through the
+    autograd Function, and states the error of the FP32 forces against the FP64 form on the same GPU."""
+    import torch
+    from paper_1905_00480_gb300.autograd import sho_project
+    w = workloads.WORKLOADS["c128"]
+    pos, sig = workloads.atoms(w)
+    N = api.nstates(w.numax)
+    D = torch.from_numpy(workloads.dmatrix_host(w, N)).cuda().float()
+    psi = workloads.psi_device(w).requires_grad_(True)
+    sig_t = torch.from_numpy(sig)
+
+    def step():
+        X = torch.tensor(pos, dtype=torch.float64, requires_grad=True)
+        c = sho_project(psi, X, sig_t, w.numax, w.cube, w.h, w.periodic, prec="fp32")
+        E = (D[:, :, None] * c * c).sum()
+        E.backward()
+        return X.grad, c.detach()
+
+    F, c = step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        psi.grad = None
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    dEdc64 = (2.0 * D[:, :, None] * c).double()
+    F64 = api.forces(psi.detach().double(), dEdc64.contiguous(), pos, sig, w.numax, w.cube, w.h, w.periodic,
+                     prec="ff64").cpu()
+    err = float((F - F64).abs().max() / F64.abs().max())
+    return {"workload": "periodic 128^3, h=0.2, 128 atoms, numax 5, cube 32, 64 bands FP32, E = sum D c^2",
+            "ms_forward_backward": round(ms, 4), "forces_err_vs_fp64_form": err,
+            "note": "forward projection + backward (forces via the numax+1 projection, dE/dpsi via the "
+                    "expansion) through torch.autograd; finite-difference and oracle checks are in the tests"}
+
+
 def _oracle_sample(w, pos, sig, nsel, nbands_sel, seed=5):
     rng = np.random.default_rng(seed)
     sel = np.sort(rng.choice(w.natoms, size=nsel, replace=False))
@@ -577,7 +620,17 @@ def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle, prec
     out = oracle.add(w.grid, w.h, w.periodic, np.zeros_like(psi), pos[sel], sig[sel], w.numax, w.cube, cin[sel])
     t2 = time.perf_counter()
     secs = t2 - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.set_threads(0)
+    # one core, on two atoms (scaled per byte like the all-core figure)
+    sel1 = sel[:2]
+    alg1 = algorithmic(workloads.Workload(**{**w.__dict__, "natoms": len(sel1)}), pos[sel1], api.nstates(w.numax))
+    oracle.set_threads(1)
+    t3 = time.perf_counter()
+    oracle.project(w.grid, w.h, w.periodic, psi, pos[sel1], sig[sel1], w.numax, w.cube)
+    oracle.add(w.grid, w.h, w.periodic, np.zeros_like(psi), pos[sel1], sig[sel1], w.numax, w.cube, cin[sel1])
+    t4 = time.perf_counter()
+    oracle.set_threads(cores)
+    one_core = (alg1["bytes_prj"] + alg1["bytes_add"]) / (t4 - t3) / 1e9
     got_c = coeff_d.cpu().numpy()[sel]
     err_c = float(np.linalg.norm(got_c - ref_c) / np.linalg.norm(ref_c))
     # GPU expansion of the same atoms into zeros
@@ -588,6 +641,7 @@ def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle, prec
     err_a = float(np.linalg.norm(z.cpu().numpy() - out) / np.linalg.norm(out))
     base = {"value": round((alg["bytes_prj"] + alg["bytes_add"]) / secs / 1e9, 5), "unit": "GB/s", "cores": cores,
             "kind": "oracle", "seconds": round(secs, 3), "project_s": round(t1 - t0, 3), "add_s": round(t2 - t1, 3),
+            "one_core_value": round(one_core, 5), "one_core_sample": "2 atoms, all bands",
             "sample": f"{len(sel)} of {w.natoms} atoms (all {w.nbands} bands), project + expand, FP64 direct "
                       "summation over fully sampled 3D projectors"}
     err = {"project_rel_norm": err_c, "expand_rel_norm": err_a, "tolerance": 1e-12, "form": prec,
@@ -625,7 +679,7 @@ def run_reference(args, ws, rank):
         a = algorithmic(sw, pos[sel], N)
         byts += a["bytes_prj"] + a["bytes_add"]
     secs = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.set_threads(0)
     value = byts / secs / 1e9
     return {
         "impl": "reference",
@@ -650,6 +704,7 @@ def main():
     ap.add_argument("--no-same-gpu-baselines", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-forces", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--prec", default=None, choices=["fp64", "ff64", "fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "bf16"])

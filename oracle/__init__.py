@@ -48,6 +48,8 @@ def _load():
             i64p = ctypes.POINTER(ctypes.c_int64)
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int)
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             lib.oracle_nstates.argtypes = [ctypes.c_int]
             lib.oracle_nstates.restype = ctypes.c_int
             lib.oracle_basis.argtypes = [ctypes.c_int, ip]
@@ -91,6 +93,11 @@ def _f64(a, shape=None):
 def _check(rc, what):
     if rc != 0:
         raise ValueError(f"oracle {what} rejected its arguments (code {rc})")
+
+
+def set_threads(n: int) -> int:
+    """Set the oracle's OpenMP thread count (n <= 0 leaves it); returns the count now in effect."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def nstates(numax: int) -> int:

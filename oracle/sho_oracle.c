@@ -42,6 +42,21 @@
 
 #define ORACLE_MAX_NUMAX 16
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of OpenMP threads the oracle uses (for timing it on one core and on all cores). */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 int oracle_nstates(int numax) {
   if (numax < 0) return 0;
   return (numax + 1) * (numax + 2) * (numax + 3) / 6;
