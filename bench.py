@@ -649,6 +649,135 @@ def cpu_baseline(w, pos, sig, psi_d, cin_d, coeff_d, hpsi_ref, api, handle, prec
     return base, err
 
 
+# ----------------------------------------------------------------------------------- the paper's Table 1
+# Timings of Table 1 (Sec. 6), seconds for 10 executions of one kernel: (#, USUprj, SHOprj, USUadd, SHOadd);
+# None where the paper has no SHO entry (no SHO basis has 18 states).  Printed next to the GB300 figures as
+# context only: other GPUs, other kernels.
+PAPER_TABLE1 = {
+    "P100": [(1, 0.480, 0.453, 0.274, 0.187), (4, 0.834, 0.471, 0.803, 0.363), (10, 1.259, 0.430, 1.820, 0.520),
+             (18, 2.080, None, 3.173, None), (20, 2.366, 0.482, 3.511, 0.733), (35, 3.904, 0.967, 6.052, 1.027),
+             (56, 6.058, 1.214, 9.625, 1.455)],
+    "V100": [(1, 0.291, 0.271, 0.140, 0.118), (4, 0.354, 0.310, 0.378, 0.189), (10, 0.555, 0.284, 0.823, 0.277),
+             (18, 0.830, None, 1.411, None), (20, 1.013, 0.300, 1.557, 0.398), (35, 2.087, 0.575, 2.660, 0.564),
+             (56, 1.806, 0.793, 4.208, 0.792)],
+}
+
+
+def _median_ms(stream, fn, reps, runs):
+    """The paper's protocol, shortened: one untimed run, then `runs` timed runs of `reps` executions each;
+    returns the median over runs of the time per execution (ms)."""
+    import torch
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    per = []
+    for _ in range(runs):
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        ev[1].synchronize()
+        per.append(ev[0].elapsed_time(ev[1]) / reps)
+    return float(np.median(per))
+
+
+def _clipped_cube_points(grid, h, cube, pos):
+    """Grid points inside the (non-periodic) domain summed over the atoms' cubes."""
+    tot = 0
+    for X in pos:
+        o = np.floor(X / h).astype(int) - cube // 2 + 1
+        cnt = 1
+        for d in range(3):
+            j = o[d] + np.arange(cube)
+            cnt *= int(((j >= 0) & (j < grid[d])).sum())
+        tot += cnt
+    return tot
+
+
+def paper_table1(args):
+    """SHO (generated on the fly) against stored projector values (USU) on the paper's benchmark system:
+    64^3 grid at 0.25 A, the 665 fcc atoms (a = 4.08 A) whose 3.55 A sphere touches the 16 A domain,
+    1024 FP64 wave functions, not periodic, cube 32 (Sec. 6, Tables 1 and 2)."""
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, pos, sig = workloads.fcc_paper_geometry()
+    cube, B = 32, 1024
+    dev = torch.device("cuda", 0)
+    handle = api.Handle(0)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(workloads.SEED_BASE + 6)
+    psi = torch.randn((grid[2], grid[1], grid[0], B), generator=g, device=dev, dtype=torch.float64)
+    hpsi = torch.zeros_like(psi)
+    A = len(pos)
+    pts = _clipped_cube_points(grid, h, cube, pos)
+    sho_reps, usu_reps, runs = args.table_reps, 1, args.table_runs
+    rows = []
+    sho = {}
+    for nu in range(6):
+        N = api.nstates(nu)
+        coeff = torch.empty((A, N, B), dtype=torch.float64, device=dev)
+        cin = torch.randn((A, N, B), generator=g, device=dev, dtype=torch.float64)
+        for prec in ("fp64", "ff64"):
+            t_prj = _median_ms(stream, lambda: api.project(psi, pos, sig, nu, cube, h, False, prec=prec, out=coeff,
+                                                           handle=handle, stream=stream), sho_reps, runs)
+            t_add = _median_ms(stream, lambda: api.add(hpsi, cin, pos, sig, nu, cube, h, False, prec=prec,
+                                                       handle=handle, stream=stream), sho_reps, runs)
+            sho[(N, prec)] = (t_prj, t_add)
+        del coeff, cin
+    usu = {}
+    check = {}
+    for N in (1, 4, 10, 18, 20, 35, 56):
+        nu = next(v for v in range(6) if api.nstates(v) >= N)
+        proj = api.usu_build(pos, sig, nu, cube, grid, h, False, device=0, handle=handle, stream=stream, nproj=N)
+        coeff = torch.empty((A, N, B), dtype=torch.float64, device=dev)
+        cin = torch.randn((A, N, B), generator=g, device=dev, dtype=torch.float64)
+        t_prj = _median_ms(stream, lambda: api.usu_project(psi, proj, pos, sig, nu, cube, h, False, out=coeff,
+                                                           handle=handle, stream=stream), usu_reps, runs)
+        t_add = _median_ms(stream, lambda: api.usu_add(hpsi, cin, proj, pos, sig, nu, cube, h, False, handle=handle,
+                                                       stream=stream), usu_reps, runs)
+        usu[N] = (t_prj, t_add, proj.numel() * 8)
+        if api.nstates(nu) == N:
+            ref = api.project(psi, pos, sig, nu, cube, h, False, prec="ff64", handle=handle, stream=stream)
+            check[N] = float((ref - coeff).norm() / ref.norm())
+        del proj, coeff, cin
+        torch.cuda.empty_cache()
+    flop_usu = lambda N: 2.0 * pts * N * B
+    for N in (1, 4, 10, 18, 20, 35, 56):
+        up, ua, pbytes = usu[N]
+        row = {"n": N, "usu_prj_ms": round(up, 3), "usu_add_ms": round(ua, 3),
+               "usu_projector_gb": round(pbytes / 1e9, 3),
+               "usu_fp64_tflops": [round(flop_usu(N) / (up * 1e-3) / 1e12, 3),
+                                   round(flop_usu(N) / (ua * 1e-3) / 1e12, 3)]}
+        for prec in ("fp64", "ff64"):
+            if (N, prec) in sho:
+                sp, sa = sho[(N, prec)]
+                row[f"sho_{prec}_prj_ms"] = round(sp, 3)
+                row[f"sho_{prec}_add_ms"] = round(sa, 3)
+                row[f"S_{prec}"] = [round(up / sp, 2), round(ua / sa, 2)]
+        if N in check:
+            row["sho_ff64_vs_usu_rel_norm"] = check[N]
+        rows.append(row)
+    fair = {}
+    up, ua, _ = usu[18]
+    for prec in ("fp64", "ff64"):
+        sp, sa = sho[(35, prec)]
+        fair[prec] = {"prj": round(up / sp, 2), "add": round(ua / sa, 2), "both": round((up + ua) / (sp + sa), 2)}
+    paper_fair = {"P100": {"prj": 2.2, "add": 3.1, "both": 2.6}, "V100": {"prj": 1.4, "add": 2.5, "both": 2.0}}
+    return {
+        "metric": "SHO vs stored-projector (USU) kernel time and speedup S = USU/SHO, the paper's Tables 1 and 2",
+        "unit": "ms per execution", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"fcc a=4.08 A, 16 A cube at h=0.25 A (64^3), {A} atoms touching (3.55 A), "
+                               f"sigma 0.59 Bohr, {B} bands FP64 N(0,1), not periodic, cube 32",
+                   "protocol": f"one untimed run, median of {runs} runs of {sho_reps} (SHO) / {usu_reps} (USU) "
+                               "executions; psi 2.1 GB > L2",
+                   "clipped_cube_points": pts},
+        "rows": rows, "fair_usu18_vs_sho35": fair, "paper_fair_usu18_vs_sho35_double": paper_fair,
+        "paper_table1_s_per_10_executions": PAPER_TABLE1,
+    }
+
+
 # ----------------------------------------------------------------------------------- reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -709,7 +838,14 @@ def main():
     ap.add_argument("--prec", default=None, choices=["fp64", "ff64", "fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
     ap.add_argument("--storage", default=None, choices=["f64", "f32", "bf16"])
     ap.add_argument("--bands", type=int, default=0)
+    ap.add_argument("--paper-table1", action="store_true",
+                    help="time SHO against stored projectors on the paper's fcc benchmark system and exit")
+    ap.add_argument("--table-reps", type=int, default=10)
+    ap.add_argument("--table-runs", type=int, default=3)
     args = ap.parse_args()
+    if args.paper_table1:
+        print(json.dumps(paper_table1(args)), flush=True)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     ws, rank, local = dist_init()

@@ -178,21 +178,23 @@ int sho_apply_nonlocal(sho_handle* handle, const sho_grid* grid, const void* psi
 /* ----------------------------------------------------------------------------------------------
  * Stored-projector FP64 baseline: the conventional scheme the paper measures against ("USU", Sec. 6,
  * Table 1): projector values sampled once onto each atom's cube and kept in device memory, then
- * streamed by the projection and expansion.  Same definitions, conventions and results as
- * sho_project / sho_add in SHO_P_FP64 (up to rounding order); numax <= SHO_USU_MAX_NUMAX (the paper's
- * Table 1 goes up to 56 coefficients, numax 5).
- *   proj   device [natoms][cube^3][sho_nstates(numax)] double, cube point index (iz*cube + iy)*cube + ix;
- *          written by sho_usu_build, read by the other two (caller allocates: 8 * A * C^3 * N bytes).
- *   psi, coeff as for sho_project / sho_add, FP64 only.  pos / sigma host arrays as above.
+ * streamed by the projection and expansion.  With the stored values taken from the SHO basis the
+ * results equal sho_project / sho_add in SHO_P_FP64 (up to rounding order).
+ *   numax  basis the stored projectors are sampled from (numax <= SHO_USU_MAX_NUMAX)
+ *   nproj  number of stored projectors: the first nproj states of that basis; one of 1, 4, 10, 18, 20,
+ *          35, 56 (the SHO sizes of numax 0..5, and 18 = the s, s*, p, p*, d, d* set of Sec. 6)
+ *   proj   device [natoms][cube^3][nproj] double, cube point index (iz*cube + iy)*cube + ix; written by
+ *          sho_usu_build, read by the other two (caller allocates 8 * A * C^3 * nproj bytes)
+ *   psi, coeff as for sho_project / sho_add ([A][nproj][B]), FP64 only.  pos / sigma host arrays.
  */
 #define SHO_USU_MAX_NUMAX 5
 int sho_usu_build(sho_handle* handle, const sho_grid* grid, int natoms, const double* pos, const double* sigma,
-                  int numax, int cube, double* proj, void* stream);
+                  int numax, int nproj, int cube, double* proj, void* stream);
 int sho_usu_project(sho_handle* handle, const sho_grid* grid, const double* psi, int nbands, int natoms,
-                    const double* pos, const double* sigma, int numax, int cube, const double* proj,
+                    const double* pos, const double* sigma, int nproj, int cube, const double* proj,
                     double* coeff, void* stream);
 int sho_usu_add(sho_handle* handle, const sho_grid* grid, const double* coeff, int nbands, int natoms,
-                const double* pos, const double* sigma, int numax, int cube, const double* proj, double* psi,
+                const double* pos, const double* sigma, int nproj, int cube, const double* proj, double* psi,
                 void* stream);
 
 /* ----------------------------------------------------------------------------------------------

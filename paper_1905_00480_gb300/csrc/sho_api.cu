@@ -571,9 +571,10 @@ int sho_apply_nonlocal(sho_handle* h, const sho_grid* grid, const void* psi, sho
 
 // ------------------------------------------------------------------ stored-projector baseline
 int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double* pos, const double* sigma, int numax,
-                  int cube, double* proj, void* stream) {
+                  int nproj, int cube, double* proj, void* stream) {
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, 0, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
+  if (nproj < 1 || nproj > nstates(numax) || !usu_supported_nproj(nproj)) return SHO_ERR_ARG;
   if (natoms == 0) return SHO_OK;
   if (!proj) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
@@ -590,6 +591,7 @@ int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double*
   L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
   L.natoms = natoms;
   L.numax = numax;
+  L.nproj = nproj;
   L.proj = proj;
   L.stream = s;
   if (launch_usu(0, L) != cudaSuccess) return SHO_ERR_CUDA;
@@ -597,10 +599,11 @@ int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double*
 }
 
 int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int nbands, int natoms,
-                    const double* pos, const double* sigma, int numax, int cube, const double* proj, double* coeff,
+                    const double* pos, const double* sigma, int nproj, int cube, const double* proj, double* coeff,
                     void* stream) {
   if (!h) return SHO_ERR_ARG;
-  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, 0, cube, SHO_USU_MAX_NUMAX));
+  if (!usu_supported_nproj(nproj)) return SHO_ERR_ARG;
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!psi || !proj || !coeff) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
@@ -616,7 +619,7 @@ int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int 
   L.g = make_grid(grid, cube, nbands);
   L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
   L.natoms = natoms;
-  L.numax = numax;
+  L.nproj = nproj;
   L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
   L.proj = const_cast<double*>(proj);
   L.psi_in = psi;
@@ -627,9 +630,10 @@ int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int 
 }
 
 int sho_usu_add(sho_handle* h, const sho_grid* grid, const double* coeff, int nbands, int natoms, const double* pos,
-                const double* sigma, int numax, int cube, const double* proj, double* psi, void* stream) {
+                const double* sigma, int nproj, int cube, const double* proj, double* psi, void* stream) {
   if (!h) return SHO_ERR_ARG;
-  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, 0, cube, SHO_USU_MAX_NUMAX));
+  if (!usu_supported_nproj(nproj)) return SHO_ERR_ARG;
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!psi || !proj || !coeff) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
@@ -652,7 +656,7 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const double* coeff, int nb
   L.g = make_grid(grid, cube, nbands);
   L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
   L.natoms = natoms;
-  L.numax = numax;
+  L.nproj = nproj;
   L.proj = const_cast<double*>(proj);
   L.coeff_in = coeff;
   L.psi_out = psi;

@@ -83,9 +83,10 @@ struct UsuLaunch {
   GridDev g;
   const AtomDev* atoms;
   int natoms;
-  int numax;
+  int numax;                // build: basis the stored projectors are taken from
+  int nproj;                // number of stored projectors (the first nproj states of that basis)
   int zsplit;
-  double* proj;             // [A][C^3][N] FP64
+  double* proj;             // [A][C^3][nproj] FP64
   const double* psi_in;     // project: psi
   double* coeff_out;        // project: coefficients
   const double* coeff_in;   // add: coefficients
@@ -97,6 +98,7 @@ struct UsuLaunch {
 
 // Kernel launchers (return a CUDA error code).
 cudaError_t launch_usu(int op, const UsuLaunch& p);
+bool usu_supported_nproj(int n);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
 cudaError_t launch_dmatrix(int natoms, int nstates, int nbands, sho_dtype dt, const void* D, const void* c, void* d,

@@ -14,10 +14,10 @@ namespace sho {
 
 // --------------------------------------------------------------------------------- build
 template <int NU>
-__global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __restrict__ atoms,
+__global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __restrict__ atoms, int nproj,
                                                    double* __restrict__ proj) {
   using BS = Basis<NU>;
-  constexpr int NP = BS::NP, N = BS::N;
+  constexpr int NP = BS::NP;
   const int C = g.cube;
   const long long c3 = (long long)C * C * C;
   const int a = blockIdx.y;
@@ -29,23 +29,25 @@ __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __r
   phi_column(cube_offset(at.o[0], ix, g.h, at.X[0]), at.sigma, NU, fx, 1);
   phi_column(cube_offset(at.o[1], iy, g.h, at.X[1]), at.sigma, NU, fy, 1);
   phi_column(cube_offset(at.o[2], iz, g.h, at.X[2]), at.sigma, NU, fz, 1);
-  double* out = proj + ((long long)a * c3 + i) * N;
+  double* out = proj + ((long long)a * c3 + i) * nproj;
   int k = 0;
 #pragma unroll
   for (int nz = 0; nz < NP; nz++)
 #pragma unroll
     for (int ny = 0; ny + nz <= NU; ny++)
 #pragma unroll
-      for (int nx = 0; nx + ny + nz <= NU; nx++) out[k++] = fx[nx] * fy[ny] * fz[nz];
+      for (int nx = 0; nx + ny + nz <= NU; nx++) {
+        if (k < nproj) out[k] = fx[nx] * fy[ny] * fz[nz];
+        k++;
+      }
 }
 
 // --------------------------------------------------------------------------------- project
-template <int NU>
+template <int N>
 __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* __restrict__ psi,
                                                        const AtomDev* __restrict__ atoms,
                                                        const double* __restrict__ proj, int zsplit,
                                                        double* __restrict__ coeff) {
-  constexpr int N = Basis<NU>::N;
   __shared__ double acc[N * kWarp];
   const int C = g.cube;
   const int lane = threadIdx.x;
@@ -93,13 +95,12 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* 
 }
 
 // --------------------------------------------------------------------------------- add (row gather)
-template <int NU>
+template <int N>
 __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __restrict__ atoms,
                                                    const int* __restrict__ plane_ptr,
                                                    const int* __restrict__ plane_atoms,
                                                    const double* __restrict__ proj,
                                                    const double* __restrict__ coeff, double* __restrict__ psi) {
-  constexpr int N = Basis<NU>::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* acc = reinterpret_cast<double*>(smem_raw);  // [Nx][32]
   const int C = g.cube;
@@ -155,14 +156,16 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
 }
 
 template <int NU>
-static cudaError_t usu_nu(int op, const UsuLaunch& p) {
-  const int C = p.g.cube;
+static cudaError_t usu_build_nu(const UsuLaunch& p) {
+  const long long c3 = (long long)p.g.cube * p.g.cube * p.g.cube;
+  k_usu_build<NU><<<dim3((unsigned)((c3 + 127) / 128), p.natoms), 128, 0, p.stream>>>(p.g, p.atoms, p.nproj,
+                                                                                     p.proj);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  if (op == 0) {
-    const long long c3 = (long long)C * C * C;
-    k_usu_build<NU><<<dim3((unsigned)((c3 + 127) / 128), p.natoms), 128, 0, p.stream>>>(p.g, p.atoms, p.proj);
-    return cudaGetLastError();
-  }
   if (op == 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(p.zsplit, nbt, p.natoms);
@@ -176,10 +179,10 @@ static cudaError_t usu_nu(int op, const UsuLaunch& p) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_usu_project<NU>, p.g, p.psi_in, p.atoms, (const double*)p.proj, p.zsplit,
+    return cudaLaunchKernelEx(&cfg, k_usu_project<N>, p.g, p.psi_in, p.atoms, (const double*)p.proj, p.zsplit,
                               p.coeff_out);
   }
-  auto kern = k_usu_add<NU>;
+  auto kern = k_usu_add<N>;
   const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -188,14 +191,32 @@ static cudaError_t usu_nu(int op, const UsuLaunch& p) {
   return cudaGetLastError();
 }
 
+// Stored-projector counts with compiled kernels: the SHO basis sizes of numax 0..5 and 18 (the
+// s, s*, p, p*, d, d* set of a transition metal, Sec. 6).
+bool usu_supported_nproj(int n) {
+  return n == 1 || n == 4 || n == 10 || n == 18 || n == 20 || n == 35 || n == 56;
+}
+
 cudaError_t launch_usu(int op, const UsuLaunch& p) {
-  switch (p.numax) {
-    case 0: return usu_nu<0>(op, p);
-    case 1: return usu_nu<1>(op, p);
-    case 2: return usu_nu<2>(op, p);
-    case 3: return usu_nu<3>(op, p);
-    case 4: return usu_nu<4>(op, p);
-    case 5: return usu_nu<5>(op, p);
+  if (op == 0) {
+    switch (p.numax) {
+      case 0: return usu_build_nu<0>(p);
+      case 1: return usu_build_nu<1>(p);
+      case 2: return usu_build_nu<2>(p);
+      case 3: return usu_build_nu<3>(p);
+      case 4: return usu_build_nu<4>(p);
+      case 5: return usu_build_nu<5>(p);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (p.nproj) {
+    case 1: return usu_run_n<1>(op, p);
+    case 4: return usu_run_n<4>(op, p);
+    case 10: return usu_run_n<10>(op, p);
+    case 18: return usu_run_n<18>(op, p);
+    case 20: return usu_run_n<20>(op, p);
+    case 35: return usu_run_n<35>(op, p);
+    case 56: return usu_run_n<56>(op, p);
     default: return cudaErrorInvalidValue;
   }
 }

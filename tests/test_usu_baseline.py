@@ -35,3 +35,36 @@ def test_usu_rejects_large_numax():
     from paper_1905_00480_gb300 import api, ShoError
     with pytest.raises(ShoError):
         api.usu_build(np.zeros((1, 3)), [1.0], 6, 16, (16, 16, 16), 0.25, True)
+
+
+def test_usu_truncated_projector_set():
+    """18 stored projectors (the first 18 states of the numax-4 basis, the size of the s, s*, p, p*, d, d*
+    set of Sec. 6): the oracle's numax-4 projection restricted to those states, and its expansion with the
+    remaining coefficients zero."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(201)
+    grid, h, numax, cube, nproj = (40, 36, 34), 0.2, 4, 16, 18
+    pos, sig = workloads.random_atoms(rng, 4, tuple(n * h for n in grid), False, min_sep=1.0)
+    psi = rng.standard_normal((34, 36, 40, 33))
+    c = rng.standard_normal((4, nproj, 33))
+    proj = api.usu_build(pos, sig, numax, cube, grid, h, False, nproj=nproj)
+    assert tuple(proj.shape) == (4, cube ** 3, nproj)
+    psi_d = torch.from_numpy(psi).cuda()
+    got = api.usu_project(psi_d, proj, pos, sig, numax, cube, h, False).cpu().numpy()
+    ref = oracle.project(grid, h, False, psi, pos, sig, numax, cube)[:, :nproj]
+    assert_coeff_close(got, ref, TOL_FP64)
+    cfull = np.zeros((4, oracle.nstates(numax), 33))
+    cfull[:, :nproj] = c
+    api.usu_add(psi_d, torch.from_numpy(c).cuda(), proj, pos, sig, numax, cube, h, False)
+    ref2 = oracle.add(grid, h, False, psi, pos, sig, numax, cube, cfull)
+    assert rel_norm(psi_d.cpu().numpy() - psi, ref2 - psi) <= TOL_FP64
+
+
+def test_usu_rejects_unsupported_nproj():
+    require_gpu()
+    from paper_1905_00480_gb300 import api, ShoError
+    for nproj in (0, 17, 36):
+        with pytest.raises(ShoError):
+            api.usu_build(np.zeros((1, 3)) + 1.0, [1.0], 4, 16, (16, 16, 16), 0.25, True, nproj=nproj)

@@ -132,6 +132,34 @@ def psi_device(w: Workload, torch_dtype=None, device="cuda", nbands: int = None)
 
 
 # ---------------------------------------------------------------------------------------------------
+# the paper's benchmark geometry (Sec. 6)
+
+ANGSTROM = 1.0 / 0.52917721092   # Bohr per Angstrom
+
+
+def fcc_paper_geometry(lattice_A=4.08, box_A=16.0, h_A=0.25, rprj_A=3.55, sigma_bohr=0.59):
+    """The benchmark system of Sec. 6: a cubic domain of 16 A edge sampled at 0.25 A (64^3 points),
+    fcc lattice with a = 4.08 A anchored at the domain corner, and every atom whose projection sphere
+    (3.55 A) overlaps the domain.  Returns (grid, h, positions [A][3], sigma [A]) in Bohr; sigma is the
+    0.59 Bohr the paper selects for Pt (Sec. 4).  Not periodic."""
+    n = int(round(box_A / h_A))
+    a = lattice_A
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    lo, hi = int(np.floor(-rprj_A / a)) - 1, int(np.ceil((box_A + rprj_A) / a)) + 1
+    pts = []
+    for i in range(lo, hi + 1):
+        for j in range(lo, hi + 1):
+            for k in range(lo, hi + 1):
+                for b in basis:
+                    p = (np.array([i, j, k]) + b) * a
+                    d = np.maximum(0.0, np.maximum(-p, p - box_A))
+                    if np.sqrt(np.dot(d, d)) < rprj_A:
+                        pts.append(p)
+    pos = np.array(pts, dtype=np.float64) * ANGSTROM
+    return (n, n, n), h_A * ANGSTROM, pos, np.full(len(pos), sigma_bohr)
+
+
+# ---------------------------------------------------------------------------------------------------
 # serving stream
 
 
