@@ -19,6 +19,7 @@ struct sho_handle {
   size_t coeff_ws_bytes = 0;
   bool has_last = false;
   int device_error = SHO_OK;   // first device-side error since the last sho_sync
+  int* dstatus = nullptr;      // device word set by kernels whose bounded waits expired
 };
 
 namespace sho {
@@ -245,6 +246,50 @@ GridDev make_grid(const sho_grid* grid, int cube, int nbands) {
     if (_st != SHO_OK) return _st; \
   } while (0)
 
+// Plane-sweep projection (FP32 psi, FP32 coefficients): plan the row segments on the host, upload
+// the plan and run tables -> plane sweep -> z-pass (sho_plane.cu).
+int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const float* psi,
+                   int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
+  PlanePlan plan;
+  plan_planes(grid, at, cube, plan);
+  const size_t A = at.size();
+  Carve cv;
+  const size_t o_atoms = cv.take(A * sizeof(AtomDev));
+  const size_t o_items = cv.take(std::max<size_t>(1, plan.items.size()) * sizeof(int4));
+  const size_t o_ptr = cv.take(plan.slot_ptr.size() * sizeof(int));
+  const size_t o_segs = cv.take(std::max<size_t>(1, plan.segs.size()) * sizeof(PlaneSeg));
+  const size_t o_xt = cv.take(A * cube * 8 * sizeof(float));
+  const size_t o_yt = cv.take(A * cube * 8 * sizeof(float));
+  const size_t o_bf = cv.take(A * kPlaneBfragBytesPerAtom);
+  const size_t o_t2 = cv.take(A * cube * (size_t)npairs(numax) * nbands * sizeof(float));
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), A * sizeof(AtomDev), s));
+  SHO_TRY(upload(h, o_items, plan.items.data(), plan.items.size() * sizeof(int4), s));
+  SHO_TRY(upload(h, o_ptr, plan.slot_ptr.data(), plan.slot_ptr.size() * sizeof(int), s));
+  SHO_TRY(upload(h, o_segs, plan.segs.data(), plan.segs.size() * sizeof(PlaneSeg), s));
+  char* ws = static_cast<char*>(h->ws);
+  PlaneLaunch L;
+  L.g = make_grid(grid, cube, nbands);
+  L.psi = psi;
+  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  L.natoms = (int)A;
+  L.numax = numax;
+  L.items = reinterpret_cast<const int4*>(ws + o_items);
+  L.nitems = (int)plan.items.size();
+  L.slot_ptr = reinterpret_cast<const int*>(ws + o_ptr);
+  L.segs = reinterpret_cast<const PlaneSeg*>(ws + o_segs);
+  L.xtab = reinterpret_cast<float*>(ws + o_xt);
+  L.ytab = reinterpret_cast<float*>(ws + o_yt);
+  L.bfrag = reinterpret_cast<uint32_t*>(ws + o_bf);
+  L.t2p = reinterpret_cast<float*>(ws + o_t2);
+  L.coeff = coeff;
+  L.status = h->dstatus;
+  L.stream = s;
+  if (launch_project_plane(L, prec) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
 }  // namespace
 
 // Workspace a call needs (an upper bound: the per-plane lists are counted as natoms * cube entries).
@@ -253,7 +298,19 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
   const size_t tc = compute_size(coeff_dtype);
   Carve cv;
   cv.take((size_t)natoms * sizeof(AtomDev));
-  if (op == SHO_OP_PROJECT) cv.take((size_t)natoms * sizeof(int));
+  if (op == SHO_OP_PROJECT) {
+    cv.take((size_t)natoms * sizeof(int));
+    if (coeff_dtype == SHO_F32 && numax <= kTcMaxNumax) {
+      // plane-sweep path (an upper bound: every (atom, plane) split into two row segments)
+      const size_t segs = 2 * (size_t)natoms * cube + 1;
+      cv.take((segs + grid->n[2]) * sizeof(int4));
+      cv.take(((segs + grid->n[2]) * 36 + 1) * sizeof(int));
+      cv.take(segs * sizeof(PlaneSeg));
+      cv.take(2 * (size_t)natoms * cube * 8 * sizeof(float));
+      cv.take((size_t)natoms * kPlaneBfragBytesPerAtom);
+      cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * sizeof(float));
+    }
+  }
   if (op == SHO_OP_EXPAND) {
     cv.take(((size_t)grid->n[2] + 1) * sizeof(int));
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
@@ -333,6 +390,13 @@ int sho_create(sho_handle** out, int device) {
     delete h;
     return SHO_ERR_CUDA;
   }
+  if (cudaMalloc(&h->dstatus, sizeof(int)) != cudaSuccess || cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->dstatus) cudaFree(h->dstatus);
+    cudaEventDestroy(h->last);
+    delete h;
+    return SHO_ERR_OOM;
+  }
   *out = h;
   return SHO_OK;
 }
@@ -345,6 +409,7 @@ int sho_destroy(sho_handle* h) {
     if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) st = SHO_ERR_CUDA;
     if (h->ws) cudaFree(h->ws);
     if (h->coeff_ws) cudaFree(h->coeff_ws);
+    if (h->dstatus) cudaFree(h->dstatus);
     if (h->last) cudaEventDestroy(h->last);
   }
   delete h;
@@ -361,6 +426,12 @@ int sho_sync(sho_handle* h) {
   if (!h) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
   if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+  int flag = 0;
+  if (cudaMemcpy(&flag, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SHO_ERR_CUDA;
+  if (flag != 0) {
+    if (cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) return SHO_ERR_CUDA;
+    if (h->device_error == SHO_OK) h->device_error = SHO_ERR_TIMEOUT;
+  }
   int e = h->device_error;
   h->device_error = SHO_OK;
   return e;
@@ -380,6 +451,9 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec))
+    return project_planes(h, grid, at, static_cast<const float*>(psi), nbands, numax, cube, prec,
+                          static_cast<float*>(coeff), s);
   std::vector<int> order = spatial_order(grid, at);
   Carve cv;
   const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/sho.h"
@@ -95,6 +97,43 @@ struct UsuLaunch {
   const int* plane_atoms;
   cudaStream_t stream;
 };
+
+// Plane-sweep projection of the FP32-class forms (sho_plane.cu).  A row segment is the run of grid
+// rows [ys, ye) of plane z that atom `atom` covers at cube plane iz, starting at cube row iy0; x0 is
+// the grid x of the atom's first cube point (wrapped when periodic).  flags: 0 whole, 1 tail of a
+// wrapped atom (rows [0, e)), 2 head (rows [s, Ny), continues from the tail's partial sums).
+struct PlaneSeg {
+  int atom, iz, iy0, x0;
+  int ys, ye, flags, t2i;  // t2i = atom * cube + iz: row of the T2 buffer
+};
+struct PlanePlan {
+  std::vector<int4> items;   // per CTA row: (z, ylo, yhi, first slot list)
+  std::vector<int> slot_ptr; // CSR over items x warps x slots -> segs
+  std::vector<PlaneSeg> segs;
+};
+struct PlaneLaunch {
+  GridDev g;
+  const float* psi;          // [Nz][Ny][Nx][B] FP32, 16-byte aligned, B % 4 == 0
+  const AtomDev* atoms;
+  int natoms;
+  int numax;
+  const int4* items;
+  int nitems;
+  const int* slot_ptr;
+  const PlaneSeg* segs;
+  float* xtab;               // [A][C][8]
+  float* ytab;               // [A][C][8]
+  uint32_t* bfrag;           // [A][32][kMaxCube / 8][4]
+  float* t2p;                // [A][C][P][B]
+  float* coeff;              // [A][N][B]
+  int* status;               // device word, bit 0 = a bounded wait expired
+  cudaStream_t stream;
+};
+bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nbands, int numax, int cube,
+              sho_prec prec);
+void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, PlanePlan& plan);
+cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec);
+constexpr size_t kPlaneBfragBytesPerAtom = 32 * (kMaxCube / 8) * 4 * sizeof(uint32_t);
 
 // Kernel launchers (return a CUDA error code).
 cudaError_t launch_usu(int op, const UsuLaunch& p);

@@ -1,0 +1,662 @@
+// sho_plane.cu -- plane-sweep projection of the FP32-class forms (FP32 psi, numax <= 7).
+//
+// The per-atom kernels (sho_fp32.cu) stream every atom's cube on its own, so a psi element that lies in
+// the cubes of k atoms is fetched k times (k ~ 4 in dense systems) and DRAM traffic is a multiple of
+// the data.  Here one CTA owns one grid plane z and one tile of 32 bands and sweeps the plane's rows
+// once: each row (all Nx points x 32 bands) is copied into shared memory by one TMA load and then
+// serves every atom whose cube contains it.  The projection is split where the sweep needs it
+// (eq. TuckerTensor, Sec. 3.4; Sec. 3.2 step 1):
+//
+//   k_plane_tables   per atom: the y table phi_ny(iy) and the x table, the latter also pre-arranged as
+//                    tensor-core B fragments (FP64 recursion of Sec. 3.7, rounded once)
+//   k_project_plane  per (plane z, band tile): x-pass and y-pass of every atom whose cube meets plane
+//                    z, T2[a][iz][(nx,ny)][b] = sum_y phi_ny(y) sum_x phi_nx(x) psi[z][y][x][b]
+//   k_plane_zpass    per (atom, band tile): c[k][b] = h^3 sum_iz phi_nz(iz) T2[a][iz][(nx,ny)][b]
+//
+// Inside k_project_plane, 11 consumer warps each carry 3 register slots of y-pass accumulators; the
+// host assigns every (atom, plane) row segment to a (warp, slot) so that the segments of one slot do
+// not overlap in y (interval colouring, plan_planes), so each row needs no dynamic indexing.  A 12th
+// warp issues the TMA row loads into a ring of `stages` rows guarded by mbarriers (full: TMA bytes
+// landed; empty: all consumer warps done with the row).  Every wait is bounded: after ~2 s the waiting
+// warp records SHO_ERR_TIMEOUT in the status word and leaves its loop; the producer then waits, again
+// bounded, for the copies it issued before it returns.
+//
+// x-pass on the tensor cores: T1[b][n] = sum_x psi[x][b] phi_n(x) is an m16n8 (bands x states) product
+// with K = x.  Row m of the two m-tiles maps to band 4g + 2j (+1 for m = g + 8), and for the TF32
+// forms k maps to x = 8s + 2t (+1 for k = t + 4), so each lane reads its four bands at one x with one
+// 16-byte shared load; with the 128-byte TMA swizzle these loads are free of bank conflicts.  The
+// B fragments (phi) are stored in the same order by k_plane_tables.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sho_tc.cuh"
+
+namespace sho {
+
+constexpr int kPlaneWarps = 11;                        // consumer warps per CTA (+ 1 producer: 384 threads, 168 registers)
+constexpr int kPlaneSlots = 3;                         // y-pass accumulator slots per warp
+constexpr int kPlaneThreads = (kPlaneWarps + 1) * 32;  // + the producer warp
+constexpr int kPlaneMaxStages = 8;
+constexpr int kT1Stride = 36;                          // padded row of the T1 transpose buffer
+constexpr int kPlaneRowBytes = 32 * 4;                 // one x point: 32 FP32 bands (one swizzle row)
+constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at the GB300 SM clock
+constexpr int kSimtMode = -1;
+
+// --------------------------------------------------------------------------------- mbarrier / TMA
+__device__ __forceinline__ uint32_t pl_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Wait for the phase of `parity` to complete; false after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_row(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ float lds32(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(addr));
+  return v;
+}
+
+// Byte offset of bands 4c..4c+3 of x point x in a 128-byte-swizzled row buffer.
+__device__ __forceinline__ uint32_t swz(int x, int c) {
+  return (uint32_t)x * kPlaneRowBytes + ((uint32_t)(c ^ (x & 7)) << 4);
+}
+
+// Grid x of cube point i for an atom whose first x is x0 (periodic: x0 in [0, Nx), one wrap at most;
+// otherwise clamped into the grid -- the tables are zero for points outside it).
+__device__ __forceinline__ int plane_x(int x0, int i, int nx, int periodic) {
+  int x = x0 + i;
+  if (periodic) return x >= nx ? x - nx : x;
+  return x < 0 ? 0 : (x >= nx ? nx - 1 : x);
+}
+
+// --------------------------------------------------------------------------------- tables
+// One warp per atom.  ytab[a][iy][8] and xtab[a][ix][8] (FP32, zero beyond numax and, when not
+// periodic, at cube points outside the grid); bfrag[a][lane][s][4] B fragments of the x table.
+template <int NU, int MODE>
+__global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev* __restrict__ atoms,
+                                                        float* __restrict__ xtab, float* __restrict__ ytab,
+                                                        uint32_t* __restrict__ bfrag) {
+  constexpr int NP = NU + 1;
+  __shared__ float xs[kMaxCube][8];
+  const int a = blockIdx.x, lane = threadIdx.x, C = g.cube;
+  const AtomDev at = atoms[a];
+  for (int i = lane; i < C; i += kWarp) {
+    double col[NP];
+    phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, col, 1);
+    const bool inside = cube_index(at.o[0], i, g.n[0], g.periodic) >= 0;
+#pragma unroll
+    for (int n = 0; n < 8; n++) {
+      const float v = (n < NP && inside) ? (float)col[n] : 0.0f;
+      xs[i][n] = v;
+      xtab[((size_t)a * C + i) * 8 + n] = v;
+    }
+    phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, col, 1);
+#pragma unroll
+    for (int n = 0; n < 8; n++) ytab[((size_t)a * C + i) * 8 + n] = n < NP ? (float)col[n] : 0.0f;
+  }
+  __syncwarp();
+  if constexpr (MODE != kSimtMode) {
+    constexpr TcMode TM = (TcMode)MODE;
+    constexpr int K = TcK<TM>::K;
+    const int gq = lane >> 2, tq = lane & 3;
+    uint32_t* out = bfrag + ((size_t)a * kWarp + lane) * (kMaxCube / 8) * 4;
+    for (int s = 0; s * K < C; s++) {
+      float b[4];
+      if constexpr (K == 8) {
+        b[0] = xs[8 * s + 2 * tq][gq];
+        b[1] = xs[8 * s + 2 * tq + 1][gq];
+        b[2] = b[3] = 0.0f;
+      } else {
+        b[0] = xs[16 * s + 2 * tq][gq];
+        b[1] = xs[16 * s + 2 * tq + 1][gq];
+        b[2] = xs[16 * s + 2 * tq + 8][gq];
+        b[3] = xs[16 * s + 2 * tq + 9][gq];
+      }
+      const BFrag<TM> f = make_bfrag<TM>(b);
+      reinterpret_cast<uint4*>(out)[s] = make_uint4(f.hi[0], f.hi[1], f.lo[0], f.lo[1]);
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------- plane sweep
+template <int NU>
+struct PlaneSmem {
+  static size_t bytes(int nx, int stages) {
+    size_t t = 1024;                                           // alignment slack of the ring
+    t += (size_t)stages * nx * kPlaneRowBytes;                 // row ring (1024-byte aligned)
+    t += 2 * kPlaneMaxStages * sizeof(unsigned long long);     // full / empty barriers
+    t += (size_t)kPlaneWarps * 8 * kT1Stride * sizeof(float);  // T1 transpose buffers
+    return t;
+  }
+};
+
+template <int NU, int MODE>
+__global__ void __launch_bounds__(kPlaneThreads, 1)
+    k_project_plane(const __grid_constant__ CUtensorMap map, GridDev g, const int4* __restrict__ items,
+                    const int* __restrict__ slot_ptr, const PlaneSeg* __restrict__ segs,
+                    const uint32_t* __restrict__ bfrag, const float* __restrict__ xtab,
+                    const float* __restrict__ ytab, int stages, float* t2p, int* status) {
+  using BS = Basis<NU>;
+  constexpr int NP = BS::NP, P = BS::P;
+  constexpr int S = kPlaneSlots;
+  constexpr bool TC = MODE != kSimtMode;
+  constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
+  constexpr int K = TcK<TM>::K;
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t base = (pl_smem(smem_raw) + 1023u) & ~1023u;
+  const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
+  const uint32_t rowbytes = (uint32_t)Nx * kPlaneRowBytes;
+  const uint32_t ring = base;
+  const uint32_t bar_full = ring + (uint32_t)stages * rowbytes;
+  const uint32_t bar_empty = bar_full + kPlaneMaxStages * 8;
+  const uint32_t t1buf = bar_empty + kPlaneMaxStages * 8;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4 item = items[blockIdx.x];  // z, ylo, yhi, first slot-list index of the item
+  const int z = item.x, ylo = item.y, R = item.z - item.y;
+  const int b0 = blockIdx.y * kWarp;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; s++) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, kPlaneWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kPlaneWarps) {
+    // ---------------------------------------------------------------- producer: TMA row loads
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int r = 0; r < R; r++) {
+        const int st = r % stages, k = r / stages;
+        if (!mbar_wait(bar_empty + 8 * st, (uint32_t)((k & 1) ^ 1))) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(bar_full + 8 * st, rowbytes);
+        tma_load_row(ring + (uint32_t)st * rowbytes, &map, b0, (z * Ny + ylo + r) * Nx, bar_full + 8 * st);
+        issued = r + 1;
+      }
+      if (!ok) {
+        atomicOr(status, 1);
+        // let the copies already issued land before the CTA's shared memory is released
+        for (int r = max(0, issued - stages); r < issued; r++)
+          (void)mbar_wait(bar_full + 8 * (r % stages), (uint32_t)((r / stages) & 1));
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  const int gq = lane >> 2, tq = lane & 3;
+  const int b = b0 + lane;
+  const bool bok = b < B;
+  const int list0 = item.w + warp * S;
+  int cur[S], end[S], ys[S], ye[S];
+#pragma unroll
+  for (int s = 0; s < S; s++) {
+    cur[s] = slot_ptr[list0 + s];
+    end[s] = slot_ptr[list0 + s + 1];
+    ys[s] = cur[s] < end[s] ? segs[cur[s]].ys : 0x7fffffff;
+    ye[s] = cur[s] < end[s] ? segs[cur[s]].ye : 0x7fffffff;
+  }
+  float t2[S][P];
+#pragma unroll
+  for (int s = 0; s < S; s++)
+#pragma unroll
+    for (int p = 0; p < P; p++) t2[s][p] = 0.0f;
+  const uint32_t myt1 = t1buf + (uint32_t)warp * 8 * kT1Stride * 4;
+
+  for (int r = 0; r < R; r++) {
+    const int st = r % stages, k = r / stages;
+    const int y = ylo + r;
+    if (!mbar_wait(bar_full + 8 * st, (uint32_t)(k & 1))) {
+      if (lane == 0) atomicOr(status, 1);
+      break;
+    }
+    const uint32_t row = ring + (uint32_t)st * rowbytes;
+#pragma unroll
+    for (int s = 0; s < S; s++) {
+      if (ys[s] <= y) {  // warp-uniform: the slot's current segment covers this row
+        const PlaneSeg sg = segs[cur[s]];
+        const size_t t2off = (size_t)sg.t2i * P * B + b;
+        if (y == ys[s]) {
+#pragma unroll
+          for (int p = 0; p < P; p++) t2[s][p] = (sg.flags == 2 && bok) ? t2p[t2off + (size_t)p * B] : 0.0f;
+        }
+        const int iy = sg.iy0 + (y - ys[s]);
+        // ---- x-pass (a3): t1[n] for this lane's band
+        float t1[NP];
+        if constexpr (!TC) {
+#pragma unroll
+          for (int n = 0; n < NP; n++) t1[n] = 0.0f;
+          const float4* xt = reinterpret_cast<const float4*>(xtab + (size_t)sg.atom * C * 8);
+          for (int i = 0; i < C; i++) {
+            const int x = plane_x(sg.x0, i, Nx, g.periodic);
+            const float v = lds32(row + swz(x, lane >> 2) + (uint32_t)(lane & 3) * 4);
+            const float4 f0 = __ldg(xt + 2 * i), f1 = __ldg(xt + 2 * i + 1);
+            const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+#pragma unroll
+            for (int n = 0; n < NP; n++) t1[n] = fmaf(v, f[n], t1[n]);
+          }
+        } else {
+          float d[2][4], dl[2][4];
+#pragma unroll
+          for (int m = 0; m < 2; m++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) d[m][j] = dl[m][j] = 0.0f;
+          const uint4* bf = reinterpret_cast<const uint4*>(bfrag + ((size_t)sg.atom * kWarp + lane) * (kMaxCube / 8) * 4);
+          for (int ks = 0; ks * K < C; ks++) {
+            const uint4 bw = __ldg(bf + ks);
+            BFrag<TM> bfr;
+            bfr.hi[0] = bw.x;
+            bfr.hi[1] = bw.y;
+            bfr.lo[0] = bw.z;
+            bfr.lo[1] = bw.w;
+            if constexpr (K == 8) {
+              const int xa = plane_x(sg.x0, 8 * ks + 2 * tq, Nx, g.periodic);
+              const int xb = plane_x(sg.x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
+              const float4 va = lds128(row + swz(xa, gq));
+              const float4 vb = lds128(row + swz(xb, gq));
+              const float a0[4] = {va.x, va.y, vb.x, vb.y};
+              const float a1[4] = {va.z, va.w, vb.z, vb.w};
+              tc_product<TM>(d[0], dl[0], a0, bfr);
+              tc_product<TM>(d[1], dl[1], a1, bfr);
+            } else {
+              const int x0 = plane_x(sg.x0, 16 * ks + 2 * tq, Nx, g.periodic);
+              const int x1 = plane_x(sg.x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
+              const int x2 = plane_x(sg.x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
+              const int x3 = plane_x(sg.x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
+              const float4 v0 = lds128(row + swz(x0, gq));
+              const float4 v1 = lds128(row + swz(x1, gq));
+              const float4 v2 = lds128(row + swz(x2, gq));
+              const float4 v3 = lds128(row + swz(x3, gq));
+              const float a0[8] = {v0.x, v1.x, v0.y, v1.y, v2.x, v3.x, v2.y, v3.y};
+              const float a1[8] = {v0.z, v1.z, v0.w, v1.w, v2.z, v3.z, v2.w, v3.w};
+              tc_product<TM>(d[0], dl[0], a0, bfr);
+              tc_product<TM>(d[1], dl[1], a1, bfr);
+            }
+          }
+          // lane (g, t) holds T1 of bands 4g..4g+3 at n = 2t, 2t+1; transpose to one band per lane
+          const float ls = tc_lo_scale<TM>();
+          float* t1w = reinterpret_cast<float*>(smem_raw + (myt1 - pl_smem(smem_raw)));
+          const float4 w0 = make_float4(d[0][0] + ls * dl[0][0], d[0][2] + ls * dl[0][2], d[1][0] + ls * dl[1][0],
+                                        d[1][2] + ls * dl[1][2]);
+          const float4 w1 = make_float4(d[0][1] + ls * dl[0][1], d[0][3] + ls * dl[0][3], d[1][1] + ls * dl[1][1],
+                                        d[1][3] + ls * dl[1][3]);
+          *reinterpret_cast<float4*>(t1w + (2 * tq) * kT1Stride + 4 * gq) = w0;
+          *reinterpret_cast<float4*>(t1w + (2 * tq + 1) * kT1Stride + 4 * gq) = w1;
+          __syncwarp();
+#pragma unroll
+          for (int n = 0; n < NP; n++) t1[n] = t1w[n * kT1Stride + lane];
+          __syncwarp();
+        }
+        // ---- y-pass (a4)
+        const float4* yt = reinterpret_cast<const float4*>(ytab + ((size_t)sg.atom * C + iy) * 8);
+        const float4 y0 = __ldg(yt), y1 = __ldg(yt + 1);
+        const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
+#pragma unroll
+        for (int ny = 0; ny < NP; ny++)
+#pragma unroll
+          for (int nx = 0; nx + ny <= NU; nx++)
+            t2[s][BS::pair(nx, ny)] = fmaf(t1[nx], wy[ny], t2[s][BS::pair(nx, ny)]);
+        if (y == ye[s] - 1) {
+          if (bok) {
+#pragma unroll
+            for (int p = 0; p < P; p++) t2p[t2off + (size_t)p * B] = t2[s][p];
+          }
+          cur[s]++;
+          ys[s] = cur[s] < end[s] ? segs[cur[s]].ys : 0x7fffffff;
+          ye[s] = cur[s] < end[s] ? segs[cur[s]].ye : 0x7fffffff;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar_empty + 8 * st);
+  }
+}
+
+// --------------------------------------------------------------------------------- z-pass
+template <int NU>
+__global__ void __launch_bounds__(kWarp) k_plane_zpass(GridDev g, const AtomDev* __restrict__ atoms,
+                                                       const float* __restrict__ t2p, float* __restrict__ coeff) {
+  using BS = Basis<NU>;
+  constexpr int NP = BS::NP, P = BS::P, N = BS::N;
+  __shared__ float zt[NP][kMaxCube];
+  const int a = blockIdx.x, lane = threadIdx.x, C = g.cube, B = g.nbands;
+  const int b = blockIdx.y * kWarp + lane;
+  const AtomDev at = atoms[a];
+  for (int i = lane; i < C; i += kWarp) phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, &zt[0][i], kMaxCube);
+  __syncwarp();
+  // rows of the cube inside the grid (not periodic); without any, no T2 was written for this atom
+  bool yrows = true;
+  if (!g.periodic) yrows = at.o[1] < g.n[1] && at.o[1] + C > 0;
+  float acc[N];
+#pragma unroll
+  for (int k = 0; k < N; k++) acc[k] = 0.0f;
+  if (yrows && b < B) {
+    for (int iz = 0; iz < C; iz++) {
+      if (cube_index(at.o[2], iz, g.n[2], g.periodic) < 0) continue;
+      const float* src = t2p + ((size_t)a * C + iz) * P * B + b;
+      float t2[P];
+#pragma unroll
+      for (int p = 0; p < P; p++) t2[p] = src[(size_t)p * B];
+      int k = 0;
+#pragma unroll
+      for (int nz = 0; nz < NP; nz++) {
+        const float w = zt[nz][iz];
+#pragma unroll
+        for (int ny = 0; ny + nz <= NU; ny++)
+#pragma unroll
+          for (int nx = 0; nx + ny + nz <= NU; nx++) {
+            acc[k] = fmaf(t2[BS::pair(nx, ny)], w, acc[k]);
+            k++;
+          }
+      }
+    }
+  }
+  if (b < B) {
+    const float h3 = (float)(g.h * g.h * g.h);
+#pragma unroll
+    for (int k = 0; k < N; k++) coeff[((size_t)a * N + k) * B + b] = acc[k] * h3;
+  }
+}
+
+// --------------------------------------------------------------------------------- host side
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+int plane_stages(int nx) {
+  const int budget = 160 * 1024;
+  return std::min(kPlaneMaxStages, std::max(2, budget / (nx * kPlaneRowBytes)));
+}
+
+template <int NU, int MODE>
+cudaError_t plane_run(const PlaneLaunch& p) {
+  const int A = p.natoms, nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, p.bfrag);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)p.g.nbands, (cuuint64_t)p.g.n[0] * p.g.n[1] * p.g.n[2]};
+  const cuuint64_t strides[1] = {(cuuint64_t)p.g.nbands * sizeof(float)};
+  const cuuint32_t box[2] = {32u, (cuuint32_t)p.g.n[0]};
+  const cuuint32_t estr[2] = {1u, 1u};
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.psi), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  if (p.nitems > 0) {
+    const int stages = plane_stages(p.g.n[0]);
+    const size_t smem = PlaneSmem<NU>::bytes(p.g.n[0], stages);
+    auto kern = k_project_plane<NU, MODE>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(p.nitems, nbt), kPlaneThreads, smem, p.stream>>>(map, p.g, p.items, p.slot_ptr, p.segs, p.bfrag,
+                                                                 p.xtab, p.ytab, stages, p.t2p, p.status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_plane_zpass<NU><<<dim3(A, nbt), kWarp, 0, p.stream>>>(p.g, p.atoms, p.t2p, p.coeff);
+  return cudaGetLastError();
+}
+
+template <int NU>
+cudaError_t plane_mode(const PlaneLaunch& p, sho_prec prec) {
+  switch (prec) {
+    case SHO_P_FP32: return plane_run<NU, kSimtMode>(p);
+    case SHO_P_TF32: return plane_run<NU, (int)TcMode::TF32>(p);
+    case SHO_P_3XTF32: return plane_run<NU, (int)TcMode::X3TF32>(p);
+    case SHO_P_BF16: return plane_run<NU, (int)TcMode::BF16>(p);
+    case SHO_P_SPLIT_FP16: return plane_run<NU, (int)TcMode::SPLIT16>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nbands, int numax, int cube,
+              sho_prec prec) {
+  if (psi_dt != SHO_F32 || !fp32_stream_ok(psi, psi_dt, nbands)) return false;
+  if (prec != SHO_P_FP32 && !is_tc(prec)) return false;
+  if (numax > kTcMaxNumax || cube % 16 != 0) return false;
+  if (grid->n[0] > 256 || (long long)grid->n[0] * grid->n[1] * grid->n[2] >= (1ll << 31)) return false;
+  if (grid->periodic && cube > grid->n[0]) return false;
+  return encode_fn() != nullptr;
+}
+
+size_t plane_stage_smem(int nx) { return (size_t)plane_stages(nx) * nx * kPlaneRowBytes; }
+
+// Row segments of every (atom, plane) and their assignment to (warp, slot) registers, per plane and
+// round.  Segments of one slot are disjoint in y; a wrapped atom (periodic) has a tail [0, e) and a
+// head [s, Ny) in the same warp: the tail's partial T2 is written first and the head continues from
+// it, so each T2[a][iz] is written once complete.  Segments that find no free slot go to another
+// round (another CTA sweeping the same plane).
+void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, PlanePlan& plan) {
+  const int nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
+  const bool per = grid->periodic != 0;
+  const int W = kPlaneWarps, S = kPlaneSlots;
+  // A head segment starts ny - cube rows after its tail ended.  With at least kPlaneMaxStages rows in
+  // between, the ring's barriers order the tail's T2 stores before the head's loads (the tail's warp
+  // released the row buffer that the head's row later reused); otherwise both go to one warp, whose
+  // program order suffices.
+  const bool same_warp = ny - cube < kPlaneMaxStages;
+  plan.items.clear();
+  plan.slot_ptr.assign(1, 0);
+  plan.segs.clear();
+  std::vector<std::vector<PlaneSeg>> byz((size_t)nz);
+  for (size_t a = 0; a < at.size(); a++) {
+    const int oy = at[a].o[1], oz = at[a].o[2];
+    int x0 = at[a].o[0];
+    if (per) {
+      x0 %= nx;
+      if (x0 < 0) x0 += nx;
+    }
+    for (int iz = 0; iz < cube; iz++) {
+      int z = oz + iz;
+      if (per) {
+        z %= nz;
+        if (z < 0) z += nz;
+      } else if (z < 0 || z >= nz) {
+        continue;
+      }
+      PlaneSeg sg;
+      sg.atom = (int)a;
+      sg.iz = iz;
+      sg.x0 = x0;
+      sg.t2i = (int)a * cube + iz;
+      if (!per) {
+        const int s0 = std::max(oy, 0), e0 = std::min(oy + cube, ny);
+        if (s0 >= e0) continue;
+        sg.ys = s0;
+        sg.ye = e0;
+        sg.iy0 = s0 - oy;
+        sg.flags = 0;
+        byz[(size_t)z].push_back(sg);
+      } else {
+        int s0 = oy % ny;
+        if (s0 < 0) s0 += ny;
+        if (s0 + cube <= ny) {
+          sg.ys = s0;
+          sg.ye = s0 + cube;
+          sg.iy0 = 0;
+          sg.flags = 0;
+          byz[(size_t)z].push_back(sg);
+        } else {
+          PlaneSeg tail = sg, head = sg;
+          tail.ys = 0;
+          tail.ye = s0 + cube - ny;
+          tail.iy0 = ny - s0;
+          tail.flags = 1;
+          head.ys = s0;
+          head.ye = ny;
+          head.iy0 = 0;
+          head.flags = 2;
+          byz[(size_t)z].push_back(tail);
+          byz[(size_t)z].push_back(head);
+        }
+      }
+    }
+  }
+  std::vector<int> free_at((size_t)W * S);
+  std::vector<std::vector<PlaneSeg>> lists((size_t)W * S);
+  for (int z = 0; z < nz; z++) {
+    std::vector<PlaneSeg> pend = byz[(size_t)z];
+    std::stable_sort(pend.begin(), pend.end(), [](const PlaneSeg& l, const PlaneSeg& r) {
+      return l.ys != r.ys ? l.ys < r.ys : (l.flags != r.flags ? l.flags < r.flags : l.atom < r.atom);
+    });
+    while (!pend.empty()) {
+      std::fill(free_at.begin(), free_at.end(), 0);
+      for (auto& l : lists) l.clear();
+      std::vector<int> tail_slot(at.size(), -1);  // slot of an atom's tail in this round
+      std::vector<char> defer(at.size(), 0);      // atom's wrapped pair moves to the next round
+      std::vector<PlaneSeg> next;
+      for (const PlaneSeg& sg : pend) {
+        if (defer[(size_t)sg.atom]) {
+          next.push_back(sg);
+          continue;
+        }
+        int best = -1, best_load = 1 << 30;
+        for (int w = 0; w < W; w++) {
+          if (same_warp && sg.flags == 2 && tail_slot[(size_t)sg.atom] >= 0 && tail_slot[(size_t)sg.atom] / S != w)
+            continue;
+          int load = 0, freeslot = -1;
+          for (int s = 0; s < S; s++) {
+            if (free_at[(size_t)w * S + s] > sg.ys)
+              load++;
+            else if (freeslot < 0)
+              freeslot = w * S + s;
+          }
+          if (freeslot >= 0 && load < best_load) {
+            best_load = load;
+            best = freeslot;
+          }
+        }
+        if (best < 0) {
+          if (sg.flags == 2 && tail_slot[(size_t)sg.atom] >= 0) {
+            // undo the tail: both halves move on together
+            auto& l = lists[(size_t)tail_slot[(size_t)sg.atom]];
+            for (size_t i = 0; i < l.size(); i++)
+              if (l[i].atom == sg.atom && l[i].flags == 1) {
+                next.push_back(l[i]);
+                l.erase(l.begin() + (long)i);
+                break;
+              }
+          }
+          if (sg.flags == 1) defer[(size_t)sg.atom] = 1;
+          next.push_back(sg);
+          continue;
+        }
+        lists[(size_t)best].push_back(sg);
+        free_at[(size_t)best] = sg.ye;
+        if (sg.flags == 1) tail_slot[(size_t)sg.atom] = best;
+      }
+      bool placed = false;
+      for (const auto& l : lists) placed = placed || !l.empty();
+      if (!placed) {
+        // Every placement of this round was undone (a head found no slot in its tail's warp): sweep
+        // the first pending segment alone, with its other half (if wrapped) in the same warp.
+        std::vector<PlaneSeg> rest;
+        const int a0 = next.front().atom;
+        int s = 0;
+        for (const PlaneSeg& sg : next) {
+          if (sg.atom == a0 && s < S) {
+            lists[(size_t)s++].push_back(sg);
+          } else {
+            rest.push_back(sg);
+          }
+        }
+        next.swap(rest);
+      }
+      int ylo = ny, yhi = 0;
+      for (const auto& l : lists)
+        for (const PlaneSeg& sg : l) {
+          ylo = std::min(ylo, sg.ys);
+          yhi = std::max(yhi, sg.ye);
+        }
+      if (yhi > ylo) {
+        plan.items.push_back(make_int4(z, ylo, yhi, (int)plan.slot_ptr.size() - 1));
+        for (const auto& l : lists) {
+          for (const PlaneSeg& sg : l) plan.segs.push_back(sg);
+          plan.slot_ptr.push_back((int)plan.segs.size());
+        }
+      }
+      std::stable_sort(next.begin(), next.end(), [](const PlaneSeg& l, const PlaneSeg& r) {
+        return l.ys != r.ys ? l.ys < r.ys : (l.flags != r.flags ? l.flags < r.flags : l.atom < r.atom);
+      });
+      pend.swap(next);
+    }
+  }
+}
+
+cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec) {
+  switch (p.numax) {
+    case 0: return plane_mode<0>(p, prec);
+    case 1: return plane_mode<1>(p, prec);
+    case 2: return plane_mode<2>(p, prec);
+    case 3: return plane_mode<3>(p, prec);
+    case 4: return plane_mode<4>(p, prec);
+    case 5: return plane_mode<5>(p, prec);
+    case 6: return plane_mode<6>(p, prec);
+    case 7: return plane_mode<7>(p, prec);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sho

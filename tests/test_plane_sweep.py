@@ -1,0 +1,136 @@
+"""Plane-sweep projection of the FP32-class forms (FP32 psi, numax <= 7) against the FP64 oracle (GPU).
+
+The plane sweep assigns every (atom, plane) row segment to a register slot on the host; these cases
+drive its corners: more overlapping atoms per row than slots (several sweeps of one plane), wrapped
+cubes on grids barely larger than the cube (both halves of a wrapped atom in one warp), atoms far
+outside a non-periodic box, every numax, and the fallback to the per-atom kernels when a row does not
+fit one TMA box."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import TOL_FP32, assert_coeff_close, rel_norm, require_gpu
+from test_parity_tc import TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def _kernels_run(fn):
+    """Names of the CUDA kernels launched by fn()."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    return {e.name for e in prof.events()}
+
+
+def _project(grid, h, periodic, pos, sig, numax, cube, nbands, prec, seed):
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands)).astype(np.float32)
+    psi_d = torch.from_numpy(psi).cuda()
+    got = api.project(psi_d, pos, sig, numax, cube, h, periodic, prec=prec).double().cpu().numpy()
+    ref = oracle.project(grid, h, periodic, psi.astype(np.float64), pos, sig, numax, cube)
+    return got, ref
+
+
+def _tol(prec):
+    return TOL_FP32 if prec == "fp32" else TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
+def test_dense_atoms_need_several_sweeps(prec):
+    """120 atoms in a periodic 48^3 box with cube 32: about 53 cubes meet each grid row, more than the
+    33 register slots of one sweep, so planes are swept more than once."""
+    require_gpu()
+    rng = np.random.default_rng(601)
+    grid, h, numax, cube = (48, 48, 48), 0.2, 3, 32
+    pos, sig = workloads.random_atoms(rng, 120, tuple(n * h for n in grid), True, min_sep=0.6)
+    got, ref = _project(grid, h, True, pos, sig, numax, cube, 8, prec, 602)
+    assert_coeff_close(got, ref, _tol(prec))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_wrapped_cubes_on_small_grid(prec):
+    """Periodic grid only 2-4 points longer than the cube in y: most cubes wrap, and the two halves of a
+    wrapped atom are summed in one warp."""
+    require_gpu()
+    rng = np.random.default_rng(603)
+    grid, h, numax, cube = (36, 34, 40), 0.2, 5, 32
+    pos, sig = workloads.random_atoms(rng, 7, tuple(n * h for n in grid), True, min_sep=1.0)
+    got, ref = _project(grid, h, True, pos, sig, numax, cube, 36, prec, 604)
+    assert_coeff_close(got, ref, _tol(prec))
+
+
+def test_atoms_outside_open_box():
+    """Not periodic: cubes clipped on every side, and one atom whose cube misses the grid in y entirely
+    (its coefficients are exactly zero)."""
+    require_gpu()
+    grid, h, numax, cube = (40, 40, 40), 0.25, 4, 32
+    L = 40 * h
+    pos = np.array([[-2.0, 3.0, 5.0], [L + 1.5, L - 0.3, 0.2], [5.0, -9.0, 5.0], [4.9, 5.1, L + 2.0],
+                    [0.1, 0.2, 0.3]])
+    sig = np.array([0.8, 0.9, 0.7, 1.0, 0.6])
+    got, ref = _project(grid, h, False, pos, sig, numax, cube, 16, "tf32", 605)
+    assert np.all(got[2] == 0.0)
+    keep = [0, 1, 3, 4]
+    assert_coeff_close(got[keep], ref[keep], TOL["tf32"])
+
+
+@pytest.mark.parametrize("numax", list(range(8)))
+def test_every_numax(numax):
+    require_gpu()
+    rng = np.random.default_rng(606 + numax)
+    grid, h, cube = (40, 36, 32), 0.2, 16
+    pos, sig = workloads.random_atoms(rng, 6, tuple(n * h for n in grid), True, min_sep=1.0)
+    for prec in ("fp32", "tf32"):
+        got, ref = _project(grid, h, True, pos, sig, numax, cube, 12, prec, 620 + numax)
+        assert_coeff_close(got, ref, _tol(prec))
+
+
+def test_plane_kernels_are_the_ones_run():
+    """Eligible calls run the plane sweep; a row longer than one TMA box (Nx > 256) and BF16 storage
+    take the per-atom kernels; all give the oracle's result."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(630)
+    grid, h, numax, cube = (40, 40, 40), 0.2, 3, 16
+    pos, sig = workloads.random_atoms(rng, 4, tuple(n * h for n in grid), True, min_sep=1.0)
+    psi = torch.from_numpy(rng.standard_normal((40, 40, 40, 8)).astype(np.float32)).cuda()
+    names = _kernels_run(lambda: api.project(psi, pos, sig, numax, cube, h, True, prec="tf32"))
+    assert any("k_project_plane" in n for n in names), names
+    assert any("k_plane_zpass" in n for n in names), names
+    names = _kernels_run(lambda: api.project(psi.to(torch.bfloat16), pos, sig, numax, cube, h, True, prec="tf32"))
+    assert not any("k_project_plane" in n for n in names), names
+
+    wide = (264, 16, 16)
+    pos2, sig2 = workloads.random_atoms(rng, 3, tuple(n * h for n in wide), True, min_sep=1.0)
+    psi2 = rng.standard_normal((16, 16, 264, 4)).astype(np.float32)
+    psi2_d = torch.from_numpy(psi2).cuda()
+    names = _kernels_run(lambda: api.project(psi2_d, pos2, sig2, numax, cube, h, True, prec="fp32"))
+    assert not any("k_project_plane" in n for n in names), names
+    got = api.project(psi2_d, pos2, sig2, numax, cube, h, True, prec="fp32").double().cpu().numpy()
+    ref = oracle.project(wide, h, True, psi2.astype(np.float64), pos2, sig2, numax, cube)
+    assert_coeff_close(got, ref, TOL_FP32)
+
+
+def test_plane_sweep_repeatable_and_status_clear():
+    """Two calls give bit-identical coefficients (fixed plan, no atomics) and no bounded wait expired."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(640)
+    grid, h, numax, cube = (64, 64, 64), 0.2, 7, 32
+    pos, sig = workloads.random_atoms(rng, 40, tuple(n * h for n in grid), True, min_sep=1.5)
+    psi = torch.from_numpy(rng.standard_normal((64, 64, 64, 64)).astype(np.float32)).cuda()
+    hd = api.Handle(0)
+    c1 = api.project(psi, pos, sig, numax, cube, h, True, prec="tf32", handle=hd)
+    c2 = api.project(psi, pos, sig, numax, cube, h, True, prec="tf32", handle=hd)
+    hd.sync()
+    assert torch.equal(c1, c2)
+    ref = oracle.project(grid, h, True, psi.double().cpu().numpy(), pos[:3], sig[:3], numax, cube)
+    assert rel_norm(c1[:3].double().cpu().numpy(), ref) <= TOL["tf32"]
