@@ -155,11 +155,17 @@ __global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev
 }
 
 // --------------------------------------------------------------------------------- plane sweep
+// Bytes of one ring stage: a row of nx x points, rounded up to 1024 so that every stage starts on a
+// 1024-byte boundary, which the 128-byte swizzle pattern of the TMA (and swz) is anchored to.
+__host__ __device__ __forceinline__ uint32_t plane_stage_bytes(int nx) {
+  return ((uint32_t)nx * kPlaneRowBytes + 1023u) & ~1023u;
+}
+
 template <int NU>
 struct PlaneSmem {
   static size_t bytes(int nx, int stages) {
     size_t t = 1024;                                           // alignment slack of the ring
-    t += (size_t)stages * nx * kPlaneRowBytes;                 // row ring (1024-byte aligned)
+    t += (size_t)stages * plane_stage_bytes(nx);               // row ring (1024-byte aligned stages)
     t += 2 * kPlaneMaxStages * sizeof(unsigned long long);     // full / empty barriers
     t += (size_t)kPlaneWarps * 8 * kT1Stride * sizeof(float);  // T1 transpose buffers
     return t;
@@ -181,9 +187,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   const uint32_t base = (pl_smem(smem_raw) + 1023u) & ~1023u;
   const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
-  const uint32_t rowbytes = (uint32_t)Nx * kPlaneRowBytes;
+  const uint32_t rowbytes = (uint32_t)Nx * kPlaneRowBytes;  // bytes one TMA row load delivers
+  const uint32_t stagebytes = plane_stage_bytes(Nx);
   const uint32_t ring = base;
-  const uint32_t bar_full = ring + (uint32_t)stages * rowbytes;
+  const uint32_t bar_full = ring + (uint32_t)stages * stagebytes;
   const uint32_t bar_empty = bar_full + kPlaneMaxStages * 8;
   const uint32_t t1buf = bar_empty + kPlaneMaxStages * 8;
 
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           break;
         }
         mbar_expect_tx(bar_full + 8 * st, rowbytes);
-        tma_load_row(ring + (uint32_t)st * rowbytes, &map, b0, (z * Ny + ylo + r) * Nx, bar_full + 8 * st);
+        tma_load_row(ring + (uint32_t)st * stagebytes, &map, b0, (z * Ny + ylo + r) * Nx, bar_full + 8 * st);
         issued = r + 1;
       }
       if (!ok) {
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
       if (lane == 0) atomicOr(status, 1);
       break;
     }
-    const uint32_t row = ring + (uint32_t)st * rowbytes;
+    const uint32_t row = ring + (uint32_t)st * stagebytes;
 #pragma unroll
     for (int s = 0; s < S; s++) {
       if (ys[s] <= y) {  // warp-uniform: the slot's current segment covers this row
@@ -422,7 +429,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int plane_stages(int nx) {
   const int budget = 160 * 1024;
-  return std::min(kPlaneMaxStages, std::max(2, budget / (nx * kPlaneRowBytes)));
+  return std::min(kPlaneMaxStages, std::max(2, budget / (int)plane_stage_bytes(nx)));
 }
 
 template <int NU, int MODE>
@@ -480,8 +487,6 @@ bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nband
   if (grid->periodic && cube > grid->n[0]) return false;
   return encode_fn() != nullptr;
 }
-
-size_t plane_stage_smem(int nx) { return (size_t)plane_stages(nx) * nx * kPlaneRowBytes; }
 
 // Row segments of every (atom, plane) and their assignment to (warp, slot) registers, per plane and
 // round.  Segments of one slot are disjoint in y; a wrapped atom (periodic) has a tail [0, e) and a
