@@ -111,7 +111,8 @@ int sho_destroy(sho_handle* handle);
 int sho_set_strict(sho_handle* handle, int strict);
 
 /* Block until the handle's enqueued work is complete; return the first device-side error since the
- * previous sho_sync (SHO_ERR_DEVICE) or a CUDA error, else SHO_OK. */
+ * previous sho_sync (SHO_ERR_DEVICE; SHO_ERR_TIMEOUT when a kernel's bounded wait on its own data
+ * pipeline expired -- its results are then incomplete) or a CUDA error, else SHO_OK. */
 int sho_sync(sho_handle* handle);
 
 /*
@@ -129,6 +130,17 @@ int sho_sync(sho_handle* handle);
 int sho_project(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                 int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                 void* coeff, sho_dtype coeff_dtype, void* stream);
+
+/* Kernel family sho_project runs for these arguments (a host-side query; no GPU work):
+ *   SHO_PATH_PLANE  plane sweep: one CTA per (grid plane, 32 bands) streams the plane's rows once
+ *                   through shared memory (TMA) for all atoms whose cubes meet it, then a z-pass per
+ *                   atom; taken for psi F32 (16-byte aligned, nbands % 4 == 0), coeff F32, a FP32-class
+ *                   form, numax <= 7, cube % 16 == 0, n[0] <= 256 (and cube <= n[0] when periodic)
+ *   SHO_PATH_ATOM   per-atom kernels: each (atom, 32 bands, z-slab) streams its own cube
+ * Returns SHO_ERR_ARG for a NULL grid. */
+typedef enum { SHO_PATH_ATOM = 1, SHO_PATH_PLANE = 2 } sho_path;
+int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int numax, int cube,
+                     sho_prec prec, sho_dtype coeff_dtype);
 
 /*
  * Expansion -- step (3) of the non-local action (Sec. 3.2), the adjoint of the projection:

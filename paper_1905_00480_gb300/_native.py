@@ -56,6 +56,7 @@ SIGNATURES = {
     "sho_destroy": (_I, [_VP]),
     "sho_set_strict": (_I, [_VP, _I]),
     "sho_sync": (_I, [_VP]),
+    "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),
     "sho_project": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
     "sho_add": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
     "sho_forces": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),

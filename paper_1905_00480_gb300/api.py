@@ -131,6 +131,18 @@ def project(psi: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, peri
     return out
 
 
+def project_path(psi: torch.Tensor, numax: int, cube: int, h: float, periodic: bool = True, prec: str = "fp64") -> str:
+    """sho_project_path: "plane" (plane sweep) or "atom" (per-atom kernels) for a projection of psi."""
+    _check_psi(psi)
+    g = _grid(psi, h, periodic)
+    cdt = _coeff_dtype(prec)
+    r = N.lib().sho_project_path(ctypes.byref(g), ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
+                                 psi.shape[3], int(numax), int(cube), N.PRECS[prec], N.DTYPES[_TORCH_DT[cdt]])
+    if r < 0:
+        N.check(r, "sho_project_path")
+    return {1: "atom", 2: "plane"}[r]
+
+
 def add(psi: torch.Tensor, coeff: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, periodic: bool = True,
         prec: str = "fp64", handle: Handle = None, stream=None) -> torch.Tensor:
     """sho_add (in place): psi[j][b] += sum_a sum_k c[a][k][b] Psi_k(u).  Returns psi."""

@@ -437,6 +437,13 @@ int sho_sync(sho_handle* h) {
   return e;
 }
 
+int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int numax, int cube,
+                     sho_prec prec, sho_dtype coeff_dtype) {
+  if (!grid) return SHO_ERR_ARG;
+  return (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec)) ? SHO_PATH_PLANE
+                                                                                              : SHO_PATH_ATOM;
+}
+
 int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
                 const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* coeff,
                 sho_dtype coeff_dtype, void* stream) {

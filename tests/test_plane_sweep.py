@@ -16,16 +16,6 @@ from test_parity_tc import TOL
 pytestmark = pytest.mark.gpu
 
 
-def _kernels_run(fn):
-    """Names of the CUDA kernels launched by fn()."""
-    import torch
-    from torch.profiler import ProfilerActivity, profile
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        fn()
-        torch.cuda.synchronize()
-    return {e.name for e in prof.events()}
-
-
 def _project(grid, h, periodic, pos, sig, numax, cube, nbands, prec, seed):
     import torch
     from paper_1905_00480_gb300 import api
@@ -91,28 +81,26 @@ def test_every_numax(numax):
         assert_coeff_close(got, ref, _tol(prec))
 
 
-def test_plane_kernels_are_the_ones_run():
-    """Eligible calls run the plane sweep; a row longer than one TMA box (Nx > 256) and BF16 storage
-    take the per-atom kernels; all give the oracle's result."""
+def test_plane_path_selection():
+    """Eligible calls take the plane sweep; a row longer than one TMA box (Nx > 256), BF16 storage,
+    unaligned band counts and numax 8 take the per-atom kernels; all give the oracle's result."""
     require_gpu()
     import torch
     from paper_1905_00480_gb300 import api
     rng = np.random.default_rng(630)
-    grid, h, numax, cube = (40, 40, 40), 0.2, 3, 16
-    pos, sig = workloads.random_atoms(rng, 4, tuple(n * h for n in grid), True, min_sep=1.0)
-    psi = torch.from_numpy(rng.standard_normal((40, 40, 40, 8)).astype(np.float32)).cuda()
-    names = _kernels_run(lambda: api.project(psi, pos, sig, numax, cube, h, True, prec="tf32"))
-    assert any("k_project_plane" in n for n in names), names
-    assert any("k_plane_zpass" in n for n in names), names
-    names = _kernels_run(lambda: api.project(psi.to(torch.bfloat16), pos, sig, numax, cube, h, True, prec="tf32"))
-    assert not any("k_project_plane" in n for n in names), names
-
+    h, numax, cube = 0.2, 3, 16
+    psi = torch.zeros((40, 40, 40, 8), dtype=torch.float32, device="cuda")
+    assert api.project_path(psi, numax, cube, h, True, "tf32") == "plane"
+    assert api.project_path(psi, numax, cube, h, True, "fp32") == "plane"
+    assert api.project_path(psi, 8, cube, h, True, "fp32") == "atom"
+    assert api.project_path(psi.to(torch.bfloat16), numax, cube, h, True, "tf32") == "atom"
+    assert api.project_path(torch.zeros((40, 40, 40, 6), device="cuda"), numax, cube, h, True, "tf32") == "atom"
+    assert api.project_path(psi.double(), numax, cube, h, True, "ff64") == "atom"
     wide = (264, 16, 16)
-    pos2, sig2 = workloads.random_atoms(rng, 3, tuple(n * h for n in wide), True, min_sep=1.0)
     psi2 = rng.standard_normal((16, 16, 264, 4)).astype(np.float32)
     psi2_d = torch.from_numpy(psi2).cuda()
-    names = _kernels_run(lambda: api.project(psi2_d, pos2, sig2, numax, cube, h, True, prec="fp32"))
-    assert not any("k_project_plane" in n for n in names), names
+    assert api.project_path(psi2_d, numax, cube, h, True, "fp32") == "atom"
+    pos2, sig2 = workloads.random_atoms(rng, 3, tuple(n * h for n in wide), True, min_sep=1.0)
     got = api.project(psi2_d, pos2, sig2, numax, cube, h, True, prec="fp32").double().cpu().numpy()
     ref = oracle.project(wide, h, True, psi2.astype(np.float64), pos2, sig2, numax, cube)
     assert_coeff_close(got, ref, TOL_FP32)
