@@ -161,15 +161,24 @@ __host__ __device__ __forceinline__ uint32_t plane_stage_bytes(int nx) {
   return ((uint32_t)nx * kPlaneRowBytes + 1023u) & ~1023u;
 }
 
-template <int NU>
+// Per (warp, slot) shared area, filled when a segment starts: the atom's B fragments (tensor forms:
+// [k-step][lane][4 words], up to 4 k-steps for a 32-point cube) or its x table (CUDA-core form,
+// [C][8]), and its y table [C][8].  The per-row work then reads shared memory only.
+constexpr int kSlotFragBytes = 4 * 32 * 16;
+constexpr int kSlotYBytes = 32 * 8 * 4;
+constexpr int kSlotBytes = kSlotFragBytes + kSlotYBytes;
+constexpr int kPlaneMaxCube = 32;
+constexpr int kPlaneSmemBudget = 227 * 1024;
+
 struct PlaneSmem {
-  static size_t bytes(int nx, int stages) {
-    size_t t = 1024;                                           // alignment slack of the ring
-    t += (size_t)stages * plane_stage_bytes(nx);               // row ring (1024-byte aligned stages)
-    t += 2 * kPlaneMaxStages * sizeof(unsigned long long);     // full / empty barriers
-    t += (size_t)kPlaneWarps * 8 * kT1Stride * sizeof(float);  // T1 transpose buffers
-    return t;
+  // everything but the ring, including the alignment slack of the ring
+  static constexpr size_t fixed() {
+    return 1024 + 2 * kPlaneMaxStages * sizeof(unsigned long long)   // full / empty barriers
+           + (size_t)kPlaneWarps * 8 * kT1Stride * sizeof(float)      // T1 transpose buffers
+           + (size_t)kPlaneWarps * kPlaneSlots * kSlotBytes           // slot tables
+           + (size_t)kPlaneWarps * kPlaneSlots * 16;                  // slot records
   }
+  static size_t bytes(int nx, int stages) { return fixed() + (size_t)stages * plane_stage_bytes(nx); }
 };
 
 template <int NU, int MODE>
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
     k_project_plane(const __grid_constant__ CUtensorMap map, GridDev g, const int4* __restrict__ items,
                     const int* __restrict__ slot_ptr, const PlaneSeg* __restrict__ segs,
                     const uint32_t* __restrict__ bfrag, const float* __restrict__ xtab,
-                    const float* __restrict__ ytab, int stages, float* t2p, int* status) {
+                    const float* __restrict__ ytab, int stages, int nbt, float* t2p, int* status) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P;
   constexpr int S = kPlaneSlots;
@@ -185,7 +194,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int K = TcK<TM>::K;
   extern __shared__ unsigned char smem_raw[];
-  const uint32_t base = (pl_smem(smem_raw) + 1023u) & ~1023u;
+  const uint32_t raw = pl_smem(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
   const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
   const uint32_t rowbytes = (uint32_t)Nx * kPlaneRowBytes;  // bytes one TMA row load delivers
   const uint32_t stagebytes = plane_stage_bytes(Nx);
@@ -193,11 +203,15 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   const uint32_t bar_full = ring + (uint32_t)stages * stagebytes;
   const uint32_t bar_empty = bar_full + kPlaneMaxStages * 8;
   const uint32_t t1buf = bar_empty + kPlaneMaxStages * 8;
+  const uint32_t slots = t1buf + kPlaneWarps * 8 * kT1Stride * 4;
+  const uint32_t recs = slots + kPlaneWarps * S * kSlotBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int4 item = items[blockIdx.x];  // z, ylo, yhi, first slot-list index of the item
+  // band tiles of one plane run next to each other: they share DRAM pages and the plan entries
+  const int item_id = (int)blockIdx.x / nbt, bt = (int)blockIdx.x - item_id * nbt;
+  const int4 item = items[item_id];  // z, ylo, yhi, first slot-list index of the item
   const int z = item.x, ylo = item.y, R = item.z - item.y;
-  const int b0 = blockIdx.y * kWarp;
+  const int b0 = bt * kWarp;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; s++) {
@@ -252,6 +266,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
 #pragma unroll
     for (int p = 0; p < P; p++) t2[s][p] = 0.0f;
   const uint32_t myt1 = t1buf + (uint32_t)warp * 8 * kT1Stride * 4;
+  float* t1w = reinterpret_cast<float*>(smem_raw + (myt1 - raw));
 
   for (int r = 0; r < R; r++) {
     const int st = r % stages, k = r / stages;
@@ -264,23 +279,50 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
 #pragma unroll
     for (int s = 0; s < S; s++) {
       if (ys[s] <= y) {  // warp-uniform: the slot's current segment covers this row
-        const PlaneSeg sg = segs[cur[s]];
-        const size_t t2off = (size_t)sg.t2i * P * B + b;
+        const uint32_t sa = slots + (uint32_t)(warp * S + s) * kSlotBytes;  // tables of this slot
+        const uint32_t ra = recs + (uint32_t)(warp * S + s) * 16;           // x0, iy - y, t2i, flags
         if (y == ys[s]) {
+          // segment start: stage the atom's tables, record its offsets, load or clear the sums
+          const PlaneSeg sg = segs[cur[s]];
+          if constexpr (TC) {
+            const uint4* src = reinterpret_cast<const uint4*>(bfrag + ((size_t)sg.atom * kWarp + lane) * (kMaxCube / 8) * 4);
+            for (int ks = 0; ks * K < C; ks++) {
+              const uint4 w = __ldg(src + ks);
+              asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};\n" ::"r"(sa + (uint32_t)(ks * 32 + lane) * 16),
+                           "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w));
+            }
+          } else if (lane < C) {
+            const float4* src = reinterpret_cast<const float4*>(xtab + ((size_t)sg.atom * C + lane) * 8);
+            const float4 f0 = __ldg(src), f1 = __ldg(src + 1);
+            float4* dst = reinterpret_cast<float4*>(smem_raw + (sa - raw) + lane * 32);
+            dst[0] = f0;
+            dst[1] = f1;
+          }
+          if (lane < C) {
+            const float4* src = reinterpret_cast<const float4*>(ytab + ((size_t)sg.atom * C + lane) * 8);
+            const float4 f0 = __ldg(src), f1 = __ldg(src + 1);
+            float4* dst = reinterpret_cast<float4*>(smem_raw + (sa - raw) + kSlotFragBytes + lane * 32);
+            dst[0] = f0;
+            dst[1] = f1;
+          }
+          if (lane == 0)
+            *reinterpret_cast<int4*>(smem_raw + (ra - raw)) = make_int4(sg.x0, sg.iy0 - sg.ys, sg.t2i, sg.flags);
+          const size_t t2off = (size_t)sg.t2i * P * B + b;
 #pragma unroll
           for (int p = 0; p < P; p++) t2[s][p] = (sg.flags == 2 && bok) ? t2p[t2off + (size_t)p * B] : 0.0f;
+          __syncwarp();
         }
-        const int iy = sg.iy0 + (y - ys[s]);
+        const int4 rc = *reinterpret_cast<const int4*>(smem_raw + (ra - raw));
+        const int x0 = rc.x, iy = y + rc.y;
         // ---- x-pass (a3): t1[n] for this lane's band
         float t1[NP];
         if constexpr (!TC) {
 #pragma unroll
           for (int n = 0; n < NP; n++) t1[n] = 0.0f;
-          const float4* xt = reinterpret_cast<const float4*>(xtab + (size_t)sg.atom * C * 8);
           for (int i = 0; i < C; i++) {
-            const int x = plane_x(sg.x0, i, Nx, g.periodic);
+            const int x = plane_x(x0, i, Nx, g.periodic);
             const float v = lds32(row + swz(x, lane >> 2) + (uint32_t)(lane & 3) * 4);
-            const float4 f0 = __ldg(xt + 2 * i), f1 = __ldg(xt + 2 * i + 1);
+            const float4 f0 = lds128(sa + (uint32_t)i * 32), f1 = lds128(sa + (uint32_t)i * 32 + 16);
             const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
 #pragma unroll
             for (int n = 0; n < NP; n++) t1[n] = fmaf(v, f[n], t1[n]);
@@ -291,41 +333,45 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           for (int m = 0; m < 2; m++)
 #pragma unroll
             for (int j = 0; j < 4; j++) d[m][j] = dl[m][j] = 0.0f;
-          const uint4* bf = reinterpret_cast<const uint4*>(bfrag + ((size_t)sg.atom * kWarp + lane) * (kMaxCube / 8) * 4);
-          for (int ks = 0; ks * K < C; ks++) {
-            const uint4 bw = __ldg(bf + ks);
-            BFrag<TM> bfr;
-            bfr.hi[0] = bw.x;
-            bfr.hi[1] = bw.y;
-            bfr.lo[0] = bw.z;
-            bfr.lo[1] = bw.w;
-            if constexpr (K == 8) {
-              const int xa = plane_x(sg.x0, 8 * ks + 2 * tq, Nx, g.periodic);
-              const int xb = plane_x(sg.x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
-              const float4 va = lds128(row + swz(xa, gq));
-              const float4 vb = lds128(row + swz(xb, gq));
-              const float a0[4] = {va.x, va.y, vb.x, vb.y};
-              const float a1[4] = {va.z, va.w, vb.z, vb.w};
-              tc_product<TM>(d[0], dl[0], a0, bfr);
-              tc_product<TM>(d[1], dl[1], a1, bfr);
-            } else {
-              const int x0 = plane_x(sg.x0, 16 * ks + 2 * tq, Nx, g.periodic);
-              const int x1 = plane_x(sg.x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
-              const int x2 = plane_x(sg.x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
-              const int x3 = plane_x(sg.x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
-              const float4 v0 = lds128(row + swz(x0, gq));
-              const float4 v1 = lds128(row + swz(x1, gq));
-              const float4 v2 = lds128(row + swz(x2, gq));
-              const float4 v3 = lds128(row + swz(x3, gq));
-              const float a0[8] = {v0.x, v1.x, v0.y, v1.y, v2.x, v3.x, v2.y, v3.y};
-              const float a1[8] = {v0.z, v1.z, v0.w, v1.w, v2.z, v3.z, v2.w, v3.w};
-              tc_product<TM>(d[0], dl[0], a0, bfr);
-              tc_product<TM>(d[1], dl[1], a1, bfr);
+#pragma unroll
+          for (int ks = 0; ks < kPlaneMaxCube / K; ks++) {
+            if (ks * K < C) {
+              uint4 bw;
+              asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\n"
+                           : "=r"(bw.x), "=r"(bw.y), "=r"(bw.z), "=r"(bw.w)
+                           : "r"(sa + (uint32_t)(ks * 32 + lane) * 16));
+              BFrag<TM> bfr;
+              bfr.hi[0] = bw.x;
+              bfr.hi[1] = bw.y;
+              bfr.lo[0] = bw.z;
+              bfr.lo[1] = bw.w;
+              if constexpr (K == 8) {
+                const int xa = plane_x(x0, 8 * ks + 2 * tq, Nx, g.periodic);
+                const int xb = plane_x(x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
+                const float4 va = lds128(row + swz(xa, gq));
+                const float4 vb = lds128(row + swz(xb, gq));
+                const float a0[4] = {va.x, va.y, vb.x, vb.y};
+                const float a1[4] = {va.z, va.w, vb.z, vb.w};
+                tc_product<TM>(d[0], dl[0], a0, bfr);
+                tc_product<TM>(d[1], dl[1], a1, bfr);
+              } else {
+                const int xq0 = plane_x(x0, 16 * ks + 2 * tq, Nx, g.periodic);
+                const int xq1 = plane_x(x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
+                const int xq2 = plane_x(x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
+                const int xq3 = plane_x(x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
+                const float4 v0 = lds128(row + swz(xq0, gq));
+                const float4 v1 = lds128(row + swz(xq1, gq));
+                const float4 v2 = lds128(row + swz(xq2, gq));
+                const float4 v3 = lds128(row + swz(xq3, gq));
+                const float a0[8] = {v0.x, v1.x, v0.y, v1.y, v2.x, v3.x, v2.y, v3.y};
+                const float a1[8] = {v0.z, v1.z, v0.w, v1.w, v2.z, v3.z, v2.w, v3.w};
+                tc_product<TM>(d[0], dl[0], a0, bfr);
+                tc_product<TM>(d[1], dl[1], a1, bfr);
+              }
             }
           }
           // lane (g, t) holds T1 of bands 4g..4g+3 at n = 2t, 2t+1; transpose to one band per lane
           const float ls = tc_lo_scale<TM>();
-          float* t1w = reinterpret_cast<float*>(smem_raw + (myt1 - pl_smem(smem_raw)));
           const float4 w0 = make_float4(d[0][0] + ls * dl[0][0], d[0][2] + ls * dl[0][2], d[1][0] + ls * dl[1][0],
                                         d[1][2] + ls * dl[1][2]);
           const float4 w1 = make_float4(d[0][1] + ls * dl[0][1], d[0][3] + ls * dl[0][3], d[1][1] + ls * dl[1][1],
@@ -338,8 +384,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           __syncwarp();
         }
         // ---- y-pass (a4)
-        const float4* yt = reinterpret_cast<const float4*>(ytab + ((size_t)sg.atom * C + iy) * 8);
-        const float4 y0 = __ldg(yt), y1 = __ldg(yt + 1);
+        const uint32_t ya = sa + kSlotFragBytes + (uint32_t)iy * 32;
+        const float4 y0 = lds128(ya), y1 = lds128(ya + 16);
         const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
         for (int ny = 0; ny < NP; ny++)
@@ -348,12 +394,14 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
             t2[s][BS::pair(nx, ny)] = fmaf(t1[nx], wy[ny], t2[s][BS::pair(nx, ny)]);
         if (y == ye[s] - 1) {
           if (bok) {
+            const size_t t2off = (size_t)rc.z * P * B + b;
 #pragma unroll
             for (int p = 0; p < P; p++) t2p[t2off + (size_t)p * B] = t2[s][p];
           }
           cur[s]++;
           ys[s] = cur[s] < end[s] ? segs[cur[s]].ys : 0x7fffffff;
           ye[s] = cur[s] < end[s] ? segs[cur[s]].ye : 0x7fffffff;
+          __syncwarp();  // the slot's tables may be restaged by the next segment
         }
       }
     }
@@ -428,7 +476,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 int plane_stages(int nx) {
-  const int budget = 160 * 1024;
+  const int budget = kPlaneSmemBudget - (int)PlaneSmem::fixed();
   return std::min(kPlaneMaxStages, std::max(2, budget / (int)plane_stage_bytes(nx)));
 }
 
@@ -446,17 +494,17 @@ cudaError_t plane_run(const PlaneLaunch& p) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.psi), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   if (p.nitems > 0) {
     const int stages = plane_stages(p.g.n[0]);
-    const size_t smem = PlaneSmem<NU>::bytes(p.g.n[0], stages);
+    const size_t smem = PlaneSmem::bytes(p.g.n[0], stages);
     auto kern = k_project_plane<NU, MODE>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(p.nitems, nbt), kPlaneThreads, smem, p.stream>>>(map, p.g, p.items, p.slot_ptr, p.segs, p.bfrag,
-                                                                 p.xtab, p.ytab, stages, p.t2p, p.status);
+    kern<<<(unsigned)p.nitems * nbt, kPlaneThreads, smem, p.stream>>>(map, p.g, p.items, p.slot_ptr, p.segs, p.bfrag,
+                                                                      p.xtab, p.ytab, stages, nbt, p.t2p, p.status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -482,7 +530,7 @@ bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nband
               sho_prec prec) {
   if (psi_dt != SHO_F32 || !fp32_stream_ok(psi, psi_dt, nbands)) return false;
   if (prec != SHO_P_FP32 && !is_tc(prec)) return false;
-  if (numax > kTcMaxNumax || cube % 16 != 0) return false;
+  if (numax > kTcMaxNumax || cube % 16 != 0 || cube > kPlaneMaxCube) return false;
   if (grid->n[0] > 256 || (long long)grid->n[0] * grid->n[1] * grid->n[2] >= (1ll << 31)) return false;
   if (grid->periodic && cube > grid->n[0]) return false;
   return encode_fn() != nullptr;
