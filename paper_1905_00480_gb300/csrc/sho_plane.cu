@@ -162,21 +162,28 @@ __host__ __device__ __forceinline__ uint32_t plane_stage_bytes(int nx) {
 }
 
 // Per (warp, slot) shared area, filled when a segment starts: the atom's B fragments (tensor forms:
-// [k-step][lane][4 words], up to 4 k-steps for a 32-point cube) or its x table (CUDA-core form,
-// [C][8]), and its y table [C][8].  The per-row work then reads shared memory only.
-constexpr int kSlotFragBytes = 4 * 32 * 16;
-constexpr int kSlotYBytes = 32 * 8 * 4;
-constexpr int kSlotBytes = kSlotFragBytes + kSlotYBytes;
+// [k-step][lane] with 2 words -- hi -- or 4 words -- hi, lo -- for the split forms; up to 4 k-steps for
+// a 32-point cube) or its x table (CUDA-core form, [C][8]), then its y table [C][8].  The per-row work
+// then reads shared memory only.
 constexpr int kPlaneMaxCube = 32;
 constexpr int kPlaneSmemBudget = 227 * 1024;
 
+template <int MODE>
+struct SlotLayout {
+  static constexpr bool kSplit = MODE == (int)TcMode::X3TF32 || MODE == (int)TcMode::SPLIT16;
+  static constexpr int kWords = kSplit ? 4 : 2;        // B-fragment words per (k-step, lane)
+  static constexpr int kFrag = 4 * 32 * kWords * 4;    // 1 or 2 KB (the CUDA-core x table: 1 KB)
+  static constexpr int kBytes = kFrag + 32 * 8 * 4;
+};
+
+template <int MODE>
 struct PlaneSmem {
   // everything but the ring, including the alignment slack of the ring
   static constexpr size_t fixed() {
     return 1024 + 2 * kPlaneMaxStages * sizeof(unsigned long long)   // full / empty barriers
            + (size_t)kPlaneWarps * 8 * kT1Stride * sizeof(float)      // T1 transpose buffers
-           + (size_t)kPlaneWarps * kPlaneSlots * kSlotBytes           // slot tables
-           + (size_t)kPlaneWarps * kPlaneSlots * 16;                  // slot records
+           + (size_t)kPlaneWarps * kPlaneSlots * SlotLayout<MODE>::kBytes  // slot tables
+           + (size_t)kPlaneWarps * kPlaneSlots * 32;                  // slot records
   }
   static size_t bytes(int nx, int stages) { return fixed() + (size_t)stages * plane_stage_bytes(nx); }
 };
@@ -203,8 +210,9 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   const uint32_t bar_full = ring + (uint32_t)stages * stagebytes;
   const uint32_t bar_empty = bar_full + kPlaneMaxStages * 8;
   const uint32_t t1buf = bar_empty + kPlaneMaxStages * 8;
+  using SL = SlotLayout<MODE>;
   const uint32_t slots = t1buf + kPlaneWarps * 8 * kT1Stride * 4;
-  const uint32_t recs = slots + kPlaneWarps * S * kSlotBytes;
+  const uint32_t recs = slots + kPlaneWarps * S * SL::kBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // band tiles of one plane run next to each other: they share DRAM pages and the plan entries
@@ -252,14 +260,21 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   const int b = b0 + lane;
   const bool bok = b < B;
   const int list0 = item.w + warp * S;
-  int cur[S], end[S], ys[S], ye[S];
+  // per slot: rows [ys, ye) of the current segment in registers; the segment cursor and list end in
+  // the slot record (words 4, 5), next to x0, iy - y, t2i and flags (words 0..3)
+  int ys[S], ye[S];
 #pragma unroll
   for (int s = 0; s < S; s++) {
-    cur[s] = slot_ptr[list0 + s];
-    end[s] = slot_ptr[list0 + s + 1];
-    ys[s] = cur[s] < end[s] ? segs[cur[s]].ys : 0x7fffffff;
-    ye[s] = cur[s] < end[s] ? segs[cur[s]].ye : 0x7fffffff;
+    const int c0 = slot_ptr[list0 + s], c1 = slot_ptr[list0 + s + 1];
+    ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
+    ye[s] = c0 < c1 ? segs[c0].ye : 0x7fffffff;
+    if (lane == 0) {
+      int* rec = reinterpret_cast<int*>(smem_raw + (recs - raw) + (warp * S + s) * 32);
+      rec[4] = c0;
+      rec[5] = c1;
+    }
   }
+  __syncwarp();
   float t2[S][P];
 #pragma unroll
   for (int s = 0; s < S; s++)
@@ -279,17 +294,22 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
 #pragma unroll
     for (int s = 0; s < S; s++) {
       if (ys[s] <= y) {  // warp-uniform: the slot's current segment covers this row
-        const uint32_t sa = slots + (uint32_t)(warp * S + s) * kSlotBytes;  // tables of this slot
-        const uint32_t ra = recs + (uint32_t)(warp * S + s) * 16;           // x0, iy - y, t2i, flags
+        const uint32_t sa = slots + (uint32_t)(warp * S + s) * SL::kBytes;  // tables of this slot
+        const uint32_t ra = recs + (uint32_t)(warp * S + s) * 32;           // slot record
+        int* rec = reinterpret_cast<int*>(smem_raw + (ra - raw));
         if (y == ys[s]) {
           // segment start: stage the atom's tables, record its offsets, load or clear the sums
-          const PlaneSeg sg = segs[cur[s]];
+          const PlaneSeg sg = segs[rec[4]];
           if constexpr (TC) {
             const uint4* src = reinterpret_cast<const uint4*>(bfrag + ((size_t)sg.atom * kWarp + lane) * (kMaxCube / 8) * 4);
             for (int ks = 0; ks * K < C; ks++) {
               const uint4 w = __ldg(src + ks);
-              asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};\n" ::"r"(sa + (uint32_t)(ks * 32 + lane) * 16),
-                           "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w));
+              if constexpr (SL::kSplit)
+                asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};\n" ::"r"(sa + (uint32_t)(ks * 32 + lane) * 16),
+                             "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w));
+              else
+                asm volatile("st.shared.v2.u32 [%0], {%1,%2};\n" ::"r"(sa + (uint32_t)(ks * 32 + lane) * 8), "r"(w.x),
+                             "r"(w.y));
             }
           } else if (lane < C) {
             const float4* src = reinterpret_cast<const float4*>(xtab + ((size_t)sg.atom * C + lane) * 8);
@@ -301,12 +321,16 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           if (lane < C) {
             const float4* src = reinterpret_cast<const float4*>(ytab + ((size_t)sg.atom * C + lane) * 8);
             const float4 f0 = __ldg(src), f1 = __ldg(src + 1);
-            float4* dst = reinterpret_cast<float4*>(smem_raw + (sa - raw) + kSlotFragBytes + lane * 32);
+            float4* dst = reinterpret_cast<float4*>(smem_raw + (sa - raw) + SL::kFrag + lane * 32);
             dst[0] = f0;
             dst[1] = f1;
           }
-          if (lane == 0)
-            *reinterpret_cast<int4*>(smem_raw + (ra - raw)) = make_int4(sg.x0, sg.iy0 - sg.ys, sg.t2i, sg.flags);
+          if (lane == 0) {
+            // bit 2 of the flags: the cube's x points are one contiguous run of the row (no wrap, no clip)
+            const bool lin = sg.x0 >= 0 && sg.x0 + C <= Nx;
+            *reinterpret_cast<int4*>(smem_raw + (ra - raw)) =
+                make_int4(sg.x0, sg.iy0 - sg.ys, sg.t2i, sg.flags | (lin ? 4 : 0));
+          }
           const size_t t2off = (size_t)sg.t2i * P * B + b;
 #pragma unroll
           for (int p = 0; p < P; p++) t2[s][p] = (sg.flags == 2 && bok) ? t2p[t2off + (size_t)p * B] : 0.0f;
@@ -333,36 +357,59 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           for (int m = 0; m < 2; m++)
 #pragma unroll
             for (int j = 0; j < 4; j++) d[m][j] = dl[m][j] = 0.0f;
+          const bool lin = (rc.w & 4) != 0;
+          // contiguous cube: x advances by 8 per TF32 k-step (1024 bytes, same swizzle phase), so the
+          // A loads are fixed offsets from two per-lane base addresses
+          const uint32_t pa = row + swz(x0 + 2 * tq, gq), pb = row + swz(x0 + 2 * tq + 1, gq);
 #pragma unroll
           for (int ks = 0; ks < kPlaneMaxCube / K; ks++) {
             if (ks * K < C) {
-              uint4 bw;
-              asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\n"
-                           : "=r"(bw.x), "=r"(bw.y), "=r"(bw.z), "=r"(bw.w)
-                           : "r"(sa + (uint32_t)(ks * 32 + lane) * 16));
+              uint4 bw = make_uint4(0u, 0u, 0u, 0u);
+              if constexpr (SL::kSplit)
+                asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\n"
+                             : "=r"(bw.x), "=r"(bw.y), "=r"(bw.z), "=r"(bw.w)
+                             : "r"(sa + (uint32_t)(ks * 32 + lane) * 16));
+              else
+                asm volatile("ld.shared.v2.u32 {%0,%1}, [%2];\n"
+                             : "=r"(bw.x), "=r"(bw.y)
+                             : "r"(sa + (uint32_t)(ks * 32 + lane) * 8));
               BFrag<TM> bfr;
               bfr.hi[0] = bw.x;
               bfr.hi[1] = bw.y;
               bfr.lo[0] = bw.z;
               bfr.lo[1] = bw.w;
               if constexpr (K == 8) {
-                const int xa = plane_x(x0, 8 * ks + 2 * tq, Nx, g.periodic);
-                const int xb = plane_x(x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
-                const float4 va = lds128(row + swz(xa, gq));
-                const float4 vb = lds128(row + swz(xb, gq));
+                float4 va, vb;
+                if (lin) {
+                  va = lds128(pa + ks * 1024);
+                  vb = lds128(pb + ks * 1024);
+                } else {
+                  const int xa = plane_x(x0, 8 * ks + 2 * tq, Nx, g.periodic);
+                  const int xb = plane_x(x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
+                  va = lds128(row + swz(xa, gq));
+                  vb = lds128(row + swz(xb, gq));
+                }
                 const float a0[4] = {va.x, va.y, vb.x, vb.y};
                 const float a1[4] = {va.z, va.w, vb.z, vb.w};
                 tc_product<TM>(d[0], dl[0], a0, bfr);
                 tc_product<TM>(d[1], dl[1], a1, bfr);
               } else {
-                const int xq0 = plane_x(x0, 16 * ks + 2 * tq, Nx, g.periodic);
-                const int xq1 = plane_x(x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
-                const int xq2 = plane_x(x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
-                const int xq3 = plane_x(x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
-                const float4 v0 = lds128(row + swz(xq0, gq));
-                const float4 v1 = lds128(row + swz(xq1, gq));
-                const float4 v2 = lds128(row + swz(xq2, gq));
-                const float4 v3 = lds128(row + swz(xq3, gq));
+                float4 v0, v1, v2, v3;
+                if (lin) {
+                  v0 = lds128(pa + ks * 2048);
+                  v1 = lds128(pb + ks * 2048);
+                  v2 = lds128(pa + ks * 2048 + 1024);
+                  v3 = lds128(pb + ks * 2048 + 1024);
+                } else {
+                  const int xq0 = plane_x(x0, 16 * ks + 2 * tq, Nx, g.periodic);
+                  const int xq1 = plane_x(x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
+                  const int xq2 = plane_x(x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
+                  const int xq3 = plane_x(x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
+                  v0 = lds128(row + swz(xq0, gq));
+                  v1 = lds128(row + swz(xq1, gq));
+                  v2 = lds128(row + swz(xq2, gq));
+                  v3 = lds128(row + swz(xq3, gq));
+                }
                 const float a0[8] = {v0.x, v1.x, v0.y, v1.y, v2.x, v3.x, v2.y, v3.y};
                 const float a1[8] = {v0.z, v1.z, v0.w, v1.w, v2.z, v3.z, v2.w, v3.w};
                 tc_product<TM>(d[0], dl[0], a0, bfr);
@@ -371,11 +418,15 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
             }
           }
           // lane (g, t) holds T1 of bands 4g..4g+3 at n = 2t, 2t+1; transpose to one band per lane
-          const float ls = tc_lo_scale<TM>();
-          const float4 w0 = make_float4(d[0][0] + ls * dl[0][0], d[0][2] + ls * dl[0][2], d[1][0] + ls * dl[1][0],
-                                        d[1][2] + ls * dl[1][2]);
-          const float4 w1 = make_float4(d[0][1] + ls * dl[0][1], d[0][3] + ls * dl[0][3], d[1][1] + ls * dl[1][1],
-                                        d[1][3] + ls * dl[1][3]);
+          if constexpr (TM == TcMode::X3TF32 || TM == TcMode::SPLIT16) {
+            const float ls = tc_lo_scale<TM>();
+#pragma unroll
+            for (int m = 0; m < 2; m++)
+#pragma unroll
+              for (int j = 0; j < 4; j++) d[m][j] = fmaf(ls, dl[m][j], d[m][j]);
+          }
+          const float4 w0 = make_float4(d[0][0], d[0][2], d[1][0], d[1][2]);
+          const float4 w1 = make_float4(d[0][1], d[0][3], d[1][1], d[1][3]);
           *reinterpret_cast<float4*>(t1w + (2 * tq) * kT1Stride + 4 * gq) = w0;
           *reinterpret_cast<float4*>(t1w + (2 * tq + 1) * kT1Stride + 4 * gq) = w1;
           __syncwarp();
@@ -384,7 +435,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           __syncwarp();
         }
         // ---- y-pass (a4)
-        const uint32_t ya = sa + kSlotFragBytes + (uint32_t)iy * 32;
+        const uint32_t ya = sa + SL::kFrag + (uint32_t)iy * 32;
         const float4 y0 = lds128(ya), y1 = lds128(ya + 16);
         const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
@@ -398,10 +449,12 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
 #pragma unroll
             for (int p = 0; p < P; p++) t2p[t2off + (size_t)p * B] = t2[s][p];
           }
-          cur[s]++;
-          ys[s] = cur[s] < end[s] ? segs[cur[s]].ys : 0x7fffffff;
-          ye[s] = cur[s] < end[s] ? segs[cur[s]].ye : 0x7fffffff;
-          __syncwarp();  // the slot's tables may be restaged by the next segment
+          const int c0 = rec[4] + 1, c1 = rec[5];
+          ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
+          ye[s] = c0 < c1 ? segs[c0].ye : 0x7fffffff;
+          __syncwarp();  // every lane has read the cursor; the slot's tables may be restaged next
+          if (lane == 0) rec[4] = c0;
+          __syncwarp();
         }
       }
     }
@@ -475,8 +528,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+template <int MODE>
 int plane_stages(int nx) {
-  const int budget = kPlaneSmemBudget - (int)PlaneSmem::fixed();
+  const int budget = kPlaneSmemBudget - (int)PlaneSmem<MODE>::fixed();
   return std::min(kPlaneMaxStages, std::max(2, budget / (int)plane_stage_bytes(nx)));
 }
 
@@ -498,8 +552,8 @@ cudaError_t plane_run(const PlaneLaunch& p) {
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   if (p.nitems > 0) {
-    const int stages = plane_stages(p.g.n[0]);
-    const size_t smem = PlaneSmem::bytes(p.g.n[0], stages);
+    const int stages = plane_stages<MODE>(p.g.n[0]);
+    const size_t smem = PlaneSmem<MODE>::bytes(p.g.n[0], stages);
     auto kern = k_project_plane<NU, MODE>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -607,7 +661,7 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
       }
     }
   }
-  std::vector<int> free_at((size_t)W * S);
+  std::vector<int> free_at((size_t)W * S), cum((size_t)W);
   std::vector<std::vector<PlaneSeg>> lists((size_t)W * S);
   for (int z = 0; z < nz; z++) {
     std::vector<PlaneSeg> pend = byz[(size_t)z];
@@ -616,6 +670,7 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
     });
     while (!pend.empty()) {
       std::fill(free_at.begin(), free_at.end(), 0);
+      std::fill(cum.begin(), cum.end(), 0);
       for (auto& l : lists) l.clear();
       std::vector<int> tail_slot(at.size(), -1);  // slot of an atom's tail in this round
       std::vector<char> defer(at.size(), 0);      // atom's wrapped pair moves to the next round
@@ -625,7 +680,9 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
           next.push_back(sg);
           continue;
         }
-        int best = -1, best_load = 1 << 30;
+        // least busy warp at the segment's first row, then the least rows assigned so far: keeps the
+        // warps' total work even, so none holds the row ring back for long
+        int best = -1, best_load = 1 << 30, best_cum = 1 << 30;
         for (int w = 0; w < W; w++) {
           if (same_warp && sg.flags == 2 && tail_slot[(size_t)sg.atom] >= 0 && tail_slot[(size_t)sg.atom] / S != w)
             continue;
@@ -636,8 +693,9 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
             else if (freeslot < 0)
               freeslot = w * S + s;
           }
-          if (freeslot >= 0 && load < best_load) {
+          if (freeslot >= 0 && (load < best_load || (load == best_load && cum[(size_t)w] < best_cum))) {
             best_load = load;
+            best_cum = cum[(size_t)w];
             best = freeslot;
           }
         }
@@ -658,6 +716,7 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
         }
         lists[(size_t)best].push_back(sg);
         free_at[(size_t)best] = sg.ye;
+        cum[(size_t)(best / S)] += sg.ye - sg.ys;
         if (sg.flags == 1) tail_slot[(size_t)sg.atom] = best;
       }
       bool placed = false;
