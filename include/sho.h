@@ -188,6 +188,27 @@ int sho_apply_nonlocal(sho_handle* handle, const sho_grid* grid, const void* psi
                        const void* D, void* hpsi, void* stream);
 
 /* ----------------------------------------------------------------------------------------------
+ * Cartesian <-> radial SHO coefficients -- eq. SHO-transform-Cartesian-to-radial (Sec. 2.4): within an
+ * energy shell nx + ny + nz = 2 nr + l the Cartesian states (Sec. 2.2) and the radial states
+ * Psi_{nr l m} = R_{nr l}(r) Y_{l m} (eq. SHO-eigenstate-radial, Sec. 2.3) span the same space, related
+ * by the orthogonal, shell-block-diagonal U[k][j] = <Psi_j^rad | Psi_k^cart>.  Conventions: real Y_{l m}
+ * from the complex ones with the Condon-Shortley phase (m > 0: sqrt(2)(-1)^m Re Y_l^m, m < 0:
+ * sqrt(2)(-1)^m Im Y_l^|m|, so l = 1, m = +1 / -1 / 0 are x / y / z); R_{nr l} ~ r^l L_nr^(l+1/2)(r^2/sigma^2)
+ * e^{-r^2/2sigma^2} normalised and positive at the origin; radial order nu ascending, then l ascending
+ * (l = nu mod 2 .. nu), then m = -l .. l.  U does not depend on sigma.
+ *   sho_radial_labels   host: nr[j], ell[j], m[j] of the N = sho_nstates(numax) radial states
+ *   sho_radial_matrix   host: U as N x N doubles, row-major U[k * N + j] (k Cartesian, library order)
+ *   sho_radial_transform  device arrays [natoms][N][nbands] of dtype F64 or F32, in != out:
+ *       direction 0 (Cartesian -> radial)  out[a][j][b] = sum_k U[k][j] in[a][k][b]
+ *       direction 1 (radial -> Cartesian)  out[a][k][b] = sum_j U[k][j] in[a][j][b]  (the inverse)
+ * numax <= SHO_MAX_NUMAX (SHO_ERR_NUMAX).  The handle caches the device copy of U per numax.
+ */
+int sho_radial_labels(int numax, int* nr, int* ell, int* m);
+int sho_radial_matrix(int numax, double* U);
+int sho_radial_transform(sho_handle* handle, int natoms, int numax, int nbands, const void* in, void* out,
+                         sho_dtype dtype, int direction, void* stream);
+
+/* ----------------------------------------------------------------------------------------------
  * Stored-projector FP64 baseline: the conventional scheme the paper measures against ("USU", Sec. 6,
  * Table 1): projector values sampled once onto each atom's cube and kept in device memory, then
  * streamed by the projection and expansion.  With the stored values taken from the SHO basis the

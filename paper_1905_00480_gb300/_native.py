@@ -43,6 +43,7 @@ _lock = threading.Lock()
 
 _VP = ctypes.c_void_p
 _DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
 _I = ctypes.c_int
 _GP = ctypes.POINTER(sho_grid)
 
@@ -57,6 +58,9 @@ SIGNATURES = {
     "sho_set_strict": (_I, [_VP, _I]),
     "sho_sync": (_I, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),
+    "sho_radial_labels": (_I, [_I, _IP, _IP, _IP]),
+    "sho_radial_matrix": (_I, [_I, _DP]),
+    "sho_radial_transform": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I, _VP]),
     "sho_project": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
     "sho_add": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
     "sho_forces": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),

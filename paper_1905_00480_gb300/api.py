@@ -143,6 +143,44 @@ def project_path(psi: torch.Tensor, numax: int, cube: int, h: float, periodic: b
     return {1: "atom", 2: "plane"}[r]
 
 
+def radial_labels(numax: int):
+    """sho_radial_labels: (nr, l, m) of the radial SHO states in the library's order."""
+    n = nstates(numax)
+    nr, ell, m = ((ctypes.c_int * n)() for _ in range(3))
+    N.check(N.lib().sho_radial_labels(int(numax), nr, ell, m), "sho_radial_labels")
+    return [(nr[i], ell[i], m[i]) for i in range(n)]
+
+
+def radial_matrix(numax: int):
+    """sho_radial_matrix: U[k][j] = <Psi_j^rad | Psi_k^cart> as a float64 numpy array [N][N]."""
+    import numpy as np
+    n = nstates(numax)
+    U = np.zeros((n, n), dtype=np.float64)
+    N.check(N.lib().sho_radial_matrix(int(numax), U.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+            "sho_radial_matrix")
+    return U
+
+
+def to_radial(coeff: torch.Tensor, numax: int, inverse: bool = False, out: torch.Tensor = None,
+              handle: Handle = None, stream=None) -> torch.Tensor:
+    """sho_radial_transform: Cartesian [A][N][B] coefficients to radial ones (inverse=True: back)."""
+    if not coeff.is_cuda or not coeff.is_contiguous() or coeff.dim() != 3 or coeff.shape[1] != nstates(numax):
+        raise ValueError("coeff must be a contiguous CUDA tensor [A][N][B]")
+    if coeff.dtype not in (torch.float64, torch.float32):
+        raise ValueError("coeff must be float64 or float32")
+    if out is None:
+        out = torch.empty_like(coeff)
+    elif out.shape != coeff.shape or out.dtype != coeff.dtype or not out.is_contiguous():
+        raise ValueError("out has the wrong dtype, shape or layout")
+    hd = handle or default_handle(coeff.device.index or 0)
+    A, _, B = coeff.shape
+    st = N.lib().sho_radial_transform(hd.ptr, A, int(numax), B, ctypes.c_void_p(coeff.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()), N.DTYPES[_TORCH_DT[coeff.dtype]],
+                                      1 if inverse else 0, _stream_ptr(coeff, stream))
+    N.check(st, "sho_radial_transform")
+    return out
+
+
 def add(psi: torch.Tensor, coeff: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, periodic: bool = True,
         prec: str = "fp64", handle: Handle = None, stream=None) -> torch.Tensor:
     """sho_add (in place): psi[j][b] += sum_a sum_k c[a][k][b] Psi_k(u).  Returns psi."""

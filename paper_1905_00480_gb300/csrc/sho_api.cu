@@ -20,6 +20,11 @@ struct sho_handle {
   bool has_last = false;
   int device_error = SHO_OK;   // first device-side error since the last sho_sync
   int* dstatus = nullptr;      // device word set by kernels whose bounded waits expired
+  // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
+  struct RadialDev {
+    void* mem = nullptr;
+    int nnz = 0;
+  } radial[SHO_MAX_NUMAX + 1][2];
 };
 
 namespace sho {
@@ -393,6 +398,9 @@ int sho_create(sho_handle** out, int device) {
   if (cudaMalloc(&h->dstatus, sizeof(int)) != cudaSuccess || cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     if (h->dstatus) cudaFree(h->dstatus);
+    for (auto& row : h->radial)
+      for (auto& r : row)
+        if (r.mem) cudaFree(r.mem);
     cudaEventDestroy(h->last);
     delete h;
     return SHO_ERR_OOM;
@@ -410,6 +418,9 @@ int sho_destroy(sho_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->coeff_ws) cudaFree(h->coeff_ws);
     if (h->dstatus) cudaFree(h->dstatus);
+    for (auto& row : h->radial)
+      for (auto& r : row)
+        if (r.mem) cudaFree(r.mem);
     if (h->last) cudaEventDestroy(h->last);
   }
   delete h;
@@ -435,6 +446,70 @@ int sho_sync(sho_handle* h) {
   int e = h->device_error;
   h->device_error = SHO_OK;
   return e;
+}
+
+int sho_radial_labels(int numax, int* nr, int* ell, int* m) {
+  if (numax < 0 || numax > SHO_MAX_NUMAX) return SHO_ERR_NUMAX;
+  if (!nr || !ell || !m) return SHO_ERR_ARG;
+  radial_labels(numax, nr, ell, m);
+  return SHO_OK;
+}
+
+int sho_radial_matrix(int numax, double* U) {
+  if (numax < 0 || numax > SHO_MAX_NUMAX) return SHO_ERR_NUMAX;
+  if (!U) return SHO_ERR_ARG;
+  const size_t N = (size_t)nstates(numax);
+  std::memcpy(U, radial_matrix(numax), N * N * sizeof(double));
+  return SHO_OK;
+}
+
+int sho_radial_transform(sho_handle* h, int natoms, int numax, int nbands, const void* in, void* out, sho_dtype dtype,
+                         int direction, void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  if (numax < 0 || numax > SHO_MAX_NUMAX) return SHO_ERR_NUMAX;
+  if (natoms < 0 || nbands < 0 || (direction != 0 && direction != 1)) return SHO_ERR_ARG;
+  if (dtype != SHO_F64 && dtype != SHO_F32) return SHO_ERR_DTYPE;
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!in || !out || in == out) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int N = nstates(numax);
+  auto& rd = h->radial[numax][direction];
+  if (!rd.mem) {
+    std::vector<int> rowp, col;
+    std::vector<double> val;
+    radial_csr(numax, direction, rowp, col, val);
+    std::vector<float> valf(val.begin(), val.end());
+    const size_t nnz = col.size();
+    const size_t bytes = (rowp.size() + nnz) * sizeof(int) + nnz * (sizeof(double) + sizeof(float)) + 64;
+    std::vector<char> blob(bytes, 0);
+    size_t off = 0;
+    std::memcpy(blob.data() + off, rowp.data(), rowp.size() * sizeof(int));
+    off += rowp.size() * sizeof(int);
+    std::memcpy(blob.data() + off, col.data(), nnz * sizeof(int));
+    off = (off + nnz * sizeof(int) + 7) & ~(size_t)7;
+    std::memcpy(blob.data() + off, val.data(), nnz * sizeof(double));
+    off += nnz * sizeof(double);
+    std::memcpy(blob.data() + off, valf.data(), nnz * sizeof(float));
+    if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+    if (cudaMalloc(&rd.mem, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rd.mem = nullptr;
+      return SHO_ERR_OOM;
+    }
+    if (cudaMemcpy(rd.mem, blob.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) return SHO_ERR_CUDA;
+    rd.nnz = (int)nnz;
+  }
+  const char* base = static_cast<const char*>(rd.mem);
+  const int* rowp = reinterpret_cast<const int*>(base);
+  const int* col = rowp + N + 1;
+  const size_t off_val = (((size_t)(N + 1) + rd.nnz) * sizeof(int) + 7) & ~(size_t)7;
+  const void* val = dtype == SHO_F64 ? (const void*)(base + off_val)
+                                     : (const void*)(base + off_val + (size_t)rd.nnz * sizeof(double));
+  SHO_TRY(begin_call(h, s));
+  if (launch_radial(natoms, N, nbands, dtype, rowp, col, val, in, out, s) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
 }
 
 int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int numax, int cube,

@@ -135,6 +135,13 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
 cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec);
 constexpr size_t kPlaneBfragBytesPerAtom = 32 * (kMaxCube / 8) * 4 * sizeof(uint32_t);
 
+// Cartesian <-> radial transform (sho_radial.cu): labels and U on the host, CSR rows for the kernel.
+int radial_labels(int numax, int* nr, int* l, int* m);
+const double* radial_matrix(int numax);
+void radial_csr(int numax, int direction, std::vector<int>& rowp, std::vector<int>& col, std::vector<double>& val);
+cudaError_t launch_radial(int natoms, int N, int nbands, sho_dtype dt, const int* rowp, const int* col,
+                          const void* val, const void* in, void* out, cudaStream_t s);
+
 // Kernel launchers (return a CUDA error code).
 cudaError_t launch_usu(int op, const UsuLaunch& p);
 bool usu_supported_nproj(int n);

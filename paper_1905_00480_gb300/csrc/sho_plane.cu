@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           // contiguous cube: x advances by 8 per TF32 k-step (1024 bytes, same swizzle phase), so the
           // A loads are fixed offsets from two per-lane base addresses
           const uint32_t pa = row + swz(x0 + 2 * tq, gq), pb = row + swz(x0 + 2 * tq + 1, gq);
-#pragma unroll
+#pragma unroll 2
           for (int ks = 0; ks < kPlaneMaxCube / K; ks++) {
             if (ks * K < C) {
               uint4 bw = make_uint4(0u, 0u, 0u, 0u);
