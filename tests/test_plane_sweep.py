@@ -1,4 +1,5 @@
-"""Plane-sweep projection of the FP32-class forms (FP32 psi, numax <= 7) against the FP64 oracle (GPU).
+"""Plane-sweep projection and expansion of the FP32-class forms (FP32 psi, numax <= 7) against the FP64
+oracle (GPU).
 
 The plane sweep assigns every (atom, plane) row segment to a register slot on the host; these cases
 drive its corners: more overlapping atoms per row than slots (several sweeps of one plane), wrapped
@@ -122,3 +123,69 @@ def test_plane_sweep_repeatable_and_status_clear():
     assert torch.equal(c1, c2)
     ref = oracle.project(grid, h, True, psi.double().cpu().numpy(), pos[:3], sig[:3], numax, cube)
     assert rel_norm(c1[:3].double().cpu().numpy(), ref) <= TOL["tf32"]
+
+
+def _expand(grid, h, periodic, pos, sig, numax, cube, nbands, prec, seed):
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands)).astype(np.float32)
+    c = rng.standard_normal((len(pos), oracle.nstates(numax), nbands)).astype(np.float32)
+    out = torch.from_numpy(psi).cuda()
+    api.add(out, torch.from_numpy(c).cuda(), pos, sig, numax, cube, h, periodic, prec=prec)
+    ref = oracle.add(grid, h, periodic, psi.astype(np.float64), pos, sig, numax, cube, c.astype(np.float64))
+    return out.double().cpu().numpy() - psi, ref - psi
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
+def test_expand_dense_atoms(prec):
+    """Planes swept more than once: the second sweep adds to rows the first one wrote."""
+    require_gpu()
+    rng = np.random.default_rng(611)
+    grid, h, numax, cube = (48, 48, 48), 0.2, 3, 32
+    pos, sig = workloads.random_atoms(rng, 120, tuple(n * h for n in grid), True, min_sep=0.6)
+    got, ref = _expand(grid, h, True, pos, sig, numax, cube, 8, prec, 612)
+    assert rel_norm(got, ref) <= _tol(prec)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "split_fp16"])
+def test_expand_wrapped_and_open(prec):
+    require_gpu()
+    rng = np.random.default_rng(613)
+    grid, h, numax, cube = (36, 34, 40), 0.2, 5, 32
+    pos, sig = workloads.random_atoms(rng, 7, tuple(n * h for n in grid), True, min_sep=1.0)
+    got, ref = _expand(grid, h, True, pos, sig, numax, cube, 36, prec, 614)
+    assert rel_norm(got, ref) <= _tol(prec)
+    grid, h, numax = (40, 40, 40), 0.25, 4
+    L = 40 * h
+    pos = np.array([[-2.0, 3.0, 5.0], [L + 1.5, L - 0.3, 0.2], [5.0, -9.0, 5.0], [4.9, 5.1, L + 2.0], [0.1, 0.2, 0.3]])
+    sig = np.array([0.8, 0.9, 0.7, 1.0, 0.6])
+    got, ref = _expand(grid, h, False, pos, sig, numax, cube, 16, prec, 615)
+    assert rel_norm(got, ref) <= _tol(prec)
+
+
+@pytest.mark.parametrize("numax", list(range(8)))
+def test_expand_every_numax(numax):
+    require_gpu()
+    rng = np.random.default_rng(616 + numax)
+    grid, h, cube = (40, 36, 32), 0.2, 16
+    pos, sig = workloads.random_atoms(rng, 6, tuple(n * h for n in grid), True, min_sep=1.0)
+    for prec in ("fp32", "tf32", "bf16"):
+        got, ref = _expand(grid, h, True, pos, sig, numax, cube, 12, prec, 640 + numax)
+        assert rel_norm(got, ref) <= _tol(prec)
+
+
+def test_expand_bitwise_repeatable():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(650)
+    grid, h, numax, cube = (64, 64, 64), 0.2, 7, 32
+    pos, sig = workloads.random_atoms(rng, 40, tuple(n * h for n in grid), True, min_sep=1.5)
+    c = torch.from_numpy(rng.standard_normal((40, oracle.nstates(numax), 64)).astype(np.float32)).cuda()
+    outs = []
+    for _ in range(2):
+        out = torch.zeros((64, 64, 64, 64), dtype=torch.float32, device="cuda")
+        api.add(out, c, pos, sig, numax, cube, h, True, prec="tf32")
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
