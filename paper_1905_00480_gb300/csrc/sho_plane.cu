@@ -532,8 +532,12 @@ constexpr int kExpSlots = kExpWarps * kPlaneSlots;
 constexpr int kExpChunk = 16;
 constexpr int kT1x = 40;  // padded stride (floats) of a T1 row [n][band]: conflict-free A loads
 
+// Per slot: two x tables (segments alternate between them: phase 2 of other warps may still read the
+// previous segment's table in the row after it ended) and one y table (read by the owner only).
+constexpr int kExpTabFloats = 3 * kPlaneMaxCube * 8;
+
 struct ExpSmem {
-  static constexpr size_t tables = (size_t)kExpSlots * 2 * kPlaneMaxCube * 8 * 4;  // x and y tables
+  static constexpr size_t tables = (size_t)kExpSlots * kExpTabFloats * 4;          // x, x', y tables
   static constexpr size_t t1 = (size_t)2 * kExpSlots * 8 * kT1x * 4;               // T1, two buffers
   static constexpr size_t recs = (size_t)2 * kExpSlots * 16 + (size_t)kExpSlots * 16;
   static constexpr size_t bytes = tables + t1 + recs;
@@ -563,10 +567,12 @@ __global__ void __launch_bounds__(kExpThreads, 1)
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int NA = TcFrag<TM>::NA, NB = TcFrag<TM>::NB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* tabs = reinterpret_cast<float*>(smem_raw);                                   // [slot][x|y][C][8]
+  float* tabs = reinterpret_cast<float*>(smem_raw);                                   // [slot][x|x'|y][C][8]
   float* t1all = reinterpret_cast<float*>(smem_raw + ExpSmem::tables);                // [buf][slot][8][kT1x]
   int4* rec = reinterpret_cast<int4*>(smem_raw + ExpSmem::tables + ExpSmem::t1);      // [buf][slot]
   int* cursor = reinterpret_cast<int*>(rec + 2 * kExpSlots);                          // [slot][4]
+  // cursor[slot]: 0 current segment, 1 end of the slot's list, 2 x0, 3 iy - y; the x table of the
+  // current segment is (segment index & 1)
   const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
   const int z = (int)blockIdx.x / nbt, bt = (int)blockIdx.x - z * nbt;
@@ -603,17 +609,19 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 #pragma unroll
       for (int s = 0; s < S; s++) {
         const int slot = warp * S + s;
-        float* tx = tabs + (size_t)slot * 2 * kPlaneMaxCube * 8;   // x table [C][8], then y table
+        float* tsl = tabs + (size_t)slot * kExpTabFloats;          // x tables [2][C][8], y table [C][8]
+        float* tyt = tsl + 2 * kPlaneMaxCube * 8;
         float* t1w = t1all + ((size_t)buf * kExpSlots + slot) * 8 * kT1x;
         if (ys[s] <= y) {
           if (y == ys[s]) {
             // segment start: tables into the slot area, z-pass of this plane into registers
-            const PlaneSeg sg = segs[cursor[slot * 4]];
+            const int cseg = cursor[slot * 4];
+            const PlaneSeg sg = segs[cseg];
             if (lane < C) {
               const float4* sx = reinterpret_cast<const float4*>(xtab + ((size_t)sg.atom * C + lane) * 8);
               const float4* sy = reinterpret_cast<const float4*>(ytab + ((size_t)sg.atom * C + lane) * 8);
-              float4* dx = reinterpret_cast<float4*>(tx + lane * 8);
-              float4* dy = reinterpret_cast<float4*>(tx + kPlaneMaxCube * 8 + lane * 8);
+              float4* dx = reinterpret_cast<float4*>(tsl + (cseg & 1) * kPlaneMaxCube * 8 + lane * 8);
+              float4* dy = reinterpret_cast<float4*>(tyt + lane * 8);
               dx[0] = __ldg(sx);
               dx[1] = __ldg(sx + 1);
               dy[0] = __ldg(sy);
@@ -643,7 +651,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             __syncwarp();
           }
           const int iy = y + cursor[slot * 4 + 3];
-          const float4* yt = reinterpret_cast<const float4*>(tx + kPlaneMaxCube * 8 + iy * 8);
+          const float4* yt = reinterpret_cast<const float4*>(tyt + iy * 8);
           const float4 y0 = yt[0], y1 = yt[1];
           const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
@@ -655,7 +663,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
           }
 #pragma unroll
           for (int nx = NP; nx < 8; nx++) t1w[nx * kT1x + lane] = 0.0f;
-          if (lane == 0) rec[buf * kExpSlots + slot] = make_int4(1, cursor[slot * 4 + 2], 0, 0);
+          if (lane == 0) rec[buf * kExpSlots + slot] = make_int4(1, cursor[slot * 4 + 2], cursor[slot * 4] & 1, 0);
           if (y == ye[s] - 1) {
             const int c0 = cursor[slot * 4] + 1, c1 = cursor[slot * 4 + 1];
             ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
@@ -711,7 +719,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             const int4 r = rb[sl];
             if (!r.x) continue;
             const float* ts = t1b + (size_t)sl * 8 * kT1x;
-            const float* xs = tabs + (size_t)sl * 2 * kPlaneMaxCube * 8;
+            const float* xs = tabs + (size_t)sl * kExpTabFloats + r.z * kPlaneMaxCube * 8;
             // A = T1[band][n], rows of tile m: bands 4g + 2m (row g) and 4g + 2m + 1 (row g + 8)
             float av[2][NA];
             {
@@ -778,7 +786,7 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             const int4 r = rb[sl];
             if (!r.x) continue;
             const float* ts = t1b + (size_t)sl * 8 * kT1x;
-            const float* xs = tabs + (size_t)sl * 2 * kPlaneMaxCube * 8;
+            const float* xs = tabs + (size_t)sl * kExpTabFloats + r.z * kPlaneMaxCube * 8;
             float t1[NP];
 #pragma unroll
             for (int n = 0; n < NP; n++) t1[n] = ts[n * kT1x + lane];
