@@ -539,7 +539,7 @@ constexpr int kExpTabFloats = 3 * kPlaneMaxCube * 8;
 struct ExpSmem {
   static constexpr size_t tables = (size_t)kExpSlots * kExpTabFloats * 4;          // x, x', y tables
   static constexpr size_t t1 = (size_t)2 * kExpSlots * 8 * kT1x * 4;               // T1, two buffers
-  static constexpr size_t recs = (size_t)2 * kExpSlots * 16 + (size_t)kExpSlots * 16;
+  static constexpr size_t recs = (size_t)2 * kExpSlots * 16 + (size_t)kExpSlots * 32 + 2 * kExpWarps * 4;
   static constexpr size_t bytes = tables + t1 + recs;
 };
 
@@ -570,9 +570,9 @@ __global__ void __launch_bounds__(kExpThreads, 1)
   float* tabs = reinterpret_cast<float*>(smem_raw);                                   // [slot][x|x'|y][C][8]
   float* t1all = reinterpret_cast<float*>(smem_raw + ExpSmem::tables);                // [buf][slot][8][kT1x]
   int4* rec = reinterpret_cast<int4*>(smem_raw + ExpSmem::tables + ExpSmem::t1);      // [buf][slot]
-  int* cursor = reinterpret_cast<int*>(rec + 2 * kExpSlots);                          // [slot][4]
-  // cursor[slot]: 0 current segment, 1 end of the slot's list, 2 x0, 3 iy - y; the x table of the
-  // current segment is (segment index & 1)
+  // per slot: current segment, end of the slot's list, x0, iy - y, chunk mask of the current segment
+  int* cursor = reinterpret_cast<int*>(rec + 2 * kExpSlots);                          // [slot][8]
+  int* wmask = cursor + kExpSlots * 8;                                                 // [buf][warp]
   const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
   const int z = (int)blockIdx.x / nbt, bt = (int)blockIdx.x - z * nbt;
@@ -592,8 +592,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
       ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
       ye[s] = c0 < c1 ? segs[c0].ye : 0x7fffffff;
       if (lane == 0) {
-        cursor[(warp * S + s) * 4 + 0] = c0;
-        cursor[(warp * S + s) * 4 + 1] = c1;
+        cursor[(warp * S + s) * 8 + 0] = c0;
+        cursor[(warp * S + s) * 8 + 1] = c1;
       }
     }
     __syncwarp();
@@ -606,16 +606,20 @@ __global__ void __launch_bounds__(kExpThreads, 1)
     for (int y = ylo; y < yhi; y++) {
       const int buf = (y - ylo) & 1;
       // ---------------------------------------------------------------- phase 1: y-pass per slot
+      int am = 0;  // slots of this warp active in this row
 #pragma unroll
       for (int s = 0; s < S; s++) {
         const int slot = warp * S + s;
+        int* cur = cursor + slot * 8;
         float* tsl = tabs + (size_t)slot * kExpTabFloats;          // x tables [2][C][8], y table [C][8]
         float* tyt = tsl + 2 * kPlaneMaxCube * 8;
         float* t1w = t1all + ((size_t)buf * kExpSlots + slot) * 8 * kT1x;
         if (ys[s] <= y) {
+          am |= 1 << s;
           if (y == ys[s]) {
-            // segment start: tables into the slot area, z-pass of this plane into registers
-            const int cseg = cursor[slot * 4];
+            // segment start: tables into the slot area, z-pass of this plane into registers, and the
+            // row chunks the cube meets (lane i: cube point i)
+            const int cseg = cur[0];
             const PlaneSeg sg = segs[cseg];
             if (lane < C) {
               const float4* sx = reinterpret_cast<const float4*>(xtab + ((size_t)sg.atom * C + lane) * 8);
@@ -627,6 +631,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
               dy[0] = __ldg(sy);
               dy[1] = __ldg(sy + 1);
             }
+            int x = sg.x0 + lane;
+            if (g.periodic && x >= Nx) x -= Nx;
+            const unsigned bit = (lane < C && x >= 0 && x < Nx) ? (1u << (x / kExpChunk)) : 0u;
+            const unsigned cm = __reduce_or_sync(0xffffffffu, bit);
             const float4* zt = reinterpret_cast<const float4*>(ztab + ((size_t)sg.atom * C + sg.iz) * 8);
             const float4 z0 = __ldg(zt), z1 = __ldg(zt + 1);
             const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
@@ -645,12 +653,13 @@ __global__ void __launch_bounds__(kExpThreads, 1)
                   k++;
                 }
             if (lane == 0) {
-              cursor[slot * 4 + 2] = sg.x0;
-              cursor[slot * 4 + 3] = sg.iy0 - sg.ys;
+              cur[2] = sg.x0;
+              cur[3] = sg.iy0 - sg.ys;
+              cur[4] = (int)cm;
             }
             __syncwarp();
           }
-          const int iy = y + cursor[slot * 4 + 3];
+          const int iy = y + cur[3];
           const float4* yt = reinterpret_cast<const float4*>(tyt + iy * 8);
           const float4 y0 = yt[0], y1 = yt[1];
           const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
@@ -663,42 +672,34 @@ __global__ void __launch_bounds__(kExpThreads, 1)
           }
 #pragma unroll
           for (int nx = NP; nx < 8; nx++) t1w[nx * kT1x + lane] = 0.0f;
-          if (lane == 0) rec[buf * kExpSlots + slot] = make_int4(1, cursor[slot * 4 + 2], cursor[slot * 4] & 1, 0);
+          if (lane == 0) rec[buf * kExpSlots + slot] = make_int4(cur[4], cur[2], cur[0] & 1, 0);
           if (y == ye[s] - 1) {
-            const int c0 = cursor[slot * 4] + 1, c1 = cursor[slot * 4 + 1];
+            const int c0 = cur[0] + 1, c1 = cur[1];
             ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
             ye[s] = c0 < c1 ? segs[c0].ye : 0x7fffffff;
             __syncwarp();
-            if (lane == 0) cursor[slot * 4] = c0;
+            if (lane == 0) cur[0] = c0;
           }
-        } else if (lane == 0) {
-          rec[buf * kExpSlots + slot] = make_int4(0, 0, 0, 0);
         }
       }
+      if (lane == 0) wmask[buf * kExpWarps + warp] = am;
       __syncthreads();
       // ---------------------------------------------------------------- phase 2: x-pass per chunk
       const int4* rb = rec + buf * kExpSlots;
       const float* t1b = t1all + (size_t)buf * kExpSlots * 8 * kT1x;
       float* rowp = psi + ((size_t)z * Ny + y) * rowstride;
+      unsigned long long act = 0ull;  // active slots of the row, bit = slot
+#pragma unroll
+      for (int w = 0; w < kExpWarps; w++) act |= (unsigned long long)wmask[buf * kExpWarps + w] << (w * S);
       for (int ch = warp; ch < nchunk; ch += kExpWarps) {
         const int c0x = ch * kExpChunk;
-        // does any active slot meet this chunk?
-        bool any = false;
-        for (int sl = 0; sl < kExpSlots && !any; sl++) {
-          const int4 r = rb[sl];
-          if (!r.x) continue;
-          if (g.periodic) {
-            int d1 = c0x - r.y, d2 = r.y - c0x;
-            d1 %= Nx;
-            if (d1 < 0) d1 += Nx;
-            d2 %= Nx;
-            if (d2 < 0) d2 += Nx;
-            any = d1 < C || d2 < kExpChunk;
-          } else {
-            any = r.y < c0x + kExpChunk && r.y + C > c0x;
-          }
+        // slots whose cube meets this chunk, in slot order
+        unsigned long long mine = 0ull;
+        for (unsigned long long a = act; a; a &= a - 1) {
+          const int sl = __ffsll((long long)a) - 1;
+          if ((rb[sl].x >> ch) & 1) mine |= 1ull << sl;
         }
-        if (!any) continue;
+        if (!mine) continue;
         if constexpr (TC) {
           // D[band][x] tiles: j = x tile (8 points), m = band tile; lane holds bands 4g..4g+3 of
           // x = c0x + 8j + 2t (+1): e = 0 / 1 of tile m are bands 4g + 2m, 4g + 2m + 1
@@ -715,37 +716,33 @@ __global__ void __launch_bounds__(kExpThreads, 1)
               d[j][1][h2] = v.z;
               d[j][1][2 + h2] = v.w;
             }
-          for (int sl = 0; sl < kExpSlots; sl++) {
+          for (unsigned long long a = mine; a; a &= a - 1) {
+            const int sl = __ffsll((long long)a) - 1;
             const int4 r = rb[sl];
-            if (!r.x) continue;
             const float* ts = t1b + (size_t)sl * 8 * kT1x;
             const float* xs = tabs + (size_t)sl * kExpTabFloats + r.z * kPlaneMaxCube * 8;
             // A = T1[band][n], rows of tile m: bands 4g + 2m (row g) and 4g + 2m + 1 (row g + 8)
             float av[2][NA];
-            {
-              if constexpr (NA == 4) {
-                const float4 lo = *reinterpret_cast<const float4*>(ts + tq * kT1x + 4 * gq);
-                const float4 hi = *reinterpret_cast<const float4*>(ts + (tq + 4) * kT1x + 4 * gq);
-                av[0][0] = lo.x; av[0][1] = lo.y; av[0][2] = hi.x; av[0][3] = hi.y;
-                av[1][0] = lo.z; av[1][1] = lo.w; av[1][2] = hi.z; av[1][3] = hi.w;
-              } else {
-                const float4 k0 = *reinterpret_cast<const float4*>(ts + (2 * tq) * kT1x + 4 * gq);
-                const float4 k1 = *reinterpret_cast<const float4*>(ts + (2 * tq + 1) * kT1x + 4 * gq);
-                av[0][0] = k0.x; av[0][1] = k1.x; av[0][2] = k0.y; av[0][3] = k1.y;
-                av[1][0] = k0.z; av[1][1] = k1.z; av[1][2] = k0.w; av[1][3] = k1.w;
+            if constexpr (NA == 4) {
+              const float4 lo = *reinterpret_cast<const float4*>(ts + tq * kT1x + 4 * gq);
+              const float4 hi = *reinterpret_cast<const float4*>(ts + (tq + 4) * kT1x + 4 * gq);
+              av[0][0] = lo.x; av[0][1] = lo.y; av[0][2] = hi.x; av[0][3] = hi.y;
+              av[1][0] = lo.z; av[1][1] = lo.w; av[1][2] = hi.z; av[1][3] = hi.w;
+            } else {
+              const float4 k0 = *reinterpret_cast<const float4*>(ts + (2 * tq) * kT1x + 4 * gq);
+              const float4 k1 = *reinterpret_cast<const float4*>(ts + (2 * tq + 1) * kT1x + 4 * gq);
+              av[0][0] = k0.x; av[0][1] = k1.x; av[0][2] = k0.y; av[0][3] = k1.y;
+              av[1][0] = k0.z; av[1][1] = k1.z; av[1][2] = k0.w; av[1][3] = k1.w;
 #pragma unroll
-                for (int i = 4; i < NA; i++) av[0][i] = av[1][i] = 0.0f;  // states 8..15 do not exist
-              }
+              for (int i = 4; i < NA; i++) av[0][i] = av[1][i] = 0.0f;  // states 8..15 do not exist
             }
 #pragma unroll
             for (int j = 0; j < 2; j++) {
               // B[n][x] = phi_n(x - x0) at x = c0x + 8j + g (zero outside the cube)
-              int ix = c0x + 8 * j + gq - r.y;
-              if (g.periodic) {
-                ix %= Nx;
-                if (ix < 0) ix += Nx;
-              }
-              const bool in = ix >= 0 && ix < C && c0x + 8 * j + gq < Nx;
+              const int x = c0x + 8 * j + gq;
+              int ix = x - r.y;
+              if (g.periodic && ix < 0) ix += Nx;
+              const bool in = ix >= 0 && ix < C && x < Nx;
               float bv[NB];
               if constexpr (NB == 2) {
                 bv[0] = in ? xs[ix * 8 + tq] : 0.0f;
@@ -782,21 +779,19 @@ __global__ void __launch_bounds__(kExpThreads, 1)
 #pragma unroll
           for (int x = 0; x < kExpChunk; x++)
             acc[x] = (c0x + x < Nx && bok) ? ldg_cg(rowp + (size_t)(c0x + x) * B + b) : 0.0f;
-          for (int sl = 0; sl < kExpSlots; sl++) {
+          for (unsigned long long a = mine; a; a &= a - 1) {
+            const int sl = __ffsll((long long)a) - 1;
             const int4 r = rb[sl];
-            if (!r.x) continue;
             const float* ts = t1b + (size_t)sl * 8 * kT1x;
             const float* xs = tabs + (size_t)sl * kExpTabFloats + r.z * kPlaneMaxCube * 8;
             float t1[NP];
 #pragma unroll
             for (int n = 0; n < NP; n++) t1[n] = ts[n * kT1x + lane];
+            const int ix0 = c0x - r.y;  // in (-Nx, Nx); ix0 + x needs one wrap at most when periodic
 #pragma unroll
             for (int x = 0; x < kExpChunk; x++) {
-              int ix = c0x + x - r.y;
-              if (g.periodic) {
-                ix %= Nx;
-                if (ix < 0) ix += Nx;
-              }
+              int ix = ix0 + x;
+              if (g.periodic) ix = ix < 0 ? ix + Nx : (ix >= Nx ? ix - Nx : ix);
               if (ix >= 0 && ix < C) {
                 const float4 f0 = *reinterpret_cast<const float4*>(xs + ix * 8);
                 const float4 f1 = *reinterpret_cast<const float4*>(xs + ix * 8 + 4);
