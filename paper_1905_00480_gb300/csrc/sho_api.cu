@@ -314,7 +314,8 @@ int expand_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev
   const size_t o_segs = cv.take(std::max<size_t>(1, plan.segs.size()) * sizeof(PlaneSeg));
   const size_t o_xt = cv.take(A * cube * 8 * sizeof(float));
   const size_t o_yt = cv.take(A * cube * 8 * sizeof(float));
-  const size_t o_zt = cv.take(A * cube * 8 * sizeof(float));
+  const size_t o_zt = cv.take(A * 2 * 8 * cube * sizeof(float));
+  const size_t o_t2 = cv.take(A * cube * (size_t)npairs(numax) * nbands * sizeof(float));
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), A * sizeof(AtomDev), s));
@@ -336,7 +337,7 @@ int expand_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev
   L.xtab = reinterpret_cast<float*>(ws + o_xt);
   L.ytab = reinterpret_cast<float*>(ws + o_yt);
   L.bfrag = nullptr;
-  L.t2p = nullptr;
+  L.t2p = reinterpret_cast<float*>(ws + o_t2);
   L.coeff = const_cast<float*>(coeff);
   L.status = h->dstatus;
   L.stream = s;
@@ -375,7 +376,7 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
       cv.take((segs + grid->n[2]) * sizeof(int4));
       cv.take(((segs + grid->n[2]) * 36 + 1) * sizeof(int));
       cv.take(segs * sizeof(PlaneSeg));
-      cv.take(3 * (size_t)natoms * cube * 8 * sizeof(float));
+      cv.take(4 * (size_t)natoms * cube * 8 * sizeof(float));
     }
     cv.take(((size_t)grid->n[2] + 1) * sizeof(int));
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));

@@ -558,10 +558,10 @@ template <int NU, int MODE>
 __global__ void __launch_bounds__(kExpThreads, 1)
     k_expand_plane(GridDev g, const int4* __restrict__ items, const int* __restrict__ plane_items,
                    const int* __restrict__ slot_ptr, const PlaneSeg* __restrict__ segs,
-                   const float* __restrict__ xtab, const float* __restrict__ ytab, const float* __restrict__ ztab,
-                   const float* __restrict__ coeff, int nbt, float* psi) {
+                   const float* __restrict__ xtab, const float* __restrict__ ytab, const float* __restrict__ t2g,
+                   int nbt, float* psi) {
   using BS = Basis<NU>;
-  constexpr int NP = BS::NP, P = BS::P, N = BS::N;
+  constexpr int NP = BS::NP, P = BS::P;
   constexpr int S = kPlaneSlots;
   constexpr bool TC = MODE != kSimtMode;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
@@ -635,23 +635,10 @@ __global__ void __launch_bounds__(kExpThreads, 1)
             if (g.periodic && x >= Nx) x -= Nx;
             const unsigned bit = (lane < C && x >= 0 && x < Nx) ? (1u << (x / kExpChunk)) : 0u;
             const unsigned cm = __reduce_or_sync(0xffffffffu, bit);
-            const float4* zt = reinterpret_cast<const float4*>(ztab + ((size_t)sg.atom * C + sg.iz) * 8);
-            const float4 z0 = __ldg(zt), z1 = __ldg(zt + 1);
-            const float wz[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+            // z-pass result of this (atom, plane), written by k_expand_zpass: 32 independent loads
+            const float* tg = t2g + ((size_t)sg.atom * C + sg.iz) * P * B + b;
 #pragma unroll
-            for (int p = 0; p < P; p++) t2[s][p] = 0.0f;
-            const float* ca = coeff + (size_t)sg.atom * N * B + b;
-            int k = 0;
-#pragma unroll
-            for (int nz = 0; nz < NP; nz++)
-#pragma unroll
-              for (int ny = 0; ny + nz <= NU; ny++)
-#pragma unroll
-                for (int nx = 0; nx + ny + nz <= NU; nx++) {
-                  const float cv = bok ? __ldg(ca + (size_t)k * B) : 0.0f;
-                  t2[s][BS::pair(nx, ny)] = fmaf(cv, wz[nz], t2[s][BS::pair(nx, ny)]);
-                  k++;
-                }
+            for (int p = 0; p < P; p++) t2[s][p] = bok ? __ldg(tg + (size_t)p * B) : 0.0f;
             if (lane == 0) {
               cur[2] = sg.x0;
               cur[3] = sg.iy0 - sg.ys;
@@ -703,19 +690,23 @@ __global__ void __launch_bounds__(kExpThreads, 1)
         if constexpr (TC) {
           // D[band][x] tiles: j = x tile (8 points), m = band tile; lane holds bands 4g..4g+3 of
           // x = c0x + 8j + 2t (+1): e = 0 / 1 of tile m are bands 4g + 2m, 4g + 2m + 1
-          float d[2][2][4];
+          // psi of the chunk is loaded first and added at the end, so its DRAM latency overlaps the
+          // products (accumulated from zero in d)
+          float4 pv[2][2];
 #pragma unroll
           for (int j = 0; j < 2; j++)
 #pragma unroll
             for (int h2 = 0; h2 < 2; h2++) {
               const int x = c0x + 8 * j + 2 * tq + h2;
-              float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (x < Nx && gok) v = ldg_cg4(rowp + (size_t)x * B + b0 + 4 * gq);
-              d[j][0][h2] = v.x;
-              d[j][0][2 + h2] = v.y;
-              d[j][1][h2] = v.z;
-              d[j][1][2 + h2] = v.w;
+              pv[j][h2] = (x < Nx && gok) ? ldg_cg4(rowp + (size_t)x * B + b0 + 4 * gq) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+          float d[2][2][4];
+#pragma unroll
+          for (int j = 0; j < 2; j++)
+#pragma unroll
+            for (int m = 0; m < 2; m++)
+#pragma unroll
+              for (int e = 0; e < 4; e++) d[j][m][e] = 0.0f;
           for (unsigned long long a = mine; a; a &= a - 1) {
             const int sl = __ffsll((long long)a) - 1;
             const int4 r = rb[sl];
@@ -772,7 +763,8 @@ __global__ void __launch_bounds__(kExpThreads, 1)
               const int x = c0x + 8 * j + 2 * tq + h2;
               if (x < Nx && gok)
                 *reinterpret_cast<float4*>(rowp + (size_t)x * B + b0 + 4 * gq) =
-                    make_float4(d[j][0][h2], d[j][0][2 + h2], d[j][1][h2], d[j][1][2 + h2]);
+                    make_float4(pv[j][h2].x + d[j][0][h2], pv[j][h2].y + d[j][0][2 + h2], pv[j][h2].z + d[j][1][h2],
+                                pv[j][h2].w + d[j][1][2 + h2]);
             }
         } else {
           float acc[kExpChunk];
@@ -873,15 +865,27 @@ cudaError_t plane_run(const PlaneLaunch& p) {
 template <int NU, int MODE>
 cudaError_t plane_expand_run(const PlaneLaunch& p) {
   const int A = p.natoms, nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, p.ztab, nullptr);
+  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, nullptr, nullptr);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ExpandLaunch z{};
+  z.g = p.g;
+  z.coeff = p.coeff;
+  z.coeff_dtype = SHO_F32;
+  z.atoms = p.atoms;
+  z.natoms = A;
+  z.numax = p.numax;
+  z.tables = p.ztab;  // [A][2][NP][C] scratch of the z-pass kernel (x and y tables, unused here)
+  z.t2 = p.t2p;
+  z.stream = p.stream;
+  e = launch_expand_zpass_f32(z);
   if (e != cudaSuccess) return e;
   if (p.nitems == 0) return cudaSuccess;
   auto kern = k_expand_plane<NU, MODE>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ExpSmem::bytes);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)p.g.n[2] * nbt, kExpThreads, ExpSmem::bytes, p.stream>>>(
-      p.g, p.items, p.plane_items, p.slot_ptr, p.segs, p.xtab, p.ytab, p.ztab, p.coeff, nbt, p.psi_rw);
+      p.g, p.items, p.plane_items, p.slot_ptr, p.segs, p.xtab, p.ytab, p.t2p, nbt, p.psi_rw);
   return cudaGetLastError();
 }
 
