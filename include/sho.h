@@ -145,9 +145,8 @@ int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype,
 /*
  * Expansion -- step (3) of the non-local action (Sec. 3.2), the adjoint of the projection:
  *     psi[j][b] += sum_a sum_{i: j(i) = j} sum_k coeff[a][k][b] * Psi_k(u_i)      (no h^3 factor)
- * so that <P psi, c> = h^3 <psi, E c>.  Evaluated z-pass, y-pass, x-pass.  Every covered grid row
- * is read and written once per sweep and the atoms of a grid point are added in an order fixed by the
- * call's arguments (no atomics): the result is deterministic, bit for bit.
+ * so that <P psi, c> = h^3 <psi, E c>.  Evaluated z-pass, y-pass, x-pass.  Every grid row is
+ * read and written once, atoms are added in ascending index order: the result is deterministic.
  *   coeff  device [natoms][sho_nstates(numax)][nbands], type coeff_dtype (read only)
  *   psi    device [n[2]][n[1]][n[0]][nbands], type psi_dtype (read-modify-write)
  * Same dtype / precision combinations as sho_project.

@@ -256,7 +256,7 @@ GridDev make_grid(const sho_grid* grid, int cube, int nbands) {
 int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const float* psi,
                    int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
   PlanePlan plan;
-  plan_planes(grid, at, cube, kPlaneProjectWarps, plan);
+  plan_planes(grid, at, cube, plan);
   const size_t A = at.size();
   Carve cv;
   const size_t o_atoms = cv.take(A * sizeof(AtomDev));
@@ -295,59 +295,6 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
   return end_call(h, s);
 }
 
-// Plane-sweep expansion (FP32 psi, FP32 coefficients): the same row-segment plan for the expansion's
-// warps; tables, then one sweep kernel that reads and writes every covered row once.
-int expand_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const float* coeff,
-                  int nbands, int numax, int cube, sho_prec prec, float* psi, cudaStream_t s) {
-  PlanePlan plan;
-  plan_planes(grid, at, cube, kPlaneExpandWarps, plan);
-  const int nz = grid->n[2];
-  std::vector<int> pitems((size_t)nz + 1, 0);
-  for (const int4& it : plan.items) pitems[(size_t)it.x + 1]++;
-  for (int z = 0; z < nz; z++) pitems[(size_t)z + 1] += pitems[(size_t)z];
-  const size_t A = at.size();
-  Carve cv;
-  const size_t o_atoms = cv.take(A * sizeof(AtomDev));
-  const size_t o_items = cv.take(std::max<size_t>(1, plan.items.size()) * sizeof(int4));
-  const size_t o_pitems = cv.take(pitems.size() * sizeof(int));
-  const size_t o_ptr = cv.take(plan.slot_ptr.size() * sizeof(int));
-  const size_t o_segs = cv.take(std::max<size_t>(1, plan.segs.size()) * sizeof(PlaneSeg));
-  const size_t o_xt = cv.take(A * cube * 8 * sizeof(float));
-  const size_t o_yt = cv.take(A * cube * 8 * sizeof(float));
-  const size_t o_zt = cv.take(A * 2 * 8 * cube * sizeof(float));
-  const size_t o_t2 = cv.take(A * cube * (size_t)npairs(numax) * nbands * sizeof(float));
-  SHO_TRY(begin_call(h, s));
-  SHO_TRY(ensure_workspace(h, cv.off));
-  SHO_TRY(upload(h, o_atoms, at.data(), A * sizeof(AtomDev), s));
-  SHO_TRY(upload(h, o_items, plan.items.data(), plan.items.size() * sizeof(int4), s));
-  SHO_TRY(upload(h, o_pitems, pitems.data(), pitems.size() * sizeof(int), s));
-  SHO_TRY(upload(h, o_ptr, plan.slot_ptr.data(), plan.slot_ptr.size() * sizeof(int), s));
-  SHO_TRY(upload(h, o_segs, plan.segs.data(), plan.segs.size() * sizeof(PlaneSeg), s));
-  char* ws = static_cast<char*>(h->ws);
-  PlaneLaunch L;
-  L.g = make_grid(grid, cube, nbands);
-  L.psi = psi;
-  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
-  L.natoms = (int)A;
-  L.numax = numax;
-  L.items = reinterpret_cast<const int4*>(ws + o_items);
-  L.nitems = (int)plan.items.size();
-  L.slot_ptr = reinterpret_cast<const int*>(ws + o_ptr);
-  L.segs = reinterpret_cast<const PlaneSeg*>(ws + o_segs);
-  L.xtab = reinterpret_cast<float*>(ws + o_xt);
-  L.ytab = reinterpret_cast<float*>(ws + o_yt);
-  L.bfrag = nullptr;
-  L.t2p = reinterpret_cast<float*>(ws + o_t2);
-  L.coeff = const_cast<float*>(coeff);
-  L.status = h->dstatus;
-  L.stream = s;
-  L.plane_items = reinterpret_cast<const int*>(ws + o_pitems);
-  L.ztab = reinterpret_cast<float*>(ws + o_zt);
-  L.psi_rw = psi;
-  if (launch_expand_plane(L, prec) != cudaSuccess) return SHO_ERR_CUDA;
-  return end_call(h, s);
-}
-
 }  // namespace
 
 // Workspace a call needs (an upper bound: the per-plane lists are counted as natoms * cube entries).
@@ -370,14 +317,6 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
     }
   }
   if (op == SHO_OP_EXPAND) {
-    if (coeff_dtype == SHO_F32 && numax <= kTcMaxNumax) {
-      // plane-sweep plan (upper bound as for the projection)
-      const size_t segs = 2 * (size_t)natoms * cube + 1;
-      cv.take((segs + grid->n[2]) * sizeof(int4));
-      cv.take(((segs + grid->n[2]) * 36 + 1) * sizeof(int));
-      cv.take(segs * sizeof(PlaneSeg));
-      cv.take(4 * (size_t)natoms * cube * 8 * sizeof(float));
-    }
     cv.take(((size_t)grid->n[2] + 1) * sizeof(int));
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
     cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
@@ -640,9 +579,6 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
-  if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec))
-    return expand_planes(h, grid, at, static_cast<const float*>(coeff), nbands, numax, cube, prec,
-                         static_cast<float*>(psi), s);
   std::vector<int> ptr, list;
   plane_lists(grid, at, cube, ptr, list);
   const size_t tc = compute_size(coeff_dtype);

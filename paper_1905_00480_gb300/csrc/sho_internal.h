@@ -125,21 +125,14 @@ struct PlaneLaunch {
   float* ytab;               // [A][C][8]
   uint32_t* bfrag;           // [A][32][kMaxCube / 8][4]
   float* t2p;                // [A][C][P][B]
-  float* coeff;              // [A][N][B] (projection: written; expansion: read)
+  float* coeff;              // [A][N][B]
   int* status;               // device word, bit 0 = a bounded wait expired
   cudaStream_t stream;
-  // expansion only
-  const int* plane_items = nullptr;  // [Nz + 1]: items of plane z are plane_items[z] .. plane_items[z+1]
-  float* ztab = nullptr;             // [A][C][8]
-  float* psi_rw = nullptr;           // psi, read-modify-write
 };
 bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nbands, int numax, int cube,
               sho_prec prec);
-void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, int warps, PlanePlan& plan);
+void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, PlanePlan& plan);
 cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec);
-cudaError_t launch_expand_plane(const PlaneLaunch& p, sho_prec prec);
-constexpr int kPlaneProjectWarps = 11;  // consumer warps of the projection sweep
-constexpr int kPlaneExpandWarps = 12;   // warps of the expansion sweep
 constexpr size_t kPlaneBfragBytesPerAtom = 32 * (kMaxCube / 8) * 4 * sizeof(uint32_t);
 
 // Cartesian <-> radial transform (sho_radial.cu): labels and U on the host, CSR rows for the kernel.

@@ -36,7 +36,7 @@
 
 namespace sho {
 
-constexpr int kPlaneWarps = kPlaneProjectWarps;        // consumer warps per CTA (+ 1 producer: 384 threads, 168 registers)
+constexpr int kPlaneWarps = 11;                        // consumer warps per CTA (+ 1 producer: 384 threads, 168 registers)
 constexpr int kPlaneSlots = 3;                         // y-pass accumulator slots per warp
 constexpr int kPlaneThreads = (kPlaneWarps + 1) * 32;  // + the producer warp
 constexpr int kPlaneMaxStages = 8;
@@ -111,7 +111,7 @@ __device__ __forceinline__ int plane_x(int x0, int i, int nx, int periodic) {
 template <int NU, int MODE>
 __global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev* __restrict__ atoms,
                                                         float* __restrict__ xtab, float* __restrict__ ytab,
-                                                        float* __restrict__ ztab, uint32_t* __restrict__ bfrag) {
+                                                        uint32_t* __restrict__ bfrag) {
   constexpr int NP = NU + 1;
   __shared__ float xs[kMaxCube][8];
   const int a = blockIdx.x, lane = threadIdx.x, C = g.cube;
@@ -129,13 +129,7 @@ __global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev
     phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, col, 1);
 #pragma unroll
     for (int n = 0; n < 8; n++) ytab[((size_t)a * C + i) * 8 + n] = n < NP ? (float)col[n] : 0.0f;
-    if (ztab) {
-      phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, col, 1);
-#pragma unroll
-      for (int n = 0; n < 8; n++) ztab[((size_t)a * C + i) * 8 + n] = n < NP ? (float)col[n] : 0.0f;
-    }
   }
-  if (bfrag == nullptr) return;
   __syncwarp();
   if constexpr (MODE != kSimtMode) {
     constexpr TcMode TM = (TcMode)MODE;
@@ -515,296 +509,6 @@ __global__ void __launch_bounds__(kWarp) k_plane_zpass(GridDev g, const AtomDev*
   }
 }
 
-// --------------------------------------------------------------------------------- expansion sweep
-// The adjoint of the plane sweep (Sec. 3.2 step 3, passes z -> y -> x).  CTA per (plane z, 32 bands),
-// all sweeps (rounds) of the plane in turn.  Per row:
-//   phase 1  slot owners: T1_a[nx][b] = sum_ny T2_a[(nx,ny)][b] phi_ny(iy), with T2_a of this plane held
-//            in the slot's registers (z-pass from the coefficients when the segment starts), written to
-//            a double-buffered shared area together with the slot's x offset;
-//   phase 2  after one barrier of the 12 warps, warp w owns the 16-point x chunks w, w + 12, ...: it
-//            loads psi of its chunk once, adds the x-pass of every slot whose cube meets the chunk in
-//            slot order (mma.sync tiles, D = psi), and stores the chunk.
-// Every psi element of a row is read and written once per sweep; the summation order is fixed by the
-// plan, so results are reproducible bit for bit.
-constexpr int kExpWarps = kPlaneExpandWarps;
-constexpr int kExpThreads = kExpWarps * 32;
-constexpr int kExpSlots = kExpWarps * kPlaneSlots;
-constexpr int kExpChunk = 16;
-constexpr int kT1x = 40;  // padded stride (floats) of a T1 row [n][band]: conflict-free A loads
-
-// Per slot: two x tables (segments alternate between them: phase 2 of other warps may still read the
-// previous segment's table in the row after it ended) and one y table (read by the owner only).
-constexpr int kExpTabFloats = 3 * kPlaneMaxCube * 8;
-
-struct ExpSmem {
-  static constexpr size_t tables = (size_t)kExpSlots * kExpTabFloats * 4;          // x, x', y tables
-  static constexpr size_t t1 = (size_t)2 * kExpSlots * 8 * kT1x * 4;               // T1, two buffers
-  static constexpr size_t recs = (size_t)2 * kExpSlots * 16 + (size_t)kExpSlots * 32 + 2 * kExpWarps * 4;
-  static constexpr size_t bytes = tables + t1 + recs;
-};
-
-__device__ __forceinline__ float4 ldg_cg4(const float* p) {
-  float4 v;
-  asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ float ldg_cg(const float* p) {
-  float v;
-  asm volatile("ld.global.cg.f32 %0, [%1];\n" : "=f"(v) : "l"(p));
-  return v;
-}
-
-template <int NU, int MODE>
-__global__ void __launch_bounds__(kExpThreads, 1)
-    k_expand_plane(GridDev g, const int4* __restrict__ items, const int* __restrict__ plane_items,
-                   const int* __restrict__ slot_ptr, const PlaneSeg* __restrict__ segs,
-                   const float* __restrict__ xtab, const float* __restrict__ ytab, const float* __restrict__ t2g,
-                   int nbt, float* psi) {
-  using BS = Basis<NU>;
-  constexpr int NP = BS::NP, P = BS::P;
-  constexpr int S = kPlaneSlots;
-  constexpr bool TC = MODE != kSimtMode;
-  constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
-  constexpr int NA = TcFrag<TM>::NA, NB = TcFrag<TM>::NB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* tabs = reinterpret_cast<float*>(smem_raw);                                   // [slot][x|x'|y][C][8]
-  float* t1all = reinterpret_cast<float*>(smem_raw + ExpSmem::tables);                // [buf][slot][8][kT1x]
-  int4* rec = reinterpret_cast<int4*>(smem_raw + ExpSmem::tables + ExpSmem::t1);      // [buf][slot]
-  // per slot: current segment, end of the slot's list, x0, iy - y, chunk mask of the current segment
-  int* cursor = reinterpret_cast<int*>(rec + 2 * kExpSlots);                          // [slot][8]
-  int* wmask = cursor + kExpSlots * 8;                                                 // [buf][warp]
-  const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-  const int z = (int)blockIdx.x / nbt, bt = (int)blockIdx.x - z * nbt;
-  const int b0 = bt * kWarp, b = b0 + lane;
-  const bool bok = b < B;
-  const bool gok = b0 + 4 * gq < B;  // bands 4g..4g+3 (B % 4 == 0)
-  const int nchunk = (Nx + kExpChunk - 1) / kExpChunk;
-  const size_t rowstride = (size_t)Nx * B;
-
-  for (int it = plane_items[z]; it < plane_items[z + 1]; it++) {
-    const int4 item = items[it];
-    const int ylo = item.y, yhi = item.z;
-    int ys[S], ye[S];
-#pragma unroll
-    for (int s = 0; s < S; s++) {
-      const int c0 = slot_ptr[item.w + warp * S + s], c1 = slot_ptr[item.w + warp * S + s + 1];
-      ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
-      ye[s] = c0 < c1 ? segs[c0].ye : 0x7fffffff;
-      if (lane == 0) {
-        cursor[(warp * S + s) * 8 + 0] = c0;
-        cursor[(warp * S + s) * 8 + 1] = c1;
-      }
-    }
-    __syncwarp();
-    float t2[S][P];
-#pragma unroll
-    for (int s = 0; s < S; s++)
-#pragma unroll
-      for (int p = 0; p < P; p++) t2[s][p] = 0.0f;
-
-    for (int y = ylo; y < yhi; y++) {
-      const int buf = (y - ylo) & 1;
-      // ---------------------------------------------------------------- phase 1: y-pass per slot
-      int am = 0;  // slots of this warp active in this row
-#pragma unroll
-      for (int s = 0; s < S; s++) {
-        const int slot = warp * S + s;
-        int* cur = cursor + slot * 8;
-        float* tsl = tabs + (size_t)slot * kExpTabFloats;          // x tables [2][C][8], y table [C][8]
-        float* tyt = tsl + 2 * kPlaneMaxCube * 8;
-        float* t1w = t1all + ((size_t)buf * kExpSlots + slot) * 8 * kT1x;
-        if (ys[s] <= y) {
-          am |= 1 << s;
-          if (y == ys[s]) {
-            // segment start: tables into the slot area, z-pass of this plane into registers, and the
-            // row chunks the cube meets (lane i: cube point i)
-            const int cseg = cur[0];
-            const PlaneSeg sg = segs[cseg];
-            if (lane < C) {
-              const float4* sx = reinterpret_cast<const float4*>(xtab + ((size_t)sg.atom * C + lane) * 8);
-              const float4* sy = reinterpret_cast<const float4*>(ytab + ((size_t)sg.atom * C + lane) * 8);
-              float4* dx = reinterpret_cast<float4*>(tsl + (cseg & 1) * kPlaneMaxCube * 8 + lane * 8);
-              float4* dy = reinterpret_cast<float4*>(tyt + lane * 8);
-              dx[0] = __ldg(sx);
-              dx[1] = __ldg(sx + 1);
-              dy[0] = __ldg(sy);
-              dy[1] = __ldg(sy + 1);
-            }
-            int x = sg.x0 + lane;
-            if (g.periodic && x >= Nx) x -= Nx;
-            const unsigned bit = (lane < C && x >= 0 && x < Nx) ? (1u << (x / kExpChunk)) : 0u;
-            const unsigned cm = __reduce_or_sync(0xffffffffu, bit);
-            // z-pass result of this (atom, plane), written by k_expand_zpass: 32 independent loads
-            const float* tg = t2g + ((size_t)sg.atom * C + sg.iz) * P * B + b;
-#pragma unroll
-            for (int p = 0; p < P; p++) t2[s][p] = bok ? __ldg(tg + (size_t)p * B) : 0.0f;
-            if (lane == 0) {
-              cur[2] = sg.x0;
-              cur[3] = sg.iy0 - sg.ys;
-              cur[4] = (int)cm;
-            }
-            __syncwarp();
-          }
-          const int iy = y + cur[3];
-          const float4* yt = reinterpret_cast<const float4*>(tyt + iy * 8);
-          const float4 y0 = yt[0], y1 = yt[1];
-          const float wy[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
-#pragma unroll
-          for (int nx = 0; nx < NP; nx++) {
-            float v = 0.0f;
-#pragma unroll
-            for (int ny = 0; nx + ny <= NU; ny++) v = fmaf(t2[s][BS::pair(nx, ny)], wy[ny], v);
-            t1w[nx * kT1x + lane] = v;
-          }
-#pragma unroll
-          for (int nx = NP; nx < 8; nx++) t1w[nx * kT1x + lane] = 0.0f;
-          if (lane == 0) rec[buf * kExpSlots + slot] = make_int4(cur[4], cur[2], cur[0] & 1, 0);
-          if (y == ye[s] - 1) {
-            const int c0 = cur[0] + 1, c1 = cur[1];
-            ys[s] = c0 < c1 ? segs[c0].ys : 0x7fffffff;
-            ye[s] = c0 < c1 ? segs[c0].ye : 0x7fffffff;
-            __syncwarp();
-            if (lane == 0) cur[0] = c0;
-          }
-        }
-      }
-      if (lane == 0) wmask[buf * kExpWarps + warp] = am;
-      __syncthreads();
-      // ---------------------------------------------------------------- phase 2: x-pass per chunk
-      const int4* rb = rec + buf * kExpSlots;
-      const float* t1b = t1all + (size_t)buf * kExpSlots * 8 * kT1x;
-      float* rowp = psi + ((size_t)z * Ny + y) * rowstride;
-      unsigned long long act = 0ull;  // active slots of the row, bit = slot
-#pragma unroll
-      for (int w = 0; w < kExpWarps; w++) act |= (unsigned long long)wmask[buf * kExpWarps + w] << (w * S);
-      for (int ch = warp; ch < nchunk; ch += kExpWarps) {
-        const int c0x = ch * kExpChunk;
-        // slots whose cube meets this chunk, in slot order
-        unsigned long long mine = 0ull;
-        for (unsigned long long a = act; a; a &= a - 1) {
-          const int sl = __ffsll((long long)a) - 1;
-          if ((rb[sl].x >> ch) & 1) mine |= 1ull << sl;
-        }
-        if (!mine) continue;
-        if constexpr (TC) {
-          // D[band][x] tiles: j = x tile (8 points), m = band tile; lane holds bands 4g..4g+3 of
-          // x = c0x + 8j + 2t (+1): e = 0 / 1 of tile m are bands 4g + 2m, 4g + 2m + 1
-          // psi of the chunk is loaded first and added at the end, so its DRAM latency overlaps the
-          // products (accumulated from zero in d)
-          float4 pv[2][2];
-#pragma unroll
-          for (int j = 0; j < 2; j++)
-#pragma unroll
-            for (int h2 = 0; h2 < 2; h2++) {
-              const int x = c0x + 8 * j + 2 * tq + h2;
-              pv[j][h2] = (x < Nx && gok) ? ldg_cg4(rowp + (size_t)x * B + b0 + 4 * gq) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-          float d[2][2][4];
-#pragma unroll
-          for (int j = 0; j < 2; j++)
-#pragma unroll
-            for (int m = 0; m < 2; m++)
-#pragma unroll
-              for (int e = 0; e < 4; e++) d[j][m][e] = 0.0f;
-          for (unsigned long long a = mine; a; a &= a - 1) {
-            const int sl = __ffsll((long long)a) - 1;
-            const int4 r = rb[sl];
-            const float* ts = t1b + (size_t)sl * 8 * kT1x;
-            const float* xs = tabs + (size_t)sl * kExpTabFloats + r.z * kPlaneMaxCube * 8;
-            // A = T1[band][n], rows of tile m: bands 4g + 2m (row g) and 4g + 2m + 1 (row g + 8)
-            float av[2][NA];
-            if constexpr (NA == 4) {
-              const float4 lo = *reinterpret_cast<const float4*>(ts + tq * kT1x + 4 * gq);
-              const float4 hi = *reinterpret_cast<const float4*>(ts + (tq + 4) * kT1x + 4 * gq);
-              av[0][0] = lo.x; av[0][1] = lo.y; av[0][2] = hi.x; av[0][3] = hi.y;
-              av[1][0] = lo.z; av[1][1] = lo.w; av[1][2] = hi.z; av[1][3] = hi.w;
-            } else {
-              const float4 k0 = *reinterpret_cast<const float4*>(ts + (2 * tq) * kT1x + 4 * gq);
-              const float4 k1 = *reinterpret_cast<const float4*>(ts + (2 * tq + 1) * kT1x + 4 * gq);
-              av[0][0] = k0.x; av[0][1] = k1.x; av[0][2] = k0.y; av[0][3] = k1.y;
-              av[1][0] = k0.z; av[1][1] = k1.z; av[1][2] = k0.w; av[1][3] = k1.w;
-#pragma unroll
-              for (int i = 4; i < NA; i++) av[0][i] = av[1][i] = 0.0f;  // states 8..15 do not exist
-            }
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-              // B[n][x] = phi_n(x - x0) at x = c0x + 8j + g (zero outside the cube)
-              const int x = c0x + 8 * j + gq;
-              int ix = x - r.y;
-              if (g.periodic && ix < 0) ix += Nx;
-              const bool in = ix >= 0 && ix < C && x < Nx;
-              float bv[NB];
-              if constexpr (NB == 2) {
-                bv[0] = in ? xs[ix * 8 + tq] : 0.0f;
-                bv[1] = in ? xs[ix * 8 + tq + 4] : 0.0f;
-              } else {
-                bv[0] = in ? xs[ix * 8 + 2 * tq] : 0.0f;
-                bv[1] = in ? xs[ix * 8 + 2 * tq + 1] : 0.0f;
-                bv[2] = bv[3] = 0.0f;
-              }
-              const BFrag<TM> bf = make_bfrag<TM>(bv);
-#pragma unroll
-              for (int m = 0; m < 2; m++) {
-                float dl[4] = {0.f, 0.f, 0.f, 0.f};
-                tc_product<TM>(d[j][m], dl, av[m], bf);
-                if constexpr (TM == TcMode::X3TF32 || TM == TcMode::SPLIT16) {
-                  const float ls = tc_lo_scale<TM>();
-#pragma unroll
-                  for (int e = 0; e < 4; e++) d[j][m][e] = fmaf(ls, dl[e], d[j][m][e]);
-                }
-              }
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 2; j++)
-#pragma unroll
-            for (int h2 = 0; h2 < 2; h2++) {
-              const int x = c0x + 8 * j + 2 * tq + h2;
-              if (x < Nx && gok)
-                *reinterpret_cast<float4*>(rowp + (size_t)x * B + b0 + 4 * gq) =
-                    make_float4(pv[j][h2].x + d[j][0][h2], pv[j][h2].y + d[j][0][2 + h2], pv[j][h2].z + d[j][1][h2],
-                                pv[j][h2].w + d[j][1][2 + h2]);
-            }
-        } else {
-          float acc[kExpChunk];
-#pragma unroll
-          for (int x = 0; x < kExpChunk; x++)
-            acc[x] = (c0x + x < Nx && bok) ? ldg_cg(rowp + (size_t)(c0x + x) * B + b) : 0.0f;
-          for (unsigned long long a = mine; a; a &= a - 1) {
-            const int sl = __ffsll((long long)a) - 1;
-            const int4 r = rb[sl];
-            const float* ts = t1b + (size_t)sl * 8 * kT1x;
-            const float* xs = tabs + (size_t)sl * kExpTabFloats + r.z * kPlaneMaxCube * 8;
-            float t1[NP];
-#pragma unroll
-            for (int n = 0; n < NP; n++) t1[n] = ts[n * kT1x + lane];
-            const int ix0 = c0x - r.y;  // in (-Nx, Nx); ix0 + x needs one wrap at most when periodic
-#pragma unroll
-            for (int x = 0; x < kExpChunk; x++) {
-              int ix = ix0 + x;
-              if (g.periodic) ix = ix < 0 ? ix + Nx : (ix >= Nx ? ix - Nx : ix);
-              if (ix >= 0 && ix < C) {
-                const float4 f0 = *reinterpret_cast<const float4*>(xs + ix * 8);
-                const float4 f1 = *reinterpret_cast<const float4*>(xs + ix * 8 + 4);
-                const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-                float sacc = acc[x];
-#pragma unroll
-                for (int n = 0; n < NP; n++) sacc = fmaf(t1[n], f[n], sacc);
-                acc[x] = sacc;
-              }
-            }
-          }
-#pragma unroll
-          for (int x = 0; x < kExpChunk; x++)
-            if (c0x + x < Nx && bok) rowp[(size_t)(c0x + x) * B + b] = acc[x];
-        }
-      }
-    }
-    __syncthreads();  // the next sweep of this plane reads rows this one wrote
-  }
-}
-
 // --------------------------------------------------------------------------------- host side
 namespace {
 
@@ -833,7 +537,7 @@ int plane_stages(int nx) {
 template <int NU, int MODE>
 cudaError_t plane_run(const PlaneLaunch& p) {
   const int A = p.natoms, nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, nullptr, p.bfrag);
+  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, p.bfrag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap map;
@@ -862,45 +566,14 @@ cudaError_t plane_run(const PlaneLaunch& p) {
   return cudaGetLastError();
 }
 
-template <int NU, int MODE>
-cudaError_t plane_expand_run(const PlaneLaunch& p) {
-  const int A = p.natoms, nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, nullptr, nullptr);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  ExpandLaunch z{};
-  z.g = p.g;
-  z.coeff = p.coeff;
-  z.coeff_dtype = SHO_F32;
-  z.atoms = p.atoms;
-  z.natoms = A;
-  z.numax = p.numax;
-  z.tables = p.ztab;  // [A][2][NP][C] scratch of the z-pass kernel (x and y tables, unused here)
-  z.t2 = p.t2p;
-  z.stream = p.stream;
-  e = launch_expand_zpass_f32(z);
-  if (e != cudaSuccess) return e;
-  if (p.nitems == 0) return cudaSuccess;
-  auto kern = k_expand_plane<NU, MODE>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ExpSmem::bytes);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)p.g.n[2] * nbt, kExpThreads, ExpSmem::bytes, p.stream>>>(
-      p.g, p.items, p.plane_items, p.slot_ptr, p.segs, p.xtab, p.ytab, p.t2p, nbt, p.psi_rw);
-  return cudaGetLastError();
-}
-
 template <int NU>
-cudaError_t plane_mode(const PlaneLaunch& p, sho_prec prec, bool expand) {
+cudaError_t plane_mode(const PlaneLaunch& p, sho_prec prec) {
   switch (prec) {
-    case SHO_P_FP32: return expand ? plane_expand_run<NU, kSimtMode>(p) : plane_run<NU, kSimtMode>(p);
-    case SHO_P_TF32:
-      return expand ? plane_expand_run<NU, (int)TcMode::TF32>(p) : plane_run<NU, (int)TcMode::TF32>(p);
-    case SHO_P_3XTF32:
-      return expand ? plane_expand_run<NU, (int)TcMode::X3TF32>(p) : plane_run<NU, (int)TcMode::X3TF32>(p);
-    case SHO_P_BF16:
-      return expand ? plane_expand_run<NU, (int)TcMode::BF16>(p) : plane_run<NU, (int)TcMode::BF16>(p);
-    case SHO_P_SPLIT_FP16:
-      return expand ? plane_expand_run<NU, (int)TcMode::SPLIT16>(p) : plane_run<NU, (int)TcMode::SPLIT16>(p);
+    case SHO_P_FP32: return plane_run<NU, kSimtMode>(p);
+    case SHO_P_TF32: return plane_run<NU, (int)TcMode::TF32>(p);
+    case SHO_P_3XTF32: return plane_run<NU, (int)TcMode::X3TF32>(p);
+    case SHO_P_BF16: return plane_run<NU, (int)TcMode::BF16>(p);
+    case SHO_P_SPLIT_FP16: return plane_run<NU, (int)TcMode::SPLIT16>(p);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -922,10 +595,10 @@ bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nband
 // head [s, Ny) in the same warp: the tail's partial T2 is written first and the head continues from
 // it, so each T2[a][iz] is written once complete.  Segments that find no free slot go to another
 // round (another CTA sweeping the same plane).
-void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, int warps, PlanePlan& plan) {
+void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, PlanePlan& plan) {
   const int nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
   const bool per = grid->periodic != 0;
-  const int W = warps, S = kPlaneSlots;
+  const int W = kPlaneWarps, S = kPlaneSlots;
   // A head segment starts ny - cube rows after its tail ended.  With at least kPlaneMaxStages rows in
   // between, the ring's barriers order the tail's T2 stores before the head's loads (the tail's warp
   // released the row buffer that the head's row later reused); otherwise both go to one warp, whose
@@ -1084,21 +757,18 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
   }
 }
 
-static cudaError_t plane_dispatch(const PlaneLaunch& p, sho_prec prec, bool expand) {
+cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec) {
   switch (p.numax) {
-    case 0: return plane_mode<0>(p, prec, expand);
-    case 1: return plane_mode<1>(p, prec, expand);
-    case 2: return plane_mode<2>(p, prec, expand);
-    case 3: return plane_mode<3>(p, prec, expand);
-    case 4: return plane_mode<4>(p, prec, expand);
-    case 5: return plane_mode<5>(p, prec, expand);
-    case 6: return plane_mode<6>(p, prec, expand);
-    case 7: return plane_mode<7>(p, prec, expand);
+    case 0: return plane_mode<0>(p, prec);
+    case 1: return plane_mode<1>(p, prec);
+    case 2: return plane_mode<2>(p, prec);
+    case 3: return plane_mode<3>(p, prec);
+    case 4: return plane_mode<4>(p, prec);
+    case 5: return plane_mode<5>(p, prec);
+    case 6: return plane_mode<6>(p, prec);
+    case 7: return plane_mode<7>(p, prec);
     default: return cudaErrorInvalidValue;
   }
 }
-
-cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec) { return plane_dispatch(p, prec, false); }
-cudaError_t launch_expand_plane(const PlaneLaunch& p, sho_prec prec) { return plane_dispatch(p, prec, true); }
 
 }  // namespace sho

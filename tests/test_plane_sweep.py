@@ -1,5 +1,5 @@
-"""Plane-sweep projection and expansion of the FP32-class forms (FP32 psi, numax <= 7) against the FP64
-oracle (GPU).
+"""Plane-sweep projection of the FP32-class forms (FP32 psi, numax <= 7) against the FP64 oracle (GPU),
+and the FP32-class expansion on the same geometries.
 
 The plane sweep assigns every (atom, plane) row segment to a register slot on the host; these cases
 drive its corners: more overlapping atoms per row than slots (several sweeps of one plane), wrapped
@@ -139,7 +139,7 @@ def _expand(grid, h, periodic, pos, sig, numax, cube, nbands, prec, seed):
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
 def test_expand_dense_atoms(prec):
-    """Planes swept more than once: the second sweep adds to rows the first one wrote."""
+    """Dense overlap: about 53 cubes meet each grid row."""
     require_gpu()
     rng = np.random.default_rng(611)
     grid, h, numax, cube = (48, 48, 48), 0.2, 3, 32
