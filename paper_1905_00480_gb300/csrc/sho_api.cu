@@ -25,6 +25,13 @@ struct sho_handle {
     void* mem = nullptr;
     int nnz = 0;
   } radial[SHO_MAX_NUMAX + 1][2];
+  // plane-sweep plan of the most recent geometry (atoms, items, slot lists, segments) on the device:
+  // repeated projections with the same atoms skip the host planning and the uploads
+  uint64_t plane_key = 0;
+  void* plane_mem = nullptr;
+  size_t plane_cap = 0;
+  int plane_nitems = 0;
+  size_t plane_off[4] = {0, 0, 0, 0};
 };
 
 namespace sho {
@@ -253,37 +260,90 @@ GridDev make_grid(const sho_grid* grid, int cube, int nbands) {
 
 // Plane-sweep projection (FP32 psi, FP32 coefficients): plan the row segments on the host, upload
 // the plan and run tables -> plane sweep -> z-pass (sho_plane.cu).
+// FNV-1a over the geometry a plane plan depends on (grid, cube, the atoms with their origins).
+uint64_t geometry_key(const sho_grid* grid, const std::vector<AtomDev>& at, int cube) {
+  uint64_t k = 1469598103934665603ull;
+  auto mix = [&k](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; i++) {
+      k ^= c[i];
+      k *= 1099511628211ull;
+    }
+  };
+  mix(grid->n, sizeof(grid->n));
+  mix(&grid->h, sizeof(grid->h));
+  mix(&grid->periodic, sizeof(grid->periodic));
+  mix(&cube, sizeof(cube));
+  const size_t A = at.size();
+  mix(&A, sizeof(A));
+  if (A) mix(at.data(), A * sizeof(AtomDev));
+  return k | 1ull;  // never 0 (0 marks "no plan")
+}
+
 int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const float* psi,
                    int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
-  PlanePlan plan;
-  plan_planes(grid, at, cube, plan);
   const size_t A = at.size();
+  const uint64_t key = geometry_key(grid, at, cube);
+  SHO_TRY(begin_call(h, s));
+  if (h->plane_key != key) {
+    PlanePlan plan;
+    plan_planes(grid, at, cube, plan);
+    Carve pc;
+    const size_t o_atoms = pc.take(A * sizeof(AtomDev));
+    const size_t o_items = pc.take(std::max<size_t>(1, plan.items.size()) * sizeof(int4));
+    const size_t o_ptr = pc.take(plan.slot_ptr.size() * sizeof(int));
+    const size_t o_segs = pc.take(std::max<size_t>(1, plan.segs.size()) * sizeof(PlaneSeg));
+    if (pc.off > h->plane_cap) {
+      if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+      if (h->plane_mem) cudaFree(h->plane_mem);
+      h->plane_mem = nullptr;
+      h->plane_cap = 0;
+      h->plane_key = 0;
+      if (cudaMalloc(&h->plane_mem, pc.off) != cudaSuccess) {
+        cudaGetLastError();
+        h->plane_mem = nullptr;
+        return SHO_ERR_OOM;
+      }
+      h->plane_cap = pc.off;
+    }
+    char* pm = static_cast<char*>(h->plane_mem);
+    // stream-ordered after the handle's earlier work (begin_call), which may still read the old plan
+    auto up = [&](size_t off, const void* src, size_t bytes) {
+      return bytes == 0 || cudaMemcpyAsync(pm + off, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    if (!up(o_atoms, at.data(), A * sizeof(AtomDev)) || !up(o_items, plan.items.data(), plan.items.size() * sizeof(int4)) ||
+        !up(o_ptr, plan.slot_ptr.data(), plan.slot_ptr.size() * sizeof(int)) ||
+        !up(o_segs, plan.segs.data(), plan.segs.size() * sizeof(PlaneSeg))) {
+      h->plane_key = 0;
+      return SHO_ERR_CUDA;
+    }
+    // pageable sources: the copies have been staged before cudaMemcpyAsync returns, so the vectors
+    // may go out of scope here
+    h->plane_key = key;
+    h->plane_nitems = (int)plan.items.size();
+    h->plane_off[0] = o_atoms;
+    h->plane_off[1] = o_items;
+    h->plane_off[2] = o_ptr;
+    h->plane_off[3] = o_segs;
+  }
   Carve cv;
-  const size_t o_atoms = cv.take(A * sizeof(AtomDev));
-  const size_t o_items = cv.take(std::max<size_t>(1, plan.items.size()) * sizeof(int4));
-  const size_t o_ptr = cv.take(plan.slot_ptr.size() * sizeof(int));
-  const size_t o_segs = cv.take(std::max<size_t>(1, plan.segs.size()) * sizeof(PlaneSeg));
   const size_t o_xt = cv.take(A * cube * 8 * sizeof(float));
   const size_t o_yt = cv.take(A * cube * 8 * sizeof(float));
   const size_t o_bf = cv.take(A * kPlaneBfragBytesPerAtom);
   const size_t o_t2 = cv.take(A * cube * (size_t)npairs(numax) * nbands * sizeof(float));
-  SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
-  SHO_TRY(upload(h, o_atoms, at.data(), A * sizeof(AtomDev), s));
-  SHO_TRY(upload(h, o_items, plan.items.data(), plan.items.size() * sizeof(int4), s));
-  SHO_TRY(upload(h, o_ptr, plan.slot_ptr.data(), plan.slot_ptr.size() * sizeof(int), s));
-  SHO_TRY(upload(h, o_segs, plan.segs.data(), plan.segs.size() * sizeof(PlaneSeg), s));
   char* ws = static_cast<char*>(h->ws);
+  const char* pm = static_cast<const char*>(h->plane_mem);
   PlaneLaunch L;
   L.g = make_grid(grid, cube, nbands);
   L.psi = psi;
-  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  L.atoms = reinterpret_cast<const AtomDev*>(pm + h->plane_off[0]);
   L.natoms = (int)A;
   L.numax = numax;
-  L.items = reinterpret_cast<const int4*>(ws + o_items);
-  L.nitems = (int)plan.items.size();
-  L.slot_ptr = reinterpret_cast<const int*>(ws + o_ptr);
-  L.segs = reinterpret_cast<const PlaneSeg*>(ws + o_segs);
+  L.items = reinterpret_cast<const int4*>(pm + h->plane_off[1]);
+  L.nitems = h->plane_nitems;
+  L.slot_ptr = reinterpret_cast<const int*>(pm + h->plane_off[2]);
+  L.segs = reinterpret_cast<const PlaneSeg*>(pm + h->plane_off[3]);
   L.xtab = reinterpret_cast<float*>(ws + o_xt);
   L.ytab = reinterpret_cast<float*>(ws + o_yt);
   L.bfrag = reinterpret_cast<uint32_t*>(ws + o_bf);
@@ -398,6 +458,7 @@ int sho_create(sho_handle** out, int device) {
   if (cudaMalloc(&h->dstatus, sizeof(int)) != cudaSuccess || cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     if (h->dstatus) cudaFree(h->dstatus);
+    if (h->plane_mem) cudaFree(h->plane_mem);
     for (auto& row : h->radial)
       for (auto& r : row)
         if (r.mem) cudaFree(r.mem);
@@ -418,6 +479,7 @@ int sho_destroy(sho_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->coeff_ws) cudaFree(h->coeff_ws);
     if (h->dstatus) cudaFree(h->dstatus);
+    if (h->plane_mem) cudaFree(h->plane_mem);
     for (auto& row : h->radial)
       for (auto& r : row)
         if (r.mem) cudaFree(r.mem);

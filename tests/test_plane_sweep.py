@@ -189,3 +189,28 @@ def test_expand_bitwise_repeatable():
         api.add(out, c, pos, sig, numax, cube, h, True, prec="tf32")
         outs.append(out)
     assert torch.equal(outs[0], outs[1])
+
+
+def test_plan_cache_follows_the_geometry():
+    """The handle keeps the plan of the last geometry: alternating atom sets on one handle must each get
+    their own plan (results equal to fresh-handle results, bit for bit)."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(660)
+    grid, h, numax, cube = (48, 48, 48), 0.2, 5, 32
+    box = tuple(n * h for n in grid)
+    pa, sa = workloads.random_atoms(rng, 12, box, True, min_sep=1.0)
+    pb, sb = workloads.random_atoms(rng, 9, box, True, min_sep=1.0)
+    psi = torch.from_numpy(rng.standard_normal((48, 48, 48, 32)).astype(np.float32)).cuda()
+    ref_a = api.project(psi, pa, sa, numax, cube, h, True, prec="tf32", handle=api.Handle(0))
+    ref_b = api.project(psi, pb, sb, numax, cube, h, True, prec="tf32", handle=api.Handle(0))
+    hd = api.Handle(0)
+    for pos, sig, ref in ((pa, sa, ref_a), (pb, sb, ref_b), (pa, sa, ref_a), (pa, sa, ref_a)):
+        got = api.project(psi, pos, sig, numax, cube, h, True, prec="tf32", handle=hd)
+        assert torch.equal(got, ref)
+    moved = pa.copy()
+    moved[3, 1] += 0.37
+    got = api.project(psi, moved, sa, numax, cube, h, True, prec="tf32", handle=hd).double().cpu().numpy()
+    exp = oracle.project(grid, h, True, psi.double().cpu().numpy(), moved, sa, numax, cube)
+    assert_coeff_close(got, exp, TOL["tf32"])
