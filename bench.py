@@ -764,7 +764,44 @@ def paper_table1(args):
     for prec in ("fp64", "ff64"):
         sp, sa = sho[(35, prec)]
         fair[prec] = {"prj": round(up / sp, 2), "add": round(ua / sa, 2), "both": round((up + ua) / (sp + sa), 2)}
+    # float (Table 2, left half): FP32 psi, stored FP32 projectors against the FP32 SHO forms
+    del hpsi
+    torch.cuda.empty_cache()
+    psi32 = psi.float()
+    del psi
+    hpsi32 = torch.zeros_like(psi32)
+    flt = {}
+    for N in (1, 4, 10, 18, 20, 35, 56):
+        nu = next(v for v in range(6) if api.nstates(v) >= N)
+        proj = api.usu_build(pos, sig, nu, cube, grid, h, False, device=0, handle=handle, stream=stream, nproj=N,
+                             dtype=torch.float32)
+        coeff = torch.empty((A, N, B), dtype=torch.float32, device=dev)
+        cin = torch.randn((A, N, B), generator=g, device=dev, dtype=torch.float32)
+        ent = {"usu_prj_ms": round(_median_ms(stream, lambda: api.usu_project(psi32, proj, pos, sig, nu, cube, h, False,
+                                                                           out=coeff, handle=handle, stream=stream),
+                                             usu_reps, runs), 3),
+               "usu_add_ms": round(_median_ms(stream, lambda: api.usu_add(hpsi32, cin, proj, pos, sig, nu, cube, h,
+                                                                       False, handle=handle, stream=stream),
+                                             usu_reps, runs), 3)}
+        del proj, coeff, cin
+        if api.nstates(nu) == N:
+            cfull = torch.randn((A, N, B), generator=g, device=dev, dtype=torch.float32)
+            for prec in ("fp32", "tf32"):
+                ent[f"sho_{prec}_prj_ms"] = round(_median_ms(stream, lambda: api.project(
+                    psi32, pos, sig, nu, cube, h, False, prec=prec, handle=handle, stream=stream), sho_reps, runs), 3)
+                ent[f"sho_{prec}_add_ms"] = round(_median_ms(stream, lambda: api.add(
+                    hpsi32, cfull, pos, sig, nu, cube, h, False, prec=prec, handle=handle, stream=stream),
+                    sho_reps, runs), 3)
+            del cfull
+        flt[N] = ent
+        torch.cuda.empty_cache()
+    for prec in ("fp32", "tf32"):
+        sp, sa = flt[35][f"sho_{prec}_prj_ms"], flt[35][f"sho_{prec}_add_ms"]
+        up, ua = flt[18]["usu_prj_ms"], flt[18]["usu_add_ms"]
+        fair[f"float_{prec}"] = {"prj": round(up / sp, 2), "add": round(ua / sa, 2),
+                                 "both": round((up + ua) / (sp + sa), 2)}
     paper_fair = {"P100": {"prj": 2.2, "add": 3.1, "both": 2.6}, "V100": {"prj": 1.4, "add": 2.5, "both": 2.0}}
+    paper_fair_float = {"P100": {"prj": 2.3, "add": 2.9, "both": 2.7}, "V100": {"prj": 1.4, "add": 1.7, "both": 1.6}}
     return {
         "metric": "SHO vs stored-projector (USU) kernel time and speedup S = USU/SHO, the paper's Tables 1 and 2",
         "unit": "ms per execution", "higher_is_better": False, "dtype": "f64", "data": "synthetic",
@@ -773,7 +810,8 @@ def paper_table1(args):
                    "protocol": f"one untimed run, median of {runs} runs of {sho_reps} (SHO) / {usu_reps} (USU) "
                                "executions; psi 2.1 GB > L2",
                    "clipped_cube_points": pts},
-        "rows": rows, "fair_usu18_vs_sho35": fair, "paper_fair_usu18_vs_sho35_double": paper_fair,
+        "rows": rows, "float_rows": flt, "fair_usu18_vs_sho35": fair,
+        "paper_fair_usu18_vs_sho35_double": paper_fair, "paper_fair_usu18_vs_sho35_float": paper_fair_float,
         "paper_table1_s_per_10_executions": PAPER_TABLE1,
     }
 

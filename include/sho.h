@@ -209,26 +209,27 @@ int sho_radial_transform(sho_handle* handle, int natoms, int numax, int nbands, 
                          sho_dtype dtype, int direction, void* stream);
 
 /* ----------------------------------------------------------------------------------------------
- * Stored-projector FP64 baseline: the conventional scheme the paper measures against ("USU", Sec. 6,
- * Table 1): projector values sampled once onto each atom's cube and kept in device memory, then
- * streamed by the projection and expansion.  With the stored values taken from the SHO basis the
- * results equal sho_project / sho_add in SHO_P_FP64 (up to rounding order).
+ * Stored-projector baseline: the conventional scheme the paper measures against ("USU", Sec. 6,
+ * Tables 1 and 2, in double and float): projector values sampled once onto each atom's cube and kept in
+ * device memory, then streamed by the projection and expansion.  With the stored values taken from the
+ * SHO basis the results equal sho_project / sho_add (up to rounding order).
  *   numax  basis the stored projectors are sampled from (numax <= SHO_USU_MAX_NUMAX)
  *   nproj  number of stored projectors: the first nproj states of that basis; one of 1, 4, 10, 18, 20,
  *          35, 56 (the SHO sizes of numax 0..5, and 18 = the s, s*, p, p*, d, d* set of Sec. 6)
- *   proj   device [natoms][cube^3][nproj] double, cube point index (iz*cube + iy)*cube + ix; written by
- *          sho_usu_build, read by the other two (caller allocates 8 * A * C^3 * nproj bytes)
- *   psi, coeff as for sho_project / sho_add ([A][nproj][B]), FP64 only.  pos / sigma host arrays.
+ *   dtype  SHO_F64 or SHO_F32: type of proj, psi and coeff alike (and of the arithmetic)
+ *   proj   device [natoms][cube^3][nproj], cube point index (iz*cube + iy)*cube + ix; written by
+ *          sho_usu_build, read by the other two (caller allocates sizeof(dtype) * A * C^3 * nproj bytes)
+ *   psi, coeff as for sho_project / sho_add ([A][nproj][B]).  pos / sigma host arrays.
  */
 #define SHO_USU_MAX_NUMAX 5
 int sho_usu_build(sho_handle* handle, const sho_grid* grid, int natoms, const double* pos, const double* sigma,
-                  int numax, int nproj, int cube, double* proj, void* stream);
-int sho_usu_project(sho_handle* handle, const sho_grid* grid, const double* psi, int nbands, int natoms,
-                    const double* pos, const double* sigma, int nproj, int cube, const double* proj,
-                    double* coeff, void* stream);
-int sho_usu_add(sho_handle* handle, const sho_grid* grid, const double* coeff, int nbands, int natoms,
-                const double* pos, const double* sigma, int nproj, int cube, const double* proj, double* psi,
-                void* stream);
+                  int numax, int nproj, int cube, sho_dtype dtype, void* proj, void* stream);
+int sho_usu_project(sho_handle* handle, const sho_grid* grid, const void* psi, int nbands, int natoms,
+                    const double* pos, const double* sigma, int nproj, int cube, sho_dtype dtype, const void* proj,
+                    void* coeff, void* stream);
+int sho_usu_add(sho_handle* handle, const sho_grid* grid, const void* coeff, int nbands, int natoms,
+                const double* pos, const double* sigma, int nproj, int cube, sho_dtype dtype, const void* proj,
+                void* psi, void* stream);
 
 /* ----------------------------------------------------------------------------------------------
  * Serving: a continuous-batching request loop over device-resident systems.  (The paper applies the

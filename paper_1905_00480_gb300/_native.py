@@ -66,9 +66,9 @@ SIGNATURES = {
     "sho_forces": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),
     "sho_forces_noalloc": (_I, [_GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),
     "sho_apply_nonlocal": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _VP, _VP]),
-    "sho_usu_build": (_I, [_VP, _GP, _I, _DP, _DP, _I, _I, _I, _VP, _VP]),
-    "sho_usu_project": (_I, [_VP, _GP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP, _VP]),
-    "sho_usu_add": (_I, [_VP, _GP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP, _VP]),
+    "sho_usu_build": (_I, [_VP, _GP, _I, _DP, _DP, _I, _I, _I, _I, _VP, _VP]),
+    "sho_usu_project": (_I, [_VP, _GP, _VP, _I, _I, _DP, _DP, _I, _I, _I, _VP, _VP, _VP]),
+    "sho_usu_add": (_I, [_VP, _GP, _VP, _I, _I, _DP, _DP, _I, _I, _I, _VP, _VP, _VP]),
     "sho_server_create": (_I, [ctypes.POINTER(_VP), _I, ctypes.c_size_t, _I]),
     "sho_server_destroy": (_I, [_VP]),
     "sho_system_register": (_I, [_VP, _GP, _I, _I, _DP, _DP, _I, _I, _I, _VP, ctypes.POINTER(_I)]),

@@ -249,41 +249,48 @@ def apply_nonlocal(psi: torch.Tensor, hpsi: torch.Tensor, D: torch.Tensor, pos, 
 
 # ------------------------------------------------------------------------ stored-projector baseline
 def usu_build(pos, sigma, numax: int, cube: int, grid_shape, h: float, periodic: bool = True, device=0,
-              handle: Handle = None, stream=None, nproj: int = None) -> torch.Tensor:
+              handle: Handle = None, stream=None, nproj: int = None, dtype=torch.float64) -> torch.Tensor:
     """sho_usu_build: sample every atom's first nproj projector values (default: all states of numax)
-    onto its cube, [A][C^3][nproj] FP64 on the device."""
+    onto its cube, [A][C^3][nproj] of dtype (float64 or float32) on the device."""
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
     A = pos_h.shape[0]
     nproj = nstates(numax) if nproj is None else int(nproj)
+    if dtype not in (torch.float64, torch.float32):
+        raise ValueError("stored projectors are float64 or float32")
     dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
-    proj = torch.empty((A, cube ** 3, nproj), dtype=torch.float64, device=dev)
+    proj = torch.empty((A, cube ** 3, nproj), dtype=dtype, device=dev)
     hd = handle or default_handle(dev.index or 0)
     g = N.sho_grid()
     g.n[0], g.n[1], g.n[2] = int(grid_shape[0]), int(grid_shape[1]), int(grid_shape[2])
     g.h, g.periodic = float(h), 1 if periodic else 0
     s = stream if stream is not None else torch.cuda.current_stream(dev)
     st = N.lib().sho_usu_build(hd.ptr, ctypes.byref(g), A, _dp(pos_h), _dp(sig_h), int(numax), nproj, int(cube),
-                               ctypes.c_void_p(proj.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+                               N.DTYPES[_TORCH_DT[dtype]], ctypes.c_void_p(proj.data_ptr()),
+                               ctypes.c_void_p(s.cuda_stream))
     N.check(st, "sho_usu_build")
     return proj
 
 
 def usu_project(psi: torch.Tensor, proj: torch.Tensor, pos, sigma, numax: int, cube: int, h: float,
                 periodic: bool = True, out: torch.Tensor = None, handle: Handle = None, stream=None):
-    """sho_usu_project: the projection with stored projector values (FP64); the projector count is
-    proj.shape[2] (numax is accepted for symmetry with usu_build and ignored)."""
+    """sho_usu_project: the projection with stored projector values (psi, proj and the result share one
+    dtype, float64 or float32); the projector count is proj.shape[2] (numax is accepted for symmetry with
+    usu_build and ignored)."""
     _check_psi(psi)
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
     A, B = pos_h.shape[0], psi.shape[3]
     nproj = int(proj.shape[2])
+    if psi.dtype != proj.dtype or psi.dtype not in (torch.float64, torch.float32):
+        raise ValueError("psi and proj must both be float64 or both float32")
     if out is None:
-        out = torch.empty((A, nproj, B), dtype=torch.float64, device=psi.device)
+        out = torch.empty((A, nproj, B), dtype=psi.dtype, device=psi.device)
     hd = handle or default_handle(psi.device.index or 0)
     g = _grid(psi, h, periodic)
     st = N.lib().sho_usu_project(hd.ptr, ctypes.byref(g), ctypes.c_void_p(psi.data_ptr()), B, A, _dp(pos_h),
-                                 _dp(sig_h), nproj, int(cube), ctypes.c_void_p(proj.data_ptr()),
+                                 _dp(sig_h), nproj, int(cube), N.DTYPES[_TORCH_DT[psi.dtype]],
+                                 ctypes.c_void_p(proj.data_ptr()),
                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(psi, stream))
     N.check(st, "sho_usu_project")
     return out
@@ -291,17 +298,20 @@ def usu_project(psi: torch.Tensor, proj: torch.Tensor, pos, sigma, numax: int, c
 
 def usu_add(psi: torch.Tensor, coeff: torch.Tensor, proj: torch.Tensor, pos, sigma, numax: int, cube: int, h: float,
             periodic: bool = True, handle: Handle = None, stream=None):
-    """sho_usu_add (in place): the expansion with stored projector values (FP64)."""
+    """sho_usu_add (in place): the expansion with stored projector values (psi, coeff and proj share one
+    dtype, float64 or float32)."""
     _check_psi(psi)
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
     A, B = pos_h.shape[0], psi.shape[3]
-    if tuple(coeff.shape) != (A, int(proj.shape[2]), B) or coeff.dtype != torch.float64:
-        raise ValueError(f"coeff must be float64 [{A}][{int(proj.shape[2])}][{B}], got {coeff.dtype} {tuple(coeff.shape)}")
+    if tuple(coeff.shape) != (A, int(proj.shape[2]), B) or coeff.dtype != psi.dtype or proj.dtype != psi.dtype:
+        raise ValueError(f"coeff must be {psi.dtype} [{A}][{int(proj.shape[2])}][{B}] like psi and proj, "
+                         f"got {coeff.dtype} {tuple(coeff.shape)}")
     hd = handle or default_handle(psi.device.index or 0)
     g = _grid(psi, h, periodic)
     st = N.lib().sho_usu_add(hd.ptr, ctypes.byref(g), ctypes.c_void_p(coeff.data_ptr()), B, A, _dp(pos_h),
-                             _dp(sig_h), int(proj.shape[2]), int(cube), ctypes.c_void_p(proj.data_ptr()),
+                             _dp(sig_h), int(proj.shape[2]), int(cube), N.DTYPES[_TORCH_DT[psi.dtype]],
+                             ctypes.c_void_p(proj.data_ptr()),
                              ctypes.c_void_p(psi.data_ptr()), _stream_ptr(psi, stream))
     N.check(st, "sho_usu_add")
     return psi

@@ -789,8 +789,9 @@ int sho_apply_nonlocal(sho_handle* h, const sho_grid* grid, const void* psi, sho
 
 // ------------------------------------------------------------------ stored-projector baseline
 int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double* pos, const double* sigma, int numax,
-                  int nproj, int cube, double* proj, void* stream) {
+                  int nproj, int cube, sho_dtype dtype, void* proj, void* stream) {
   if (!h) return SHO_ERR_ARG;
+  if (dtype != SHO_F64 && dtype != SHO_F32) return SHO_ERR_DTYPE;
   SHO_TRY(check_common(grid, 0, natoms, pos, sigma, numax, cube, SHO_USU_MAX_NUMAX));
   if (nproj < 1 || nproj > nstates(numax) || !usu_supported_nproj(nproj)) return SHO_ERR_ARG;
   if (natoms == 0) return SHO_OK;
@@ -810,16 +811,18 @@ int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double*
   L.natoms = natoms;
   L.numax = numax;
   L.nproj = nproj;
+  L.dtype = dtype;
   L.proj = proj;
   L.stream = s;
   if (launch_usu(0, L) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
 }
 
-int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int nbands, int natoms,
-                    const double* pos, const double* sigma, int nproj, int cube, const double* proj, double* coeff,
-                    void* stream) {
+int sho_usu_project(sho_handle* h, const sho_grid* grid, const void* psi, int nbands, int natoms,
+                    const double* pos, const double* sigma, int nproj, int cube, sho_dtype dtype, const void* proj,
+                    void* coeff, void* stream) {
   if (!h) return SHO_ERR_ARG;
+  if (dtype != SHO_F64 && dtype != SHO_F32) return SHO_ERR_DTYPE;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, 0, cube, SHO_USU_MAX_NUMAX));
   if (!usu_supported_nproj(nproj)) return SHO_ERR_ARG;
   if (natoms == 0 || nbands == 0) return SHO_OK;
@@ -839,7 +842,8 @@ int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int 
   L.natoms = natoms;
   L.nproj = nproj;
   L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
-  L.proj = const_cast<double*>(proj);
+  L.dtype = dtype;
+  L.proj = const_cast<void*>(proj);
   L.psi_in = psi;
   L.coeff_out = coeff;
   L.stream = s;
@@ -847,9 +851,10 @@ int sho_usu_project(sho_handle* h, const sho_grid* grid, const double* psi, int 
   return end_call(h, s);
 }
 
-int sho_usu_add(sho_handle* h, const sho_grid* grid, const double* coeff, int nbands, int natoms, const double* pos,
-                const double* sigma, int nproj, int cube, const double* proj, double* psi, void* stream) {
+int sho_usu_add(sho_handle* h, const sho_grid* grid, const void* coeff, int nbands, int natoms, const double* pos,
+                const double* sigma, int nproj, int cube, sho_dtype dtype, const void* proj, void* psi, void* stream) {
   if (!h) return SHO_ERR_ARG;
+  if (dtype != SHO_F64 && dtype != SHO_F32) return SHO_ERR_DTYPE;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, 0, cube, SHO_USU_MAX_NUMAX));
   if (!usu_supported_nproj(nproj)) return SHO_ERR_ARG;
   if (natoms == 0 || nbands == 0) return SHO_OK;
@@ -875,7 +880,8 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const double* coeff, int nb
   L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
   L.natoms = natoms;
   L.nproj = nproj;
-  L.proj = const_cast<double*>(proj);
+  L.dtype = dtype;
+  L.proj = const_cast<void*>(proj);
   L.coeff_in = coeff;
   L.psi_out = psi;
   L.plane_ptr = reinterpret_cast<const int*>(ws + o_ptr);

@@ -88,11 +88,12 @@ struct UsuLaunch {
   int numax;                // build: basis the stored projectors are taken from
   int nproj;                // number of stored projectors (the first nproj states of that basis)
   int zsplit;
-  double* proj;             // [A][C^3][nproj] FP64
-  const double* psi_in;     // project: psi
-  double* coeff_out;        // project: coefficients
-  const double* coeff_in;   // add: coefficients
-  double* psi_out;          // add: psi (read-modify-write)
+  sho_dtype dtype;          // F64 or F32: type of every array below
+  void* proj;               // [A][C^3][nproj]
+  const void* psi_in;       // project: psi
+  void* coeff_out;          // project: coefficients
+  const void* coeff_in;     // add: coefficients
+  void* psi_out;            // add: psi (read-modify-write)
   const int* plane_ptr;
   const int* plane_atoms;
   cudaStream_t stream;

@@ -1,7 +1,7 @@
-// sho_usu.cu -- stored-projector FP64 baseline (the conventional scheme the paper compares with,
-// "USU" in Sec. 6): the projector values Psi_k(u_i) of every atom are sampled once onto its cube and
-// stored in device memory, [A][C^3][N] FP64; projection and expansion then stream them from memory
-// instead of generating the 1D functions on the fly.  Same cube convention, same band-major psi, same
+// sho_usu.cu -- stored-projector baseline (the conventional scheme the paper compares with, "USU" in
+// Sec. 6, in double and float as its Tables 1 and 2): the projector values Psi_k(u_i) of every atom are
+// sampled once onto its cube and stored in device memory, [A][C^3][N] of the compute type; projection
+// and expansion then stream them from memory instead of generating the 1D functions on the fly.  Same cube convention, same band-major psi, same
 // deterministic decomposition as the SHO kernels (cluster-reduced z-slabs; row gather), so the two
 // differ only in where the projector values come from.
 #include <cooperative_groups.h>
@@ -13,9 +13,9 @@ namespace cg = cooperative_groups;
 namespace sho {
 
 // --------------------------------------------------------------------------------- build
-template <int NU>
+template <typename T, int NU>
 __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __restrict__ atoms, int nproj,
-                                                   double* __restrict__ proj) {
+                                                   T* __restrict__ proj) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP;
   const int C = g.cube;
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __r
   phi_column(cube_offset(at.o[0], ix, g.h, at.X[0]), at.sigma, NU, fx, 1);
   phi_column(cube_offset(at.o[1], iy, g.h, at.X[1]), at.sigma, NU, fy, 1);
   phi_column(cube_offset(at.o[2], iz, g.h, at.X[2]), at.sigma, NU, fz, 1);
-  double* out = proj + ((long long)a * c3 + i) * nproj;
+  T* out = proj + ((long long)a * c3 + i) * nproj;
   int k = 0;
 #pragma unroll
   for (int nz = 0; nz < NP; nz++)
@@ -37,18 +37,18 @@ __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __r
     for (int ny = 0; ny + nz <= NU; ny++)
 #pragma unroll
       for (int nx = 0; nx + ny + nz <= NU; nx++) {
-        if (k < nproj) out[k] = fx[nx] * fy[ny] * fz[nz];
+        if (k < nproj) out[k] = (T)(fx[nx] * fy[ny] * fz[nz]);
         k++;
       }
 }
 
 // --------------------------------------------------------------------------------- project
-template <int N>
-__global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* __restrict__ psi,
+template <typename T, int N>
+__global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const T* __restrict__ psi,
                                                        const AtomDev* __restrict__ atoms,
-                                                       const double* __restrict__ proj, int zsplit,
-                                                       double* __restrict__ coeff) {
-  __shared__ double acc[N * kWarp];
+                                                       const T* __restrict__ proj, int zsplit,
+                                                       T* __restrict__ coeff) {
+  __shared__ T acc[N * kWarp];
   const int C = g.cube;
   const int lane = threadIdx.x;
   const int a = blockIdx.z;
@@ -57,10 +57,10 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* 
   const bool bok = b < B;
   const AtomDev at = atoms[a];
   const long long c3 = (long long)C * C * C;
-  const double* pa = proj + (long long)a * c3 * N;
-  double r[N];
+  const T* pa = proj + (long long)a * c3 * N;
+  T r[N];
 #pragma unroll
-  for (int k = 0; k < N; k++) r[k] = 0.0;
+  for (int k = 0; k < N; k++) r[k] = (T)0;
   const int chunk = (C + zsplit - 1) / zsplit;
   const int iz0 = blockIdx.x * chunk, iz1 = min(C, iz0 + chunk);
   for (int iz = iz0; iz < iz1; iz++) {
@@ -69,12 +69,12 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* 
     for (int iy = 0; iy < C; iy++) {
       const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
       if (jy < 0) continue;
-      const double* row = psi + ((long long)jz * g.n[1] + jy) * g.n[0] * B + b;
+      const T* row = psi + ((long long)jz * g.n[1] + jy) * g.n[0] * B + b;
       for (int ix = 0; ix < C; ix++) {
         const int jx = cube_index(at.o[0], ix, g.n[0], g.periodic);
         if (jx < 0) continue;
-        const double v = bok ? row[(long long)jx * B] : 0.0;
-        const double* p = pa + (((long long)iz * C + iy) * C + ix) * N;
+        const T v = bok ? row[(long long)jx * B] : (T)0;
+        const T* p = pa + (((long long)iz * C + iy) * C + ix) * N;
 #pragma unroll
         for (int k = 0; k < N; k++) r[k] = fma(__ldg(p + k), v, r[k]);
       }
@@ -85,9 +85,9 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* 
   cg::cluster_group cl = cg::this_cluster();
   cl.sync();
   const int rank = (int)cl.block_rank();
-  const double h3 = g.h * g.h * g.h;
+  const T h3 = (T)(g.h * g.h * g.h);
   for (int k = rank; k < N; k += zsplit) {
-    double s = 0.0;
+    T s = (T)0;
     for (int q = 0; q < zsplit; q++) s += cl.map_shared_rank(acc, q)[k * kWarp + lane];
     if (bok) coeff[((long long)a * N + k) * B + b] = s * h3;
   }
@@ -95,14 +95,14 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const double* 
 }
 
 // --------------------------------------------------------------------------------- add (row gather)
-template <int N>
+template <typename T, int N>
 __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __restrict__ atoms,
                                                    const int* __restrict__ plane_ptr,
                                                    const int* __restrict__ plane_atoms,
-                                                   const double* __restrict__ proj,
-                                                   const double* __restrict__ coeff, double* __restrict__ psi) {
+                                                   const T* __restrict__ proj,
+                                                   const T* __restrict__ coeff, T* __restrict__ psi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* acc = reinterpret_cast<double*>(smem_raw);  // [Nx][32]
+  T* acc = reinterpret_cast<T*>(smem_raw);  // [Nx][32]
   const int C = g.cube;
   const int Nx = g.n[0], Ny = g.n[1];
   const int lane = threadIdx.x;
@@ -122,8 +122,8 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
     any = (iy >= 0 && iy < C);
   }
   if (!any) return;
-  double* row = psi + (long long)r * Nx * B + b;
-  for (int jx = 0; jx < Nx; jx++) acc[jx * kWarp + lane] = bok ? row[(long long)jx * B] : 0.0;
+  T* row = psi + (long long)r * Nx * B + b;
+  for (int jx = 0; jx < Nx; jx++) acc[jx * kWarp + lane] = bok ? row[(long long)jx * B] : (T)0;
   const long long c3 = (long long)C * C * C;
   for (int q = q0; q < q1; q++) {
     const int a = plane_atoms[q];
@@ -136,16 +136,16 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
       if (iz < 0) iz += g.n[2];
     }
     if (iy < 0 || iy >= C) continue;
-    double cr[N];
-    const double* ca = coeff + (long long)a * N * B + b;
+    T cr[N];
+    const T* ca = coeff + (long long)a * N * B + b;
 #pragma unroll
-    for (int k = 0; k < N; k++) cr[k] = bok ? ca[(long long)k * B] : 0.0;
-    const double* pa = proj + ((long long)a * c3 + ((long long)iz * C + iy) * C) * N;
+    for (int k = 0; k < N; k++) cr[k] = bok ? ca[(long long)k * B] : (T)0;
+    const T* pa = proj + ((long long)a * c3 + ((long long)iz * C + iy) * C) * N;
     for (int ix = 0; ix < C; ix++) {
       const int jx = cube_index(at.o[0], ix, Nx, g.periodic);
       if (jx < 0) continue;
-      const double* p = pa + (long long)ix * N;
-      double s = 0.0;
+      const T* p = pa + (long long)ix * N;
+      T s = (T)0;
 #pragma unroll
       for (int k = 0; k < N; k++) s = fma(cr[k], __ldg(p + k), s);
       acc[jx * kWarp + lane] += s;
@@ -155,15 +155,15 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
     for (int jx = 0; jx < Nx; jx++) row[(long long)jx * B] = acc[jx * kWarp + lane];
 }
 
-template <int NU>
+template <typename T, int NU>
 static cudaError_t usu_build_nu(const UsuLaunch& p) {
   const long long c3 = (long long)p.g.cube * p.g.cube * p.g.cube;
-  k_usu_build<NU><<<dim3((unsigned)((c3 + 127) / 128), p.natoms), 128, 0, p.stream>>>(p.g, p.atoms, p.nproj,
-                                                                                     p.proj);
+  k_usu_build<T, NU><<<dim3((unsigned)((c3 + 127) / 128), p.natoms), 128, 0, p.stream>>>(p.g, p.atoms, p.nproj,
+                                                                                        static_cast<T*>(p.proj));
   return cudaGetLastError();
 }
 
-template <int N>
+template <typename T, int N>
 static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
   if (op == 1) {
@@ -179,16 +179,43 @@ static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_usu_project<N>, p.g, p.psi_in, p.atoms, (const double*)p.proj, p.zsplit,
-                              p.coeff_out);
+    return cudaLaunchKernelEx(&cfg, k_usu_project<T, N>, p.g, static_cast<const T*>(p.psi_in), p.atoms,
+                              static_cast<const T*>(p.proj), p.zsplit, static_cast<T*>(p.coeff_out));
   }
-  auto kern = k_usu_add<N>;
-  const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(double);
+  auto kern = k_usu_add<T, N>;
+  const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<dim3(p.g.n[1] * p.g.n[2], nbt), kWarp, smem, p.stream>>>(p.g, p.atoms, p.plane_ptr, p.plane_atoms, p.proj,
-                                                                  p.coeff_in, p.psi_out);
+  kern<<<dim3(p.g.n[1] * p.g.n[2], nbt), kWarp, smem, p.stream>>>(p.g, p.atoms, p.plane_ptr, p.plane_atoms,
+                                                                  static_cast<const T*>(p.proj),
+                                                                  static_cast<const T*>(p.coeff_in),
+                                                                  static_cast<T*>(p.psi_out));
   return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_usu_t(int op, const UsuLaunch& p) {
+  if (op == 0) {
+    switch (p.numax) {
+      case 0: return usu_build_nu<T, 0>(p);
+      case 1: return usu_build_nu<T, 1>(p);
+      case 2: return usu_build_nu<T, 2>(p);
+      case 3: return usu_build_nu<T, 3>(p);
+      case 4: return usu_build_nu<T, 4>(p);
+      case 5: return usu_build_nu<T, 5>(p);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (p.nproj) {
+    case 1: return usu_run_n<T, 1>(op, p);
+    case 4: return usu_run_n<T, 4>(op, p);
+    case 10: return usu_run_n<T, 10>(op, p);
+    case 18: return usu_run_n<T, 18>(op, p);
+    case 20: return usu_run_n<T, 20>(op, p);
+    case 35: return usu_run_n<T, 35>(op, p);
+    case 56: return usu_run_n<T, 56>(op, p);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // Stored-projector counts with compiled kernels: the SHO basis sizes of numax 0..5 and 18 (the
@@ -198,27 +225,7 @@ bool usu_supported_nproj(int n) {
 }
 
 cudaError_t launch_usu(int op, const UsuLaunch& p) {
-  if (op == 0) {
-    switch (p.numax) {
-      case 0: return usu_build_nu<0>(p);
-      case 1: return usu_build_nu<1>(p);
-      case 2: return usu_build_nu<2>(p);
-      case 3: return usu_build_nu<3>(p);
-      case 4: return usu_build_nu<4>(p);
-      case 5: return usu_build_nu<5>(p);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (p.nproj) {
-    case 1: return usu_run_n<1>(op, p);
-    case 4: return usu_run_n<4>(op, p);
-    case 10: return usu_run_n<10>(op, p);
-    case 18: return usu_run_n<18>(op, p);
-    case 20: return usu_run_n<20>(op, p);
-    case 35: return usu_run_n<35>(op, p);
-    case 56: return usu_run_n<56>(op, p);
-    default: return cudaErrorInvalidValue;
-  }
+  return p.dtype == SHO_F32 ? launch_usu_t<float>(op, p) : launch_usu_t<double>(op, p);
 }
 
 }  // namespace sho
