@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const T* __res
   const AtomDev at = atoms[a];
   const long long c3 = (long long)C * C * C;
   const T* pa = proj + (long long)a * c3 * N;
+  const int oxm = g.periodic ? ((at.o[0] % g.n[0]) + g.n[0]) % g.n[0] : at.o[0];
   T r[N];
 #pragma unroll
   for (int k = 0; k < N; k++) r[k] = (T)0;
@@ -70,9 +71,12 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const T* __res
       const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
       if (jy < 0) continue;
       const T* row = psi + ((long long)jz * g.n[1] + jy) * g.n[0] * B + b;
-      for (int ix = 0; ix < C; ix++) {
-        const int jx = cube_index(at.o[0], ix, g.n[0], g.periodic);
-        if (jx < 0) continue;
+      // cube points of this row inside the grid: all when periodic, one contiguous run otherwise
+      const int ix0 = g.periodic ? 0 : max(0, -at.o[0]), ix1 = g.periodic ? C : min(C, g.n[0] - at.o[0]);
+#pragma unroll 4
+      for (int ix = ix0; ix < ix1; ix++) {
+        int jx = oxm + ix;  // periodic: oxm in [0, Nx) and ix < C <= Nx, so one wrap at most
+        if (g.periodic && jx >= g.n[0]) jx -= g.n[0];
         const T v = bok ? row[(long long)jx * B] : (T)0;
         const T* p = pa + (((long long)iz * C + iy) * C + ix) * N;
 #pragma unroll
@@ -141,9 +145,12 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
 #pragma unroll
     for (int k = 0; k < N; k++) cr[k] = bok ? ca[(long long)k * B] : (T)0;
     const T* pa = proj + ((long long)a * c3 + ((long long)iz * C + iy) * C) * N;
-    for (int ix = 0; ix < C; ix++) {
-      const int jx = cube_index(at.o[0], ix, Nx, g.periodic);
-      if (jx < 0) continue;
+    const int ix0 = g.periodic ? 0 : max(0, -at.o[0]), ix1 = g.periodic ? C : min(C, Nx - at.o[0]);
+    const int oxm = g.periodic ? ((at.o[0] % Nx) + Nx) % Nx : at.o[0];
+#pragma unroll 4
+    for (int ix = ix0; ix < ix1; ix++) {
+      int jx = oxm + ix;  // periodic: one wrap at most
+      if (g.periodic && jx >= Nx) jx -= Nx;
       const T* p = pa + (long long)ix * N;
       T s = (T)0;
 #pragma unroll

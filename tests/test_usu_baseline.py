@@ -92,3 +92,20 @@ def test_usu_float():
     api.usu_add(psi_d, torch.from_numpy(c).cuda(), proj, pos, sig, numax, cube, h, True)
     ref2 = oracle.add(grid, h, True, psi.astype(np.float64), pos, sig, numax, cube, cfull)
     assert rel_norm(psi_d.double().cpu().numpy() - psi, ref2 - psi) <= 2e-5
+
+
+def test_usu_positions_outside_periodic_box():
+    """Periodic grid, atoms given several box lengths outside the cell: the stored-projector kernels wrap
+    the cube origin and agree with the oracle."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(203)
+    grid, h, numax, cube = (36, 40, 32), 0.2, 3, 16
+    L = np.array(grid) * h
+    pos, sig = workloads.random_atoms(rng, 4, tuple(L), True, min_sep=1.0)
+    pos = pos + np.array([[-2, 0, 3], [5, -1, 0], [0, 0, -7], [1, 1, 1]]) * L
+    psi = rng.standard_normal((32, 40, 36, 8))
+    proj = api.usu_build(pos, sig, numax, cube, grid, h, True)
+    got = api.usu_project(torch.from_numpy(psi).cuda(), proj, pos, sig, numax, cube, h, True).cpu().numpy()
+    assert_coeff_close(got, oracle.project(grid, h, True, psi, pos, sig, numax, cube), TOL_FP64)
