@@ -43,25 +43,48 @@ __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __r
 }
 
 // --------------------------------------------------------------------------------- project
-template <typename T, int N>
+// BPL consecutive bands per lane (1 in double; 2 or 4 in float, where the stored values -- one load per
+// grid point and state, shared by the warp -- would otherwise outnumber the FMAs they feed).
+template <typename T, int BPL>
+__device__ __forceinline__ void usu_load(const T* p, bool full, int valid, T (&v)[BPL]) {
+  if (BPL == 4 && full) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2 % BPL] = q.z;
+    v[3 % BPL] = q.w;
+  } else if (BPL == 2 && full) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x;
+    v[1 % BPL] = q.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < BPL; j++) v[j] = j < valid ? p[j] : (T)0;
+  }
+}
+
+template <typename T, int N, int BPL>
 __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const T* __restrict__ psi,
                                                        const AtomDev* __restrict__ atoms,
                                                        const T* __restrict__ proj, int zsplit,
                                                        T* __restrict__ coeff) {
-  __shared__ T acc[N * kWarp];
+  __shared__ T acc[N * kWarp * BPL];
   const int C = g.cube;
   const int lane = threadIdx.x;
   const int a = blockIdx.z;
   const int B = g.nbands;
-  const int b = blockIdx.y * kWarp + lane;
-  const bool bok = b < B;
+  const int b = (blockIdx.y * kWarp + lane) * BPL;  // first band of this lane
+  const int valid = min(BPL, B - b);               // bands of this lane inside [0, B)
+  const bool full = valid == BPL;
   const AtomDev at = atoms[a];
   const long long c3 = (long long)C * C * C;
   const T* pa = proj + (long long)a * c3 * N;
   const int oxm = g.periodic ? ((at.o[0] % g.n[0]) + g.n[0]) % g.n[0] : at.o[0];
-  T r[N];
+  T r[N][BPL];
 #pragma unroll
-  for (int k = 0; k < N; k++) r[k] = (T)0;
+  for (int k = 0; k < N; k++)
+#pragma unroll
+    for (int j = 0; j < BPL; j++) r[k][j] = (T)0;
   const int chunk = (C + zsplit - 1) / zsplit;
   const int iz0 = blockIdx.x * chunk, iz1 = min(C, iz0 + chunk);
   for (int iz = iz0; iz < iz1; iz++) {
@@ -77,44 +100,56 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const T* __res
       for (int ix = ix0; ix < ix1; ix++) {
         int jx = oxm + ix;  // periodic: oxm in [0, Nx) and ix < C <= Nx, so one wrap at most
         if (g.periodic && jx >= g.n[0]) jx -= g.n[0];
-        const T v = bok ? row[(long long)jx * B] : (T)0;
+        T v[BPL];
+        if (valid > 0) usu_load<T, BPL>(row + (long long)jx * B, full, valid, v);
+        else
+#pragma unroll
+          for (int j = 0; j < BPL; j++) v[j] = (T)0;
         const T* p = pa + (((long long)iz * C + iy) * C + ix) * N;
 #pragma unroll
-        for (int k = 0; k < N; k++) r[k] = fma(__ldg(p + k), v, r[k]);
+        for (int k = 0; k < N; k++) {
+          const T w = __ldg(p + k);
+#pragma unroll
+          for (int j = 0; j < BPL; j++) r[k][j] = fma(w, v[j], r[k][j]);
+        }
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < N; k++) acc[k * kWarp + lane] = r[k];
+  for (int k = 0; k < N; k++)
+#pragma unroll
+    for (int j = 0; j < BPL; j++) acc[(k * kWarp + lane) * BPL + j] = r[k][j];
   cg::cluster_group cl = cg::this_cluster();
   cl.sync();
   const int rank = (int)cl.block_rank();
   const T h3 = (T)(g.h * g.h * g.h);
-  for (int k = rank; k < N; k += zsplit) {
-    T s = (T)0;
-    for (int q = 0; q < zsplit; q++) s += cl.map_shared_rank(acc, q)[k * kWarp + lane];
-    if (bok) coeff[((long long)a * N + k) * B + b] = s * h3;
-  }
+  for (int k = rank; k < N; k += zsplit)
+#pragma unroll
+    for (int j = 0; j < BPL; j++) {
+      T s = (T)0;
+      for (int q = 0; q < zsplit; q++) s += cl.map_shared_rank(acc, q)[(k * kWarp + lane) * BPL + j];
+      if (j < valid) coeff[((long long)a * N + k) * B + b + j] = s * h3;
+    }
   cl.sync();
 }
 
 // --------------------------------------------------------------------------------- add (row gather)
-template <typename T, int N>
+template <typename T, int N, int BPL>
 __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __restrict__ atoms,
                                                    const int* __restrict__ plane_ptr,
                                                    const int* __restrict__ plane_atoms,
                                                    const T* __restrict__ proj,
                                                    const T* __restrict__ coeff, T* __restrict__ psi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* acc = reinterpret_cast<T*>(smem_raw);  // [Nx][32]
+  T* acc = reinterpret_cast<T*>(smem_raw);  // [Nx][32 * BPL]
   const int C = g.cube;
   const int Nx = g.n[0], Ny = g.n[1];
   const int lane = threadIdx.x;
   const int r = blockIdx.x;
   const int z = r / Ny, y = r - z * Ny;
   const int B = g.nbands;
-  const int b = blockIdx.y * kWarp + lane;
-  const bool bok = b < B;
+  const int b = (blockIdx.y * kWarp + lane) * BPL;
+  const int valid = min(BPL, B - b);
   const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
   bool any = false;
   for (int q = q0; q < q1 && !any; q++) {
@@ -127,7 +162,9 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
   }
   if (!any) return;
   T* row = psi + (long long)r * Nx * B + b;
-  for (int jx = 0; jx < Nx; jx++) acc[jx * kWarp + lane] = bok ? row[(long long)jx * B] : (T)0;
+  for (int jx = 0; jx < Nx; jx++)
+#pragma unroll
+    for (int j = 0; j < BPL; j++) acc[(jx * kWarp + lane) * BPL + j] = j < valid ? row[(long long)jx * B + j] : (T)0;
   const long long c3 = (long long)C * C * C;
   for (int q = q0; q < q1; q++) {
     const int a = plane_atoms[q];
@@ -140,10 +177,12 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
       if (iz < 0) iz += g.n[2];
     }
     if (iy < 0 || iy >= C) continue;
-    T cr[N];
+    T cr[N][BPL];
     const T* ca = coeff + (long long)a * N * B + b;
 #pragma unroll
-    for (int k = 0; k < N; k++) cr[k] = bok ? ca[(long long)k * B] : (T)0;
+    for (int k = 0; k < N; k++)
+#pragma unroll
+      for (int j = 0; j < BPL; j++) cr[k][j] = j < valid ? ca[(long long)k * B + j] : (T)0;
     const T* pa = proj + ((long long)a * c3 + ((long long)iz * C + iy) * C) * N;
     const int ix0 = g.periodic ? 0 : max(0, -at.o[0]), ix1 = g.periodic ? C : min(C, Nx - at.o[0]);
     const int oxm = g.periodic ? ((at.o[0] % Nx) + Nx) % Nx : at.o[0];
@@ -152,14 +191,23 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
       int jx = oxm + ix;  // periodic: one wrap at most
       if (g.periodic && jx >= Nx) jx -= Nx;
       const T* p = pa + (long long)ix * N;
-      T s = (T)0;
+      T sv[BPL];
 #pragma unroll
-      for (int k = 0; k < N; k++) s = fma(cr[k], __ldg(p + k), s);
-      acc[jx * kWarp + lane] += s;
+      for (int j = 0; j < BPL; j++) sv[j] = (T)0;
+#pragma unroll
+      for (int k = 0; k < N; k++) {
+        const T w = __ldg(p + k);
+#pragma unroll
+        for (int j = 0; j < BPL; j++) sv[j] = fma(cr[k][j], w, sv[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < BPL; j++) acc[(jx * kWarp + lane) * BPL + j] += sv[j];
     }
   }
-  if (bok)
-    for (int jx = 0; jx < Nx; jx++) row[(long long)jx * B] = acc[jx * kWarp + lane];
+  for (int jx = 0; jx < Nx; jx++)
+#pragma unroll
+    for (int j = 0; j < BPL; j++)
+      if (j < valid) row[(long long)jx * B + j] = acc[(jx * kWarp + lane) * BPL + j];
 }
 
 template <typename T, int NU>
@@ -170,9 +218,9 @@ static cudaError_t usu_build_nu(const UsuLaunch& p) {
   return cudaGetLastError();
 }
 
-template <typename T, int N>
-static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
-  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+template <typename T, int N, int BPL>
+static cudaError_t usu_run_nb(int op, const UsuLaunch& p) {
+  const int nbt = (p.g.nbands + kWarp * BPL - 1) / (kWarp * BPL);
   if (op == 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(p.zsplit, nbt, p.natoms);
@@ -186,11 +234,11 @@ static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_usu_project<T, N>, p.g, static_cast<const T*>(p.psi_in), p.atoms,
+    return cudaLaunchKernelEx(&cfg, k_usu_project<T, N, BPL>, p.g, static_cast<const T*>(p.psi_in), p.atoms,
                               static_cast<const T*>(p.proj), p.zsplit, static_cast<T*>(p.coeff_out));
   }
-  auto kern = k_usu_add<T, N>;
-  const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(T);
+  auto kern = k_usu_add<T, N, BPL>;
+  const size_t smem = (size_t)p.g.n[0] * kWarp * BPL * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3(p.g.n[1] * p.g.n[2], nbt), kWarp, smem, p.stream>>>(p.g, p.atoms, p.plane_ptr, p.plane_atoms,
@@ -198,6 +246,28 @@ static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
                                                                   static_cast<const T*>(p.coeff_in),
                                                                   static_cast<T*>(p.psi_out));
   return cudaGetLastError();
+}
+
+// Bands per lane: 1 in double; in float 4 (up to 20 stored values per point) or 2, when the band rows
+// are aligned for vector loads (nbands a multiple of BPL, 16-byte aligned psi) and, for the expansion,
+// the row buffer [Nx][32 BPL] fits in shared memory.
+template <typename T, int N>
+static cudaError_t usu_run_n(int op, const UsuLaunch& p) {
+  if constexpr (sizeof(T) == 4) {
+    const void* ps = op == 1 ? p.psi_in : (const void*)p.psi_out;
+    const bool aligned = ((uintptr_t)ps & 15u) == 0;
+    const int want = N <= 20 ? 4 : 2;
+    const size_t row_limit = 200 * 1024;
+    auto fits = [&](int bpl) {
+      return p.g.nbands % bpl == 0 && aligned &&
+             (op == 1 || (size_t)p.g.n[0] * kWarp * bpl * sizeof(T) <= row_limit);
+    };
+    if constexpr (N <= 20) {
+      if (want == 4 && fits(4)) return usu_run_nb<T, N, 4>(op, p);
+    }
+    if (fits(2)) return usu_run_nb<T, N, 2>(op, p);
+  }
+  return usu_run_nb<T, N, 1>(op, p);
 }
 
 template <typename T>

@@ -70,24 +70,26 @@ def test_usu_rejects_unsupported_nproj():
             api.usu_build(np.zeros((1, 3)) + 1.0, [1.0], 4, 16, (16, 16, 16), 0.25, True, nproj=nproj)
 
 
-def test_usu_float():
+@pytest.mark.parametrize("nbands,nproj", [(40, 18), (42, 18), (45, 35), (40, 56)])
+def test_usu_float(nbands, nproj):
     """Float stored projectors (the paper's float column of Table 2): projection and expansion against
     the FP64 oracle run on the same FP32-rounded inputs; the 32^3-term sums in FP32 bound the error by
-    a few 1e-6 norm-wise."""
+    a few 1e-6 norm-wise.  40 / 42 / 45 bands take 4, 2 and 1 bands per lane."""
     require_gpu()
     import torch
     from paper_1905_00480_gb300 import api
-    rng = np.random.default_rng(202)
-    grid, h, numax, cube, nproj = (36, 40, 32), 0.2, 4, 16, 18
+    rng = np.random.default_rng(202 + nbands)
+    grid, h, cube = (36, 40, 32), 0.2, 16
+    numax = next(v for v in range(6) if oracle.nstates(v) >= nproj)
     pos, sig = workloads.random_atoms(rng, 5, tuple(n * h for n in grid), True, min_sep=1.0)
-    psi = rng.standard_normal((32, 40, 36, 40)).astype(np.float32)
-    c = rng.standard_normal((5, nproj, 40)).astype(np.float32)
+    psi = rng.standard_normal((32, 40, 36, nbands)).astype(np.float32)
+    c = rng.standard_normal((5, nproj, nbands)).astype(np.float32)
     proj = api.usu_build(pos, sig, numax, cube, grid, h, True, nproj=nproj, dtype=torch.float32)
     psi_d = torch.from_numpy(psi).cuda()
     got = api.usu_project(psi_d, proj, pos, sig, numax, cube, h, True).double().cpu().numpy()
     ref = oracle.project(grid, h, True, psi.astype(np.float64), pos, sig, numax, cube)[:, :nproj]
     assert rel_norm(got, ref) <= 2e-5
-    cfull = np.zeros((5, oracle.nstates(numax), 40))
+    cfull = np.zeros((5, oracle.nstates(numax), nbands))
     cfull[:, :nproj] = c
     api.usu_add(psi_d, torch.from_numpy(c).cuda(), proj, pos, sig, numax, cube, h, True)
     ref2 = oracle.add(grid, h, True, psi.astype(np.float64), pos, sig, numax, cube, cfull)
