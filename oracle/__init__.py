@@ -69,7 +69,12 @@ def _load():
                                                    ctypes.c_int, dp, dp]
             lib.oracle_expand_points.argtypes = common + [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
                                                           ctypes.c_int, dp, ctypes.c_int, i64p, dp]
-            for f in (lib.oracle_project, lib.oracle_add, lib.oracle_forces, lib.oracle_expand_points):
+            lib.oracle_project_bloch.argtypes = [ip, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp,
+                                                 ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_add_bloch.argtypes = [ip, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp,
+                                             ctypes.c_int, ctypes.c_int, dp]
+            for f in (lib.oracle_project, lib.oracle_add, lib.oracle_forces, lib.oracle_expand_points,
+                      lib.oracle_project_bloch, lib.oracle_add_bloch):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -192,4 +197,40 @@ def forces(grid, h, periodic, psi, pos, sigma, numax, cube, dEdc):
     rc = _load().oracle_forces(_grid(n), float(h), int(bool(periodic)), _dp(psi), B, A, _dp(pos), _dp(sigma),
                                int(numax), int(cube), _dp(dEdc), _dp(out))
     _check(rc, "forces")
+    return out
+
+
+def project_bloch(grid, h, kvec, psi, pos, sigma, numax, cube):
+    """Bloch projection on a periodic grid: psi complex [Nz][Ny][Nx][B]; returns complex [A][N][B] with
+    c = h^3 sum_i Psi_k(u_i) e^{+i k.T_i} psi[j(i)], T_i the lattice translation of cube point i."""
+    n = [int(v) for v in grid]
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    B = psi.shape[-1]
+    assert psi.shape == (n[2], n[1], n[0], B), psi.shape
+    pos = _f64(pos).reshape(-1, 3)
+    sigma = _f64(sigma).reshape(-1)
+    A = pos.shape[0]
+    N = nstates(numax)
+    c = np.zeros((A, N, B), dtype=np.complex128)
+    k = _f64(kvec).reshape(3)
+    rc = _load().oracle_project_bloch(_grid(n), float(h), _dp(k), _dp(psi.view(np.float64)), B, A, _dp(pos),
+                                      _dp(sigma), int(numax), int(cube), _dp(c.view(np.float64)))
+    _check(rc, "project_bloch")
+    return c
+
+
+def add_bloch(grid, h, kvec, psi, pos, sigma, numax, cube, coeff):
+    """Returns psi + sum_a sum_k c Psi_k e^{-i k.T} (complex; the input is not modified)."""
+    n = [int(v) for v in grid]
+    out = np.array(psi, dtype=np.complex128, copy=True, order="C")
+    B = out.shape[-1]
+    pos = _f64(pos).reshape(-1, 3)
+    sigma = _f64(sigma).reshape(-1)
+    A = pos.shape[0]
+    coeff = np.ascontiguousarray(coeff, dtype=np.complex128)
+    assert coeff.shape == (A, nstates(numax), B)
+    k = _f64(kvec).reshape(3)
+    rc = _load().oracle_add_bloch(_grid(n), float(h), _dp(k), _dp(out.view(np.float64)), B, A, _dp(pos),
+                                  _dp(sigma), int(numax), int(cube), _dp(coeff.view(np.float64)))
+    _check(rc, "add_bloch")
     return out

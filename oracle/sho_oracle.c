@@ -137,6 +137,7 @@ typedef struct {
   double* dpoly[3];  /* [numax+1][cube]: d/du of (N_n H_n(u/sigma) exp(-u^2/2s^2)) / exp(-u^2/2s^2) */
   double* gauss;     /* [cube^3] */
   int64_t* gidx;     /* [cube^3] */
+  double shift[3][256]; /* lattice translation (o + i - j) h of cube point i along each axis */
 } atom_samples;
 
 static void atom_samples_init(atom_samples* s, const int n[3], double h, int periodic, const double X[3],
@@ -153,6 +154,7 @@ static void atom_samples_init(atom_samples* s, const int n[3], double h, int per
     for (int i = 0; i < cube; i++) {
       u[d][i] = (double)(o + i) * h - X[d];
       j[d][i] = grid_index(o, i, n[d], periodic);
+      s->shift[d][i] = j[d][i] < 0 ? 0.0 : (double)(o + i - j[d][i]) * h;
       long double xi = (long double)u[d][i] / sg;
       for (int m = 0; m <= numax; m++) {
         long double nm = norm_ld(m, sigma);
@@ -392,6 +394,105 @@ int oracle_forces(const int n[3], double h, int periodic, const double* psi, int
     free(P);
     atom_samples_free(&s);
   }
+  free(nxyz);
+  return 0;
+}
+
+
+/* ---------------------------------------------------------------------------------------------
+ * Bloch (complex) wave functions on a periodic grid.  psi and coeff hold complex numbers as (re, im)
+ * pairs: psi[j][b][2], coeff[a][k][b][2].  A cube point i that lies outside the cell maps to grid point
+ * j(i) = r_i - T_i with the lattice translation T_i; the Bloch condition psi(r + T) = e^{i k.T} psi(r)
+ * gives the value there, so
+ *   projection  c[a][k][b] = h^3 sum_i Psi_k(u_i) e^{+i k.T_i} psi[j(i)][b]
+ *   expansion   psi[j][b] += sum_a sum_{i: j(i)=j} sum_k c[a][k][b] Psi_k(u_i) e^{-i k.T_i}
+ * (adjoint in the complex inner product weighted by h^3; k = 0 gives the real transform of the real
+ * and imaginary parts). */
+int oracle_project_bloch(const int n[3], double h, const double kvec[3], const double* psi, int nbands, int natoms,
+                         const double* pos, const double* sigma, int numax, int cube, double* coeff) {
+  int err = check_args(n, h, natoms, numax, cube, nbands);
+  if (err) return err;
+  int N = oracle_nstates(numax);
+  int* nxyz = (int*)malloc(sizeof(int) * 3 * N);
+  oracle_basis(numax, nxyz);
+  const double h3 = h * h * h;
+  const int64_t c3 = (int64_t)cube * cube * cube;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int a = 0; a < natoms; a++) {
+    atom_samples s;
+    atom_samples_init(&s, n, h, 1, pos + 3 * a, sigma[a], numax, cube, 0);
+    double* P = (double*)malloc(sizeof(double) * c3);
+    double* cph = (double*)malloc(sizeof(double) * c3);
+    double* sph = (double*)malloc(sizeof(double) * c3);
+    for (int iz = 0; iz < cube; iz++)
+      for (int iy = 0; iy < cube; iy++)
+        for (int ix = 0; ix < cube; ix++) {
+          int64_t i = ((int64_t)iz * cube + iy) * cube + ix;
+          double th = kvec[0] * s.shift[0][ix] + kvec[1] * s.shift[1][iy] + kvec[2] * s.shift[2][iz];
+          cph[i] = cos(th);
+          sph[i] = sin(th);
+        }
+    double* acc = (double*)malloc(sizeof(double) * 2 * (nbands > 0 ? nbands : 1));
+    for (int k = 0; k < N; k++) {
+      sample_projector(&s, nxyz[3 * k], nxyz[3 * k + 1], nxyz[3 * k + 2], P);
+      for (int b = 0; b < 2 * nbands; b++) acc[b] = 0.0;
+      for (int64_t i = 0; i < c3; i++) {
+        const double* row = psi + s.gidx[i] * 2 * nbands;
+        const double wr = P[i] * cph[i], wi = P[i] * sph[i];
+        for (int b = 0; b < nbands; b++) {
+          const double pr = row[2 * b], pi = row[2 * b + 1];
+          acc[2 * b] += wr * pr - wi * pi;
+          acc[2 * b + 1] += wr * pi + wi * pr;
+        }
+      }
+      double* out = coeff + ((int64_t)a * N + k) * 2 * nbands;
+      for (int b = 0; b < 2 * nbands; b++) out[b] = h3 * acc[b];
+    }
+    free(acc);
+    free(sph);
+    free(cph);
+    free(P);
+    atom_samples_free(&s);
+  }
+  free(nxyz);
+  return 0;
+}
+
+int oracle_add_bloch(const int n[3], double h, const double kvec[3], double* psi, int nbands, int natoms,
+                     const double* pos, const double* sigma, int numax, int cube, const double* coeff) {
+  int err = check_args(n, h, natoms, numax, cube, nbands);
+  if (err) return err;
+  if (cube > n[0] || cube > n[1] || cube > n[2]) return -3;
+  int N = oracle_nstates(numax);
+  int* nxyz = (int*)malloc(sizeof(int) * 3 * N);
+  oracle_basis(numax, nxyz);
+  const int64_t c3 = (int64_t)cube * cube * cube;
+  double* P = (double*)malloc(sizeof(double) * c3 * N);
+  for (int a = 0; a < natoms; a++) {
+    atom_samples s;
+    atom_samples_init(&s, n, h, 1, pos + 3 * a, sigma[a], numax, cube, 0);
+    for (int k = 0; k < N; k++) sample_projector(&s, nxyz[3 * k], nxyz[3 * k + 1], nxyz[3 * k + 2], P + k * c3);
+    const double* ca = coeff + (int64_t)a * N * 2 * nbands;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < c3; i++) {
+      const int ix = (int)(i % cube), iy = (int)((i / cube) % cube), iz = (int)(i / ((int64_t)cube * cube));
+      const double th = kvec[0] * s.shift[0][ix] + kvec[1] * s.shift[1][iy] + kvec[2] * s.shift[2][iz];
+      const double cr = cos(th), ci = -sin(th);  /* e^{-i k.T} */
+      double* row = psi + s.gidx[i] * 2 * nbands;
+      for (int b = 0; b < nbands; b++) {
+        double sr = 0.0, si = 0.0;
+        for (int k = 0; k < N; k++) {
+          const double w = P[k * c3 + i];
+          sr += ca[((int64_t)k * nbands + b) * 2] * w;
+          si += ca[((int64_t)k * nbands + b) * 2 + 1] * w;
+        }
+        row[2 * b] += sr * cr - si * ci;
+        row[2 * b + 1] += sr * ci + si * cr;
+      }
+    }
+    atom_samples_free(&s);
+  }
+  free(P);
   free(nxyz);
   return 0;
 }
