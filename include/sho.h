@@ -188,6 +188,26 @@ int sho_apply_nonlocal(sho_handle* handle, const sho_grid* grid, const void* psi
                        const void* D, void* hpsi, void* stream);
 
 /* ----------------------------------------------------------------------------------------------
+ * Bloch (complex) wave functions on a periodic grid, FP64.  The SHO states span functions R^3 -> C
+ * (Sec. 2.5); for psi(r + T) = e^{i k.T} psi(r) a cube point i outside the cell maps to grid point
+ * j(i) = r_i - T_i with the lattice translation T_i = (o + i - j(i)) h (per axis), and
+ *     sho_project_bloch   coeff[a][k][b] = h^3 sum_i Psi_k(u_i) e^{+i k.T_i} psi[j(i)][b]
+ *     sho_add_bloch       psi[j][b] += sum_a sum_{i: j(i)=j} sum_k coeff[a][k][b] Psi_k(u_i) e^{-i k.T_i}
+ * (adjoint in the h^3-weighted complex inner product; k = 0 is the real transform of the real and
+ * imaginary parts).  The phase rides on the 1D tables, so the three-pass form is kept.
+ *   grid   periodic (SHO_ERR_ARG otherwise); sho_add_bloch needs n[0] <= 448
+ *   kvec   host double[3], the Bloch vector in inverse length units
+ *   psi    device complex double [n[2]][n[1]][n[0]][nbands] as (re, im) pairs
+ *   coeff  device complex double [natoms][sho_nstates(numax)][nbands] as (re, im) pairs
+ * numax <= 7 (SHO_ERR_NUMAX).  Deterministic (fixed summation order, no atomics).
+ */
+int sho_project_bloch(sho_handle* handle, const sho_grid* grid, const double* kvec, const void* psi, int nbands,
+                      int natoms, const double* pos, const double* sigma, int numax, int cube, void* coeff,
+                      void* stream);
+int sho_add_bloch(sho_handle* handle, const sho_grid* grid, const double* kvec, const void* coeff, int nbands,
+                  int natoms, const double* pos, const double* sigma, int numax, int cube, void* psi, void* stream);
+
+/* ----------------------------------------------------------------------------------------------
  * Cartesian <-> radial SHO coefficients -- eq. SHO-transform-Cartesian-to-radial (Sec. 2.4): within an
  * energy shell nx + ny + nz = 2 nr + l the Cartesian states (Sec. 2.2) and the radial states
  * Psi_{nr l m} = R_{nr l}(r) Y_{l m} (eq. SHO-eigenstate-radial, Sec. 2.3) span the same space, related

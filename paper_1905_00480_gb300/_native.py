@@ -58,6 +58,8 @@ SIGNATURES = {
     "sho_set_strict": (_I, [_VP, _I]),
     "sho_sync": (_I, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),
+    "sho_project_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP]),
+    "sho_add_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP]),
     "sho_radial_labels": (_I, [_I, _IP, _IP, _IP]),
     "sho_radial_matrix": (_I, [_I, _DP]),
     "sho_radial_transform": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I, _VP]),

@@ -143,6 +143,58 @@ def project_path(psi: torch.Tensor, numax: int, cube: int, h: float, periodic: b
     return {1: "atom", 2: "plane"}[r]
 
 
+def _grid_complex(psi: torch.Tensor, h: float):
+    g = N.sho_grid()
+    g.n[0], g.n[1], g.n[2] = int(psi.shape[2]), int(psi.shape[1]), int(psi.shape[0])
+    g.h, g.periodic = float(h), 1
+    return g
+
+
+def _check_complex(t: torch.Tensor, what: str, dims: int):
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != torch.complex128 or t.dim() != dims:
+        raise ValueError(f"{what} must be a contiguous CUDA complex128 tensor with {dims} dimensions")
+
+
+def project_bloch(psi: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h: float, out: torch.Tensor = None,
+                  handle: Handle = None, stream=None) -> torch.Tensor:
+    """sho_project_bloch: complex Bloch psi [Nz][Ny][Nx][B] (periodic grid) -> complex [A][N][B]."""
+    _check_complex(psi, "psi", 4)
+    pos_h = _host_f64(pos, 3)
+    sig_h = _host_f64(sigma).reshape(-1)
+    k = _host_f64(kvec).reshape(3)
+    A, B = pos_h.shape[0], psi.shape[3]
+    if out is None:
+        out = torch.empty((A, nstates(numax), B), dtype=torch.complex128, device=psi.device)
+    _check_complex(out, "out", 3)
+    hd = handle or default_handle(psi.device.index or 0)
+    g = _grid_complex(psi, h)
+    st = N.lib().sho_project_bloch(hd.ptr, ctypes.byref(g), _dp(k), ctypes.c_void_p(psi.data_ptr()), B, A,
+                                   _dp(pos_h), _dp(sig_h), int(numax), int(cube), ctypes.c_void_p(out.data_ptr()),
+                                   _stream_ptr(psi, stream))
+    N.check(st, "sho_project_bloch")
+    return out
+
+
+def add_bloch(psi: torch.Tensor, coeff: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h: float,
+              handle: Handle = None, stream=None) -> torch.Tensor:
+    """sho_add_bloch (in place): psi += sum_a sum_k c Psi_k e^{-i k.T} for complex Bloch psi."""
+    _check_complex(psi, "psi", 4)
+    _check_complex(coeff, "coeff", 3)
+    pos_h = _host_f64(pos, 3)
+    sig_h = _host_f64(sigma).reshape(-1)
+    k = _host_f64(kvec).reshape(3)
+    A, B = pos_h.shape[0], psi.shape[3]
+    if tuple(coeff.shape) != (A, nstates(numax), B):
+        raise ValueError("coeff must be [A][N][B]")
+    hd = handle or default_handle(psi.device.index or 0)
+    g = _grid_complex(psi, h)
+    st = N.lib().sho_add_bloch(hd.ptr, ctypes.byref(g), _dp(k), ctypes.c_void_p(coeff.data_ptr()), B, A, _dp(pos_h),
+                               _dp(sig_h), int(numax), int(cube), ctypes.c_void_p(psi.data_ptr()),
+                               _stream_ptr(psi, stream))
+    N.check(st, "sho_add_bloch")
+    return psi
+
+
 def radial_labels(numax: int):
     """sho_radial_labels: (nr, l, m) of the radial SHO states in the library's order."""
     n = nstates(numax)

@@ -574,6 +574,73 @@ int sho_radial_transform(sho_handle* h, int natoms, int numax, int nbands, const
   return end_call(h, s);
 }
 
+static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, int op, const void* src, void* dst,
+                      int nbands, int natoms, const double* pos, const double* sigma, int numax, int cube,
+                      void* stream) {
+  if (!h) return SHO_ERR_ARG;
+  SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, kTcMaxNumax));
+  if (!grid->periodic || !kvec) return SHO_ERR_ARG;
+  for (int d = 0; d < 3; d++)
+    if (!std::isfinite(kvec[d])) return SHO_ERR_ARG;
+  if (op == 1 && grid->n[0] > kBlochMaxNx) return SHO_ERR_ARG;
+  SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  if (natoms == 0 || nbands == 0) return SHO_OK;
+  if (!src || !dst) return SHO_ERR_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return SHO_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  const int N = nstates(numax), NP = numax + 1;
+  const int zsplit = op == 0 ? choose_zsplit(natoms, nbands, cube, h->sms) : 1;
+  std::vector<int> ptr, list;
+  if (op == 1) plane_lists(grid, at, cube, ptr, list);
+  Carve cv;
+  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
+  const size_t o_ptr = cv.take(std::max<size_t>(1, ptr.size()) * sizeof(int));
+  const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
+  const size_t o_tab = cv.take((size_t)natoms * 3 * NP * cube * 2 * sizeof(double));
+  const size_t work = op == 0 ? (size_t)zsplit * natoms * N * nbands : (size_t)natoms * cube * npairs(numax) * nbands;
+  const size_t o_work = cv.take(work * 2 * sizeof(double));
+  SHO_TRY(begin_call(h, s));
+  SHO_TRY(ensure_workspace(h, cv.off));
+  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
+  if (op == 1) {
+    SHO_TRY(upload(h, o_ptr, ptr.data(), ptr.size() * sizeof(int), s));
+    SHO_TRY(upload(h, o_list, list.data(), list.size() * sizeof(int), s));
+  }
+  char* ws = static_cast<char*>(h->ws);
+  BlochLaunch L = {};
+  L.g = make_grid(grid, cube, nbands);
+  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  L.natoms = natoms;
+  L.numax = numax;
+  for (int d = 0; d < 3; d++) L.k[d] = kvec[d];
+  L.op = op;
+  L.zsplit = zsplit;
+  L.psi_in = op == 0 ? static_cast<const double*>(src) : nullptr;
+  L.coeff_out = op == 0 ? static_cast<double*>(dst) : nullptr;
+  L.coeff_in = op == 1 ? static_cast<const double*>(src) : nullptr;
+  L.psi_out = op == 1 ? static_cast<double*>(dst) : nullptr;
+  L.plane_ptr = reinterpret_cast<const int*>(ws + o_ptr);
+  L.plane_atoms = reinterpret_cast<const int*>(ws + o_list);
+  L.tab = reinterpret_cast<double*>(ws + o_tab);
+  L.work = reinterpret_cast<double*>(ws + o_work);
+  L.stream = s;
+  if (launch_bloch(L) != cudaSuccess) return SHO_ERR_CUDA;
+  return end_call(h, s);
+}
+
+int sho_project_bloch(sho_handle* h, const sho_grid* grid, const double* kvec, const void* psi, int nbands,
+                      int natoms, const double* pos, const double* sigma, int numax, int cube, void* coeff,
+                      void* stream) {
+  return bloch_call(h, grid, kvec, 0, psi, coeff, nbands, natoms, pos, sigma, numax, cube, stream);
+}
+
+int sho_add_bloch(sho_handle* h, const sho_grid* grid, const double* kvec, const void* coeff, int nbands, int natoms,
+                  const double* pos, const double* sigma, int numax, int cube, void* psi, void* stream) {
+  return bloch_call(h, grid, kvec, 1, coeff, psi, nbands, natoms, pos, sigma, numax, cube, stream);
+}
+
 int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int numax, int cube,
                      sho_prec prec, sho_dtype coeff_dtype) {
   if (!grid) return SHO_ERR_ARG;

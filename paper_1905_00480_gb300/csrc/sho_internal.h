@@ -143,6 +143,28 @@ void radial_csr(int numax, int direction, std::vector<int>& rowp, std::vector<in
 cudaError_t launch_radial(int natoms, int N, int nbands, sho_dtype dt, const int* rowp, const int* col,
                           const void* val, const void* in, void* out, cudaStream_t s);
 
+// Bloch (complex) projection / expansion, FP64 (sho_bloch.cu).  Complex arrays hold (re, im) pairs.
+struct BlochLaunch {
+  GridDev g;                // periodic
+  const AtomDev* atoms;
+  int natoms;
+  int numax;
+  double k[3];              // Bloch vector
+  int op;                   // 0: project, 1: expand
+  int zsplit;               // projection: cube z-slabs per (atom, band tile)
+  const double* psi_in;     // project: psi [Nz][Ny][Nx][B][2]
+  double* coeff_out;        // project: [A][N][B][2]
+  const double* coeff_in;   // expand: [A][N][B][2]
+  double* psi_out;          // expand: psi, read-modify-write
+  const int* plane_ptr;     // expand: per-plane atom lists (CSR), ascending
+  const int* plane_atoms;
+  double* tab;              // [A][3][numax+1][C][2]
+  double* work;             // project: [zsplit][A][N][B][2]; expand: [A][C][P][B][2]
+  cudaStream_t stream;
+};
+cudaError_t launch_bloch(const BlochLaunch& p);
+constexpr int kBlochMaxNx = 448;  // the expansion keeps one grid row of 32 complex bands in shared memory
+
 // Kernel launchers (return a CUDA error code).
 cudaError_t launch_usu(int op, const UsuLaunch& p);
 bool usu_supported_nproj(int n);

@@ -1,0 +1,80 @@
+"""Bloch (complex) projection and expansion on the GPU against the oracle (FP64, 1e-12)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import TOL_FP64, assert_coeff_close, rel_norm, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(seed, grid, h, natoms, nbands):
+    rng = np.random.default_rng(seed)
+    L = np.array(grid) * h
+    pos, sig = workloads.random_atoms(rng, natoms, tuple(L), True, min_sep=1.0)
+    pos[0] = [0.3 * h + 0.01, L[1] - 0.4 * h, 0.6 * h]  # a cube that wraps on every axis
+    psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands)) + 1j * rng.standard_normal(
+        (grid[2], grid[1], grid[0], nbands))
+    return rng, pos, sig, psi
+
+
+@pytest.mark.parametrize("numax,nbands", [(3, 5), (5, 40), (7, 33)])
+def test_bloch_project_and_add(numax, nbands):
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, cube = (40, 36, 34), 0.2, 32
+    rng, pos, sig, psi = _case(910 + numax, grid, h, 5, nbands)
+    k = np.array([0.9, -0.35, 1.7])
+    psi_d = torch.from_numpy(psi).cuda()
+    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h).cpu().numpy()
+    ref = oracle.project_bloch(grid, h, k, psi, pos, sig, numax, cube)
+    assert_coeff_close(got.view(np.float64), ref.view(np.float64), TOL_FP64)
+    coef = rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)
+    out = psi_d.clone()
+    api.add_bloch(out, torch.from_numpy(coef).cuda(), k, pos, sig, numax, cube, h)
+    ref2 = oracle.add_bloch(grid, h, k, psi, pos, sig, numax, cube, coef)
+    assert rel_norm((out.cpu().numpy() - psi).view(np.float64), (ref2 - psi).view(np.float64)) <= TOL_FP64
+
+
+def test_bloch_zero_k_matches_real_path_and_adjoint():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, numax, cube = (40, 36, 34), 0.2, 5, 32
+    rng, pos, sig, psi = _case(920, grid, h, 4, 16)
+    psi_d = torch.from_numpy(psi).cuda()
+    c0 = api.project_bloch(psi_d, [0, 0, 0], pos, sig, numax, cube, h)
+    cr = api.project(psi_d.real.contiguous(), pos, sig, numax, cube, h, True, prec="fp64")
+    ci = api.project(psi_d.imag.contiguous(), pos, sig, numax, cube, h, True, prec="fp64")
+    assert rel_norm(c0.real.cpu().numpy(), cr.cpu().numpy()) <= TOL_FP64
+    assert rel_norm(c0.imag.cpu().numpy(), ci.cpu().numpy()) <= TOL_FP64
+    # adjoint identity on the GPU path, k != 0
+    k = [1.1, 0.4, -0.8]
+    c = api.project_bloch(psi_d, k, pos, sig, numax, cube, h)
+    coef = torch.from_numpy(rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).cuda()
+    ec = api.add_bloch(torch.zeros_like(psi_d), coef, k, pos, sig, numax, cube, h)
+    lhs = torch.vdot(c.flatten(), coef.flatten()).item()
+    rhs = h ** 3 * torch.vdot(psi_d.flatten(), ec.flatten()).item()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_bloch_rejects_open_grid():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api, ShoError
+    from paper_1905_00480_gb300 import _native as N
+    import ctypes
+    psi = torch.zeros((16, 16, 16, 2), dtype=torch.complex128, device="cuda")
+    out = torch.zeros((1, 4, 2), dtype=torch.complex128, device="cuda")
+    g = N.sho_grid()
+    g.n[0] = g.n[1] = g.n[2] = 16
+    g.h, g.periodic = 0.25, 0
+    k = np.zeros(3)
+    pos = np.array([[2.0, 2.0, 2.0]])
+    sig = np.array([1.0])
+    st = N.lib().sho_project_bloch(api.default_handle(0).ptr, ctypes.byref(g), k.ctypes.data_as(N._DP),
+                                   ctypes.c_void_p(psi.data_ptr()), 2, 1, pos.ctypes.data_as(N._DP),
+                                   sig.ctypes.data_as(N._DP), 1, 16, ctypes.c_void_p(out.data_ptr()), None)
+    assert st != 0
