@@ -419,6 +419,30 @@ def same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream):
     out["fp32_cuda_cores"] = {"value": round(bytes32 / (ms32 * 1e-3) / 1e9, 3), "unit": "GB/s",
                               "ms_per_step": round(ms32, 4), "note": "same workload with psi and coefficients in FP32"}
     del psi32, h32
+    # complex Bloch wave functions (FP64): 32 complex bands of the same geometry, Bloch vector k
+    B = 32
+    g = torch.Generator(device=psi.device)
+    g.manual_seed(w.seed + 7)
+    nx, ny, nz = w.grid
+    zc = torch.complex(torch.randn((nz, ny, nx, B), generator=g, device=psi.device, dtype=torch.float64),
+                       torch.randn((nz, ny, nx, B), generator=g, device=psi.device, dtype=torch.float64))
+    cz = torch.complex(torch.randn((w.natoms, cin.shape[1], B), generator=g, device=psi.device, dtype=torch.float64),
+                       torch.randn((w.natoms, cin.shape[1], B), generator=g, device=psi.device, dtype=torch.float64))
+    oz = torch.empty_like(cz)
+    hz = torch.zeros_like(zc)
+    kvec = [0.9, -0.35, 1.7]
+
+    def bloch_step():
+        api.project_bloch(zc, kvec, pos, sig, w.numax, w.cube, w.h, out=oz, handle=handle, stream=stream)
+        api.add_bloch(hz, cz, kvec, pos, sig, w.numax, w.cube, w.h, handle=handle, stream=stream)
+
+    msb = _time_steps(stream, bloch_step, warmup=1, steps=3)
+    bytes_b = (alg["bytes_prj"] + alg["bytes_add"]) * 2 * B // w.nbands
+    out["bloch_complex_fp64"] = {"value": round(bytes_b / (msb * 1e-3) / 1e9, 3), "unit": "GB/s",
+                                 "ms_per_step": round(msb, 4),
+                                 "note": f"{B} complex128 bands, k = {kvec}: Bloch projection + expansion (4 DFMA "
+                                         "per complex FMA)"}
+    del zc, cz, oz, hz
     torch.cuda.empty_cache()
     return out
 
