@@ -294,9 +294,12 @@ constexpr int kXSeg = 32;            // x points per tile
 template <int NU>
 struct BlkSmem {
   static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 3) & ~3;
-  // per buffer: T2 slice [P][32] + x table [C][NPX] (x-major) + y table [NP][C]
+  // staged x table row stride: 12 floats for 8 states, so that the B-fragment loads of a quarter warp
+  // (8 x points x 4 states) hit 32 distinct banks
+  static constexpr int NPXS = NPX == 8 ? 12 : NPX;
+  // per buffer: T2 slice [P][32] + x table [C][NPXS] (x-major) + y table [NP][C]
   __host__ __device__ static size_t buf_floats(int cube) {
-    return (size_t)P * 32 + (size_t)NPX * cube + (size_t)NP * cube;
+    return (size_t)P * 32 + (size_t)NPXS * cube + (size_t)NP * cube;
   }
   static size_t bytes(int cube, int max_plane) {
     return (2 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * 4;
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
                                                                     const float* __restrict__ t2,
                                                                     TP* __restrict__ psi) {
   using BS = Basis<NU>;
-  constexpr int NP = BS::NP, P = BS::P, NPX = BlkSmem<NU>::NPX;
+  constexpr int NP = BS::NP, P = BS::P, NPX = BlkSmem<NU>::NPX, NPXS = BlkSmem<NU>::NPXS;
   constexpr bool TC = MODE != kSimt;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA, NB = TcFrag<TM>::NB;
@@ -377,11 +380,13 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
                                                            : (const void*)t2, nb);
     }
     const float* src_x = txm + (size_t)a * C * NPX;             // x table, x-major [C][NPX]
-    for (int q = tid; q < C * NPX / 4; q += kRowsPerBlk * kWarp)
-      cp_async16(smem_u32(dst + P * 32 + q * 4), src_x + q * 4, 16);
+    for (int q = tid; q < C * NPX / 4; q += kRowsPerBlk * kWarp) {
+      const int ix = q / (NPX / 4), part = q - ix * (NPX / 4);   // staged with row stride NPXS
+      cp_async16(smem_u32(dst + P * 32 + ix * NPXS + part * 4), src_x + q * 4, 16);
+    }
     const float* src_y = tables + (size_t)a * 2 * NP * C + (size_t)NP * C;  // y table [NP][C]
     for (int q = tid; q < NP * C / 4; q += kRowsPerBlk * kWarp)
-      cp_async16(smem_u32(dst + P * 32 + C * NPX + q * 4), src_y + q * 4, 16);
+      cp_async16(smem_u32(dst + P * 32 + C * NPXS + q * 4), src_y + q * 4, 16);
   };
 
   // register tile: 32 x points of this warp's row, 32 bands
@@ -444,8 +449,8 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
     cp_async_wait<1>();
     __syncthreads();
     const float* t2s = bufs + (size_t)buf * bufsz;
-    const float* txs = t2s + P * 32;       // [C][NPX]
-    const float* tys = txs + NPX * C;      // [NP][C]
+    const float* txs = t2s + P * 32;       // [C][NPXS]
+    const float* tys = txs + NPXS * C;     // [NP][C]
     const AtomDev at = atoms[a];
     int iy = y - at.o[1];
     if (g.periodic) {
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
           if (g.periodic && ix >= Nx) ix -= Nx;
           if (ix >= 0 && ix < C) {
             float s = accr[x];
-            const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
+            const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPXS);
 #pragma unroll
             for (int q = 0; q < NPX / 4; q++) {
               const float4 f = f4[q];
@@ -501,7 +506,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
             av[m][i] = t1s[k * 36 + 16 * m + mm];
           }
         __syncwarp();
-        const float ls = tc_lo_scale<TM>();
+        constexpr bool SPLIT = TM == TcMode::X3TF32 || TM == TcMode::SPLIT16;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
           float bv[NB];
@@ -511,17 +516,19 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
             b_coord<TM>(i, gq, tq, k, n);
             int ix = dx + 8 * j + n;
             if (g.periodic && ix >= Nx) ix -= Nx;
-            bv[i] = (k <= NU && ix >= 0 && ix < C) ? txs[ix * NPX + k] : 0.0f;
+            bv[i] = (k <= NU && ix >= 0 && ix < C) ? txs[ix * NPXS + k] : 0.0f;
           }
           const BFrag<TM> bfr = make_bfrag<TM>(bv);
 #pragma unroll
           for (int m = 0; m < 2; m++) {
-            float d[4], dl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int e = 0; e < 4; e++) d[e] = accr[(j * 2 + m) * 4 + e];
+            float(&d)[4] = *reinterpret_cast<float(*)[4]>(&accr[(j * 2 + m) * 4]);
+            float dl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             tc_product<TM>(d, dl, av[m], bfr);
+            if constexpr (SPLIT) {
+              const float ls = tc_lo_scale<TM>();
 #pragma unroll
-            for (int e = 0; e < 4; e++) accr[(j * 2 + m) * 4 + e] = d[e] + ls * dl[e];
+              for (int e = 0; e < 4; e++) d[e] = fmaf(ls, dl[e], d[e]);
+            }
           }
         }
       }
