@@ -315,8 +315,9 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
                                                                     const float* __restrict__ t2,
                                                                     TP* __restrict__ psi) {
   using BS = Basis<NU>;
-  constexpr int NP = BS::NP, P = BS::P, NPX = BlkSmem<NU>::NPX, NPXS = BlkSmem<NU>::NPXS;
   constexpr bool TC = MODE != kSimt;
+  // x-table row stride in shared memory: padded for the tensor-core B-fragment loads only
+  constexpr int NP = BS::NP, P = BS::P, NPX = BlkSmem<NU>::NPX, NPXS = TC ? BlkSmem<NU>::NPXS : NPX;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA, NB = TcFrag<TM>::NB;
   static_assert(!TC || K >= NP, "one MMA K step covers the states");
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
     __syncthreads();
     const float* t2s = bufs + (size_t)buf * bufsz;
     const float* txs = t2s + P * 32;       // [C][NPXS]
-    const float* tys = txs + NPXS * C;     // [NP][C]
+    const float* tys = txs + NPXS * C;     // [NP][C] (the buffer is sized for the padded stride)
     const AtomDev at = atoms[a];
     int iy = y - at.o[1];
     if (g.periodic) {
