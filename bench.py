@@ -227,35 +227,63 @@ def run_ours(args, ws, rank, local):
     bytes_step = alg["bytes_prj"] + alg["bytes_add"]
     value = ws * bytes_step / (ms_step * 1e-3) / 1e9
 
-    # end to end through the public API: pinned host psi and coefficients in, expansion result out
+    # end to end through the public API: pinned host psi and coefficients in, expansion result out.  Steps
+    # are pipelined over two device buffer sets on three streams (copy in, compute, copy out), as a caller
+    # streaming many steps would drive it: step i's copies overlap step i-1's kernels; every step's copies
+    # lie inside the timed region.
     psi_h = torch.empty(psi.shape, dtype=psi.dtype, pin_memory=True)
     psi_h.copy_(psi)
     cin_h = torch.empty(cin.shape, dtype=cin.dtype, pin_memory=True)
     cin_h.copy_(cin)
-    out_h = torch.empty(psi.shape, dtype=psi.dtype, pin_memory=True)
-    psi_d = torch.empty_like(psi)
-    cin_d = torch.empty_like(cin)
+    out_h = [torch.empty(psi.shape, dtype=psi.dtype, pin_memory=True) for _ in range(2)]
+    del hpsi
+    psi_d = [psi if i == 0 else torch.empty_like(psi) for i in range(2)]
+    cin_d = [torch.empty_like(cin) for _ in range(2)]
+    hps = [torch.empty_like(psi) for _ in range(2)]
+    co = [coeff, torch.empty_like(coeff)]
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    s_cmp = stream
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    started = [False, False]
 
-    def e2e_step():
-        psi_d.copy_(psi_h, non_blocking=True)
-        cin_d.copy_(cin_h, non_blocking=True)
-        api.project(psi_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
-                    stream=stream)
-        hpsi.zero_()
-        api.add(hpsi, cin_d, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle, stream=stream)
-        out_h.copy_(hpsi, non_blocking=True)
+    def e2e_step(i):
+        b = i % 2
+        if started[b]:
+            s_in.wait_event(ev_cmp[b])       # the compute of step i-2 is done with psi_d[b], cin_d[b]
+        with torch.cuda.stream(s_in):
+            psi_d[b].copy_(psi_h, non_blocking=True)
+            cin_d[b].copy_(cin_h, non_blocking=True)
+            ev_in[b].record(s_in)
+        s_cmp.wait_event(ev_in[b])
+        if started[b]:
+            s_cmp.wait_event(ev_out[b])      # the copy-out of step i-2 is done with hps[b]
+        with torch.cuda.stream(s_cmp):
+            api.project(psi_d[b], pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=co[b], handle=handle,
+                        stream=s_cmp)
+            hps[b].zero_()
+            api.add(hps[b], cin_d[b], pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle,
+                    stream=s_cmp)
+            ev_cmp[b].record(s_cmp)
+        s_out.wait_event(ev_cmp[b])
+        with torch.cuda.stream(s_out):
+            out_h[b].copy_(hps[b], non_blocking=True)
+            ev_out[b].record(s_out)
+        started[b] = True
 
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+    for i in range(max(2, args.warmup)):
+        e2e_step(i)
     torch.cuda.synchronize()
     K2 = max(2, min(K, 10))
     barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(K2):
-        e2e_step()
-    e1.record(stream)
+    e0.record(s_in)
+    for i in range(K2):
+        e2e_step(i)
+    s_in.wait_stream(s_out)
+    e1.record(s_in)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(ws, e0.elapsed_time(e1) / K2)
     h2d = psi.numel() * psi.element_size() + cin.numel() * cin.element_size()
@@ -312,7 +340,9 @@ def run_ours(args, ws, rank, local):
             "hbm_fraction": round(value / ws / peaks.get("hbm_gbs", 6793.4), 4),
             "roofline": roof,
             "e2e": {"value": round(ws * bytes_step / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
-                    "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "mode": "pinned host psi + coefficients in, expanded psi out, every step; pipelined over two "
+                            "device buffer sets (copy-in, compute and copy-out streams)"},
             "gpu_launches": 3 * K,
             "clocks": clk,
         }
@@ -329,7 +359,7 @@ def run_ours(args, ws, rank, local):
             st = result["serving"]["loads"].get("0.8") or next(iter(result["serving"]["loads"].values()))
             result["p50_ms"], result["p99_ms"] = st["p50_ms"], st["p99_ms"]
         if not args.no_precision_forms:
-            del hpsi, psi_h, out_h, psi_d, cin_d
+            del psi_h, out_h, psi_d, cin_d, hps
             torch.cuda.empty_cache()
             result["precision_forms"] = precision_forms(api, handle, stream)
         if not args.no_cpu_baseline and ws == 1:
