@@ -25,6 +25,16 @@ struct sho_handle {
     void* mem = nullptr;
     int nnz = 0;
   } radial[SHO_MAX_NUMAX + 1][2];
+  // per-geometry plan arrays of the most recent projection / expansion geometry on the device (atoms,
+  // launch order or per-plane lists): repeated calls skip the host planning and the uploads, whose
+  // pageable copies would stall the host until the stream drained
+  struct GeoCache {
+    uint64_t key = 0;
+    void* mem = nullptr;
+    size_t cap = 0;
+    size_t off[4] = {0, 0, 0, 0};
+    int extra = 0;
+  } geo[2];
   // plane-sweep plan of the most recent geometry (atoms, items, slot lists, segments) on the device:
   // repeated projections with the same atoms skip the host planning and the uploads
   uint64_t plane_key = 0;
@@ -280,6 +290,41 @@ uint64_t geometry_key(const sho_grid* grid, const std::vector<AtomDev>& at, int 
   return k | 1ull;  // never 0 (0 marks "no plan")
 }
 
+// Make the handle's cache slot hold `parts` for geometry `key` (uploaded, stream-ordered on s, only when
+// the key changed).  Call after begin_call.
+int geo_cache(sho_handle* h, int slot, uint64_t key, const std::vector<std::pair<const void*, size_t>>& parts,
+              cudaStream_t s) {
+  auto& gc = h->geo[slot];
+  if (gc.key == key && gc.mem) return SHO_OK;
+  Carve cv;
+  size_t off[4] = {0, 0, 0, 0};
+  for (size_t i = 0; i < parts.size() && i < 4; i++) off[i] = cv.take(std::max<size_t>(1, parts[i].second));
+  if (cv.off > gc.cap) {
+    if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+    if (gc.mem) cudaFree(gc.mem);
+    gc.mem = nullptr;
+    gc.cap = 0;
+    gc.key = 0;
+    if (cudaMalloc(&gc.mem, cv.off) != cudaSuccess) {
+      cudaGetLastError();
+      gc.mem = nullptr;
+      return SHO_ERR_OOM;
+    }
+    gc.cap = cv.off;
+  }
+  for (size_t i = 0; i < parts.size() && i < 4; i++) {
+    if (parts[i].second == 0) continue;
+    if (cudaMemcpyAsync(static_cast<char*>(gc.mem) + off[i], parts[i].first, parts[i].second, cudaMemcpyHostToDevice,
+                        s) != cudaSuccess) {
+      gc.key = 0;
+      return SHO_ERR_CUDA;
+    }
+  }
+  for (int i = 0; i < 4; i++) gc.off[i] = off[i];
+  gc.key = key;
+  return SHO_OK;
+}
+
 int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const float* psi,
                    int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
   const size_t A = at.size();
@@ -296,6 +341,8 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
     if (pc.off > h->plane_cap) {
       if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
       if (h->plane_mem) cudaFree(h->plane_mem);
+    for (auto& gc : h->geo)
+      if (gc.mem) cudaFree(gc.mem);
       h->plane_mem = nullptr;
       h->plane_cap = 0;
       h->plane_key = 0;
@@ -459,6 +506,8 @@ int sho_create(sho_handle** out, int device) {
     cudaGetLastError();
     if (h->dstatus) cudaFree(h->dstatus);
     if (h->plane_mem) cudaFree(h->plane_mem);
+    for (auto& gc : h->geo)
+      if (gc.mem) cudaFree(gc.mem);
     for (auto& row : h->radial)
       for (auto& r : row)
         if (r.mem) cudaFree(r.mem);
@@ -480,6 +529,8 @@ int sho_destroy(sho_handle* h) {
     if (h->coeff_ws) cudaFree(h->coeff_ws);
     if (h->dstatus) cudaFree(h->dstatus);
     if (h->plane_mem) cudaFree(h->plane_mem);
+    for (auto& gc : h->geo)
+      if (gc.mem) cudaFree(gc.mem);
     for (auto& row : h->radial)
       for (auto& r : row)
         if (r.mem) cudaFree(r.mem);
@@ -665,20 +716,20 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec))
     return project_planes(h, grid, at, static_cast<const float*>(psi), nbands, numax, cube, prec,
                           static_cast<float*>(coeff), s);
-  std::vector<int> order = spatial_order(grid, at);
-  Carve cv;
-  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
-  const size_t o_order = cv.take(order.size() * sizeof(int));
   SHO_TRY(begin_call(h, s));
-  SHO_TRY(ensure_workspace(h, cv.off));
-  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
-  SHO_TRY(upload(h, o_order, order.data(), order.size() * sizeof(int), s));
+  const uint64_t key = geometry_key(grid, at, cube);
+  if (h->geo[0].key != key) {
+    std::vector<int> order = spatial_order(grid, at);
+    SHO_TRY(geo_cache(h, 0, key, {{at.data(), at.size() * sizeof(AtomDev)}, {order.data(), order.size() * sizeof(int)}},
+                      s));
+  }
+  const char* gm = static_cast<const char*>(h->geo[0].mem);
   ProjectLaunch L;
-  L.order = reinterpret_cast<const int*>(static_cast<char*>(h->ws) + o_order);
+  L.order = reinterpret_cast<const int*>(gm + h->geo[0].off[1]);
   L.g = make_grid(grid, cube, nbands);
   L.psi = psi;
   L.psi_dtype = psi_dtype;
-  L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
+  L.atoms = reinterpret_cast<const AtomDev*>(gm + h->geo[0].off[0]);
   L.natoms = natoms;
   L.numax = numax;
   L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
@@ -708,35 +759,40 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
-  std::vector<int> ptr, list;
-  plane_lists(grid, at, cube, ptr, list);
   const size_t tc = compute_size(coeff_dtype);
   Carve cv;
-  const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
-  const size_t o_ptr = cv.take(ptr.size() * sizeof(int));
-  const size_t o_list = cv.take(std::max<size_t>(1, list.size()) * sizeof(int));
   const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
   const size_t o_t2 = cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
   const size_t o_txm = cv.take((size_t)natoms * cube * (size_t)((numax + 4) & ~3) * 16);
   SHO_TRY(begin_call(h, s));
+  const uint64_t key = geometry_key(grid, at, cube);
+  if (h->geo[1].key != key) {
+    std::vector<int> ptr, list;
+    plane_lists(grid, at, cube, ptr, list);
+    int max_plane = 0;
+    for (size_t z = 0; z + 1 < ptr.size(); z++) max_plane = std::max(max_plane, ptr[z + 1] - ptr[z]);
+    SHO_TRY(geo_cache(h, 1, key,
+                      {{at.data(), at.size() * sizeof(AtomDev)},
+                       {ptr.data(), ptr.size() * sizeof(int)},
+                       {list.data(), list.size() * sizeof(int)}},
+                      s));
+    h->geo[1].extra = max_plane;
+  }
   SHO_TRY(ensure_workspace(h, cv.off));
-  SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
-  SHO_TRY(upload(h, o_ptr, ptr.data(), ptr.size() * sizeof(int), s));
-  SHO_TRY(upload(h, o_list, list.data(), list.size() * sizeof(int), s));
   char* ws = static_cast<char*>(h->ws);
+  const char* gm = static_cast<const char*>(h->geo[1].mem);
   ExpandLaunch L;
   L.g = make_grid(grid, cube, nbands);
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
   L.psi = psi;
   L.psi_dtype = psi_dtype;
-  L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
+  L.atoms = reinterpret_cast<const AtomDev*>(gm + h->geo[1].off[0]);
   L.natoms = natoms;
   L.numax = numax;
-  L.plane_ptr = reinterpret_cast<const int*>(ws + o_ptr);
-  L.plane_atoms = reinterpret_cast<const int*>(ws + o_list);
-  L.max_plane = 0;
-  for (size_t z = 0; z + 1 < ptr.size(); z++) L.max_plane = std::max(L.max_plane, ptr[z + 1] - ptr[z]);
+  L.plane_ptr = reinterpret_cast<const int*>(gm + h->geo[1].off[1]);
+  L.plane_atoms = reinterpret_cast<const int*>(gm + h->geo[1].off[2]);
+  L.max_plane = h->geo[1].extra;
   L.tables = ws + o_tab;
   L.t2 = ws + o_t2;
   L.tables_xmajor = ws + o_txm;
