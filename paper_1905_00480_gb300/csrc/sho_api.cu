@@ -226,6 +226,9 @@ int ensure_workspace(sho_handle* h, size_t bytes) {
 }
 
 int begin_call(sho_handle* h, cudaStream_t s) {
+  // a launch-time error left by unrelated work of the process must not be taken for ours (the launchers
+  // check cudaGetLastError after their own launches)
+  (void)cudaGetLastError();
   if (h->has_last && cudaStreamWaitEvent(s, h->last, 0) != cudaSuccess) return SHO_ERR_CUDA;
   return SHO_OK;
 }
