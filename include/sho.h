@@ -106,6 +106,10 @@ int sho_create(sho_handle** out, int device);
 /* Wait for the handle's outstanding work, free its workspace and the handle. */
 int sho_destroy(sho_handle* handle);
 
+/* Text of the CUDA error behind the handle's most recent SHO_ERR_CUDA ("no error" when none); a
+ * diagnostic, valid until the next call on the handle. */
+const char* sho_last_cuda_error(const sho_handle* handle);
+
 /* strict != 0: a spacing above h_max (eq. max_grid_spacing) is an error (SHO_ERR_SPACING); default 0
  * (allowed: the method still computes the defined sums, only their sampling is coarse). */
 int sho_set_strict(sho_handle* handle, int strict);

@@ -9,6 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libsho.so")
 
 SHO_OK = 0
+SHO_ERR_CUDA = -7
 STATUS_NAMES = {
     0: "SHO_OK", -1: "SHO_ERR_ARG", -2: "SHO_ERR_NUMAX", -3: "SHO_ERR_CUBE", -4: "SHO_ERR_SPACING",
     -5: "SHO_ERR_DTYPE", -6: "SHO_ERR_OOM", -7: "SHO_ERR_CUDA", -8: "SHO_ERR_TIMEOUT", -9: "SHO_ERR_DEVICE",
@@ -57,6 +58,7 @@ SIGNATURES = {
     "sho_destroy": (_I, [_VP]),
     "sho_set_strict": (_I, [_VP, _I]),
     "sho_sync": (_I, [_VP]),
+    "sho_last_cuda_error": (ctypes.c_char_p, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),
     "sho_project_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP]),
     "sho_add_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP]),

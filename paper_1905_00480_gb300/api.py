@@ -127,7 +127,8 @@ def project(psi: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, peri
     st = N.lib().sho_project(hd.ptr, ctypes.byref(g), ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
                              B, A, _dp(pos_h), _dp(sig_h), int(numax), int(cube), N.PRECS[prec],
                              ctypes.c_void_p(out.data_ptr()), N.DTYPES[_TORCH_DT[cdt]], _stream_ptr(psi, stream))
-    N.check(st, "sho_project")
+    N.check(st, "sho_project" if st != N.SHO_ERR_CUDA else
+            f"sho_project ({N.lib().sho_last_cuda_error(hd.ptr).decode()})")
     return out
 
 
@@ -248,7 +249,8 @@ def add(psi: torch.Tensor, coeff: torch.Tensor, pos, sigma, numax: int, cube: in
                          N.DTYPES[_TORCH_DT[coeff.dtype]], B, A, _dp(pos_h), _dp(sig_h), int(numax), int(cube),
                          N.PRECS[prec], ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
                          _stream_ptr(psi, stream))
-    N.check(st, "sho_add")
+    N.check(st, "sho_add" if st != N.SHO_ERR_CUDA else
+            f"sho_add ({N.lib().sho_last_cuda_error(hd.ptr).decode()})")
     return psi
 
 

@@ -19,6 +19,7 @@ struct sho_handle {
   size_t coeff_ws_bytes = 0;
   bool has_last = false;
   int device_error = SHO_OK;   // first device-side error since the last sho_sync
+  cudaError_t last_cuda = cudaSuccess;  // CUDA error behind the most recent SHO_ERR_CUDA of this handle
   int* dstatus = nullptr;      // device word set by kernels whose bounded waits expired
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
   struct RadialDev {
@@ -543,6 +544,11 @@ int sho_destroy(sho_handle* h) {
   return st;
 }
 
+const char* sho_last_cuda_error(const sho_handle* h) {
+  if (!h) return "no handle";
+  return cudaGetErrorString(h->last_cuda);
+}
+
 int sho_set_strict(sho_handle* h, int strict) {
   if (!h) return SHO_ERR_ARG;
   h->strict = strict ? 1 : 0;
@@ -744,7 +750,10 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
                         : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_project_fp32(L, prec)
                         : is_tc(prec) ? launch_project_tc(L, prec)
                         : launch_project(L);
-  if (e != cudaSuccess) return SHO_ERR_CUDA;
+  if (e != cudaSuccess) {
+    h->last_cuda = e;
+    return SHO_ERR_CUDA;
+  }
   return end_call(h, s);
 }
 
@@ -805,7 +814,10 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
                         : fp32_stream_ok(psi, psi_dtype, nbands) ? launch_expand_fp32(L, prec)
                         : is_tc(prec) ? launch_expand_tc(L, prec)
                         : launch_expand(L);
-  if (e != cudaSuccess) return SHO_ERR_CUDA;
+  if (e != cudaSuccess) {
+    h->last_cuda = e;
+    return SHO_ERR_CUDA;
+  }
   return end_call(h, s);
 }
 
