@@ -20,6 +20,7 @@ struct sho_handle {
   bool has_last = false;
   int device_error = SHO_OK;   // first device-side error since the last sho_sync
   cudaError_t last_cuda = cudaSuccess;  // CUDA error behind the most recent SHO_ERR_CUDA of this handle
+  const char* last_where = "";          // and the step that raised it
   int* dstatus = nullptr;      // device word set by kernels whose bounded waits expired
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
   struct RadialDev {
@@ -230,7 +231,14 @@ int begin_call(sho_handle* h, cudaStream_t s) {
   // a launch-time error left by unrelated work of the process must not be taken for ours (the launchers
   // check cudaGetLastError after their own launches)
   (void)cudaGetLastError();
-  if (h->has_last && cudaStreamWaitEvent(s, h->last, 0) != cudaSuccess) return SHO_ERR_CUDA;
+  if (h->has_last) {
+    const cudaError_t e = cudaStreamWaitEvent(s, h->last, 0);
+    if (e != cudaSuccess) {
+      h->last_cuda = e;
+      h->last_where = "stream wait";
+      return SHO_ERR_CUDA;
+    }
+  }
   return SHO_OK;
 }
 
@@ -304,7 +312,14 @@ int geo_cache(sho_handle* h, int slot, uint64_t key, const std::vector<std::pair
   size_t off[4] = {0, 0, 0, 0};
   for (size_t i = 0; i < parts.size() && i < 4; i++) off[i] = cv.take(std::max<size_t>(1, parts[i].second));
   if (cv.off > gc.cap) {
-    if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
+    if (h->has_last) {
+      const cudaError_t e = cudaEventSynchronize(h->last);
+      if (e != cudaSuccess) {
+        h->last_cuda = e;
+        h->last_where = "plan cache: wait";
+        return SHO_ERR_CUDA;
+      }
+    }
     if (gc.mem) cudaFree(gc.mem);
     gc.mem = nullptr;
     gc.cap = 0;
@@ -318,8 +333,11 @@ int geo_cache(sho_handle* h, int slot, uint64_t key, const std::vector<std::pair
   }
   for (size_t i = 0; i < parts.size() && i < 4; i++) {
     if (parts[i].second == 0) continue;
-    if (cudaMemcpyAsync(static_cast<char*>(gc.mem) + off[i], parts[i].first, parts[i].second, cudaMemcpyHostToDevice,
-                        s) != cudaSuccess) {
+    const cudaError_t e = cudaMemcpyAsync(static_cast<char*>(gc.mem) + off[i], parts[i].first, parts[i].second,
+                                          cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      h->last_cuda = e;
+      h->last_where = "plan cache: upload";
       gc.key = 0;
       return SHO_ERR_CUDA;
     }
@@ -546,7 +564,10 @@ int sho_destroy(sho_handle* h) {
 
 const char* sho_last_cuda_error(const sho_handle* h) {
   if (!h) return "no handle";
-  return cudaGetErrorString(h->last_cuda);
+  static thread_local char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s%s%s", cudaGetErrorString(h->last_cuda), h->last_where[0] ? " at " : "",
+                h->last_where);
+  return buf;
 }
 
 int sho_set_strict(sho_handle* h, int strict) {
@@ -752,6 +773,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
                         : launch_project(L);
   if (e != cudaSuccess) {
     h->last_cuda = e;
+    h->last_where = "projection launch";
     return SHO_ERR_CUDA;
   }
   return end_call(h, s);
@@ -816,6 +838,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
                         : launch_expand(L);
   if (e != cudaSuccess) {
     h->last_cuda = e;
+    h->last_where = "expansion launch";
     return SHO_ERR_CUDA;
   }
   return end_call(h, s);
