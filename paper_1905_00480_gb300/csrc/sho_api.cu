@@ -320,7 +320,18 @@ int geo_cache(sho_handle* h, int slot, uint64_t key, const std::vector<std::pair
         return SHO_ERR_CUDA;
       }
     }
-    if (gc.mem) cudaFree(gc.mem);
+    if (gc.mem) {
+      const cudaError_t e = cudaFree(gc.mem);
+      if (e != cudaSuccess) {
+        h->last_cuda = e;
+        h->last_where = "plan cache: free";
+        gc.mem = nullptr;
+        gc.cap = 0;
+        gc.key = 0;
+        (void)cudaGetLastError();
+        return SHO_ERR_CUDA;
+      }
+    }
     gc.mem = nullptr;
     gc.cap = 0;
     gc.key = 0;
@@ -363,8 +374,6 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
     if (pc.off > h->plane_cap) {
       if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
       if (h->plane_mem) cudaFree(h->plane_mem);
-    for (auto& gc : h->geo)
-      if (gc.mem) cudaFree(gc.mem);
       h->plane_mem = nullptr;
       h->plane_cap = 0;
       h->plane_key = 0;
@@ -527,12 +536,6 @@ int sho_create(sho_handle** out, int device) {
   if (cudaMalloc(&h->dstatus, sizeof(int)) != cudaSuccess || cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     if (h->dstatus) cudaFree(h->dstatus);
-    if (h->plane_mem) cudaFree(h->plane_mem);
-    for (auto& gc : h->geo)
-      if (gc.mem) cudaFree(gc.mem);
-    for (auto& row : h->radial)
-      for (auto& r : row)
-        if (r.mem) cudaFree(r.mem);
     cudaEventDestroy(h->last);
     delete h;
     return SHO_ERR_OOM;

@@ -214,3 +214,30 @@ def test_plan_cache_follows_the_geometry():
     got = api.project(psi, moved, sa, numax, cube, h, True, prec="tf32", handle=hd).double().cpu().numpy()
     exp = oracle.project(grid, h, True, psi.double().cpu().numpy(), moved, sa, numax, cube)
     assert_coeff_close(got, exp, TOL["tf32"])
+
+
+def test_plan_caches_survive_each_other():
+    """One handle alternating FP32-class projections whose plane plan grows and expansions / generic
+    projections whose geometry plans are cached: each cache keeps its own buffers (regression test)."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(670)
+    grid, h, numax, cube = (48, 48, 48), 0.2, 3, 32
+    box = tuple(n * h for n in grid)
+    hd = api.Handle(0)
+    psi32 = torch.from_numpy(rng.standard_normal((48, 48, 48, 8)).astype(np.float32)).cuda()
+    psi64 = psi32.double()
+    small, ssig = workloads.random_atoms(rng, 4, box, True, min_sep=1.0)
+    big, bsig = workloads.random_atoms(rng, 60, box, True, min_sep=0.8)
+    c_small = torch.from_numpy(rng.standard_normal((4, 20, 8)).astype(np.float32)).cuda()
+    ref = oracle.add(grid, h, True, np.zeros((48, 48, 48, 8)), small, ssig, numax, cube, c_small.double().cpu().numpy())
+    for _ in range(2):
+        out = torch.zeros_like(psi32)
+        api.add(out, c_small, small, ssig, numax, cube, h, True, prec="fp32", handle=hd)  # geometry cache
+        api.project(psi64, small, ssig, numax, cube, h, True, prec="fp64", handle=hd)     # geometry cache
+        api.project(psi32, big, bsig, numax, cube, h, True, prec="tf32", handle=hd)       # plane plan grows
+        out2 = torch.zeros_like(psi32)
+        api.add(out2, c_small, small, ssig, numax, cube, h, True, prec="fp32", handle=hd)  # cached geometry
+        assert rel_norm(out2.double().cpu().numpy(), ref) <= TOL_FP32
+        assert torch.equal(out, out2)
