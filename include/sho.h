@@ -143,6 +143,14 @@ int sho_project(sho_handle* handle, const sho_grid* grid, const void* psi, sho_d
  *   SHO_PATH_ATOM   per-atom kernels: each (atom, 32 bands, z-slab) streams its own cube
  * Returns SHO_ERR_ARG for a NULL grid. */
 typedef enum { SHO_PATH_ATOM = 1, SHO_PATH_PLANE = 2 } sho_path;
+
+/* Host-side check of the plane-sweep plan for a geometry (no GPU work): builds the plan the plane sweep
+ * would use and verifies it -- every (atom, cube plane, grid row) covered exactly once, the row segments
+ * of each register slot disjoint and ordered, both halves of a wrapped cube in one sweep.  Returns
+ * SHO_OK, SHO_ERR_STATE for a violated rule, or an argument error; *nitems / *nsegs (optional) receive
+ * the number of plane sweeps (CTA rows of work) and row segments. */
+int sho_plane_plan_check(const sho_grid* grid, int natoms, const double* pos, const double* sigma, int cube,
+                         int* nitems, int* nsegs);
 int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int numax, int cube,
                      sho_prec prec, sho_dtype coeff_dtype);
 

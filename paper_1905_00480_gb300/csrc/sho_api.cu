@@ -725,6 +725,18 @@ int sho_add_bloch(sho_handle* h, const sho_grid* grid, const double* kvec, const
   return bloch_call(h, grid, kvec, 1, coeff, psi, nbands, natoms, pos, sigma, numax, cube, stream);
 }
 
+int sho_plane_plan_check(const sho_grid* grid, int natoms, const double* pos, const double* sigma, int cube,
+                         int* nitems, int* nsegs) {
+  SHO_TRY(check_common(grid, 0, natoms, pos, sigma, 0, cube, SHO_MAX_NUMAX));
+  std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
+  PlanePlan plan;
+  plan_planes(grid, at, cube, plan);
+  if (nitems) *nitems = (int)plan.items.size();
+  if (nsegs) *nsegs = (int)plan.segs.size();
+  const int r = plane_plan_check(grid, at, cube, plan);
+  return r == 0 ? SHO_OK : SHO_ERR_STATE;
+}
+
 int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int numax, int cube,
                      sho_prec prec, sho_dtype coeff_dtype) {
   if (!grid) return SHO_ERR_ARG;

@@ -134,6 +134,7 @@ bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nband
               sho_prec prec);
 void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, PlanePlan& plan);
 cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec);
+int plane_plan_check(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, const PlanePlan& plan);
 constexpr size_t kPlaneBfragBytesPerAtom = 32 * (kMaxCube / 8) * 4 * sizeof(uint32_t);
 
 // Cartesian <-> radial transform (sho_radial.cu): labels and U on the host, CSR rows for the kernel.

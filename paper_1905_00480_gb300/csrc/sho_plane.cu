@@ -757,6 +757,69 @@ void plan_planes(const sho_grid* grid, const std::vector<AtomDev>& at, int cube,
   }
 }
 
+// Check a plan against its definition: every (atom, plane, grid row) of every cube exactly once, the
+// segments of one slot ordered and disjoint, items of one plane contiguous, rows inside [ylo, yhi), and a
+// wrapped atom's two halves in one warp when the grid is too small for the ring to order them.
+// Returns 0 or the number of the first violated rule.
+int plane_plan_check(const sho_grid* grid, const std::vector<AtomDev>& at, int cube, const PlanePlan& plan) {
+  const int ny = grid->n[1], nz = grid->n[2];
+  const bool per = grid->periodic != 0;
+  const int W = kPlaneWarps, S = kPlaneSlots;
+  const bool same_warp = ny - cube < kPlaneMaxStages;
+  std::vector<int> count((size_t)at.size() * cube * ny, 0);  // (atom, iz, y) -> times covered
+  int last_z = -1;
+  std::vector<char> seen_z((size_t)nz, 0);
+  for (size_t it = 0; it < plan.items.size(); it++) {
+    const int4 item = plan.items[it];
+    if (item.x < 0 || item.x >= nz) return 1;
+    if (item.x != last_z) {
+      if (seen_z[(size_t)item.x]) return 2;  // items of a plane are contiguous
+      seen_z[(size_t)item.x] = 1;
+      last_z = item.x;
+    }
+    std::vector<int> tail_warp(at.size(), -1), head_warp(at.size(), -1);
+    for (int w = 0; w < W; w++)
+      for (int s2 = 0; s2 < S; s2++) {
+        const int li = item.w + w * S + s2;
+        int prev_end = -1;
+        for (int q = plan.slot_ptr[(size_t)li]; q < plan.slot_ptr[(size_t)li + 1]; q++) {
+          const PlaneSeg& sg = plan.segs[(size_t)q];
+          if (sg.ys < item.y || sg.ye > item.z || sg.ys >= sg.ye) return 3;
+          if (sg.ys < prev_end) return 4;  // overlap within a slot
+          prev_end = sg.ye;
+          const AtomDev& a = at[(size_t)sg.atom];
+          int z = a.o[2] + sg.iz;
+          if (per) z = ((z % nz) + nz) % nz;
+          if (z != item.x || sg.t2i != sg.atom * cube + sg.iz) return 5;
+          for (int y = sg.ys; y < sg.ye; y++) {
+            int iy = y - a.o[1];
+            if (per) iy = ((iy % ny) + ny) % ny;
+            if (iy != sg.iy0 + (y - sg.ys) || iy < 0 || iy >= cube) return 6;
+            count[((size_t)sg.atom * cube + sg.iz) * ny + y]++;
+          }
+          if (sg.flags == 1) tail_warp[(size_t)sg.atom] = w;
+          if (sg.flags == 2) head_warp[(size_t)sg.atom] = w;
+        }
+      }
+    for (size_t a = 0; a < at.size(); a++) {
+      if ((tail_warp[a] >= 0) != (head_warp[a] >= 0)) return 7;  // both halves in the same sweep
+      if (same_warp && tail_warp[a] >= 0 && tail_warp[a] != head_warp[a]) return 8;
+    }
+  }
+  for (size_t a = 0; a < at.size(); a++)
+    for (int iz = 0; iz < cube; iz++) {
+      int z = at[a].o[2] + iz;
+      const bool zin = per || (z >= 0 && z < nz);
+      for (int y = 0; y < ny; y++) {
+        int iy = y - at[a].o[1];
+        if (per) iy = ((iy % ny) + ny) % ny;
+        const int want = (zin && iy >= 0 && iy < cube) ? 1 : 0;
+        if (count[((size_t)a * cube + iz) * ny + y] != want) return 9;
+      }
+    }
+  return 0;
+}
+
 cudaError_t launch_project_plane(const PlaneLaunch& p, sho_prec prec) {
   switch (p.numax) {
     case 0: return plane_mode<0>(p, prec);
