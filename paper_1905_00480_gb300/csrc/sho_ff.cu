@@ -8,9 +8,9 @@
 // and the final accumulation into psi stay in FP64.
 //   projection  T1[n] = sum_x psi[x] phi_n(x): psi split into float pairs with integer instructions,
 //               then one float-float dot step per (x, n); T1 is rebuilt in FP64 per grid row.
-//   expansion   the update sum_a sum_n T1_a[n] phi_n(x) of each grid point is accumulated over atoms as
-//               a float pair in registers (block gather over 8-row x 32-point tiles) and added to psi in
-//               FP64 once.
+//   expansion   the update sum_a sum_n T1_a[n] phi_n(x) of each grid point is one float-float dot
+//               product over all atoms and states, its running pair kept in shared memory (block gather
+//               over 8-row x 32-point tiles), and added to psi in FP64 once.
 #include <cooperative_groups.h>
 
 #include "sho_device.cuh"
@@ -289,7 +289,7 @@ struct FfBlkSmem {
   }
   // 2 staging buffers + per-warp update accumulators [8 warps][32 x][32 bands] float pairs + atom list
   static size_t bytes(int cube, int max_plane) {
-    return 2 * buf_bytes(cube) + (size_t)kFfRows * kFfXSeg * kWarp * 8 + (size_t)(max_plane + 1) * 4;
+    return 2 * buf_bytes(cube) + (size_t)kFfRows * kFfXSeg * kWarp * 8 + (size_t)(max_plane + 1) * sizeof(int4);
   }
 };
 
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
   const size_t bufb = SM::buf_bytes(C);
   float2* accs = reinterpret_cast<float2*>(smem_raw + 2 * bufb);  // [warps][32 x][32 bands]
-  int* slist = reinterpret_cast<int*>(accs + kFfRows * kFfXSeg * kWarp);
+  int4* slist = reinterpret_cast<int4*>(accs + kFfRows * kFfXSeg * kWarp);  // (atom, offsets), ascending
   __shared__ int wcount[kFfRows];
   __shared__ int s_nlist;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -326,30 +326,34 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   const int b0 = blockIdx.y * kWarp;
   const bool bok = b0 + lane < B;
   const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
-
-  auto meets = [&](const AtomDev& at) {
-    int dy = yb * kFfRows - at.o[1], dx = xs - at.o[0];
+  // Offsets of atom a's cube against this tile, wrapped into [0, N) on a periodic grid: r.y = cube
+  // row of the tile's first row, r.z = cube point of its first x point, r.w = cube plane of z.  True
+  // when the cube meets the tile's rows and x segment.  Computed once per (tile, atom) here, so the
+  // atom loop below does no integer division.
+  auto locate = [&](const AtomDev& at, int4& r) {
+    int dy = yb * kFfRows - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
+    bool m;
     if (g.periodic) {
       dy %= Ny;
       if (dy < 0) dy += Ny;
       dx %= Nx;
       if (dx < 0) dx += Nx;
-      return (dy < C || dy + kFfRows > Ny) && (dx < C || dx + kFfXSeg > Nx);
+      dz %= Nz;
+      if (dz < 0) dz += Nz;
+      m = (dy < C || dy + kFfRows > Ny) && (dx < C || dx + kFfXSeg > Nx);
+    } else {
+      m = dy < C && dy + kFfRows > 0 && dx < C && dx + kFfXSeg > 0;
     }
-    return dy < C && dy + kFfRows > 0 && dx < C && dx + kFfXSeg > 0;
+    r = make_int4(0, dy, dx, dz);
+    return m;
   };
 
   // staging with 8-byte asynchronous copies (FP64 rows of an arbitrary band count are 8-byte aligned)
   auto cp8 = [](void* dst, const void* src, int bytes) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(ff_smem_u32(dst)), "l"(src), "r"(bytes));
   };
-  auto stage = [&](int a, int buf) {
-    const AtomDev at = atoms[a];
-    int iz = z - at.o[2];
-    if (g.periodic) {
-      iz %= Nz;
-      if (iz < 0) iz += Nz;
-    }
+  auto stage = [&](const int4 r, int buf) {
+    const int a = r.x, iz = r.w;
     unsigned char* dst = smem_raw + (size_t)buf * bufb;
     float2* dt2 = reinterpret_cast<float2*>(dst);
     const float2* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
@@ -371,18 +375,19 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   __syncthreads();
   for (int base = q0; base < q1; base += kFfRows * kWarp) {
     const int q = base + tid;
-    int a = -1;
+    int4 r = make_int4(-1, 0, 0, 0);
     bool m = false;
     if (q < q1) {
-      a = plane_atoms[q];
-      m = meets(atoms[a]);
+      const int a = plane_atoms[q];
+      m = locate(atoms[a], r);
+      r.x = a;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, m);
     if (lane == 0) wcount[warp] = __popc(bal);
     __syncthreads();
     int off = s_nlist;
     for (int w = 0; w < warp; w++) off += wcount[w];
-    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = a;
+    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = r;
     __syncthreads();
     if (tid == 0)
       for (int w = 0; w < kFfRows; w++) s_nlist += wcount[w];
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   if (nlist > 0) stage(slist[0], 0);
   ff_commit();
   for (int li = 0; li < nlist; li++) {
-    const int a = slist[li];
+    const int4 r = slist[li];
     if (li + 1 < nlist) stage(slist[li + 1], buf ^ 1);
     ff_commit();
     ff_wait<1>();
@@ -408,12 +413,8 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     const float2* t2s = reinterpret_cast<const float2*>(src);
     const float2* txs = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8);
     const float2* tys = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
-    const AtomDev at = atoms[a];
-    int iy = y - at.o[1];
-    if (g.periodic) {
-      iy %= Ny;
-      if (iy < 0) iy += Ny;
-    }
+    int iy = r.y + warp;  // cube row of this warp's grid row
+    if (g.periodic && iy >= Ny) iy -= Ny;
     if (yok && iy >= 0 && iy < C) {
       // y-pass as float-float dot steps
       float ys[NP], yc[NP];
@@ -431,11 +432,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
       ff t1f[NP];
 #pragma unroll
       for (int n = 0; n < NP; n++) t1f[n] = ff_norm(ys[n], yc[n]);
-      int dx = xs - at.o[0];
-      if (g.periodic) {
-        dx %= Nx;
-        if (dx < 0) dx += Nx;
-      }
+      const int dx = r.z;  // cube index of tile point x is dx + x (mod Nx when periodic)
       // x-pass as float-float dot products over the tile points inside the cube: one contiguous run
       // of x (two when the cube wraps around a periodic grid)
       int r0a, r0b, r1a, r1b;
@@ -455,16 +452,15 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
 #pragma unroll 2
         for (int x = xa; x < xb; x++) {
           const int ix = x + shift;
-          float s = 0.0f, c = 0.0f;
+          // the point's dot product over all atoms and states continues from its running (s, c)
+          float2 v = accw[x * kWarp + lane];
           const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
 #pragma unroll
           for (int qn = 0; qn < NPX / 2; qn++) {
             const float4 f = f4[qn];
-            if (2 * qn < NP) ff_dot_step(s, c, t1f[2 * qn], ff{f.x, f.y});
-            if (2 * qn + 1 < NP) ff_dot_step(s, c, t1f[2 * qn + 1], ff{f.z, f.w});
+            if (2 * qn < NP) ff_dot_step(v.x, v.y, t1f[2 * qn], ff{f.x, f.y});
+            if (2 * qn + 1 < NP) ff_dot_step(v.x, v.y, t1f[2 * qn + 1], ff{f.z, f.w});
           }
-          float2 v = accw[x * kWarp + lane];
-          ff_add(v.x, v.y, s, c);
           accw[x * kWarp + lane] = v;
         }
       }

@@ -94,13 +94,4 @@ __device__ __forceinline__ ff ff_norm(float s, float c) {
   return r;
 }
 
-// (s, c) += (u, v): add two pair values, error-free on the leading parts.
-__device__ __forceinline__ void ff_add(float& s, float& c, float u, float v) {
-  const float t = s + u;
-  const float bb = t - s;
-  const float err = (s - (t - bb)) + (u - bb);
-  s = t;
-  c += err + v;
-}
-
 }  // namespace sho

@@ -291,43 +291,86 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
 constexpr int kRowsPerBlk = 8;       // grid rows (warps) per CTA
 constexpr int kXSeg = 32;            // x points per tile
 
-template <int NU>
+// Expansion x-pass B fragments, per atom and cube x point: entry (ix, t) is the fragment that lane
+// t = lane % 4 of a warp uses for grid point ix (column n = lane / 4 of an MMA tile), converted to the
+// mode's operand type once per atom: 4 words (hi and lo parts) for the split forms, else 2.
+template <TcMode TM>
+struct XFrag {
+  static constexpr int WORDS = (TM == TcMode::X3TF32 || TM == TcMode::SPLIT16) ? 4 : 2;
+};
+
+template <int NU, int MODE>
 struct BlkSmem {
+  static constexpr bool TC = MODE != kSimt;
   static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 3) & ~3;
-  // staged x table row stride: 12 floats for 8 states, so that the B-fragment loads of a quarter warp
-  // (8 x points x 4 states) hit 32 distinct banks
-  static constexpr int NPXS = NPX == 8 ? 12 : NPX;
-  // per buffer: T2 slice [P][32] + x table [C][NPXS] (x-major) + y table [NP][C]
+  static constexpr int XW = TC ? XFrag<TC ? (TcMode)MODE : TcMode::TF32>::WORDS : 0;
+  // x data of one atom: CUDA cores the x table [C][NPX] (x-major); tensor forms the B fragments
+  // [C + 1][4] of XW words, row C all zero (the fragment of points outside the cube)
+  __host__ __device__ static size_t xtab_floats(int cube) {
+    return TC ? (size_t)(cube + 1) * 4 * XW : (size_t)NPX * cube;
+  }
+  // per buffer: T2 slice [P][32] + x data + y table [NP][C]
   __host__ __device__ static size_t buf_floats(int cube) {
-    return (size_t)P * 32 + (size_t)NPXS * cube + (size_t)NP * cube;
+    return (size_t)P * 32 + xtab_floats(cube) + (size_t)NP * cube;
   }
   static size_t bytes(int cube, int max_plane) {
-    return (2 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * 4;
+    return (2 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * sizeof(int4);
   }
 };
 
+// The B-fragment table of the tensor forms, [A][C][4] entries of XFrag::WORDS words, from the x-major
+// x table [A][C][NPX] (one block per atom).
+template <int NU, int MODE>
+__global__ void k_expand_xfrag(int cube, const float* __restrict__ txm, uint32_t* __restrict__ xf) {
+  constexpr TcMode TM = (TcMode)MODE;
+  constexpr int NP = NU + 1, NPX = (NP + 3) & ~3, NB = TcFrag<TM>::NB, W = XFrag<TM>::WORDS;
+  const int a = blockIdx.x;
+  for (int i = threadIdx.x; i < cube * 4; i += blockDim.x) {
+    const int ix = i >> 2, t = i & 3;
+    float bv[NB];
+#pragma unroll
+    for (int e = 0; e < NB; e++) {
+      int k, n;
+      b_coord<TM>(e, 0, t, k, n);
+      bv[e] = k < NP ? txm[((size_t)a * cube + ix) * NPX + k] : 0.0f;
+    }
+    const BFrag<TM> f = make_bfrag<TM>(bv);
+    uint32_t* dst = xf + ((size_t)a * cube * 4 + i) * W;
+    dst[0] = f.hi[0];
+    dst[1] = f.hi[1];
+    if constexpr (W == 4) {
+      dst[2] = f.lo[0];
+      dst[3] = f.lo[1];
+    }
+  }
+}
+
+// Tensor forms: at most 128 registers, two blocks of 8 warps per SM; the CUDA-core form keeps the
+// compiler's choice (64 to 106 registers, three or four blocks).
 template <int NU, typename TP, int MODE>
-__global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, const AtomDev* __restrict__ atoms,
+__global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_expand_blk(GridDev g, const AtomDev* __restrict__ atoms,
                                                                     const int* __restrict__ plane_ptr,
                                                                     const int* __restrict__ plane_atoms,
                                                                     const float* __restrict__ tables,
                                                                     const float* __restrict__ txm,
+                                                                    const uint32_t* __restrict__ xf,
                                                                     const float* __restrict__ t2,
                                                                     TP* __restrict__ psi) {
   using BS = Basis<NU>;
+  using SM = BlkSmem<NU, MODE>;
   constexpr bool TC = MODE != kSimt;
-  // x-table row stride in shared memory: padded for the tensor-core B-fragment loads only
-  constexpr int NP = BS::NP, P = BS::P, NPX = BlkSmem<NU>::NPX, NPXS = TC ? BlkSmem<NU>::NPXS : NPX;
+  constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX, XW = SM::XW;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
-  constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA, NB = TcFrag<TM>::NB;
+  constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA;
   static_assert(!TC || K >= NP, "one MMA K step covers the states");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int C = g.cube;
   const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
-  const size_t bufsz = BlkSmem<NU>::buf_floats(C);
+  const size_t bufsz = SM::buf_floats(C);
+  const size_t xtab = SM::xtab_floats(C);
   float* bufs = reinterpret_cast<float*>(smem_raw);             // 2 x [T2 slice | x table | y table]
   float* t1all = bufs + 2 * bufsz;                               // [warps][16][36]
-  int* slist = reinterpret_cast<int*>(t1all + kRowsPerBlk * 16 * 36);  // atoms meeting the tile, ascending
+  int4* slist = reinterpret_cast<int4*>(t1all + kRowsPerBlk * 16 * 36);  // atoms meeting the tile, ascending
   __shared__ int wcount[kRowsPerBlk];
   __shared__ int s_nlist;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
@@ -347,29 +390,31 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
   const bool bok = b0 + lane < B;
   const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
 
-  // Does atom a's cube meet this tile's y rows and x segment?
-  auto meets = [&](const AtomDev& at) {
-    int dy = yb * kRowsPerBlk - at.o[1], dx = xs - at.o[0];
+  // Offsets of atom a's cube against this tile, wrapped into [0, N) on a periodic grid: r.y = cube
+  // row of the tile's first row, r.z = cube point of its first x point, r.w = cube plane of z.  True
+  // when the cube meets the tile's rows and x segment.  Computed once per (tile, atom) here, so the
+  // atom loop below does no integer division.
+  auto locate = [&](const AtomDev& at, int4& r) {
+    int dy = yb * kRowsPerBlk - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
+    bool m;
     if (g.periodic) {
       dy %= Ny;
       if (dy < 0) dy += Ny;
       dx %= Nx;
       if (dx < 0) dx += Nx;
-      const bool ymeet = dy < C || dy + kRowsPerBlk > Ny;
-      const bool xmeet = dx < C || dx + kXSeg > Nx;
-      return ymeet && xmeet;
+      dz %= Nz;
+      if (dz < 0) dz += Nz;
+      m = (dy < C || dy + kRowsPerBlk > Ny) && (dx < C || dx + kXSeg > Nx);
+    } else {
+      m = dy < C && dy + kRowsPerBlk > 0 && dx < C && dx + kXSeg > 0;
     }
-    return dy < C && dy + kRowsPerBlk > 0 && dx < C && dx + kXSeg > 0;
+    r = make_int4(0, dy, dx, dz);
+    return m;
   };
 
   // Stage atom a's T2 slice (plane z) and tables into buffer `buf` (all threads).
-  auto stage = [&](int a, int buf) {
-    const AtomDev at = atoms[a];
-    int iz = z - at.o[2];
-    if (g.periodic) {
-      iz %= Nz;
-      if (iz < 0) iz += Nz;
-    }
+  auto stage = [&](const int4 r, int buf) {
+    const int a = r.x, iz = r.w;
     float* dst = bufs + (size_t)buf * bufsz;
     const float* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
     const int band_bytes = (B - b0) * 4;
@@ -380,14 +425,18 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
       cp_async16(smem_u32(dst + p * 32 + part * 4), nb > 0 ? (const void*)(src_t2 + (size_t)p * B + part * 4)
                                                            : (const void*)t2, nb);
     }
-    const float* src_x = txm + (size_t)a * C * NPX;             // x table, x-major [C][NPX]
-    for (int q = tid; q < C * NPX / 4; q += kRowsPerBlk * kWarp) {
-      const int ix = q / (NPX / 4), part = q - ix * (NPX / 4);   // staged with row stride NPXS
-      cp_async16(smem_u32(dst + P * 32 + ix * NPXS + part * 4), src_x + q * 4, 16);
+    if constexpr (TC) {
+      const uint32_t* src_f = xf + (size_t)a * C * 4 * XW;     // B fragments [C][4] (row C stays zero)
+      for (int q = tid; q < C * XW; q += kRowsPerBlk * kWarp)
+        cp_async16(smem_u32(dst + P * 32 + q * 4), src_f + q * 4, 16);
+    } else {
+      const float* src_x = txm + (size_t)a * C * NPX;           // x table, x-major [C][NPX]
+      for (int q = tid; q < C * NPX / 4; q += kRowsPerBlk * kWarp)
+        cp_async16(smem_u32(dst + P * 32 + q * 4), src_x + q * 4, 16);
     }
     const float* src_y = tables + (size_t)a * 2 * NP * C + (size_t)NP * C;  // y table [NP][C]
     for (int q = tid; q < NP * C / 4; q += kRowsPerBlk * kWarp)
-      cp_async16(smem_u32(dst + P * 32 + C * NPXS + q * 4), src_y + q * 4, 16);
+      cp_async16(smem_u32(dst + P * 32 + xtab + q * 4), src_y + q * 4, 16);
   };
 
   // register tile: 32 x points of this warp's row, 32 bands
@@ -413,6 +462,8 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
   }
   if (TC) {
     for (int i = lane; i < 16 * 36; i += kWarp) t1s[i] = 0.0f;
+    // the zero fragment row (index C) of both staging buffers; staging never writes it
+    if (tid < 2 * 4 * XW) bufs[(size_t)(tid / (4 * XW)) * bufsz + P * 32 + (size_t)C * 4 * XW + tid % (4 * XW)] = 0.0f;
   }
 
   // The plane's atoms that meet this tile, tested in parallel and compacted in ascending order.
@@ -420,18 +471,19 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
   __syncthreads();
   for (int base = q0; base < q1; base += kRowsPerBlk * kWarp) {
     const int q = base + tid;
-    int a = -1;
+    int4 r = make_int4(-1, 0, 0, 0);
     bool m = false;
     if (q < q1) {
-      a = plane_atoms[q];
-      m = meets(atoms[a]);
+      const int a = plane_atoms[q];
+      m = locate(atoms[a], r);
+      r.x = a;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, m);
     if (lane == 0) wcount[warp] = __popc(bal);
     __syncthreads();
     int off = s_nlist;
     for (int w = 0; w < warp; w++) off += wcount[w];
-    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = a;
+    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = r;
     __syncthreads();
     if (tid == 0)
       for (int w = 0; w < kRowsPerBlk; w++) s_nlist += wcount[w];
@@ -444,20 +496,16 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
   if (nlist > 0) stage(slist[0], 0);
   cp_async_commit();
   for (int li = 0; li < nlist; li++) {
-    const int a = slist[li];
+    const int4 r = slist[li];
     if (li + 1 < nlist) stage(slist[li + 1], buf ^ 1);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
     const float* t2s = bufs + (size_t)buf * bufsz;
-    const float* txs = t2s + P * 32;       // [C][NPXS]
-    const float* tys = txs + NPXS * C;     // [NP][C] (the buffer is sized for the padded stride)
-    const AtomDev at = atoms[a];
-    int iy = y - at.o[1];
-    if (g.periodic) {
-      iy %= Ny;
-      if (iy < 0) iy += Ny;
-    }
+    const float* txs = t2s + P * 32;       // x table [C][NPX], or B fragments [C + 1][4][XW] words
+    const float* tys = txs + xtab;         // [NP][C]
+    int iy = r.y + warp;  // cube row of this warp's grid row
+    if (g.periodic && iy >= Ny) iy -= Ny;
     if (yok && iy >= 0 && iy < C) {
       // y-pass: T1[nx] for this row, lane = band
       float t1[NP];
@@ -469,11 +517,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
 #pragma unroll
         for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fmaf(t2s[BS::pair(nx, ny) * 32 + lane], w, t1[nx]);
       }
-      int dx = xs - at.o[0];  // cube index of tile point x is dx + x (mod Nx when periodic)
-      if (g.periodic) {
-        dx %= Nx;
-        if (dx < 0) dx += Nx;
-      }
+      const int dx = r.z;  // cube index of tile point x is dx + x (mod Nx when periodic)
       if constexpr (!TC) {
 #pragma unroll
         for (int x = 0; x < kXSeg; x++) {
@@ -481,7 +525,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
           if (g.periodic && ix >= Nx) ix -= Nx;
           if (ix >= 0 && ix < C) {
             float s = accr[x];
-            const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPXS);
+            const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
 #pragma unroll
             for (int q = 0; q < NPX / 4; q++) {
               const float4 f = f4[q];
@@ -497,34 +541,45 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp) k_expand_blk(GridDev g, c
 #pragma unroll
         for (int n = 0; n < NP; n++) t1s[n * 36 + lane] = t1[n];
         __syncwarp();
-        float av[2][NA];
+        AFrag<TM> afr[2];  // converted once, used by the four x tiles
 #pragma unroll
-        for (int m = 0; m < 2; m++)
+        for (int m = 0; m < 2; m++) {
+          float av[NA];
 #pragma unroll
           for (int i = 0; i < NA; i++) {
             int mm, k;
             a_coord<TM>(i, gq, tq, mm, k);
-            av[m][i] = t1s[k * 36 + 16 * m + mm];
+            av[i] = t1s[k * 36 + 16 * m + mm];
           }
+          afr[m] = make_afrag<TM>(av);
+        }
         __syncwarp();
         constexpr bool SPLIT = TM == TcMode::X3TF32 || TM == TcMode::SPLIT16;
+        const uint32_t* xfs = reinterpret_cast<const uint32_t*>(txs);
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-          float bv[NB];
-#pragma unroll
-          for (int i = 0; i < NB; i++) {
-            int k, n;
-            b_coord<TM>(i, gq, tq, k, n);
-            int ix = dx + 8 * j + n;
-            if (g.periodic && ix >= Nx) ix -= Nx;
-            bv[i] = (k <= NU && ix >= 0 && ix < C) ? txs[ix * NPXS + k] : 0.0f;
+          // this lane's column n = gq of tile j is cube point ix; outside the cube the zero row C
+          int ix = dx + 8 * j + gq;
+          if (g.periodic && ix >= Nx) ix -= Nx;
+          ix = (unsigned)ix < (unsigned)C ? ix : C;
+          BFrag<TM> bfr;
+          if constexpr (XW == 4) {
+            const uint4 v = *reinterpret_cast<const uint4*>(xfs + (ix * 4 + tq) * 4);
+            bfr.hi[0] = v.x;
+            bfr.hi[1] = v.y;
+            bfr.lo[0] = v.z;
+            bfr.lo[1] = v.w;
+          } else {
+            const uint2 v = *reinterpret_cast<const uint2*>(xfs + (ix * 4 + tq) * 2);
+            bfr.hi[0] = v.x;
+            bfr.hi[1] = v.y;
+            bfr.lo[0] = bfr.lo[1] = 0u;
           }
-          const BFrag<TM> bfr = make_bfrag<TM>(bv);
 #pragma unroll
           for (int m = 0; m < 2; m++) {
             float(&d)[4] = *reinterpret_cast<float(*)[4]>(&accr[(j * 2 + m) * 4]);
             float dl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            tc_product<TM>(d, dl, av[m], bfr);
+            tc_product_pre<TM>(d, dl, afr[m], bfr);
             if constexpr (SPLIT) {
               const float ls = tc_lo_scale<TM>();
 #pragma unroll
@@ -585,7 +640,17 @@ template <int NU, typename TP, int MODE>
 static cudaError_t blk_expand_t(const ExpandLaunch& p) {
   cudaError_t e = launch_expand_zpass_f32(p);
   if (e != cudaSuccess) return e;
-  const size_t smem = BlkSmem<NU>::bytes(p.g.cube, p.max_plane);
+  const uint32_t* xf = nullptr;
+  if constexpr (MODE != kSimt) {
+    // B fragments after the x-major x table in the same workspace
+    constexpr int NPX = BlkSmem<NU, MODE>::NPX;
+    uint32_t* f = reinterpret_cast<uint32_t*>(static_cast<float*>(p.tables_xmajor) + (size_t)p.natoms * p.g.cube * NPX);
+    k_expand_xfrag<NU, MODE><<<p.natoms, 128, 0, p.stream>>>(p.g.cube, static_cast<const float*>(p.tables_xmajor), f);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    xf = f;
+  }
+  const size_t smem = BlkSmem<NU, MODE>::bytes(p.g.cube, p.max_plane);
   auto kern = k_expand_blk<NU, TP, MODE>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -593,7 +658,7 @@ static cudaError_t blk_expand_t(const ExpandLaunch& p) {
   const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
   kern<<<dim3(nblk, (p.g.nbands + kWarp - 1) / kWarp), kRowsPerBlk * kWarp, smem, p.stream>>>(
       p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const float*>(p.tables),
-      static_cast<const float*>(p.tables_xmajor), static_cast<const float*>(p.t2), static_cast<TP*>(p.psi));
+      static_cast<const float*>(p.tables_xmajor), xf, static_cast<const float*>(p.t2), static_cast<TP*>(p.psi));
   return cudaGetLastError();
 }
 

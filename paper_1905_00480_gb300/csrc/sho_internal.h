@@ -64,9 +64,19 @@ struct ExpandLaunch {
   int max_plane;            // longest per-plane list
   void* tables;             // workspace [A][2][numax+1][cube] of the compute type (x and y tables)
   void* t2;                 // workspace [A][cube][P][B] of the compute type (z-pass result)
-  void* tables_xmajor = nullptr;  // optional workspace [A][cube][NPX] FP32: x table, x-major
+  void* tables_xmajor = nullptr;  // optional workspace, txm_bytes_per_point(numax) bytes per (atom, cube
+                                  // point): the FP32 x table x-major [A][cube][NPX], then (tensor forms)
+                                  // the B fragments of the x-pass; FP64-accurate form: float-pair tables
   cudaStream_t stream;
 };
+
+// Bytes per (atom, cube point) of ExpandLaunch::tables_xmajor, NPX = numax + 1 rounded up to 4: the
+// float-pair tables of the FP64-accurate form fit in 16 NPX; the FP32 x table with up to four
+// 16-byte B-fragment entries behind it in 4 NPX + 64.
+inline size_t txm_bytes_per_point(int numax) {
+  const size_t npx = (size_t)((numax + 4) & ~3);
+  return npx * 16 > npx * 4 + 64 ? npx * 16 : npx * 4 + 64;
+}
 
 struct ForcesLaunch {
   int natoms;

@@ -147,6 +147,65 @@ __device__ __forceinline__ void tc_product(float (&d)[4], float (&dlo)[4], const
   }
 }
 
+// A operand of one MMA step converted to the mode's operand type (hi and, for the split forms, lo
+// parts), for reuse across several B tiles of the same rows.
+template <TcMode M>
+struct AFrag {
+  uint32_t hi[4];
+  uint32_t lo[4];  // used by the split forms
+};
+
+// Same conversions as tc_product applies to its A elements (fragment order as there).
+template <TcMode M>
+__device__ __forceinline__ AFrag<M> make_afrag(const float* a) {
+  AFrag<M> f;
+  if constexpr (M == TcMode::TF32) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      f.hi[i] = tf32_bits(a[i]);
+      f.lo[i] = 0u;
+    }
+  } else if constexpr (M == TcMode::X3TF32) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) tf32_split(a[i], f.hi[i], f.lo[i]);
+  } else if constexpr (M == TcMode::BF16) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      f.hi[i] = pack_bf16(a[2 * i], a[2 * i + 1]);
+      f.lo[i] = 0u;
+    }
+  } else {
+    float ah[8], al[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) f16_split(a[i], ah[i], al[i]);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      f.hi[i] = pack_f16(ah[2 * i], ah[2 * i + 1]);
+      f.lo[i] = pack_f16(al[2 * i], al[2 * i + 1]);
+    }
+  }
+  return f;
+}
+
+// tc_product with the A operand already converted (make_afrag); the same MMAs in the same order.
+template <TcMode M>
+__device__ __forceinline__ void tc_product_pre(float (&d)[4], float (&dlo)[4], const AFrag<M>& a,
+                                               const BFrag<M>& b) {
+  if constexpr (M == TcMode::TF32) {
+    mma_tf32(d, a.hi, b.hi[0], b.hi[1]);
+  } else if constexpr (M == TcMode::X3TF32) {
+    mma_tf32(dlo, a.lo, b.hi[0], b.hi[1]);
+    mma_tf32(dlo, a.hi, b.lo[0], b.lo[1]);
+    mma_tf32(d, a.hi, b.hi[0], b.hi[1]);
+  } else if constexpr (M == TcMode::BF16) {
+    mma_bf16(d, a.hi, b.hi[0], b.hi[1]);
+  } else {
+    mma_f16(dlo, a.lo, b.hi[0], b.hi[1]);
+    mma_f16(dlo, a.hi, b.lo[0], b.lo[1]);
+    mma_f16(d, a.hi, b.hi[0], b.hi[1]);
+  }
+}
+
 // Scale applied to the correction accumulator before it is added to the main one.
 template <TcMode M>
 __device__ __forceinline__ float tc_lo_scale() {

@@ -77,6 +77,35 @@ def test_tc_ragged_and_clipped(mode):
 
 
 @pytest.mark.parametrize("mode", ["tf32", "3xtf32", "bf16", "split_fp16"])
+@pytest.mark.parametrize("grid,periodic,numax,cube", [
+    ((40, 36, 44), False, 2, 16),    # cubes sticking out of an open box on both sides of x
+    ((64, 52, 56), False, 7, 48),    # cube wider than the 32-point tile
+    ((34, 40, 36), True, 5, 32),     # periodic grid barely wider than the cube: wrapped tiles
+])
+def test_tc_block_expansion_edges(mode, grid, periodic, numax, cube):
+    """Expansion through the block-gather kernel (band count a multiple of 4) with the x-pass B
+    fragments precomputed per atom: tiles where the cube starts before or ends inside the tile, cubes
+    wider than a tile, and tiles that see a wrapped cube on both ends."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    rng = np.random.default_rng(310 + cube + numax)
+    h = 0.2
+    L = np.array(grid) * h
+    pos = rng.uniform(0.0, 1.0, size=(5, 3)) * L
+    pos[0] = [0.1 * h, 0.5 * L[1], 0.5 * L[2]]          # cube starts before x = 0
+    pos[1] = [L[0] - 0.3 * h, 0.3 * L[1], 0.6 * L[2]]   # cube ends past x = Nx
+    sig = rng.uniform(0.5, 0.9, size=5)
+    nb = 32
+    c = rng.standard_normal((5, oracle.nstates(numax), nb))
+    out = torch.zeros((grid[2], grid[1], grid[0], nb), dtype=torch.float32, device="cuda")
+    c_d = torch.from_numpy(c).cuda().float()
+    api.add(out, c_d, pos, sig, numax, cube, h, periodic, prec=mode)
+    ref = oracle.add(grid, h, periodic, np.zeros(out.shape), pos, sig, numax, cube, c_d.double().cpu().numpy())
+    assert rel_norm(out.double().cpu().numpy(), ref) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", ["tf32", "3xtf32", "bf16", "split_fp16"])
 def test_tc_forces(mode):
     require_gpu()
     import torch
