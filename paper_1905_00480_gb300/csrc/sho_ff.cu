@@ -49,6 +49,7 @@ struct FfProjectSmem {
     t += (size_t)NP * cube * sizeof(float2);                       // y table (pairs)
     t += (size_t)NP * cube * sizeof(double);                       // z table (FP64)
     t += (size_t)cube * sizeof(long long);                         // x offsets
+    t += (size_t)2 * cube * sizeof(int);                           // y and z grid indices
     t = (t + 15) & ~(size_t)15;
     if (!ACCR) t += (size_t)N * kWarp * sizeof(double);            // partial coefficients
     return t;
@@ -71,8 +72,10 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
   float2* phy = phx + (size_t)C * NPX;                                       // [NP][C] pairs
   double* phz = reinterpret_cast<double*>(phy + (size_t)NP * C);             // [NP][C]
   long long* xoff = reinterpret_cast<long long*>(phz + (size_t)NP * C);      // [C]
+  int* yidx = reinterpret_cast<int*>(xoff + C);                              // [C] grid row of cube row
+  int* zidx = yidx + C;                                                      // [C] grid plane of cube plane
   size_t off = ringb + (size_t)C * NPX * sizeof(float2) + (size_t)NP * C * (sizeof(float2) + sizeof(double)) +
-               (size_t)C * 8;
+               (size_t)C * 8 + (size_t)2 * C * sizeof(int);
   off = (off + 15) & ~(size_t)15;
   double* acc = ACCR ? reinterpret_cast<double*>(ring) : reinterpret_cast<double*>(smem_raw + off);  // [N][32]
 
@@ -100,6 +103,8 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
     const int jx = cube_index(at.o[0], i, g.n[0], g.periodic);
     xoff[i] = jx < 0 ? -1ll : (long long)jx * B;
+    yidx[i] = cube_index(at.o[1], i, g.n[1], g.periodic);
+    zidx[i] = cube_index(at.o[2], i, g.n[2], g.periodic);
   }
   double accr[ACCR ? N : 1];
   if constexpr (ACCR) {
@@ -115,30 +120,36 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
   const int R = max(0, iz1 - iz0) * C;
   const long long rowlen = (long long)g.n[0] * B;
   const int valid_bytes = (B - b0) * 8;
+  const int cpart = lane & 15;                                      // this lane's 16-byte chunk of a point
+  const int cbytes = min(16, max(0, valid_bytes - cpart * 16));     // its bytes inside the band tile
   // 16-byte asynchronous copies need every (grid point, band tile) run of psi to start on a 16-byte
   // boundary: an even band count and a 16-byte aligned base.  Otherwise the ring is filled with
   // plain 8-byte loads (same data layout, no overlap of loads and compute).
   const bool async_ok = ((B & 1) == 0) && (((uintptr_t)psi & 15u) == 0);
 
-  // copies of slab row r (x points x 32 bands) into ring stage r % kFfStages
-  auto issue = [&](int r) {
+  // copies of the next slab row r (x points x 32 bands) into ring stage r % kFfStages; rows are issued
+  // in order, their cube plane and row kept as counters
+  int qr = 0, qz = iz0, qy = 0;
+  auto issue_next = [&]() {
+    const int r = qr, iz = qz, iy = qy;
+    qr++;
+    if (++qy == C) {
+      qy = 0;
+      qz++;
+    }
     if (r >= R) return;
-    const int iz = iz0 + r / C, iy = r - (r / C) * C;
-    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
-    const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
+    const int jz = zidx[iz], jy = yidx[iy];
     if (jz < 0 || jy < 0) return;
     const double* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b0;
     unsigned char* st = ring + (size_t)(r % kFfStages) * C * kFfRowBytes;
     if (async_ok) {
-      for (int q = lane; q < C * 16; q += kWarp) {  // 16 chunks of 16 bytes per x point
-        const int x = q >> 4, part = q & 15;
+      // 16 chunks of 16 bytes per x point: this lane copies chunk `cpart` of every other x point
+      const unsigned char* rowb = reinterpret_cast<const unsigned char*>(row) + cpart * 16;
+      const uint32_t dst0 = ff_smem_u32(st + cpart * 16);
+      for (int x = lane >> 4; x < C; x += 2) {
         const long long o = xoff[x];
-        int nb = valid_bytes - part * 16;
-        nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
-        const void* src = (o >= 0 && nb > 0)
-                               ? (const void*)(reinterpret_cast<const unsigned char*>(row + o) + part * 16)
-                               : (const void*)psi;
-        ff_cp16(ff_smem_u32(st + x * kFfRowBytes + part * 16), src, o >= 0 ? nb : 0);
+        const bool ok = o >= 0 && cbytes > 0;
+        ff_cp16(dst0 + x * kFfRowBytes, ok ? (const void*)(rowb + o * 8) : (const void*)psi, ok ? cbytes : 0);
       }
     } else {
       double* sd = reinterpret_cast<double*>(st);
@@ -151,22 +162,19 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
 
 #pragma unroll
   for (int r = 0; r < kFfStages - 1; r++) {
-    issue(r);
+    issue_next();
     ff_commit();
   }
   float t2s[P], t2c[P];  // y-pass accumulators of the current plane, float pairs
 #pragma unroll
   for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
 
-  for (int r = 0; r < R; r++) {
+  for (int r = 0, iz = iz0, iy = 0; r < R; r++) {
     ff_wait<kFfStages - 2>();
     __syncwarp();
-    issue(r + kFfStages - 1);
+    issue_next();  // row r + kFfStages - 1
     ff_commit();
-    const int iz = iz0 + r / C, iy = r - (r / C) * C;
-    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
-    const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
-    if (jz >= 0 && jy >= 0) {
+    if (zidx[iz] >= 0 && yidx[iy] >= 0) {
       const double* st = reinterpret_cast<const double*>(ring + (size_t)(r % kFfStages) * C * kFfRowBytes);
       // x-pass (a3) as float-float dot products
       float S[NP], E[NP];
@@ -218,6 +226,10 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       }
 #pragma unroll
       for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
+    }
+    if (++iy == C) {
+      iy = 0;
+      iz++;
     }
   }
   ff_wait<0>();
@@ -471,9 +483,19 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   ff_wait<0>();
   if (!yok || !bok || nlist == 0) return;
   double* rowp = psi + ((size_t)z * Ny + y) * (size_t)Nx * B + b0 + lane;
-  for (int x = 0; x < xend; x++) {
-    const float2 v = accw[x * kWarp + lane];
-    rowp[(size_t)(xs + x) * B] += ff_to_double(v.x, v.y);
+  // loads of 16 points first, so that they are in flight together, then their adds and stores
+#pragma unroll
+  for (int x0 = 0; x0 < kFfXSeg; x0 += 16) {
+    double pv[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) pv[i] = x0 + i < xend ? rowp[(size_t)(xs + x0 + i) * B] : 0.0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      if (x0 + i < xend) {
+        const float2 v = accw[(x0 + i) * kWarp + lane];
+        rowp[(size_t)(xs + x0 + i) * B] = pv[i] + ff_to_double(v.x, v.y);
+      }
+    }
   }
 }
 

@@ -72,17 +72,21 @@ __device__ __forceinline__ double ff_to_double(float s, float c) { return f2d_in
 
 // Accumulate a*b (pairs) into the running dot product (s, c):  s + c += (a.hi + a.lo)(b.hi + b.lo),
 // dropping only a.lo*b.lo.  s carries the error-free sum of the leading products, c the errors and
-// the cross terms.
+// the cross terms.  With p = fl(a.hi b.hi) and TwoSum(s, p) = (t, (s - (t - bb)) + (p - bb)), the
+// product's exact low part a.hi b.hi - p and TwoSum's exact term p - bb are taken together as one
+// fused a.hi b.hi - bb (rounded once, as their sum would be), so a step is 10 FP32 instructions.
+// p must be the rounded product: __fmul_rn keeps the compiler from fusing it into s + a.hi b.hi,
+// which would break TwoSum's exactness (errors near 1e-8 instead of 1e-15).
 __device__ __forceinline__ void ff_dot_step(float& s, float& c, const ff a, const ff b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);           // exact low part of a.hi*b.hi
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
+  const float p = __fmul_rn(a.hi, b.hi);
   const float t = s + p;                     // TwoSum(s, p)
   const float bb = t - s;
-  const float err = (s - (t - bb)) + (p - bb);
+  float q = fmaf(a.hi, b.hi, -bb);           // (a.hi b.hi - p) + (p - bb)
+  q = fmaf(a.hi, b.lo, q);
+  q = fmaf(a.lo, b.hi, q);
+  const float r = s - (t - bb);              // TwoSum's other exact term
   s = t;
-  c += err + e;
+  c += q + r;
 }
 
 // Renormalise a pair so that |lo| <= ulp(hi)/2 (Fast2Sum; valid because |c| <= |s| here).

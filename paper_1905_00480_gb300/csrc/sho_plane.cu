@@ -235,8 +235,11 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
-      for (int r = 0; r < R; r++) {
-        const int st = r % stages, k = r / stages;
+      for (int r = 0, st = 0, k = 0; r < R; r++) {  // st = r % stages, k = r / stages
+        if (r > 0 && ++st == stages) {
+          st = 0;
+          k++;
+        }
         if (!mbar_wait(bar_empty + 8 * st, (uint32_t)((k & 1) ^ 1))) {
           ok = false;
           break;
@@ -283,8 +286,11 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   const uint32_t myt1 = t1buf + (uint32_t)warp * 8 * kT1Stride * 4;
   float* t1w = reinterpret_cast<float*>(smem_raw + (myt1 - raw));
 
-  for (int r = 0; r < R; r++) {
-    const int st = r % stages, k = r / stages;
+  for (int r = 0, st = 0, k = 0; r < R; r++) {  // st = r % stages, k = r / stages
+    if (r > 0 && ++st == stages) {
+      st = 0;
+      k++;
+    }
     const int y = ylo + r;
     if (!mbar_wait(bar_full + 8 * st, (uint32_t)(k & 1))) {
       if (lane == 0) atomicOr(status, 1);
