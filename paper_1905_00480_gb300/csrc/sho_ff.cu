@@ -286,8 +286,8 @@ __global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tab
 // ------------------------------------------------------------------------------- expansion, block gather
 // Tiles of 8 grid rows x 32 x points x 32 bands of one z plane (8 warps, one per row).  For each atom
 // whose cube meets the tile, its z-pass slice T2[a][z][P][32] (FP64), its x table as float pairs
-// [C][NPX] and its y table [NP][C] (FP64) are staged once in shared memory, double-buffered across
-// atoms, and shared by the 8 row-warps.  Each warp keeps the update of its 32 x points as float pairs
+// [C][NPX] and its y table [NP][C] (FP64) are staged once in shared memory, two atoms ahead in three
+// buffers, and shared by the 8 row-warps.  Each warp keeps the update of its 32 x points as float pairs
 // in registers and adds it to psi in FP64 at the end.  Atoms in ascending order; deterministic.
 constexpr int kFfRows = 8;
 constexpr int kFfXSeg = 32;
@@ -299,9 +299,9 @@ struct FfBlkSmem {
   __host__ __device__ static size_t buf_bytes(int cube) {
     return (size_t)P * 32 * 8 + (size_t)cube * NPX * 8 + (size_t)NP * cube * 8;
   }
-  // 2 staging buffers + per-warp update accumulators [8 warps][32 x][32 bands] float pairs + atom list
+  // 3 staging buffers + per-warp update accumulators [8 warps][32 x][32 bands] float pairs + atom list
   static size_t bytes(int cube, int max_plane) {
-    return 2 * buf_bytes(cube) + (size_t)kFfRows * kFfXSeg * kWarp * 8 + (size_t)(max_plane + 1) * sizeof(int4);
+    return 3 * buf_bytes(cube) + (size_t)kFfRows * kFfXSeg * kWarp * 8 + (size_t)(max_plane + 1) * sizeof(int4);
   }
 };
 
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   const int C = g.cube;
   const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
   const size_t bufb = SM::buf_bytes(C);
-  float2* accs = reinterpret_cast<float2*>(smem_raw + 2 * bufb);  // [warps][32 x][32 bands]
+  float2* accs = reinterpret_cast<float2*>(smem_raw + 3 * bufb);  // [warps][32 x][32 bands]
   int4* slist = reinterpret_cast<int4*>(accs + kFfRows * kFfXSeg * kWarp);  // (atom, offsets), ascending
   __shared__ int wcount[kFfRows];
   __shared__ int s_nlist;
@@ -412,15 +412,18 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   for (int x = 0; x < kFfXSeg; x++) accw[x * kWarp + lane] = make_float2(0.0f, 0.0f);
   const int xend = min(kFfXSeg, Nx - xs);       // tile points that exist on the grid
 
-  int buf = 0;
+  // three staging buffers, atoms staged two ahead: the one barrier per atom also shows that every warp
+  // is done with atom li - 1, whose buffer is refilled with atom li + 2
   if (nlist > 0) stage(slist[0], 0);
   ff_commit();
-  for (int li = 0; li < nlist; li++) {
+  if (nlist > 1) stage(slist[1], 1);
+  ff_commit();
+  for (int li = 0, buf = 0; li < nlist; li++, buf = buf == 2 ? 0 : buf + 1) {
     const int4 r = slist[li];
-    if (li + 1 < nlist) stage(slist[li + 1], buf ^ 1);
-    ff_commit();
-    ff_wait<1>();
+    ff_wait<1>();  // this thread's copies of atom li have landed
     __syncthreads();
+    if (li + 2 < nlist) stage(slist[li + 2], buf == 0 ? 2 : buf - 1);
+    ff_commit();
     const unsigned char* src = smem_raw + (size_t)buf * bufb;
     const float2* t2s = reinterpret_cast<const float2*>(src);
     const float2* txs = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8);
@@ -477,8 +480,6 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
         }
       }
     }
-    __syncthreads();
-    buf ^= 1;
   }
   ff_wait<0>();
   if (!yok || !bok || nlist == 0) return;

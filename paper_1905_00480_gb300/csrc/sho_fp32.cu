@@ -9,7 +9,7 @@
 //
 // Expansion (k_expand_blk): a gather over tiles of 8 grid rows x 32 x points x 32 bands of one z plane
 // (8 warps, one per row).  For each atom whose cube meets the tile, the z-pass slice T2[a][z][P][32]
-// and the atom's x/y tables are staged once in shared memory (cp.async, double-buffered across atoms)
+// and the atom's x/y tables are staged once in shared memory (cp.async, two atoms ahead in three buffers)
 // and shared by the 8 row-warps; each warp runs the y-pass from shared memory and accumulates the
 // x-pass into a register tile of its row (32 x points per lane on CUDA cores, or the MMA accumulator
 // fragments).  Atoms are added in ascending order and each psi element is read and written once:
@@ -314,7 +314,7 @@ struct BlkSmem {
     return (size_t)P * 32 + xtab_floats(cube) + (size_t)NP * cube;
   }
   static size_t bytes(int cube, int max_plane) {
-    return (2 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * sizeof(int4);
+    return (3 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * sizeof(int4);
   }
 };
 
@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
   const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
   const size_t bufsz = SM::buf_floats(C);
   const size_t xtab = SM::xtab_floats(C);
-  float* bufs = reinterpret_cast<float*>(smem_raw);             // 2 x [T2 slice | x table | y table]
-  float* t1all = bufs + 2 * bufsz;                               // [warps][16][36]
+  float* bufs = reinterpret_cast<float*>(smem_raw);             // 3 x [T2 slice | x data | y table]
+  float* t1all = bufs + 3 * bufsz;                               // [warps][16][36]
   int4* slist = reinterpret_cast<int4*>(t1all + kRowsPerBlk * 16 * 36);  // atoms meeting the tile, ascending
   __shared__ int wcount[kRowsPerBlk];
   __shared__ int s_nlist;
@@ -462,8 +462,8 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
   }
   if (TC) {
     for (int i = lane; i < 16 * 36; i += kWarp) t1s[i] = 0.0f;
-    // the zero fragment row (index C) of both staging buffers; staging never writes it
-    if (tid < 2 * 4 * XW) bufs[(size_t)(tid / (4 * XW)) * bufsz + P * 32 + (size_t)C * 4 * XW + tid % (4 * XW)] = 0.0f;
+    // the zero fragment row (index C) of the staging buffers; staging never writes it
+    if (tid < 3 * 4 * XW) bufs[(size_t)(tid / (4 * XW)) * bufsz + P * 32 + (size_t)C * 4 * XW + tid % (4 * XW)] = 0.0f;
   }
 
   // The plane's atoms that meet this tile, tested in parallel and compacted in ascending order.
@@ -492,15 +492,18 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
   const int nlist = s_nlist;
 
   // walk them, staging the next atom while computing the current one
-  int buf = 0;
+  // three staging buffers, atoms staged two ahead: the one barrier per atom also shows that every warp
+  // is done with atom li - 1, whose buffer is refilled with atom li + 2
   if (nlist > 0) stage(slist[0], 0);
   cp_async_commit();
-  for (int li = 0; li < nlist; li++) {
+  if (nlist > 1) stage(slist[1], 1);
+  cp_async_commit();
+  for (int li = 0, buf = 0; li < nlist; li++, buf = buf == 2 ? 0 : buf + 1) {
     const int4 r = slist[li];
-    if (li + 1 < nlist) stage(slist[li + 1], buf ^ 1);
-    cp_async_commit();
-    cp_async_wait<1>();
+    cp_async_wait<1>();  // this thread's copies of atom li have landed
     __syncthreads();
+    if (li + 2 < nlist) stage(slist[li + 2], buf == 0 ? 2 : buf - 1);
+    cp_async_commit();
     const float* t2s = bufs + (size_t)buf * bufsz;
     const float* txs = t2s + P * 32;       // x table [C][NPX], or B fragments [C + 1][4][XW] words
     const float* tys = txs + xtab;         // [NP][C]
@@ -589,8 +592,6 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
         }
       }
     }
-    __syncthreads();
-    buf ^= 1;
   }
   cp_async_wait<0>();
 
