@@ -443,6 +443,7 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
   cv.take((size_t)natoms * sizeof(AtomDev));
   if (op == SHO_OP_PROJECT) {
     cv.take((size_t)natoms * sizeof(int));
+    if (coeff_dtype == SHO_F64) cv.take(ff_t2_bytes(natoms, cube, numax, nbands));  // FP64-accurate form
     if (coeff_dtype == SHO_F32 && numax <= kTcMaxNumax) {
       // plane-sweep path (an upper bound: every (atom, plane) split into two row segments)
       const size_t segs = 2 * (size_t)natoms * cube + 1;
@@ -762,6 +763,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
     return project_planes(h, grid, at, static_cast<const float*>(psi), nbands, numax, cube, prec,
                           static_cast<float*>(coeff), s);
   SHO_TRY(begin_call(h, s));
+  if (prec == SHO_P_FF64) SHO_TRY(ensure_workspace(h, ff_t2_bytes(natoms, cube, numax, nbands)));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[0].key != key) {
     std::vector<int> order = spatial_order(grid, at);
@@ -777,9 +779,10 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   L.atoms = reinterpret_cast<const AtomDev*>(gm + h->geo[0].off[0]);
   L.natoms = natoms;
   L.numax = numax;
-  L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
+  L.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : choose_zsplit(natoms, nbands, cube, h->sms);
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
+  L.t2 = h->ws;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
                         : prec == SHO_P_FF64 ? launch_project_ff(L)
@@ -885,6 +888,7 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   const size_t o_atoms = cv.take(at.size() * sizeof(AtomDev));
   const size_t o_order = cv.take(order.size() * sizeof(int));
   const size_t o_cp = cv.take((size_t)natoms * nstates(numax + 1) * (size_t)nbands * tc);
+  const size_t o_ft2 = prec == SHO_P_FF64 ? cv.take(ff_t2_bytes(natoms, cube, numax + 1, nbands)) : 0;
   SHO_TRY(begin_call(h, s));
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
@@ -898,9 +902,10 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   P.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
   P.natoms = natoms;
   P.numax = numax + 1;
-  P.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
+  P.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : choose_zsplit(natoms, nbands, cube, h->sms);
   P.coeff = ws + o_cp;
   P.coeff_dtype = coeff_dtype;
+  P.t2 = prec == SHO_P_FF64 ? ws + o_ft2 : nullptr;
   P.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(P)
                         : prec == SHO_P_FF64 ? launch_project_ff(P)

@@ -3,25 +3,22 @@
 // Same decomposition, cube convention and deterministic reductions as the FP64 kernels
 // (sho_project.cu, sho_expand.cu).  On GB300 the FP64 pipe runs at 1/61 of the FP32 pipe, and the
 // x-pass is 89 % of the FMAs of a projection or expansion (C^3 (numax+1) of C^3 (numax+1) + C^2 P + C N
-// per atom-band).  Here that pass runs as float-float dot products on the FP32 pipe (sho_ff.cuh);
-// the 1D tables are generated in FP64 and split once, and the y- and z-passes, the cluster reduction
-// and the final accumulation into psi stay in FP64.
+// per atom-band).  Here that pass and the y-pass run as float-float dot products on the FP32 pipe
+// (sho_ff.cuh); the 1D tables are generated in FP64 and split once, and the z-pass and the final
+// accumulation into psi are FP64.
 //   projection  T1[n] = sum_x psi[x] phi_n(x): psi split into float pairs with integer instructions,
-//               then one float-float dot step per (x, n); T1 is rebuilt in FP64 per grid row.
+//               then one float-float dot step per (x, n); the y-pass sums of each cube plane go to a
+//               workspace in FP64 and a second kernel runs the z-pass over the planes in order.
 //   expansion   the update sum_a sum_n T1_a[n] phi_n(x) of each grid point is one float-float dot
 //               product over all atoms and states, its running pair kept in shared memory (block gather
 //               over 8-row x 32-point tiles), and added to psi in FP64 once.
-#include <cooperative_groups.h>
-
 #include "sho_device.cuh"
 #include "sho_ff.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace sho {
 
 // ------------------------------------------------------------------------------- projection
-constexpr int kFfStages = 3;   // cp.async ring depth (rows of 32 x points x 32 bands x 8 bytes)
+constexpr int kFfStages = 2;   // cp.async ring depth (rows of 32 x points x 32 bands x 8 bytes)
 constexpr int kFfRowBytes = 32 * 8;
 
 __device__ __forceinline__ uint32_t ff_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -36,48 +33,35 @@ __device__ __forceinline__ void ff_wait() {
 
 template <int NU>
 struct FfProjectSmem {
-  static constexpr int NP = NU + 1, NPX = (NP + 1) & ~1, N = Basis<NU>::N;
-  static constexpr bool ACCR = N <= 56;  // z-pass accumulators in registers up to numax 5
-  __host__ __device__ static size_t ring_bytes(int cube) {
-    const size_t ring = (size_t)kFfStages * cube * kFfRowBytes;
-    const size_t red = (size_t)N * kWarp * sizeof(double);
-    return ACCR ? (ring > red ? ring : red) : ring;
-  }
+  static constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
   static size_t bytes(int cube) {
-    size_t t = ring_bytes(cube);
+    size_t t = (size_t)kFfStages * cube * kFfRowBytes;             // ring of psi rows
     t += (size_t)cube * NPX * sizeof(float2);                      // x table (pairs), x-major
     t += (size_t)NP * cube * sizeof(float2);                       // y table (pairs)
-    t += (size_t)NP * cube * sizeof(double);                       // z table (FP64)
     t += (size_t)cube * sizeof(long long);                         // x offsets
     t += (size_t)2 * cube * sizeof(int);                           // y and z grid indices
-    t = (t + 15) & ~(size_t)15;
-    if (!ACCR) t += (size_t)N * kWarp * sizeof(double);            // partial coefficients
     return t;
   }
 };
 
+// x- and y-passes of one (atom, 32-band tile, slab of cube planes): T2[a][iz][P][B] of each plane of
+// the slab, converted from its float pair to FP64, goes to a workspace; the z-pass is k_project_ff_zpass.
+// Without z-pass accumulators a lane holds about 130 registers, and the ring two rows.
 template <int NU>
 __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* __restrict__ psi,
                                                       const AtomDev* __restrict__ atoms, int zsplit,
-                                                      double* __restrict__ coeff) {
+                                                      double* __restrict__ t2g) {
   using BS = Basis<NU>;
   using SM = FfProjectSmem<NU>;
-  constexpr int NP = BS::NP, P = BS::P, N = BS::N, NPX = SM::NPX;
-  constexpr bool ACCR = SM::ACCR;
+  constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int C = g.cube;
   unsigned char* ring = smem_raw;
-  const size_t ringb = SM::ring_bytes(C);
-  float2* phx = reinterpret_cast<float2*>(ring + ringb);                     // [C][NPX] pairs
+  float2* phx = reinterpret_cast<float2*>(ring + (size_t)kFfStages * C * kFfRowBytes);  // [C][NPX] pairs
   float2* phy = phx + (size_t)C * NPX;                                       // [NP][C] pairs
-  double* phz = reinterpret_cast<double*>(phy + (size_t)NP * C);             // [NP][C]
-  long long* xoff = reinterpret_cast<long long*>(phz + (size_t)NP * C);      // [C]
+  long long* xoff = reinterpret_cast<long long*>(phy + (size_t)NP * C);      // [C]
   int* yidx = reinterpret_cast<int*>(xoff + C);                              // [C] grid row of cube row
   int* zidx = yidx + C;                                                      // [C] grid plane of cube plane
-  size_t off = ringb + (size_t)C * NPX * sizeof(float2) + (size_t)NP * C * (sizeof(float2) + sizeof(double)) +
-               (size_t)C * 8 + (size_t)2 * C * sizeof(int);
-  off = (off + 15) & ~(size_t)15;
-  double* acc = ACCR ? reinterpret_cast<double*>(ring) : reinterpret_cast<double*>(smem_raw + off);  // [N][32]
 
   const int lane = threadIdx.x;
   const int a = blockIdx.z;
@@ -100,18 +84,10 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       const ff f = ff_from_double_exact(col[n]);
       phy[n * C + i] = make_float2(f.hi, f.lo);
     }
-    phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
     const int jx = cube_index(at.o[0], i, g.n[0], g.periodic);
     xoff[i] = jx < 0 ? -1ll : (long long)jx * B;
     yidx[i] = cube_index(at.o[1], i, g.n[1], g.periodic);
     zidx[i] = cube_index(at.o[2], i, g.n[2], g.periodic);
-  }
-  double accr[ACCR ? N : 1];
-  if constexpr (ACCR) {
-#pragma unroll
-    for (int k = 0; k < N; k++) accr[k] = 0.0;
-  } else {
-    for (int i = lane; i < N * kWarp; i += kWarp) acc[i] = 0.0;
   }
   __syncwarp();
 
@@ -205,24 +181,11 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     }
     __syncwarp();
     if (iy == C - 1) {
-      // z-pass (a5) in FP64 for the finished plane
-      double t2[P];
+      // the finished plane's T2 (zero for a plane outside an open grid), in FP64, for the z-pass
+      if (bok) {
+        double* out = t2g + ((size_t)a * C + iz) * P * B + b0 + lane;
 #pragma unroll
-      for (int p = 0; p < P; p++) t2[p] = ff_to_double(t2s[p], t2c[p]);
-      int k = 0;
-#pragma unroll
-      for (int nz = 0; nz < NP; nz++) {
-        const double w = phz[nz * C + iz];
-#pragma unroll
-        for (int ny = 0; ny + nz <= NU; ny++)
-#pragma unroll
-          for (int nx = 0; nx + ny + nz <= NU; nx++) {
-            if constexpr (ACCR)
-              accr[k] = fma(t2[BS::pair(nx, ny)], w, accr[k]);
-            else
-              acc[k * kWarp + lane] = fma(t2[BS::pair(nx, ny)], w, acc[k * kWarp + lane]);
-            k++;
-          }
+        for (int p = 0; p < P; p++) out[(size_t)p * B] = ff_to_double(t2s[p], t2c[p]);
       }
 #pragma unroll
       for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
@@ -233,22 +196,86 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     }
   }
   ff_wait<0>();
+}
+
+// z-pass (a5) of the FP64-accurate projection in FP64, one warp per (atom, 32-band tile):
+// c[a][(nx,ny,nz)][b] = h^3 sum_iz phi_nz(z_iz) T2[a][iz][(nx,ny)][b], planes in ascending order.
+template <int NU>
+struct FfZpassSmem {
+  static constexpr int NP = NU + 1, P = Basis<NU>::P, N = Basis<NU>::N;
+  static constexpr bool ACCR = N <= 56;  // accumulators and the plane's T2 in registers up to numax 5
+  static size_t bytes(int cube) {
+    return (size_t)NP * cube * sizeof(double) + (ACCR ? 0 : (size_t)(N + P) * kWarp * sizeof(double));
+  }
+};
+
+template <int NU>
+__global__ void __launch_bounds__(kWarp) k_project_ff_zpass(GridDev g, const AtomDev* __restrict__ atoms,
+                                                            const double* __restrict__ t2g,
+                                                            double* __restrict__ coeff) {
+  using BS = Basis<NU>;
+  using SM = FfZpassSmem<NU>;
+  constexpr int NP = BS::NP, P = BS::P, N = BS::N;
+  constexpr bool ACCR = SM::ACCR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int C = g.cube, B = g.nbands;
+  double* phz = reinterpret_cast<double*>(smem_raw);  // [NP][C]
+  double* acc = phz + (size_t)NP * C;                 // [N][32] when not in registers
+  double* t2p = acc + (size_t)N * kWarp;              // [P][32] the plane's T2, same case
+  const int lane = threadIdx.x;
+  const int a = blockIdx.y;
+  const int b = blockIdx.x * kWarp + lane;
+  const bool bok = b < B;
+  const AtomDev at = atoms[a];
+  for (int i = lane; i < C; i += kWarp) phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
   __syncwarp();
+  if (!bok) return;
+  const double* src = t2g + (size_t)a * C * P * B + b;
+  double accr[ACCR ? N : 1];
   if constexpr (ACCR) {
 #pragma unroll
-    for (int k = 0; k < N; k++) acc[k * kWarp + lane] = accr[k];
+    for (int k = 0; k < N; k++) accr[k] = 0.0;
+    for (int iz = 0; iz < C; iz++) {
+      double t2[P];
+#pragma unroll
+      for (int p = 0; p < P; p++) t2[p] = src[((size_t)iz * P + p) * B];
+      int k = 0;
+#pragma unroll
+      for (int nz = 0; nz < NP; nz++) {
+        const double w = phz[nz * C + iz];
+#pragma unroll
+        for (int ny = 0; ny + nz <= NU; ny++)
+#pragma unroll
+          for (int nx = 0; nx + ny + nz <= NU; nx++) {
+            accr[k] = fma(t2[BS::pair(nx, ny)], w, accr[k]);
+            k++;
+          }
+      }
+    }
+  } else {
+    // larger bases: accumulators and the plane's T2 in this lane's columns of shared memory, loops kept
+    // rolled (states in the order nz, ny, nx, so k counts up)
+    for (int k = 0; k < N; k++) acc[k * kWarp + lane] = 0.0;
+#pragma unroll 1
+    for (int iz = 0; iz < C; iz++) {
+      for (int p = 0; p < P; p++) t2p[p * kWarp + lane] = src[((size_t)iz * P + p) * B];
+      int k = 0;
+#pragma unroll 1
+      for (int nz = 0; nz < NP; nz++) {
+        const double w = phz[nz * C + iz];
+#pragma unroll 1
+        for (int ny = 0; ny + nz <= NU; ny++) {
+          const int p0 = BS::pair(0, ny);
+#pragma unroll 1
+          for (int nx = 0; nx + ny + nz <= NU; nx++, k++)
+            acc[k * kWarp + lane] = fma(t2p[(p0 + nx) * kWarp + lane], w, acc[k * kWarp + lane]);
+        }
+      }
+    }
   }
-
-  cg::cluster_group cl = cg::this_cluster();
-  cl.sync();
-  const int rank = (int)cl.block_rank();
   const double h3 = g.h * g.h * g.h;
-  for (int k = rank; k < N; k += zsplit) {
-    double s = 0.0;
-    for (int q = 0; q < zsplit; q++) s += cl.map_shared_rank(acc, q)[k * kWarp + lane];
-    if (bok) coeff[((long long)a * N + k) * B + b0 + lane] = s * h3;
-  }
-  cl.sync();
+  double* out = coeff + (size_t)a * N * B + b;
+  for (int k = 0; k < N; k++) out[(size_t)k * B] = (ACCR ? accr[k] : acc[k * kWarp + lane]) * h3;
 }
 
 // ------------------------------------------------------------------------------- expansion
@@ -503,24 +530,23 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
 // ------------------------------------------------------------------------------- launchers
 template <int NU>
 static cudaError_t ff_project_nu(const ProjectLaunch& p) {
+  if (!p.t2) return cudaErrorInvalidValue;
   const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
   auto kern = k_project_ff<NU>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(p.zsplit, (p.g.nbands + kWarp - 1) / kWarp, p.natoms);
-  cfg.blockDim = dim3(kWarp, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = p.stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = p.zsplit;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit,
-                            static_cast<double*>(p.coeff));
+  const unsigned nbt = (unsigned)((p.g.nbands + kWarp - 1) / kWarp);
+  kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
+      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
+  auto zk = k_project_ff_zpass<NU>;
+  e = cudaFuncSetAttribute(zk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem);
+  if (e != cudaSuccess) return e;
+  zk<<<dim3(nbt, (unsigned)p.natoms), kWarp, zsmem, p.stream>>>(p.g, p.atoms, static_cast<const double*>(p.t2),
+                                                                static_cast<double*>(p.coeff));
+  return cudaGetLastError();
 }
 
 template <int NU>

@@ -43,9 +43,10 @@ struct ProjectLaunch {
   const AtomDev* atoms;     // device [A]
   int natoms;
   int numax;
-  int zsplit;               // cube z-planes split over this many CTAs of one cluster
+  int zsplit;               // cube z-planes split over this many CTAs (of one cluster, FP64 form)
   const int* order = nullptr;  // optional device [A]: atoms in spatial (Morton) order of their cubes
   void* coeff;              // [A][N][B], FP64 or FP32
+  void* t2 = nullptr;       // FP64-accurate form: workspace [A][cube][P][B] FP64 of per-plane y-pass sums
   sho_dtype coeff_dtype;
   cudaStream_t stream;
 };
@@ -73,6 +74,20 @@ struct ExpandLaunch {
 // Bytes per (atom, cube point) of ExpandLaunch::tables_xmajor, NPX = numax + 1 rounded up to 4: the
 // float-pair tables of the FP64-accurate form fit in 16 NPX; the FP32 x table with up to four
 // 16-byte B-fragment entries behind it in 4 NPX + 64.
+// Bytes of ProjectLaunch::t2 for the FP64-accurate form.
+inline size_t ff_t2_bytes(int natoms, int cube, int numax, int nbands) {
+  return (size_t)natoms * cube * (size_t)((numax + 1) * (numax + 2) / 2) * (size_t)nbands * sizeof(double);
+}
+
+// Cube z-slabs per (atom, band tile) of the FP64-accurate projection: enough CTAs for about two waves
+// of eleven one-warp CTAs per SM, at least two planes per slab.
+inline int ff_zsplit(int natoms, int nbands, int cube, int sms) {
+  const long long ctas = (long long)natoms * ((nbands + 31) / 32);
+  int zs = 1;
+  while (zs * 2 <= cube / 2 && ctas * zs < 22LL * sms) zs *= 2;
+  return zs;
+}
+
 inline size_t txm_bytes_per_point(int numax) {
   const size_t npx = (size_t)((numax + 4) & ~3);
   return npx * 16 > npx * 4 + 64 ? npx * 16 : npx * 4 + 64;
