@@ -40,7 +40,7 @@ def _peaks():
 
 # DRAM bytes (read + write) per launch from one ncu capture of the dominant kernel of the default bench
 # step (k_expand_blk_ff<5>, 96^3 / 64 atoms / 128 bands); valid only while that kernel is unchanged.
-NCU_TRAFFIC = {"k_expand": 951.233792e6 + 845.862144e6}
+NCU_TRAFFIC = {"k_expand": 951.009536e6 + 841.406208e6}
 
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
 # 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.
@@ -159,6 +159,19 @@ def max_over_ranks(ws, value):
     t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def launches_per_step(api, psi, w, prec):
+    """Kernels of this library that one project + expand step launches (mirrors the library's dispatch)."""
+    if prec == "ff64":
+        return 2 + 3  # x/y-pass + z-pass kernels; z-pass tables, float-pair tables, block gather
+    if prec == "fp64":
+        return 1 + 2  # cluster projection; z-pass + row gather
+    tc = prec in ("tf32", "3xtf32", "bf16", "split_fp16")
+    prj = 3 if api.project_path(psi, w.numax, w.cube, w.h, w.periodic, prec=prec) == "plane" else 1
+    stream_ok = (w.nbands * psi.element_size()) % 16 == 0 and w.nbands % 4 == 0
+    add = (3 if tc else 2) if stream_ok else 2
+    return prj + add
 
 
 # --------------------------------------------------------------------------------------- our arm
@@ -343,7 +356,7 @@ def run_ours(args, ws, rank, local):
                     "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "mode": "pinned host psi + coefficients in, expanded psi out, every step; pipelined over two "
                             "device buffer sets (copy-in, compute and copy-out streams)"},
-            "gpu_launches": 3 * K,
+            "gpu_launches": launches_per_step(api, psi, w, prec) * K,
             "clocks": clk,
         }
         default_case = args.workload == WORKLOAD and prec == "ff64" and not args.bands
