@@ -65,6 +65,7 @@ struct PipeSmem {
     if (!ACCR) t += (size_t)N * kWarp * 4;                                // partial coefficients
     t = (t + 15) & ~(size_t)15;
     t += (size_t)cube * 8;                                                // x offsets
+    t += (size_t)2 * cube * 4;                                            // y and z grid indices
     return t;
   }
 };
@@ -92,6 +93,8 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
   size_t off = ringb + ((size_t)C * NPX + 2 * (size_t)NP * C + 8 * 36 + (ACCR ? 0 : (size_t)N * kWarp)) * 4;
   off = (off + 15) & ~(size_t)15;
   long long* xoff = reinterpret_cast<long long*>(smem_raw + off);          // [C] element offset of x point
+  int* yidx = reinterpret_cast<int*>(xoff + C);                            // [C] grid row of cube row
+  int* zidx = yidx + C;                                                    // [C] grid plane of cube plane
 
   const int lane = threadIdx.x, gq = lane >> 2, tq = lane & 3;
   // atoms in the plan's spatial order, so CTAs running together read overlapping cubes
@@ -110,6 +113,8 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
     phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
     const int jx = cube_index(at.o[0], i, g.n[0], g.periodic);
     xoff[i] = jx < 0 ? -1ll : (long long)jx * B;
+    yidx[i] = cube_index(at.o[1], i, g.n[1], g.periodic);
+    zidx[i] = cube_index(at.o[2], i, g.n[2], g.periodic);
   }
   float accr[ACCR ? N : 1];
   if constexpr (ACCR) {
@@ -126,12 +131,18 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
   const long long rowlen = (long long)g.n[0] * B;
   const int valid_band_bytes = (B - b0) * (int)sizeof(TP);
 
-  // Issue the copies of slab row r into its ring stage (nothing for clipped rows).
-  auto issue = [&](int r) {
+  // Issue the copies of the next slab row r into its ring stage (nothing for clipped rows); rows are
+  // issued in order, their cube plane and row kept as counters.
+  int qr = 0, qz = iz0, qy = 0;
+  auto issue_next = [&]() {
+    const int r = qr, iz = qz, iy = qy;
+    qr++;
+    if (++qy == C) {
+      qy = 0;
+      qz++;
+    }
     if (r >= R) return;
-    const int iz = iz0 + r / C, iy = r - (r / C) * C;
-    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
-    const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
+    const int jz = zidx[iz], jy = yidx[iy];
     if (jz < 0 || jy < 0) return;
     const TP* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b0;
     unsigned char* st = ring + (size_t)(r % kStages) * C * RS;
@@ -171,22 +182,19 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
 
 #pragma unroll
   for (int r = 0; r < kStages - 1; r++) {
-    issue(r);
+    issue_next();
     cp_async_commit();
   }
   float t2[P];
 #pragma unroll
   for (int p = 0; p < P; p++) t2[p] = 0.0f;
 
-  for (int r = 0; r < R; r++) {
+  for (int r = 0, iz = iz0, iy = 0; r < R; r++) {
     cp_async_wait<kStages - 2>();
     __syncwarp();
-    issue(r + kStages - 1);
+    issue_next();  // row r + kStages - 1
     cp_async_commit();
-    const int iz = iz0 + r / C, iy = r - (r / C) * C;
-    const int jz = cube_index(at.o[2], iz, g.n[2], g.periodic);
-    const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
-    if (jz >= 0 && jy >= 0) {
+    if (zidx[iz] >= 0 && yidx[iy] >= 0) {
       const TP* st = reinterpret_cast<const TP*>(ring + (size_t)(r % kStages) * C * RS);
       float t1[NP];
       if constexpr (!TC) {
@@ -266,6 +274,10 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
       }
 #pragma unroll
       for (int p = 0; p < P; p++) t2[p] = 0.0f;
+    }
+    if (++iy == C) {
+      iy = 0;
+      iz++;
     }
   }
   cp_async_wait<0>();
