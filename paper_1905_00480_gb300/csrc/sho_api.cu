@@ -459,7 +459,7 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
     cv.take(((size_t)grid->n[2] + 1) * sizeof(int));
     cv.take(std::max<size_t>(1, (size_t)natoms * cube) * sizeof(int));
     cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
-    cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
+    cv.take(t2_bytes(natoms, cube, numax, nbands, tc));
     cv.take((size_t)natoms * cube * txm_bytes_per_point(numax));
   }
   return cv.off;
@@ -814,7 +814,7 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   const size_t tc = compute_size(coeff_dtype);
   Carve cv;
   const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
-  const size_t o_t2 = cv.take((size_t)natoms * cube * npairs(numax) * (size_t)nbands * tc);
+  const size_t o_t2 = cv.take(t2_bytes(natoms, cube, numax, nbands, tc));
   const size_t o_txm = cv.take((size_t)natoms * cube * txm_bytes_per_point(numax));
   SHO_TRY(begin_call(h, s));
   const uint64_t key = geometry_key(grid, at, cube);

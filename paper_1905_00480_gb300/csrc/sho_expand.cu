@@ -17,7 +17,12 @@
 namespace sho {
 
 // ------------------------------------------------------------------------------ kernel 1: z-pass
-template <int NU, typename TCo, typename TC>
+constexpr int kZChunk = 4;  // planes per shared-memory chunk of the band-tiled z-pass output
+
+// TILED: T2 goes out band-tiled, [A][C][B/32][32][PP] with PP = tiled_pairs(P), zero for the padding
+// pairs and for bands past B (the block-gather expansion stages one contiguous [32][PP] slice per
+// atom and plane); otherwise [A][C][P][B].
+template <int NU, typename TCo, typename TC, bool TILED = false>
 __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
                                                         const TCo* __restrict__ coeff, TC* __restrict__ tables,
                                                         TC* __restrict__ t2, TC* __restrict__ txm) {
@@ -49,25 +54,64 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
     }
   }
   __syncwarp();
-  if (!bok) return;
+  if (!TILED && !bok) return;
 
-  const TCo* ca = coeff + (size_t)a * N * B + b;
-  TC* out = t2 + (size_t)a * C * P * B + b;
+  constexpr int PP = tiled_pairs(P);
+  const TCo* ca = coeff + (size_t)a * N * B + (bok ? b : 0);
+  if constexpr (!TILED) {
+    TC* out = t2 + (size_t)a * C * P * B + b;
 #pragma unroll
-  for (int ny = 0; ny < NP; ny++) {
+    for (int ny = 0; ny < NP; ny++) {
 #pragma unroll
-    for (int nx = 0; nx + ny <= NU; nx++) {
-      TC cz[NP];
+      for (int nx = 0; nx + ny <= NU; nx++) {
+        TC cz[NP];
 #pragma unroll
-      for (int nz = 0; nz < NP; nz++)
-        cz[nz] = (nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * B], (TC)0) : (TC)0;
-      const int p = BS::pair(nx, ny);
-      for (int iz = 0; iz < C; iz++) {
-        TC s = (TC)0;
+        for (int nz = 0; nz < NP; nz++)
+          cz[nz] = (nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * B], (TC)0) : (TC)0;
+        const int p = BS::pair(nx, ny);
+        for (int iz = 0; iz < C; iz++) {
+          TC s = (TC)0;
 #pragma unroll
-        for (int nz = 0; nz + nx + ny <= NU; nz++) s = fma(cz[nz], phz[nz * C + iz], s);
-        out[((size_t)iz * P + p) * B] = s;
+          for (int nz = 0; nz + nx + ny <= NU; nz++) s = fma(cz[nz], phz[nz * C + iz], s);
+          out[((size_t)iz * P + p) * B] = s;
+        }
       }
+    }
+  } else {
+    // band-tiled: kZChunk planes at a time are assembled in shared memory as [plane][32][PP] (this
+    // lane's row of pairs, zero padded) and each plane's [32][PP] slice, contiguous in T2, is written
+    // with 16-byte stores (a lane-strided store per pair would leave DRAM sectors half written)
+    TC* stage = phz + (size_t)NP * C;  // [kZChunk][32][PP]
+    const size_t nbt = gridDim.x;
+    for (int z0 = 0; z0 < C; z0 += kZChunk) {
+      const int nzc = min(kZChunk, C - z0);
+#pragma unroll
+      for (int ny = 0; ny < NP; ny++) {
+#pragma unroll
+        for (int nx = 0; nx + ny <= NU; nx++) {
+          TC cz[NP];
+#pragma unroll
+          for (int nz = 0; nz < NP; nz++)
+            cz[nz] = (bok && nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * B], (TC)0) : (TC)0;
+          const int p = BS::pair(nx, ny);
+          for (int i = 0; i < nzc; i++) {
+            TC s = (TC)0;
+#pragma unroll
+            for (int nz = 0; nz + nx + ny <= NU; nz++) s = fma(cz[nz], phz[nz * C + z0 + i], s);
+            stage[((size_t)i * kWarp + lane) * PP + p] = s;
+          }
+        }
+      }
+      for (int i = 0; i < nzc; i++)
+#pragma unroll
+        for (int p = P; p < PP; p++) stage[((size_t)i * kWarp + lane) * PP + p] = (TC)0;
+      __syncwarp();
+      for (int i = 0; i < nzc; i++) {
+        const float4* src = reinterpret_cast<const float4*>(stage + (size_t)i * kWarp * PP);
+        float4* dst = reinterpret_cast<float4*>(t2 + (((size_t)a * C + z0 + i) * nbt + blockIdx.x) * kWarp * PP);
+        for (int q = lane; q < kWarp * PP / 4; q += kWarp) dst[q] = src[q];
+      }
+      __syncwarp();
     }
   }
 }
@@ -208,6 +252,17 @@ static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
 }
 
 template <int NU>
+static cudaError_t zpass_f32_tiled_nu(const ExpandLaunch& p) {
+  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  constexpr int PP = tiled_pairs(Basis<NU>::P);
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float) + (size_t)kZChunk * kWarp * PP * sizeof(float);
+  k_expand_zpass<NU, float, float, true><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+      p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
+      static_cast<float*>(p.tables_xmajor));
+  return cudaGetLastError();
+}
+
+template <int NU>
 static cudaError_t zpass_f64_nu(const ExpandLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double);
@@ -245,6 +300,22 @@ cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p) {
     case 7: return zpass_f32_nu<7>(p);
     case 8: return zpass_f32_nu<8>(p);
     case 9: return zpass_f32_nu<9>(p);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_expand_zpass_f32_tiled(const ExpandLaunch& p) {
+  switch (p.numax) {
+    case 0: return zpass_f32_tiled_nu<0>(p);
+    case 1: return zpass_f32_tiled_nu<1>(p);
+    case 2: return zpass_f32_tiled_nu<2>(p);
+    case 3: return zpass_f32_tiled_nu<3>(p);
+    case 4: return zpass_f32_tiled_nu<4>(p);
+    case 5: return zpass_f32_tiled_nu<5>(p);
+    case 6: return zpass_f32_tiled_nu<6>(p);
+    case 7: return zpass_f32_tiled_nu<7>(p);
+    case 8: return zpass_f32_tiled_nu<8>(p);
+    case 9: return zpass_f32_tiled_nu<9>(p);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -8,7 +8,7 @@
 // those of the CUDA-core kernel.
 //
 // Expansion (k_expand_blk): a gather over tiles of 8 grid rows x 32 x points x 32 bands of one z plane
-// (8 warps, one per row).  For each atom whose cube meets the tile, the z-pass slice T2[a][z][P][32]
+// (8 warps, one per row).  For each atom whose cube meets the tile, the z-pass slice T2[a][z][32][PP] (band-tiled)
 // and the atom's x/y tables are staged once in shared memory (cp.async, two atoms ahead in three buffers)
 // and shared by the 8 row-warps; each warp runs the y-pass from shared memory and accumulates the
 // x-pass into a register tile of its row (32 x points per lane on CUDA cores, or the MMA accumulator
@@ -314,16 +314,16 @@ struct XFrag {
 template <int NU, int MODE>
 struct BlkSmem {
   static constexpr bool TC = MODE != kSimt;
-  static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 3) & ~3;
+  static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 3) & ~3, PP = tiled_pairs(P);
   static constexpr int XW = TC ? XFrag<TC ? (TcMode)MODE : TcMode::TF32>::WORDS : 0;
   // x data of one atom: CUDA cores the x table [C][NPX] (x-major); tensor forms the B fragments
   // [C + 1][4] of XW words, row C all zero (the fragment of points outside the cube)
   __host__ __device__ static size_t xtab_floats(int cube) {
     return TC ? (size_t)(cube + 1) * 4 * XW : (size_t)NPX * cube;
   }
-  // per buffer: T2 slice [P][32] + x data + y table [NP][C]
+  // per buffer: T2 slice [32 bands][PP] + x data + y table [NP][C]
   __host__ __device__ static size_t buf_floats(int cube) {
-    return (size_t)P * 32 + xtab_floats(cube) + (size_t)NP * cube;
+    return (size_t)PP * 32 + xtab_floats(cube) + (size_t)NP * cube;
   }
   static size_t bytes(int cube, int max_plane) {
     return (3 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * sizeof(int4);
@@ -357,10 +357,10 @@ __global__ void k_expand_xfrag(int cube, const float* __restrict__ txm, uint32_t
   }
 }
 
-// Tensor forms: at most 128 registers, two blocks of 8 warps per SM; the CUDA-core form keeps the
-// compiler's choice (64 to 106 registers, three or four blocks).
+// Tensor forms: at most 128 registers, two blocks of 8 warps per SM; the CUDA-core form on FP32 psi at
+// most 64 (four blocks); on BF16 psi the compiler's choice (about 80 registers, three blocks).
 template <int NU, typename TP, int MODE>
-__global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_expand_blk(GridDev g, const AtomDev* __restrict__ atoms,
+__global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeof(TP) == 4 ? 4 : 0) k_expand_blk(GridDev g, const AtomDev* __restrict__ atoms,
                                                                     const int* __restrict__ plane_ptr,
                                                                     const int* __restrict__ plane_atoms,
                                                                     const float* __restrict__ tables,
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
   using BS = Basis<NU>;
   using SM = BlkSmem<NU, MODE>;
   constexpr bool TC = MODE != kSimt;
-  constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX, XW = SM::XW;
+  constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX, XW = SM::XW, PP = SM::PP;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA;
   static_assert(!TC || K >= NP, "one MMA K step covers the states");
@@ -428,27 +428,21 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
   auto stage = [&](const int4 r, int buf) {
     const int a = r.x, iz = r.w;
     float* dst = bufs + (size_t)buf * bufsz;
-    const float* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
-    const int band_bytes = (B - b0) * 4;
-    for (int q = tid; q < P * 8; q += kRowsPerBlk * kWarp) {
-      const int p = q >> 3, part = q & 7;
-      int nb = band_bytes - part * 16;
-      nb = nb < 0 ? 0 : (nb > 16 ? 16 : nb);
-      cp_async16(smem_u32(dst + p * 32 + part * 4), nb > 0 ? (const void*)(src_t2 + (size_t)p * B + part * 4)
-                                                           : (const void*)t2, nb);
-    }
+    // band-tiled T2: the [32][PP] slice of (atom, plane, band tile) is contiguous
+    const float* src_t2 = t2 + (((size_t)a * C + iz) * gridDim.y + blockIdx.y) * kWarp * PP;
+    for (int q = tid; q < 8 * PP; q += kRowsPerBlk * kWarp) cp_async16(smem_u32(dst + q * 4), src_t2 + q * 4, 16);
     if constexpr (TC) {
       const uint32_t* src_f = xf + (size_t)a * C * 4 * XW;     // B fragments [C][4] (row C stays zero)
       for (int q = tid; q < C * XW; q += kRowsPerBlk * kWarp)
-        cp_async16(smem_u32(dst + P * 32 + q * 4), src_f + q * 4, 16);
+        cp_async16(smem_u32(dst + PP * 32 + q * 4), src_f + q * 4, 16);
     } else {
       const float* src_x = txm + (size_t)a * C * NPX;           // x table, x-major [C][NPX]
       for (int q = tid; q < C * NPX / 4; q += kRowsPerBlk * kWarp)
-        cp_async16(smem_u32(dst + P * 32 + q * 4), src_x + q * 4, 16);
+        cp_async16(smem_u32(dst + PP * 32 + q * 4), src_x + q * 4, 16);
     }
     const float* src_y = tables + (size_t)a * 2 * NP * C + (size_t)NP * C;  // y table [NP][C]
     for (int q = tid; q < NP * C / 4; q += kRowsPerBlk * kWarp)
-      cp_async16(smem_u32(dst + P * 32 + xtab + q * 4), src_y + q * 4, 16);
+      cp_async16(smem_u32(dst + PP * 32 + xtab + q * 4), src_y + q * 4, 16);
   };
 
   // register tile: 32 x points of this warp's row, 32 bands
@@ -475,7 +469,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
   if (TC) {
     for (int i = lane; i < 16 * 36; i += kWarp) t1s[i] = 0.0f;
     // the zero fragment row (index C) of the staging buffers; staging never writes it
-    if (tid < 3 * 4 * XW) bufs[(size_t)(tid / (4 * XW)) * bufsz + P * 32 + (size_t)C * 4 * XW + tid % (4 * XW)] = 0.0f;
+    if (tid < 3 * 4 * XW) bufs[(size_t)(tid / (4 * XW)) * bufsz + PP * 32 + (size_t)C * 4 * XW + tid % (4 * XW)] = 0.0f;
   }
 
   // The plane's atoms that meet this tile, tested in parallel and compacted in ascending order.
@@ -517,21 +511,28 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE == kSimt ? 0 : 2) k_
     if (li + 2 < nlist) stage(slist[li + 2], buf == 0 ? 2 : buf - 1);
     cp_async_commit();
     const float* t2s = bufs + (size_t)buf * bufsz;
-    const float* txs = t2s + P * 32;       // x table [C][NPX], or B fragments [C + 1][4][XW] words
+    const float* txs = t2s + PP * 32;      // x table [C][NPX], or B fragments [C + 1][4][XW] words
     const float* tys = txs + xtab;         // [NP][C]
     int iy = r.y + warp;  // cube row of this warp's grid row
     if (g.periodic && iy >= Ny) iy -= Ny;
     if (yok && iy >= 0 && iy < C) {
-      // y-pass: T1[nx] for this row, lane = band
-      float t1[NP];
+      // y-pass: T1[nx] for this row, lane = band; the lane's [PP] row of pairs comes in 16-byte loads
+      float t1[NP], wy[NP];
 #pragma unroll
-      for (int n = 0; n < NP; n++) t1[n] = 0.0f;
-#pragma unroll
-      for (int ny = 0; ny < NP; ny++) {
-        const float w = tys[ny * C + iy];
-#pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fmaf(t2s[BS::pair(nx, ny) * 32 + lane], w, t1[nx]);
+      for (int n = 0; n < NP; n++) {
+        t1[n] = 0.0f;
+        wy[n] = tys[n * C + iy];
       }
+      const float4* row4 = reinterpret_cast<const float4*>(t2s + lane * PP);
+#pragma unroll
+      for (int ny = 0; ny < NP; ny++)
+#pragma unroll
+        for (int nx = 0; nx + ny <= NU; nx++) {
+          const int p = BS::pair(nx, ny);
+          const float4 v = row4[p >> 2];  // the 16-byte chunk holding pair p (one load per chunk after unrolling)
+          const float tv = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+          t1[nx] = fmaf(tv, wy[ny], t1[nx]);
+        }
       const int dx = r.z;  // cube index of tile point x is dx + x (mod Nx when periodic)
       if constexpr (!TC) {
 #pragma unroll
@@ -651,7 +652,7 @@ static cudaError_t pipe_project_t(const ProjectLaunch& p) {
 
 template <int NU, typename TP, int MODE>
 static cudaError_t blk_expand_t(const ExpandLaunch& p) {
-  cudaError_t e = launch_expand_zpass_f32(p);
+  cudaError_t e = launch_expand_zpass_f32_tiled(p);
   if (e != cudaSuccess) return e;
   const uint32_t* xf = nullptr;
   if constexpr (MODE != kSimt) {

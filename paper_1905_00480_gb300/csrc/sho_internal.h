@@ -64,7 +64,8 @@ struct ExpandLaunch {
   const int* plane_atoms;   //   plane_atoms[plane_ptr[z] .. plane_ptr[z+1]), ascending
   int max_plane;            // longest per-plane list
   void* tables;             // workspace [A][2][numax+1][cube] of the compute type (x and y tables)
-  void* t2;                 // workspace [A][cube][P][B] of the compute type (z-pass result)
+  void* t2;                 // workspace [A][cube][P][B] of the compute type (z-pass result); the FP32
+                            // block gather takes it band-tiled, t2_bytes() covers both
   void* tables_xmajor = nullptr;  // optional workspace, txm_bytes_per_point(numax) bytes per (atom, cube
                                   // point): the FP32 x table x-major [A][cube][NPX], then (tensor forms)
                                   // the B fragments of the x-pass; FP64-accurate form: float-pair tables
@@ -74,6 +75,16 @@ struct ExpandLaunch {
 // Bytes per (atom, cube point) of ExpandLaunch::tables_xmajor, NPX = numax + 1 rounded up to 4: the
 // float-pair tables of the FP64-accurate form fit in 16 NPX; the FP32 x table with up to four
 // 16-byte B-fragment entries behind it in 4 NPX + 64.
+// Bytes of ExpandLaunch::t2: [A][cube][P][B] of the compute type, or band-tiled FP32
+// [A][cube][ceil(B/32)][32][tiled_pairs(P)], whichever is larger.
+inline size_t t2_bytes(int natoms, int cube, int numax, int nbands, size_t elem) {
+  const size_t P = (size_t)((numax + 1) * (numax + 2) / 2);
+  const size_t PP = ((P + 3) / 4 * 4) % 8 == 0 ? (P + 3) / 4 * 4 + 4 : (P + 3) / 4 * 4;
+  const size_t plain = (size_t)natoms * cube * P * (size_t)nbands * elem;
+  const size_t tiled = (size_t)natoms * cube * (size_t)((nbands + 31) / 32) * 32 * PP * sizeof(float);
+  return plain > tiled ? plain : tiled;
+}
+
 // Bytes of ProjectLaunch::t2 for the FP64-accurate form.
 inline size_t ff_t2_bytes(int natoms, int cube, int numax, int nbands) {
   return (size_t)natoms * cube * (size_t)((numax + 1) * (numax + 2) / 2) * (size_t)nbands * sizeof(double);
@@ -195,6 +206,7 @@ constexpr int kBlochMaxNx = 448;  // the expansion keeps one grid row of 32 comp
 cudaError_t launch_usu(int op, const UsuLaunch& p);
 bool usu_supported_nproj(int n);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
+cudaError_t launch_expand_zpass_f32_tiled(const ExpandLaunch& p);  // T2 as [A][C][B/32][32][tiled_pairs(P)]
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
 cudaError_t launch_dmatrix(int natoms, int nstates, int nbands, sho_dtype dt, const void* D, const void* c, void* d,
                            cudaStream_t s);

@@ -75,9 +75,16 @@ def test_admission_respects_budget():
     systems = _systems(3, seed=5)[:3]
     resident = sum(s["psi"].numel() * 4 for s in systems) + sum(
         len(s["pos"]) * oracle.nstates(s["numax"]) * s["psi"].shape[3] * 4 for s in systems)
-    # the largest expansion workspace of these systems (z-pass intermediate dominates), plus plan slack
-    need = max(len(s["pos"]) * 32 * (s["numax"] + 1) * (s["numax"] + 2) // 2 * s["psi"].shape[3] * 4
-               for s in systems)
+    # the largest expansion workspace of these systems (the z-pass intermediate dominates: FP32, stored
+    # band-tiled [A][cube][B/32][32][PP] for the block gather, PP = pairs rounded up to 4, plus 4 when
+    # that is a multiple of 8), plus plan slack
+    def t2_bytes(s):
+        P = (s["numax"] + 1) * (s["numax"] + 2) // 2
+        PP = (P + 3) // 4 * 4
+        PP += 4 if PP % 8 == 0 else 0
+        B = s["psi"].shape[3]
+        return len(s["pos"]) * 32 * max(P * B, (B + 31) // 32 * 32 * PP) * 4
+    need = max(t2_bytes(s) for s in systems)
     budget = resident + need + (1 << 20)
     with Server(0, budget_bytes=budget, slots=4) as srv:
         _run(srv, systems, ["expand", "expand"], concurrent=True)
