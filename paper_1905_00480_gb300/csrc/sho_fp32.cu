@@ -8,12 +8,12 @@
 // those of the CUDA-core kernel.
 //
 // Expansion (k_expand_blk): a gather over tiles of 8 grid rows x 32 x points x 32 bands of one z plane
-// (8 warps, one per row).  For each atom whose cube meets the tile, the z-pass slice T2[a][z][32][PP] (band-tiled)
-// and the atom's x/y tables are staged once in shared memory (cp.async, two atoms ahead in three buffers)
-// and shared by the 8 row-warps; each warp runs the y-pass from shared memory and accumulates the
-// x-pass into a register tile of its row (32 x points per lane on CUDA cores, or the MMA accumulator
-// fragments).  Atoms are added in ascending order and each psi element is read and written once:
-// deterministic, no atomics.
+// (8 warps, one per row).  For each atom whose cube meets the tile, the z-pass slice T2[a][z][32][PP]
+// (band-tiled) and the atom's x/y tables are staged once in shared memory (cp.async, in groups of one
+// or two atoms staged two groups ahead) and shared by the 8 row-warps; each warp runs the y-pass from
+// shared memory and accumulates the x-pass into a register tile of its row (32 x points per lane on
+// CUDA cores, or the MMA accumulator fragments).  Atoms are added in ascending order and each psi
+// element is read and written once: deterministic, no atomics.
 #include <cooperative_groups.h>
 
 #include "sho_tc.cuh"
@@ -301,6 +301,12 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
 
 // ------------------------------------------------------------------------------- expansion
 constexpr int kRowsPerBlk = 8;       // grid rows (warps) per CTA
+// atoms staged and computed per block barrier: two for the CUDA-core x-pass (its per-atom work is
+// short), one for the MMA forms (measured faster with the smaller staging footprint)
+template <int MODE>
+struct AtomsPerBarrier {
+  static constexpr int value = MODE == kSimt ? 2 : 1;
+};
 constexpr int kXSeg = 32;            // x points per tile
 
 // Expansion x-pass B fragments, per atom and cube x point: entry (ix, t) is the fragment that lane
@@ -316,6 +322,7 @@ struct BlkSmem {
   static constexpr bool TC = MODE != kSimt;
   static constexpr int NP = NU + 1, P = Basis<NU>::P, NPX = (NP + 3) & ~3, PP = tiled_pairs(P);
   static constexpr int XW = TC ? XFrag<TC ? (TcMode)MODE : TcMode::TF32>::WORDS : 0;
+  static constexpr int kAtomsPerBarrier = AtomsPerBarrier<MODE>::value;
   // x data of one atom: CUDA cores the x table [C][NPX] (x-major); tensor forms the B fragments
   // [C + 1][4] of XW words, row C all zero (the fragment of points outside the cube)
   __host__ __device__ static size_t xtab_floats(int cube) {
@@ -325,8 +332,10 @@ struct BlkSmem {
   __host__ __device__ static size_t buf_floats(int cube) {
     return (size_t)PP * 32 + xtab_floats(cube) + (size_t)NP * cube;
   }
+  // 3 groups of kAtomsPerBarrier staging buffers + (tensor forms) per-warp T1 transposes + atom list
   static size_t bytes(int cube, int max_plane) {
-    return (3 * buf_floats(cube) + (size_t)kRowsPerBlk * 16 * 36) * 4 + (size_t)(max_plane + 1) * sizeof(int4);
+    return (3 * kAtomsPerBarrier * buf_floats(cube) + (TC ? (size_t)kRowsPerBlk * 16 * 36 : 0)) * 4 +
+           (size_t)(max_plane + 1) * sizeof(int4);
   }
 };
 
@@ -372,6 +381,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
   using SM = BlkSmem<NU, MODE>;
   constexpr bool TC = MODE != kSimt;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX, XW = SM::XW, PP = SM::PP;
+  constexpr int kAtomsPerBarrier = SM::kAtomsPerBarrier;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA;
   static_assert(!TC || K >= NP, "one MMA K step covers the states");
@@ -380,9 +390,9 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
   const int Nx = g.n[0], Ny = g.n[1], Nz = g.n[2];
   const size_t bufsz = SM::buf_floats(C);
   const size_t xtab = SM::xtab_floats(C);
-  float* bufs = reinterpret_cast<float*>(smem_raw);             // 3 x [T2 slice | x data | y table]
-  float* t1all = bufs + 3 * bufsz;                               // [warps][16][36]
-  int4* slist = reinterpret_cast<int4*>(t1all + kRowsPerBlk * 16 * 36);  // atoms meeting the tile, ascending
+  float* bufs = reinterpret_cast<float*>(smem_raw);  // 3 x kAtomsPerBarrier x [T2 slice | x data | y table]
+  float* t1all = bufs + 3 * kAtomsPerBarrier * bufsz;            // [warps][16][36] (tensor forms)
+  int4* slist = reinterpret_cast<int4*>(t1all + (TC ? kRowsPerBlk * 16 * 36 : 0));  // atoms meeting the tile, ascending
   __shared__ int wcount[kRowsPerBlk];
   __shared__ int s_nlist;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
@@ -469,7 +479,8 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
   if (TC) {
     for (int i = lane; i < 16 * 36; i += kWarp) t1s[i] = 0.0f;
     // the zero fragment row (index C) of the staging buffers; staging never writes it
-    if (tid < 3 * 4 * XW) bufs[(size_t)(tid / (4 * XW)) * bufsz + PP * 32 + (size_t)C * 4 * XW + tid % (4 * XW)] = 0.0f;
+    for (int i = tid; i < 3 * kAtomsPerBarrier * 4 * XW; i += kRowsPerBlk * kWarp)
+      bufs[(size_t)(i / (4 * XW)) * bufsz + PP * 32 + (size_t)C * 4 * XW + i % (4 * XW)] = 0.0f;
   }
 
   // The plane's atoms that meet this tile, tested in parallel and compacted in ascending order.
@@ -497,109 +508,121 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
   }
   const int nlist = s_nlist;
 
-  // walk them, staging the next atom while computing the current one
-  // three staging buffers, atoms staged two ahead: the one barrier per atom also shows that every warp
-  // is done with atom li - 1, whose buffer is refilled with atom li + 2
-  if (nlist > 0) stage(slist[0], 0);
+  // walk them in groups of kAtomsPerBarrier atoms, three groups of staging buffers, groups staged two
+  // ahead: the one barrier per group also shows that every warp is done with group gi - 1, whose
+  // buffers are refilled with group gi + 2
+  const int ngroups = (nlist + kAtomsPerBarrier - 1) / kAtomsPerBarrier;
+  auto stage_group = [&](int gi, int slot) {
+    for (int k = 0; k < kAtomsPerBarrier; k++) {
+      const int li = gi * kAtomsPerBarrier + k;
+      if (li < nlist) stage(slist[li], slot * kAtomsPerBarrier + k);
+    }
+  };
+  if (ngroups > 0) stage_group(0, 0);
   cp_async_commit();
-  if (nlist > 1) stage(slist[1], 1);
+  if (ngroups > 1) stage_group(1, 1);
   cp_async_commit();
-  for (int li = 0, buf = 0; li < nlist; li++, buf = buf == 2 ? 0 : buf + 1) {
-    const int4 r = slist[li];
-    cp_async_wait<1>();  // this thread's copies of atom li have landed
+  for (int gi = 0, slot = 0; gi < ngroups; gi++, slot = slot == 2 ? 0 : slot + 1) {
+    cp_async_wait<1>();  // this thread's copies of group gi have landed
     __syncthreads();
-    if (li + 2 < nlist) stage(slist[li + 2], buf == 0 ? 2 : buf - 1);
+    if (gi + 2 < ngroups) stage_group(gi + 2, slot == 0 ? 2 : slot - 1);
     cp_async_commit();
-    const float* t2s = bufs + (size_t)buf * bufsz;
-    const float* txs = t2s + PP * 32;      // x table [C][NPX], or B fragments [C + 1][4][XW] words
-    const float* tys = txs + xtab;         // [NP][C]
-    int iy = r.y + warp;  // cube row of this warp's grid row
-    if (g.periodic && iy >= Ny) iy -= Ny;
-    if (yok && iy >= 0 && iy < C) {
-      // y-pass: T1[nx] for this row, lane = band; the lane's [PP] row of pairs comes in 16-byte loads
-      float t1[NP], wy[NP];
+    for (int k = 0; k < kAtomsPerBarrier; k++) {
+      const int li = gi * kAtomsPerBarrier + k;
+      if (li >= nlist) break;
+      const int4 r = slist[li];
+      const int buf = slot * kAtomsPerBarrier + k;
+      const float* t2s = bufs + (size_t)buf * bufsz;
+      const float* txs = t2s + PP * 32;      // x table [C][NPX], or B fragments [C + 1][4][XW] words
+      const float* tys = txs + xtab;         // [NP][C]
+      int iy = r.y + warp;  // cube row of this warp's grid row
+      if (g.periodic && iy >= Ny) iy -= Ny;
+      if (yok && iy >= 0 && iy < C) {
+        // y-pass: T1[nx] for this row, lane = band; the lane's [PP] row of pairs comes in 16-byte loads
+        float t1[NP], wy[NP];
 #pragma unroll
-      for (int n = 0; n < NP; n++) {
-        t1[n] = 0.0f;
-        wy[n] = tys[n * C + iy];
-      }
-      const float4* row4 = reinterpret_cast<const float4*>(t2s + lane * PP);
-#pragma unroll
-      for (int ny = 0; ny < NP; ny++)
-#pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++) {
-          const int p = BS::pair(nx, ny);
-          const float4 v = row4[p >> 2];  // the 16-byte chunk holding pair p (one load per chunk after unrolling)
-          const float tv = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
-          t1[nx] = fmaf(tv, wy[ny], t1[nx]);
+        for (int n = 0; n < NP; n++) {
+          t1[n] = 0.0f;
+          wy[n] = tys[n * C + iy];
         }
-      const int dx = r.z;  // cube index of tile point x is dx + x (mod Nx when periodic)
-      if constexpr (!TC) {
+        const float4* row4 = reinterpret_cast<const float4*>(t2s + lane * PP);
 #pragma unroll
-        for (int x = 0; x < kXSeg; x++) {
-          int ix = dx + x;
-          if (g.periodic && ix >= Nx) ix -= Nx;
-          if (ix >= 0 && ix < C) {
-            float s = accr[x];
-            const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
+        for (int ny = 0; ny < NP; ny++)
 #pragma unroll
-            for (int q = 0; q < NPX / 4; q++) {
-              const float4 f = f4[q];
-              if (4 * q + 0 < NP) s = fmaf(t1[4 * q + 0], f.x, s);
-              if (4 * q + 1 < NP) s = fmaf(t1[4 * q + 1], f.y, s);
-              if (4 * q + 2 < NP) s = fmaf(t1[4 * q + 2], f.z, s);
-              if (4 * q + 3 < NP) s = fmaf(t1[4 * q + 3], f.w, s);
+          for (int nx = 0; nx + ny <= NU; nx++) {
+            const int p = BS::pair(nx, ny);
+            const float4 v = row4[p >> 2];  // the 16-byte chunk holding pair p (one load per chunk after unrolling)
+            const float tv = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+            t1[nx] = fmaf(tv, wy[ny], t1[nx]);
+          }
+        const int dx = r.z;  // cube index of tile point x is dx + x (mod Nx when periodic)
+        if constexpr (!TC) {
+#pragma unroll
+          for (int x = 0; x < kXSeg; x++) {
+            int ix = dx + x;
+            if (g.periodic && ix >= Nx) ix -= Nx;
+            if (ix >= 0 && ix < C) {
+              float s = accr[x];
+              const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
+#pragma unroll
+              for (int q = 0; q < NPX / 4; q++) {
+                const float4 f = f4[q];
+                if (4 * q + 0 < NP) s = fmaf(t1[4 * q + 0], f.x, s);
+                if (4 * q + 1 < NP) s = fmaf(t1[4 * q + 1], f.y, s);
+                if (4 * q + 2 < NP) s = fmaf(t1[4 * q + 2], f.z, s);
+                if (4 * q + 3 < NP) s = fmaf(t1[4 * q + 3], f.w, s);
+              }
+              accr[x] = s;
             }
-            accr[x] = s;
           }
-        }
-      } else {
+        } else {
 #pragma unroll
-        for (int n = 0; n < NP; n++) t1s[n * 36 + lane] = t1[n];
-        __syncwarp();
-        AFrag<TM> afr[2];  // converted once, used by the four x tiles
-#pragma unroll
-        for (int m = 0; m < 2; m++) {
-          float av[NA];
-#pragma unroll
-          for (int i = 0; i < NA; i++) {
-            int mm, k;
-            a_coord<TM>(i, gq, tq, mm, k);
-            av[i] = t1s[k * 36 + 16 * m + mm];
-          }
-          afr[m] = make_afrag<TM>(av);
-        }
-        __syncwarp();
-        constexpr bool SPLIT = TM == TcMode::X3TF32 || TM == TcMode::SPLIT16;
-        const uint32_t* xfs = reinterpret_cast<const uint32_t*>(txs);
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-          // this lane's column n = gq of tile j is cube point ix; outside the cube the zero row C
-          int ix = dx + 8 * j + gq;
-          if (g.periodic && ix >= Nx) ix -= Nx;
-          ix = (unsigned)ix < (unsigned)C ? ix : C;
-          BFrag<TM> bfr;
-          if constexpr (XW == 4) {
-            const uint4 v = *reinterpret_cast<const uint4*>(xfs + (ix * 4 + tq) * 4);
-            bfr.hi[0] = v.x;
-            bfr.hi[1] = v.y;
-            bfr.lo[0] = v.z;
-            bfr.lo[1] = v.w;
-          } else {
-            const uint2 v = *reinterpret_cast<const uint2*>(xfs + (ix * 4 + tq) * 2);
-            bfr.hi[0] = v.x;
-            bfr.hi[1] = v.y;
-            bfr.lo[0] = bfr.lo[1] = 0u;
-          }
+          for (int n = 0; n < NP; n++) t1s[n * 36 + lane] = t1[n];
+          __syncwarp();
+          AFrag<TM> afr[2];  // converted once, used by the four x tiles
 #pragma unroll
           for (int m = 0; m < 2; m++) {
-            float(&d)[4] = *reinterpret_cast<float(*)[4]>(&accr[(j * 2 + m) * 4]);
-            float dl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            tc_product_pre<TM>(d, dl, afr[m], bfr);
-            if constexpr (SPLIT) {
-              const float ls = tc_lo_scale<TM>();
+            float av[NA];
 #pragma unroll
-              for (int e = 0; e < 4; e++) d[e] = fmaf(ls, dl[e], d[e]);
+            for (int i = 0; i < NA; i++) {
+              int mm, k;
+              a_coord<TM>(i, gq, tq, mm, k);
+              av[i] = t1s[k * 36 + 16 * m + mm];
+            }
+            afr[m] = make_afrag<TM>(av);
+          }
+          __syncwarp();
+          constexpr bool SPLIT = TM == TcMode::X3TF32 || TM == TcMode::SPLIT16;
+          const uint32_t* xfs = reinterpret_cast<const uint32_t*>(txs);
+#pragma unroll
+          for (int j = 0; j < 4; j++) {
+            // this lane's column n = gq of tile j is cube point ix; outside the cube the zero row C
+            int ix = dx + 8 * j + gq;
+            if (g.periodic && ix >= Nx) ix -= Nx;
+            ix = (unsigned)ix < (unsigned)C ? ix : C;
+            BFrag<TM> bfr;
+            if constexpr (XW == 4) {
+              const uint4 v = *reinterpret_cast<const uint4*>(xfs + (ix * 4 + tq) * 4);
+              bfr.hi[0] = v.x;
+              bfr.hi[1] = v.y;
+              bfr.lo[0] = v.z;
+              bfr.lo[1] = v.w;
+            } else {
+              const uint2 v = *reinterpret_cast<const uint2*>(xfs + (ix * 4 + tq) * 2);
+              bfr.hi[0] = v.x;
+              bfr.hi[1] = v.y;
+              bfr.lo[0] = bfr.lo[1] = 0u;
+            }
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+              float(&d)[4] = *reinterpret_cast<float(*)[4]>(&accr[(j * 2 + m) * 4]);
+              float dl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+              tc_product_pre<TM>(d, dl, afr[m], bfr);
+              if constexpr (SPLIT) {
+                const float ls = tc_lo_scale<TM>();
+#pragma unroll
+                for (int e = 0; e < 4; e++) d[e] = fmaf(ls, dl[e], d[e]);
+              }
             }
           }
         }
