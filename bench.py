@@ -289,16 +289,22 @@ def run_ours(args, ws, rank, local):
         e2e_step(i)
     torch.cuda.synchronize()
     K2 = max(2, min(K, 10))
-    barrier(ws)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s_in)
-    for i in range(K2):
-        e2e_step(i)
-    s_in.wait_stream(s_out)
-    e1.record(s_in)
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(ws, e0.elapsed_time(e1) / K2)
+    # three timed windows of K2 steps; the median is reported with all three (the host link is shared
+    # with the machine's other GPUs, and one window can catch another job's traffic)
+    e2e_runs = []
+    for _ in range(3):
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(s_in)
+        for i in range(K2):
+            e2e_step(i)
+        s_in.wait_stream(s_out)
+        e1.record(s_in)
+        torch.cuda.synchronize()
+        e2e_runs.append(max_over_ranks(ws, e0.elapsed_time(e1) / K2))
+    ms_e2e = float(np.median(e2e_runs))
     h2d = psi.numel() * psi.element_size() + cin.numel() * cin.element_size()
     d2h = psi.numel() * psi.element_size()
 
@@ -375,7 +381,9 @@ def run_ours(args, ws, rank, local):
             "e2e": {"value": round(ws * bytes_step / (ms_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                     "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "mode": "pinned host psi + coefficients in, expanded psi out, every step; pipelined over two "
-                            "device buffer sets (copy-in, compute and copy-out streams)",
+                            "device buffer sets (copy-in, compute and copy-out streams); median of three "
+                            "timed windows",
+                    "ms_per_step_windows": [round(v, 4) for v in e2e_runs],
                     "copy_floor_ms_per_step": round(ms_copy, 4),
                     "copy_floor_note": "the same host<->device copies on the same streams without kernels"},
             "gpu_launches": launches_per_step(api, psi, w, prec) * K,
