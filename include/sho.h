@@ -130,6 +130,8 @@ int sho_sync(sho_handle* handle);
  * psi F32 or BF16, coeff F32).  The tensor-core forms (TF32, 3XTF32, BF16, SPLIT_FP16) need
  * numax <= 7 (SHO_ERR_NUMAX otherwise; for sho_forces numax + 1 <= 7) and a cube that is a multiple
  * of 16 (SHO_ERR_CUBE).  natoms == 0 or nbands == 0 is a no-op returning SHO_OK.
+ * Workspace: SHO_P_FF64 keeps the per-plane y-pass sums of every cube in the handle's workspace,
+ * natoms * cube * (numax+1)(numax+2)/2 * nbands * 8 bytes (SHO_ERR_OOM when it cannot grow).
  */
 int sho_project(sho_handle* handle, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                 int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
