@@ -21,29 +21,21 @@ struct ff {
 // mantissa bits (truncation), lo the next bits of the remainder (rounded once to float).  Magnitudes
 // outside the float normal range (below 2^-126 or at/above 2^128) are flushed to zero; the FP64-accurate
 // form documents that its inputs must lie inside that range.
+//   hi: bits 29..60 of the double hold the low 9 exponent bits and the top 23 mantissa bits; subtracting
+//       384 from that 9-bit field modulo 2^32 rebases the exponent from 1023 to 127 for every exponent in
+//       range (the result's field, e - 896, fits in 8 bits), then the sign is or-ed in.
+//   lo: the low 29 mantissa bits converted to float times 2^(e - 1075), a signed power of two taken from
+//       hi's exponent field minus 52; zero when that would leave the normal range (|v| < 2^-74).
 __device__ __forceinline__ ff ff_from_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned int hw = (unsigned int)(b >> 32);
-  const int e = (int)((hw >> 20) & 0x7ff);  // biased double exponent
+  const unsigned int lw = (unsigned int)b, hw = (unsigned int)(b >> 32);
+  const unsigned int ax = hw & 0x7fffffffu;
+  const bool ok = ax - 0x38100000u < 0x47f00000u - 0x38100000u;  // biased exponent in [897, 1150]
+  const unsigned int hib = ((unsigned int)(b >> 29) - 0xc0000000u) | (hw & 0x80000000u);
+  const unsigned int sb = (hib - 0x1a000000u) & 0xff800000u;       // sign | (e - 948) << 23
   ff r;
-  if (e < 1023 - 126 || e > 1023 + 127) {
-    r.hi = 0.0f;
-    r.lo = 0.0f;
-    return r;
-  }
-  const unsigned int sign = hw & 0x80000000u;
-  const unsigned int mhi = (unsigned int)(b >> 29) & 0x7fffffu;  // mantissa bits 51..29
-  r.hi = __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | mhi);
-  // remainder: mantissa bits 28..0, value m_lo * 2^(e - 1023 - 52)
-  const unsigned int mlo = (unsigned int)b & 0x1fffffffu;
-  const int el = e - 1023 - 52 + 127;  // float exponent of 2^(e-1075)
-  if (mlo == 0u || el < 1) {
-    r.lo = 0.0f;
-  } else {
-    const float scale = __uint_as_float((unsigned int)el << 23);
-    const float m = __uint2float_rn(mlo) * scale;
-    r.lo = sign ? -m : m;
-  }
+  r.hi = ok ? __uint_as_float(hib) : 0.0f;
+  r.lo = (ok && ax >= 0x3b500000u) ? __uint2float_rn(lw & 0x1fffffffu) * __uint_as_float(sb) : 0.0f;
   return r;
 }
 
