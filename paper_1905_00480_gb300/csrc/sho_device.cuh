@@ -29,12 +29,6 @@ struct Basis {
   }
 };
 
-// Pairs per band row of the band-tiled z-pass result [A][C][B/32][32][PP]: P rounded up to 4, plus 4
-// when that is a multiple of 8, so that the 16-byte row loads of 8 consecutive lanes hit distinct banks.
-__host__ __device__ constexpr int tiled_pairs(int P) {
-  return ((P + 3) / 4 * 4) % 8 == 0 ? (P + 3) / 4 * 4 + 4 : (P + 3) / 4 * 4;
-}
-
 // Runtime state index (nx, ny, nz) within the basis of numax nu (same order as Basis<NU>::state).
 __host__ __device__ inline int state_index(int nu, int nx, int ny, int nz) {
   int k = 0;

@@ -75,11 +75,17 @@ struct ExpandLaunch {
 // Bytes per (atom, cube point) of ExpandLaunch::tables_xmajor, NPX = numax + 1 rounded up to 4: the
 // float-pair tables of the FP64-accurate form fit in 16 NPX; the FP32 x table with up to four
 // 16-byte B-fragment entries behind it in 4 NPX + 64.
+// Pairs per band row of the band-tiled z-pass result [A][C][B/32][32][PP]: P rounded up to 4, plus 4
+// when that is a multiple of 8, so that the 16-byte row loads of 8 consecutive lanes hit distinct banks.
+__host__ __device__ constexpr int tiled_pairs(int P) {
+  return ((P + 3) / 4 * 4) % 8 == 0 ? (P + 3) / 4 * 4 + 4 : (P + 3) / 4 * 4;
+}
+
 // Bytes of ExpandLaunch::t2: [A][cube][P][B] of the compute type, or band-tiled FP32
 // [A][cube][ceil(B/32)][32][tiled_pairs(P)], whichever is larger.
 inline size_t t2_bytes(int natoms, int cube, int numax, int nbands, size_t elem) {
   const size_t P = (size_t)((numax + 1) * (numax + 2) / 2);
-  const size_t PP = ((P + 3) / 4 * 4) % 8 == 0 ? (P + 3) / 4 * 4 + 4 : (P + 3) / 4 * 4;
+  const size_t PP = (size_t)tiled_pairs((int)P);
   const size_t plain = (size_t)natoms * cube * P * (size_t)nbands * elem;
   const size_t tiled = (size_t)natoms * cube * (size_t)((nbands + 31) / 32) * 32 * PP * sizeof(float);
   return plain > tiled ? plain : tiled;
