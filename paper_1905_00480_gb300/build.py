@@ -87,8 +87,10 @@ def build(verbose: bool = False, jobs: int = None) -> str:
     lib = os.path.join(LIB_DIR, LIB_NAME)
     key = hashlib.sha1("".join(objs).encode()).hexdigest()[:16]
     stamp = lib + ".stamp"
-    if os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == key:
-        return lib
+    if os.path.exists(lib) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read() == key:
+                return lib
     tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
   using BS = Basis<NU>;
   using SM = BlkSmem<NU, MODE>;
   constexpr bool TC = MODE != kSimt;
-  constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX, XW = SM::XW, PP = SM::PP;
+  constexpr int NP = BS::NP, NPX = SM::NPX, XW = SM::XW, PP = SM::PP;
   constexpr int kAtomsPerBarrier = SM::kAtomsPerBarrier;
   constexpr TcMode TM = TC ? (TcMode)MODE : TcMode::TF32;
   constexpr int K = TcK<TM>::K, NA = TcFrag<TM>::NA;
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
               (yok && x < Nx && b0 + band < B) ? to_real(rowp[(size_t)x * B + band], 0.0f) : 0.0f;
         }
   }
-  if (TC) {
+  if constexpr (TC) {
     for (int i = lane; i < 16 * 36; i += kWarp) t1s[i] = 0.0f;
     // the zero fragment row (index C) of the staging buffers; staging never writes it
     for (int i = tid; i < 3 * kAtomsPerBarrier * 4 * XW; i += kRowsPerBlk * kWarp)

@@ -173,7 +173,6 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows_tc(GridDev g, const AtomD
   static_assert(NU <= 7, "one K tile of states");
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P;
-  constexpr int K = TcK<MODE>::K;
   constexpr int NA = TcFrag<MODE>::NA, NB = TcFrag<MODE>::NB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* t1s = reinterpret_cast<float*>(smem_raw);   // [16][kT1Stride]  (K up to 16, rows >= NP zero)

@@ -68,7 +68,8 @@ def _sample_state(grid, h, X, sigma, m):
 
 # --------------------------------------------------------------------------- 1. basis size
 def test_state_count_matches_paper_table():
-    rows = [l.split() for l in open(os.path.join(GOLDEN, "state_counts.txt")) if l.strip() and l[0] != "#"]
+    with open(os.path.join(GOLDEN, "state_counts.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and l[0] != "#"]
     assert rows, "golden file empty"
     for nu, count in rows:
         assert oracle.nstates(int(nu)) == int(count)

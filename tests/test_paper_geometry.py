@@ -10,10 +10,11 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fcc_geometry.txt")
 
 def _golden():
     vals = {}
-    for line in open(GOLDEN):
-        if line.strip() and not line.startswith("#"):
-            k, v = line.split()
-            vals[k] = int(v)
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = int(v)
     return vals
 
 
