@@ -76,3 +76,38 @@ def test_fused_step_as_accurate_as_textbook_and_contraction_is_not():
         assert e_fused <= 4 * e_text + 2.0 ** -50, (seed, e_text, e_fused)
     # fusing s + p breaks TwoSum's exactness for some inputs: errors of single-float size
     assert worst_contracted > 2.0 ** -36, worst_contracted
+
+
+def _split_model(v):
+    """Bit-level model of the kernel's double -> (hi, lo) float split (integer instructions only)."""
+    b = int(np.array(v, dtype=np.float64).view(np.uint64))
+    lw, hw = b & 0xFFFFFFFF, b >> 32
+    ax = hw & 0x7FFFFFFF
+    ok = ((ax - 0x38100000) & 0xFFFFFFFF) < (0x47F00000 - 0x38100000)       # exponent in [897, 1150]
+    hib = (((b >> 29) & 0xFFFFFFFF) - 0xC0000000) & 0xFFFFFFFF | (hw & 0x80000000)
+    sb = ((hib - 0x1A000000) & 0xFFFFFFFF) & 0xFF800000
+    hi = np.array(hib, dtype=np.uint32).view(np.float32) if ok else f32(0)
+    lo = (f32(lw & 0x1FFFFFFF) * np.array(sb, dtype=np.uint32).view(np.float32)) if (ok and ax >= 0x3B500000) \
+        else f32(0)
+    return f32(hi), f32(lo)
+
+
+def test_branch_free_split_of_a_double():
+    """hi carries the sign, exponent and top 23 mantissa bits of v (truncation), lo the remainder rounded once
+    to float: |v - (hi + lo)| <= 2^-48 |v| wherever lo is a normal float; values outside the float normal
+    range give (0, 0); below 2^-74 lo is dropped (relative error below 2^-23)."""
+    rng = np.random.default_rng(7100)
+    vals = np.concatenate([rng.standard_normal(3000) * 10.0 ** rng.uniform(-37, 37, 3000),
+                           [1.0, -1.0, 2.0 ** -126, -(2.0 ** -126), 2.0 ** 127 * 1.999, 2.0 ** -74, 2.0 ** -73]])
+    for v in vals:
+        hi, lo = _split_model(v)
+        if not 2.0 ** -126 <= abs(v) < 2.0 ** 128:
+            assert (hi, lo) == (0.0, 0.0), v
+            continue
+        assert np.float32(hi) == np.float32(np.float64(hi)), v
+        assert abs(float(hi)) <= abs(v) and (hi == 0 or np.sign(hi) == np.sign(v)), v   # truncation toward zero
+        err = abs(Fr(float(v)) - Fr(float(hi)) - Fr(float(lo)))
+        bound = Fr(2) ** -48 if abs(v) >= 2.0 ** -73 else Fr(2) ** -23
+        assert err <= bound * abs(Fr(float(v))), (v, float(err))
+    for v in [0.0, -0.0, 2.0 ** -127, 1e-300, 2.0 ** 128, -1e300]:
+        assert _split_model(v) == (0.0, 0.0), v
