@@ -58,10 +58,13 @@ typedef enum {
   SHO_ERR_DTYPE = -5,      /* dtype / precision combination not supported */
   SHO_ERR_OOM = -6,        /* device or pinned host allocation failed */
   SHO_ERR_CUDA = -7,       /* a CUDA runtime call or launch failed */
-  SHO_ERR_TIMEOUT = -8,    /* a bounded wait ran out (serving) */
-  SHO_ERR_DEVICE = -9,     /* a device-side check failed (reported by sho_sync) */
+  SHO_ERR_TIMEOUT = -8,    /* a bounded wait ran out: a host wait (serving) or a kernel's wait on its
+                              own data pipeline (reported by sho_sync) */
+  SHO_ERR_DEVICE = -9,     /* a device-side check failed (reported by sho_sync): an SHO_P_FF64 input
+                              outside the float-pair range */
   SHO_ERR_CAPACITY = -10,  /* serving admission: request can never fit the memory budget */
-  SHO_ERR_STATE = -11      /* unknown ticket / system, or call not valid in the current state */
+  SHO_ERR_STATE = -11,     /* unknown ticket / system, or call not valid in the current state */
+  SHO_ERR_CANCELLED = -12  /* serving: the request was cancelled before it started (sho_cancel) */
 } sho_status;
 
 typedef enum { SHO_F64 = 0, SHO_F32 = 1, SHO_BF16 = 2 } sho_dtype;
@@ -75,7 +78,11 @@ typedef enum {
   SHO_P_SPLIT_FP16 = 5,  /* x-pass as three FP16 products of a hi/lo split, FP32 accumulation */
   SHO_P_FF64 = 6         /* FP64-accurate: FP64 psi and coefficients, x-pass as float-float
                             (double-FP32) dot products on the FP32 pipe, y/z passes and accumulation in
-                            FP64; |psi| must lie in the FP32 normal range (smaller values count as 0) */
+                            FP64.  Range: every nonzero psi value (projection, forces) and every z-pass
+                            sum of the coefficients (expansion) must lie in [2^-126, 2^128) in magnitude.
+                            The kernels check this on the device; a call that meets a value outside the
+                            range completes, but its results are not FP64-accurate and sho_sync returns
+                            SHO_ERR_DEVICE.  Such data needs SHO_P_FP64. */
 } sho_prec;
 
 typedef struct {
@@ -115,8 +122,9 @@ const char* sho_last_cuda_error(const sho_handle* handle);
 int sho_set_strict(sho_handle* handle, int strict);
 
 /* Block until the handle's enqueued work is complete; return the first device-side error since the
- * previous sho_sync (SHO_ERR_DEVICE; SHO_ERR_TIMEOUT when a kernel's bounded wait on its own data
- * pipeline expired -- its results are then incomplete) or a CUDA error, else SHO_OK. */
+ * previous sho_sync (SHO_ERR_TIMEOUT when a kernel's bounded wait on its own data pipeline expired --
+ * its results are then incomplete; SHO_ERR_DEVICE when an SHO_P_FF64 input lay outside its range) or a
+ * CUDA error, else SHO_OK.  The device status word is cleared. */
 int sho_sync(sho_handle* handle);
 
 /*
@@ -168,6 +176,20 @@ int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype,
 int sho_add(sho_handle* handle, const sho_grid* grid, const void* coeff, sho_dtype coeff_dtype, int nbands,
             int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
             sho_dtype psi_dtype, void* stream);
+
+/*
+ * Scaled expansion -- psi = (overwrite ? 0 : psi) + alpha * E c, the expansion of sho_add with the
+ * factor alpha applied inside the kernels (to the z-pass table).  With alpha = h^3 this is the adjoint
+ * of the projection in the plain grid inner product, <P psi, c> = <psi, h^3 E c> (Sec. 3.2, steps 1
+ * and 3), i.e. the gradient of a function of the coefficients with respect to psi.  overwrite != 0
+ * first clears the whole psi array on `stream` (points outside every cube end as zero), so the caller
+ * needs no separate fill.  alpha must be finite (SHO_ERR_ARG).  alpha = 1, overwrite = 0 is sho_add
+ * bit for bit.  Other arguments, dtypes and precisions as sho_add; natoms == 0 with overwrite != 0
+ * only clears psi.
+ */
+int sho_add_scaled(sho_handle* handle, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
+                   sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
+                   int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream);
 
 /*
  * Forces -- gradient of a function E(c) of the projection coefficients with respect to the atom
@@ -322,6 +344,15 @@ int sho_system_write_coeff(sho_server* server, int system_id, const void* coeff_
 /* Queue a request; *ticket identifies it for sho_wait. */
 int sho_submit(sho_server* server, int system_id, sho_op op, sho_prec prec, uint64_t* ticket);
 int sho_wait(sho_server* server, uint64_t ticket, int timeout_ms);
+/* sho_wait with the two outcomes kept apart: returns SHO_OK once the request is complete and stores its
+ * status in *request_status (the ticket is then released; a request whose kernel's bounded wait expired
+ * has status SHO_ERR_TIMEOUT, one whose SHO_P_FF64 input was out of range SHO_ERR_DEVICE), or
+ * SHO_ERR_TIMEOUT when it is not complete within timeout_ms (the ticket stays valid). */
+int sho_wait_status(sho_server* server, uint64_t ticket, int timeout_ms, int* request_status);
+/* Cancel a queued request: it is removed from the queue and never starts; a later sho_wait on its
+ * ticket returns SHO_ERR_CANCELLED.  Returns SHO_OK, or SHO_ERR_STATE when the ticket is unknown, has
+ * already started (GPU work is not interrupted) or has finished. */
+int sho_cancel(sho_server* server, uint64_t ticket);
 int sho_server_get_stats(sho_server* server, sho_server_stats* stats);
 /* Clear latency records and counters (not the systems). */
 int sho_server_reset_stats(sho_server* server);

@@ -13,7 +13,7 @@ SHO_ERR_CUDA = -7
 STATUS_NAMES = {
     0: "SHO_OK", -1: "SHO_ERR_ARG", -2: "SHO_ERR_NUMAX", -3: "SHO_ERR_CUBE", -4: "SHO_ERR_SPACING",
     -5: "SHO_ERR_DTYPE", -6: "SHO_ERR_OOM", -7: "SHO_ERR_CUDA", -8: "SHO_ERR_TIMEOUT", -9: "SHO_ERR_DEVICE",
-    -10: "SHO_ERR_CAPACITY", -11: "SHO_ERR_STATE",
+    -10: "SHO_ERR_CAPACITY", -11: "SHO_ERR_STATE", -12: "SHO_ERR_CANCELLED",
 }
 DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
 PRECS = {"fp64": 0, "fp32": 1, "tf32": 2, "3xtf32": 3, "bf16": 4, "split_fp16": 5, "ff64": 6}
@@ -48,7 +48,7 @@ _IP = ctypes.POINTER(ctypes.c_int)
 _I = ctypes.c_int
 _GP = ctypes.POINTER(sho_grid)
 
-# name -> (restype, argtypes); every symbol declared in include/sho.h
+# name -> (restype, argtypes); every symbol declared in include/sho.h and include/sho_fault.h
 SIGNATURES = {
     "sho_version": (_I, []),
     "sho_nstates": (_I, [_I]),
@@ -68,6 +68,7 @@ SIGNATURES = {
     "sho_radial_transform": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I, _VP]),
     "sho_project": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
     "sho_add": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
+    "sho_add_scaled": (_I, [_VP, _GP, ctypes.c_double, _I, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _VP]),
     "sho_forces": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),
     "sho_forces_noalloc": (_I, [_GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _I, _DP, _VP]),
     "sho_apply_nonlocal": (_I, [_VP, _GP, _VP, _I, _I, _I, _DP, _DP, _I, _I, _I, _VP, _VP, _VP]),
@@ -82,8 +83,15 @@ SIGNATURES = {
     "sho_system_write_coeff": (_I, [_VP, _I, _VP]),
     "sho_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "sho_wait": (_I, [_VP, ctypes.c_uint64, _I]),
+    "sho_cancel": (_I, [_VP, ctypes.c_uint64]),
+    "sho_wait_status": (_I, [_VP, ctypes.c_uint64, _I, _IP]),
     "sho_server_get_stats": (_I, [_VP, ctypes.POINTER(sho_server_stats)]),
     "sho_server_reset_stats": (_I, [_VP]),
+    # include/sho_fault.h
+    "sho_fault_wait_limit": (_I, [_VP, ctypes.c_longlong]),
+    "sho_fault_stop_rows": (_I, [_VP, _I]),
+    "sho_fault_hold": (_I, [_VP, _I, _I]),
+    "sho_fault_server_pipeline": (_I, [_VP, ctypes.c_longlong, _I]),
 }
 
 

@@ -235,8 +235,12 @@ def to_radial(coeff: torch.Tensor, numax: int, inverse: bool = False, out: torch
 
 
 def add(psi: torch.Tensor, coeff: torch.Tensor, pos, sigma, numax: int, cube: int, h: float, periodic: bool = True,
-        prec: str = "fp64", handle: Handle = None, stream=None) -> torch.Tensor:
-    """sho_add (in place): psi[j][b] += sum_a sum_k c[a][k][b] Psi_k(u).  Returns psi."""
+        prec: str = "fp64", handle: Handle = None, stream=None, alpha: float = 1.0,
+        overwrite: bool = False) -> torch.Tensor:
+    """sho_add (in place): psi[j][b] += sum_a sum_k c[a][k][b] Psi_k(u).  Returns psi.
+
+    With alpha != 1 or overwrite=True it is sho_add_scaled: psi = (0 if overwrite else psi) + alpha E c,
+    the factor applied inside the kernels and the clearing done by the library."""
     _check_psi(psi)
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
@@ -245,12 +249,16 @@ def add(psi: torch.Tensor, coeff: torch.Tensor, pos, sigma, numax: int, cube: in
         raise ValueError("coeff must be a contiguous CUDA tensor [A][N][B]")
     hd = handle or default_handle(psi.device.index or 0)
     g = _grid(psi, h, periodic)
-    st = N.lib().sho_add(hd.ptr, ctypes.byref(g), ctypes.c_void_p(coeff.data_ptr()),
-                         N.DTYPES[_TORCH_DT[coeff.dtype]], B, A, _dp(pos_h), _dp(sig_h), int(numax), int(cube),
-                         N.PRECS[prec], ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
-                         _stream_ptr(psi, stream))
-    N.check(st, "sho_add" if st != N.SHO_ERR_CUDA else
-            f"sho_add ({N.lib().sho_last_cuda_error(hd.ptr).decode()})")
+    tail = (ctypes.c_void_p(coeff.data_ptr()), N.DTYPES[_TORCH_DT[coeff.dtype]], B, A, _dp(pos_h), _dp(sig_h),
+            int(numax), int(cube), N.PRECS[prec], ctypes.c_void_p(psi.data_ptr()), N.DTYPES[_TORCH_DT[psi.dtype]],
+            _stream_ptr(psi, stream))
+    if alpha == 1.0 and not overwrite:
+        name = "sho_add"
+        st = N.lib().sho_add(hd.ptr, ctypes.byref(g), *tail)
+    else:
+        name = "sho_add_scaled"
+        st = N.lib().sho_add_scaled(hd.ptr, ctypes.byref(g), float(alpha), 1 if overwrite else 0, *tail)
+    N.check(st, name if st != N.SHO_ERR_CUDA else f"{name} ({N.lib().sho_last_cuda_error(hd.ptr).decode()})")
     return psi
 
 

@@ -2,8 +2,10 @@
 
 Forward:  c = P(psi; X)  (sho_project).
 Backward, for an upstream gradient g = dL/dc:
-  dL/dpsi = h^3 E(g)          -- the expansion is the adjoint of the projection in the plain grid inner
-                                 product up to the quadrature weight h^3 (Sec. 3.2 steps 1 and 3)
+  dL/dpsi = h^3 E(g)          -- sho_add_scaled(alpha = h^3, overwrite): the expansion is the adjoint of
+                                 the projection in the plain grid inner product up to the quadrature
+                                 weight h^3 (Sec. 3.2 steps 1 and 3); the library applies the weight in
+                                 its z-pass and clears the output itself
   dL/dX   = sho_forces(psi, g) -- projection at numax+1 and the ladder relation of the Hermite
                                  functions (derivative of the recursion of Sec. 3.7)
 Every step runs in libsho's kernels; this module only wires them into autograd.
@@ -35,9 +37,9 @@ class ShoProject(torch.autograd.Function):
         g = g.contiguous()
         grad_psi = grad_pos = None
         if ctx.needs_input_grad[0]:
-            grad_psi = torch.zeros_like(psi)
-            api.add(grad_psi, g * (h ** 3), ctx.pos_h.numpy(), ctx.sig_h.numpy(), numax, cube, h, periodic,
-                    prec=prec)
+            grad_psi = torch.empty_like(psi)
+            api.add(grad_psi, g, ctx.pos_h.numpy(), ctx.sig_h.numpy(), numax, cube, h, periodic, prec=prec,
+                    alpha=h ** 3, overwrite=True)
         if ctx.needs_input_grad[1]:
             f = api.forces(psi.detach(), g, ctx.pos_h.numpy(), ctx.sig_h.numpy(), numax, cube, h, periodic,
                            prec=prec)

@@ -21,7 +21,9 @@ struct sho_handle {
   int device_error = SHO_OK;   // first device-side error since the last sho_sync
   cudaError_t last_cuda = cudaSuccess;  // CUDA error behind the most recent SHO_ERR_CUDA of this handle
   const char* last_where = "";          // and the step that raised it
-  int* dstatus = nullptr;      // device word set by kernels whose bounded waits expired
+  int* dstatus = nullptr;      // device status word (kStatusTimeout | kStatusRange bits) set by kernels
+  long long wait_cycles = sho::kDefaultWaitCycles;  // fault injection: limit of the bounded device waits
+  int stop_rows = 0x7fffffff;                       // fault injection: rows a plane-sweep producer issues
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
   struct RadialDev {
     void* mem = nullptr;
@@ -193,7 +195,7 @@ std::vector<int> spatial_order(const sho_grid* grid, const std::vector<AtomDev>&
 }
 
 // Number of cube z-slabs per (atom, band tile) so that the CTAs spread evenly over the SMs.
-int choose_zsplit(int natoms, int nbands, int cube, int sms) {
+int zsplit_balanced(int natoms, int nbands, int cube, int sms) {
   const int nbt = (nbands + kWarp - 1) / kWarp;
   int best = 1;
   double best_score = -1.0;
@@ -428,6 +430,8 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
   L.t2p = reinterpret_cast<float*>(ws + o_t2);
   L.coeff = coeff;
   L.status = h->dstatus;
+  L.wait_cycles = h->wait_cycles;
+  L.stop_rows = h->stop_rows;
   L.stream = s;
   if (launch_project_plane(L, prec) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
@@ -483,6 +487,17 @@ int handle_reserve(sho_handle* h, size_t bytes) {
 
 size_t handle_workspace(const sho_handle* h) { return h->ws_bytes; }
 
+int choose_zsplit(int natoms, int nbands, int cube, int sms) { return zsplit_balanced(natoms, nbands, cube, sms); }
+
+int handle_take_status(sho_handle* h) {
+  DeviceGuard guard(h->device);
+  int flag = 0;
+  if (cudaMemcpy(&flag, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SHO_ERR_CUDA;
+  if (flag == 0) return SHO_OK;
+  if (cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) return SHO_ERR_CUDA;
+  return (flag & kStatusTimeout) ? SHO_ERR_TIMEOUT : SHO_ERR_DEVICE;
+}
+
 }  // namespace sho
 
 using namespace sho;
@@ -512,6 +527,7 @@ const char* sho_strerror(int status) {
     case SHO_ERR_DEVICE: return "device-side check failed";
     case SHO_ERR_CAPACITY: return "request exceeds the memory budget";
     case SHO_ERR_STATE: return "invalid state";
+    case SHO_ERR_CANCELLED: return "request cancelled";
     default: return "unknown status";
   }
 }
@@ -584,12 +600,8 @@ int sho_sync(sho_handle* h) {
   if (!h) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
   if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
-  int flag = 0;
-  if (cudaMemcpy(&flag, h->dstatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SHO_ERR_CUDA;
-  if (flag != 0) {
-    if (cudaMemset(h->dstatus, 0, sizeof(int)) != cudaSuccess) return SHO_ERR_CUDA;
-    if (h->device_error == SHO_OK) h->device_error = SHO_ERR_TIMEOUT;
-  }
+  const int dst = handle_take_status(h);
+  if (dst != SHO_OK && h->device_error == SHO_OK) h->device_error = dst;
   int e = h->device_error;
   h->device_error = SHO_OK;
   return e;
@@ -676,7 +688,7 @@ static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, i
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
   const int N = nstates(numax), NP = numax + 1;
-  const int zsplit = op == 0 ? choose_zsplit(natoms, nbands, cube, h->sms) : 1;
+  const int zsplit = op == 0 ? zsplit_balanced(natoms, nbands, cube, h->sms) : 1;
   std::vector<int> ptr, list;
   if (op == 1) plane_lists(grid, at, cube, ptr, list);
   Carve cv;
@@ -779,10 +791,11 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   L.atoms = reinterpret_cast<const AtomDev*>(gm + h->geo[0].off[0]);
   L.natoms = natoms;
   L.numax = numax;
-  L.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : choose_zsplit(natoms, nbands, cube, h->sms);
+  L.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : zsplit_balanced(natoms, nbands, cube, h->sms);
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
   L.t2 = h->ws;
+  L.status = h->dstatus;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
                         : prec == SHO_P_FF64 ? launch_project_ff(L)
@@ -797,19 +810,34 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   return end_call(h, s);
 }
 
-int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype coeff_dtype, int nbands, int natoms,
-            const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
-            sho_dtype psi_dtype, void* stream) {
+static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
+                    sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
+                    int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream) {
   if (!h) return SHO_ERR_ARG;
+  if (!std::isfinite(alpha)) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
   SHO_TRY(check_tc(prec, numax, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
-  if (natoms == 0 || nbands == 0) return SHO_OK;
-  if (!psi || !coeff) return SHO_ERR_ARG;
+  if (nbands == 0) return SHO_OK;
+  if (!psi || (natoms > 0 && !coeff)) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (overwrite) {
+    // psi = alpha E c: clear the whole grid first (points outside every cube end as zero)
+    const size_t es = psi_dtype == SHO_F64 ? 8 : (psi_dtype == SHO_F32 ? 4 : 2);
+    const size_t bytes = (size_t)grid->n[0] * grid->n[1] * grid->n[2] * (size_t)nbands * es;
+    SHO_TRY(begin_call(h, s));
+    const cudaError_t e = cudaMemsetAsync(psi, 0, bytes, s);
+    if (e != cudaSuccess) {
+      h->last_cuda = e;
+      h->last_where = "expansion: clear psi";
+      return SHO_ERR_CUDA;
+    }
+    SHO_TRY(end_call(h, s));
+  }
+  if (natoms == 0) return SHO_OK;
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
   const size_t tc = compute_size(coeff_dtype);
   Carve cv;
@@ -848,6 +876,8 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
   L.tables = ws + o_tab;
   L.t2 = ws + o_t2;
   L.tables_xmajor = ws + o_txm;
+  L.scale = alpha;
+  L.status = h->dstatus;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_expand(L)
                         : prec == SHO_P_FF64 ? launch_expand_ff(L)
@@ -860,6 +890,20 @@ int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype co
     return SHO_ERR_CUDA;
   }
   return end_call(h, s);
+}
+
+int sho_add(sho_handle* h, const sho_grid* grid, const void* coeff, sho_dtype coeff_dtype, int nbands, int natoms,
+            const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
+            sho_dtype psi_dtype, void* stream) {
+  return add_impl(h, grid, 1.0, 0, coeff, coeff_dtype, nbands, natoms, pos, sigma, numax, cube, prec, psi, psi_dtype,
+                  stream);
+}
+
+int sho_add_scaled(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
+                   sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
+                   int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream) {
+  return add_impl(h, grid, alpha, overwrite, coeff, coeff_dtype, nbands, natoms, pos, sigma, numax, cube, prec, psi,
+                  psi_dtype, stream);
 }
 
 int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
@@ -902,10 +946,11 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   P.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
   P.natoms = natoms;
   P.numax = numax + 1;
-  P.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : choose_zsplit(natoms, nbands, cube, h->sms);
+  P.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : zsplit_balanced(natoms, nbands, cube, h->sms);
   P.coeff = ws + o_cp;
   P.coeff_dtype = coeff_dtype;
   P.t2 = prec == SHO_P_FF64 ? ws + o_ft2 : nullptr;
+  P.status = h->dstatus;
   P.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(P)
                         : prec == SHO_P_FF64 ? launch_project_ff(P)
@@ -1022,7 +1067,7 @@ int sho_usu_project(sho_handle* h, const sho_grid* grid, const void* psi, int nb
   L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
   L.natoms = natoms;
   L.nproj = nproj;
-  L.zsplit = choose_zsplit(natoms, nbands, cube, h->sms);
+  L.zsplit = zsplit_balanced(natoms, nbands, cube, h->sms);
   L.dtype = dtype;
   L.proj = const_cast<void*>(proj);
   L.psi_in = psi;
@@ -1070,6 +1115,19 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const void* coeff, int nban
   L.stream = s;
   if (launch_usu(2, L) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
+}
+
+// ------------------------------------------------------------------ fault injection (include/sho_fault.h)
+int sho_fault_wait_limit(sho_handle* h, long long cycles) {
+  if (!h || cycles < 0) return SHO_ERR_ARG;
+  h->wait_cycles = cycles == 0 ? kDefaultWaitCycles : cycles;
+  return SHO_OK;
+}
+
+int sho_fault_stop_rows(sho_handle* h, int rows) {
+  if (!h) return SHO_ERR_ARG;
+  h->stop_rows = rows < 0 ? 0x7fffffff : rows;
+  return SHO_OK;
 }
 
 }  // extern "C"

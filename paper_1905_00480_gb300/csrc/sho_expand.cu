@@ -25,7 +25,7 @@ constexpr int kZChunk = 4;  // planes per shared-memory chunk of the band-tiled 
 template <int NU, typename TCo, typename TC, bool TILED = false>
 __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
                                                         const TCo* __restrict__ coeff, TC* __restrict__ tables,
-                                                        TC* __restrict__ t2, TC* __restrict__ txm) {
+                                                        TC* __restrict__ t2, TC* __restrict__ txm, double scale) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -41,7 +41,11 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
   TC* tx = tables + (size_t)a * 2 * NP * C;  // [NP][C]
   TC* ty = tx + (size_t)NP * C;              // [NP][C]
   for (int i = lane; i < C; i += kWarp) {
-    phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, phz + i, C);
+    // z table times the caller's scale (psi += scale * E c), rounded once to the compute type
+    double zc[NP];
+    phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, zc, 1);
+#pragma unroll
+    for (int n = 0; n < NP; n++) phz[n * C + i] = (TC)(zc[n] * scale);
     if (blockIdx.x == 0) {
       phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, tx + i, C);
       phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, ty + i, C);
@@ -214,7 +218,7 @@ static cudaError_t launch_expand_t(const ExpandLaunch& p) {
     const size_t smem = (size_t)(NU + 1) * C * sizeof(TC);
     k_expand_zpass<NU, TCo, TC><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
         p.g, p.atoms, static_cast<const TCo*>(p.coeff), static_cast<TC*>(p.tables), static_cast<TC*>(p.t2),
-        (TC*)nullptr);
+        (TC*)nullptr, p.scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -247,7 +251,7 @@ static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float);
   k_expand_zpass<NU, float, float><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
-      static_cast<float*>(p.tables_xmajor));
+      static_cast<float*>(p.tables_xmajor), p.scale);
   return cudaGetLastError();
 }
 
@@ -258,7 +262,7 @@ static cudaError_t zpass_f32_tiled_nu(const ExpandLaunch& p) {
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float) + (size_t)kZChunk * kWarp * PP * sizeof(float);
   k_expand_zpass<NU, float, float, true><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
-      static_cast<float*>(p.tables_xmajor));
+      static_cast<float*>(p.tables_xmajor), p.scale);
   return cudaGetLastError();
 }
 
@@ -268,7 +272,7 @@ static cudaError_t zpass_f64_nu(const ExpandLaunch& p) {
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double);
   k_expand_zpass<NU, double, double><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const double*>(p.coeff), static_cast<double*>(p.tables), static_cast<double*>(p.t2),
-      (double*)nullptr);
+      (double*)nullptr, p.scale);
   return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ struct FfProjectSmem {
 template <int NU>
 __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* __restrict__ psi,
                                                       const AtomDev* __restrict__ atoms, int zsplit,
-                                                      double* __restrict__ t2g) {
+                                                      double* __restrict__ t2g, int* __restrict__ status) {
   using BS = Basis<NU>;
   using SM = FfProjectSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
   float t2s[P], t2c[P];  // y-pass accumulators of the current plane, float pairs
 #pragma unroll
   for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
+  bool range_bad = false;  // a psi value the float pairs cannot carry (reported through the status word)
 
   for (int r = 0, iz = iz0, iy = 0; r < R; r++) {
     ff_wait<kFfStages - 2>();
@@ -158,7 +159,9 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       for (int n = 0; n < NP; n++) S[n] = E[n] = 0.0f;
 #pragma unroll 4
       for (int ix = 0; ix < C; ix++) {
-        const ff pv = ff_from_double(st[ix * 32 + lane]);
+        const double pd = st[ix * 32 + lane];
+        range_bad |= ff_out_of_range(pd);
+        const ff pv = ff_from_double(pd);
         const float4* f4 = reinterpret_cast<const float4*>(phx + (size_t)ix * NPX);
 #pragma unroll
         for (int q = 0; q < NPX / 2; q++) {
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     }
   }
   ff_wait<0>();
+  if (__any_sync(0xffffffffu, range_bad) && lane == 0 && status) atomicOr(status, kStatusRange);
 }
 
 // z-pass (a5) of the FP64-accurate projection in FP64, one warp per (atom, 32-band tile):
@@ -284,7 +288,8 @@ __global__ void __launch_bounds__(kWarp) k_project_ff_zpass(GridDev g, const Ato
 // converted in place: a double and a float pair are both 8 bytes).
 template <int NU>
 __global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tables, float2* __restrict__ txff,
-                            float2* __restrict__ tyff, double* __restrict__ t2, long long t2_count) {
+                            float2* __restrict__ tyff, double* __restrict__ t2, long long t2_count,
+                            int* __restrict__ status) {
   constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
   const long long nx_total = (long long)natoms * cube * NPX;
   const long long ny_total = (long long)natoms * NP * cube;
@@ -304,10 +309,14 @@ __global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tab
     tyff[i] = make_float2(f.hi, f.lo);
   }
   float2* t2f = reinterpret_cast<float2*>(t2);
+  bool range_bad = false;  // a z-pass sum the float pairs cannot carry (coefficients out of range)
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < t2_count; i += stride) {
-    const ff f = ff_from_double_exact(t2[i]);
+    const double v = t2[i];
+    range_bad |= ff_out_of_range(v);
+    const ff f = ff_from_double_exact(v);
     t2f[i] = make_float2(f.hi, f.lo);
   }
+  if (range_bad && status) atomicOr(status, kStatusRange);
 }
 
 // ------------------------------------------------------------------------------- expansion, block gather
@@ -537,7 +546,7 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   if (e != cudaSuccess) return e;
   const unsigned nbt = (unsigned)((p.g.nbands + kWarp - 1) / kWarp);
   kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
-      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2));
+      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
@@ -560,7 +569,8 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   float2* txff = static_cast<float2*>(p.tables_xmajor);
   float2* tyff = txff + (size_t)p.natoms * p.g.cube * NPX;
   k_ff_tables<NU><<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, p.stream>>>(
-      p.natoms, p.g.cube, static_cast<const double*>(p.tables), txff, tyff, static_cast<double*>(p.t2), t2_count);
+      p.natoms, p.g.cube, static_cast<const double*>(p.tables), txff, tyff, static_cast<double*>(p.t2), t2_count,
+      p.status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   auto kern = k_expand_blk_ff<NU>;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/sho.h"
+#include "../../include/sho_fault.h"
 
 namespace sho {
 
@@ -36,6 +37,15 @@ struct GridDev {
 
 enum class Real { F64, F32 };
 
+// Bits of a handle's device status word (read and cleared by sho_sync): a bounded wait on the kernel's
+// own data pipeline expired; an FP64-accurate (float-float) input lay outside the float normal range.
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusRange = 2;
+
+// Bounded waits of the device pipelines give up after this many SM clock cycles (~2 s at 2.07 GHz)
+// unless a handle's fault-injection setting (include/sho_fault.h) shortens it.
+constexpr long long kDefaultWaitCycles = 4000000000ll;
+
 struct ProjectLaunch {
   GridDev g;
   const void* psi;          // [Nz][Ny][Nx][B]
@@ -48,6 +58,7 @@ struct ProjectLaunch {
   void* coeff;              // [A][N][B], FP64 or FP32
   void* t2 = nullptr;       // FP64-accurate form: workspace [A][cube][P][B] FP64 of per-plane y-pass sums
   sho_dtype coeff_dtype;
+  int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   cudaStream_t stream;
 };
 
@@ -69,6 +80,8 @@ struct ExpandLaunch {
   void* tables_xmajor = nullptr;  // optional workspace, txm_bytes_per_point(numax) bytes per (atom, cube
                                   // point): the FP32 x table x-major [A][cube][NPX], then (tensor forms)
                                   // the B fragments of the x-pass; FP64-accurate form: float-pair tables
+  double scale = 1.0;       // psi += scale * E c: applied to the z table of the z-pass
+  int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   cudaStream_t stream;
 };
 
@@ -169,7 +182,9 @@ struct PlaneLaunch {
   uint32_t* bfrag;           // [A][32][kMaxCube / 8][4]
   float* t2p;                // [A][C][P][B]
   float* coeff;              // [A][N][B]
-  int* status;               // device word, bit 0 = a bounded wait expired
+  int* status;               // device status word: kStatusTimeout when a bounded wait expired
+  long long wait_cycles = kDefaultWaitCycles;  // limit of every mbarrier wait
+  int stop_rows = 0x7fffffff;  // fault injection: producers issue only this many rows per sweep
   cudaStream_t stream;
 };
 bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nbands, int numax, int cube,
@@ -226,7 +241,11 @@ bool fp32_stream_ok(const void* psi, sho_dtype dt, int nbands);
 cudaError_t launch_project_fp32(const ProjectLaunch& p, sho_prec prec);
 cudaError_t launch_expand_fp32(const ExpandLaunch& p, sho_prec prec);
 
-// Host helpers shared with the serving loop (sho_api.cu).
+// Host helpers shared with the serving loop and the allocation-free entry point (sho_api.cu).
+int choose_zsplit(int natoms, int nbands, int cube, int sms);
+// Read and clear the handle's device status word (the handle's work must have completed): SHO_OK,
+// SHO_ERR_TIMEOUT (a bounded wait expired) or SHO_ERR_DEVICE (an input outside the form's range).
+int handle_take_status(sho_handle* h);
 size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, int cube, int nbands,
                        sho_dtype coeff_dtype);
 int handle_reserve(sho_handle* h, size_t bytes);

@@ -3,9 +3,12 @@
 // Some callers cannot let a library call cudaMalloc: an application whose own pool allocator owns
 // all device memory and must account for every byte, a plug-in hosted inside a program that forbids
 // foreign allocations, or a process running close to the memory limit that must not fail half-way
-// through a step.  For them this entry point computes exactly what sho_forces computes, but its
-// scratch (the per-atom plan and the numax+1 projection) lives in one fixed, file-scope device array
-// that is part of the library image.  The caller still owns and passes psi, dEdc and dEdX.
+// through a step.  For them this entry point computes what sho_forces computes, but its scratch (the
+// per-atom plan and the numax+1 projection) lives in one fixed, file-scope device array that is part
+// of the library image.  The caller still owns and passes psi, dEdc and dEdX.  The projection runs on
+// the generic per-atom kernels with the same slab split as sho_forces: for SHO_P_FP64 that is the same
+// kernel and summation order as sho_forces; for SHO_P_FP32, where sho_forces may take the streaming
+// kernels, the two agree within the FP32 form's tolerance, not bit for bit.
 //
 // The array is loaded with the library: every GPU that loads libsho.so holds
 // SHO_NOALLOC_SCRATCH_BYTES of it until the process exits.  All calls on a device share it and it
@@ -79,24 +82,6 @@ int validate(const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nba
   return SHO_OK;
 }
 
-// Same slab count as the allocating entry point, so both give the same summation order.
-int zsplit_for(int natoms, int nbands, int cube, int sms) {
-  const int nbt = (nbands + kWarp - 1) / kWarp;
-  int best = 1;
-  double best_score = -1.0;
-  for (int zs = 1; zs <= 8; zs *= 2) {
-    if (zs > 1 && cube / zs < 4) break;
-    const double ctas = (double)natoms * nbt * zs;
-    const double per_sm = std::ceil(ctas / sms);
-    const double score = (ctas / (per_sm * sms)) * std::min(1.0, ctas / (4.0 * sms));
-    if (score > best_score + 1e-9) {
-      best_score = score;
-      best = zs;
-    }
-  }
-  return best;
-}
-
 }  // namespace
 }  // namespace sho
 
@@ -149,7 +134,7 @@ extern "C" int sho_forces_noalloc(const sho_grid* grid, const void* psi, sho_dty
   P.atoms = reinterpret_cast<const AtomDev*>(ws);
   P.natoms = natoms;
   P.numax = numax + 1;
-  P.zsplit = zsplit_for(natoms, nbands, cube, sms);
+  P.zsplit = choose_zsplit(natoms, nbands, cube, sms);
   P.coeff = ws + atoms_bytes;
   P.coeff_dtype = coeff_dtype;
   P.stream = s;

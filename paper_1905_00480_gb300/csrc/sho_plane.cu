@@ -17,9 +17,9 @@
 // host assigns every (atom, plane) row segment to a (warp, slot) so that the segments of one slot do
 // not overlap in y (interval colouring, plan_planes), so each row needs no dynamic indexing.  A 12th
 // warp issues the TMA row loads into a ring of `stages` rows guarded by mbarriers (full: TMA bytes
-// landed; empty: all consumer warps done with the row).  Every wait is bounded: after ~2 s the waiting
-// warp records SHO_ERR_TIMEOUT in the status word and leaves its loop; the producer then waits, again
-// bounded, for the copies it issued before it returns.
+// landed; empty: all consumer warps done with the row).  Every wait is bounded (a launch parameter,
+// ~2 s by default): when it runs out the waiting warp records kStatusTimeout in the status word and
+// leaves its loop; the producer then waits, again bounded, for the copies it issued before it returns.
 //
 // x-pass on the tensor cores: T1[b][n] = sum_x psi[x][b] phi_n(x) is an m16n8 (bands x states) product
 // with K = x.  Row m of the two m-tiles maps to band 4g + 2j (+1 for m = g + 8), and for the TF32
@@ -42,7 +42,6 @@ constexpr int kPlaneThreads = (kPlaneWarps + 1) * 32;  // + the producer warp
 constexpr int kPlaneMaxStages = 8;
 constexpr int kT1Stride = 36;                          // padded row of the T1 transpose buffer
 constexpr int kPlaneRowBytes = 32 * 4;                 // one x point: 32 FP32 bands (one swizzle row)
-constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at the GB300 SM clock
 constexpr int kSimtMode = -1;
 
 // --------------------------------------------------------------------------------- mbarrier / TMA
@@ -66,12 +65,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0u;
 }
-// Wait for the phase of `parity` to complete; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete; false after `limit` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void tma_load_row(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
@@ -193,7 +192,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
     k_project_plane(const __grid_constant__ CUtensorMap map, GridDev g, const int4* __restrict__ items,
                     const int* __restrict__ slot_ptr, const PlaneSeg* __restrict__ segs,
                     const uint32_t* __restrict__ bfrag, const float* __restrict__ xtab,
-                    const float* __restrict__ ytab, int stages, int nbt, float* t2p, int* status) {
+                    const float* __restrict__ ytab, int stages, int nbt, float* t2p, int* status,
+                    long long wait_cycles, int stop_rows) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P;
   constexpr int S = kPlaneSlots;
@@ -235,12 +235,15 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
-      for (int r = 0, st = 0, k = 0; r < R; r++) {  // st = r % stages, k = r / stages
+      // stop_rows < R only under fault injection: the rows after it are never issued, so the consumers'
+      // bounded waits for them expire
+      const int Rp = min(R, stop_rows);
+      for (int r = 0, st = 0, k = 0; r < Rp; r++) {  // st = r % stages, k = r / stages
         if (r > 0 && ++st == stages) {
           st = 0;
           k++;
         }
-        if (!mbar_wait(bar_empty + 8 * st, (uint32_t)((k & 1) ^ 1))) {
+        if (!mbar_wait(bar_empty + 8 * st, (uint32_t)((k & 1) ^ 1), wait_cycles)) {
           ok = false;
           break;
         }
@@ -248,11 +251,12 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
         tma_load_row(ring + (uint32_t)st * stagebytes, &map, b0, (z * Ny + ylo + r) * Nx, bar_full + 8 * st);
         issued = r + 1;
       }
-      if (!ok) {
-        atomicOr(status, 1);
-        // let the copies already issued land before the CTA's shared memory is released
+      if (!ok || Rp < R) {
+        if (!ok) atomicOr(status, kStatusTimeout);
+        // let the copies already issued land before the CTA's shared memory is released (they complete
+        // whatever the consumers do, so this wait keeps the default limit)
         for (int r = max(0, issued - stages); r < issued; r++)
-          (void)mbar_wait(bar_full + 8 * (r % stages), (uint32_t)((r / stages) & 1));
+          (void)mbar_wait(bar_full + 8 * (r % stages), (uint32_t)((r / stages) & 1), kDefaultWaitCycles);
       }
     }
     return;
@@ -292,8 +296,10 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
       k++;
     }
     const int y = ylo + r;
-    if (!mbar_wait(bar_full + 8 * st, (uint32_t)(k & 1))) {
-      if (lane == 0) atomicOr(status, 1);
+    // the warp leaves together: a lane whose wait ran out takes the others with it, so no lane is left
+    // behind at a warp barrier of the row
+    if (!__all_sync(0xffffffffu, mbar_wait(bar_full + 8 * st, (uint32_t)(k & 1), wait_cycles))) {
+      if (lane == 0) atomicOr(status, kStatusTimeout);
       break;
     }
     const uint32_t row = ring + (uint32_t)st * stagebytes;
@@ -564,7 +570,8 @@ cudaError_t plane_run(const PlaneLaunch& p) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)p.nitems * nbt, kPlaneThreads, smem, p.stream>>>(map, p.g, p.items, p.slot_ptr, p.segs, p.bfrag,
-                                                                      p.xtab, p.ytab, stages, nbt, p.t2p, p.status);
+                                                                      p.xtab, p.ytab, stages, nbt, p.t2p, p.status,
+                                                                      p.wait_cycles, p.stop_rows);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

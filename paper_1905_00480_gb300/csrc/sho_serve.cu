@@ -8,11 +8,16 @@
 // resident systems + all slot workspaces within the memory budget.  Requests that arrive while others
 // run are admitted as soon as a slot and memory free up; requests of different systems overlap on the
 // device.  Nothing here waits on the device without a bound: completion is polled with
-// cudaEventQuery, and host waits (sho_wait) take a timeout.
+// cudaEventQuery, and host waits (sho_wait) take a timeout.  A finished request's status includes the
+// device status word of its slot's handle (a kernel's expired bounded wait, an out-of-range input).
+// Each request is an NVTX range ("sho project/expand sys=<id>") from its start to its retirement.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -38,7 +43,8 @@ struct SysRec {
   void* coeff = nullptr;
   size_t psi_bytes = 0, coeff_bytes = 0;
   bool busy = false;
-  int pending = 0;  // queued + running requests
+  bool held = false;  // fault injection: a running request of this system is not retired
+  int pending = 0;    // queued + running requests
   double bytes_prj = 0.0, bytes_add = 0.0;
 };
 
@@ -58,6 +64,7 @@ struct Slot {
   cudaEvent_t done = nullptr;
   bool busy = false;
   uint64_t ticket = 0;
+  nvtxRangeId_t range = 0;
 };
 
 // Distinct grid points covered by the cubes (algorithmic psi traffic of one request).
@@ -152,6 +159,8 @@ void finish(sho_server* s, Slot& sl, int status) {
   sys.busy = false;
   sys.pending--;
   sl.busy = false;
+  if (sl.range) nvtxRangeEnd(sl.range);
+  sl.range = 0;
   s->inflight--;
   s->completed++;
   if (status != SHO_OK) s->failed++;
@@ -170,6 +179,9 @@ void start(sho_server* s, int k, uint64_t ticket) {
   s->inflight++;
   s->max_inflight = std::max(s->max_inflight, s->inflight);
   if (s->t_first < 0.0) s->t_first = now_s();
+  char name[64];
+  std::snprintf(name, sizeof(name), "sho %s sys=%d", r.op == SHO_OP_PROJECT ? "project" : "expand", r.sys);
+  sl.range = nvtxRangeStartA(name);
   int st = sho::handle_reserve(sl.h, r.need);
   note_peak(s);
   if (st == SHO_OK) {
@@ -191,10 +203,13 @@ void scheduler(sho_server* s) {
     bool progress = false;
     for (Slot& sl : s->slots) {
       if (!sl.busy) continue;
+      if (s->systems[s->reqs[sl.ticket].sys].held) continue;  // fault injection: a stuck request
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
-      finish(s, sl, q == cudaSuccess ? SHO_OK : SHO_ERR_CUDA);
+      // the request's kernels are done: fold in what they reported through the handle's status word
+      int st = q == cudaSuccess ? sho::handle_take_status(sl.h) : SHO_ERR_CUDA;
       if (q != cudaSuccess) cudaGetLastError();
+      finish(s, sl, st);
       progress = true;
     }
     if (!s->stop) {
@@ -271,6 +286,7 @@ int sho_server_destroy(sho_server* s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    for (auto& kv : s->systems) kv.second.held = false;  // held requests retire once their work is done
     for (uint64_t t : s->queue) {
       Req& r = s->reqs[t];
       r.status = SHO_ERR_STATE;
@@ -418,8 +434,8 @@ int sho_submit(sho_server* s, int id, sho_op op, sho_prec prec, uint64_t* ticket
   return SHO_OK;
 }
 
-int sho_wait(sho_server* s, uint64_t ticket, int timeout_ms) {
-  if (!s) return SHO_ERR_ARG;
+int sho_wait_status(sho_server* s, uint64_t ticket, int timeout_ms, int* request_status) {
+  if (!s || !request_status) return SHO_ERR_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return SHO_ERR_STATE;
@@ -428,9 +444,55 @@ int sho_wait(sho_server* s, uint64_t ticket, int timeout_ms) {
     if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !s->reqs[ticket].done)
       return SHO_ERR_TIMEOUT;
   }
-  const int st = s->reqs[ticket].status;
+  *request_status = s->reqs[ticket].status;
   s->reqs.erase(ticket);
-  return st;
+  return SHO_OK;
+}
+
+int sho_wait(sho_server* s, uint64_t ticket, int timeout_ms) {
+  int st = SHO_OK;
+  const int w = sho_wait_status(s, ticket, timeout_ms, &st);
+  return w != SHO_OK ? w : st;
+}
+
+int sho_cancel(sho_server* s, uint64_t ticket) {
+  if (!s) return SHO_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end() || it->second.done) return SHO_ERR_STATE;
+  auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+  if (q == s->queue.end()) return SHO_ERR_STATE;  // already started: its GPU work is not interrupted
+  s->queue.erase(q);
+  Req& r = it->second;
+  r.status = SHO_ERR_CANCELLED;
+  r.done = true;
+  r.t_done = now_s();
+  s->systems[r.sys].pending--;
+  s->cv_done.notify_all();
+  return SHO_OK;
+}
+
+int sho_fault_server_pipeline(sho_server* s, long long cycles, int rows) {
+  if (!s || cycles < 0) return SHO_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (Slot& sl : s->slots) {
+    const int st = sho_fault_wait_limit(sl.h, cycles);
+    if (st != SHO_OK) return st;
+    sho_fault_stop_rows(sl.h, rows);
+  }
+  return SHO_OK;
+}
+
+int sho_fault_hold(sho_server* s, int id, int hold) {
+  if (!s) return SHO_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->systems.find(id);
+    if (it == s->systems.end()) return SHO_ERR_STATE;
+    it->second.held = hold != 0;
+  }
+  s->cv_work.notify_all();
+  return SHO_OK;
 }
 
 int sho_server_get_stats(sho_server* s, sho_server_stats* out) {

@@ -85,11 +85,27 @@ class Server:
         return t.value
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
-        """Returns the request's status (0 = ok); raises on timeout."""
-        st = N.lib().sho_wait(self._s, ctypes.c_uint64(ticket), int(timeout_ms))
+        """sho_wait_status: returns the request's status (0 = ok); raises TimeoutError when the request
+        is not complete within timeout_ms (the ticket stays valid)."""
+        rs = ctypes.c_int()
+        st = N.lib().sho_wait_status(self._s, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(rs))
         if st == -8:
             raise TimeoutError(f"ticket {ticket} not complete after {timeout_ms} ms")
-        return st
+        N.check(st, "sho_wait_status")
+        return rs.value
+
+    def cancel(self, ticket: int) -> int:
+        """sho_cancel: 0 when the queued request was removed, SHO_ERR_STATE (-11) when it already started
+        or finished."""
+        return int(N.lib().sho_cancel(self._s, ctypes.c_uint64(ticket)))
+
+    def fault_hold(self, sid: int, hold: bool = True):
+        """sho_fault_hold (fault injection): while held, a running request of the system is not retired."""
+        N.check(N.lib().sho_fault_hold(self._s, int(sid), 1 if hold else 0), "sho_fault_hold")
+
+    def fault_pipeline(self, cycles: int = 0, rows: int = -1):
+        """sho_fault_server_pipeline (fault injection): wait limit and producer row stop of every slot."""
+        N.check(N.lib().sho_fault_server_pipeline(self._s, int(cycles), int(rows)), "sho_fault_server_pipeline")
 
     def stats(self) -> dict:
         s = N.sho_server_stats()

@@ -51,7 +51,7 @@ def test_host_only_entry_points(lib):
     assert lib.sho_nstates(-1) == 0
     import math
     assert abs(lib.sho_max_spacing(0.8, 5) - math.pi * 0.8 / math.sqrt(11)) < 1e-15
-    for st in range(-11, 1):
+    for st in range(-12, 1):
         assert lib.sho_strerror(st)
 
 

@@ -98,3 +98,35 @@ def test_fp64_autograd_forces_vs_oracle():
     dEdc = 2.0 * Dm[:, :, None] * c.detach().cpu().numpy()
     ref = oracle.forces(grid, h, True, psi_h, pos, sig, numax, cube, dEdc)
     assert rel_max(X.grad.numpy(), ref) <= 1e-12
+
+
+def test_backward_runs_only_library_kernels():
+    """The backward of the projection (dL/dpsi = h^3 E(g) through sho_add_scaled, which also clears the
+    output; dL/dX through sho_forces) launches only libsho's kernels: no elementwise torch kernel scales
+    the gradient or fills the output."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300.autograd import sho_project
+    rng = np.random.default_rng(12)
+    grid, h, numax, cube = (32, 32, 32), 0.2, 4, 16
+    pos, sig = workloads.random_atoms(rng, 3, tuple(n * h for n in grid), True, min_sep=1.0)
+    psi = torch.from_numpy(rng.standard_normal((32, 32, 32, 8))).cuda().requires_grad_(True)
+    X = torch.tensor(pos, requires_grad=True)
+    c = sho_project(psi, X, torch.from_numpy(sig), numax, cube, h, True, prec="fp64")
+    g = torch.from_numpy(rng.standard_normal(tuple(c.shape))).cuda()
+    torch.cuda.synchronize()
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            gpsi, gX = torch.autograd.grad(c, (psi, X), grad_outputs=g)
+            torch.cuda.synchronize()
+    except Exception as e:  # profiler backend unavailable on this machine
+        pytest.skip(f"CUDA profiler unavailable: {e}")
+    kernels = [ev.name for ev in prof.events() if ev.device_type == torch.autograd.DeviceType.CUDA]
+    kernels = [k for k in kernels if "emcpy" not in k and "emset" not in k]
+    if not kernels:
+        pytest.skip("the profiler recorded no CUDA kernels")
+    foreign = [k for k in kernels if "k_" not in k]
+    assert not foreign, f"non-library kernels in the backward: {foreign}"
+    ref = h ** 3 * oracle.add(grid, h, True, np.zeros((32, 32, 32, 8)), pos, sig, numax, cube, g.cpu().numpy())
+    assert np.linalg.norm(gpsi.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-12

@@ -1,11 +1,14 @@
-"""sho_forces_noalloc, the allocation-free forces entry point, agrees with sho_forces (GPU).
+"""sho_forces_noalloc, the allocation-free forces entry point, agrees with sho_forces and with the
+oracle (GPU).
 
 Callers that cannot allocate device memory (their own pool owns it, their host forbids foreign
 allocations, or they run at the memory limit) use sho_forces_noalloc, whose scratch is a fixed static
 device array inside the library.  This test calls it through the C ABI twice in a row -- the second
 call reuses the array left by the first -- and checks both results against the allocating entry point
-within the tolerances of the other parity tests.  It also checks that a problem larger than the fixed
-scratch is rejected before anything runs.  The file is named so that pytest collects it last.
+and against the FP64 oracle within the tolerances of the other parity tests, and that the two calls
+changed neither the device's free memory nor the torch allocator's allocation count.  It also checks
+that a problem larger than the fixed scratch is rejected before anything runs.  The file is named so
+that pytest collects it last.
 """
 import ctypes
 
@@ -54,25 +57,41 @@ def _case(seed, natoms, numax, nbands, grid=(40, 36, 44), h=0.2):
     return pos, sig, psi, dEdc
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_noalloc_matches_allocating_entry_point_twice(lib, prec):
+@pytest.mark.parametrize("prec,storage", [("fp64", "f64"), ("fp32", "f32"), ("fp32", "bf16")])
+def test_noalloc_matches_allocating_entry_point_and_oracle_twice(lib, prec, storage):
     import torch
     from paper_1905_00480_gb300 import api
-    numax, cube, h = 4, 16, 0.2
-    pos, sig, psi, dEdc = _case(123, 6, numax, 45)
-    tdt = torch.float64 if prec == "fp64" else torch.float32
+    numax, cube, h, grid = 4, 16, 0.2, (40, 36, 44)
+    pos, sig, psi, dEdc = _case(123, 6, numax, 45, grid=grid, h=h)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[storage]
+    cdt = torch.float64 if prec == "fp64" else torch.float32
     psi_d = torch.from_numpy(psi).cuda().to(tdt)
-    dEdc_d = torch.from_numpy(dEdc).cuda().to(tdt)
+    dEdc_d = torch.from_numpy(dEdc).cuda().to(cdt)
     ref = api.forces(psi_d, dEdc_d, pos, sig, numax, cube, h, True, prec=prec).cpu().numpy()
-    tol = TOL_FP64 if prec == "fp64" else TOL_FP32
-    for _ in range(2):
-        out = torch.full((len(pos), 3), float("nan"), dtype=torch.float64, device="cuda")
-        st = _noalloc(lib, psi_d, dEdc_d, pos, sig, numax, cube, h, True, prec, out)
+    # the oracle on the storage-rounded inputs the kernels see (ladder-relation forces difference
+    # neighbouring coefficients: the FP32 bar is 10x the coefficient bar, as in the FP32 parity tests)
+    ora = oracle.forces(grid, h, True, psi_d.double().cpu().numpy(), pos, sig, numax, cube,
+                        dEdc_d.double().cpu().numpy())
+    tol = TOL_FP64 if prec == "fp64" else 10 * TOL_FP32
+    # the first call on the device looks up the scratch array (and may load the library's kernels)
+    out = torch.empty((len(pos), 3), dtype=torch.float64, device="cuda")
+    assert _noalloc(lib, psi_d, dEdc_d, pos, sig, numax, cube, h, True, prec, out) == 0
+    outs = [torch.full((len(pos), 3), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    allocs1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for o in outs:  # two calls in a row: the second reuses the array the first left behind
+        st = _noalloc(lib, psi_d, dEdc_d, pos, sig, numax, cube, h, True, prec, o)
         assert st == 0, f"sho_forces_noalloc returned {st}"
-        torch.cuda.synchronize()
-        got = out.cpu().numpy()
+    torch.cuda.synchronize()
+    # the calls allocated no device memory, neither through the driver nor through torch's allocator
+    assert torch.cuda.mem_get_info()[0] == free1
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == allocs1
+    for o in outs:
+        got = o.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert rel_max(got, ref) <= tol
+        assert rel_max(got, ora) <= tol
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(lib):
