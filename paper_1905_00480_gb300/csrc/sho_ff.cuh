@@ -39,13 +39,13 @@ __device__ __forceinline__ ff ff_from_double(double v) {
   return r;
 }
 
-// True for a value the split above cannot carry: nonzero and outside [2^-126, 2^128) in magnitude
-// (subnormal doubles, values too small or too large for a float exponent, inf and NaN).  Integer
-// instructions on the same words as ff_from_double.
+// True for a value the split above cannot carry: outside [2^-126, 2^128) in magnitude (values too small
+// or too large for a float exponent, inf and NaN) and not zero.  Integer instructions on the high word
+// that ff_from_double also tests; a double whose high word is zero apart from the sign (|v| < 2^-1042)
+// counts as zero.
 __device__ __forceinline__ bool ff_out_of_range(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned int lw = (unsigned int)b, ax = (unsigned int)(b >> 32) & 0x7fffffffu;
-  return (ax - 0x38100000u >= 0x47f00000u - 0x38100000u) && ((ax | lw) != 0u);
+  const unsigned int ax = (unsigned int)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu;
+  return (ax - 0x38100000u >= 0x47f00000u - 0x38100000u) && ax != 0u;
 }
 
 // Split a double into hi + lo with FP64 arithmetic (for values computed once per table entry).

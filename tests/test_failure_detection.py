@@ -82,7 +82,7 @@ def test_ff64_range_guard_projection(scale):
     got = api.project(torch.from_numpy(bad).cuda(), pos, sig, numax, 16, 0.2, True, prec="fp64", handle=hd)
     assert N.lib().sho_sync(hd.ptr) == 0
     ref = oracle.project(grid, 0.2, True, bad, pos, sig, numax, 16)
-    assert_coeff_close(got.cpu().numpy(), ref, TOL_FP64)
+    assert_coeff_close(got.cpu().numpy() / scale, ref / scale, TOL_FP64)   # rescaled: norms stay finite
     # exact zeros are inside the range: a band of zeros is not flagged and the result is FP64-accurate
     zeros = psi.copy()
     zeros[:, :, :, 0] = 0.0
@@ -123,7 +123,7 @@ def test_ff64_range_guard_expansion():
     api.add(out, torch.from_numpy(c * 1e300).cuda(), pos, sig, numax, 16, 0.2, True, prec="fp64", handle=hd)
     assert N.lib().sho_sync(hd.ptr) == 0
     ref = oracle.add(grid, 0.2, True, np.zeros_like(psi), pos, sig, numax, 16, c * 1e300)
-    assert rel_norm(out.cpu().numpy(), ref) <= TOL_FP64
+    assert rel_norm(out.cpu().numpy() / 1e300, ref / 1e300) <= TOL_FP64   # rescaled: norms stay finite
     out.zero_()
     api.add(out, torch.from_numpy(c).cuda(), pos, sig, numax, 16, 0.2, True, prec="ff64", handle=hd)
     assert N.lib().sho_sync(hd.ptr) == 0
