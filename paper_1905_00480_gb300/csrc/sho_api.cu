@@ -360,8 +360,8 @@ int geo_cache(sho_handle* h, int slot, uint64_t key, const std::vector<std::pair
   return SHO_OK;
 }
 
-int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const float* psi,
-                   int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
+int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const void* psi,
+                   sho_dtype psi_dtype, int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
   const size_t A = at.size();
   const uint64_t key = geometry_key(grid, at, cube);
   SHO_TRY(begin_call(h, s));
@@ -417,6 +417,7 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
   PlaneLaunch L;
   L.g = make_grid(grid, cube, nbands);
   L.psi = psi;
+  L.psi_dtype = psi_dtype;
   L.atoms = reinterpret_cast<const AtomDev*>(pm + h->plane_off[0]);
   L.natoms = (int)A;
   L.numax = numax;
@@ -772,8 +773,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
   if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec))
-    return project_planes(h, grid, at, static_cast<const float*>(psi), nbands, numax, cube, prec,
-                          static_cast<float*>(coeff), s);
+    return project_planes(h, grid, at, psi, psi_dtype, nbands, numax, cube, prec, static_cast<float*>(coeff), s);
   SHO_TRY(begin_call(h, s));
   if (prec == SHO_P_FF64) SHO_TRY(ensure_workspace(h, ff_t2_bytes(natoms, cube, numax, nbands)));
   const uint64_t key = geometry_key(grid, at, cube);

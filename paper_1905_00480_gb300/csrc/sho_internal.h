@@ -169,7 +169,8 @@ struct PlanePlan {
 };
 struct PlaneLaunch {
   GridDev g;
-  const float* psi;          // [Nz][Ny][Nx][B] FP32, 16-byte aligned, B % 4 == 0
+  const void* psi;           // [Nz][Ny][Nx][B] FP32 or BF16, 16-byte aligned, rows of whole 16-byte units
+  sho_dtype psi_dtype;       // SHO_F32 or SHO_BF16
   const AtomDev* atoms;
   int natoms;
   int numax;

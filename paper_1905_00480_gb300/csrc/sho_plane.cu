@@ -41,7 +41,11 @@ constexpr int kPlaneSlots = 3;                         // y-pass accumulator slo
 constexpr int kPlaneThreads = (kPlaneWarps + 1) * 32;  // + the producer warp
 constexpr int kPlaneMaxStages = 8;
 constexpr int kT1Stride = 36;                          // padded row of the T1 transpose buffer
-constexpr int kPlaneRowBytes = 32 * 4;                 // one x point: 32 FP32 bands (one swizzle row)
+// Bytes of one x point of a row buffer: 32 bands of the storage type (SB bytes each).  FP32 rows are
+// 128-byte swizzled (one swizzle row per point); BF16 rows (64 bytes) are not swizzled: their MMA A loads
+// take x = base + t (+4, +8, +12) for lane quad t, so the quads alternate between the two bank halves.
+template <int SB>
+__host__ __device__ constexpr int plane_row_bytes() { return 32 * SB; }
 constexpr int kSimtMode = -1;
 
 // --------------------------------------------------------------------------------- mbarrier / TMA
@@ -93,7 +97,21 @@ __device__ __forceinline__ float lds32(uint32_t addr) {
 
 // Byte offset of bands 4c..4c+3 of x point x in a 128-byte-swizzled row buffer.
 __device__ __forceinline__ uint32_t swz(int x, int c) {
-  return (uint32_t)x * kPlaneRowBytes + ((uint32_t)(c ^ (x & 7)) << 4);
+  return (uint32_t)x * 128u + ((uint32_t)(c ^ (x & 7)) << 4);
+}
+// Byte offset of bands 4c..4c+3 of x point x in a BF16 row buffer (64 bytes per point, no swizzle).
+__device__ __forceinline__ uint32_t bfo(int x, int c) { return (uint32_t)x * 64u + ((uint32_t)c << 3); }
+// Four BF16 values (8 bytes of shared memory) widened exactly to FP32.
+__device__ __forceinline__ float4 lds_bf16x4(uint32_t addr) {
+  uint32_t u0, u1;
+  asm volatile("ld.shared.v2.u32 {%0,%1}, [%2];\n" : "=r"(u0), "=r"(u1) : "r"(addr));
+  return make_float4(__uint_as_float(u0 << 16), __uint_as_float(u0 & 0xffff0000u), __uint_as_float(u1 << 16),
+                     __uint_as_float(u1 & 0xffff0000u));
+}
+__device__ __forceinline__ float lds_bf16(uint32_t addr) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];\n" : "=h"(v) : "r"(addr));
+  return __uint_as_float((uint32_t)v << 16);
 }
 
 // Grid x of cube point i for an atom whose first x is x0 (periodic: x0 in [0, Nx), one wrap at most;
@@ -107,7 +125,7 @@ __device__ __forceinline__ int plane_x(int x0, int i, int nx, int periodic) {
 // --------------------------------------------------------------------------------- tables
 // One warp per atom.  ytab[a][iy][8] and xtab[a][ix][8] (FP32, zero beyond numax and, when not
 // periodic, at cube points outside the grid); bfrag[a][lane][s][4] B fragments of the x table.
-template <int NU, int MODE>
+template <int NU, int MODE, int SB>
 __global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev* __restrict__ atoms,
                                                         float* __restrict__ xtab, float* __restrict__ ytab,
                                                         uint32_t* __restrict__ bfrag) {
@@ -136,16 +154,17 @@ __global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev
     const int gq = lane >> 2, tq = lane & 3;
     uint32_t* out = bfrag + ((size_t)a * kWarp + lane) * (kMaxCube / 8) * 4;
     for (int s = 0; s * K < C; s++) {
+      // k -> x of the A loads: FP32 rows x = 2t, 2t+1 (+8, +9); BF16 rows x = t, t+4 (+8, +12)
       float b[4];
       if constexpr (K == 8) {
-        b[0] = xs[8 * s + 2 * tq][gq];
-        b[1] = xs[8 * s + 2 * tq + 1][gq];
+        b[0] = xs[8 * s + (SB == 4 ? 2 * tq : tq)][gq];
+        b[1] = xs[8 * s + (SB == 4 ? 2 * tq + 1 : tq + 4)][gq];
         b[2] = b[3] = 0.0f;
       } else {
-        b[0] = xs[16 * s + 2 * tq][gq];
-        b[1] = xs[16 * s + 2 * tq + 1][gq];
-        b[2] = xs[16 * s + 2 * tq + 8][gq];
-        b[3] = xs[16 * s + 2 * tq + 9][gq];
+        b[0] = xs[16 * s + (SB == 4 ? 2 * tq : tq)][gq];
+        b[1] = xs[16 * s + (SB == 4 ? 2 * tq + 1 : tq + 4)][gq];
+        b[2] = xs[16 * s + (SB == 4 ? 2 * tq + 8 : tq + 8)][gq];
+        b[3] = xs[16 * s + (SB == 4 ? 2 * tq + 9 : tq + 12)][gq];
       }
       const BFrag<TM> f = make_bfrag<TM>(b);
       reinterpret_cast<uint4*>(out)[s] = make_uint4(f.hi[0], f.hi[1], f.lo[0], f.lo[1]);
@@ -156,8 +175,9 @@ __global__ void __launch_bounds__(kWarp) k_plane_tables(GridDev g, const AtomDev
 // --------------------------------------------------------------------------------- plane sweep
 // Bytes of one ring stage: a row of nx x points, rounded up to 1024 so that every stage starts on a
 // 1024-byte boundary, which the 128-byte swizzle pattern of the TMA (and swz) is anchored to.
+template <int SB>
 __host__ __device__ __forceinline__ uint32_t plane_stage_bytes(int nx) {
-  return ((uint32_t)nx * kPlaneRowBytes + 1023u) & ~1023u;
+  return ((uint32_t)nx * plane_row_bytes<SB>() + 1023u) & ~1023u;
 }
 
 // Per (warp, slot) shared area, filled when a segment starts: the atom's B fragments (tensor forms:
@@ -175,7 +195,7 @@ struct SlotLayout {
   static constexpr int kBytes = kFrag + 32 * 8 * 4;
 };
 
-template <int MODE>
+template <int MODE, int SB>
 struct PlaneSmem {
   // everything but the ring, including the alignment slack of the ring
   static constexpr size_t fixed() {
@@ -184,10 +204,10 @@ struct PlaneSmem {
            + (size_t)kPlaneWarps * kPlaneSlots * SlotLayout<MODE>::kBytes  // slot tables
            + (size_t)kPlaneWarps * kPlaneSlots * 32;                  // slot records
   }
-  static size_t bytes(int nx, int stages) { return fixed() + (size_t)stages * plane_stage_bytes(nx); }
+  static size_t bytes(int nx, int stages) { return fixed() + (size_t)stages * plane_stage_bytes<SB>(nx); }
 };
 
-template <int NU, int MODE>
+template <int NU, int MODE, int SB>
 __global__ void __launch_bounds__(kPlaneThreads, 1)
     k_project_plane(const __grid_constant__ CUtensorMap map, GridDev g, const int4* __restrict__ items,
                     const int* __restrict__ slot_ptr, const PlaneSeg* __restrict__ segs,
@@ -204,8 +224,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
   const uint32_t raw = pl_smem(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   const int Nx = g.n[0], Ny = g.n[1], C = g.cube, B = g.nbands;
-  const uint32_t rowbytes = (uint32_t)Nx * kPlaneRowBytes;  // bytes one TMA row load delivers
-  const uint32_t stagebytes = plane_stage_bytes(Nx);
+  const uint32_t rowbytes = (uint32_t)Nx * plane_row_bytes<SB>();  // bytes one TMA row load delivers
+  const uint32_t stagebytes = plane_stage_bytes<SB>(Nx);
   const uint32_t ring = base;
   const uint32_t bar_full = ring + (uint32_t)stages * stagebytes;
   const uint32_t bar_empty = bar_full + kPlaneMaxStages * 8;
@@ -357,7 +377,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           for (int n = 0; n < NP; n++) t1[n] = 0.0f;
           for (int i = 0; i < C; i++) {
             const int x = plane_x(x0, i, Nx, g.periodic);
-            const float v = lds32(row + swz(x, lane >> 2) + (uint32_t)(lane & 3) * 4);
+            const float v = SB == 4 ? lds32(row + swz(x, lane >> 2) + (uint32_t)(lane & 3) * 4)
+                                    : lds_bf16(row + (uint32_t)x * 64u + (uint32_t)lane * 2u);
             const float4 f0 = lds128(sa + (uint32_t)i * 32), f1 = lds128(sa + (uint32_t)i * 32 + 16);
             const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
 #pragma unroll
@@ -372,7 +393,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
           const bool lin = (rc.w & 4) != 0;
           // contiguous cube: x advances by 8 per TF32 k-step (1024 bytes, same swizzle phase), so the
           // A loads are fixed offsets from two per-lane base addresses
-          const uint32_t pa = row + swz(x0 + 2 * tq, gq), pb = row + swz(x0 + 2 * tq + 1, gq);
+          const uint32_t pa = SB == 4 ? row + swz(x0 + 2 * tq, gq) : row + bfo(x0 + tq, gq);
+          const uint32_t pb = SB == 4 ? row + swz(x0 + 2 * tq + 1, gq) : row + bfo(x0 + tq + 4, gq);
 #pragma unroll 2
           for (int ks = 0; ks < kPlaneMaxCube / K; ks++) {
             if (ks * K < C) {
@@ -392,14 +414,24 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
               bfr.lo[1] = bw.w;
               if constexpr (K == 8) {
                 float4 va, vb;
-                if (lin) {
-                  va = lds128(pa + ks * 1024);
-                  vb = lds128(pb + ks * 1024);
+                if constexpr (SB == 4) {
+                  if (lin) {
+                    va = lds128(pa + ks * 1024);
+                    vb = lds128(pb + ks * 1024);
+                  } else {
+                    const int xa = plane_x(x0, 8 * ks + 2 * tq, Nx, g.periodic);
+                    const int xb = plane_x(x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
+                    va = lds128(row + swz(xa, gq));
+                    vb = lds128(row + swz(xb, gq));
+                  }
                 } else {
-                  const int xa = plane_x(x0, 8 * ks + 2 * tq, Nx, g.periodic);
-                  const int xb = plane_x(x0, 8 * ks + 2 * tq + 1, Nx, g.periodic);
-                  va = lds128(row + swz(xa, gq));
-                  vb = lds128(row + swz(xb, gq));
+                  if (lin) {
+                    va = lds_bf16x4(pa + ks * 512);
+                    vb = lds_bf16x4(pb + ks * 512);
+                  } else {
+                    va = lds_bf16x4(row + bfo(plane_x(x0, 8 * ks + tq, Nx, g.periodic), gq));
+                    vb = lds_bf16x4(row + bfo(plane_x(x0, 8 * ks + tq + 4, Nx, g.periodic), gq));
+                  }
                 }
                 const float a0[4] = {va.x, va.y, vb.x, vb.y};
                 const float a1[4] = {va.z, va.w, vb.z, vb.w};
@@ -407,20 +439,34 @@ __global__ void __launch_bounds__(kPlaneThreads, 1)
                 tc_product<TM>(d[1], dl[1], a1, bfr);
               } else {
                 float4 v0, v1, v2, v3;
-                if (lin) {
-                  v0 = lds128(pa + ks * 2048);
-                  v1 = lds128(pb + ks * 2048);
-                  v2 = lds128(pa + ks * 2048 + 1024);
-                  v3 = lds128(pb + ks * 2048 + 1024);
+                if constexpr (SB == 4) {
+                  if (lin) {
+                    v0 = lds128(pa + ks * 2048);
+                    v1 = lds128(pb + ks * 2048);
+                    v2 = lds128(pa + ks * 2048 + 1024);
+                    v3 = lds128(pb + ks * 2048 + 1024);
+                  } else {
+                    const int xq0 = plane_x(x0, 16 * ks + 2 * tq, Nx, g.periodic);
+                    const int xq1 = plane_x(x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
+                    const int xq2 = plane_x(x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
+                    const int xq3 = plane_x(x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
+                    v0 = lds128(row + swz(xq0, gq));
+                    v1 = lds128(row + swz(xq1, gq));
+                    v2 = lds128(row + swz(xq2, gq));
+                    v3 = lds128(row + swz(xq3, gq));
+                  }
                 } else {
-                  const int xq0 = plane_x(x0, 16 * ks + 2 * tq, Nx, g.periodic);
-                  const int xq1 = plane_x(x0, 16 * ks + 2 * tq + 1, Nx, g.periodic);
-                  const int xq2 = plane_x(x0, 16 * ks + 2 * tq + 8, Nx, g.periodic);
-                  const int xq3 = plane_x(x0, 16 * ks + 2 * tq + 9, Nx, g.periodic);
-                  v0 = lds128(row + swz(xq0, gq));
-                  v1 = lds128(row + swz(xq1, gq));
-                  v2 = lds128(row + swz(xq2, gq));
-                  v3 = lds128(row + swz(xq3, gq));
+                  if (lin) {
+                    v0 = lds_bf16x4(pa + ks * 1024);
+                    v1 = lds_bf16x4(pb + ks * 1024);
+                    v2 = lds_bf16x4(pa + ks * 1024 + 512);
+                    v3 = lds_bf16x4(pb + ks * 1024 + 512);
+                  } else {
+                    v0 = lds_bf16x4(row + bfo(plane_x(x0, 16 * ks + tq, Nx, g.periodic), gq));
+                    v1 = lds_bf16x4(row + bfo(plane_x(x0, 16 * ks + tq + 4, Nx, g.periodic), gq));
+                    v2 = lds_bf16x4(row + bfo(plane_x(x0, 16 * ks + tq + 8, Nx, g.periodic), gq));
+                    v3 = lds_bf16x4(row + bfo(plane_x(x0, 16 * ks + tq + 12, Nx, g.periodic), gq));
+                  }
                 }
                 const float a0[8] = {v0.x, v1.x, v0.y, v1.y, v2.x, v3.x, v2.y, v3.y};
                 const float a1[8] = {v0.z, v1.z, v0.w, v1.w, v2.z, v3.z, v2.w, v3.w};
@@ -540,33 +586,34 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int MODE>
+template <int MODE, int SB>
 int plane_stages(int nx) {
-  const int budget = kPlaneSmemBudget - (int)PlaneSmem<MODE>::fixed();
-  return std::min(kPlaneMaxStages, std::max(2, budget / (int)plane_stage_bytes(nx)));
+  const int budget = kPlaneSmemBudget - (int)PlaneSmem<MODE, SB>::fixed();
+  return std::min(kPlaneMaxStages, std::max(2, budget / (int)plane_stage_bytes<SB>(nx)));
 }
 
-template <int NU, int MODE>
+template <int NU, int MODE, int SB>
 cudaError_t plane_run(const PlaneLaunch& p) {
   const int A = p.natoms, nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  k_plane_tables<NU, MODE><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, p.bfrag);
+  k_plane_tables<NU, MODE, SB><<<A, kWarp, 0, p.stream>>>(p.g, p.atoms, p.xtab, p.ytab, p.bfrag);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   CUtensorMap map;
   const cuuint64_t dims[2] = {(cuuint64_t)p.g.nbands, (cuuint64_t)p.g.n[0] * p.g.n[1] * p.g.n[2]};
-  const cuuint64_t strides[1] = {(cuuint64_t)p.g.nbands * sizeof(float)};
+  const cuuint64_t strides[1] = {(cuuint64_t)p.g.nbands * SB};
   const cuuint32_t box[2] = {32u, (cuuint32_t)p.g.n[0]};
   const cuuint32_t estr[2] = {1u, 1u};
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p.psi), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+  if (enc(&map, SB == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+          const_cast<void*>(p.psi), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          SB == 4 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   if (p.nitems > 0) {
-    const int stages = plane_stages<MODE>(p.g.n[0]);
-    const size_t smem = PlaneSmem<MODE>::bytes(p.g.n[0], stages);
-    auto kern = k_project_plane<NU, MODE>;
+    const int stages = plane_stages<MODE, SB>(p.g.n[0]);
+    const size_t smem = PlaneSmem<MODE, SB>::bytes(p.g.n[0], stages);
+    auto kern = k_project_plane<NU, MODE, SB>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)p.nitems * nbt, kPlaneThreads, smem, p.stream>>>(map, p.g, p.items, p.slot_ptr, p.segs, p.bfrag,
@@ -579,23 +626,28 @@ cudaError_t plane_run(const PlaneLaunch& p) {
   return cudaGetLastError();
 }
 
-template <int NU>
-cudaError_t plane_mode(const PlaneLaunch& p, sho_prec prec) {
+template <int NU, int SB>
+cudaError_t plane_mode_sb(const PlaneLaunch& p, sho_prec prec) {
   switch (prec) {
-    case SHO_P_FP32: return plane_run<NU, kSimtMode>(p);
-    case SHO_P_TF32: return plane_run<NU, (int)TcMode::TF32>(p);
-    case SHO_P_3XTF32: return plane_run<NU, (int)TcMode::X3TF32>(p);
-    case SHO_P_BF16: return plane_run<NU, (int)TcMode::BF16>(p);
-    case SHO_P_SPLIT_FP16: return plane_run<NU, (int)TcMode::SPLIT16>(p);
+    case SHO_P_FP32: return plane_run<NU, kSimtMode, SB>(p);
+    case SHO_P_TF32: return plane_run<NU, (int)TcMode::TF32, SB>(p);
+    case SHO_P_3XTF32: return plane_run<NU, (int)TcMode::X3TF32, SB>(p);
+    case SHO_P_BF16: return plane_run<NU, (int)TcMode::BF16, SB>(p);
+    case SHO_P_SPLIT_FP16: return plane_run<NU, (int)TcMode::SPLIT16, SB>(p);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int NU>
+cudaError_t plane_mode(const PlaneLaunch& p, sho_prec prec) {
+  return p.psi_dtype == SHO_BF16 ? plane_mode_sb<NU, 2>(p, prec) : plane_mode_sb<NU, 4>(p, prec);
 }
 
 }  // namespace
 
 bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nbands, int numax, int cube,
               sho_prec prec) {
-  if (psi_dt != SHO_F32 || !fp32_stream_ok(psi, psi_dt, nbands)) return false;
+  if ((psi_dt != SHO_F32 && psi_dt != SHO_BF16) || !fp32_stream_ok(psi, psi_dt, nbands)) return false;
   if (prec != SHO_P_FP32 && !is_tc(prec)) return false;
   if (numax > kTcMaxNumax || cube % 16 != 0 || cube > kPlaneMaxCube) return false;
   if (grid->n[0] > 256 || (long long)grid->n[0] * grid->n[1] * grid->n[2] >= (1ll << 31)) return false;

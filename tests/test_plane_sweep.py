@@ -1,5 +1,5 @@
-"""Plane-sweep projection of the FP32-class forms (FP32 psi, numax <= 7) against the FP64 oracle (GPU),
-and the FP32-class expansion on the same geometries.
+"""Plane-sweep projection of the FP32-class forms (FP32 or BF16 psi, numax <= 7) against the FP64 oracle
+run on the storage-rounded psi (GPU), and the FP32-class expansion on the same geometries.
 
 The plane sweep assigns every (atom, plane) row segment to a register slot on the host; these cases
 drive its corners: more overlapping atoms per row than slots (several sweeps of one plane), wrapped
@@ -17,14 +17,15 @@ from test_parity_tc import TOL
 pytestmark = pytest.mark.gpu
 
 
-def _project(grid, h, periodic, pos, sig, numax, cube, nbands, prec, seed):
+def _project(grid, h, periodic, pos, sig, numax, cube, nbands, prec, seed, storage="f32"):
     import torch
     from paper_1905_00480_gb300 import api
     rng = np.random.default_rng(seed)
     psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands)).astype(np.float32)
-    psi_d = torch.from_numpy(psi).cuda()
+    psi_d = torch.from_numpy(psi).cuda().to(torch.bfloat16 if storage == "bf16" else torch.float32)
+    assert api.project_path(psi_d, numax, cube, h, periodic, prec=prec) == "plane"
     got = api.project(psi_d, pos, sig, numax, cube, h, periodic, prec=prec).double().cpu().numpy()
-    ref = oracle.project(grid, h, periodic, psi.astype(np.float64), pos, sig, numax, cube)
+    ref = oracle.project(grid, h, periodic, psi_d.double().cpu().numpy(), pos, sig, numax, cube)
     return got, ref
 
 
@@ -32,31 +33,34 @@ def _tol(prec):
     return TOL_FP32 if prec == "fp32" else TOL[prec]
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "3xtf32", "bf16", "split_fp16"])
-def test_dense_atoms_need_several_sweeps(prec):
+def test_dense_atoms_need_several_sweeps(prec, storage):
     """120 atoms in a periodic 48^3 box with cube 32: about 53 cubes meet each grid row, more than the
     33 register slots of one sweep, so planes are swept more than once."""
     require_gpu()
     rng = np.random.default_rng(601)
     grid, h, numax, cube = (48, 48, 48), 0.2, 3, 32
     pos, sig = workloads.random_atoms(rng, 120, tuple(n * h for n in grid), True, min_sep=0.6)
-    got, ref = _project(grid, h, True, pos, sig, numax, cube, 8, prec, 602)
+    got, ref = _project(grid, h, True, pos, sig, numax, cube, 8, prec, 602, storage)
     assert_coeff_close(got, ref, _tol(prec))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32"])
-def test_wrapped_cubes_on_small_grid(prec):
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_wrapped_cubes_on_small_grid(prec, storage):
     """Periodic grid only 2-4 points longer than the cube in y: most cubes wrap, and the two halves of a
     wrapped atom are summed in one warp."""
     require_gpu()
     rng = np.random.default_rng(603)
     grid, h, numax, cube = (36, 34, 40), 0.2, 5, 32
     pos, sig = workloads.random_atoms(rng, 7, tuple(n * h for n in grid), True, min_sep=1.0)
-    got, ref = _project(grid, h, True, pos, sig, numax, cube, 36, prec, 604)
+    got, ref = _project(grid, h, True, pos, sig, numax, cube, 40 if storage == "bf16" else 36, prec, 604, storage)
     assert_coeff_close(got, ref, _tol(prec))
 
 
-def test_atoms_outside_open_box():
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_atoms_outside_open_box(storage):
     """Not periodic: cubes clipped on every side, and one atom whose cube misses the grid in y entirely
     (its coefficients are exactly zero)."""
     require_gpu()
@@ -65,7 +69,7 @@ def test_atoms_outside_open_box():
     pos = np.array([[-2.0, 3.0, 5.0], [L + 1.5, L - 0.3, 0.2], [5.0, -9.0, 5.0], [4.9, 5.1, L + 2.0],
                     [0.1, 0.2, 0.3]])
     sig = np.array([0.8, 0.9, 0.7, 1.0, 0.6])
-    got, ref = _project(grid, h, False, pos, sig, numax, cube, 16, "tf32", 605)
+    got, ref = _project(grid, h, False, pos, sig, numax, cube, 16, "tf32", 605, storage)
     assert np.all(got[2] == 0.0)
     keep = [0, 1, 3, 4]
     assert_coeff_close(got[keep], ref[keep], TOL["tf32"])
@@ -80,11 +84,15 @@ def test_every_numax(numax):
     for prec in ("fp32", "tf32"):
         got, ref = _project(grid, h, True, pos, sig, numax, cube, 12, prec, 620 + numax)
         assert_coeff_close(got, ref, _tol(prec))
+    for prec in ("fp32", "split_fp16"):
+        got, ref = _project(grid, h, True, pos, sig, numax, cube, 24, prec, 640 + numax, "bf16")
+        assert_coeff_close(got, ref, _tol(prec))
 
 
 def test_plane_path_selection():
-    """Eligible calls take the plane sweep; a row longer than one TMA box (Nx > 256), BF16 storage,
-    unaligned band counts and numax 8 take the per-atom kernels; all give the oracle's result."""
+    """Eligible calls take the plane sweep (FP32 or BF16 rows of whole 16-byte units); a row longer than
+    one TMA box (Nx > 256), unaligned band counts and numax 8 take the per-atom kernels; all give the
+    oracle's result."""
     require_gpu()
     import torch
     from paper_1905_00480_gb300 import api
@@ -94,7 +102,8 @@ def test_plane_path_selection():
     assert api.project_path(psi, numax, cube, h, True, "tf32") == "plane"
     assert api.project_path(psi, numax, cube, h, True, "fp32") == "plane"
     assert api.project_path(psi, 8, cube, h, True, "fp32") == "atom"
-    assert api.project_path(psi.to(torch.bfloat16), numax, cube, h, True, "tf32") == "atom"
+    assert api.project_path(psi.to(torch.bfloat16), numax, cube, h, True, "tf32") == "plane"
+    assert api.project_path(psi[..., :4].contiguous().to(torch.bfloat16), numax, cube, h, True, "tf32") == "atom"
     assert api.project_path(torch.zeros((40, 40, 40, 6), device="cuda"), numax, cube, h, True, "tf32") == "atom"
     assert api.project_path(psi.double(), numax, cube, h, True, "ff64") == "atom"
     wide = (264, 16, 16)
