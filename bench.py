@@ -329,11 +329,17 @@ def run_ours(args, ws, rank, local):
     ms_copy = max_over_ranks(ws, e0.elapsed_time(e1) / K2)
 
     # the paper's timing protocol (Sec. 6): median over 15 runs of 10 back-to-back steps
+    def step_p():
+        api.project(psi, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
+                    stream=stream)
+        api.add(hps[0], cin, pos, sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle, stream=stream)
+
+    step_p()
     per = []
     for _ in range(15):
         e0.record(stream)
         for _ in range(10):
-            step()
+            step_p()
         e1.record(stream)
         e1.synchronize()
         per.append(e0.elapsed_time(e1) / 10)
