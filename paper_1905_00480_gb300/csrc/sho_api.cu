@@ -360,8 +360,11 @@ int geo_cache(sho_handle* h, int slot, uint64_t key, const std::vector<std::pair
   return SHO_OK;
 }
 
+// t2_out != nullptr: stop after the per-plane sums and leave them in t2_out ([A][cube][P][B] FP32, owned by
+// the caller) for a fused z-pass; coeff is then not written.
 int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDev>& at, const void* psi,
-                   sho_dtype psi_dtype, int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s) {
+                   sho_dtype psi_dtype, int nbands, int numax, int cube, sho_prec prec, float* coeff, cudaStream_t s,
+                   float* t2_out = nullptr) {
   const size_t A = at.size();
   const uint64_t key = geometry_key(grid, at, cube);
   SHO_TRY(begin_call(h, s));
@@ -410,7 +413,7 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
   const size_t o_xt = cv.take(A * cube * 8 * sizeof(float));
   const size_t o_yt = cv.take(A * cube * 8 * sizeof(float));
   const size_t o_bf = cv.take(A * kPlaneBfragBytesPerAtom);
-  const size_t o_t2 = cv.take(A * cube * (size_t)npairs(numax) * nbands * sizeof(float));
+  const size_t o_t2 = t2_out ? 0 : cv.take(A * cube * (size_t)npairs(numax) * nbands * sizeof(float));
   SHO_TRY(ensure_workspace(h, cv.off));
   char* ws = static_cast<char*>(h->ws);
   const char* pm = static_cast<const char*>(h->plane_mem);
@@ -428,7 +431,8 @@ int project_planes(sho_handle* h, const sho_grid* grid, const std::vector<AtomDe
   L.xtab = reinterpret_cast<float*>(ws + o_xt);
   L.ytab = reinterpret_cast<float*>(ws + o_yt);
   L.bfrag = reinterpret_cast<uint32_t*>(ws + o_bf);
-  L.t2p = reinterpret_cast<float*>(ws + o_t2);
+  L.t2p = t2_out ? t2_out : reinterpret_cast<float*>(ws + o_t2);
+  L.t2_only = t2_out != nullptr;
   L.coeff = coeff;
   L.status = h->dstatus;
   L.wait_cycles = h->wait_cycles;
@@ -758,9 +762,13 @@ int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype,
                                                                                               : SHO_PATH_ATOM;
 }
 
-int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
-                const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* coeff,
-                sho_dtype coeff_dtype, void* stream) {
+// t2_out != nullptr (fused non-local action): where the path has a separate z-pass (FP64-accurate form,
+// plane sweep) stop after the per-plane y-pass sums, leave them in t2_out ([A][cube][P][B], compute type)
+// and set *at_t2; other paths write coeff as usual.
+static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
+                        int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                        void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2) {
+  if (at_t2) *at_t2 = false;
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
@@ -772,10 +780,14 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
-  if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec))
-    return project_planes(h, grid, at, psi, psi_dtype, nbands, numax, cube, prec, static_cast<float*>(coeff), s);
+  if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec)) {
+    if (t2_out && at_t2) *at_t2 = true;
+    return project_planes(h, grid, at, psi, psi_dtype, nbands, numax, cube, prec, static_cast<float*>(coeff), s,
+                          static_cast<float*>(t2_out));
+  }
   SHO_TRY(begin_call(h, s));
-  if (prec == SHO_P_FF64) SHO_TRY(ensure_workspace(h, ff_t2_bytes(natoms, cube, numax, nbands)));
+  const bool ff_t2 = prec == SHO_P_FF64 && t2_out;
+  if (prec == SHO_P_FF64 && !ff_t2) SHO_TRY(ensure_workspace(h, ff_t2_bytes(natoms, cube, numax, nbands)));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[0].key != key) {
     std::vector<int> order = spatial_order(grid, at);
@@ -794,7 +806,8 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
   L.zsplit = prec == SHO_P_FF64 ? ff_zsplit(natoms, nbands, cube, h->sms) : zsplit_balanced(natoms, nbands, cube, h->sms);
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
-  L.t2 = h->ws;
+  L.t2 = ff_t2 ? t2_out : h->ws;
+  L.t2_only = ff_t2;
   L.status = h->dstatus;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
@@ -807,12 +820,21 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
     h->last_where = "projection launch";
     return SHO_ERR_CUDA;
   }
+  if (ff_t2 && at_t2) *at_t2 = true;
   return end_call(h, s);
+}
+
+int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands, int natoms,
+                const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* coeff,
+                sho_dtype coeff_dtype, void* stream) {
+  return project_impl(h, grid, psi, psi_dtype, nbands, natoms, pos, sigma, numax, cube, prec, coeff, coeff_dtype,
+                      stream, nullptr, nullptr);
 }
 
 static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
                     sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
-                    int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream) {
+                    int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream,
+                    const NonlocalIn* nl = nullptr) {
   if (!h) return SHO_ERR_ARG;
   if (!std::isfinite(alpha)) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
@@ -877,6 +899,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   L.t2 = ws + o_t2;
   L.tables_xmajor = ws + o_txm;
   L.scale = alpha;
+  if (nl) L.nl = *nl;
   L.status = h->dstatus;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_expand(L)
@@ -987,30 +1010,39 @@ int sho_apply_nonlocal(sho_handle* h, const sho_grid* grid, const void* psi, sho
   DeviceGuard guard(h->device);
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Coefficient buffers: c (projection) and d = D c.  They sit in a second allocation owned by the
-  // handle's workspace growth, ahead of what the nested calls carve, so use a dedicated region: the
-  // workspace is sized for the larger of the nested calls plus both coefficient arrays.
-  const size_t nco = (size_t)natoms * nstates(numax) * (size_t)nbands * compute_size(cdt);
+  // The projection leaves its per-plane y-pass sums (paths with a separate z-pass: FP64-accurate form, plane
+  // sweep) or its coefficients (the other paths) in a buffer of the handle; the expansion's z-pass kernel
+  // then finishes the projection, multiplies by D and expands, with c and d in shared memory only.
+  const size_t es = compute_size(cdt);
+  const size_t nco = (size_t)natoms * nstates(numax) * (size_t)nbands * es;
+  const size_t nt2 = (size_t)natoms * cube * (size_t)npairs(numax) * (size_t)nbands * es;
+  const size_t need = std::max(nco, nt2);
   const size_t inner = std::max(workspace_bytes(SHO_OP_PROJECT, grid, natoms, numax, cube, nbands, cdt),
                                 workspace_bytes(SHO_OP_EXPAND, grid, natoms, numax, cube, nbands, cdt));
   SHO_TRY(begin_call(h, s));
-  if (!h->coeff_ws || h->coeff_ws_bytes < 2 * nco) {
+  if (!h->coeff_ws || h->coeff_ws_bytes < need) {
     if (h->has_last && cudaEventSynchronize(h->last) != cudaSuccess) return SHO_ERR_CUDA;
     if (h->coeff_ws) cudaFree(h->coeff_ws);
     h->coeff_ws = nullptr;
     h->coeff_ws_bytes = 0;
-    if (cudaMalloc(&h->coeff_ws, 2 * nco) != cudaSuccess) {
+    if (cudaMalloc(&h->coeff_ws, need) != cudaSuccess) {
       cudaGetLastError();
       return SHO_ERR_OOM;
     }
-    h->coeff_ws_bytes = 2 * nco;
+    h->coeff_ws_bytes = need;
   }
   SHO_TRY(ensure_workspace(h, inner));
-  void* c = h->coeff_ws;
-  void* d = static_cast<char*>(h->coeff_ws) + nco;
-  SHO_TRY(sho_project(h, grid, psi, psi_dtype, nbands, natoms, pos, sigma, numax, cube, prec, c, cdt, stream));
-  if (launch_dmatrix(natoms, nstates(numax), nbands, cdt, D, c, d, s) != cudaSuccess) return SHO_ERR_CUDA;
-  return sho_add(h, grid, d, cdt, nbands, natoms, pos, sigma, numax, cube, prec, hpsi, psi_dtype, stream);
+  void* buf = h->coeff_ws;
+  bool at_t2 = false;
+  SHO_TRY(project_impl(h, grid, psi, psi_dtype, nbands, natoms, pos, sigma, numax, cube, prec, buf, cdt, stream, buf,
+                       &at_t2));
+  NonlocalIn nl;
+  nl.D = D;
+  nl.t2p = at_t2 ? buf : nullptr;
+  nl.c = at_t2 ? nullptr : buf;
+  nl.h3 = grid->h * grid->h * grid->h;
+  return add_impl(h, grid, 1.0, 0, buf, cdt, nbands, natoms, pos, sigma, numax, cube, prec, hpsi, psi_dtype, stream,
+                  &nl);
 }
 
 // ------------------------------------------------------------------ stored-projector baseline

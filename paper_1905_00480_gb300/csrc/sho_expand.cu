@@ -25,12 +25,18 @@ constexpr int kZChunk = 4;  // planes per shared-memory chunk of the band-tiled 
 template <int NU, typename TCo, typename TC, bool TILED = false>
 __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
                                                         const TCo* __restrict__ coeff, TC* __restrict__ tables,
-                                                        TC* __restrict__ t2, TC* __restrict__ txm, double scale) {
+                                                        TC* __restrict__ t2, TC* __restrict__ txm, double scale,
+                                                        NonlocalIn nl) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int C = g.cube;
   TC* phz = reinterpret_cast<TC*>(smem_raw);  // [NP][C]
+  // fused non-local action: unscaled z table [NP][C] (projection), then c and d as [N][32] columns
+  TC* nls = phz + (size_t)NP * C + (TILED ? (size_t)kZChunk * kWarp * tiled_pairs(P) : 0);
+  TC* pz = nls;
+  TC* cs = pz + (nl.t2p ? (size_t)NP * C : 0);
+  TC* ds = cs + (size_t)N * kWarp;
   const int lane = threadIdx.x;
   const int a = blockIdx.y;
   const int B = g.nbands;
@@ -46,6 +52,9 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
     phi_column(cube_offset(at.o[2], i, g.h, at.X[2]), at.sigma, NU, zc, 1);
 #pragma unroll
     for (int n = 0; n < NP; n++) phz[n * C + i] = (TC)(zc[n] * scale);
+    if (nl.D && nl.t2p)
+#pragma unroll
+      for (int n = 0; n < NP; n++) pz[n * C + i] = (TC)zc[n];
     if (blockIdx.x == 0) {
       phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, tx + i, C);
       phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, ty + i, C);
@@ -58,10 +67,52 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
     }
   }
   __syncwarp();
+
+  // coefficients of this (atom, band): from global memory, or (fused action) d = D c in shared memory
+  const TCo* ca = coeff + (size_t)a * N * B + (bok ? b : 0);
+  size_t cstr = (size_t)B;
+  if (nl.D) {
+    if (nl.t2p) {
+      // the projection's z-pass over the per-plane sums, planes ascending (cube planes outside an open
+      // grid, and every plane of a cube that misses the grid in y, contribute nothing)
+      const TC* t2a = static_cast<const TC*>(nl.t2p) + (size_t)a * C * P * B + (bok ? b : 0);
+      for (int k = 0; k < N; k++) cs[k * kWarp + lane] = (TC)0;
+      const bool yrows = g.periodic || (at.o[1] < g.n[1] && at.o[1] + C > 0);
+      if (bok && yrows) {
+        for (int iz = 0; iz < C; iz++) {
+          if (cube_index(at.o[2], iz, g.n[2], g.periodic) < 0) continue;
+#pragma unroll
+          for (int ny = 0; ny < NP; ny++)
+#pragma unroll
+            for (int nx = 0; nx + ny <= NU; nx++) {
+              const TC v = t2a[((size_t)iz * P + BS::pair(nx, ny)) * B];
+#pragma unroll
+              for (int nz = 0; nx + ny + nz <= NU; nz++) {
+                const int k = BS::state(nx, ny, nz);
+                cs[k * kWarp + lane] = fma(v, pz[nz * C + iz], cs[k * kWarp + lane]);
+              }
+            }
+        }
+      }
+      const TC h3 = (TC)nl.h3;
+      for (int k = 0; k < N; k++) cs[k * kWarp + lane] *= h3;
+    } else {
+      const TC* cg = static_cast<const TC*>(nl.c) + (size_t)a * N * B + (bok ? b : 0);
+      for (int k = 0; k < N; k++) cs[k * kWarp + lane] = bok ? cg[(size_t)k * B] : (TC)0;
+    }
+    // d = D c (step 2 of the action), states k' ascending
+    const TC* Da = static_cast<const TC*>(nl.D) + (size_t)a * N * N;
+    for (int k = 0; k < N; k++) {
+      TC acc = (TC)0;
+      for (int kp = 0; kp < N; kp++) acc = fma(__ldg(Da + (size_t)k * N + kp), cs[kp * kWarp + lane], acc);
+      ds[k * kWarp + lane] = acc;
+    }
+    ca = reinterpret_cast<const TCo*>(ds + lane);
+    cstr = kWarp;
+  }
   if (!TILED && !bok) return;
 
   constexpr int PP = tiled_pairs(P);
-  const TCo* ca = coeff + (size_t)a * N * B + (bok ? b : 0);
   if constexpr (!TILED) {
     TC* out = t2 + (size_t)a * C * P * B + b;
 #pragma unroll
@@ -71,7 +122,7 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
         TC cz[NP];
 #pragma unroll
         for (int nz = 0; nz < NP; nz++)
-          cz[nz] = (nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * B], (TC)0) : (TC)0;
+          cz[nz] = (nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * cstr], (TC)0) : (TC)0;
         const int p = BS::pair(nx, ny);
         for (int iz = 0; iz < C; iz++) {
           TC s = (TC)0;
@@ -96,7 +147,7 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
           TC cz[NP];
 #pragma unroll
           for (int nz = 0; nz < NP; nz++)
-            cz[nz] = (bok && nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * B], (TC)0) : (TC)0;
+            cz[nz] = (bok && nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * cstr], (TC)0) : (TC)0;
           const int p = BS::pair(nx, ny);
           for (int i = 0; i < nzc; i++) {
             TC s = (TC)0;
@@ -210,16 +261,32 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
     for (int jx = 0; jx < Nx; jx++) row[(size_t)jx * B] = store_cast(acc[jx * kWarp + lane], (TP*)nullptr);
 }
 
+// Shared memory of k_expand_zpass beyond its z table (and band-tiled staging): the fused action's unscaled
+// z table and its c and d columns.
+template <int NU, typename TC>
+static size_t nl_smem(const ExpandLaunch& p) {
+  if (!p.nl.D) return 0;
+  return ((p.nl.t2p ? (size_t)(NU + 1) * p.g.cube : 0) + 2 * (size_t)Basis<NU>::N * kWarp) * sizeof(TC);
+}
+
+template <typename K>
+static cudaError_t zpass_smem(K kern, size_t smem) {
+  return smem > 48 * 1024 ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                          : cudaSuccess;
+}
+
 template <int NU, typename TP, typename TCo, typename TC>
 static cudaError_t launch_expand_t(const ExpandLaunch& p) {
   const int C = p.g.cube;
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
   {
-    const size_t smem = (size_t)(NU + 1) * C * sizeof(TC);
+    const size_t smem = (size_t)(NU + 1) * C * sizeof(TC) + nl_smem<NU, TC>(p);
+    cudaError_t e = zpass_smem(k_expand_zpass<NU, TCo, TC>, smem);
+    if (e != cudaSuccess) return e;
     k_expand_zpass<NU, TCo, TC><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
         p.g, p.atoms, static_cast<const TCo*>(p.coeff), static_cast<TC*>(p.tables), static_cast<TC*>(p.t2),
-        (TC*)nullptr, p.scale);
-    cudaError_t e = cudaGetLastError();
+        (TC*)nullptr, p.scale, p.nl);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   {
@@ -248,10 +315,12 @@ static cudaError_t launch_expand_nu(const ExpandLaunch& p) {
 template <int NU>
 static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float);
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float) + nl_smem<NU, float>(p);
+  const cudaError_t e = zpass_smem(k_expand_zpass<NU, float, float>, smem);
+  if (e != cudaSuccess) return e;
   k_expand_zpass<NU, float, float><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
-      static_cast<float*>(p.tables_xmajor), p.scale);
+      static_cast<float*>(p.tables_xmajor), p.scale, p.nl);
   return cudaGetLastError();
 }
 
@@ -259,20 +328,25 @@ template <int NU>
 static cudaError_t zpass_f32_tiled_nu(const ExpandLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
   constexpr int PP = tiled_pairs(Basis<NU>::P);
-  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float) + (size_t)kZChunk * kWarp * PP * sizeof(float);
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float) + (size_t)kZChunk * kWarp * PP * sizeof(float) +
+                      nl_smem<NU, float>(p);
+  const cudaError_t e = zpass_smem(k_expand_zpass<NU, float, float, true>, smem);
+  if (e != cudaSuccess) return e;
   k_expand_zpass<NU, float, float, true><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
-      static_cast<float*>(p.tables_xmajor), p.scale);
+      static_cast<float*>(p.tables_xmajor), p.scale, p.nl);
   return cudaGetLastError();
 }
 
 template <int NU>
 static cudaError_t zpass_f64_nu(const ExpandLaunch& p) {
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double);
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double) + nl_smem<NU, double>(p);
+  const cudaError_t e = zpass_smem(k_expand_zpass<NU, double, double>, smem);
+  if (e != cudaSuccess) return e;
   k_expand_zpass<NU, double, double><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const double*>(p.coeff), static_cast<double*>(p.tables), static_cast<double*>(p.t2),
-      (double*)nullptr, p.scale);
+      (double*)nullptr, p.scale, p.nl);
   return cudaGetLastError();
 }
 

@@ -548,7 +548,7 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
       p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || p.t2_only) return e;
   const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
   auto zk = k_project_ff_zpass<NU>;
   e = cudaFuncSetAttribute(zk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem);

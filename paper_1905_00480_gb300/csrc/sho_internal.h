@@ -59,7 +59,20 @@ struct ProjectLaunch {
   void* t2 = nullptr;       // FP64-accurate form: workspace [A][cube][P][B] FP64 of per-plane y-pass sums
   sho_dtype coeff_dtype;
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
+  bool t2_only = false;     // FP64-accurate form: stop after the per-plane sums (the z-pass runs fused later)
   cudaStream_t stream;
+};
+
+// Inputs of the fused non-local action (Sec. 3.2 steps 1-3) taken by the expansion's z-pass kernel: the
+// projection coefficients c of each (atom, band) -- from the projection's per-plane y-pass sums t2p
+// ([A][cube][P][B], z-pass and h^3 applied here) or, when t2p is null, from c ([A][N][B]) -- are multiplied
+// by the atom's matrix, d = D c, in shared memory, and d feeds the expansion; neither c nor d goes to
+// global memory.  All arrays in the expansion's compute type.  D == nullptr: a plain expansion.
+struct NonlocalIn {
+  const void* D = nullptr;    // [A][N][N]
+  const void* t2p = nullptr;  // [A][cube][P][B] per-plane y-pass sums of the projection
+  const void* c = nullptr;    // [A][N][B] projection coefficients (when t2p is null)
+  double h3 = 1.0;            // projection weight applied with the projection's z-pass
 };
 
 struct ExpandLaunch {
@@ -81,6 +94,7 @@ struct ExpandLaunch {
                                   // point): the FP32 x table x-major [A][cube][NPX], then (tensor forms)
                                   // the B fragments of the x-pass; FP64-accurate form: float-pair tables
   double scale = 1.0;       // psi += scale * E c: applied to the z table of the z-pass
+  NonlocalIn nl;            // fused non-local action (nl.D set): the coefficients are D times a projection
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   cudaStream_t stream;
 };
@@ -186,6 +200,7 @@ struct PlaneLaunch {
   int* status;               // device status word: kStatusTimeout when a bounded wait expired
   long long wait_cycles = kDefaultWaitCycles;  // limit of every mbarrier wait
   int stop_rows = 0x7fffffff;  // fault injection: producers issue only this many rows per sweep
+  bool t2_only = false;        // stop after the per-plane sums t2p (the z-pass runs fused later)
   cudaStream_t stream;
 };
 bool plane_ok(const sho_grid* grid, const void* psi, sho_dtype psi_dt, int nbands, int numax, int cube,
@@ -230,8 +245,6 @@ bool usu_supported_nproj(int n);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
 cudaError_t launch_expand_zpass_f32_tiled(const ExpandLaunch& p);  // T2 as [A][C][B/32][32][tiled_pairs(P)]
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
-cudaError_t launch_dmatrix(int natoms, int nstates, int nbands, sho_dtype dt, const void* D, const void* c, void* d,
-                           cudaStream_t s);
 cudaError_t launch_project_ff(const ProjectLaunch& p);
 cudaError_t launch_expand_ff(const ExpandLaunch& p);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);

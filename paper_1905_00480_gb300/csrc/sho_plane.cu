@@ -622,6 +622,7 @@ cudaError_t plane_run(const PlaneLaunch& p) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (p.t2_only) return cudaSuccess;
   k_plane_zpass<NU><<<dim3(A, nbt), kWarp, 0, p.stream>>>(p.g, p.atoms, p.t2p, p.coeff);
   return cudaGetLastError();
 }

@@ -1,5 +1,11 @@
 """Non-local action hpsi += sum_a |k> D_a <k|psi> (Sec. 3.2 steps 1-3 with the SHO basis of Sec. 3.5)
-against the oracle: oracle projection, the matrix product as a library step, oracle expansion (GPU)."""
+against the oracle: oracle projection, the matrix product, oracle expansion (GPU).
+
+The library fuses the action: the projection stops at its per-plane sums (FP64-accurate form, plane sweep)
+or its coefficients (other paths), and the expansion's z-pass kernel finishes the projection, multiplies
+by D and expands with c and d in shared memory.  The cases cover every path into that kernel: FP64
+clusters and per-atom FP32 kernels (coefficient input), FF64 and plane sweep (per-plane-sum input, FP32
+and BF16 storage), numax 8-9 (shared-memory columns beyond 48 KB)."""
 import numpy as np
 import pytest
 
@@ -71,3 +77,46 @@ def test_nonlocal_identity_D_is_projector():
     D = torch.eye(N, dtype=torch.float64, device="cuda")[None].contiguous()
     api.apply_nonlocal(psi_d, out, D, X, [sigma], numax, cube, h, False, prec="ff64")
     assert rel_norm(out.cpu().numpy(), state) < 1e-11
+
+
+@pytest.mark.parametrize("prec,storage,numax,tol", [
+    ("split_fp16", "f32", 5, 1e-5), ("bf16", "f32", 5, 3e-2),              # plane sweep, tensor forms
+    ("tf32", "bf16", 5, 1e-2), ("fp32", "bf16", 7, 10 * TOL_FP32),         # plane sweep over BF16 rows
+    ("fp32", "f32", 8, 10 * TOL_FP32),                                     # per-atom kernels (numax 8)
+    ("ff64", "f64", 9, TOL_FP64), ("fp64", "f64", 9, TOL_FP64)])           # 220 states
+def test_nonlocal_paths(prec, storage, numax, tol):
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, pos, sig, psi, hpsi, D = _case(701 + numax, numax=numax, nbands=48, natoms=5)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[storage]
+    cdt = torch.float64 if prec in ("fp64", "ff64") else torch.float32
+    psi_d = torch.from_numpy(psi).cuda().to(tdt)
+    hpsi_d = torch.zeros_like(psi_d)
+    D_d = torch.from_numpy(D).cuda().to(cdt)
+    api.apply_nonlocal(psi_d, hpsi_d, D_d, pos, sig, numax, 32, h, True, prec=prec)
+    ref = _reference(grid, h, True, pos, sig, psi_d.double().cpu().numpy(), np.zeros(psi.shape),
+                     D_d.double().cpu().numpy(), numax, 32)
+    tol_store = 2.0 ** -8 if storage == "bf16" else 0.0    # the result is rounded to BF16 on store
+    assert rel_norm(hpsi_d.double().cpu().numpy(), ref) <= tol + tol_store
+
+
+@pytest.mark.parametrize("prec", ["ff64", "tf32"])
+def test_fused_action_matches_composed_calls(prec):
+    """The fused action equals projection, D c and expansion run as separate library calls (the same
+    arithmetic up to the order of the D product's sums)."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, pos, sig, psi, hpsi, D = _case(720)
+    cdt = torch.float64 if prec == "ff64" else torch.float32
+    psi_d = torch.from_numpy(psi).cuda().to(cdt)
+    D_d = torch.from_numpy(D).cuda().to(cdt)
+    fused = torch.zeros_like(psi_d)
+    api.apply_nonlocal(psi_d, fused, D_d, pos, sig, 5, 32, h, True, prec=prec)
+    c = api.project(psi_d, pos, sig, 5, 32, h, True, prec=prec)
+    d = torch.einsum("akl,alb->akb", D_d.double(), c.double()).to(cdt).contiguous()
+    composed = torch.zeros_like(psi_d)
+    api.add(composed, d, pos, sig, 5, 32, h, True, prec=prec)
+    tol = 1e-13 if prec == "ff64" else 1e-5
+    assert rel_norm(fused.double().cpu().numpy(), composed.double().cpu().numpy()) <= tol
