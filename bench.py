@@ -349,12 +349,12 @@ def run_ours(args, ws, rank, local):
     rng_md = np.random.default_rng([w.seed, rank, 17])
     moved = [pos + rng_md.normal(0.0, 0.02, size=pos.shape) for _ in range(10 + 2)]
     for i in range(2):
-        api.project(psi, moved[i], sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
+        api.project(psi, moved[i], sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=co[1], handle=handle,
                     stream=stream)
     torch.cuda.synchronize()
     e0.record(stream)
     for i in range(10):
-        api.project(psi, moved[2 + i], sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=coeff, handle=handle,
+        api.project(psi, moved[2 + i], sig, w.numax, w.cube, w.h, w.periodic, prec=prec, out=co[1], handle=handle,
                     stream=stream)
         api.add(hps[0], cin, moved[2 + i], sig, w.numax, w.cube, w.h, w.periodic, prec=prec, handle=handle,
                 stream=stream)

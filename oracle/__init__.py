@@ -73,8 +73,18 @@ def _load():
                                                  ctypes.c_int, ctypes.c_int, dp]
             lib.oracle_add_bloch.argtypes = [ip, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp,
                                              ctypes.c_int, ctypes.c_int, dp]
+            lib.oracle_project_r.argtypes = common + [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
+                                                      ctypes.c_int, ctypes.c_double, dp]
+            lib.oracle_add_r.argtypes = common + [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_double, dp]
+            lib.oracle_forces_r.argtypes = common + [dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_double, dp, dp]
+            lib.oracle_expand_points_r.argtypes = common + [ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
+                                                            ctypes.c_int, ctypes.c_double, dp, ctypes.c_int, i64p,
+                                                            dp]
             for f in (lib.oracle_project, lib.oracle_add, lib.oracle_forces, lib.oracle_expand_points,
-                      lib.oracle_project_bloch, lib.oracle_add_bloch):
+                      lib.oracle_project_bloch, lib.oracle_add_bloch, lib.oracle_project_r, lib.oracle_add_r,
+                      lib.oracle_forces_r, lib.oracle_expand_points_r):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -133,8 +143,9 @@ def dphi(n: int, u: float, sigma: float) -> float:
     return float(_load().oracle_dphi(int(n), float(u), float(sigma)))
 
 
-def project(grid, h, periodic, psi, pos, sigma, numax, cube):
-    """c[a][k][b] = h^3 sum over the atom's cube of Psi_k(u) psi[j][b]; psi is [Nz][Ny][Nx][B]."""
+def project(grid, h, periodic, psi, pos, sigma, numax, cube, rprj=0.0):
+    """c[a][k][b] = h^3 sum over the atom's cube of Psi_k(u) psi[j][b]; psi is [Nz][Ny][Nx][B].
+    rprj > 0: only cube points with (ux^2 + uy^2) + uz^2 <= rprj^2 (FP64, in that order) contribute."""
     n = [int(v) for v in grid]
     psi = _f64(psi)
     B = psi.shape[-1]
@@ -144,14 +155,14 @@ def project(grid, h, periodic, psi, pos, sigma, numax, cube):
     A = pos.shape[0]
     N = nstates(numax)
     c = np.zeros((A, N, B), dtype=np.float64)
-    rc = _load().oracle_project(_grid(n), float(h), int(bool(periodic)), _dp(psi), B, A, _dp(pos), _dp(sigma),
-                                int(numax), int(cube), _dp(c))
+    rc = _load().oracle_project_r(_grid(n), float(h), int(bool(periodic)), _dp(psi), B, A, _dp(pos), _dp(sigma),
+                                  int(numax), int(cube), float(rprj), _dp(c))
     _check(rc, "project")
     return c
 
 
-def add(grid, h, periodic, psi, pos, sigma, numax, cube, coeff):
-    """Returns psi + sum_a sum_k c[a][k][b] Psi_k (the input array is not modified)."""
+def add(grid, h, periodic, psi, pos, sigma, numax, cube, coeff, rprj=0.0):
+    """Returns psi + sum_a sum_k c[a][k][b] Psi_k (the input array is not modified); rprj as in project."""
     n = [int(v) for v in grid]
     out = np.array(psi, dtype=np.float64, copy=True, order="C")
     B = out.shape[-1]
@@ -160,14 +171,14 @@ def add(grid, h, periodic, psi, pos, sigma, numax, cube, coeff):
     sigma = _f64(sigma).reshape(-1)
     A = pos.shape[0]
     coeff = _f64(coeff, (A, nstates(numax), B))
-    rc = _load().oracle_add(_grid(n), float(h), int(bool(periodic)), _dp(out), B, A, _dp(pos), _dp(sigma),
-                            int(numax), int(cube), _dp(coeff))
+    rc = _load().oracle_add_r(_grid(n), float(h), int(bool(periodic)), _dp(out), B, A, _dp(pos), _dp(sigma),
+                              int(numax), int(cube), float(rprj), _dp(coeff))
     _check(rc, "add")
     return out
 
 
-def expand_points(grid, h, periodic, pos, sigma, numax, cube, coeff, points):
-    """Expansion evaluated at selected flat grid indices: returns [P][B]."""
+def expand_points(grid, h, periodic, pos, sigma, numax, cube, coeff, points, rprj=0.0):
+    """Expansion evaluated at selected flat grid indices: returns [P][B]; rprj as in project."""
     n = [int(v) for v in grid]
     pos = _f64(pos).reshape(-1, 3)
     sigma = _f64(sigma).reshape(-1)
@@ -177,15 +188,16 @@ def expand_points(grid, h, periodic, pos, sigma, numax, cube, coeff, points):
     assert coeff.shape == (A, nstates(numax), B)
     pts = np.ascontiguousarray(points, dtype=np.int64)
     out = np.zeros((pts.size, B), dtype=np.float64)
-    rc = _load().oracle_expand_points(_grid(n), float(h), int(bool(periodic)), B, A, _dp(pos), _dp(sigma),
-                                      int(numax), int(cube), _dp(coeff), int(pts.size),
-                                      pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+    rc = _load().oracle_expand_points_r(_grid(n), float(h), int(bool(periodic)), B, A, _dp(pos), _dp(sigma),
+                                        int(numax), int(cube), float(rprj), _dp(coeff), int(pts.size),
+                                        pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
     _check(rc, "expand_points")
     return out
 
 
-def forces(grid, h, periodic, psi, pos, sigma, numax, cube, dEdc):
-    """dE/dX[a][d] = sum_b sum_k dEdc[a][k][b] dc[a][k][b]/dX_{a,d} (cube origin held fixed)."""
+def forces(grid, h, periodic, psi, pos, sigma, numax, cube, dEdc, rprj=0.0):
+    """dE/dX[a][d] = sum_b sum_k dEdc[a][k][b] dc[a][k][b]/dX_{a,d} (cube origin held fixed; with rprj > 0
+    the set of points inside the sphere is held fixed as well)."""
     n = [int(v) for v in grid]
     psi = _f64(psi)
     B = psi.shape[-1]
@@ -194,8 +206,8 @@ def forces(grid, h, periodic, psi, pos, sigma, numax, cube, dEdc):
     A = pos.shape[0]
     dEdc = _f64(dEdc, (A, nstates(numax), B))
     out = np.zeros((A, 3), dtype=np.float64)
-    rc = _load().oracle_forces(_grid(n), float(h), int(bool(periodic)), _dp(psi), B, A, _dp(pos), _dp(sigma),
-                               int(numax), int(cube), _dp(dEdc), _dp(out))
+    rc = _load().oracle_forces_r(_grid(n), float(h), int(bool(periodic)), _dp(psi), B, A, _dp(pos), _dp(sigma),
+                                 int(numax), int(cube), float(rprj), _dp(dEdc), _dp(out))
     _check(rc, "forces")
     return out
 

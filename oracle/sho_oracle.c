@@ -34,6 +34,12 @@
  *
  * 1D polynomials are evaluated by the explicit power sum in long double -- deliberately not by the
  * three-term recursion -- and the 3D Gaussian by one exponential per point.
+ *
+ * Spherical support (the *_r entry points; the paper projects over spheres of radius R_prj around the
+ * atoms, Sec. 6): with rprj > 0 only cube points whose offset lies in the sphere contribute,
+ *     (ux*ux + uy*uy) + uz*uz <= rprj*rprj,
+ * each product and sum rounded to FP64 in that order (the library decides boundary points the same
+ * way); rprj <= 0 is the plain cube.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -140,8 +146,15 @@ typedef struct {
   double shift[3][256]; /* lattice translation (o + i - j) h of cube point i along each axis */
 } atom_samples;
 
+/* Is the offset u inside the sphere of radius rprj (always, for rprj <= 0)? */
+static int in_sphere(double ux, double uy, double uz, double rprj) {
+  if (!(rprj > 0.0)) return 1;
+  const double r2 = (ux * ux + uy * uy) + uz * uz;
+  return r2 <= rprj * rprj;
+}
+
 static void atom_samples_init(atom_samples* s, const int n[3], double h, int periodic, const double X[3],
-                              double sigma, int numax, int cube, int with_deriv) {
+                              double sigma, int numax, int cube, int with_deriv, double rprj) {
   s->cube = cube;
   s->numax = numax;
   long double sg = (long double)sigma;
@@ -175,7 +188,7 @@ static void atom_samples_init(atom_samples* s, const int n[3], double h, int per
         long double r2 = (long double)u[0][ix] * u[0][ix] + (long double)u[1][iy] * u[1][iy] +
                          (long double)u[2][iz] * u[2][iz];
         s->gauss[i] = (double)expl(-r2 / (2.0L * sg * sg));
-        if (j[0][ix] < 0 || j[1][iy] < 0 || j[2][iz] < 0)
+        if (j[0][ix] < 0 || j[1][iy] < 0 || j[2][iz] < 0 || !in_sphere(u[0][ix], u[1][iy], u[2][iz], rprj))
           s->gidx[i] = -1;
         else
           s->gidx[i] = ((int64_t)j[2][iz] * n[1] + j[1][iy]) * n[0] + j[0][ix];
@@ -227,8 +240,8 @@ static int check_args(const int n[3], double h, int natoms, int numax, int cube,
 
 /* Projection: coeff[a][k][b] = h^3 sum_i Psi_k(u_i) psi[j(i)][b].  Loop order atoms -> k -> cube
  * points -> bands.  Returns 0 or a negative error. */
-int oracle_project(const int n[3], double h, int periodic, const double* psi, int nbands, int natoms,
-                   const double* pos, const double* sigma, int numax, int cube, double* coeff) {
+int oracle_project_r(const int n[3], double h, int periodic, const double* psi, int nbands, int natoms,
+                     const double* pos, const double* sigma, int numax, int cube, double rprj, double* coeff) {
   int err = check_args(n, h, natoms, numax, cube, nbands);
   if (err) return err;
   int N = oracle_nstates(numax);
@@ -239,7 +252,7 @@ int oracle_project(const int n[3], double h, int periodic, const double* psi, in
 #pragma omp parallel for schedule(dynamic, 1)
   for (int a = 0; a < natoms; a++) {
     atom_samples s;
-    atom_samples_init(&s, n, h, periodic, pos + 3 * a, sigma[a], numax, cube, 0);
+    atom_samples_init(&s, n, h, periodic, pos + 3 * a, sigma[a], numax, cube, 0, rprj);
     double* P = (double*)malloc(sizeof(double) * c3);
     double* acc = (double*)malloc(sizeof(double) * (nbands > 0 ? nbands : 1));
     for (int k = 0; k < N; k++) {
@@ -265,8 +278,13 @@ int oracle_project(const int n[3], double h, int periodic, const double* psi, in
 /* Expansion: psi[j][b] += sum_a sum_{i: j(i)=j} sum_k coeff[a][k][b] Psi_k(u_i).  Atoms are added one
  * after another in ascending order; within an atom the cube points map to distinct grid points, so
  * they are processed in parallel without conflict. */
-int oracle_add(const int n[3], double h, int periodic, double* psi, int nbands, int natoms, const double* pos,
-               const double* sigma, int numax, int cube, const double* coeff) {
+int oracle_project(const int n[3], double h, int periodic, const double* psi, int nbands, int natoms,
+                   const double* pos, const double* sigma, int numax, int cube, double* coeff) {
+  return oracle_project_r(n, h, periodic, psi, nbands, natoms, pos, sigma, numax, cube, 0.0, coeff);
+}
+
+int oracle_add_r(const int n[3], double h, int periodic, double* psi, int nbands, int natoms, const double* pos,
+                 const double* sigma, int numax, int cube, double rprj, const double* coeff) {
   int err = check_args(n, h, natoms, numax, cube, nbands);
   if (err) return err;
   if (cube > n[0] || cube > n[1] || cube > n[2]) {
@@ -279,7 +297,7 @@ int oracle_add(const int n[3], double h, int periodic, double* psi, int nbands, 
   double* P = (double*)malloc(sizeof(double) * c3 * N);
   for (int a = 0; a < natoms; a++) {
     atom_samples s;
-    atom_samples_init(&s, n, h, periodic, pos + 3 * a, sigma[a], numax, cube, 0);
+    atom_samples_init(&s, n, h, periodic, pos + 3 * a, sigma[a], numax, cube, 0, rprj);
     for (int k = 0; k < N; k++) sample_projector(&s, nxyz[3 * k], nxyz[3 * k + 1], nxyz[3 * k + 2], P + k * c3);
     const double* ca = coeff + (int64_t)a * N * nbands;
 #pragma omp parallel for schedule(static)
@@ -302,9 +320,14 @@ int oracle_add(const int n[3], double h, int periodic, double* psi, int nbands, 
 /* Expansion evaluated only at selected grid points: out[p][b] = sum_a sum_k coeff[a][k][b] Psi_k(u)
  * for every atom whose cube holds grid point flat index pts[p] (atoms in ascending order).  Used to
  * check full-size expansions point by point. */
-int oracle_expand_points(const int n[3], double h, int periodic, int nbands, int natoms, const double* pos,
-                         const double* sigma, int numax, int cube, const double* coeff, int npts,
-                         const int64_t* pts, double* out) {
+int oracle_add(const int n[3], double h, int periodic, double* psi, int nbands, int natoms, const double* pos,
+               const double* sigma, int numax, int cube, const double* coeff) {
+  return oracle_add_r(n, h, periodic, psi, nbands, natoms, pos, sigma, numax, cube, 0.0, coeff);
+}
+
+int oracle_expand_points_r(const int n[3], double h, int periodic, int nbands, int natoms, const double* pos,
+                           const double* sigma, int numax, int cube, double rprj, const double* coeff, int npts,
+                           const int64_t* pts, double* out) {
   int err = check_args(n, h, natoms, numax, cube, nbands);
   if (err) return err;
   int N = oracle_nstates(numax);
@@ -336,7 +359,7 @@ int oracle_expand_points(const int n[3], double h, int periodic, int nbands, int
         }
         u[d] = (double)(o + i) * h - X[d];
       }
-      if (!inside) continue;
+      if (!inside || !in_sphere(u[0], u[1], u[2], rprj)) continue;
       long double sg = sigma[a];
       long double r2 = (long double)u[0] * u[0] + (long double)u[1] * u[1] + (long double)u[2] * u[2];
       long double g3 = expl(-r2 / (2.0L * sg * sg));
@@ -358,9 +381,9 @@ int oracle_expand_points(const int n[3], double h, int periodic, int nbands, int
 }
 
 /* Forces: dEdX[a][d] = sum_b sum_k dEdc[a][k][b] * h^3 sum_i dPsi_k/dX_d(u_i) psi[j(i)][b]. */
-int oracle_forces(const int n[3], double h, int periodic, const double* psi, int nbands, int natoms,
-                  const double* pos, const double* sigma, int numax, int cube, const double* dEdc,
-                  double* dEdX) {
+int oracle_forces_r(const int n[3], double h, int periodic, const double* psi, int nbands, int natoms,
+                    const double* pos, const double* sigma, int numax, int cube, double rprj, const double* dEdc,
+                    double* dEdX) {
   int err = check_args(n, h, natoms, numax, cube, nbands);
   if (err) return err;
   int N = oracle_nstates(numax);
@@ -371,7 +394,7 @@ int oracle_forces(const int n[3], double h, int periodic, const double* psi, int
 #pragma omp parallel for schedule(dynamic, 1)
   for (int a = 0; a < natoms; a++) {
     atom_samples s;
-    atom_samples_init(&s, n, h, periodic, pos + 3 * a, sigma[a], numax, cube, 1);
+    atom_samples_init(&s, n, h, periodic, pos + 3 * a, sigma[a], numax, cube, 1, rprj);
     double* P = (double*)malloc(sizeof(double) * c3);
     double* acc = (double*)malloc(sizeof(double) * (nbands > 0 ? nbands : 1));
     for (int d = 0; d < 3; d++) {
@@ -398,6 +421,19 @@ int oracle_forces(const int n[3], double h, int periodic, const double* psi, int
   return 0;
 }
 
+/* Forces for spherical support hold the set of included points fixed, as they hold the cube origin. */
+int oracle_forces(const int n[3], double h, int periodic, const double* psi, int nbands, int natoms,
+                  const double* pos, const double* sigma, int numax, int cube, const double* dEdc,
+                  double* dEdX) {
+  return oracle_forces_r(n, h, periodic, psi, nbands, natoms, pos, sigma, numax, cube, 0.0, dEdc, dEdX);
+}
+
+int oracle_expand_points(const int n[3], double h, int periodic, int nbands, int natoms, const double* pos,
+                         const double* sigma, int numax, int cube, const double* coeff, int npts,
+                         const int64_t* pts, double* out) {
+  return oracle_expand_points_r(n, h, periodic, nbands, natoms, pos, sigma, numax, cube, 0.0, coeff, npts, pts, out);
+}
+
 
 /* ---------------------------------------------------------------------------------------------
  * Bloch (complex) wave functions on a periodic grid.  psi and coeff hold complex numbers as (re, im)
@@ -420,7 +456,7 @@ int oracle_project_bloch(const int n[3], double h, const double kvec[3], const d
 #pragma omp parallel for schedule(dynamic, 1)
   for (int a = 0; a < natoms; a++) {
     atom_samples s;
-    atom_samples_init(&s, n, h, 1, pos + 3 * a, sigma[a], numax, cube, 0);
+    atom_samples_init(&s, n, h, 1, pos + 3 * a, sigma[a], numax, cube, 0, 0.0);
     double* P = (double*)malloc(sizeof(double) * c3);
     double* cph = (double*)malloc(sizeof(double) * c3);
     double* sph = (double*)malloc(sizeof(double) * c3);
@@ -470,7 +506,7 @@ int oracle_add_bloch(const int n[3], double h, const double kvec[3], double* psi
   double* P = (double*)malloc(sizeof(double) * c3 * N);
   for (int a = 0; a < natoms; a++) {
     atom_samples s;
-    atom_samples_init(&s, n, h, 1, pos + 3 * a, sigma[a], numax, cube, 0);
+    atom_samples_init(&s, n, h, 1, pos + 3 * a, sigma[a], numax, cube, 0, 0.0);
     for (int k = 0; k < N; k++) sample_projector(&s, nxyz[3 * k], nxyz[3 * k + 1], nxyz[3 * k + 2], P + k * c3);
     const double* ca = coeff + (int64_t)a * N * 2 * nbands;
 #pragma omp parallel for schedule(static)

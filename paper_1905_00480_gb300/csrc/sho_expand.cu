@@ -79,19 +79,41 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
       for (int k = 0; k < N; k++) cs[k * kWarp + lane] = (TC)0;
       const bool yrows = g.periodic || (at.o[1] < g.n[1] && at.o[1] + C > 0);
       if (bok && yrows) {
-        for (int iz = 0; iz < C; iz++) {
-          if (cube_index(at.o[2], iz, g.n[2], g.periodic) < 0) continue;
+        if constexpr (N <= 56) {
+          // accumulators in registers up to numax 5
+          TC acc[N];
 #pragma unroll
-          for (int ny = 0; ny < NP; ny++)
+          for (int k = 0; k < N; k++) acc[k] = (TC)0;
+          for (int iz = 0; iz < C; iz++) {
+            if (cube_index(at.o[2], iz, g.n[2], g.periodic) < 0) continue;
+            TC t2v[P];
 #pragma unroll
-            for (int nx = 0; nx + ny <= NU; nx++) {
-              const TC v = t2a[((size_t)iz * P + BS::pair(nx, ny)) * B];
+            for (int p = 0; p < P; p++) t2v[p] = t2a[((size_t)iz * P + p) * B];
 #pragma unroll
-              for (int nz = 0; nx + ny + nz <= NU; nz++) {
-                const int k = BS::state(nx, ny, nz);
-                cs[k * kWarp + lane] = fma(v, pz[nz * C + iz], cs[k * kWarp + lane]);
+            for (int ny = 0; ny < NP; ny++)
+#pragma unroll
+              for (int nx = 0; nx + ny <= NU; nx++)
+#pragma unroll
+                for (int nz = 0; nx + ny + nz <= NU; nz++)
+                  acc[BS::state(nx, ny, nz)] = fma(t2v[BS::pair(nx, ny)], pz[nz * C + iz], acc[BS::state(nx, ny, nz)]);
+          }
+#pragma unroll
+          for (int k = 0; k < N; k++) cs[k * kWarp + lane] = acc[k];
+        } else {
+          for (int iz = 0; iz < C; iz++) {
+            if (cube_index(at.o[2], iz, g.n[2], g.periodic) < 0) continue;
+#pragma unroll
+            for (int ny = 0; ny < NP; ny++)
+#pragma unroll
+              for (int nx = 0; nx + ny <= NU; nx++) {
+                const TC v = t2a[((size_t)iz * P + BS::pair(nx, ny)) * B];
+#pragma unroll
+                for (int nz = 0; nx + ny + nz <= NU; nz++) {
+                  const int k = BS::state(nx, ny, nz);
+                  cs[k * kWarp + lane] = fma(v, pz[nz * C + iz], cs[k * kWarp + lane]);
+                }
               }
-            }
+          }
         }
       }
       const TC h3 = (TC)nl.h3;
@@ -100,12 +122,22 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
       const TC* cg = static_cast<const TC*>(nl.c) + (size_t)a * N * B + (bok ? b : 0);
       for (int k = 0; k < N; k++) cs[k * kWarp + lane] = bok ? cg[(size_t)k * B] : (TC)0;
     }
-    // d = D c (step 2 of the action), states k' ascending
+    // d = D c (step 2 of the action), states k' ascending; eight output states at a time so that eight
+    // independent FMA chains are in flight
     const TC* Da = static_cast<const TC*>(nl.D) + (size_t)a * N * N;
-    for (int k = 0; k < N; k++) {
-      TC acc = (TC)0;
-      for (int kp = 0; kp < N; kp++) acc = fma(__ldg(Da + (size_t)k * N + kp), cs[kp * kWarp + lane], acc);
-      ds[k * kWarp + lane] = acc;
+    for (int k0 = 0; k0 < N; k0 += 8) {
+      TC acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) acc[j] = (TC)0;
+      for (int kp = 0; kp < N; kp++) {
+        const TC v = cs[kp * kWarp + lane];
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+          if (k0 + j < N) acc[j] = fma(__ldg(Da + (size_t)(k0 + j) * N + kp), v, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; j++)
+        if (k0 + j < N) ds[(k0 + j) * kWarp + lane] = acc[j];
     }
     ca = reinterpret_cast<const TCo*>(ds + lane);
     cstr = kWarp;

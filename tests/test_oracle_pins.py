@@ -34,8 +34,9 @@ def _enumerate(numax):
             for nx in range(numax + 1 - nz - ny)]
 
 
-def _brute_project(grid, h, periodic, psi, pos, sigma, numax, cube):
-    """Direct definition with scipy functions and explicit loops (tiny inputs only)."""
+def _brute_project(grid, h, periodic, psi, pos, sigma, numax, cube, rprj=0.0):
+    """Direct definition with scipy functions and explicit loops (tiny inputs only); rprj > 0 keeps only
+    the cube points inside the atom's sphere."""
     nx_, ny_, nz_ = grid
     states = _enumerate(numax)
     B = psi.shape[-1]
@@ -51,6 +52,8 @@ def _brute_project(grid, h, periodic, psi, pos, sigma, numax, cube):
                     elif not (0 <= j[0] < nx_ and 0 <= j[1] < ny_ and 0 <= j[2] < nz_):
                         continue
                     u = [(o[0] + ix) * h - X[0], (o[1] + iy) * h - X[1], (o[2] + iz) * h - X[2]]
+                    if rprj > 0 and not (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2] <= rprj * rprj:
+                        continue
                     for k, (mx, my, mz) in enumerate(states):
                         w = _phi_scipy(mx, u[0], s) * _phi_scipy(my, u[1], s) * _phi_scipy(mz, u[2], s)
                         out[a, k] += h ** 3 * w * psi[j[2], j[1], j[0]]
@@ -332,3 +335,89 @@ def test_forces_match_ladder_identity():
                     term = term - math.sqrt(m[d] / 2) * cp[a, big.index(tuple(dn))]
                 ref[a, d] += np.sum(g[a, k] * term) / sig[a]
     assert np.max(np.abs(f - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+# --------------------------------------------------------------------------- spherical support (Sec. 6)
+def test_sphere_brute_force_tiny():
+    """Projection over the points of the cube inside a sphere of radius R (the paper's projection spheres)
+    against the direct definition with scipy functions, periodic and clipped, R cutting through the cube."""
+    rng = np.random.default_rng(17)
+    grid, h, numax, cube = (10, 12, 11), 0.3, 2, 8
+    pos = np.array([[1.31, 1.72, 1.55], [0.2, 3.1, 2.9]])
+    sig = np.array([0.7, 0.9])
+    psi = rng.standard_normal((grid[2], grid[1], grid[0], 2))
+    for periodic in (True, False):
+        for R in (0.65, 0.9, 1.07):
+            got = oracle.project(grid, h, periodic, psi, pos, sig, numax, cube, rprj=R)
+            ref = _brute_project(grid, h, periodic, psi, pos, sig, numax, cube, rprj=R)
+            assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref)), (periodic, R)
+
+
+def test_sphere_enclosing_the_cube_is_the_cube():
+    rng = np.random.default_rng(18)
+    grid, h, numax, cube = (16, 16, 16), 0.25, 3, 12
+    pos = np.array([[2.1, 1.9, 2.3]])
+    psi = rng.standard_normal((16, 16, 16, 3))
+    c = rng.standard_normal((1, oracle.nstates(numax), 3))
+    R = cube * h  # longer than any offset inside the cube
+    assert np.array_equal(oracle.project(grid, h, True, psi, pos, [0.8], numax, cube),
+                          oracle.project(grid, h, True, psi, pos, [0.8], numax, cube, rprj=R))
+    assert np.array_equal(oracle.add(grid, h, True, psi, pos, [0.8], numax, cube, c),
+                          oracle.add(grid, h, True, psi, pos, [0.8], numax, cube, c, rprj=R))
+
+
+def test_sphere_equals_cube_of_masked_psi_and_adjoint():
+    """Masking the support equals zeroing psi outside the sphere (one atom), and E stays the h^3-adjoint
+    of P with the same support; expand_points agrees with add."""
+    rng = np.random.default_rng(19)
+    grid, h, numax, cube, R = (14, 14, 14), 0.25, 3, 12, 1.1
+    X = np.array([[1.63, 1.77, 1.52]])
+    sig = [0.75]
+    psi = rng.standard_normal((14, 14, 14, 2))
+    o = np.floor(X[0] / h).astype(int) - cube // 2 + 1
+    u = [(o[d] + np.arange(cube)) * h - X[0, d] for d in range(3)]
+    masked = np.zeros_like(psi)
+    for iz in range(cube):
+        for iy in range(cube):
+            for ix in range(cube):
+                if (u[0][ix] * u[0][ix] + u[1][iy] * u[1][iy]) + u[2][iz] * u[2][iz] <= R * R:
+                    j = ((o[2] + iz) % 14, (o[1] + iy) % 14, (o[0] + ix) % 14)
+                    masked[j] = psi[j]
+    a = oracle.project(grid, h, True, psi, X, sig, numax, cube, rprj=R)
+    b = oracle.project(grid, h, True, masked, X, sig, numax, cube)
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(b))
+    c = rng.standard_normal(a.shape)
+    e = oracle.add(grid, h, True, np.zeros_like(psi), X, sig, numax, cube, c, rprj=R)
+    lhs, rhs = float((a * c).sum()), h ** 3 * float((psi * e).sum())
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+    pts = np.array([0, 500, 1234, 2000, 2743])
+    ep = oracle.expand_points(grid, h, True, X, sig, numax, cube, c, pts, rprj=R)
+    assert np.max(np.abs(ep - e.reshape(-1, 2)[pts])) <= 1e-14 * max(1.0, np.max(np.abs(e)))
+
+
+def test_sphere_forces_match_finite_difference():
+    """With no cube point near the sphere's surface the support does not change under a small shift, and
+    the forces are the central differences of E = sum D c^2."""
+    rng = np.random.default_rng(20)
+    grid, h, numax, cube = (16, 16, 16), 0.25, 3, 12
+    X = np.array([[2.03, 1.96, 2.11]])
+    sig = [0.7]
+    o = np.floor(X[0] / h).astype(int) - cube // 2 + 1
+    u = [(o[d] + np.arange(cube)) * h - X[0, d] for d in range(3)]
+    r = np.sqrt(u[0][None, None, :] ** 2 + u[1][None, :, None] ** 2 + u[2][:, None, None] ** 2).ravel()
+    R = 0.5 * (np.sort(r)[200] + np.sort(r)[201])           # halfway between two point shells
+    assert np.min(np.abs(r - R)) > 1e-3
+    psi = rng.standard_normal((16, 16, 16, 2))
+    Dm = rng.uniform(-1, 1, size=(1, oracle.nstates(numax)))
+    c = oracle.project(grid, h, True, psi, X, sig, numax, cube, rprj=R)
+    f = oracle.forces(grid, h, True, psi, X, sig, numax, cube, 2 * Dm[:, :, None] * c, rprj=R)
+    step = 1e-5
+    for d in range(3):
+        e = []
+        for sgn in (1, -1):
+            Xs = X.copy()
+            Xs[0, d] += sgn * step
+            cs = oracle.project(grid, h, True, psi, Xs, sig, numax, cube, rprj=R)
+            e.append(float((Dm[:, :, None] * cs * cs).sum()))
+        fd = (e[0] - e[1]) / (2 * step)
+        assert abs(f[0, d] - fd) <= 1e-7 * max(1.0, np.abs(f).max()), (d, f[0, d], fd)
