@@ -121,6 +121,18 @@ const char* sho_last_cuda_error(const sho_handle* handle);
  * (allowed: the method still computes the defined sums, only their sampling is coarse). */
 int sho_set_strict(sho_handle* handle, int strict);
 
+/* Spherical projector support (the paper projects over spheres of radius R_prj around each atom, Sec. 6):
+ * with rprj > 0 the handle's projections, expansions, forces, non-local actions and stored-projector
+ * builds use only the cube points whose offset u from the atom satisfies
+ *     (ux*ux + uy*uy) + uz*uz <= rprj*rprj      (each product and sum rounded to FP64 in that order)
+ * -- the cube stays the outer bound, so a sphere wider than the cube changes nothing.  Forces hold the
+ * set of included points fixed (as they hold the cube origin).  rprj = 0 restores the whole cube
+ * (default); negative or non-finite values return SHO_ERR_ARG.  Implemented by SHO_P_FP64 and
+ * SHO_P_FF64 (and sho_usu_build, which stores zeros outside the sphere); the other precision forms and
+ * the Bloch entry points return SHO_ERR_DTYPE while a radius is set.  The points inside a sphere form
+ * one contiguous run of each cube row, and the kernels skip the rest. */
+int sho_set_support_radius(sho_handle* handle, double rprj);
+
 /* Block until the handle's enqueued work is complete; return the first device-side error since the
  * previous sho_sync (SHO_ERR_TIMEOUT when a kernel's bounded wait on its own data pipeline expired --
  * its results are then incomplete; SHO_ERR_DEVICE when an SHO_P_FF64 input lay outside its range) or a

@@ -57,6 +57,7 @@ SIGNATURES = {
     "sho_create": (_I, [ctypes.POINTER(_VP), _I]),
     "sho_destroy": (_I, [_VP]),
     "sho_set_strict": (_I, [_VP, _I]),
+    "sho_set_support_radius": (_I, [_VP, ctypes.c_double]),
     "sho_sync": (_I, [_VP]),
     "sho_last_cuda_error": (ctypes.c_char_p, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),

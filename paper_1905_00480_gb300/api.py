@@ -46,6 +46,10 @@ class Handle:
     def sync(self):
         N.check(N.lib().sho_sync(self._h), "sho_sync")
 
+    def set_support_radius(self, rprj: float):
+        """sho_set_support_radius: spherical projector support of radius rprj (0 = the whole cube)."""
+        N.check(N.lib().sho_set_support_radius(self._h, float(rprj)), "sho_set_support_radius")
+
     def close(self):
         if self._h:
             N.lib().sho_destroy(self._h)

@@ -24,6 +24,7 @@ struct sho_handle {
   int* dstatus = nullptr;      // device status word (kStatusTimeout | kStatusRange bits) set by kernels
   long long wait_cycles = sho::kDefaultWaitCycles;  // fault injection: limit of the bounded device waits
   int stop_rows = 0x7fffffff;                       // fault injection: rows a plane-sweep producer issues
+  double rprj = 0.0;                                // spherical support radius (0: the whole cube)
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
   struct RadialDev {
     void* mem = nullptr;
@@ -266,14 +267,20 @@ int check_tc(sho_prec prec, int numax_run, int cube) {
   return SHO_OK;
 }
 
-GridDev make_grid(const sho_grid* grid, int cube, int nbands) {
+GridDev make_grid(const sho_grid* grid, int cube, int nbands, double rprj = 0.0) {
   GridDev g;
   for (int d = 0; d < 3; d++) g.n[d] = grid->n[d];
   g.periodic = grid->periodic ? 1 : 0;
   g.h = grid->h;
   g.cube = cube;
   g.nbands = nbands;
+  g.r2max = rprj > 0.0 ? rprj * rprj : 0.0;
   return g;
+}
+
+// Spherical support is implemented by the FP64 and FP64-accurate kernels (and the stored-projector build).
+int check_support(const sho_handle* h, sho_prec prec) {
+  return (h->rprj > 0.0 && !is_f64_form(prec)) ? SHO_ERR_DTYPE : SHO_OK;
 }
 
 #define SHO_TRY(x)                \
@@ -682,6 +689,7 @@ static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, i
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, kTcMaxNumax));
   if (!grid->periodic || !kvec) return SHO_ERR_ARG;
+  if (h->rprj > 0.0) return SHO_ERR_DTYPE;  // spherical support: FP64 / FP64-accurate real forms only
   for (int d = 0; d < 3; d++)
     if (!std::isfinite(kvec[d])) return SHO_ERR_ARG;
   if (op == 1 && grid->n[0] > kBlochMaxNx) return SHO_ERR_ARG;
@@ -774,6 +782,7 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
   SHO_TRY(check_tc(prec, numax, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  SHO_TRY(check_support(h, prec));
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!psi || !coeff) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
@@ -797,7 +806,7 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   const char* gm = static_cast<const char*>(h->geo[0].mem);
   ProjectLaunch L;
   L.order = reinterpret_cast<const int*>(gm + h->geo[0].off[1]);
-  L.g = make_grid(grid, cube, nbands);
+  L.g = make_grid(grid, cube, nbands, h->rprj);
   L.psi = psi;
   L.psi_dtype = psi_dtype;
   L.atoms = reinterpret_cast<const AtomDev*>(gm + h->geo[0].off[0]);
@@ -841,6 +850,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
   SHO_TRY(check_tc(prec, numax, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  SHO_TRY(check_support(h, prec));
   if (nbands == 0) return SHO_OK;
   if (!psi || (natoms > 0 && !coeff)) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
@@ -884,7 +894,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   char* ws = static_cast<char*>(h->ws);
   const char* gm = static_cast<const char*>(h->geo[1].mem);
   ExpandLaunch L;
-  L.g = make_grid(grid, cube, nbands);
+  L.g = make_grid(grid, cube, nbands, h->rprj);
   L.coeff = coeff;
   L.coeff_dtype = coeff_dtype;
   L.psi = psi;
@@ -937,6 +947,7 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   SHO_TRY(check_dtypes(prec, psi_dtype, coeff_dtype));
   SHO_TRY(check_tc(prec, numax + 1, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  SHO_TRY(check_support(h, prec));
   if (natoms == 0) return SHO_OK;
   if (!dEdX) return SHO_ERR_ARG;
   if (nbands > 0 && (!psi || !dEdc)) return SHO_ERR_ARG;
@@ -963,7 +974,7 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   char* ws = static_cast<char*>(h->ws);
   ProjectLaunch P;
   P.order = reinterpret_cast<const int*>(ws + o_order);
-  P.g = make_grid(grid, cube, nbands);
+  P.g = make_grid(grid, cube, nbands, h->rprj);
   P.psi = psi;
   P.psi_dtype = psi_dtype;
   P.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
@@ -1005,6 +1016,7 @@ int sho_apply_nonlocal(sho_handle* h, const sho_grid* grid, const void* psi, sho
   SHO_TRY(check_dtypes(prec, psi_dtype, cdt));
   SHO_TRY(check_tc(prec, numax, cube));
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
+  SHO_TRY(check_support(h, prec));
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!psi || !hpsi || !D || psi == hpsi) return SHO_ERR_ARG;
   DeviceGuard guard(h->device);
@@ -1064,7 +1076,7 @@ int sho_usu_build(sho_handle* h, const sho_grid* grid, int natoms, const double*
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
   UsuLaunch L = {};
-  L.g = make_grid(grid, cube, 0);
+  L.g = make_grid(grid, cube, 0, h->rprj);
   L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
   L.natoms = natoms;
   L.numax = numax;
@@ -1147,6 +1159,12 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const void* coeff, int nban
   L.stream = s;
   if (launch_usu(2, L) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
+}
+
+int sho_set_support_radius(sho_handle* h, double rprj) {
+  if (!h || !std::isfinite(rprj) || rprj < 0.0) return SHO_ERR_ARG;
+  h->rprj = rprj;
+  return SHO_OK;
 }
 
 // ------------------------------------------------------------------ fault injection (include/sho_fault.h)

@@ -78,6 +78,34 @@ __device__ __forceinline__ double cube_offset(int o, int i, double h, double X) 
   return __dsub_rn(__dmul_rn((double)(o + i), h), X);
 }
 
+// Spherical support (projection spheres of radius R, Sec. 6): is the cube point with offsets (ux, uy, uz)
+// inside, (ux^2 + uy^2) + uz^2 <= R^2, each product and sum rounded to FP64 in that order?
+__device__ __forceinline__ bool sphere_inside(double ux, double uy, double uz, double r2max) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)) <= r2max;
+}
+
+// Bit i set: cube point i of cube row (iy, iz) of atom `at` is in its support (all C bits without a
+// sphere).  The points inside form one contiguous run of the row.  Warp-collective (full warp): lane l
+// decides points l and l + 32.
+__device__ __forceinline__ unsigned long long row_support(const GridDev& g, const AtomDev& at, int iy, int iz,
+                                                          int lane) {
+  const int C = g.cube;
+  const unsigned long long all = C >= 64 ? ~0ull : ((1ull << C) - 1ull);
+  if (!(g.r2max > 0.0)) return all;
+  const double uy = cube_offset(at.o[1], iy, g.h, at.X[1]);
+  const double uz = cube_offset(at.o[2], iz, g.h, at.X[2]);
+  const bool in0 = lane < C && sphere_inside(cube_offset(at.o[0], lane, g.h, at.X[0]), uy, uz, g.r2max);
+  const bool in1 = lane + 32 < C && sphere_inside(cube_offset(at.o[0], lane + 32, g.h, at.X[0]), uy, uz, g.r2max);
+  return (unsigned long long)__ballot_sync(0xffffffffu, in0) |
+         ((unsigned long long)__ballot_sync(0xffffffffu, in1) << 32);
+}
+
+// First and one-past-last set bit of a support mask (lo = hi = 0 when empty).
+__device__ __forceinline__ void support_run(unsigned long long m, int& lo, int& hi) {
+  lo = m ? __ffsll((long long)m) - 1 : 0;
+  hi = m ? 64 - __clzll((long long)m) : 0;
+}
+
 // Normalised 1D oscillator functions phi_0 .. phi_nmax at offset u (FP64):
 //   phi_0 = (sigma sqrt(pi))^(-1/2) exp(-xi^2/2),  xi = u / sigma
 //   phi_1 = sqrt(2) xi phi_0

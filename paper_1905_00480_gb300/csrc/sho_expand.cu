@@ -251,6 +251,8 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
       if (iz < 0) iz += g.n[2];
     }
     if (iy < 0 || iy >= C) continue;
+    const unsigned long long sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
+    if (sup == 0) continue;
     const TC* tx = tables + (size_t)a * 2 * NP * C;
     const TC* ty = tx + (size_t)NP * C;
     // y-pass (a6, middle pass)
@@ -271,11 +273,12 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
     // with the accumulator value, so eight independent FMA chains are in flight and every point
     // costs exactly numax+1 FMAs.
     for (int ix0 = 0; ix0 < C; ix0 += 8) {
+      if (((sup >> ix0) & 0xffull) == 0) continue;
       int jx[8];
       TC s[8];
 #pragma unroll
       for (int u = 0; u < 8; u++) {
-        jx[u] = cube_index(at.o[0], ix0 + u, Nx, g.periodic);
+        jx[u] = ((sup >> (ix0 + u)) & 1ull) ? cube_index(at.o[0], ix0 + u, Nx, g.periodic) : -1;
         s[u] = jx[u] >= 0 ? acc[jx[u] * kWarp + lane] : (TC)0;
       }
 #pragma unroll

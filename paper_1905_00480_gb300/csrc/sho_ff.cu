@@ -151,14 +151,17 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     __syncwarp();
     issue_next();  // row r + kFfStages - 1
     ff_commit();
-    if (zidx[iz] >= 0 && yidx[iy] >= 0) {
+    // spherical support of the row: the points inside are the contiguous run [xlo, xhi) of the cube row
+    int xlo = 0, xhi = 0;
+    if (zidx[iz] >= 0 && yidx[iy] >= 0) support_run(row_support(g, at, iy, iz, lane), xlo, xhi);
+    if (xhi > xlo) {
       const double* st = reinterpret_cast<const double*>(ring + (size_t)(r % kFfStages) * C * kFfRowBytes);
       // x-pass (a3) as float-float dot products
       float S[NP], E[NP];
 #pragma unroll
       for (int n = 0; n < NP; n++) S[n] = E[n] = 0.0f;
 #pragma unroll 4
-      for (int ix = 0; ix < C; ix++) {
+      for (int ix = xlo; ix < xhi; ix++) {
         const double pd = st[ix * 32 + lane];
         range_bad |= ff_out_of_range(pd);
         const ff pv = ff_from_double(pd);
@@ -466,7 +469,11 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     const float2* tys = reinterpret_cast<const float2*>(src + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
     int iy = r.y + warp;  // cube row of this warp's grid row
     if (g.periodic && iy >= Ny) iy -= Ny;
-    if (yok && iy >= 0 && iy < C) {
+    const bool rowin = yok && iy >= 0 && iy < C;
+    // spherical support of the row in cube x coordinates, [slo, shi) (the whole row without a sphere)
+    int slo = 0, shi = C;
+    if (g.r2max > 0.0) support_run(row_support(g, atoms[r.x], rowin ? iy : 0, r.w, lane), slo, shi);
+    if (rowin && shi > slo) {
       // y-pass as float-float dot steps
       float ys[NP], yc[NP];
 #pragma unroll
@@ -498,8 +505,9 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
         r1a = r1b = 0;
       }
       for (int run = 0; run < 2; run++) {
-        const int xa = run ? max(r1a, r0b) : r0a, xb = run ? r1b : r0b;
         const int shift = run ? dx - Nx : dx;
+        // tile points of this run whose cube index ix = x + shift lies in the row's support
+        const int xa = max(run ? max(r1a, r0b) : r0a, slo - shift), xb = min(run ? r1b : r0b, shi - shift);
 #pragma unroll 2
         for (int x = xa; x < xb; x++) {
           const int ix = x + shift;

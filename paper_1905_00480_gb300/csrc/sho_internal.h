@@ -33,6 +33,7 @@ struct GridDev {
   double h;
   int cube;
   int nbands;
+  double r2max = 0.0;  // spherical support: R^2 of the projection sphere; 0 = the whole cube
 };
 
 enum class Real { F64, F32 };

@@ -88,17 +88,20 @@ __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restri
     for (int iy = 0; iy < C; iy++) {
       const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
       if (jy < 0) continue;
+      const unsigned long long sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
+      if (sup == 0) continue;
       const TP* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b;
       // x-pass (a3)
       TC t1[NP];
 #pragma unroll
       for (int n = 0; n < NP; n++) t1[n] = (TC)0;
       for (int ix = 0; ix < C; ix += 8) {
+        if (((sup >> ix) & 0xffull) == 0) continue;
         TC v[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const long long o = xoff[ix + u];
-          v[u] = (o >= 0 && bok) ? to_real(row[o], (TC)0) : (TC)0;
+          v[u] = (o >= 0 && bok && ((sup >> (ix + u)) & 1ull)) ? to_real(row[o], (TC)0) : (TC)0;
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {

@@ -30,6 +30,10 @@ __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __r
   phi_column(cube_offset(at.o[1], iy, g.h, at.X[1]), at.sigma, NU, fy, 1);
   phi_column(cube_offset(at.o[2], iz, g.h, at.X[2]), at.sigma, NU, fz, 1);
   T* out = proj + ((long long)a * c3 + i) * nproj;
+  // spherical support: stored values outside the atom's projection sphere are zero
+  const bool in = !(g.r2max > 0.0) ||
+                  sphere_inside(cube_offset(at.o[0], ix, g.h, at.X[0]), cube_offset(at.o[1], iy, g.h, at.X[1]),
+                                cube_offset(at.o[2], iz, g.h, at.X[2]), g.r2max);
   int k = 0;
 #pragma unroll
   for (int nz = 0; nz < NP; nz++)
@@ -37,7 +41,7 @@ __global__ void __launch_bounds__(128) k_usu_build(GridDev g, const AtomDev* __r
     for (int ny = 0; ny + nz <= NU; ny++)
 #pragma unroll
       for (int nx = 0; nx + ny + nz <= NU; nx++) {
-        if (k < nproj) out[k] = (T)(fx[nx] * fy[ny] * fz[nz]);
+        if (k < nproj) out[k] = in ? (T)(fx[nx] * fy[ny] * fz[nz]) : (T)0;
         k++;
       }
 }
