@@ -133,6 +133,16 @@ int sho_set_strict(sho_handle* handle, int strict);
  * one contiguous run of each cube row, and the kernels skip the rest. */
 int sho_set_support_radius(sho_handle* handle, double rprj);
 
+/* Engine of the x-pass of the handle's TF32 / BF16 expansions (FP32 or BF16 psi, numax <= 7, bands in
+ * whole 16-byte rows, no spherical support): SHO_KERNEL_AUTO (default) and SHO_KERNEL_TCGEN05 take the
+ * fifth-generation tensor cores -- tiles of 8 rows x 32 points x 128 bands whose update stays in tensor
+ * memory across the atoms, one M=128 N=32 MMA per row and atom; SHO_KERNEL_MMA_SYNC takes the warp-level
+ * MMA kernel (tiles of 8 rows x 32 points x 32 bands, accumulators in registers).  Both add the same
+ * products in the same atom order; the FP32 sums of the tensor cores may round differently.  Other
+ * calls ignore the setting.  SHO_ERR_ARG for an unknown value. */
+typedef enum { SHO_KERNEL_AUTO = 0, SHO_KERNEL_MMA_SYNC = 1, SHO_KERNEL_TCGEN05 = 2 } sho_kernel;
+int sho_set_expand_kernel(sho_handle* handle, int kernel);
+
 /* Block until the handle's enqueued work is complete; return the first device-side error since the
  * previous sho_sync (SHO_ERR_TIMEOUT when a kernel's bounded wait on its own data pipeline expired --
  * its results are then incomplete; SHO_ERR_DEVICE when an SHO_P_FF64 input lay outside its range) or a

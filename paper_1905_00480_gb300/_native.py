@@ -48,7 +48,7 @@ _IP = ctypes.POINTER(ctypes.c_int)
 _I = ctypes.c_int
 _GP = ctypes.POINTER(sho_grid)
 
-# name -> (restype, argtypes); every symbol declared in include/sho.h and include/sho_fault.h
+# name -> (restype, argtypes); every symbol declared in include/*.h
 SIGNATURES = {
     "sho_version": (_I, []),
     "sho_nstates": (_I, [_I]),
@@ -58,6 +58,10 @@ SIGNATURES = {
     "sho_destroy": (_I, [_VP]),
     "sho_set_strict": (_I, [_VP, _I]),
     "sho_set_support_radius": (_I, [_VP, ctypes.c_double]),
+    "sho_set_expand_kernel": (_I, [_VP, _I]),
+    # include/sho_selftest.h
+    "sho_selftest_umma": (_I, [_I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_float)]),
     "sho_sync": (_I, [_VP]),
     "sho_last_cuda_error": (ctypes.c_char_p, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),

@@ -46,6 +46,11 @@ class Handle:
     def sync(self):
         N.check(N.lib().sho_sync(self._h), "sho_sync")
 
+    def set_expand_kernel(self, kernel: str):
+        """sho_set_expand_kernel: "auto", "mma_sync" or "tcgen05" x-pass of the TF32 / BF16 expansions."""
+        N.check(N.lib().sho_set_expand_kernel(self._h, {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]),
+                "sho_set_expand_kernel")
+
     def set_support_radius(self, rprj: float):
         """sho_set_support_radius: spherical projector support of radius rprj (0 = the whole cube)."""
         N.check(N.lib().sho_set_support_radius(self._h, float(rprj)), "sho_set_support_radius")

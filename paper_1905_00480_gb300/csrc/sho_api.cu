@@ -25,6 +25,7 @@ struct sho_handle {
   long long wait_cycles = sho::kDefaultWaitCycles;  // fault injection: limit of the bounded device waits
   int stop_rows = 0x7fffffff;                       // fault injection: rows a plane-sweep producer issues
   double rprj = 0.0;                                // spherical support radius (0: the whole cube)
+  int expand_kernel = SHO_KERNEL_AUTO;              // x-pass engine of the FP32-class expansion
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
   struct RadialDev {
     void* mem = nullptr;
@@ -910,6 +911,8 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   L.tables_xmajor = ws + o_txm;
   L.scale = alpha;
   if (nl) L.nl = *nl;
+  L.kernel = h->expand_kernel;
+  L.wait_cycles = h->wait_cycles;
   L.status = h->dstatus;
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_expand(L)
@@ -1107,7 +1110,7 @@ int sho_usu_project(sho_handle* h, const sho_grid* grid, const void* psi, int nb
   SHO_TRY(ensure_workspace(h, cv.off));
   SHO_TRY(upload(h, o_atoms, at.data(), at.size() * sizeof(AtomDev), s));
   UsuLaunch L = {};
-  L.g = make_grid(grid, cube, nbands);
+  L.g = make_grid(grid, cube, nbands, h->rprj);
   L.atoms = reinterpret_cast<const AtomDev*>(static_cast<char*>(h->ws) + o_atoms);
   L.natoms = natoms;
   L.nproj = nproj;
@@ -1146,7 +1149,7 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const void* coeff, int nban
   SHO_TRY(upload(h, o_list, list.data(), list.size() * sizeof(int), s));
   char* ws = static_cast<char*>(h->ws);
   UsuLaunch L = {};
-  L.g = make_grid(grid, cube, nbands);
+  L.g = make_grid(grid, cube, nbands, h->rprj);
   L.atoms = reinterpret_cast<const AtomDev*>(ws + o_atoms);
   L.natoms = natoms;
   L.nproj = nproj;
@@ -1159,6 +1162,12 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const void* coeff, int nban
   L.stream = s;
   if (launch_usu(2, L) != cudaSuccess) return SHO_ERR_CUDA;
   return end_call(h, s);
+}
+
+int sho_set_expand_kernel(sho_handle* h, int kernel) {
+  if (!h || kernel < SHO_KERNEL_AUTO || kernel > SHO_KERNEL_TCGEN05) return SHO_ERR_ARG;
+  h->expand_kernel = kernel;
+  return SHO_OK;
 }
 
 int sho_set_support_radius(sho_handle* h, double rprj) {

@@ -751,6 +751,9 @@ bool fp32_stream_ok(const void* psi, sho_dtype dt, int nbands) {
 
 cudaError_t launch_project_fp32(const ProjectLaunch& p, sho_prec prec) { return fp32_dispatch(0, p.numax, prec, &p, nullptr); }
 
-cudaError_t launch_expand_fp32(const ExpandLaunch& p, sho_prec prec) { return fp32_dispatch(1, p.numax, prec, nullptr, &p); }
+cudaError_t launch_expand_fp32(const ExpandLaunch& p, sho_prec prec) {
+  if (p.kernel != 1 && umma_expand_ok(p, prec)) return launch_expand_umma(p, prec);
+  return fp32_dispatch(1, p.numax, prec, nullptr, &p);
+}
 
 }  // namespace sho

@@ -8,6 +8,7 @@
 
 #include "../../include/sho.h"
 #include "../../include/sho_fault.h"
+#include "../../include/sho_selftest.h"
 
 namespace sho {
 
@@ -96,6 +97,8 @@ struct ExpandLaunch {
                                   // the B fragments of the x-pass; FP64-accurate form: float-pair tables
   double scale = 1.0;       // psi += scale * E c: applied to the z table of the z-pass
   NonlocalIn nl;            // fused non-local action (nl.D set): the coefficients are D times a projection
+  int kernel = 0;           // FP32-class x-pass engine: 0 automatic, 1 warp-level mma.sync, 2 tcgen05
+  long long wait_cycles = kDefaultWaitCycles;  // limit of the bounded waits (tcgen05 kernel)
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   cudaStream_t stream;
 };
@@ -254,6 +257,10 @@ cudaError_t launch_expand_tc(const ExpandLaunch& p, sho_prec prec);
 // 16-byte aligned (fp32_stream_ok); the CUDA-core / tensor-core row kernels serve the other cases.
 bool fp32_stream_ok(const void* psi, sho_dtype dt, int nbands);
 cudaError_t launch_project_fp32(const ProjectLaunch& p, sho_prec prec);
+// Block-gather expansion with the x-pass on tcgen05 MMAs and the tile in tensor memory (TF32 and BF16
+// forms, numax <= 7, FP32 or BF16 psi, no spherical support; sho_umma_expand.cu).
+bool umma_expand_ok(const ExpandLaunch& p, sho_prec prec);
+cudaError_t launch_expand_umma(const ExpandLaunch& p, sho_prec prec);
 cudaError_t launch_expand_fp32(const ExpandLaunch& p, sho_prec prec);
 
 // Host helpers shared with the serving loop and the allocation-free entry point (sho_api.cu).

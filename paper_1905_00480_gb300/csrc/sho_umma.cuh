@@ -1,0 +1,114 @@
+// sho_umma.cuh -- fifth-generation tensor-core primitives (tcgen05 MMA, tensor memory) for sm_103a, as
+// inline PTX.  Only what the SHO kernels use:
+//   * operands in shared memory without swizzle, K-major ("interleaved" core matrices of 8 rows x 16 bytes,
+//     128 contiguous bytes each);
+//   * cta_group::1, kind::tf32 and kind::f16 (BF16 operands), FP32 accumulators in tensor memory;
+//   * completion through tcgen05.commit to an mbarrier, read back with tcgen05.ld (32x32b shape).
+// Encodings follow the PTX ISA description of the shared-memory matrix descriptor and of the instruction
+// descriptor for .kind::tf32 / .kind::f16.
+#pragma once
+
+#include <cstdint>
+
+namespace sho {
+
+// ------------------------------------------------------------------------------ descriptors
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension byte offset (distance of
+// core matrices adjacent in K), stride-dimension byte offset (distance of core matrices adjacent in M or
+// N), all in 16-byte units; bits 46-47 hold the descriptor version (1), bits 61-63 the layout (0: none).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t smem_addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3fffu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3fffu) << 16;
+  d |= (uint64_t)((sbo_bytes >> 4) & 0x3fffu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A / B type (bits 7-9 / 10-12: 1 = BF16 for
+// kind::f16, 2 = TF32 for kind::tf32), both operands K-major (bits 15, 16 = 0), N / 8 in bits 17-22,
+// M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc(uint32_t ab_type, int M, int N) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+constexpr uint32_t kUmmaBF16 = 1;
+constexpr uint32_t kUmmaTF32 = 2;
+
+// Byte offset of element (row r, k) in a K-major, unswizzled operand of `kbytes` bytes per row: core
+// matrices (8 rows x 16 bytes) with the K-neighbours adjacent (LBO = 128) and row blocks of 8 at
+// SBO = 8 * kbytes.
+__host__ __device__ constexpr uint32_t umma_kmajor_offset(int r, int kbyte, int kbytes) {
+  return (uint32_t)((r >> 3) * (8 * kbytes) + (kbyte >> 4) * 128 + (r & 7) * 16 + (kbyte & 15));
+}
+
+// ------------------------------------------------------------------------------ tensor memory
+// Allocate `ncols` (a power of two, >= 32) tensor-memory columns for this CTA; warp-collective (one full
+// warp).  The base address is written to shared memory at `dst_smem`.
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+      : "memory");
+}
+
+// Make the mbarrier at `bar` track completion of this thread's earlier tcgen05 operations (one arrival).
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc05_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc05_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Generic-proxy writes to shared memory made visible to the tensor core (async proxy).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 32 consecutive 32-bit columns of this thread's tensor-memory lane (warp w reads lanes 32 (w % 4) ..).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive columns of this thread's lane set to zero.
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(taddr),
+      "r"(0u)
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+}  // namespace sho

@@ -1,0 +1,467 @@
+// sho_umma_expand.cu -- FP32-class expansion with the x-pass on the fifth-generation tensor cores
+// (tcgen05.mma, accumulators in tensor memory), for the TF32 and BF16 forms.
+//
+//   psi[z][y][x][b] += sum_a sum_nx T1_a[y][b][nx] phi_nx(x - X_a),   T1 from the y-pass of the z-pass
+//   result T2 (Sec. 3.2 step 3, passes in the order z, y, x; eq. TuckerTensor, Sec. 3.4)
+//
+// A CTA owns a tile of one z plane: 8 grid rows x 32 x points x 128 bands.  The tile's update lives in
+// tensor memory for the whole atom loop: 8 accumulators (one per row) of 128 lanes (bands) x 32
+// columns (x points), 256 columns.  For each atom whose cube meets the tile (ascending order):
+//   * its band-tiled T2 slice (128 bands x pairs), y table and x table are staged in shared memory by
+//     cp.async, one atom ahead;
+//   * 256 threads run the y-pass (thread = band, four rows each) and write T1 of every row as an MMA A
+//     operand, [128 bands][8 states] TF32 (or [128][16] BF16, states 8..15 zero), K-major without
+//     swizzle; the atom's x functions on the tile's 32 points become the B operand [32][8];
+//   * one thread issues one M=128, N=32 MMA per row, D[row] += A[row] B^T, and commits it to the
+//     operand slot's mbarrier; the next atom's y-pass writes the other slot meanwhile.
+// At the end each warp reads its quarter of the lanes (tcgen05.ld) and adds the tile to psi in global
+// memory once.  Atoms are added in ascending order: deterministic.  Every wait is bounded; on expiry the
+// kernel records kStatusTimeout, waits (bounded) for its own MMAs and copies, frees tensor memory and
+// returns.
+#include "sho_tc.cuh"
+#include "sho_umma.cuh"
+
+namespace sho {
+
+constexpr int kUmRows = 8;       // grid rows per tile
+constexpr int kUmX = 32;         // x points per tile (the MMA N)
+constexpr int kUmBands = 128;    // bands per tile (the MMA M)
+constexpr int kUmThreads = 256;
+constexpr int kUmCols = kUmRows * kUmX;  // tensor-memory columns: 8 accumulators of 32 columns
+constexpr int kUmKBytes = 32;    // bytes per operand row: 8 TF32 or 16 BF16 values
+
+__device__ __forceinline__ uint32_t um_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void um_cp16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void um_commit_cp() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void um_wait_cp0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void um_mbar_init(uint32_t bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool um_mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Wait for the phase of `parity` of a commit barrier; false after `limit` SM clock cycles.
+__device__ __forceinline__ bool um_mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+  if (um_mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!um_mbar_try(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+template <int NU>
+struct UmSmem {
+  static constexpr int NP = NU + 1, P = Basis<NU>::P, PP = tiled_pairs(P), NPX = (NP + 3) & ~3;
+  static constexpr size_t kA = (size_t)kUmRows * kUmBands * kUmKBytes;  // one A slot: 32 KB
+  static constexpr size_t kB = (size_t)kUmX * kUmKBytes;                // one B slot: 1 KB
+  // staging buffer: T2 [128][PP] floats, y table [NP][C], x table [C][NPX]
+  __host__ __device__ static size_t stage_floats(int cube) {
+    return (size_t)kUmBands * PP + (size_t)NP * cube + (size_t)cube * NPX;
+  }
+  __host__ __device__ static size_t off_b() { return 2 * kA; }
+  __host__ __device__ static size_t off_stage() { return 2 * kA + 2 * kB; }
+  __host__ __device__ static size_t off_bar(int cube) { return off_stage() + 2 * stage_floats(cube) * 4; }
+  static size_t bytes(int cube, int max_plane) {
+    return off_bar(cube) + 128 + (size_t)(max_plane + 1) * sizeof(int4);
+  }
+};
+
+template <int NU, typename TP, bool BF>
+__global__ void __launch_bounds__(kUmThreads, 2)
+    k_expand_umma(GridDev g, const AtomDev* __restrict__ atoms, const int* __restrict__ plane_ptr,
+                  const int* __restrict__ plane_atoms, const float* __restrict__ tables,
+                  const float* __restrict__ txm, const float* __restrict__ t2, TP* __restrict__ psi,
+                  int* __restrict__ status, long long wait_cycles) {
+  using BS = Basis<NU>;
+  using SM = UmSmem<NU>;
+  constexpr int NP = SM::NP, P = SM::P, PP = SM::PP, NPX = SM::NPX;
+  static_assert(NP <= 8, "one MMA covers at most 8 states");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int C = g.cube, Nx = g.n[0], Ny = g.n[1], Nz = g.n[2], B = g.nbands;
+  const uint32_t sbase = um_smem(smem_raw);
+  const uint32_t sA = sbase, sB = sbase + (uint32_t)SM::off_b();
+  float* stage = reinterpret_cast<float*>(smem_raw + SM::off_stage());
+  const size_t stf = SM::stage_floats(C);
+  unsigned char* barp = smem_raw + SM::off_bar(C);
+  const uint32_t bar0 = um_smem(barp);                      // commit barriers of operand slots 0 and 1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 16);
+  int* s_misc = reinterpret_cast<int*>(barp + 32);          // [0] list length, [1..8] warp counts
+  int4* slist = reinterpret_cast<int4*>(barp + 128);        // after s_misc[0..8] (bytes 32..67)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  const int nseg = (Nx + kUmX - 1) / kUmX, nyb = (Ny + kUmRows - 1) / kUmRows;
+  int bid = blockIdx.x;
+  const int seg = bid % nseg;
+  bid /= nseg;
+  const int yb = bid % nyb;
+  const int z = bid / nyb;
+  const int xs = seg * kUmX;
+  const int nbt32 = (B + 31) / 32;                 // 32-band tiles of the band-tiled T2
+  const int bt0 = blockIdx.y * 4;                  // first of this CTA's four
+  const int ntile = min(4, nbt32 - bt0);
+  const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+
+  // atoms of the plane whose cube meets the tile, ascending (offsets as in the block gather)
+  if (tid == 0) s_misc[0] = 0;
+  __syncthreads();
+  for (int base = q0; base < q1; base += kUmThreads) {
+    const int q = base + tid;
+    int4 r = make_int4(-1, 0, 0, 0);
+    bool m = false;
+    if (q < q1) {
+      const int a = plane_atoms[q];
+      const AtomDev at = atoms[a];
+      int dy = yb * kUmRows - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
+      if (g.periodic) {
+        dy %= Ny;
+        if (dy < 0) dy += Ny;
+        dx %= Nx;
+        if (dx < 0) dx += Nx;
+        dz %= Nz;
+        if (dz < 0) dz += Nz;
+        m = (dy < C || dy + kUmRows > Ny) && (dx < C || dx + kUmX > Nx);
+      } else {
+        m = dy < C && dy + kUmRows > 0 && dx < C && dx + kUmX > 0;
+      }
+      r = make_int4(a, dy, dx, dz);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) s_misc[1 + warp] = __popc(bal);
+    __syncthreads();
+    int off = s_misc[0];
+    for (int w = 0; w < warp; w++) off += s_misc[1 + w];
+    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = r;
+    __syncthreads();
+    if (tid == 0)
+      for (int w = 0; w < kUmThreads / 32; w++) s_misc[0] += s_misc[1 + w];
+    __syncthreads();
+  }
+  const int nlist = s_misc[0];
+  if (nlist == 0) return;  // no cube meets the tile: psi is unchanged
+
+  // tensor memory for the 8 row accumulators, zeroed; commit barriers; the BF16 operands' zero halves
+  if (warp == 0) tmem_alloc(um_smem(tmem_slot), kUmCols);
+  if (tid == 0) {
+    um_mbar_init(bar0);
+    um_mbar_init(bar0 + 8);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if constexpr (BF) {
+    // states 8..15 of every A and B row stay zero: the second 16 bytes of each row
+    for (int i = tid; i < 2 * kUmRows * kUmBands; i += kUmThreads)
+      *reinterpret_cast<uint4*>(smem_raw + (size_t)(i / (kUmRows * kUmBands)) * SM::kA +
+                                umma_kmajor_offset(i % (kUmRows * kUmBands), 16, kUmKBytes)) = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 2 * kUmX; i += kUmThreads)
+      *reinterpret_cast<uint4*>(smem_raw + SM::off_b() + (size_t)(i / kUmX) * SM::kB +
+                                umma_kmajor_offset(i % kUmX, 16, kUmKBytes)) = make_uint4(0, 0, 0, 0);
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int quarter = warp & 3;                    // tensor-memory lanes 32 quarter .. of this warp
+  const uint32_t tlane = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll
+  for (int c = 0; c < 4; c++) tmem_zero32(tlane + (uint32_t)((warp >> 2) * 128 + 32 * c));
+
+  // stage atom li into staging buffer sb
+  auto stage_atom = [&](int li, int sb) {
+    const int4 r = slist[li];
+    const int a = r.x, iz = r.w;
+    float* dst = stage + (size_t)sb * stf;
+    const float* src = t2 + (((size_t)a * C + iz) * nbt32 + bt0) * 32 * PP;
+    for (int q = tid; q < ntile * 32 * PP / 4; q += kUmThreads) um_cp16(um_smem(dst + 4 * q), src + 4 * q);
+    const float* sy = tables + (size_t)a * 2 * NP * C + (size_t)NP * C;   // y table [NP][C]
+    for (int q = tid; q < NP * C / 4; q += kUmThreads) um_cp16(um_smem(dst + kUmBands * PP + 4 * q), sy + 4 * q);
+    const float* sx = txm + (size_t)a * C * NPX;                          // x table [C][NPX]
+    for (int q = tid; q < C * NPX / 4; q += kUmThreads)
+      um_cp16(um_smem(dst + kUmBands * PP + NP * C + 4 * q), sx + 4 * q);
+  };
+
+  const int bl = tid & 127, rh = tid >> 7;         // this thread's band and row half (rows 4 rh .. 4 rh + 3)
+  const bool bvalid = bt0 * 32 + bl < B && bl < ntile * 32;
+  constexpr uint32_t idesc = umma_idesc(BF ? kUmmaBF16 : kUmmaTF32, kUmBands, kUmX);
+  bool ok = true;
+  int issued = 0;  // atoms whose MMAs have been issued and committed (the same count in every thread)
+
+  stage_atom(0, 0);
+  um_commit_cp();
+  for (int li = 0; li < nlist; li++) {
+    const int slot = li & 1;
+    um_wait_cp0();
+    __syncthreads();  // atom li staged; every thread is past atom li - 1 (its staging buffer is free)
+    if (li + 1 < nlist) stage_atom(li + 1, slot ^ 1);
+    um_commit_cp();
+    // operand slot `slot` was last read by the MMAs of atom li - 2
+    if (li >= 2 && !um_mbar_wait(bar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1), wait_cycles)) ok = false;
+    if (!__syncthreads_and(ok)) break;
+    const int4 r = slist[li];
+    const float* st = stage + (size_t)slot * stf;
+    const float* tys = st + kUmBands * PP;
+    const float* txs = tys + NP * C;
+    // y-pass for four rows of this band, written as A rows (K-major, 32 bytes per band)
+    float t2r[P];
+    {
+      const float4* row4 = reinterpret_cast<const float4*>(st + (size_t)bl * PP);
+#pragma unroll
+      for (int p4 = 0; p4 < (P + 3) / 4; p4++) {
+        const float4 v = bvalid ? row4[p4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * p4 + 0 < P) t2r[4 * p4 + 0] = v.x;
+        if (4 * p4 + 1 < P) t2r[4 * p4 + 1] = v.y;
+        if (4 * p4 + 2 < P) t2r[4 * p4 + 2] = v.z;
+        if (4 * p4 + 3 < P) t2r[4 * p4 + 3] = v.w;
+      }
+    }
+    unsigned char* arow = smem_raw + (size_t)slot * SM::kA;
+#pragma unroll
+    for (int rr = 0; rr < 4; rr++) {
+      const int row = 4 * rh + rr;
+      int iy = r.y + row;
+      if (g.periodic && iy >= Ny) iy -= Ny;
+      const bool yin = iy >= 0 && iy < C && yb * kUmRows + row < Ny;
+      float t1[8];
+#pragma unroll
+      for (int n = 0; n < 8; n++) t1[n] = 0.0f;
+      if (yin) {
+#pragma unroll
+        for (int ny = 0; ny < NP; ny++) {
+          const float w = tys[ny * C + iy];
+#pragma unroll
+          for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fmaf(t2r[BS::pair(nx, ny)], w, t1[nx]);
+        }
+      }
+      unsigned char* dst = arow + (size_t)row * kUmBands * kUmKBytes + umma_kmajor_offset(bl, 0, kUmKBytes);
+      if constexpr (BF) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(pack_bf16(t1[0], t1[1]), pack_bf16(t1[2], t1[3]),
+                                                    pack_bf16(t1[4], t1[5]), pack_bf16(t1[6], t1[7]));
+      } else {
+        *reinterpret_cast<uint4*>(dst) =
+            make_uint4(tf32_bits(t1[0]), tf32_bits(t1[1]), tf32_bits(t1[2]), tf32_bits(t1[3]));
+        *reinterpret_cast<uint4*>(dst + 128) =   // K bytes 16..31: the next core matrix along K
+            make_uint4(tf32_bits(t1[4]), tf32_bits(t1[5]), tf32_bits(t1[6]), tf32_bits(t1[7]));
+      }
+    }
+    // B: the atom's x functions on the tile's points, [32 x][8 states], zero outside the cube
+    {
+      const int x = tid >> 3, n = tid & 7;
+      int ix = r.z + x;
+      if (g.periodic && ix >= Nx) ix -= Nx;
+      const float v = (ix >= 0 && ix < C && n < NP && xs + x < Nx) ? txs[ix * NPX + n] : 0.0f;
+      unsigned char* bs = smem_raw + SM::off_b() + (size_t)slot * SM::kB;
+      if constexpr (BF) {
+        *reinterpret_cast<__nv_bfloat16*>(bs + umma_kmajor_offset(x, 2 * n, kUmKBytes)) = __float2bfloat16_rn(v);
+      } else {
+        *reinterpret_cast<uint32_t*>(bs + umma_kmajor_offset(x, 4 * n, kUmKBytes)) = tf32_bits(v);
+      }
+    }
+    fence_async_smem();  // the operands written above become visible to the tensor core
+    tc05_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc05_fence_after();
+      const uint64_t bdesc = umma_desc(sB + (uint32_t)(slot * SM::kB), 128, 8 * kUmKBytes);
+#pragma unroll
+      for (int row = 0; row < kUmRows; row++) {
+        const uint64_t adesc =
+            umma_desc(sA + (uint32_t)(slot * SM::kA + row * kUmBands * kUmKBytes), 128, 8 * kUmKBytes);
+        if constexpr (BF)
+          umma_f16(tmem + (uint32_t)(row * kUmX), adesc, bdesc, idesc, true);
+        else
+          umma_tf32(tmem + (uint32_t)(row * kUmX), adesc, bdesc, idesc, true);
+      }
+      umma_commit(bar0 + 8 * slot);
+    }
+    issued = li + 1;
+  }
+  um_wait_cp0();
+  // the last commit covers every MMA issued before it
+  const int last = issued - 1;
+  bool done = ok && last >= 0 && um_mbar_wait(bar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), wait_cycles);
+  if (!done) {
+    if (tid == 0) atomicOr(status, kStatusTimeout);
+    // the MMAs issued so far still complete; give them the default limit before tensor memory is freed
+    if (last >= 0) (void)um_mbar_wait(bar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), kDefaultWaitCycles);
+  }
+  tc05_fence_after();
+  if (done) {
+    // warp w: lanes 32 (w % 4) .. (bands), rows 4 (w / 4) .. 4 (w / 4) + 3
+    const int b = bt0 * 32 + 32 * quarter + lane;
+    const bool bok = b < B && 32 * quarter < ntile * 32;
+#pragma unroll 1
+    for (int rr = 0; rr < 4; rr++) {
+      const int row = 4 * (warp >> 2) + rr;
+      const int y = yb * kUmRows + row;
+      float v[32];
+      tmem_ld32(tlane + (uint32_t)(row * kUmX), v);
+      if (y < Ny && bok) {
+        TP* rp = psi + ((size_t)z * Ny + y) * (size_t)Nx * B + b;
+        const int xend = min(kUmX, Nx - xs);
+        float old[32];
+#pragma unroll
+        for (int x = 0; x < 32; x++) old[x] = x < xend ? to_real(rp[(size_t)(xs + x) * B], 0.0f) : 0.0f;
+#pragma unroll
+        for (int x = 0; x < 32; x++)
+          if (x < xend) rp[(size_t)(xs + x) * B] = store_cast(old[x] + v[x], (TP*)nullptr);
+      }
+    }
+  }
+  tc05_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kUmCols);
+}
+
+// One tcgen05 MMA, M = 128, N = 32, of host operands (test of the operand layouts and descriptors).
+template <bool BF>
+__global__ void __launch_bounds__(128) k_umma_selftest(const float* __restrict__ A, const float* __restrict__ Bm,
+                                                       float* __restrict__ D, int* __restrict__ status) {
+  __shared__ __align__(1024) unsigned char sm[kUmBands * kUmKBytes + kUmX * kUmKBytes];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ uint32_t tslot;
+  constexpr int K = BF ? 16 : 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < kUmBands * K; i += 128) {
+    const int r = i / K, k = i % K;
+    if constexpr (BF)
+      *reinterpret_cast<__nv_bfloat16*>(sm + umma_kmajor_offset(r, 2 * k, kUmKBytes)) = __float2bfloat16_rn(A[i]);
+    else
+      *reinterpret_cast<uint32_t*>(sm + umma_kmajor_offset(r, 4 * k, kUmKBytes)) = tf32_bits(A[i]);
+  }
+  for (int i = tid; i < kUmX * K; i += 128) {
+    const int r = i / K, k = i % K;
+    unsigned char* bs = sm + kUmBands * kUmKBytes;
+    if constexpr (BF)
+      *reinterpret_cast<__nv_bfloat16*>(bs + umma_kmajor_offset(r, 2 * k, kUmKBytes)) = __float2bfloat16_rn(Bm[i]);
+    else
+      *reinterpret_cast<uint32_t*>(bs + umma_kmajor_offset(r, 4 * k, kUmKBytes)) = tf32_bits(Bm[i]);
+  }
+  if (warp == 0) tmem_alloc(um_smem(&tslot), 32);
+  if (tid == 0) {
+    um_mbar_init(um_smem(&bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  fence_async_smem();
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = umma_idesc(BF ? kUmmaBF16 : kUmmaTF32, kUmBands, kUmX);
+    const uint64_t adesc = umma_desc(um_smem(sm), 128, 8 * kUmKBytes);
+    const uint64_t bdesc = umma_desc(um_smem(sm + kUmBands * kUmKBytes), 128, 8 * kUmKBytes);
+    if constexpr (BF)
+      umma_f16(tmem, adesc, bdesc, idesc, false);
+    else
+      umma_tf32(tmem, adesc, bdesc, idesc, false);
+    umma_commit(um_smem(&bar));
+  }
+  const bool done = um_mbar_wait(um_smem(&bar), 0, 2000000000ll);
+  if (!done && tid == 0) atomicOr(status, kStatusTimeout);
+  if (!done) (void)um_mbar_wait(um_smem(&bar), 0, kDefaultWaitCycles);
+  tc05_fence_after();
+  float v[32];
+  tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16), v);
+#pragma unroll
+  for (int x = 0; x < 32; x++) D[(32 * warp + lane) * kUmX + x] = done ? v[x] : 0.0f;
+  tc05_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 32);
+}
+
+// ------------------------------------------------------------------------------------ launchers
+template <int NU, typename TP, bool BF>
+static cudaError_t umma_run(const ExpandLaunch& p) {
+  const size_t smem = UmSmem<NU>::bytes(p.g.cube, p.max_plane);
+  if (smem > 227 * 1024) return cudaErrorNotSupported;
+  auto kern = k_expand_umma<NU, TP, BF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int nseg = (p.g.n[0] + kUmX - 1) / kUmX, nyb = (p.g.n[1] + kUmRows - 1) / kUmRows;
+  const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
+  kern<<<dim3(nblk, (p.g.nbands + kUmBands - 1) / kUmBands), kUmThreads, smem, p.stream>>>(
+      p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const float*>(p.tables),
+      static_cast<const float*>(p.tables_xmajor), static_cast<const float*>(p.t2), static_cast<TP*>(p.psi), p.status,
+      p.wait_cycles);
+  return cudaGetLastError();
+}
+
+template <int NU>
+static cudaError_t umma_nu(const ExpandLaunch& p, sho_prec prec) {
+  if constexpr (NU > 7) {
+    return cudaErrorNotSupported;
+  } else {
+    cudaError_t e = launch_expand_zpass_f32_tiled(p);
+    if (e != cudaSuccess) return e;
+    const bool bf = prec == SHO_P_BF16;
+    if (p.psi_dtype == SHO_F32) return bf ? umma_run<NU, float, true>(p) : umma_run<NU, float, false>(p);
+    return bf ? umma_run<NU, __nv_bfloat16, true>(p) : umma_run<NU, __nv_bfloat16, false>(p);
+  }
+}
+
+bool umma_expand_ok(const ExpandLaunch& p, sho_prec prec) {
+  if (prec != SHO_P_TF32 && prec != SHO_P_BF16) return false;
+  if (p.numax > 7 || (p.psi_dtype != SHO_F32 && p.psi_dtype != SHO_BF16)) return false;
+  if (p.g.r2max > 0.0) return false;
+  return UmSmem<7>::bytes(p.g.cube, p.max_plane) <= 227 * 1024;
+}
+
+cudaError_t launch_expand_umma(const ExpandLaunch& p, sho_prec prec) {
+  switch (p.numax) {
+    case 0: return umma_nu<0>(p, prec);
+    case 1: return umma_nu<1>(p, prec);
+    case 2: return umma_nu<2>(p, prec);
+    case 3: return umma_nu<3>(p, prec);
+    case 4: return umma_nu<4>(p, prec);
+    case 5: return umma_nu<5>(p, prec);
+    case 6: return umma_nu<6>(p, prec);
+    case 7: return umma_nu<7>(p, prec);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace sho
+
+using namespace sho;
+
+extern "C" int sho_selftest_umma(int bf16, const float* A, const float* Bm, float* D) {
+  if (!A || !Bm || !D) return SHO_ERR_ARG;
+  const int K = bf16 ? 16 : 8;
+  float *dA = nullptr, *dB = nullptr, *dD = nullptr;
+  int* dst = nullptr;
+  int st = SHO_OK;
+  if (cudaMalloc(&dA, sizeof(float) * kUmBands * K) != cudaSuccess ||
+      cudaMalloc(&dB, sizeof(float) * kUmX * K) != cudaSuccess ||
+      cudaMalloc(&dD, sizeof(float) * kUmBands * kUmX) != cudaSuccess || cudaMalloc(&dst, sizeof(int)) != cudaSuccess) {
+    st = SHO_ERR_OOM;
+  } else if (cudaMemcpy(dA, A, sizeof(float) * kUmBands * K, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(dB, Bm, sizeof(float) * kUmX * K, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemset(dst, 0, sizeof(int)) != cudaSuccess) {
+    st = SHO_ERR_CUDA;
+  } else {
+    if (bf16)
+      k_umma_selftest<true><<<1, 128>>>(dA, dB, dD, dst);
+    else
+      k_umma_selftest<false><<<1, 128>>>(dA, dB, dD, dst);
+    int flag = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(D, dD, sizeof(float) * kUmBands * kUmX, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&flag, dst, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = SHO_ERR_CUDA;
+    else if (flag)
+      st = SHO_ERR_TIMEOUT;
+  }
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dD);
+  cudaFree(dst);
+  cudaGetLastError();
+  return st;
+}

@@ -98,8 +98,12 @@ __global__ void __launch_bounds__(kWarp) k_usu_project(GridDev g, const T* __res
       const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
       if (jy < 0) continue;
       const T* row = psi + ((long long)jz * g.n[1] + jy) * g.n[0] * B + b;
-      // cube points of this row inside the grid: all when periodic, one contiguous run otherwise
-      const int ix0 = g.periodic ? 0 : max(0, -at.o[0]), ix1 = g.periodic ? C : min(C, g.n[0] - at.o[0]);
+      // cube points of this row inside the grid (all when periodic, one contiguous run otherwise) and
+      // inside the projection sphere (a contiguous run too; the stored values outside it are zero)
+      int slo = 0, shi = C;
+      if (g.r2max > 0.0) support_run(row_support(g, at, iy, iz, lane), slo, shi);
+      const int ix0 = max(slo, g.periodic ? 0 : max(0, -at.o[0]));
+      const int ix1 = min(shi, g.periodic ? C : min(C, g.n[0] - at.o[0]));
 #pragma unroll 4
       for (int ix = ix0; ix < ix1; ix++) {
         int jx = oxm + ix;  // periodic: oxm in [0, Nx) and ix < C <= Nx, so one wrap at most
@@ -188,7 +192,9 @@ __global__ void __launch_bounds__(kWarp) k_usu_add(GridDev g, const AtomDev* __r
 #pragma unroll
       for (int j = 0; j < BPL; j++) cr[k][j] = j < valid ? ca[(long long)k * B + j] : (T)0;
     const T* pa = proj + ((long long)a * c3 + ((long long)iz * C + iy) * C) * N;
-    const int ix0 = g.periodic ? 0 : max(0, -at.o[0]), ix1 = g.periodic ? C : min(C, Nx - at.o[0]);
+    int slo = 0, shi = C;  // projection-sphere run of the row (stored values outside it are zero)
+    if (g.r2max > 0.0) support_run(row_support(g, at, iy, iz, lane), slo, shi);
+    const int ix0 = max(slo, g.periodic ? 0 : max(0, -at.o[0])), ix1 = min(shi, g.periodic ? C : min(C, Nx - at.o[0]));
     const int oxm = g.periodic ? ((at.o[0] % Nx) + Nx) % Nx : at.o[0];
 #pragma unroll 4
     for (int ix = ix0; ix < ix1; ix++) {
