@@ -439,8 +439,9 @@ def run_ours(args, ws, rank, local):
             result["roofline_fp64"] = result["same_gpu_baselines"]["fp64_dfma"]["roofline"]
         if not args.no_forces:
             result["forces"] = forces_bench(api, handle, stream)
+        serve_sample = None
         if not args.no_serving:
-            result["serving"] = serving_bench(api)
+            result["serving"], serve_sample = serving_bench(api)
             st = result["serving"]["loads"].get("0.8") or next(iter(result["serving"]["loads"].values()))
             result["p50_ms"], result["p99_ms"] = st["p50_ms"], st["p99_ms"]
         prec_samples = None
@@ -453,6 +454,8 @@ def run_ours(args, ws, rank, local):
                 w, pos, sig, psi, cin, coeff, hpsi_ref=None, api=api, handle=handle, prec=prec)
             if prec_samples is not None:
                 oracle_precision_errors(result["precision_forms"], prec_samples)
+            if serve_sample is not None:
+                oracle_serving_errors(result["serving"], serve_sample)
     return result
 
 
@@ -732,46 +735,50 @@ def oracle_precision_errors(prec_out, samples):
                                    "norm-wise over the sampled points (expansion into zero psi of the storage type)")
 
 
-def serving_bench(api, nsys=12, warm=200, measured=1000, loads=(0.5, 0.8, 0.95), slots=4, prec="fp32"):
+def serving_bench(api, nsys=12, warm=200, measured=1000, loads=(0.5, 0.8, 0.95), slots=4, sweep=(8, 16),
+                  prec="fp32", nsample=20):
     """Poisson stream of project / expand requests (50/50) over heterogeneous device-resident systems
     (grid 48^3..192^3, 8..1024 atoms, 16..512 bands, numax 3/5/7/9, FP32 psi).  Capacity = completed
     requests per second of a saturating burst; each offered load rho submits `measured` requests at
     rate rho * capacity after `warm` warm-up requests.  Latency = submit -> completion as recorded by the
-    server; GB/s = algorithmic psi + coefficient bytes of the completed requests / busy wall time."""
+    server, per request; slowdown = latency / the same request's latency alone; GB/s = algorithmic psi +
+    coefficient bytes of the completed requests / busy wall time.  The slot count is swept at rho = 0.8.
+    A seeded sample of `nsample` served requests (2 % of the measured stream) keeps its inputs and results
+    (16 bands) for the CPU-baseline leg to check against the FP64 oracle."""
     import torch
     from paper_1905_00480_gb300.serve import Server
     specs = workloads.serving_systems(nsys)
-    srv = Server(torch.cuda.current_device(), budget_bytes=96 << 30, slots=slots)
-    ids = []
+    geo = []
     for sp in specs:
         rng = np.random.default_rng(sp.seed)
         L = sp.grid * sp.h
-        pos, sig = workloads.random_atoms(rng, sp.natoms, (L, L, L), True, min_sep=1.0)
-        g = torch.Generator(device="cuda")
-        g.manual_seed(sp.seed)
-        psi = torch.randn((sp.grid, sp.grid, sp.grid, sp.nbands), generator=g, device="cuda", dtype=torch.float32)
-        ids.append(srv.register(psi, pos, sig, sp.numax, sp.cube, sp.h, sp.periodic))
-        del psi
-    torch.cuda.empty_cache()
+        geo.append(workloads.random_atoms(rng, sp.natoms, (L, L, L), True, min_sep=1.0))
+
+    def start(nslots):
+        srv = Server(torch.cuda.current_device(), budget_bytes=96 << 30, slots=nslots)
+        ids = []
+        for sp, (pos, sig) in zip(specs, geo):
+            g = torch.Generator(device="cuda")
+            g.manual_seed(sp.seed)
+            psi = torch.randn((sp.grid, sp.grid, sp.grid, sp.nbands), generator=g, device="cuda", dtype=torch.float32)
+            ids.append(srv.register(psi, pos, sig, sp.numax, sp.cube, sp.h, sp.periodic))
+            del psi
+        torch.cuda.empty_cache()
+        return srv, ids
+
     rng = np.random.default_rng(SERVE_SEED)
 
     def draw(n):
-        return [(ids[int(rng.integers(len(ids)))], "project" if rng.random() < 0.5 else "expand") for _ in range(n)]
+        return [(int(rng.integers(len(specs))), "project" if rng.random() < 0.5 else "expand") for _ in range(n)]
 
-    def run_burst(reqs):
+    def run_burst(srv, ids, reqs):
         t0 = time.perf_counter()
-        ts = [srv.submit(i, op, prec) for i, op in reqs]
+        ts = [srv.submit(ids[i], op, prec) for i, op in reqs]
         for t in ts:
             srv.wait(t, 600000)
         return time.perf_counter() - t0
 
-    run_burst(draw(warm))
-    nburst = 400
-    cap = nburst / run_burst(draw(nburst))
-    out = {"systems": [dict(grid=sp.grid, atoms=sp.natoms, bands=sp.nbands, numax=sp.numax) for sp in specs],
-           "slots": slots, "precision": prec, "capacity_rps": round(cap, 2), "warmup_requests": warm,
-           "measured_requests": measured, "loads": {}}
-    for rho in loads:
+    def run_load(srv, ids, cap, rho):
         srv.reset_stats()
         reqs = draw(measured)
         arrivals = workloads.poisson_arrivals(rng, measured, rho * cap)
@@ -781,18 +788,106 @@ def serving_bench(api, nsys=12, warm=200, measured=1000, loads=(0.5, 0.8, 0.95),
             dt = t0 + ta - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            ts.append(srv.submit(i, op, prec))
-        for t in ts:
-            srv.wait(t, 600000)
-        st = srv.stats()
-        out["loads"][str(rho)] = {"offered_rps": round(rho * cap, 2), "p50_ms": round(st["p50_ms"], 3),
-                                  "p99_ms": round(st["p99_ms"], 3), "mean_ms": round(st["mean_ms"], 3),
-                                  "max_ms": round(st["max_ms"], 3), "completed": st["completed"],
-                                  "failed": st["failed"], "gbs": round(st["gbs"], 2),
-                                  "max_inflight": st["max_inflight"], "peak_gb": round(st["peak_bytes"] / 1e9, 2)}
+            ts.append(srv.submit(ids[i], op, prec))
+        lat = np.array([srv.wait(t, 600000, with_latency=True)[1] for t in ts])
+        return reqs, lat, srv.stats()
+
+    def summary(reqs, lat, st, alone, cap, rho):
+        slow = np.array([l / alone[(i, op)] for (i, op), l in zip(reqs, lat)])
+        size = np.array([specs[i].grid ** 3 * specs[i].nbands for i, _ in reqs], dtype=np.float64)
+        cls = {}
+        edges = np.quantile(size, [0.0, 0.5, 0.9, 1.0])
+        for name, lo, hi in (("small (below median size)", edges[0], edges[1]),
+                             ("medium (median-90 %)", edges[1], edges[2]), ("large (top 10 %)", edges[2], edges[3])):
+            m = (size >= lo) & (size <= hi) if name.startswith("large") else (size >= lo) & (size < hi)
+            if m.any():
+                cls[name] = {"requests": int(m.sum()), "p50_ms": round(float(np.percentile(lat[m], 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat[m], 99)), 3),
+                             "alone_p50_ms": round(float(np.median([alone[r] for r, k in zip(reqs, m) if k])), 3)}
+        p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+        return {"offered_rps": round(rho * cap, 2), "p50_ms": round(p50, 3), "p99_ms": round(p99, 3),
+                "p99_over_p50": round(p99 / p50, 2), "mean_ms": round(float(lat.mean()), 3),
+                "max_ms": round(float(lat.max()), 3), "slowdown_p50": round(float(np.percentile(slow, 50)), 2),
+                "slowdown_p99": round(float(np.percentile(slow, 99)), 2), "by_size": cls,
+                "completed": st["completed"], "failed": st["failed"], "gbs": round(st["gbs"], 2),
+                "max_inflight": st["max_inflight"], "peak_gb": round(st["peak_bytes"] / 1e9, 2)}
+
+    srv, ids = start(slots)
+    run_burst(srv, ids, draw(warm))
+    # every request type alone (median of three), the denominator of the slowdown
+    alone = {}
+    for i in range(len(specs)):
+        for op in ("project", "expand"):
+            ls = []
+            for _ in range(3):
+                ls.append(srv.wait(srv.submit(ids[i], op, prec), 600000, with_latency=True)[1])
+            alone[(i, op)] = float(np.median(ls))
+    nburst = 400
+    cap = nburst / run_burst(srv, ids, draw(nburst))
+    out = {"systems": [dict(grid=sp.grid, atoms=sp.natoms, bands=sp.nbands, numax=sp.numax) for sp in specs],
+           "slots": slots, "precision": prec, "capacity_rps": round(cap, 2), "warmup_requests": warm,
+           "measured_requests": measured, "loads": {}, "slot_sweep_rho_0.8": {}}
+    for rho in loads:
+        reqs, lat, st = run_load(srv, ids, cap, rho)
+        out["loads"][str(rho)] = summary(reqs, lat, st, alone, cap, rho)
+    # seeded 2 % sample of served requests, inputs and results kept (16 bands) for the oracle check
+    srng = np.random.default_rng(SERVE_SEED + 1)
+    sample = []
+    for _ in range(nsample):
+        i = int(srng.integers(len(specs)))
+        op = "project" if srng.random() < 0.5 else "expand"
+        sp = specs[i]
+        p0, c0 = srv.read(ids[i])
+        assert srv.wait(srv.submit(ids[i], op, prec), 600000) == 0
+        p1, c1 = srv.read(ids[i])
+        pos, sig = geo[i]
+        rec = {"grid": (sp.grid,) * 3, "h": sp.h, "numax": sp.numax, "cube": sp.cube, "op": op}
+        if op == "project":
+            sel = np.sort(srng.choice(sp.natoms, size=min(2, sp.natoms), replace=False))
+            rec.update(psi=p0[..., :16].double().numpy(), pos=pos[sel], sig=sig[sel],
+                       got=c1[torch.as_tensor(sel)][:, :, :16].double().numpy())
+        else:
+            pts = np.sort(srng.choice(sp.grid ** 3, size=50, replace=False))
+            d = (p1.reshape(-1, sp.nbands)[torch.as_tensor(pts)] - p0.reshape(-1, sp.nbands)[torch.as_tensor(pts)])
+            rec.update(pos=pos, sig=sig, coeff=c0[:, :, :16].double().numpy(), pts=pts, got=d[:, :16].double().numpy())
+        sample.append(rec)
+        del p0, c0, p1, c1
     srv.close()
     torch.cuda.empty_cache()
-    return out
+    for ns in sweep:
+        srv, ids = start(ns)
+        run_burst(srv, ids, draw(warm // 2))
+        capn = nburst / run_burst(srv, ids, draw(nburst))
+        reqs, lat, st = run_load(srv, ids, capn, 0.8)
+        ent = summary(reqs, lat, st, alone, capn, 0.8)
+        ent["capacity_rps"] = round(capn, 2)
+        ent.pop("by_size")
+        out["slot_sweep_rho_0.8"][str(ns)] = ent
+        srv.close()
+        torch.cuda.empty_cache()
+    out["slot_sweep_rho_0.8"][str(slots)] = {k: v for k, v in out["loads"]["0.8"].items() if k != "by_size"}
+    out["slot_sweep_rho_0.8"][str(slots)]["capacity_rps"] = out["capacity_rps"]
+    return out, sample
+
+
+def oracle_serving_errors(serving_out, sample):
+    """CPU-baseline leg: the served sample against the FP64 oracle (storage-rounded FP32 inputs)."""
+    import oracle
+    errs = {"project": [], "expand": []}
+    for rec in sample:
+        if rec["op"] == "project":
+            ref = oracle.project(rec["grid"], rec["h"], True, rec["psi"], rec["pos"], rec["sig"], rec["numax"],
+                                 rec["cube"])
+            errs["project"].append(float(np.linalg.norm(rec["got"] - ref) / np.linalg.norm(ref)))
+        else:
+            ref = oracle.expand_points(rec["grid"], rec["h"], True, rec["pos"], rec["sig"], rec["numax"], rec["cube"],
+                                       rec["coeff"], rec["pts"])
+            errs["expand"].append(float(np.linalg.norm(rec["got"] - ref) / max(np.linalg.norm(ref), 1e-300)))
+    serving_out["oracle_sample"] = {
+        "requests": len(sample), "sample": "seeded 2 % of the measured stream, 16 bands; projections on 2 atoms, "
+                                           "expansions at 50 grid points",
+        "max_rel_norm_project": max(errs["project"], default=None),
+        "max_rel_norm_expand": max(errs["expand"], default=None), "tolerance": 2e-6}
 
 
 SERVE_SEED = 4242

@@ -368,9 +368,11 @@ int sho_submit(sho_server* server, int system_id, sho_op op, sho_prec prec, uint
 int sho_wait(sho_server* server, uint64_t ticket, int timeout_ms);
 /* sho_wait with the two outcomes kept apart: returns SHO_OK once the request is complete and stores its
  * status in *request_status (the ticket is then released; a request whose kernel's bounded wait expired
- * has status SHO_ERR_TIMEOUT, one whose SHO_P_FF64 input was out of range SHO_ERR_DEVICE), or
- * SHO_ERR_TIMEOUT when it is not complete within timeout_ms (the ticket stays valid). */
-int sho_wait_status(sho_server* server, uint64_t ticket, int timeout_ms, int* request_status);
+ * has status SHO_ERR_TIMEOUT, one whose SHO_P_FF64 input was out of range SHO_ERR_DEVICE) and, when
+ * latency_ms is not NULL, its latency (submission to completion seen by the scheduler, ms; 0 for a
+ * cancelled request); or SHO_ERR_TIMEOUT when it is not complete within timeout_ms (the ticket stays
+ * valid). */
+int sho_wait_status(sho_server* server, uint64_t ticket, int timeout_ms, int* request_status, double* latency_ms);
 /* Cancel a queued request: it is removed from the queue and never starts; a later sho_wait on its
  * ticket returns SHO_ERR_CANCELLED.  Returns SHO_OK, or SHO_ERR_STATE when the ticket is unknown, has
  * already started (GPU work is not interrupted) or has finished. */

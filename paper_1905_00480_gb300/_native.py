@@ -89,7 +89,7 @@ SIGNATURES = {
     "sho_submit": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_uint64)]),
     "sho_wait": (_I, [_VP, ctypes.c_uint64, _I]),
     "sho_cancel": (_I, [_VP, ctypes.c_uint64]),
-    "sho_wait_status": (_I, [_VP, ctypes.c_uint64, _I, _IP]),
+    "sho_wait_status": (_I, [_VP, ctypes.c_uint64, _I, _IP, _DP]),
     "sho_server_get_stats": (_I, [_VP, ctypes.POINTER(sho_server_stats)]),
     "sho_server_reset_stats": (_I, [_VP]),
     # include/sho_fault.h

@@ -434,7 +434,7 @@ int sho_submit(sho_server* s, int id, sho_op op, sho_prec prec, uint64_t* ticket
   return SHO_OK;
 }
 
-int sho_wait_status(sho_server* s, uint64_t ticket, int timeout_ms, int* request_status) {
+int sho_wait_status(sho_server* s, uint64_t ticket, int timeout_ms, int* request_status, double* latency_ms) {
   if (!s || !request_status) return SHO_ERR_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
@@ -444,14 +444,16 @@ int sho_wait_status(sho_server* s, uint64_t ticket, int timeout_ms, int* request
     if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !s->reqs[ticket].done)
       return SHO_ERR_TIMEOUT;
   }
-  *request_status = s->reqs[ticket].status;
+  const Req& r = s->reqs[ticket];
+  *request_status = r.status;
+  if (latency_ms) latency_ms[0] = r.status == SHO_ERR_CANCELLED ? 0.0 : (r.t_done - r.t_submit) * 1e3;
   s->reqs.erase(ticket);
   return SHO_OK;
 }
 
 int sho_wait(sho_server* s, uint64_t ticket, int timeout_ms) {
   int st = SHO_OK;
-  const int w = sho_wait_status(s, ticket, timeout_ms, &st);
+  const int w = sho_wait_status(s, ticket, timeout_ms, &st, nullptr);
   return w != SHO_OK ? w : st;
 }
 

@@ -84,15 +84,18 @@ class Server:
         N.check(N.lib().sho_submit(self._s, int(sid), OPS[op], N.PRECS[prec], ctypes.byref(t)), "sho_submit")
         return t.value
 
-    def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
-        """sho_wait_status: returns the request's status (0 = ok); raises TimeoutError when the request
-        is not complete within timeout_ms (the ticket stays valid)."""
+    def wait(self, ticket: int, timeout_ms: int = 60000, with_latency: bool = False):
+        """sho_wait_status: returns the request's status (0 = ok), or (status, latency_ms) with
+        with_latency=True; raises TimeoutError when the request is not complete within timeout_ms (the
+        ticket stays valid)."""
         rs = ctypes.c_int()
-        st = N.lib().sho_wait_status(self._s, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(rs))
+        lat = ctypes.c_double()
+        st = N.lib().sho_wait_status(self._s, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(rs),
+                                     ctypes.byref(lat))
         if st == -8:
             raise TimeoutError(f"ticket {ticket} not complete after {timeout_ms} ms")
         N.check(st, "sho_wait_status")
-        return rs.value
+        return (rs.value, lat.value) if with_latency else rs.value
 
     def cancel(self, ticket: int) -> int:
         """sho_cancel: 0 when the queued request was removed, SHO_ERR_STATE (-11) when it already started

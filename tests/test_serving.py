@@ -65,6 +65,20 @@ def test_alone_equals_mix_and_direct_and_oracle():
     # and the oracle within the FP32 tolerance
     ref = oracle.project((64,) * 3, 0.2, True, s0["psi"].double().cpu().numpy(), s0["pos"], s0["sig"], 5, 32)
     assert rel_norm(alone[1][1].double().numpy(), ref) <= TOL_FP32
+    # the served expansion (psi += E c with c the served projection) against the oracle expansion
+    psi_in = s0["psi"].double().cpu().numpy()
+    ref_add = oracle.add((64,) * 3, 0.2, True, np.zeros_like(psi_in), s0["pos"], s0["sig"], 5, 32,
+                         alone[1][1].double().numpy())
+    assert rel_norm(alone[1][0].double().numpy() - psi_in, ref_add) <= TOL_FP32
+    for k in (0, 2, 5):   # other sizes and numax 3 / 7 / 3
+        sk = systems[k]
+        g = sk["psi"].shape[0]
+        pin = sk["psi"].double().cpu().numpy()
+        refc = oracle.project((g,) * 3, 0.2, True, pin, sk["pos"], sk["sig"], sk["numax"], 32)
+        assert rel_norm(alone[k][1].double().numpy(), refc) <= TOL_FP32
+        refa = oracle.add((g,) * 3, 0.2, True, np.zeros_like(pin), sk["pos"], sk["sig"], sk["numax"], 32,
+                          alone[k][1].double().numpy())
+        assert rel_norm(alone[k][0].double().numpy() - pin, refa) <= TOL_FP32
 
 
 def test_admission_respects_budget():
