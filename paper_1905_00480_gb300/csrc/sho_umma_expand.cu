@@ -193,17 +193,50 @@ __global__ void __launch_bounds__(kUmThreads, 2)
   bool ok = true;
   int issued = 0;  // atoms whose MMAs have been issued and committed (the same count in every thread)
 
+  // the tile's psi rows go to L2 now, so the read-modify-write at the end finds them there
+  {
+    const int row = tid >> 5, x = tid & 31, y = yb * kUmRows + row;
+    if (y < Ny && xs + x < Nx) {
+      const TP* p = psi + (((size_t)z * Ny + y) * Nx + xs + x) * (size_t)B + (size_t)bt0 * 32;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"((uint32_t)(ntile * 32 * sizeof(TP)))
+                   : "memory");
+    }
+  }
+
+  // MMAs of atom li are issued after the block barrier that opens iteration li + 1 (one barrier per atom)
+  auto issue = [&](int li) {
+    const int slot = li & 1;
+    tc05_fence_after();
+    const uint64_t bdesc = umma_desc(sB + (uint32_t)(slot * SM::kB), 128, 8 * kUmKBytes);
+#pragma unroll
+    for (int row = 0; row < kUmRows; row++) {
+      const uint64_t adesc =
+          umma_desc(sA + (uint32_t)(slot * SM::kA + row * kUmBands * kUmKBytes), 128, 8 * kUmKBytes);
+      if constexpr (BF)
+        umma_f16(tmem + (uint32_t)(row * kUmX), adesc, bdesc, idesc, true);
+      else
+        umma_tf32(tmem + (uint32_t)(row * kUmX), adesc, bdesc, idesc, true);
+    }
+    umma_commit(bar0 + 8 * slot);
+  };
+
   stage_atom(0, 0);
   um_commit_cp();
   for (int li = 0; li < nlist; li++) {
     const int slot = li & 1;
     um_wait_cp0();
-    __syncthreads();  // atom li staged; every thread is past atom li - 1 (its staging buffer is free)
+    tc05_fence_before();
+    // atom li staged; the operands of atom li - 1 are written and its staging buffer is free; a wait
+    // that ran out in any thread ends the loop for all
+    if (!__syncthreads_and(ok)) break;
+    if (li >= 1) {
+      if (tid == 0) issue(li - 1);
+      issued = li;
+    }
     if (li + 1 < nlist) stage_atom(li + 1, slot ^ 1);
     um_commit_cp();
     // operand slot `slot` was last read by the MMAs of atom li - 2
     if (li >= 2 && !um_mbar_wait(bar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1), wait_cycles)) ok = false;
-    if (!__syncthreads_and(ok)) break;
     const int4 r = slist[li];
     const float* st = stage + (size_t)slot * stf;
     const float* tys = st + kUmBands * PP;
@@ -264,28 +297,19 @@ __global__ void __launch_bounds__(kUmThreads, 2)
       }
     }
     fence_async_smem();  // the operands written above become visible to the tensor core
-    tc05_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc05_fence_after();
-      const uint64_t bdesc = umma_desc(sB + (uint32_t)(slot * SM::kB), 128, 8 * kUmKBytes);
-#pragma unroll
-      for (int row = 0; row < kUmRows; row++) {
-        const uint64_t adesc =
-            umma_desc(sA + (uint32_t)(slot * SM::kA + row * kUmBands * kUmKBytes), 128, 8 * kUmKBytes);
-        if constexpr (BF)
-          umma_f16(tmem + (uint32_t)(row * kUmX), adesc, bdesc, idesc, true);
-        else
-          umma_tf32(tmem + (uint32_t)(row * kUmX), adesc, bdesc, idesc, true);
-      }
-      umma_commit(bar0 + 8 * slot);
-    }
-    issued = li + 1;
+  }
+  // the last atom's operands: one more barrier, then its MMAs
+  tc05_fence_before();
+  ok = __syncthreads_and(ok);  // the same verdict in every thread
+  if (ok && issued == nlist - 1) {
+    if (tid == 0) issue(nlist - 1);
+    issued = nlist;
   }
   um_wait_cp0();
   // the last commit covers every MMA issued before it
   const int last = issued - 1;
   bool done = ok && last >= 0 && um_mbar_wait(bar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), wait_cycles);
+  done = __syncthreads_and(done);
   if (!done) {
     if (tid == 0) atomicOr(status, kStatusTimeout);
     // the MMAs issued so far still complete; give them the default limit before tensor memory is freed
