@@ -833,14 +833,24 @@ def serving_bench(api, nsys=12, warm=200, measured=1000, loads=(0.5, 0.8, 0.95),
     # seeded 2 % sample of served requests, inputs and results kept (16 bands) for the oracle check
     srng = np.random.default_rng(SERVE_SEED + 1)
     sample = []
-    for _ in range(nsample):
+    for k in range(nsample):
         i = int(srng.integers(len(specs)))
         op = "project" if srng.random() < 0.5 else "expand"
         sp = specs[i]
-        p0, c0 = srv.read(ids[i])
-        assert srv.wait(srv.submit(ids[i], op, prec), 600000) == 0
-        p1, c1 = srv.read(ids[i])
         pos, sig = geo[i]
+        # a fresh copy of the system (the stream's alternating projections and expansions grow psi by about
+        # the projector's norm each cycle, so long-served systems leave the FP32 range), N(0, 1) coefficients
+        g = torch.Generator(device="cuda")
+        g.manual_seed(sp.seed + 7777 + k)
+        psi_k = torch.randn((sp.grid,) * 3 + (sp.nbands,), generator=g, device="cuda", dtype=torch.float32)
+        sid = srv.register(psi_k, pos, sig, sp.numax, sp.cube, sp.h, sp.periodic)
+        del psi_k
+        srv.write_coeff(sid, torch.randn((sp.natoms, api.nstates(sp.numax), sp.nbands), generator=g,
+                                         dtype=torch.float32, device="cuda").cpu())
+        p0, c0 = srv.read(sid)
+        assert srv.wait(srv.submit(sid, op, prec), 600000) == 0
+        p1, c1 = srv.read(sid)
+        srv.unregister(sid)
         rec = {"grid": (sp.grid,) * 3, "h": sp.h, "numax": sp.numax, "cube": sp.cube, "op": op}
         if op == "project":
             sel = np.sort(srng.choice(sp.natoms, size=min(2, sp.natoms), replace=False))

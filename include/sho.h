@@ -320,7 +320,10 @@ int sho_usu_add(sho_handle* handle, const sho_grid* grid, const void* coeff, int
  * coeff; expand: psi += E coeff) are queued by sho_submit and started by the scheduler as soon as a
  * slot is free, the request's workspace fits the memory budget next to the resident systems and
  * in-flight workspaces, and no earlier request of the same system is still running (requests of one
- * system run in submission order; requests of different systems overlap on the device).  Results of
+ * system run in submission order; requests of different systems overlap on the device).  When several
+ * requests are startable the scheduler takes the one with the smallest expected service time (its
+ * algorithmic bytes at 500 GB/s) minus the time it has already waited: small requests do not queue
+ * behind large ones, and a large one waits at most about its own service time longer.  Results of
  * a request do not depend on what else runs: every kernel is deterministic and works on its own
  * system's buffers.
  *   budget_bytes  device memory the server may hold: resident systems + slot workspaces.

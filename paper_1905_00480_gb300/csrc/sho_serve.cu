@@ -3,9 +3,10 @@
 //
 // One scheduler thread owns `slots` execution slots (stream + handle/workspace + completion event).
 // It repeatedly (1) retires slots whose completion event has fired, recording the request latency,
-// and (2) walks the request queue in submission order and starts every request whose system is idle
-// and for which a free slot exists whose workspace, grown to the request's need, keeps
-// resident systems + all slot workspaces within the memory budget.  Requests that arrive while others
+// and (2) starts queued requests whose system is idle and for which a free slot exists whose workspace,
+// grown to the request's need, keeps resident systems + all slot workspaces within the memory budget:
+// the earliest request of each system is a candidate, and the candidate with the smallest expected
+// service time minus its waiting time goes first (shortest job first with aging).  Requests that arrive while others
 // run are admitted as soon as a slot and memory free up; requests of different systems overlap on the
 // device.  Nothing here waits on the device without a bound: completion is polled with
 // cudaEventQuery, and host waits (sho_wait) take a timeout.  A finished request's status includes the
@@ -33,6 +34,9 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
+
+// Service-rate estimate of the admission order: algorithmic bytes per second of one request on the GPU.
+constexpr double kServeBytesPerSecond = 500e9;
 
 struct SysRec {
   sho_grid grid;
@@ -213,20 +217,35 @@ void scheduler(sho_server* s) {
       progress = true;
     }
     if (!s->stop) {
-      for (auto it = s->queue.begin(); it != s->queue.end();) {
-        Req& r = s->reqs[*it];
-        if (s->systems[r.sys].busy) {
-          ++it;
-          continue;
+      // Admission order: among the earliest queued request of every idle system (a system's requests
+      // run in submission order), start the one with the smallest expected service time minus the time
+      // it has waited -- shortest job first, aged so that a large request waits at most about its own
+      // service time longer than small ones -- while a slot and memory allow.
+      for (;;) {
+        const double tnow = now_s();
+        auto best = s->queue.end();
+        double best_score = 0.0;
+        int best_slot = -1;
+        std::vector<int> seen;
+        for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+          const Req& r = s->reqs[*it];
+          if (std::find(seen.begin(), seen.end(), r.sys) != seen.end()) continue;
+          seen.push_back(r.sys);
+          const SysRec& sys = s->systems[r.sys];
+          if (sys.busy) continue;
+          const double est = (r.op == SHO_OP_PROJECT ? sys.bytes_prj : sys.bytes_add) / kServeBytesPerSecond;
+          const double score = est - (tnow - r.t_submit);
+          if (best != s->queue.end() && score >= best_score) continue;
+          const int k = pick_slot(s, r.need);
+          if (k < 0) continue;
+          best = it;
+          best_score = score;
+          best_slot = k;
         }
-        const int k = pick_slot(s, r.need);
-        if (k < 0) {
-          ++it;
-          continue;
-        }
-        const uint64_t t = *it;
-        it = s->queue.erase(it);
-        start(s, k, t);
+        if (best == s->queue.end()) break;
+        const uint64_t t = *best;
+        s->queue.erase(best);
+        start(s, best_slot, t);
         progress = true;
       }
     }
