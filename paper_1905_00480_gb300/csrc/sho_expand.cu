@@ -26,7 +26,7 @@ template <int NU, typename TCo, typename TC, bool TILED = false>
 __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
                                                         const TCo* __restrict__ coeff, TC* __restrict__ tables,
                                                         TC* __restrict__ t2, TC* __restrict__ txm, double scale,
-                                                        NonlocalIn nl) {
+                                                        NonlocalIn nl, TC* __restrict__ tym = nullptr) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -62,6 +62,12 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
         constexpr int NPX = (NP + 3) & ~3;
         TC* row = txm + ((size_t)a * C + i) * NPX;
         phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, row, 1);
+        for (int n = NP; n < NPX; n++) row[n] = (TC)0;
+      }
+      if (tym) {  // y table y-major [C][NPX] (tensor-memory expansion: a row's functions in 16-byte loads)
+        constexpr int NPX = (NP + 3) & ~3;
+        TC* row = tym + ((size_t)a * C + i) * NPX;
+        phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, row, 1);
         for (int n = NP; n < NPX; n++) row[n] = (TC)0;
       }
     }
@@ -204,7 +210,8 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
 }
 
 // ------------------------------------------------------------------------------ kernel 2: rows
-template <int NU, typename TP, typename TC>
+// SPH: spherical support (one support mask per atom row), compiled separately from the cube form.
+template <int NU, typename TP, typename TC, bool SPH = false>
 __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev* __restrict__ atoms,
                                                        const int* __restrict__ plane_ptr,
                                                        const int* __restrict__ plane_atoms,
@@ -251,8 +258,11 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
       if (iz < 0) iz += g.n[2];
     }
     if (iy < 0 || iy >= C) continue;
-    const unsigned long long sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
-    if (sup == 0) continue;
+    unsigned long long sup = ~0ull;
+    if constexpr (SPH) {
+      sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
+      if (sup == 0) continue;
+    }
     const TC* tx = tables + (size_t)a * 2 * NP * C;
     const TC* ty = tx + (size_t)NP * C;
     // y-pass (a6, middle pass)
@@ -273,12 +283,14 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
     // with the accumulator value, so eight independent FMA chains are in flight and every point
     // costs exactly numax+1 FMAs.
     for (int ix0 = 0; ix0 < C; ix0 += 8) {
-      if (((sup >> ix0) & 0xffull) == 0) continue;
+      if constexpr (SPH) {
+        if (((sup >> ix0) & 0xffull) == 0) continue;
+      }
       int jx[8];
       TC s[8];
 #pragma unroll
       for (int u = 0; u < 8; u++) {
-        jx[u] = ((sup >> (ix0 + u)) & 1ull) ? cube_index(at.o[0], ix0 + u, Nx, g.periodic) : -1;
+        jx[u] = (!SPH || ((sup >> (ix0 + u)) & 1ull)) ? cube_index(at.o[0], ix0 + u, Nx, g.periodic) : -1;
         s[u] = jx[u] >= 0 ? acc[jx[u] * kWarp + lane] : (TC)0;
       }
 #pragma unroll
@@ -310,7 +322,7 @@ static cudaError_t zpass_smem(K kern, size_t smem) {
                           : cudaSuccess;
 }
 
-template <int NU, typename TP, typename TCo, typename TC>
+template <int NU, typename TP, typename TCo, typename TC, bool SPH = false>
 static cudaError_t launch_expand_t(const ExpandLaunch& p) {
   const int C = p.g.cube;
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
@@ -325,7 +337,7 @@ static cudaError_t launch_expand_t(const ExpandLaunch& p) {
     if (e != cudaSuccess) return e;
   }
   {
-    auto kern = k_expand_rows<NU, TP, TC>;
+    auto kern = k_expand_rows<NU, TP, TC, SPH>;
     const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(TC);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -339,9 +351,12 @@ static cudaError_t launch_expand_t(const ExpandLaunch& p) {
 template <int NU>
 static cudaError_t launch_expand_nu(const ExpandLaunch& p) {
   if (p.coeff_dtype == SHO_F64) {
-    if (p.psi_dtype == SHO_F64) return launch_expand_t<NU, double, double, double>(p);
+    if (p.psi_dtype == SHO_F64)
+      return p.g.r2max > 0.0 ? launch_expand_t<NU, double, double, double, true>(p)
+                             : launch_expand_t<NU, double, double, double>(p);
     return cudaErrorInvalidValue;
   }
+  if (p.g.r2max > 0.0) return cudaErrorInvalidValue;  // spherical support: FP64 forms only
   if (p.psi_dtype == SHO_F32) return launch_expand_t<NU, float, float, float>(p);
   if (p.psi_dtype == SHO_BF16) return launch_expand_t<NU, __nv_bfloat16, float, float>(p);
   return cudaErrorInvalidValue;
@@ -369,7 +384,7 @@ static cudaError_t zpass_f32_tiled_nu(const ExpandLaunch& p) {
   if (e != cudaSuccess) return e;
   k_expand_zpass<NU, float, float, true><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
-      static_cast<float*>(p.tables_xmajor), p.scale, p.nl);
+      static_cast<float*>(p.tables_xmajor), p.scale, p.nl, static_cast<float*>(p.tables_ymajor));
   return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ struct ExpandLaunch {
   void* tables_xmajor = nullptr;  // optional workspace, txm_bytes_per_point(numax) bytes per (atom, cube
                                   // point): the FP32 x table x-major [A][cube][NPX], then (tensor forms)
                                   // the B fragments of the x-pass; FP64-accurate form: float-pair tables
+  void* tables_ymajor = nullptr;  // optional: the FP32 y table y-major [A][cube][NPX] (tensor-memory kernel)
   double scale = 1.0;       // psi += scale * E c: applied to the z table of the z-pass
   NonlocalIn nl;            // fused non-local action (nl.D set): the coefficients are D times a projection
   int kernel = 0;           // FP32-class x-pass engine: 0 automatic, 1 warp-level mma.sync, 2 tcgen05

@@ -37,7 +37,9 @@ struct ProjectSmem {
   }
 };
 
-template <int NU, typename TP, typename TC>
+// SPH: spherical support (one support mask per cube row); compiled separately so that the cube form keeps
+// its plain inner loop.
+template <int NU, typename TP, typename TC, bool SPH = false>
 __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restrict__ psi,
                                                    const AtomDev* __restrict__ atoms, int zsplit,
                                                    TC* __restrict__ coeff) {
@@ -88,20 +90,25 @@ __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restri
     for (int iy = 0; iy < C; iy++) {
       const int jy = cube_index(at.o[1], iy, g.n[1], g.periodic);
       if (jy < 0) continue;
-      const unsigned long long sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
-      if (sup == 0) continue;
+      unsigned long long sup = ~0ull;
+      if constexpr (SPH) {
+        sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
+        if (sup == 0) continue;
+      }
       const TP* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b;
       // x-pass (a3)
       TC t1[NP];
 #pragma unroll
       for (int n = 0; n < NP; n++) t1[n] = (TC)0;
       for (int ix = 0; ix < C; ix += 8) {
-        if (((sup >> ix) & 0xffull) == 0) continue;
+        if constexpr (SPH) {
+          if (((sup >> ix) & 0xffull) == 0) continue;
+        }
         TC v[8];
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const long long o = xoff[ix + u];
-          v[u] = (o >= 0 && bok && ((sup >> (ix + u)) & 1ull)) ? to_real(row[o], (TC)0) : (TC)0;
+          v[u] = (o >= 0 && bok && (!SPH || ((sup >> (ix + u)) & 1ull))) ? to_real(row[o], (TC)0) : (TC)0;
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {
@@ -150,11 +157,11 @@ __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restri
   cl.sync();
 }
 
-template <int NU, typename TP, typename TC>
+template <int NU, typename TP, typename TC, bool SPH = false>
 static cudaError_t launch_project_t(const ProjectLaunch& p) {
   const int C = p.g.cube;
   const size_t smem = ProjectSmem<NU>::template bytes<TC>(C);
-  auto kern = k_project<NU, TP, TC>;
+  auto kern = k_project<NU, TP, TC, SPH>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -176,9 +183,11 @@ static cudaError_t launch_project_t(const ProjectLaunch& p) {
 template <int NU>
 static cudaError_t launch_project_nu(const ProjectLaunch& p) {
   if (p.coeff_dtype == SHO_F64) {
-    if (p.psi_dtype == SHO_F64) return launch_project_t<NU, double, double>(p);
+    if (p.psi_dtype == SHO_F64)
+      return p.g.r2max > 0.0 ? launch_project_t<NU, double, double, true>(p) : launch_project_t<NU, double, double>(p);
     return cudaErrorInvalidValue;
   }
+  if (p.g.r2max > 0.0) return cudaErrorInvalidValue;  // spherical support: FP64 forms only
   if (p.psi_dtype == SHO_F32) return launch_project_t<NU, float, float>(p);
   if (p.psi_dtype == SHO_BF16) return launch_project_t<NU, __nv_bfloat16, float>(p);
   return cudaErrorInvalidValue;

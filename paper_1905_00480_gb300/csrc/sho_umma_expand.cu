@@ -7,8 +7,9 @@
 // A CTA owns a tile of one z plane: 8 grid rows x 32 x points x 128 bands.  The tile's update lives in
 // tensor memory for the whole atom loop: 8 accumulators (one per row) of 128 lanes (bands) x 32
 // columns (x points), 256 columns.  For each atom whose cube meets the tile (ascending order):
-//   * its band-tiled T2 slice (128 bands x pairs), y table and x table are staged in shared memory by
-//     cp.async, one atom ahead;
+//   * its band-tiled T2 slice (128 bands x pairs), y table and x table (both point-major) are staged in
+//     shared memory by three bulk TMA copies issued by one thread, one atom ahead, completing on the
+//     buffer's mbarrier;
 //   * 256 threads run the y-pass (thread = band, four rows each) and write T1 of every row as an MMA A
 //     operand, [128 bands][8 states] TF32 (or [128][16] BF16, states 8..15 zero), K-major without
 //     swizzle; the atom's x functions on the tile's 32 points become the B operand [32][8];
@@ -31,11 +32,15 @@ constexpr int kUmCols = kUmRows * kUmX;  // tensor-memory columns: 8 accumulator
 constexpr int kUmKBytes = 32;    // bytes per operand row: 8 TF32 or 16 BF16 values
 
 __device__ __forceinline__ uint32_t um_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void um_cp16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on `bar`.
+__device__ __forceinline__ void um_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
-__device__ __forceinline__ void um_commit_cp() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void um_wait_cp0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void um_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void um_mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
@@ -63,9 +68,9 @@ struct UmSmem {
   static constexpr int NP = NU + 1, P = Basis<NU>::P, PP = tiled_pairs(P), NPX = (NP + 3) & ~3;
   static constexpr size_t kA = (size_t)kUmRows * kUmBands * kUmKBytes;  // one A slot: 32 KB
   static constexpr size_t kB = (size_t)kUmX * kUmKBytes;                // one B slot: 1 KB
-  // staging buffer: T2 [128][PP] floats, y table [NP][C], x table [C][NPX]
+  // staging buffer: T2 [128][PP] floats, y table [C][NPX], x table [C][NPX] (point-major)
   __host__ __device__ static size_t stage_floats(int cube) {
-    return (size_t)kUmBands * PP + (size_t)NP * cube + (size_t)cube * NPX;
+    return (size_t)kUmBands * PP + 2 * (size_t)cube * NPX;
   }
   __host__ __device__ static size_t off_b() { return 2 * kA; }
   __host__ __device__ static size_t off_stage() { return 2 * kA + 2 * kB; }
@@ -78,7 +83,7 @@ struct UmSmem {
 template <int NU, typename TP, bool BF>
 __global__ void __launch_bounds__(kUmThreads, 2)
     k_expand_umma(GridDev g, const AtomDev* __restrict__ atoms, const int* __restrict__ plane_ptr,
-                  const int* __restrict__ plane_atoms, const float* __restrict__ tables,
+                  const int* __restrict__ plane_atoms, const float* __restrict__ tym,
                   const float* __restrict__ txm, const float* __restrict__ t2, TP* __restrict__ psi,
                   int* __restrict__ status, long long wait_cycles) {
   using BS = Basis<NU>;
@@ -93,9 +98,10 @@ __global__ void __launch_bounds__(kUmThreads, 2)
   const size_t stf = SM::stage_floats(C);
   unsigned char* barp = smem_raw + SM::off_bar(C);
   const uint32_t bar0 = um_smem(barp);                      // commit barriers of operand slots 0 and 1
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 16);
-  int* s_misc = reinterpret_cast<int*>(barp + 32);          // [0] list length, [1..8] warp counts
-  int4* slist = reinterpret_cast<int4*>(barp + 128);        // after s_misc[0..8] (bytes 32..67)
+  const uint32_t fbar0 = bar0 + 16;                         // staging barriers of buffers 0 and 1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 32);
+  int* s_misc = reinterpret_cast<int*>(barp + 48);          // [0] list length, [1..8] warp counts
+  int4* slist = reinterpret_cast<int4*>(barp + 128);        // after s_misc[0..8] (bytes 48..83)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const int nseg = (Nx + kUmX - 1) / kUmX, nyb = (Ny + kUmRows - 1) / kUmRows;
@@ -153,6 +159,8 @@ __global__ void __launch_bounds__(kUmThreads, 2)
   if (tid == 0) {
     um_mbar_init(bar0);
     um_mbar_init(bar0 + 8);
+    um_mbar_init(fbar0);
+    um_mbar_init(fbar0 + 8);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if constexpr (BF) {
@@ -173,25 +181,26 @@ __global__ void __launch_bounds__(kUmThreads, 2)
 #pragma unroll
   for (int c = 0; c < 4; c++) tmem_zero32(tlane + (uint32_t)((warp >> 2) * 128 + 32 * c));
 
-  // stage atom li into staging buffer sb
+  // stage atom li into staging buffer sb: three bulk copies by one thread, completing on the buffer's barrier
   auto stage_atom = [&](int li, int sb) {
+    if (tid != 0) return;
     const int4 r = slist[li];
     const int a = r.x, iz = r.w;
-    float* dst = stage + (size_t)sb * stf;
-    const float* src = t2 + (((size_t)a * C + iz) * nbt32 + bt0) * 32 * PP;
-    for (int q = tid; q < ntile * 32 * PP / 4; q += kUmThreads) um_cp16(um_smem(dst + 4 * q), src + 4 * q);
-    const float* sy = tables + (size_t)a * 2 * NP * C + (size_t)NP * C;   // y table [NP][C]
-    for (int q = tid; q < NP * C / 4; q += kUmThreads) um_cp16(um_smem(dst + kUmBands * PP + 4 * q), sy + 4 * q);
-    const float* sx = txm + (size_t)a * C * NPX;                          // x table [C][NPX]
-    for (int q = tid; q < C * NPX / 4; q += kUmThreads)
-      um_cp16(um_smem(dst + kUmBands * PP + NP * C + 4 * q), sx + 4 * q);
+    const uint32_t dst = um_smem(stage + (size_t)sb * stf), bar = fbar0 + 8 * sb;
+    const uint32_t bt2 = (uint32_t)(ntile * 32 * PP * 4), btab = (uint32_t)(C * NPX * 4);
+    fence_async_smem();  // the buffer's earlier readers (generic proxy) are ordered before the copies
+    um_expect_tx(bar, bt2 + 2 * btab);
+    um_bulk(dst, t2 + (((size_t)a * C + iz) * nbt32 + bt0) * 32 * PP, bt2, bar);
+    um_bulk(dst + kUmBands * PP * 4, tym + (size_t)a * C * NPX, btab, bar);             // y table [C][NPX]
+    um_bulk(dst + (kUmBands * PP + C * NPX) * 4, txm + (size_t)a * C * NPX, btab, bar); // x table [C][NPX]
   };
 
   const int bl = tid & 127, rh = tid >> 7;         // this thread's band and row half (rows 4 rh .. 4 rh + 3)
   const bool bvalid = bt0 * 32 + bl < B && bl < ntile * 32;
   constexpr uint32_t idesc = umma_idesc(BF ? kUmmaBF16 : kUmmaTF32, kUmBands, kUmX);
   bool ok = true;
-  int issued = 0;  // atoms whose MMAs have been issued and committed (the same count in every thread)
+  int issued = 0;    // atoms whose MMAs have been issued and committed (the same count in every thread)
+  int pending = -1;  // atom whose staging copies may still be in flight when the loop stops early
 
   // the tile's psi rows go to L2 now, so the read-modify-write at the end finds them there
   {
@@ -221,26 +230,28 @@ __global__ void __launch_bounds__(kUmThreads, 2)
   };
 
   stage_atom(0, 0);
-  um_commit_cp();
   for (int li = 0; li < nlist; li++) {
     const int slot = li & 1;
-    um_wait_cp0();
+    // atom li's staging buffer (its (li >> 1)-th fill) has landed
+    if (!um_mbar_wait(fbar0 + 8 * slot, (uint32_t)((li >> 1) & 1), wait_cycles)) ok = false;
     tc05_fence_before();
     // atom li staged; the operands of atom li - 1 are written and its staging buffer is free; a wait
     // that ran out in any thread ends the loop for all
-    if (!__syncthreads_and(ok)) break;
+    if (!__syncthreads_and(ok)) {
+      pending = li;
+      break;
+    }
     if (li >= 1) {
       if (tid == 0) issue(li - 1);
       issued = li;
     }
     if (li + 1 < nlist) stage_atom(li + 1, slot ^ 1);
-    um_commit_cp();
     // operand slot `slot` was last read by the MMAs of atom li - 2
     if (li >= 2 && !um_mbar_wait(bar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1), wait_cycles)) ok = false;
     const int4 r = slist[li];
     const float* st = stage + (size_t)slot * stf;
-    const float* tys = st + kUmBands * PP;
-    const float* txs = tys + NP * C;
+    const float* tys = st + kUmBands * PP;   // [C][NPX]
+    const float* txs = tys + C * NPX;         // [C][NPX]
     // y-pass for four rows of this band, written as A rows (K-major, 32 bytes per band)
     float t2r[P];
     {
@@ -265,12 +276,19 @@ __global__ void __launch_bounds__(kUmThreads, 2)
 #pragma unroll
       for (int n = 0; n < 8; n++) t1[n] = 0.0f;
       if (yin) {
+        float wy[NPX];
 #pragma unroll
-        for (int ny = 0; ny < NP; ny++) {
-          const float w = tys[ny * C + iy];
-#pragma unroll
-          for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fmaf(t2r[BS::pair(nx, ny)], w, t1[nx]);
+        for (int q = 0; q < NPX / 4; q++) {
+          const float4 w4 = reinterpret_cast<const float4*>(tys + iy * NPX)[q];
+          wy[4 * q] = w4.x;
+          wy[4 * q + 1] = w4.y;
+          wy[4 * q + 2] = w4.z;
+          wy[4 * q + 3] = w4.w;
         }
+#pragma unroll
+        for (int ny = 0; ny < NP; ny++)
+#pragma unroll
+          for (int nx = 0; nx + ny <= NU; nx++) t1[nx] = fmaf(t2r[BS::pair(nx, ny)], wy[ny], t1[nx]);
       }
       unsigned char* dst = arow + (size_t)row * kUmBands * kUmKBytes + umma_kmajor_offset(bl, 0, kUmKBytes);
       if constexpr (BF) {
@@ -305,11 +323,15 @@ __global__ void __launch_bounds__(kUmThreads, 2)
     if (tid == 0) issue(nlist - 1);
     issued = nlist;
   }
-  um_wait_cp0();
   // the last commit covers every MMA issued before it
   const int last = issued - 1;
   bool done = ok && last >= 0 && um_mbar_wait(bar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), wait_cycles);
   done = __syncthreads_and(done);
+  if (pending >= 0) {
+    // the copies staging atom `pending` may still be in flight: they complete whatever else happens, so
+    // wait for them with the default limit before the CTA's shared memory is released
+    (void)um_mbar_wait(fbar0 + 8 * (pending & 1), (uint32_t)((pending >> 1) & 1), kDefaultWaitCycles);
+  }
   if (!done) {
     if (tid == 0) atomicOr(status, kStatusTimeout);
     // the MMAs issued so far still complete; give them the default limit before tensor memory is freed
@@ -411,7 +433,7 @@ static cudaError_t umma_run(const ExpandLaunch& p) {
   const int nseg = (p.g.n[0] + kUmX - 1) / kUmX, nyb = (p.g.n[1] + kUmRows - 1) / kUmRows;
   const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
   kern<<<dim3(nblk, (p.g.nbands + kUmBands - 1) / kUmBands), kUmThreads, smem, p.stream>>>(
-      p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const float*>(p.tables),
+      p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const float*>(p.tables_ymajor),
       static_cast<const float*>(p.tables_xmajor), static_cast<const float*>(p.t2), static_cast<TP*>(p.psi), p.status,
       p.wait_cycles);
   return cudaGetLastError();
@@ -422,11 +444,15 @@ static cudaError_t umma_nu(const ExpandLaunch& p, sho_prec prec) {
   if constexpr (NU > 7) {
     return cudaErrorNotSupported;
   } else {
-    cudaError_t e = launch_expand_zpass_f32_tiled(p);
+    // the y table y-major goes after the x-major x table in the same workspace region (the region holds
+    // txm_bytes_per_point(numax) >= 8 NPX bytes per atom and cube point)
+    ExpandLaunch q = p;
+    q.tables_ymajor = static_cast<float*>(p.tables_xmajor) + (size_t)p.natoms * p.g.cube * ((NU + 4) & ~3);
+    cudaError_t e = launch_expand_zpass_f32_tiled(q);
     if (e != cudaSuccess) return e;
     const bool bf = prec == SHO_P_BF16;
-    if (p.psi_dtype == SHO_F32) return bf ? umma_run<NU, float, true>(p) : umma_run<NU, float, false>(p);
-    return bf ? umma_run<NU, __nv_bfloat16, true>(p) : umma_run<NU, __nv_bfloat16, false>(p);
+    if (p.psi_dtype == SHO_F32) return bf ? umma_run<NU, float, true>(q) : umma_run<NU, float, false>(q);
+    return bf ? umma_run<NU, __nv_bfloat16, true>(q) : umma_run<NU, __nv_bfloat16, false>(q);
   }
 }
 
