@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
     if (nl.D && nl.t2p)
 #pragma unroll
       for (int n = 0; n < NP; n++) pz[n * C + i] = (TC)zc[n];
-    if (blockIdx.x == 0) {
+    if (blockIdx.x == 0 && blockIdx.z == 0) {
       phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, tx + i, C);
       phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, ty + i, C);
       if (txm) {  // x table again, x-major [C][NPX] with NPX = NP rounded up to 4 (zero padded)
@@ -151,6 +151,9 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
   if (!TILED && !bok) return;
 
   constexpr int PP = tiled_pairs(P);
+  // planes of this block: its chunk of the cube's planes (the planes are independent here)
+  const int zper = (C + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int zb = (int)blockIdx.z * zper, ze = min(C, zb + zper);
   if constexpr (!TILED) {
     TC* out = t2 + (size_t)a * C * P * B + b;
 #pragma unroll
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
         for (int nz = 0; nz < NP; nz++)
           cz[nz] = (nx + ny + nz <= NU) ? to_real(ca[(size_t)BS::state(nx, ny, nz) * cstr], (TC)0) : (TC)0;
         const int p = BS::pair(nx, ny);
-        for (int iz = 0; iz < C; iz++) {
+        for (int iz = zb; iz < ze; iz++) {
           TC s = (TC)0;
 #pragma unroll
           for (int nz = 0; nz + nx + ny <= NU; nz++) s = fma(cz[nz], phz[nz * C + iz], s);
@@ -176,8 +179,8 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
     // with 16-byte stores (a lane-strided store per pair would leave DRAM sectors half written)
     TC* stage = phz + (size_t)NP * C;  // [kZChunk][32][PP]
     const size_t nbt = gridDim.x;
-    for (int z0 = 0; z0 < C; z0 += kZChunk) {
-      const int nzc = min(kZChunk, C - z0);
+    for (int z0 = zb; z0 < ze; z0 += kZChunk) {
+      const int nzc = min(kZChunk, ze - z0);
 #pragma unroll
       for (int ny = 0; ny < NP; ny++) {
 #pragma unroll
@@ -316,6 +319,17 @@ static size_t nl_smem(const ExpandLaunch& p) {
   return ((p.nl.t2p ? (size_t)(NU + 1) * p.g.cube : 0) + 2 * (size_t)Basis<NU>::N * kWarp) * sizeof(TC);
 }
 
+// Plane chunks of the expansion's z-pass (grid z): enough warps for the GPU when the (atom, band tile)
+// warps alone are few; one chunk when the fused action's prologue runs (it needs every plane), and chunks
+// of whole kZChunk planes.
+static unsigned zpass_chunks(const ExpandLaunch& p) {
+  if (p.nl.D) return 1;
+  const long long warps = (long long)p.natoms * ((p.g.nbands + kWarp - 1) / kWarp);
+  unsigned n = 1;
+  while (warps * n * 2 <= 4096 && (int)(n * 2) * kZChunk <= p.g.cube) n *= 2;
+  return n;
+}
+
 template <typename K>
 static cudaError_t zpass_smem(K kern, size_t smem) {
   return smem > 48 * 1024 ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
@@ -330,7 +344,7 @@ static cudaError_t launch_expand_t(const ExpandLaunch& p) {
     const size_t smem = (size_t)(NU + 1) * C * sizeof(TC) + nl_smem<NU, TC>(p);
     cudaError_t e = zpass_smem(k_expand_zpass<NU, TCo, TC>, smem);
     if (e != cudaSuccess) return e;
-    k_expand_zpass<NU, TCo, TC><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+    k_expand_zpass<NU, TCo, TC><<<dim3(nbt, p.natoms, zpass_chunks(p)), kWarp, smem, p.stream>>>(
         p.g, p.atoms, static_cast<const TCo*>(p.coeff), static_cast<TC*>(p.tables), static_cast<TC*>(p.t2),
         (TC*)nullptr, p.scale, p.nl);
     e = cudaGetLastError();
@@ -368,7 +382,7 @@ static cudaError_t zpass_f32_nu(const ExpandLaunch& p) {
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(float) + nl_smem<NU, float>(p);
   const cudaError_t e = zpass_smem(k_expand_zpass<NU, float, float>, smem);
   if (e != cudaSuccess) return e;
-  k_expand_zpass<NU, float, float><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+  k_expand_zpass<NU, float, float><<<dim3(nbt, p.natoms, zpass_chunks(p)), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
       static_cast<float*>(p.tables_xmajor), p.scale, p.nl);
   return cudaGetLastError();
@@ -382,7 +396,7 @@ static cudaError_t zpass_f32_tiled_nu(const ExpandLaunch& p) {
                       nl_smem<NU, float>(p);
   const cudaError_t e = zpass_smem(k_expand_zpass<NU, float, float, true>, smem);
   if (e != cudaSuccess) return e;
-  k_expand_zpass<NU, float, float, true><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+  k_expand_zpass<NU, float, float, true><<<dim3(nbt, p.natoms, zpass_chunks(p)), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const float*>(p.coeff), static_cast<float*>(p.tables), static_cast<float*>(p.t2),
       static_cast<float*>(p.tables_xmajor), p.scale, p.nl, static_cast<float*>(p.tables_ymajor));
   return cudaGetLastError();
@@ -394,7 +408,7 @@ static cudaError_t zpass_f64_nu(const ExpandLaunch& p) {
   const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double) + nl_smem<NU, double>(p);
   const cudaError_t e = zpass_smem(k_expand_zpass<NU, double, double>, smem);
   if (e != cudaSuccess) return e;
-  k_expand_zpass<NU, double, double><<<dim3(nbt, p.natoms), kWarp, smem, p.stream>>>(
+  k_expand_zpass<NU, double, double><<<dim3(nbt, p.natoms, zpass_chunks(p)), kWarp, smem, p.stream>>>(
       p.g, p.atoms, static_cast<const double*>(p.coeff), static_cast<double*>(p.tables), static_cast<double*>(p.t2),
       (double*)nullptr, p.scale, p.nl);
   return cudaGetLastError();
