@@ -34,32 +34,15 @@ __device__ __forceinline__ void ff_wait() {
 template <int NU>
 struct FfProjectSmem {
   static constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
-  __host__ __device__ static size_t bytes(int cube) {
+  static size_t bytes(int cube) {
     size_t t = (size_t)kFfStages * cube * kFfRowBytes;             // ring of psi rows
     t += (size_t)cube * NPX * sizeof(float2);                      // x table (pairs), x-major
     t += (size_t)NP * cube * sizeof(float2);                       // y table (pairs)
     t += (size_t)cube * sizeof(long long);                         // x offsets
     t += (size_t)2 * cube * sizeof(int);                           // y and z grid indices
-    t = (t + 15) & ~(size_t)15;
-    t += (size_t)cube * NPX * sizeof(double) + (size_t)NP * cube * sizeof(double);  // FP64 x / y tables
     return t;
   }
 };
-
-// Band tiles whose x- and y-passes run natively on the FP64 pipe next to the float-float tiles of the
-// same launch: the FP64 pipe (1/64 of the FP32 rate on GB300) is otherwise idle in this form, and one
-// DFMA does the work of a ten-instruction float-float step.  About a quarter of the work balances the two
-// pipes (the FP64 form takes ~3.3x the time of the float-float form); the last round(0.23 nbt) tiles.
-inline int ff_fp64_tiles(int nbt) { return (int)(0.23 * nbt + 0.25); }
-
-// A double kept in the bits of two floats (the FP64 tiles reuse the float-pair accumulators' registers).
-__device__ __forceinline__ double ff_bits_d(float hi, float lo) {
-  return __hiloint2double(__float_as_int(hi), __float_as_int(lo));
-}
-__device__ __forceinline__ void ff_set_bits(float& hi, float& lo, double d) {
-  hi = __int_as_float(__double2hiint(d));
-  lo = __int_as_float(__double2loint(d));
-}
 
 // x- and y-passes of one (atom, 32-band tile, slab of cube planes): T2[a][iz][P][B] of each plane of
 // the slab, converted from its float pair to FP64, goes to a workspace; the z-pass is k_project_ff_zpass.
@@ -67,8 +50,7 @@ __device__ __forceinline__ void ff_set_bits(float& hi, float& lo, double d) {
 template <int NU>
 __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* __restrict__ psi,
                                                       const AtomDev* __restrict__ atoms, int zsplit,
-                                                      double* __restrict__ t2g, int* __restrict__ status,
-                                                      int ndp) {
+                                                      double* __restrict__ t2g, int* __restrict__ status) {
   using BS = Basis<NU>;
   using SM = FfProjectSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -80,10 +62,6 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
   long long* xoff = reinterpret_cast<long long*>(phy + (size_t)NP * C);      // [C]
   int* yidx = reinterpret_cast<int*>(xoff + C);                              // [C] grid row of cube row
   int* zidx = yidx + C;                                                      // [C] grid plane of cube plane
-  double* phxd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(smem_raw) +
-                                           ((SM::bytes(C) - (size_t)C * NPX * 8 - (size_t)NP * C * 8)));  // [C][NPX]
-  double* phyd = phxd + (size_t)C * NPX;                                     // [NP][C]
-  const bool dp = (int)blockIdx.y >= (int)gridDim.y - ndp;  // this band tile runs on the FP64 pipe
 
   const int lane = threadIdx.x;
   const int a = blockIdx.z;
@@ -99,14 +77,12 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     for (int n = 0; n < NPX; n++) {
       const ff f = n < NP ? ff_from_double_exact(col[n]) : ff{0.0f, 0.0f};
       phx[i * NPX + n] = make_float2(f.hi, f.lo);
-      phxd[i * NPX + n] = n < NP ? col[n] : 0.0;
     }
     phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, col, 1);
 #pragma unroll
     for (int n = 0; n < NP; n++) {
       const ff f = ff_from_double_exact(col[n]);
       phy[n * C + i] = make_float2(f.hi, f.lo);
-      phyd[n * C + i] = col[n];
     }
     const int jx = cube_index(at.o[0], i, g.n[0], g.periodic);
     xoff[i] = jx < 0 ? -1ll : (long long)jx * B;
@@ -178,29 +154,7 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     // spherical support of the row: the points inside are the contiguous run [xlo, xhi) of the cube row
     int xlo = 0, xhi = 0;
     if (zidx[iz] >= 0 && yidx[iy] >= 0) support_run(row_support(g, at, iy, iz, lane), xlo, xhi);
-    if (xhi > xlo && dp) {
-      // FP64 tile: x-pass and y-pass with DFMA, the plane's sums kept as doubles in the pair registers
-      const double* st = reinterpret_cast<const double*>(ring + (size_t)(r % kFfStages) * C * kFfRowBytes);
-      double t1[NP];
-#pragma unroll
-      for (int n = 0; n < NP; n++) t1[n] = 0.0;
-#pragma unroll 4
-      for (int ix = xlo; ix < xhi; ix++) {
-        const double v = st[ix * 32 + lane];
-        const double* f = phxd + (size_t)ix * NPX;
-#pragma unroll
-        for (int n = 0; n < NP; n++) t1[n] = fma(v, f[n], t1[n]);
-      }
-#pragma unroll
-      for (int ny = 0; ny < NP; ny++) {
-        const double w = phyd[ny * C + iy];
-#pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++) {
-          const int p = BS::pair(nx, ny);
-          ff_set_bits(t2s[p], t2c[p], fma(t1[nx], w, ff_bits_d(t2s[p], t2c[p])));
-        }
-      }
-    } else if (xhi > xlo) {
+    if (xhi > xlo) {
       const double* st = reinterpret_cast<const double*>(ring + (size_t)(r % kFfStages) * C * kFfRowBytes);
       // x-pass (a3) as float-float dot products
       float S[NP], E[NP];
@@ -237,7 +191,7 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       if (bok) {
         double* out = t2g + ((size_t)a * C + iz) * P * B + b0 + lane;
 #pragma unroll
-        for (int p = 0; p < P; p++) out[(size_t)p * B] = dp ? ff_bits_d(t2s[p], t2c[p]) : ff_to_double(t2s[p], t2c[p]);
+        for (int p = 0; p < P; p++) out[(size_t)p * B] = ff_to_double(t2s[p], t2c[p]);
       }
 #pragma unroll
       for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
@@ -338,7 +292,7 @@ __global__ void __launch_bounds__(kWarp) k_project_ff_zpass(GridDev g, const Ato
 template <int NU>
 __global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tables, float2* __restrict__ txff,
                             float2* __restrict__ tyff, double* __restrict__ t2, long long t2_count,
-                            int* __restrict__ status, int nbands, int b_dp) {
+                            int* __restrict__ status) {
   constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
   const long long nx_total = (long long)natoms * cube * NPX;
   const long long ny_total = (long long)natoms * NP * cube;
@@ -360,7 +314,6 @@ __global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tab
   float2* t2f = reinterpret_cast<float2*>(t2);
   bool range_bad = false;  // a z-pass sum the float pairs cannot carry (coefficients out of range)
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < t2_count; i += stride) {
-    if ((int)(i % nbands) >= b_dp) continue;  // bands of the FP64 tiles keep their doubles
     const double v = t2[i];
     range_bad |= ff_out_of_range(v);
     const ff f = ff_from_double_exact(v);
@@ -398,8 +351,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
                                                                    const float2* __restrict__ tyff,
                                                                    const float2* __restrict__ txff,
                                                                    const float2* __restrict__ t2,
-                                                                   double* __restrict__ psi,
-                                                                   const double* __restrict__ tabd, int ndp) {
+                                                                   double* __restrict__ psi) {
   using BS = Basis<NU>;
   using SM = FfBlkSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -425,9 +377,6 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   const int b0 = blockIdx.y * kWarp;
   const bool bok = b0 + lane < B;
   const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
-  // FP64 tile: the y- and x-passes run natively on the FP64 pipe (tables staged as doubles [NP][C], the
-  // update kept as doubles in the pair accumulators), next to the float-float tiles of the launch
-  const bool dp = (int)blockIdx.y >= (int)gridDim.y - ndp;
   // Offsets of atom a's cube against this tile, wrapped into [0, N) on a periodic grid: r.y = cube
   // row of the tile's first row, r.z = cube point of its first x point, r.w = cube plane of z.  True
   // when the cube meets the tile's rows and x segment.  Computed once per (tile, atom) here, so the
@@ -465,17 +414,11 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
       cp8(dt2 + q, ok ? (const void*)(src_t2 + (size_t)p * B + bl) : (const void*)t2, ok ? 8 : 0);
     }
     float2* dx = reinterpret_cast<float2*>(dst + (size_t)P * 32 * 8);
+    const float2* src_x = txff + (size_t)a * C * NPX;
+    for (int q = tid; q < C * NPX; q += kFfRows * kWarp) cp8(dx + q, src_x + q, 8);
     float2* dy = reinterpret_cast<float2*>(dst + (size_t)P * 32 * 8 + (size_t)C * NPX * 8);
-    if (dp) {  // FP64 tables [NP][C] for x and y (8 bytes per entry, as the pairs)
-      const double* sx = tabd + (size_t)a * 2 * NP * C;
-      for (int q = tid; q < 2 * NP * C; q += kFfRows * kWarp)
-        cp8(q < NP * C ? (void*)(dx + q) : (void*)(dy + (q - NP * C)), sx + q, 8);
-    } else {
-      const float2* src_x = txff + (size_t)a * C * NPX;
-      for (int q = tid; q < C * NPX; q += kFfRows * kWarp) cp8(dx + q, src_x + q, 8);
-      const float2* src_y = tyff + (size_t)a * NP * C;
-      for (int q = tid; q < NP * C; q += kFfRows * kWarp) cp8(dy + q, src_y + q, 8);
-    }
+    const float2* src_y = tyff + (size_t)a * NP * C;
+    for (int q = tid; q < NP * C; q += kFfRows * kWarp) cp8(dy + q, src_y + q, 8);
   };
 
   // the plane's atoms that meet the tile, compacted in ascending order
@@ -530,46 +473,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     // spherical support of the row in cube x coordinates, [slo, shi) (the whole row without a sphere)
     int slo = 0, shi = C;
     if (g.r2max > 0.0) support_run(row_support(g, atoms[r.x], rowin ? iy : 0, r.w, lane), slo, shi);
-    if (rowin && shi > slo && dp) {
-      const double* txd = reinterpret_cast<const double*>(txs);  // [NP][C]
-      const double* tyd = reinterpret_cast<const double*>(tys);  // [NP][C]
-      double t1[NP];
-#pragma unroll
-      for (int n = 0; n < NP; n++) t1[n] = 0.0;
-#pragma unroll
-      for (int ny = 0; ny < NP; ny++) {
-        const double w = tyd[ny * C + iy];
-#pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++) {
-          t1[nx] = fma(reinterpret_cast<const double*>(t2s)[BS::pair(nx, ny) * 32 + lane], w, t1[nx]);
-        }
-      }
-      const int dx = r.z;
-      int r0a, r0b, r1a, r1b;
-      if (g.periodic) {
-        r0a = 0;
-        r0b = dx < C ? min(xend, C - dx) : 0;
-        r1a = Nx - dx;
-        r1b = min(xend, Nx - dx + C);
-      } else {
-        r0a = max(0, -dx);
-        r0b = min(xend, C - dx);
-        r1a = r1b = 0;
-      }
-      for (int run = 0; run < 2; run++) {
-        const int shift = run ? dx - Nx : dx;
-        const int xa = max(run ? max(r1a, r0b) : r0a, slo - shift), xb = min(run ? r1b : r0b, shi - shift);
-        for (int x = xa; x < xb; x++) {
-          const int ix = x + shift;
-          float2 acc = accw[x * kWarp + lane];
-          double v = ff_bits_d(acc.x, acc.y);
-#pragma unroll
-          for (int n = 0; n < NP; n++) v = fma(t1[n], txd[n * C + ix], v);
-          ff_set_bits(acc.x, acc.y, v);
-          accw[x * kWarp + lane] = acc;
-        }
-      }
-    } else if (rowin && shi > slo) {
+    if (rowin && shi > slo) {
       // y-pass as float-float dot steps
       float ys[NP], yc[NP];
 #pragma unroll
@@ -634,7 +538,7 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     for (int i = 0; i < 16; i++) {
       if (x0 + i < xend) {
         const float2 v = accw[(x0 + i) * kWarp + lane];
-        rowp[(size_t)(xs + x0 + i) * B] = pv[i] + (dp ? ff_bits_d(v.x, v.y) : ff_to_double(v.x, v.y));
+        rowp[(size_t)(xs + x0 + i) * B] = pv[i] + ff_to_double(v.x, v.y);
       }
     }
   }
@@ -650,8 +554,7 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   if (e != cudaSuccess) return e;
   const unsigned nbt = (unsigned)((p.g.nbands + kWarp - 1) / kWarp);
   kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
-      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status,
-      ff_fp64_tiles((int)nbt));
+      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.t2_only) return e;
   const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
@@ -675,7 +578,7 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   float2* tyff = txff + (size_t)p.natoms * p.g.cube * NPX;
   k_ff_tables<NU><<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, p.stream>>>(
       p.natoms, p.g.cube, static_cast<const double*>(p.tables), txff, tyff, static_cast<double*>(p.t2), t2_count,
-      p.status, p.g.nbands, ((p.g.nbands + kWarp - 1) / kWarp - ff_fp64_tiles((p.g.nbands + kWarp - 1) / kWarp)) * kWarp);
+      p.status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   auto kern = k_expand_blk_ff<NU>;
@@ -683,10 +586,9 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nseg = (p.g.n[0] + kFfXSeg - 1) / kFfXSeg, nyb = (p.g.n[1] + kFfRows - 1) / kFfRows;
-  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
-  kern<<<dim3((unsigned)nseg * nyb * p.g.n[2], nbt), kFfRows * kWarp, smem, p.stream>>>(
+  kern<<<dim3((unsigned)nseg * nyb * p.g.n[2], (p.g.nbands + kWarp - 1) / kWarp), kFfRows * kWarp, smem, p.stream>>>(
       p.g, p.atoms, p.plane_ptr, p.plane_atoms, tyff, txff, static_cast<const float2*>(p.t2),
-      static_cast<double*>(p.psi), static_cast<const double*>(p.tables), ff_fp64_tiles(nbt));
+      static_cast<double*>(p.psi));
   return cudaGetLastError();
 }
 

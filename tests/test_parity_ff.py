@@ -89,18 +89,3 @@ def test_ff_production_size_sampled():
     pts = np.random.default_rng(1).choice(out.shape[0], size=300, replace=False)
     ref_pts = oracle.expand_points(w.grid, w.h, w.periodic, pos, sig, w.numax, w.cube, c_in, pts)
     assert rel_norm(out[pts] - psi.reshape(-1, w.nbands)[pts], ref_pts) <= TOL_FP64
-
-
-@pytest.mark.parametrize("periodic", [True, False])
-@pytest.mark.parametrize("nbands,numax", [(128, 5), (100, 3), (256, 7)])
-def test_ff_fp64_band_tiles(periodic, nbands, numax):
-    """From four 32-band tiles up the last quarter of the band tiles runs its x- and y-passes on the FP64
-    pipe next to the float-float tiles (128 bands: tile 3; 100 bands: the ragged tile 3 of bands 96..99;
-    256 bands: tiles 6 and 7); every band meets the FP64 bar, and the FP64 tiles' results are the native
-    FP64 form's."""
-    rng = np.random.default_rng(640 + nbands + numax)
-    grid, h = (36, 40, 34), 0.2
-    pos, sig = workloads.random_atoms(rng, 4, tuple(n * h for n in grid), periodic, min_sep=1.0)
-    psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands))
-    c = rng.standard_normal((4, oracle.nstates(numax), nbands))
-    _check(grid, h, periodic, pos, sig, psi, c, numax, 32, forces=(nbands == 128))
