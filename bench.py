@@ -39,8 +39,8 @@ def _peaks():
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the dominant kernel of the default bench
-# step (k_expand_blk_ff<5>, 96^3 / 64 atoms / 128 bands); valid only while that kernel is unchanged.
-NCU_TRAFFIC = {"k_expand": 951.009536e6 + 841.406208e6}
+# step (96^3 / 64 atoms / 128 bands), keyed by the timed call; empty until a capture of the current kernel.
+NCU_TRAFFIC = {}
 
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
 # 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.

@@ -16,14 +16,16 @@ extern "C" {
 #endif
 
 /* Limit, in SM clock cycles, of every bounded wait the handle's kernels make on their own data pipeline
- * (the plane-sweep projection's mbarrier waits on its TMA row ring).  0 restores the default of about
+ * (the plane-sweep projection's mbarrier waits on its TMA row ring; the tensor-core expansions' waits on
+ * their bulk-copy staging and MMA commits).  0 restores the default of about
  * 2 s (4e9 cycles); a negative value returns SHO_ERR_ARG.  When a wait runs out the kernel records
  * SHO_ERR_TIMEOUT in the handle's status word, leaves its loop (its results are incomplete) and
  * returns; sho_sync then reports SHO_ERR_TIMEOUT. */
 int sho_fault_wait_limit(sho_handle* handle, long long cycles);
 
-/* Make the plane-sweep projection's producer warps issue only the first `rows` rows of each sweep (a
- * pipeline stage that never arrives), so that the consumers' bounded waits run out.  The producer
+/* Make the plane-sweep projection's producer warps issue only the first `rows` rows of each sweep, and
+ * the FP64-accurate tensor-core expansion stage the z-pass slices of only the first `rows` atoms of each
+ * tile (a pipeline stage that never arrives), so that the consumers' bounded waits run out.  Each kernel
  * still waits for the copies it did issue before it returns, so nothing is in flight when its block
  * exits.  A negative value restores normal operation. */
 int sho_fault_stop_rows(sho_handle* handle, int rows);

@@ -62,6 +62,8 @@ SIGNATURES = {
     # include/sho_selftest.h
     "sho_selftest_umma": (_I, [_I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(ctypes.c_float)]),
+    "sho_selftest_ozaki": (_I, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                ctypes.POINTER(ctypes.c_float)]),
     "sho_sync": (_I, [_VP]),
     "sho_last_cuda_error": (ctypes.c_char_p, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),

@@ -47,7 +47,8 @@ class Handle:
         N.check(N.lib().sho_sync(self._h), "sho_sync")
 
     def set_expand_kernel(self, kernel: str):
-        """sho_set_expand_kernel: "auto", "mma_sync" or "tcgen05" x-pass of the TF32 / BF16 expansions."""
+        """sho_set_expand_kernel: "auto", "mma_sync" or "tcgen05" x-pass of the TF32 / BF16 expansions
+        ("tcgen05" also selects the digit-sliced tensor-core x-pass of the FF64 expansion)."""
         N.check(N.lib().sho_set_expand_kernel(self._h, {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]),
                 "sho_set_expand_kernel")
 

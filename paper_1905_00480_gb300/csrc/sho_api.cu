@@ -478,6 +478,7 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
     cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
     cv.take(t2_bytes(natoms, cube, numax, nbands, tc));
     cv.take((size_t)natoms * cube * txm_bytes_per_point(numax));
+    if (coeff_dtype == SHO_F64) cv.take(oz_layout(natoms, cube, nbands).total);  // FP64-accurate form
   }
   return cv.off;
 }
@@ -877,6 +878,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   const size_t o_tab = cv.take((size_t)natoms * 2 * (numax + 1) * cube * tc);
   const size_t o_t2 = cv.take(t2_bytes(natoms, cube, numax, nbands, tc));
   const size_t o_txm = cv.take((size_t)natoms * cube * txm_bytes_per_point(numax));
+  const size_t o_oz = prec == SHO_P_FF64 ? cv.take(oz_layout(natoms, cube, nbands).total) : 0;
   SHO_TRY(begin_call(h, s));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[1].key != key) {
@@ -909,6 +911,8 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   L.tables = ws + o_tab;
   L.t2 = ws + o_t2;
   L.tables_xmajor = ws + o_txm;
+  if (prec == SHO_P_FF64) L.oz = ws + o_oz;
+  L.stop_stage = h->stop_rows;
   L.scale = alpha;
   if (nl) L.nl = *nl;
   L.kernel = h->expand_kernel;

@@ -581,6 +581,9 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
       p.status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // the x-pass on the tensor cores when chosen (kernel choice 2) and where it applies; by default the
+  // float-float block gather, which measures as fast on GB300 at a tenth of the error
+  if (p.kernel == 2 && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
   auto kern = k_expand_blk_ff<NU>;
   const size_t smem = FfBlkSmem<NU>::bytes(p.g.cube, p.max_plane);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -101,8 +101,27 @@ struct ExpandLaunch {
   int kernel = 0;           // FP32-class x-pass engine: 0 automatic, 1 warp-level mma.sync, 2 tcgen05
   long long wait_cycles = kDefaultWaitCycles;  // limit of the bounded waits (tcgen05 kernel)
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
+  void* oz = nullptr;       // FP64-accurate form on the tensor cores: oz_layout() workspace, may be null
+  int stop_stage = 0x7fffffff;  // fault injection: that kernel stages the z-pass slices of this many atoms
   cudaStream_t stream;
 };
+
+// Workspace of the FP64-accurate expansion on the tensor cores (sho_ozaki.cu), offsets in bytes from
+// ExpandLaunch::oz, each region 256-byte aligned: the digit tables of the x functions
+// [A][6 digits][2 state chunks][96 rows][4] floats, the per-atom power of two G_a [A], and the bound
+// max_y max_nx |T1[nx]| of each (atom, plane, band) [A][C][B] (floats).
+struct OzLayout {
+  size_t dtab, gpow, tmax, total;
+};
+inline OzLayout oz_layout(int natoms, int cube, int nbands) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  OzLayout L;
+  L.dtab = 0;
+  L.gpow = up((size_t)natoms * 6 * 2 * 96 * 4 * sizeof(float));
+  L.tmax = L.gpow + up((size_t)natoms * sizeof(float));
+  L.total = L.tmax + up((size_t)natoms * cube * (size_t)nbands * sizeof(float));
+  return L;
+}
 
 // Bytes per (atom, cube point) of ExpandLaunch::tables_xmajor, NPX = numax + 1 rounded up to 4: the
 // float-pair tables of the FP64-accurate form fit in 16 NPX; the FP32 x table with up to four
@@ -252,6 +271,10 @@ cudaError_t launch_expand_zpass_f32_tiled(const ExpandLaunch& p);  // T2 as [A][
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
 cudaError_t launch_project_ff(const ProjectLaunch& p);
 cudaError_t launch_expand_ff(const ExpandLaunch& p);
+// FP64-accurate expansion with the x-pass on the tensor cores (exact digit slices); the caller has run the
+// z-pass and k_ff_tables (T2 as float pairs, float-pair y tables at `tyff`)
+bool ozaki_expand_ok(const ExpandLaunch& p);
+cudaError_t launch_expand_ozaki(const ExpandLaunch& p, const void* tyff);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
 cudaError_t launch_expand_tc(const ExpandLaunch& p, sho_prec prec);
 // Streaming FP32-class kernels (cp.async row pipeline / block gather), used when rows of bands are

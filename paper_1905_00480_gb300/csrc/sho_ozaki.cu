@@ -1,0 +1,639 @@
+// sho_ozaki.cu -- FP64-accurate expansion (SHO_P_FF64) with the x-pass on the fifth-generation tensor
+// cores, by exact digit slicing of both operands.
+//
+//   psi[z][y][x][b] += sum_a sum_nx T1_a[y][b][nx] phi^a_nx(x)          (Sec. 3.2 step 3; eq. TuckerTensor)
+//
+// T1_a comes from the float-float y-pass of the FP64 z-pass result; the x-pass is, per grid row, a
+// product of a (bands x states) and a (states x points) matrix summed over the atoms.  On GB300 the FP64
+// pipe is slow and a float-float x-pass costs ten FP32 instructions per (atom, point, band, state), so
+// here the x-pass runs on the tensor cores with the splitting of Ozaki, Ogita, Oishi and Rump ("Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012), in the fixed-point form:
+//   * per (row, band) a power of two F above every covering atom's max_nx |T1_a[nx]| G_a (bounded ahead of
+//     the y-pass: an FP32 y-pass over all rows of each (atom, plane, band) with an error term), and per
+//     atom a power of two G_a above max |phi^a|;
+//   * T1_a[nx] G_a / F = sum_{i=1..6} d_i and phi^a_nx(x) / G_a = sum_{j=1..6} e_j, where d_i, e_j are
+//     signed integers times 2^(-8 i), 2^(-8 j) (round-to-nearest digits; at most 256 in magnitude for the
+//     first digit, 128 for the others, 256 for d_4 which also takes the low float of T1);
+//   * every product d_i e_j is an integer of at most 2^16 times 2^(-8 (i + j)), exact in the tensor
+//     core's FP32 products.  Products of level L = i + j = 2, 3, 4 go to one accumulator per level, where
+//     their sums stay integers below 2^24 and so are exact (at most 204 / (numax + 1) atoms per tile);
+//     levels 5 .. 8 share a fourth accumulator and round at 2^-24 of a term that is 2^-24 below the
+//     leading one; levels above 8 are dropped (below 2^-56 F per product);
+//   * the point's update is F (D_2 + D_3 + D_4 + D_5..8), summed as a float pair and added to psi in FP64.
+// The operands are TF32 (digits of at most 9 significant bits are exact in TF32), K = 8 states.
+//
+// A CTA owns a tile of one z plane: 2 grid rows x 32 x points x 128 bands, thread = (row, band).  Its
+// four level accumulators per row live in tensor memory (2 x 4 x 32 = 256 columns) for the whole atom
+// loop.  For each atom whose cube meets the tile (ascending order):
+//   * its T2 slice (float pairs) and y table are staged by bulk copies one atom ahead; its x digit table
+//     window for the tile's 32 points (six digits x two chunks of four states) is staged after the MMAs
+//     that last read the buffer;
+//   * each thread runs the float-float y-pass of its (row, band) and cuts T1 into six digit slices in
+//     registers, then (once the previous atom's MMAs are done) writes them as the A operands;
+//   * one thread issues 2 rows x 26 digit-pair MMAs (M = 128 bands, N = 32 points, K = 8) and commits them.
+// At the end each thread reads its row's four accumulators for its band, and adds the 32 points to psi.
+// Deterministic: fixed atom order, exact integer sums in the leading levels.  Every wait is bounded; on
+// expiry the kernel records kStatusTimeout, waits (bounded) for its own copies and MMAs, frees tensor
+// memory and returns without touching psi.
+#include "sho_device.cuh"
+#include "sho_ff.cuh"
+#include "sho_umma.cuh"
+
+namespace sho {
+
+constexpr int kOzRows = 2;                           // grid rows per tile
+constexpr int kOzX = 32;                             // x points per tile (the MMA N)
+constexpr int kOzBands = 128;                        // bands per tile (the MMA M)
+constexpr int kOzThreads = kOzRows * kOzBands;       // thread = (row, band)
+constexpr int kOzDigits = 6;                         // digits per operand value
+constexpr int kOzMaxLevel = 8;                       // digit pairs (i, j) with i + j <= 8 are multiplied
+constexpr int kOzGroups = 4;                         // accumulators: levels 2, 3, 4 and 5..8
+constexpr int kOzCols = kOzRows * kOzGroups * kOzX;  // tensor-memory columns: 256
+constexpr int kOzTabRows = 96;                       // rows of a digit table: cube point ix = row - 32
+constexpr uint32_t kOzA = kOzBands * 8 * 4;          // one A digit slice [128 bands][8 states] TF32: 4 KB
+constexpr uint32_t kOzAChunk = kOzBands * 16;        // its states 4..7 (the second core matrix along K)
+constexpr uint32_t kOzB = kOzX * 8 * 4;              // one B digit slice [32 points][8 states]: 1 KB
+constexpr uint32_t kOzBChunk = kOzX * 16;            // its states 4..7
+constexpr int kOzTabFloats = kOzDigits * 2 * kOzTabRows * 4;  // digit table of one atom
+
+// Atoms per tile that keep the levels 2..4 exact: the level-4 products (first digits up to 256, the others
+// up to 128) are at most 2 * 2^15 + 2^14 per state and atom, so (numax + 1) states x atoms x 2.5 * 2^15 <= 2^24.
+__host__ __device__ constexpr int oz_max_atoms(int numax) { return 2048 / (10 * (numax + 1)); }
+
+template <int NU>
+struct OzSmem {
+  static constexpr int NP = NU + 1, P = Basis<NU>::P;
+  static constexpr size_t kA = (size_t)kOzRows * kOzDigits * kOzA;  // A slices of both rows, one slot: 48 KB
+  static constexpr size_t kBs = (size_t)kOzDigits * kOzB;           // one digit window: 6 KB
+  // two operand slots (A, then B), the y values of the tile's atoms [atom][row][NP] float pairs, the
+  // exponents of their G_a [atom], barriers
+  __host__ __device__ static size_t off_b() { return 2 * kA; }
+  __host__ __device__ static size_t off_y() { return 2 * kA + 2 * kBs; }
+  __host__ __device__ static size_t off_e(int max_plane) { return off_y() + (size_t)max_plane * kOzRows * NP * 8; }
+  __host__ __device__ static size_t off_bar(int max_plane) {
+    return (off_e(max_plane) + (size_t)max_plane * 4 + 127) & ~(size_t)127;
+  }
+  static size_t bytes(int max_plane) { return off_bar(max_plane) + 128 + (size_t)(max_plane + 1) * sizeof(int4); }
+};
+
+// float 2^e for e in [-126, 127]
+__device__ __forceinline__ float oz_pow2(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Knuth's TwoSum: s + e = a + b exactly.
+__device__ __forceinline__ void oz_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Round r to the grid 2^(k - 23) with the constant 1.5 * 2^k (|r| <= 2^(k-1)): the digit, and r less it.
+__device__ __forceinline__ float oz_digit(float& r, float sigma) {
+  const float d = __fsub_rn(__fadd_rn(r, sigma), sigma);
+  r = __fsub_rn(r, d);
+  return d;
+}
+
+// ------------------------------------------------------------------------------------- tables
+// Blocks [0, A), one per atom: G_a = 2^e with max |phi_x| < 2^e, and the digit table of phi_x / G_a,
+// [6 digits][2 chunks][96 rows][4 states] with row = ix + 32 and zeros outside the cube and above numax
+// (from the FP64 tables [A][2][NP][C]).  The other blocks, one thread per (atom, plane, band): a bound of
+// max_y max_nx |T1[nx](y)| from the float-pair T2 and y tables, T1 summed in FP32 from the leading floats
+// plus 2^-20 sum |T2| |phi| for the dropped low parts and the FP32 rounding (at most (numax + 3) 2^-24 of
+// that sum), rounded up.
+template <int NU>
+__global__ void __launch_bounds__(128) k_oz_tables(int natoms, int cube, int nbands, const double* __restrict__ tables,
+                                                   const float2* __restrict__ t2, const float2* __restrict__ tyff,
+                                                   float* __restrict__ dtab, float* __restrict__ gpow,
+                                                   float* __restrict__ tmax) {
+  using BS = Basis<NU>;
+  constexpr int NP = NU + 1, P = BS::P;
+  const int tid = threadIdx.x, C = cube;
+  if ((int)blockIdx.x >= natoms) {
+    const long long i = (long long)(blockIdx.x - natoms) * 128 + tid;
+    if (i >= (long long)natoms * C * nbands) return;
+    const long long az = i / nbands, b = i - az * nbands;
+    const int a = (int)(az / C);
+    float t[P];
+#pragma unroll
+    for (int p = 0; p < P; p++) t[p] = t2[(az * P + p) * nbands + b].x;
+    const float2* ty = tyff + (size_t)a * NP * C;
+    float m = 0.0f;
+    for (int iy = 0; iy < C; iy++) {
+      float w[NP];
+#pragma unroll
+      for (int n = 0; n < NP; n++) w[n] = __ldg(&ty[n * C + iy].x);
+#pragma unroll
+      for (int nx = 0; nx < NP; nx++) {
+        float s = 0.0f, e = 0.0f;
+#pragma unroll
+        for (int ny = 0; nx + ny <= NU; ny++) {
+          s = fmaf(t[BS::pair(nx, ny)], w[ny], s);
+          e = fmaf(fabsf(t[BS::pair(nx, ny)]), fabsf(w[ny]), e);
+        }
+        m = fmaxf(m, fmaf(e, 0x1p-20f, fabsf(s)));
+      }
+    }
+    tmax[i] = m * (1.0f + 0x1p-20f);
+    return;
+  }
+  __shared__ double red[4];
+  const int a = blockIdx.x;
+  const double* tx = tables + (size_t)a * 2 * NP * C;
+  double m = 0.0;
+  for (int i = tid; i < NP * C; i += 128) m = fmax(m, fabs(tx[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  m = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+  int e = 0;
+  if (m > 0.0) (void)frexp(m, &e);  // m < 2^e
+  const double G = m > 0.0 ? ldexp(1.0, e) : 1.0;
+  if (tid == 0) gpow[a] = (float)G;
+  // one (chunk, row, state) entry per iteration, its six digits in one pass: v = phi / G (exact: a power of
+  // two), d_j = rint(v 2^(8j)) 2^(-8j), v -= d_j; every step is exact in FP64
+  float* dt = dtab + (size_t)a * kOzTabFloats;
+  const double ginv = 1.0 / G;
+  for (int idx = tid; idx < 2 * kOzTabRows * 4; idx += 128) {
+    const int q = idx & 3, row = (idx >> 2) % kOzTabRows, c = idx / (4 * kOzTabRows);
+    const int n = 4 * c + q, ix = row - 32;
+    double v = (n < NP && ix >= 0 && ix < C) ? tx[(size_t)n * C + ix] * ginv : 0.0;  // |v| < 1
+    double sc = 1.0, isc = 1.0;
+#pragma unroll
+    for (int j = 0; j < kOzDigits; j++) {
+      sc *= 256.0;
+      isc *= 0.00390625;
+      const double d = rint(v * sc) * isc;
+      v -= d;
+      dt[(size_t)j * 2 * kOzTabRows * 4 + idx] = (float)d;  // at most 256 (then 128) times 2^(-8 (j + 1))
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------- expansion
+template <int NU>
+__global__ void __launch_bounds__(kOzThreads, 2)
+    k_expand_ozaki(GridDev g, const AtomDev* __restrict__ atoms, const int* __restrict__ plane_ptr,
+                   const int* __restrict__ plane_atoms, int max_plane, const float2* __restrict__ tyff,
+                   const float2* __restrict__ t2, const float* __restrict__ dtab, const float* __restrict__ gpow,
+                   const float* __restrict__ tmax, double* __restrict__ psi, int* __restrict__ status,
+                   long long wait_cycles, int stop_stage) {
+  using BS = Basis<NU>;
+  using SM = OzSmem<NU>;
+  constexpr int NP = SM::NP, P = SM::P;
+  static_assert(NP <= 8, "a digit slice holds at most 8 states");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int C = g.cube, Nx = g.n[0], Ny = g.n[1], Nz = g.n[2], B = g.nbands;
+  const uint32_t sbase = um_smem(smem_raw);
+  const uint32_t sB = sbase + (uint32_t)SM::off_b();
+  float2* ylist = reinterpret_cast<float2*>(smem_raw + SM::off_y());  // [atom][row][NP]
+  int* gexp = reinterpret_cast<int*>(smem_raw + SM::off_e(max_plane));  // [atom] exponent of G_a
+  unsigned char* barp = smem_raw + SM::off_bar(max_plane);
+  const uint32_t cbar0 = um_smem(barp);  // MMA commits of operand slots 0 and 1
+  const uint32_t bbar0 = cbar0 + 16;     // digit-window staging of slots 0 and 1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 32);
+  int* s_misc = reinterpret_cast<int*>(barp + 48);  // [0] list length, [1..8] warp counts (bytes 48..83)
+  int4* slist = reinterpret_cast<int4*>(barp + 128);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rr = tid >> 7, bl = tid & 127;  // this thread's tile row and band
+
+  const int nseg = (Nx + kOzX - 1) / kOzX, nyb = (Ny + kOzRows - 1) / kOzRows;
+  int bid = blockIdx.x;
+  const int seg = bid % nseg;
+  bid /= nseg;
+  const int yb = bid % nyb;
+  const int z = bid / nyb;
+  const int xs = seg * kOzX;
+  const int b0 = blockIdx.y * kOzBands;
+  const int nb = min(kOzBands, B - b0);  // bands of this tile (an even count)
+  const int b = b0 + bl;
+  const bool bvalid = bl < nb;
+  const int y = yb * kOzRows + rr;
+  const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+
+  // atoms of the plane whose cube meets the tile, ascending: (atom, cube row of the tile's first row,
+  // cube-relative x offset, cube plane)
+  if (tid == 0) s_misc[0] = 0;
+  __syncthreads();
+  for (int base = q0; base < q1; base += kOzThreads) {
+    const int q = base + tid;
+    int4 r = make_int4(-1, 0, 0, 0);
+    bool m = false;
+    if (q < q1) {
+      const int a = plane_atoms[q];
+      const AtomDev at = atoms[a];
+      int dy = yb * kOzRows - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
+      if (g.periodic) {
+        dy %= Ny;
+        if (dy < 0) dy += Ny;
+        dx %= Nx;
+        if (dx < 0) dx += Nx;
+        dz %= Nz;
+        if (dz < 0) dz += Nz;
+        m = (dy < C || dy + kOzRows > Ny) && (dx < C || dx + kOzX > Nx);
+        if (dx >= C) dx -= Nx;  // the cube starts inside the tile (one run: Nx >= C + 32)
+      } else {
+        m = dy < C && dy + kOzRows > 0 && dx < C && dx + kOzX > 0;
+      }
+      r = make_int4(a, dy, dx, dz);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) s_misc[1 + warp] = __popc(bal);
+    __syncthreads();
+    int off = s_misc[0];
+    for (int w = 0; w < warp; w++) off += s_misc[1 + w];
+    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = r;
+    __syncthreads();
+    if (tid == 0)
+      for (int w = 0; w < kOzThreads / 32; w++) s_misc[0] += s_misc[1 + w];
+    __syncthreads();
+  }
+  const int nlist = s_misc[0];
+  if (nlist == 0) return;  // no cube meets the tile: psi is unchanged
+
+  // cube row of tile row `row` for list entry li, or -1 outside the cube or the grid
+  auto cube_row = [&](int li, int row) {
+    int iy = slist[li].y + row;
+    if (g.periodic && iy >= Ny) iy -= Ny;
+    return (yb * kOzRows + row < Ny && iy >= 0 && iy < C) ? iy : -1;
+  };
+  // the y functions of every listed atom at the tile's two rows (float pairs), and the tile's psi to L2
+  for (int i = tid; i < nlist * kOzRows * NP; i += kOzThreads) {
+    const int li = i / (kOzRows * NP), row = (i / NP) % kOzRows, n = i % NP;
+    const int iy = cube_row(li, row);
+    ylist[i] = iy >= 0 ? tyff[((size_t)slist[li].x * NP + n) * C + iy] : make_float2(0.0f, 0.0f);
+  }
+  for (int li = tid; li < nlist; li += kOzThreads)
+    gexp[li] = (int)((__float_as_uint(gpow[slist[li].x]) >> 23) & 0xffu) - 127;
+  if (tid < kOzRows * kOzX) {
+    const int row = tid >> 5, x = tid & 31, yy = yb * kOzRows + row;
+    if (yy < Ny && xs + x < Nx) {
+      const double* pp = psi + (((size_t)z * Ny + yy) * Nx + xs + x) * (size_t)B + b0;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(pp), "r"((uint32_t)(nb * 8)) : "memory");
+    }
+  }
+
+  // the frame F of this (row, band): a power of two above every covering atom's bound |T1_a| G_a
+  float xb = 0.0f;
+  if (bvalid && y < Ny) {
+    for (int l0 = 0; l0 < nlist; l0 += 4) {
+      float tv4[4], gv4[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int li = l0 + u;
+        const bool in = li < nlist && cube_row(li, rr) >= 0;
+        const int4 r = slist[min(li, nlist - 1)];
+        tv4[u] = in ? tmax[((size_t)r.x * C + r.w) * B + b] : 0.0f;
+        gv4[u] = in ? gpow[r.x] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) xb = fmaxf(xb, tv4[u] * gv4[u]);
+    }
+  }
+  int eF = 0;
+  if (xb > 0.0f) eF = (int)((__float_as_uint(xb * (1.0f + 0x1p-20f)) >> 23) & 0xffu) - 127 + 1;  // xb < 2^eF
+  const bool range_bad = eF > 127;  // the bound overflowed the float range
+  eF = max(-124, min(eF, 127));
+  const float F = oz_pow2(eF);
+
+  // tensor memory (zeroed), barriers
+  if (warp == 0) tmem_alloc(um_smem(tmem_slot), kOzCols);
+  if (tid == 0) {
+    um_mbar_init(cbar0);
+    um_mbar_init(cbar0 + 8);
+    um_mbar_init(bbar0);
+    um_mbar_init(bbar0 + 8);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // lanes of this warp's bands
+#pragma unroll
+  for (int c = 0; c < 4; c++) tmem_zero32(tlane + (uint32_t)(rr * kOzGroups * kOzX + 32 * c));
+
+  // digit window of atom li for the tile's 32 points into operand slot `slot` (one thread, bulk copies)
+  auto stage_b = [&](int li, int slot) {
+    const int4 r = slist[li];
+    const uint32_t dst = sB + (uint32_t)(slot * SM::kBs), bar = bbar0 + 8 * slot;
+    const float* src = dtab + (size_t)r.x * kOzTabFloats + (size_t)(r.z + 32) * 4;  // rows r.z + 32 ..
+    fence_async_smem();  // the slot's earlier use (by the tensor core, completed) comes before the copies
+    um_expect_tx(bar, (uint32_t)SM::kBs);
+#pragma unroll
+    for (int jc = 0; jc < 2 * kOzDigits; jc++)
+      um_bulk(dst + (uint32_t)(jc * kOzBChunk), src + (size_t)jc * kOzTabRows * 4, kOzBChunk, bar);
+  };
+
+  constexpr uint32_t idesc = umma_idesc(kUmmaTF32, kOzBands, kOzX);
+  // MMAs of atom li from operand slot `slot`: both rows, digit pairs (i, j) with i + j <= kOzMaxLevel
+  auto issue = [&](int slot) {
+    const uint32_t abase = sbase + (uint32_t)(slot * SM::kA), bbase = sB + (uint32_t)(slot * SM::kBs);
+    tc05_fence_after();
+#pragma unroll
+    for (int row = 0; row < kOzRows; row++)
+#pragma unroll
+      for (int i = 1; i <= kOzDigits; i++)
+#pragma unroll
+        for (int j = 1; j <= kOzDigits; j++) {
+          if (i + j > kOzMaxLevel) continue;
+          const int grp = (i + j < 5 ? i + j : 5) - 2;
+          const uint64_t ad = umma_desc(abase + (uint32_t)((row * kOzDigits + i - 1) * kOzA), kOzAChunk, 128);
+          const uint64_t bd = umma_desc(bbase + (uint32_t)((j - 1) * kOzB), kOzBChunk, 128);
+          umma_tf32(tmem + (uint32_t)((row * kOzGroups + grp) * kOzX), ad, bd, idesc, true);
+        }
+    umma_commit(cbar0 + 8 * slot);
+  };
+
+  // T2 of the current atom for this thread's band (float pairs), loaded one step ahead
+  float2 tv[P];
+  auto load_t2 = [&](int li) {
+    if (!bvalid || cube_row(li, rr) < 0) return;
+    const int4 r = slist[li];
+    const float2* src = t2 + ((size_t)r.x * C + r.w) * P * B + b;
+#pragma unroll
+    for (int p = 0; p < P; p++) tv[p] = src[(size_t)p * B];
+  };
+
+  bool ok = true;
+  int issued = 0;  // atoms whose MMAs are issued (uniform)
+  // digit windows staged (uniform); stop_stage < nlist only under fault injection: the windows from atom
+  // stop_stage on are never staged, so the waits for them run out
+  int bn = 0, loop_end = nlist;
+  load_t2(0);
+  for (int li = 0; li < nlist; li++) {
+    const int slot = li & 1;
+    // operand slot free: the MMAs of atom li - 2 are done; then stage this atom's digit window into it
+    if (li >= 2 && !um_mbar_wait(cbar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1), wait_cycles)) ok = false;
+    if (li < stop_stage) {
+      if (tid == 0) stage_b(li, slot);
+      bn = li + 1;
+    }
+    // y-pass of this (row, band) as float-float dot steps
+    const int iyr = cube_row(li, rr);
+    const bool yin = bvalid && iyr >= 0;
+    float ys[NP], yc[NP];
+#pragma unroll
+    for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
+    if (yin) {
+      const float2* yv = ylist + (li * kOzRows + rr) * NP;
+#pragma unroll
+      for (int ny = 0; ny < NP; ny++) {
+        const float2 w = yv[ny];
+#pragma unroll
+        for (int nx = 0; nx + ny <= NU; nx++)
+          ff_dot_step(ys[nx], yc[nx], ff{tv[BS::pair(nx, ny)].x, tv[BS::pair(nx, ny)].y}, ff{w.x, w.y});
+      }
+    }
+    if (li + 1 < nlist) load_t2(li + 1);  // in flight during the digits, the barrier and the next waits
+    // six digit slices of T1 G_a / F, written as the A operands of this row (two chunks of four states)
+    const int k = gexp[li] - eF;  // G_a / F = 2^k
+    const float sa = (k < -126 || !yin) ? 0.0f : oz_pow2(min(k, 127));
+    unsigned char* arow = smem_raw + (size_t)slot * SM::kA + (size_t)rr * kOzDigits * kOzA + (size_t)bl * 16;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+      float dg[kOzDigits][4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int n = 4 * c + q;
+        if (n < NP) {
+          const ff tt = ff_norm(ys[n], yc[n]);
+          float rem = __fmul_rn(tt.hi, sa);  // |rem| < 1
+          const float lo = __fmul_rn(tt.lo, sa);
+          dg[0][q] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
+          dg[1][q] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
+          dg[2][q] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
+          rem = __fadd_rn(rem, lo);
+          dg[3][q] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
+          dg[4][q] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
+          dg[5][q] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
+        } else {
+#pragma unroll
+          for (int i = 0; i < kOzDigits; i++) dg[i][q] = 0.0f;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kOzDigits; i++)
+        *reinterpret_cast<float4*>(arow + i * kOzA + c * kOzAChunk) = make_float4(dg[i][0], dg[i][1], dg[i][2], dg[i][3]);
+    }
+    fence_async_smem();  // the A slices become visible to the tensor core
+    // this atom's digit window has landed
+    if (!um_mbar_wait(bbar0 + 8 * slot, (uint32_t)((li >> 1) & 1), wait_cycles)) ok = false;
+    tc05_fence_before();
+    // a wait that ran out in any thread ends the loop for all
+    if (!__syncthreads_and(ok)) {
+      loop_end = li;
+      break;
+    }
+    if (tid == 0) issue(slot);
+    issued = li + 1;
+  }
+  const int last = issued - 1;  // the last commit covers every MMA issued before it
+  bool done = loop_end == nlist && last >= 0 &&
+              um_mbar_wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), wait_cycles);
+  done = __syncthreads_and(done);
+  // copies issued and not yet seen complete (at most the last fill of each slot) complete whatever else
+  // happens: wait for them with the default limit before the CTA's shared memory is released
+  for (int q = max(0, bn - 2); q < bn; q++)
+    (void)um_mbar_wait(bbar0 + 8 * (q & 1), (uint32_t)((q >> 1) & 1), kDefaultWaitCycles);
+  if (!done) {
+    if (tid == 0 && status) atomicOr(status, kStatusTimeout);
+    if (last >= 0) (void)um_mbar_wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), kDefaultWaitCycles);
+  }
+  tc05_fence_after();
+  if (done) {
+    const bool wr = bvalid && y < Ny;
+    const int xend = min(kOzX, Nx - xs);
+    double* rowp = psi + (((size_t)z * Ny + (wr ? y : 0)) * Nx + xs) * (size_t)B + b;
+    const uint32_t tcol = tlane + (uint32_t)(rr * kOzGroups * kOzX);
+#pragma unroll 1
+    for (int x0 = 0; x0 < kOzX; x0 += 8) {
+      float d[32];  // d[8 g + k]: level accumulator g of point x0 + k
+      tmem_ld8x4(tcol + (uint32_t)x0, tcol + (uint32_t)(kOzX + x0), tcol + (uint32_t)(2 * kOzX + x0),
+                 tcol + (uint32_t)(3 * kOzX + x0), d);
+      if (wr) {
+        double pv[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) pv[k] = x0 + k < xend ? rowp[(size_t)(x0 + k) * B] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          if (x0 + k < xend) {
+            float s, e1, e2;
+            oz_two_sum(d[k], d[8 + k], s, e1);
+            oz_two_sum(s, d[16 + k], s, e2);
+            const float c = __fadd_rn(__fadd_rn(e1, e2), d[24 + k]);
+            rowp[(size_t)(x0 + k) * B] = pv[k] + ff_to_double(__fmul_rn(s, F), __fmul_rn(c, F));
+          }
+        }
+      }
+    }
+  }
+  tc05_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kOzCols);
+  if (range_bad && status) atomicOr(status, kStatusRange);
+}
+
+// The kernel's MMA schedule on host digits: A [6][128][8] and B [6][32][8] (digit values), D [4][128][32]
+// the four level accumulators (test of the operand layouts and of the exactness of the level sums).
+__global__ void __launch_bounds__(128) k_oz_selftest(const float* __restrict__ A, const float* __restrict__ Bm,
+                                                     float* __restrict__ D, int* __restrict__ status) {
+  __shared__ __align__(1024) unsigned char sm[kOzDigits * kOzA + kOzDigits * kOzB];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < kOzDigits * kOzBands * 8; i += 128) {
+    const int s = i / (kOzBands * 8), m = (i / 8) % kOzBands, k = i % 8;
+    *reinterpret_cast<float*>(sm + s * kOzA + (k / 4) * kOzAChunk + m * 16 + (k % 4) * 4) = A[i];
+  }
+  for (int i = tid; i < kOzDigits * kOzX * 8; i += 128) {
+    const int s = i / (kOzX * 8), n = (i / 8) % kOzX, k = i % 8;
+    *reinterpret_cast<float*>(sm + kOzDigits * kOzA + s * kOzB + (k / 4) * kOzBChunk + n * 16 + (k % 4) * 4) = Bm[i];
+  }
+  if (warp == 0) tmem_alloc(um_smem(&tslot), kOzGroups * kOzX);
+  if (tid == 0) {
+    um_mbar_init(um_smem(&bar));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  fence_async_smem();
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+  for (int c = 0; c < kOzGroups; c++) tmem_zero32(tlane + (uint32_t)(32 * c));
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  if (tid == 0) {
+    constexpr uint32_t idesc = umma_idesc(kUmmaTF32, kOzBands, kOzX);
+    const uint32_t sa = um_smem(sm), sb = sa + kOzDigits * kOzA;
+    for (int i = 1; i <= kOzDigits; i++)
+      for (int j = 1; j <= kOzDigits; j++) {
+        if (i + j > kOzMaxLevel) continue;
+        const int grp = (i + j < 5 ? i + j : 5) - 2;
+        umma_tf32(tmem + (uint32_t)(grp * kOzX), umma_desc(sa + (uint32_t)((i - 1) * kOzA), kOzAChunk, 128),
+                  umma_desc(sb + (uint32_t)((j - 1) * kOzB), kOzBChunk, 128), idesc, true);
+      }
+    umma_commit(um_smem(&bar));
+  }
+  const bool done = um_mbar_wait(um_smem(&bar), 0, 2000000000ll);
+  if (!done && tid == 0) atomicOr(status, kStatusTimeout);
+  if (!done) (void)um_mbar_wait(um_smem(&bar), 0, kDefaultWaitCycles);
+  tc05_fence_after();
+  for (int c = 0; c < kOzGroups; c++) {
+    float v[32];
+    tmem_ld32(tlane + (uint32_t)(32 * c), v);
+#pragma unroll
+    for (int x = 0; x < 32; x++) D[((size_t)c * kOzBands + 32 * warp + lane) * kOzX + x] = done ? v[x] : 0.0f;
+  }
+  tc05_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kOzGroups * kOzX);
+}
+
+// ------------------------------------------------------------------------------------ launchers
+template <int NU>
+static cudaError_t ozaki_nu(const ExpandLaunch& p, const void* tyff) {
+  if constexpr (NU > 7) {
+    return cudaErrorNotSupported;
+  } else {
+    const OzLayout L = oz_layout(p.natoms, p.g.cube, p.g.nbands);
+    char* ws = static_cast<char*>(p.oz);
+    float* dtab = reinterpret_cast<float*>(ws + L.dtab);
+    float* gpow = reinterpret_cast<float*>(ws + L.gpow);
+    float* tmax = reinterpret_cast<float*>(ws + L.tmax);
+    const long long nbound = (long long)p.natoms * p.g.cube * p.g.nbands;
+    k_oz_tables<NU><<<(unsigned)(p.natoms + (nbound + 127) / 128), 128, 0, p.stream>>>(
+        p.natoms, p.g.cube, p.g.nbands, static_cast<const double*>(p.tables), static_cast<const float2*>(p.t2),
+        static_cast<const float2*>(tyff), dtab, gpow, tmax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = OzSmem<NU>::bytes(p.max_plane);
+    auto kern = k_expand_ozaki<NU>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nseg = (p.g.n[0] + kOzX - 1) / kOzX, nyb = (p.g.n[1] + kOzRows - 1) / kOzRows;
+    const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
+    kern<<<dim3(nblk, (p.g.nbands + kOzBands - 1) / kOzBands), kOzThreads, smem, p.stream>>>(
+        p.g, p.atoms, p.plane_ptr, p.plane_atoms, p.max_plane, static_cast<const float2*>(tyff),
+        static_cast<const float2*>(p.t2),
+        dtab, gpow, tmax, static_cast<double*>(p.psi), p.status, p.wait_cycles, p.stop_stage);
+    return cudaGetLastError();
+  }
+}
+
+// The tensor-core form covers numax <= 7 (K = 8 states), cubes of at most 32 points (even), one run of
+// cube points per tile row (a periodic grid of at least cube + 32 points along x), no spherical support,
+// an even band count (16-byte rows of float pairs), at most oz_max_atoms(numax) atoms per plane, and the
+// shared memory of one CTA.
+bool ozaki_expand_ok(const ExpandLaunch& p) {
+  if (!p.oz || p.numax > 7 || p.g.r2max > 0.0) return false;
+  if (p.g.cube > 32 || (p.g.cube & 1) || (p.g.nbands & 1)) return false;
+  if (p.g.periodic && p.g.n[0] < p.g.cube + kOzX) return false;
+  if (p.max_plane > oz_max_atoms(p.numax)) return false;
+  size_t smem = 0;
+  switch (p.numax) {
+    case 0: smem = OzSmem<0>::bytes(p.max_plane); break;
+    case 1: smem = OzSmem<1>::bytes(p.max_plane); break;
+    case 2: smem = OzSmem<2>::bytes(p.max_plane); break;
+    case 3: smem = OzSmem<3>::bytes(p.max_plane); break;
+    case 4: smem = OzSmem<4>::bytes(p.max_plane); break;
+    case 5: smem = OzSmem<5>::bytes(p.max_plane); break;
+    case 6: smem = OzSmem<6>::bytes(p.max_plane); break;
+    default: smem = OzSmem<7>::bytes(p.max_plane); break;
+  }
+  return smem <= 227 * 1024;
+}
+
+cudaError_t launch_expand_ozaki(const ExpandLaunch& p, const void* tyff) {
+  switch (p.numax) {
+    case 0: return ozaki_nu<0>(p, tyff);
+    case 1: return ozaki_nu<1>(p, tyff);
+    case 2: return ozaki_nu<2>(p, tyff);
+    case 3: return ozaki_nu<3>(p, tyff);
+    case 4: return ozaki_nu<4>(p, tyff);
+    case 5: return ozaki_nu<5>(p, tyff);
+    case 6: return ozaki_nu<6>(p, tyff);
+    case 7: return ozaki_nu<7>(p, tyff);
+    default: return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace sho
+
+using namespace sho;
+
+extern "C" int sho_selftest_ozaki(const float* A, const float* Bm, float* D) {
+  if (!A || !Bm || !D) return SHO_ERR_ARG;
+  const size_t na = (size_t)kOzDigits * kOzBands * 8, nbm = (size_t)kOzDigits * kOzX * 8;
+  const size_t nd = (size_t)kOzGroups * kOzBands * kOzX;
+  float *dA = nullptr, *dB = nullptr, *dD = nullptr;
+  int* dst = nullptr;
+  int st = SHO_OK;
+  if (cudaMalloc(&dA, sizeof(float) * na) != cudaSuccess || cudaMalloc(&dB, sizeof(float) * nbm) != cudaSuccess ||
+      cudaMalloc(&dD, sizeof(float) * nd) != cudaSuccess || cudaMalloc(&dst, sizeof(int)) != cudaSuccess) {
+    st = SHO_ERR_OOM;
+  } else if (cudaMemcpy(dA, A, sizeof(float) * na, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(dB, Bm, sizeof(float) * nbm, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemset(dst, 0, sizeof(int)) != cudaSuccess) {
+    st = SHO_ERR_CUDA;
+  } else {
+    k_oz_selftest<<<1, 128>>>(dA, dB, dD, dst);
+    int flag = 0;
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(D, dD, sizeof(float) * nd, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&flag, dst, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = SHO_ERR_CUDA;
+    else if (flag)
+      st = SHO_ERR_TIMEOUT;
+  }
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dD);
+  cudaFree(dst);
+  cudaGetLastError();
+  return st;
+}

@@ -31,38 +31,6 @@ constexpr int kUmThreads = 256;
 constexpr int kUmCols = kUmRows * kUmX;  // tensor-memory columns: 8 accumulators of 32 columns
 constexpr int kUmKBytes = 32;    // bytes per operand row: 8 TF32 or 16 BF16 values
 
-__device__ __forceinline__ uint32_t um_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-// Untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on `bar`.
-__device__ __forceinline__ void um_bulk(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void um_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void um_mbar_init(uint32_t bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool um_mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
-// Wait for the phase of `parity` of a commit barrier; false after `limit` SM clock cycles.
-__device__ __forceinline__ bool um_mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
-  if (um_mbar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!um_mbar_try(bar, parity))
-    if (clock64() - t0 > limit) return false;
-  return true;
-}
-
 template <int NU>
 struct UmSmem {
   static constexpr int NP = NU + 1, P = Basis<NU>::P, PP = tiled_pairs(P), NPX = (NP + 3) & ~3;
