@@ -39,8 +39,8 @@ def _peaks():
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the dominant kernel of the default bench
-# step (96^3 / 64 atoms / 128 bands), keyed by the timed call; empty until a capture of the current kernel.
-NCU_TRAFFIC = {}
+# step (k_expand_blk_ff<5>, 96^3 / 64 atoms / 128 bands); valid only while that kernel is unchanged.
+NCU_TRAFFIC = {"k_expand": 950.974208e6 + 844.720640e6}
 
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
 # 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.
@@ -161,10 +161,14 @@ def max_over_ranks(ws, value):
     return float(t.item())
 
 
-def launches_per_step(api, psi, w, prec):
+def launches_per_step(api, psi, w, prec, expand_kernel="auto"):
     """Kernels of this library that one project + expand step launches (mirrors the library's dispatch)."""
     if prec == "ff64":
-        return 2 + 3  # x/y-pass + z-pass kernels; z-pass tables, float-pair tables, block gather
+        oz = (expand_kernel == "tcgen05" and w.numax <= 7 and w.cube <= 32 and w.cube % 2 == 0
+              and w.nbands % 2 == 0 and (not w.periodic or w.grid[0] >= w.cube + 32))
+        # x/y-pass + z-pass kernels; z-pass tables, float-pair tables, then the block gather, or the digit
+        # tables and the tensor-core x-pass
+        return 2 + (4 if oz else 3)
     if prec == "fp64":
         return 1 + 2  # cluster projection; z-pass + row gather
     tc = prec in ("tf32", "3xtf32", "bf16", "split_fp16")
@@ -201,6 +205,8 @@ def run_ours(args, ws, rank, local):
     hpsi = torch.zeros_like(psi)
     coeff = torch.empty((w.natoms, nst, w.nbands), dtype=cdt, device=dev)
     handle = api.Handle(local)
+    if args.expand_kernel != "auto":
+        handle.set_expand_kernel(args.expand_kernel)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -396,7 +402,7 @@ def run_ours(args, ws, rank, local):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64": "f64", "ff64": "f64 storage, f32x2 x-pass", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
+            "dtype": {"fp64": "f64", "ff64": "f64 (float-float x/y-passes)", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
                       "split_fp16": "split-f16"}[prec],
             "data": "synthetic (seeded N(0,1) psi and coefficients, uniform atoms with min separation 2.0)",
             "config": {
@@ -406,6 +412,7 @@ def run_ours(args, ws, rank, local):
                 "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                 "l2": f"inputs larger than L2 (psi {psi.numel() * psi.element_size() / 1e6:.0f} MB per buffer), "
                       "no flush",
+                **({"expand_kernel": args.expand_kernel} if args.expand_kernel != "auto" else {}),
                 "union_cube_points": alg["union_points"],
                 "algorithmic_bytes_per_step": bytes_step,
             },
@@ -420,7 +427,7 @@ def run_ours(args, ws, rank, local):
                     "ms_per_step_windows": [round(v, 4) for v in e2e_runs],
                     "copy_floor_ms_per_step": round(ms_copy, 4),
                     "copy_floor_note": "the same host<->device copies on the same streams without kernels"},
-            "gpu_launches": launches_per_step(api, psi, w, prec) * K,
+            "gpu_launches": launches_per_step(api, psi, w, prec, args.expand_kernel) * K,
             "clocks": clk,
             "paper_protocol": {"ms_per_step": round(ms_paper, 4),
                                "value": round(ws * bytes_step / (ms_paper * 1e-3) / 1e9, 3), "unit": "GB/s",
@@ -1240,6 +1247,9 @@ def main():
                     help="time SHO against stored projectors on the paper's fcc benchmark system and exit")
     ap.add_argument("--table-reps", type=int, default=10)
     ap.add_argument("--table-runs", type=int, default=3)
+    ap.add_argument("--expand-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
+                    help="x-pass engine of the expansion (sho_set_expand_kernel); tcgen05 also selects the "
+                         "digit-sliced tensor-core x-pass of the FF64 form")
     ap.add_argument("--table-sphere", type=float, default=3.55,
                     help="projection sphere radius in Angstrom for --paper-table1 (0: whole cube)")
     args = ap.parse_args()

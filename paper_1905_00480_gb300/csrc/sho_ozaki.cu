@@ -25,13 +25,15 @@
 //
 // A CTA owns a tile of one z plane: 2 grid rows x 32 x points x 128 bands, thread = (row, band).  Its
 // four level accumulators per row live in tensor memory (2 x 4 x 32 = 256 columns) for the whole atom
-// loop.  For each atom whose cube meets the tile (ascending order):
-//   * its T2 slice (float pairs) and y table are staged by bulk copies one atom ahead; its x digit table
-//     window for the tile's 32 points (six digits x two chunks of four states) is staged after the MMAs
-//     that last read the buffer;
-//   * each thread runs the float-float y-pass of its (row, band) and cuts T1 into six digit slices in
-//     registers, then (once the previous atom's MMAs are done) writes them as the A operands;
-//   * one thread issues 2 rows x 26 digit-pair MMAs (M = 128 bands, N = 32 points, K = 8) and commits them.
+// loop.  The y functions of the listed atoms at the tile's two rows are gathered into shared memory once.
+// For each atom whose cube meets the tile (ascending order), with two operand slots used by atom parity:
+//   * once the MMAs of atom li - 2 are done, one thread stages the atom's x digit window for the tile's
+//     32 points (six digits x two chunks of four states) into the slot by bulk copies;
+//   * each thread runs the float-float y-pass of its (row, band) on its band's T2 slice (float pairs,
+//     loaded from global memory one atom ahead), cuts T1 into six digit slices and writes them into the
+//     slot as the A operands;
+//   * after one block barrier, one thread issues 2 rows x 26 digit-pair MMAs (M = 128 bands, N = 32
+//     points, K = 8) from the slot and commits them to the slot's barrier.
 // At the end each thread reads its row's four accumulators for its band, and adds the 32 points to psi.
 // Deterministic: fixed atom order, exact integer sums in the leading levels.  Every wait is bounded; on
 // expiry the kernel records kStatusTimeout, waits (bounded) for its own copies and MMAs, frees tensor
