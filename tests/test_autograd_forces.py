@@ -115,6 +115,15 @@ def test_backward_runs_only_library_kernels():
     c = sho_project(psi, X, torch.from_numpy(sig), numax, cube, h, True, prec="fp64")
     g = torch.from_numpy(rng.standard_normal(tuple(c.shape))).cuda()
     torch.cuda.synchronize()
+    # one backward inside an NVTX range, outside the torch profiler, so that an ncu launch list can be
+    # restricted to it (ncu --nvtx --nvtx-include "sho_autograd_backward/") where the torch profiler
+    # records nothing
+    torch.cuda.nvtx.range_push("sho_autograd_backward")
+    gpsi, gX = torch.autograd.grad(c, (psi, X), grad_outputs=g, retain_graph=True)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    ref = h ** 3 * oracle.add(grid, h, True, np.zeros((32, 32, 32, 8)), pos, sig, numax, cube, g.cpu().numpy())
+    assert np.linalg.norm(gpsi.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-12
     try:
         from torch.profiler import ProfilerActivity, profile
         with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as prof:
