@@ -150,6 +150,16 @@ int sho_set_support_radius(sho_handle* handle, double rprj);
 typedef enum { SHO_KERNEL_AUTO = 0, SHO_KERNEL_MMA_SYNC = 1, SHO_KERNEL_TCGEN05 = 2 } sho_kernel;
 int sho_set_expand_kernel(sho_handle* handle, int kernel);
 
+/* Debug mode (on != 0; off by default): the handle's SHO_P_FP64 and SHO_P_FF64 projection, expansion and
+ * forces kernels (the FP64 per-atom projection and row-gather expansion, the float-float projection and
+ * block-gather expansion) check every global index of psi, of the coefficients and of their z-pass /
+ * per-plane intermediate against the buffer's extent before the access.  An index outside skips the
+ * access and latches SHO_ERR_DEVICE, returned by the next sho_sync (a stand-in for an out-of-bounds
+ * access that a memory checker would report).  The checked kernels are separate instantiations: with
+ * the mode off nothing is checked and nothing is slower.  The z-pass, table, tensor-core, FP32-class,
+ * Bloch and serving kernels are not checked.  SHO_ERR_ARG for a null handle. */
+int sho_set_device_checks(sho_handle* handle, int on);
+
 /* Block until the handle's enqueued work is complete; return the first device-side error since the
  * previous sho_sync (SHO_ERR_TIMEOUT when a kernel's bounded wait on its own data pipeline expired --
  * its results are then incomplete; SHO_ERR_DEVICE when an SHO_P_FF64 input lay outside its range) or a

@@ -30,6 +30,11 @@ int sho_fault_wait_limit(sho_handle* handle, long long cycles);
  * exits.  A negative value restores normal operation. */
 int sho_fault_stop_rows(sho_handle* handle, int rows);
 
+/* Make the device checks (sho_set_device_checks) take psi's extent as at most `psi_elems` elements, so
+ * that indices at and above it count as out of bounds while every access stays inside the real buffer
+ * (the checked access is skipped).  A negative value restores the real extent. */
+int sho_fault_check_extent(sho_handle* handle, long long psi_elems);
+
 /* Apply sho_fault_wait_limit(cycles) and sho_fault_stop_rows(rows) to every execution slot of a server
  * (its requests' kernels), so that served requests meet the same injected pipeline failure. */
 int sho_fault_server_pipeline(sho_server* server, long long cycles, int rows);

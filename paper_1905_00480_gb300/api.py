@@ -52,6 +52,10 @@ class Handle:
         N.check(N.lib().sho_set_expand_kernel(self._h, {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]),
                 "sho_set_expand_kernel")
 
+    def set_device_checks(self, on: bool = True):
+        """sho_set_device_checks: the FP64 / FF64 kernels check every psi, coefficient and intermediate index."""
+        N.check(N.lib().sho_set_device_checks(self._h, 1 if on else 0), "sho_set_device_checks")
+
     def set_support_radius(self, rprj: float):
         """sho_set_support_radius: spherical projector support of radius rprj (0 = the whole cube)."""
         N.check(N.lib().sho_set_support_radius(self._h, float(rprj)), "sho_set_support_radius")

@@ -26,6 +26,8 @@ struct sho_handle {
   int stop_rows = 0x7fffffff;                       // fault injection: rows a plane-sweep producer issues
   double rprj = 0.0;                                // spherical support radius (0: the whole cube)
   int expand_kernel = SHO_KERNEL_AUTO;              // x-pass engine of the FP32-class expansion
+  bool dev_checks = false;                          // device checks of the FP64 / FF64 kernels' indices
+  long long check_psi_cap = -1;                     // fault injection: psi extent the checks assume (-1: real)
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
   struct RadialDev {
     void* mem = nullptr;
@@ -503,6 +505,18 @@ size_t handle_workspace(const sho_handle* h) { return h->ws_bytes; }
 
 int choose_zsplit(int natoms, int nbands, int cube, int sms) { return zsplit_balanced(natoms, nbands, cube, sms); }
 
+// Extents for the device checks of a call (sho_set_device_checks); checks off: flag null.
+DevCheck make_check(const sho_handle* h, const sho_grid* grid, int nbands, int natoms, int numax, int cube) {
+  DevCheck d;
+  if (!h->dev_checks) return d;
+  d.psi_n = (long long)grid->n[0] * grid->n[1] * grid->n[2] * nbands;
+  if (h->check_psi_cap >= 0 && h->check_psi_cap < d.psi_n) d.psi_n = h->check_psi_cap;
+  d.coeff_n = (long long)natoms * nstates(numax) * nbands;
+  d.t2_n = (long long)natoms * cube * npairs(numax) * nbands;
+  d.flag = h->dstatus;
+  return d;
+}
+
 int handle_take_status(sho_handle* h) {
   DeviceGuard guard(h->device);
   int flag = 0;
@@ -820,6 +834,7 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   L.t2 = ff_t2 ? t2_out : h->ws;
   L.t2_only = ff_t2;
   L.status = h->dstatus;
+  L.chk = make_check(h, grid, nbands, natoms, numax, cube);
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
                         : prec == SHO_P_FF64 ? launch_project_ff(L)
@@ -913,6 +928,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   L.tables_xmajor = ws + o_txm;
   if (prec == SHO_P_FF64) L.oz = ws + o_oz;
   L.stop_stage = h->stop_rows;
+  L.chk = make_check(h, grid, nbands, natoms, numax, cube);
   L.scale = alpha;
   if (nl) L.nl = *nl;
   L.kernel = h->expand_kernel;
@@ -992,6 +1008,7 @@ int sho_forces(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype p
   P.coeff_dtype = coeff_dtype;
   P.t2 = prec == SHO_P_FF64 ? ws + o_ft2 : nullptr;
   P.status = h->dstatus;
+  P.chk = make_check(h, grid, nbands, natoms, numax + 1, cube);
   P.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(P)
                         : prec == SHO_P_FF64 ? launch_project_ff(P)
@@ -1174,6 +1191,12 @@ int sho_set_expand_kernel(sho_handle* h, int kernel) {
   return SHO_OK;
 }
 
+int sho_set_device_checks(sho_handle* h, int on) {
+  if (!h) return SHO_ERR_ARG;
+  h->dev_checks = on != 0;
+  return SHO_OK;
+}
+
 int sho_set_support_radius(sho_handle* h, double rprj) {
   if (!h || !std::isfinite(rprj) || rprj < 0.0) return SHO_ERR_ARG;
   h->rprj = rprj;
@@ -1190,6 +1213,12 @@ int sho_fault_wait_limit(sho_handle* h, long long cycles) {
 int sho_fault_stop_rows(sho_handle* h, int rows) {
   if (!h) return SHO_ERR_ARG;
   h->stop_rows = rows < 0 ? 0x7fffffff : rows;
+  return SHO_OK;
+}
+
+int sho_fault_check_extent(sho_handle* h, long long psi_elems) {
+  if (!h) return SHO_ERR_ARG;
+  h->check_psi_cap = psi_elems < 0 ? -1 : psi_elems;
   return SHO_OK;
 }
 

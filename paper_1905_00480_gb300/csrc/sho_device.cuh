@@ -9,6 +9,19 @@
 
 namespace sho {
 
+// Device checks: true when 0 <= i < n; otherwise sets kStatusBounds in *flag and returns false, and the
+// caller skips the access.  Compiled to `true` in the unchecked kernels.
+template <bool CHK>
+__device__ __forceinline__ bool dc_ok(long long i, long long n, int* flag) {
+  if constexpr (!CHK) {
+    return true;
+  } else {
+    if ((unsigned long long)i < (unsigned long long)n) return true;
+    atomicOr(flag, kStatusBounds);
+    return false;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Compile-time basis bookkeeping for numax NU (eq. SHO-basis / SHO_basis_size, Sec. 2.5).
 //   pairs (nx, ny) with nx + ny <= NU: ny outer, nx inner

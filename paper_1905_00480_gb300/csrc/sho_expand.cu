@@ -214,12 +214,13 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
 
 // ------------------------------------------------------------------------------ kernel 2: rows
 // SPH: spherical support (one support mask per atom row), compiled separately from the cube form.
-template <int NU, typename TP, typename TC, bool SPH = false>
+// CHK: device checks of every psi and z-pass-result index (sho_set_device_checks), a separate instantiation.
+template <int NU, typename TP, typename TC, bool SPH = false, bool CHK = false>
 __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev* __restrict__ atoms,
                                                        const int* __restrict__ plane_ptr,
                                                        const int* __restrict__ plane_atoms,
                                                        const TC* __restrict__ tables, const TC* __restrict__ t2,
-                                                       TP* __restrict__ psi) {
+                                                       TP* __restrict__ psi, DevCheck dc) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -247,8 +248,11 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
   }
   if (!any) return;
 
-  TP* row = psi + (size_t)r * Nx * B + b;
-  for (int jx = 0; jx < Nx; jx++) acc[jx * kWarp + lane] = bok ? to_real(row[(size_t)jx * B], (TC)0) : (TC)0;
+  const long long row0 = (long long)r * Nx * B + b;  // psi index of this row's x = 0
+  TP* row = psi + row0;
+  for (int jx = 0; jx < Nx; jx++)
+    acc[jx * kWarp + lane] =
+        (bok && dc_ok<CHK>(row0 + (long long)jx * B, dc.psi_n, dc.flag)) ? to_real(row[(size_t)jx * B], (TC)0) : (TC)0;
 
   for (int q = q0; q < q1; q++) {
     const int a = plane_atoms[q];
@@ -269,10 +273,12 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
     const TC* tx = tables + (size_t)a * 2 * NP * C;
     const TC* ty = tx + (size_t)NP * C;
     // y-pass (a6, middle pass)
-    const TC* t2a = t2 + ((size_t)a * C + iz) * P * B + b;
+    const long long t20 = ((long long)a * C + iz) * P * B + b;
+    const TC* t2a = t2 + t20;
     TC t2r[P];
 #pragma unroll
-    for (int p = 0; p < P; p++) t2r[p] = bok ? t2a[(size_t)p * B] : (TC)0;
+    for (int p = 0; p < P; p++)
+      t2r[p] = (bok && dc_ok<CHK>(t20 + (long long)p * B, dc.t2_n, dc.flag)) ? t2a[(size_t)p * B] : (TC)0;
     TC t1[NP];
 #pragma unroll
     for (int nx = 0; nx < NP; nx++) t1[nx] = (TC)0;
@@ -308,7 +314,9 @@ __global__ void __launch_bounds__(kWarp) k_expand_rows(GridDev g, const AtomDev*
     }
   }
   if (bok)
-    for (int jx = 0; jx < Nx; jx++) row[(size_t)jx * B] = store_cast(acc[jx * kWarp + lane], (TP*)nullptr);
+    for (int jx = 0; jx < Nx; jx++)
+      if (dc_ok<CHK>(row0 + (long long)jx * B, dc.psi_n, dc.flag))
+        row[(size_t)jx * B] = store_cast(acc[jx * kWarp + lane], (TP*)nullptr);
 }
 
 // Shared memory of k_expand_zpass beyond its z table (and band-tiled staging): the fused action's unscaled
@@ -336,8 +344,11 @@ static cudaError_t zpass_smem(K kern, size_t smem) {
                           : cudaSuccess;
 }
 
-template <int NU, typename TP, typename TCo, typename TC, bool SPH = false>
+template <int NU, typename TP, typename TCo, typename TC, bool SPH = false, bool CHK = false>
 static cudaError_t launch_expand_t(const ExpandLaunch& p) {
+  if constexpr (!CHK) {
+    if (p.chk.flag) return launch_expand_t<NU, TP, TCo, TC, SPH, true>(p);
+  }
   const int C = p.g.cube;
   const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
   {
@@ -351,13 +362,13 @@ static cudaError_t launch_expand_t(const ExpandLaunch& p) {
     if (e != cudaSuccess) return e;
   }
   {
-    auto kern = k_expand_rows<NU, TP, TC, SPH>;
+    auto kern = k_expand_rows<NU, TP, TC, SPH, CHK>;
     const size_t smem = (size_t)p.g.n[0] * kWarp * sizeof(TC);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(p.g.n[1] * p.g.n[2], nbt), kWarp, smem, p.stream>>>(
         p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const TC*>(p.tables), static_cast<const TC*>(p.t2),
-        static_cast<TP*>(p.psi));
+        static_cast<TP*>(p.psi), p.chk);
     return cudaGetLastError();
   }
 }

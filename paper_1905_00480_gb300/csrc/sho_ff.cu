@@ -47,10 +47,12 @@ struct FfProjectSmem {
 // x- and y-passes of one (atom, 32-band tile, slab of cube planes): T2[a][iz][P][B] of each plane of
 // the slab, converted from its float pair to FP64, goes to a workspace; the z-pass is k_project_ff_zpass.
 // Without z-pass accumulators a lane holds about 130 registers, and the ring two rows.
-template <int NU>
+// CHK: device checks of every psi and workspace index (sho_set_device_checks), a separate instantiation.
+template <int NU, bool CHK = false>
 __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* __restrict__ psi,
                                                       const AtomDev* __restrict__ atoms, int zsplit,
-                                                      double* __restrict__ t2g, int* __restrict__ status) {
+                                                      double* __restrict__ t2g, int* __restrict__ status,
+                                                      DevCheck dc) {
   using BS = Basis<NU>;
   using SM = FfProjectSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     if (r >= R) return;
     const int jz = zidx[iz], jy = yidx[iy];
     if (jz < 0 || jy < 0) return;
-    const double* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b0;
+    const long long row0 = ((long long)jz * g.n[1] + jy) * rowlen + b0;  // psi index of the row's x = 0
+    const double* row = psi + row0;
     unsigned char* st = ring + (size_t)(r % kFfStages) * C * kFfRowBytes;
     if (async_ok) {
       // 16 chunks of 16 bytes per x point: this lane copies chunk `cpart` of every other x point
@@ -124,14 +127,15 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       const uint32_t dst0 = ff_smem_u32(st + cpart * 16);
       for (int x = lane >> 4; x < C; x += 2) {
         const long long o = xoff[x];
-        const bool ok = o >= 0 && cbytes > 0;
+        const bool ok = o >= 0 && cbytes > 0 &&
+                        dc_ok<CHK>(row0 + o + cpart * 2 + cbytes / 8 - 1, dc.psi_n, dc.flag);  // last element
         ff_cp16(dst0 + x * kFfRowBytes, ok ? (const void*)(rowb + o * 8) : (const void*)psi, ok ? cbytes : 0);
       }
     } else {
       double* sd = reinterpret_cast<double*>(st);
       for (int x = 0; x < C; x++) {
         const long long o = xoff[x];
-        sd[x * 32 + lane] = (o >= 0 && bok) ? row[o + lane] : 0.0;
+        sd[x * 32 + lane] = (o >= 0 && bok && dc_ok<CHK>(row0 + o + lane, dc.psi_n, dc.flag)) ? row[o + lane] : 0.0;
       }
     }
   };
@@ -189,9 +193,11 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
     if (iy == C - 1) {
       // the finished plane's T2 (zero for a plane outside an open grid), in FP64, for the z-pass
       if (bok) {
-        double* out = t2g + ((size_t)a * C + iz) * P * B + b0 + lane;
+        const long long o0 = ((long long)a * C + iz) * P * B + b0 + lane;
+        double* out = t2g + o0;
 #pragma unroll
-        for (int p = 0; p < P; p++) out[(size_t)p * B] = ff_to_double(t2s[p], t2c[p]);
+        for (int p = 0; p < P; p++)
+          if (dc_ok<CHK>(o0 + (long long)p * B, dc.t2_n, dc.flag)) out[(size_t)p * B] = ff_to_double(t2s[p], t2c[p]);
       }
 #pragma unroll
       for (int p = 0; p < P; p++) t2s[p] = t2c[p] = 0.0f;
@@ -344,14 +350,15 @@ struct FfBlkSmem {
   }
 };
 
-template <int NU>
+// CHK: device checks of every psi and z-pass-result index (sho_set_device_checks), a separate instantiation.
+template <int NU, bool CHK = false>
 __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, const AtomDev* __restrict__ atoms,
                                                                    const int* __restrict__ plane_ptr,
                                                                    const int* __restrict__ plane_atoms,
                                                                    const float2* __restrict__ tyff,
                                                                    const float2* __restrict__ txff,
                                                                    const float2* __restrict__ t2,
-                                                                   double* __restrict__ psi) {
+                                                                   double* __restrict__ psi, DevCheck dc) {
   using BS = Basis<NU>;
   using SM = FfBlkSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -407,10 +414,11 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
     const int a = r.x, iz = r.w;
     unsigned char* dst = smem_raw + (size_t)buf * bufb;
     float2* dt2 = reinterpret_cast<float2*>(dst);
-    const float2* src_t2 = t2 + ((size_t)a * C + iz) * P * B + b0;
+    const long long s0 = ((long long)a * C + iz) * P * B + b0;
+    const float2* src_t2 = t2 + s0;
     for (int q = tid; q < P * 32; q += kFfRows * kWarp) {
       const int p = q >> 5, bl = q & 31;
-      const bool ok = b0 + bl < B;
+      const bool ok = b0 + bl < B && dc_ok<CHK>(s0 + (long long)p * B + bl, dc.t2_n, dc.flag);
       cp8(dt2 + q, ok ? (const void*)(src_t2 + (size_t)p * B + bl) : (const void*)t2, ok ? 8 : 0);
     }
     float2* dx = reinterpret_cast<float2*>(dst + (size_t)P * 32 * 8);
@@ -527,16 +535,21 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   }
   ff_wait<0>();
   if (!yok || !bok || nlist == 0) return;
-  double* rowp = psi + ((size_t)z * Ny + y) * (size_t)Nx * B + b0 + lane;
+  const long long row0 = ((long long)z * Ny + y) * Nx * B + b0 + lane;  // psi index of the row's x = 0
+  double* rowp = psi + row0;
   // loads of 16 points first, so that they are in flight together, then their adds and stores
 #pragma unroll
   for (int x0 = 0; x0 < kFfXSeg; x0 += 16) {
     double pv[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) pv[i] = x0 + i < xend ? rowp[(size_t)(xs + x0 + i) * B] : 0.0;
+    bool in[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) {
-      if (x0 + i < xend) {
+      in[i] = x0 + i < xend && dc_ok<CHK>(row0 + (long long)(xs + x0 + i) * B, dc.psi_n, dc.flag);
+      pv[i] = in[i] ? rowp[(size_t)(xs + x0 + i) * B] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      if (in[i]) {
         const float2 v = accw[(x0 + i) * kWarp + lane];
         rowp[(size_t)(xs + x0 + i) * B] = pv[i] + ff_to_double(v.x, v.y);
       }
@@ -549,12 +562,12 @@ template <int NU>
 static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   if (!p.t2) return cudaErrorInvalidValue;
   const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
-  auto kern = k_project_ff<NU>;
+  auto kern = p.chk.flag ? k_project_ff<NU, true> : k_project_ff<NU, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned nbt = (unsigned)((p.g.nbands + kWarp - 1) / kWarp);
   kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
-      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status);
+      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status, p.chk);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.t2_only) return e;
   const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
@@ -584,14 +597,14 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   // the x-pass on the tensor cores when chosen (kernel choice 2) and where it applies; by default the
   // float-float block gather, which measures as fast on GB300 at a tenth of the error
   if (p.kernel == 2 && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
-  auto kern = k_expand_blk_ff<NU>;
+  auto kern = p.chk.flag ? k_expand_blk_ff<NU, true> : k_expand_blk_ff<NU, false>;
   const size_t smem = FfBlkSmem<NU>::bytes(p.g.cube, p.max_plane);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nseg = (p.g.n[0] + kFfXSeg - 1) / kFfXSeg, nyb = (p.g.n[1] + kFfRows - 1) / kFfRows;
   kern<<<dim3((unsigned)nseg * nyb * p.g.n[2], (p.g.nbands + kWarp - 1) / kWarp), kFfRows * kWarp, smem, p.stream>>>(
       p.g, p.atoms, p.plane_ptr, p.plane_atoms, tyff, txff, static_cast<const float2*>(p.t2),
-      static_cast<double*>(p.psi));
+      static_cast<double*>(p.psi), p.chk);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,15 @@ enum class Real { F64, F32 };
 // own data pipeline expired; an FP64-accurate (float-float) input lay outside the float normal range.
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusRange = 2;
+constexpr int kStatusBounds = 4;  // device checks: an index outside its buffer (the access was skipped)
+
+// Device checks (sho_set_device_checks): the extents, in elements, of the buffers the checked kernels
+// index -- psi, the coefficients and the z-pass / per-plane intermediate -- and the status word that an
+// index outside its extent sets (kStatusBounds).  flag == nullptr: checks off, unchecked kernels run.
+struct DevCheck {
+  long long psi_n = 0, coeff_n = 0, t2_n = 0;
+  int* flag = nullptr;
+};
 
 // Bounded waits of the device pipelines give up after this many SM clock cycles (~2 s at 2.07 GHz)
 // unless a handle's fault-injection setting (include/sho_fault.h) shortens it.
@@ -62,6 +71,7 @@ struct ProjectLaunch {
   sho_dtype coeff_dtype;
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   bool t2_only = false;     // FP64-accurate form: stop after the per-plane sums (the z-pass runs fused later)
+  DevCheck chk;             // device checks (FP64 and FP64-accurate kernels), off by default
   cudaStream_t stream;
 };
 
@@ -103,6 +113,7 @@ struct ExpandLaunch {
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   void* oz = nullptr;       // FP64-accurate form on the tensor cores: oz_layout() workspace, may be null
   int stop_stage = 0x7fffffff;  // fault injection: that kernel stages the z-pass slices of this many atoms
+  DevCheck chk;             // device checks (FP64 and FP64-accurate kernels), off by default
   cudaStream_t stream;
 };
 

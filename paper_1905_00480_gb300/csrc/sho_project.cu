@@ -39,10 +39,11 @@ struct ProjectSmem {
 
 // SPH: spherical support (one support mask per cube row); compiled separately so that the cube form keeps
 // its plain inner loop.
-template <int NU, typename TP, typename TC, bool SPH = false>
+// CHK: device checks of every psi and coefficient index (sho_set_device_checks), a separate instantiation.
+template <int NU, typename TP, typename TC, bool SPH = false, bool CHK = false>
 __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restrict__ psi,
                                                    const AtomDev* __restrict__ atoms, int zsplit,
-                                                   TC* __restrict__ coeff) {
+                                                   TC* __restrict__ coeff, DevCheck dc) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N;
   constexpr int NPX = ProjectSmem<NU>::NPX;
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restri
         sup = row_support(g, at, iy, iz, lane);  // spherical support of the row
         if (sup == 0) continue;
       }
-      const TP* row = psi + ((long long)jz * g.n[1] + jy) * rowlen + b;
+      const long long row0 = ((long long)jz * g.n[1] + jy) * rowlen + b;  // psi index of this row's x = 0
+      const TP* row = psi + row0;
       // x-pass (a3)
       TC t1[NP];
 #pragma unroll
@@ -108,7 +110,9 @@ __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restri
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const long long o = xoff[ix + u];
-          v[u] = (o >= 0 && bok && (!SPH || ((sup >> (ix + u)) & 1ull))) ? to_real(row[o], (TC)0) : (TC)0;
+          v[u] = (o >= 0 && bok && (!SPH || ((sup >> (ix + u)) & 1ull)) && dc_ok<CHK>(row0 + o, dc.psi_n, dc.flag))
+                     ? to_real(row[o], (TC)0)
+                     : (TC)0;
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {
@@ -152,16 +156,20 @@ __global__ void __launch_bounds__(kWarp) k_project(GridDev g, const TP* __restri
       const TC* rem = cl.map_shared_rank(acc, r);
       s += rem[k * kWarp + lane];
     }
-    if (bok) coeff[((long long)a * N + k) * B + b] = s * h3;
+    const long long ci = ((long long)a * N + k) * B + b;
+    if (bok && dc_ok<CHK>(ci, dc.coeff_n, dc.flag)) coeff[ci] = s * h3;
   }
   cl.sync();
 }
 
-template <int NU, typename TP, typename TC, bool SPH = false>
+template <int NU, typename TP, typename TC, bool SPH = false, bool CHK = false>
 static cudaError_t launch_project_t(const ProjectLaunch& p) {
+  if constexpr (!CHK) {
+    if (p.chk.flag) return launch_project_t<NU, TP, TC, SPH, true>(p);
+  }
   const int C = p.g.cube;
   const size_t smem = ProjectSmem<NU>::template bytes<TC>(C);
-  auto kern = k_project<NU, TP, TC, SPH>;
+  auto kern = k_project<NU, TP, TC, SPH, CHK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -177,7 +185,7 @@ static cudaError_t launch_project_t(const ProjectLaunch& p) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, p.g, static_cast<const TP*>(p.psi), p.atoms, p.zsplit,
-                            static_cast<TC*>(p.coeff));
+                            static_cast<TC*>(p.coeff), p.chk);
 }
 
 template <int NU>
