@@ -12,6 +12,8 @@
 //   expansion   the update sum_a sum_n T1_a[n] phi_n(x) of each grid point is one float-float dot
 //               product over all atoms and states, its running pair kept in shared memory (block gather
 //               over 8-row x 32-point tiles), and added to psi in FP64 once.
+#include <type_traits>
+
 #include "sho_device.cuh"
 #include "sho_ff.cuh"
 
@@ -246,25 +248,49 @@ __global__ void __launch_bounds__(kWarp) k_project_ff_zpass(GridDev g, const Ato
   const double* src = t2g + (size_t)a * C * P * B + b;
   double accr[ACCR ? N : 1];
   if constexpr (ACCR) {
+    // grid z splits the states between two warps by nz: nz in half ((nz + 1) / 2) % 2 (numax 5: 30 and
+    // 26 states), each warp over all planes in order (the same sums, twice the warps)
+    auto run = [&](auto hz) {
+      constexpr int HZ = decltype(hz)::value;
+      auto own = [](int nz) { return (((nz + 1) >> 1) & 1) == HZ; };
+      double acch[N];
 #pragma unroll
-    for (int k = 0; k < N; k++) accr[k] = 0.0;
-    for (int iz = 0; iz < C; iz++) {
-      double t2[P];
+      for (int k = 0; k < N; k++) acch[k] = 0.0;
+      for (int iz = 0; iz < C; iz++) {
+        double t2[P];
 #pragma unroll
-      for (int p = 0; p < P; p++) t2[p] = src[((size_t)iz * P + p) * B];
+        for (int p = 0; p < P; p++) t2[p] = src[((size_t)iz * P + p) * B];
+        int k = 0;
+#pragma unroll
+        for (int nz = 0; nz < NP; nz++) {
+          const double w = phz[nz * C + iz];
+#pragma unroll
+          for (int ny = 0; ny + nz <= NU; ny++)
+#pragma unroll
+            for (int nx = 0; nx + ny + nz <= NU; nx++) {
+              if (own(nz)) acch[k] = fma(t2[BS::pair(nx, ny)], w, acch[k]);
+              k++;
+            }
+        }
+      }
+      const double h3 = g.h * g.h * g.h;
+      double* out = coeff + (size_t)a * N * B + b;
       int k = 0;
 #pragma unroll
-      for (int nz = 0; nz < NP; nz++) {
-        const double w = phz[nz * C + iz];
+      for (int nz = 0; nz < NP; nz++)
 #pragma unroll
         for (int ny = 0; ny + nz <= NU; ny++)
 #pragma unroll
           for (int nx = 0; nx + ny + nz <= NU; nx++) {
-            accr[k] = fma(t2[BS::pair(nx, ny)], w, accr[k]);
+            if (own(nz)) out[(size_t)k * B] = acch[k] * h3;
             k++;
           }
-      }
-    }
+    };
+    if (blockIdx.z == 0)
+      run(std::integral_constant<int, 0>{});
+    else
+      run(std::integral_constant<int, 1>{});
+    return;
   } else {
     // larger bases: accumulators and the plane's T2 in this lane's columns of shared memory, loops kept
     // rolled (states in the order nz, ny, nx, so k counts up)
@@ -574,8 +600,8 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   auto zk = k_project_ff_zpass<NU>;
   e = cudaFuncSetAttribute(zk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem);
   if (e != cudaSuccess) return e;
-  zk<<<dim3(nbt, (unsigned)p.natoms), kWarp, zsmem, p.stream>>>(p.g, p.atoms, static_cast<const double*>(p.t2),
-                                                                static_cast<double*>(p.coeff));
+  zk<<<dim3(nbt, (unsigned)p.natoms, FfZpassSmem<NU>::ACCR ? 2u : 1u), kWarp, zsmem, p.stream>>>(
+      p.g, p.atoms, static_cast<const double*>(p.t2), static_cast<double*>(p.coeff));
   return cudaGetLastError();
 }
 
