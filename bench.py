@@ -166,9 +166,9 @@ def launches_per_step(api, psi, w, prec, expand_kernel="auto"):
     if prec == "ff64":
         oz = (expand_kernel == "tcgen05" and w.numax <= 7 and w.cube <= 32 and w.cube % 2 == 0
               and w.nbands % 2 == 0 and (not w.periodic or w.grid[0] >= w.cube + 32))
-        # x/y-pass + z-pass kernels; z-pass tables, float-pair tables, then the block gather, or the digit
-        # tables and the tensor-core x-pass
-        return 2 + (4 if oz else 3)
+        # x/y-pass + z-pass kernels; the float-pair z-pass (with the tables), then the block gather, or the
+        # digit tables and the tensor-core x-pass
+        return 2 + (3 if oz else 2)
     if prec == "fp64":
         return 1 + 2  # cluster projection; z-pass + row gather
     tc = prec in ("tf32", "3xtf32", "bf16", "split_fp16")

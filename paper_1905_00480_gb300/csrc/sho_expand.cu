@@ -13,6 +13,7 @@
 // every atom whose cube covers the row in ascending atom order, and writes the row back once.  No
 // atomics: every psi element is written by exactly one warp, in a fixed order (deterministic).
 #include "sho_device.cuh"
+#include "sho_ff.cuh"
 
 namespace sho {
 
@@ -22,11 +23,18 @@ constexpr int kZChunk = 4;  // planes per shared-memory chunk of the band-tiled 
 // TILED: T2 goes out band-tiled, [A][C][B/32][32][PP] with PP = tiled_pairs(P), zero for the padding
 // pairs and for bands past B (the block-gather expansion stages one contiguous [32][PP] slice per
 // atom and plane); otherwise [A][C][P][B].
-template <int NU, typename TCo, typename TC, bool TILED = false>
+// FFOUT (FP64-accurate form, TC = double): T2 goes out as float pairs in the same [A][C][P][B] slots
+// (8 bytes each, the integer split of ff_from_double), a sum outside the float-pair range sets
+// kStatusRange, and the x and y tables also go out as float pairs, x-major txff [A][C][NPX2] (NPX2 = NP
+// rounded up to 2, zero padded) and tyff [A][NP][C].
+template <int NU, typename TCo, typename TC, bool TILED = false, bool FFOUT = false>
 __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev* __restrict__ atoms,
                                                         const TCo* __restrict__ coeff, TC* __restrict__ tables,
                                                         TC* __restrict__ t2, TC* __restrict__ txm, double scale,
-                                                        NonlocalIn nl, TC* __restrict__ tym = nullptr) {
+                                                        NonlocalIn nl, TC* __restrict__ tym = nullptr,
+                                                        float2* __restrict__ txff = nullptr,
+                                                        float2* __restrict__ tyff = nullptr,
+                                                        int* __restrict__ status = nullptr) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -69,6 +77,22 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
         TC* row = tym + ((size_t)a * C + i) * NPX;
         phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, row, 1);
         for (int n = NP; n < NPX; n++) row[n] = (TC)0;
+      }
+      if constexpr (FFOUT) {  // the x and y tables as float pairs (each entry split once, in FP64)
+        constexpr int NPX2 = (NP + 1) & ~1;
+        double col[NP];
+        phi_column(cube_offset(at.o[0], i, g.h, at.X[0]), at.sigma, NU, col, 1);
+#pragma unroll
+        for (int n = 0; n < NPX2; n++) {
+          const ff f = n < NP ? ff_from_double_exact(col[n]) : ff{0.0f, 0.0f};
+          txff[((size_t)a * C + i) * NPX2 + n] = make_float2(f.hi, f.lo);
+        }
+        phi_column(cube_offset(at.o[1], i, g.h, at.X[1]), at.sigma, NU, col, 1);
+#pragma unroll
+        for (int n = 0; n < NP; n++) {
+          const ff f = ff_from_double_exact(col[n]);
+          tyff[((size_t)a * NP + n) * C + i] = make_float2(f.hi, f.lo);
+        }
       }
     }
   }
@@ -156,6 +180,7 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
   const int zb = (int)blockIdx.z * zper, ze = min(C, zb + zper);
   if constexpr (!TILED) {
     TC* out = t2 + (size_t)a * C * P * B + b;
+    bool range_bad = false;  // FFOUT: a sum the float pairs cannot carry
 #pragma unroll
     for (int ny = 0; ny < NP; ny++) {
 #pragma unroll
@@ -169,9 +194,18 @@ __global__ void __launch_bounds__(kWarp) k_expand_zpass(GridDev g, const AtomDev
           TC s = (TC)0;
 #pragma unroll
           for (int nz = 0; nz + nx + ny <= NU; nz++) s = fma(cz[nz], phz[nz * C + iz], s);
-          out[((size_t)iz * P + p) * B] = s;
+          if constexpr (FFOUT) {
+            range_bad |= ff_out_of_range((double)s);
+            const ff f = ff_from_double((double)s);  // integer split: no FP64-pipe work per element
+            reinterpret_cast<float2*>(out)[((size_t)iz * P + p) * B] = make_float2(f.hi, f.lo);
+          } else {
+            out[((size_t)iz * P + p) * B] = s;
+          }
         }
       }
+    }
+    if constexpr (FFOUT) {
+      if (range_bad && status) atomicOr(status, kStatusRange);
     }
   } else {
     // band-tiled: kZChunk planes at a time are assembled in shared memory as [plane][32][PP] (this
@@ -423,6 +457,35 @@ static cudaError_t zpass_f64_nu(const ExpandLaunch& p) {
       p.g, p.atoms, static_cast<const double*>(p.coeff), static_cast<double*>(p.tables), static_cast<double*>(p.t2),
       (double*)nullptr, p.scale, p.nl);
   return cudaGetLastError();
+}
+
+template <int NU>
+static cudaError_t zpass_ff_nu(const ExpandLaunch& p, float2* txff, float2* tyff) {
+  const int nbt = (p.g.nbands + kWarp - 1) / kWarp;
+  const size_t smem = (size_t)(NU + 1) * p.g.cube * sizeof(double) + nl_smem<NU, double>(p);
+  auto kern = k_expand_zpass<NU, double, double, false, true>;
+  const cudaError_t e = zpass_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(nbt, p.natoms, zpass_chunks(p)), kWarp, smem, p.stream>>>(
+      p.g, p.atoms, static_cast<const double*>(p.coeff), static_cast<double*>(p.tables), static_cast<double*>(p.t2),
+      (double*)nullptr, p.scale, p.nl, (double*)nullptr, txff, tyff, p.status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_zpass_ff(const ExpandLaunch& p, float2* txff, float2* tyff) {
+  switch (p.numax) {
+    case 0: return zpass_ff_nu<0>(p, txff, tyff);
+    case 1: return zpass_ff_nu<1>(p, txff, tyff);
+    case 2: return zpass_ff_nu<2>(p, txff, tyff);
+    case 3: return zpass_ff_nu<3>(p, txff, tyff);
+    case 4: return zpass_ff_nu<4>(p, txff, tyff);
+    case 5: return zpass_ff_nu<5>(p, txff, tyff);
+    case 6: return zpass_ff_nu<6>(p, txff, tyff);
+    case 7: return zpass_ff_nu<7>(p, txff, tyff);
+    case 8: return zpass_ff_nu<8>(p, txff, tyff);
+    case 9: return zpass_ff_nu<9>(p, txff, tyff);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p) {

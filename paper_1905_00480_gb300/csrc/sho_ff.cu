@@ -317,43 +317,6 @@ __global__ void __launch_bounds__(kWarp) k_project_ff_zpass(GridDev g, const Ato
   for (int k = 0; k < N; k++) out[(size_t)k * B] = (ACCR ? accr[k] : acc[k * kWarp + lane]) * h3;
 }
 
-// ------------------------------------------------------------------------------- expansion
-// Float-pair copies of the expansion intermediates: the x tables x-major [A][C][NPX], the y tables
-// [A][NP][C] (from the FP64 tables [A][2][NP][C]) and the z-pass result T2 (same layout as the FP64 T2,
-// converted in place: a double and a float pair are both 8 bytes).
-template <int NU>
-__global__ void k_ff_tables(int natoms, int cube, const double* __restrict__ tables, float2* __restrict__ txff,
-                            float2* __restrict__ tyff, double* __restrict__ t2, long long t2_count,
-                            int* __restrict__ status) {
-  constexpr int NP = NU + 1, NPX = (NP + 1) & ~1;
-  const long long nx_total = (long long)natoms * cube * NPX;
-  const long long ny_total = (long long)natoms * NP * cube;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nx_total; i += stride) {
-    const int n = (int)(i % NPX);
-    const long long ai = i / NPX;
-    const int ix = (int)(ai % cube);
-    const int a = (int)(ai / cube);
-    const ff f = n < NP ? ff_from_double_exact(tables[((long long)a * 2 * NP + n) * cube + ix]) : ff{0.0f, 0.0f};
-    txff[i] = make_float2(f.hi, f.lo);
-  }
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ny_total; i += stride) {
-    const long long a = i / ((long long)NP * cube);
-    const long long rest = i - a * NP * cube;  // n * cube + iy
-    const ff f = ff_from_double_exact(tables[(a * 2 + 1) * NP * cube + rest]);
-    tyff[i] = make_float2(f.hi, f.lo);
-  }
-  float2* t2f = reinterpret_cast<float2*>(t2);
-  bool range_bad = false;  // a z-pass sum the float pairs cannot carry (coefficients out of range)
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < t2_count; i += stride) {
-    const double v = t2[i];
-    range_bad |= ff_out_of_range(v);
-    const ff f = ff_from_double_exact(v);
-    t2f[i] = make_float2(f.hi, f.lo);
-  }
-  if (range_bad && status) atomicOr(status, kStatusRange);
-}
-
 // ------------------------------------------------------------------------------- expansion, block gather
 // Tiles of 8 grid rows x 32 x points x 32 bands of one z plane (8 warps, one per row).  For each atom
 // whose cube meets the tile, its z-pass slice T2[a][z][P][32] (FP64), its x table as float pairs
@@ -608,17 +571,11 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
 template <int NU>
 static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   constexpr int NPX = (NU + 2) & ~1;
-  cudaError_t e = launch_expand_zpass_f64(p);
-  if (e != cudaSuccess) return e;
-  const long long t2_count = (long long)p.natoms * p.g.cube * Basis<NU>::P * p.g.nbands;
-  const long long total = std::max<long long>(t2_count, (long long)p.natoms * p.g.cube * NPX);
-  // y pairs go after the x pairs in the x-major region (sized for [A][C][4 * ceil(NP/4)] doubles)
+  // y pairs go after the x pairs in the x-major region (sized for [A][C][4 * ceil(NP/4)] doubles); the
+  // z-pass writes T2 and both tables as float pairs
   float2* txff = static_cast<float2*>(p.tables_xmajor);
   float2* tyff = txff + (size_t)p.natoms * p.g.cube * NPX;
-  k_ff_tables<NU><<<(unsigned)std::min<long long>((total + 255) / 256, 8192), 256, 0, p.stream>>>(
-      p.natoms, p.g.cube, static_cast<const double*>(p.tables), txff, tyff, static_cast<double*>(p.t2), t2_count,
-      p.status);
-  e = cudaGetLastError();
+  cudaError_t e = launch_expand_zpass_ff(p, txff, tyff);
   if (e != cudaSuccess) return e;
   // the x-pass on the tensor cores when chosen (kernel choice 2) and where it applies; by default the
   // float-float block gather, which measures as fast on GB300 at a tenth of the error

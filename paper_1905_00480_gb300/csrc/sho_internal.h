@@ -280,10 +280,12 @@ bool usu_supported_nproj(int n);
 cudaError_t launch_expand_zpass_f32(const ExpandLaunch& p);
 cudaError_t launch_expand_zpass_f32_tiled(const ExpandLaunch& p);  // T2 as [A][C][B/32][32][tiled_pairs(P)]
 cudaError_t launch_expand_zpass_f64(const ExpandLaunch& p);
+// the same z-pass with T2 and the x / y tables written as float pairs (FP64-accurate expansion)
+cudaError_t launch_expand_zpass_ff(const ExpandLaunch& p, float2* txff, float2* tyff);
 cudaError_t launch_project_ff(const ProjectLaunch& p);
 cudaError_t launch_expand_ff(const ExpandLaunch& p);
 // FP64-accurate expansion with the x-pass on the tensor cores (exact digit slices); the caller has run the
-// z-pass and k_ff_tables (T2 as float pairs, float-pair y tables at `tyff`)
+// float-pair z-pass (T2 as float pairs, float-pair y tables at `tyff`)
 bool ozaki_expand_ok(const ExpandLaunch& p);
 cudaError_t launch_expand_ozaki(const ExpandLaunch& p, const void* tyff);
 cudaError_t launch_project_tc(const ProjectLaunch& p, sho_prec prec);
