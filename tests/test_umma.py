@@ -1,4 +1,5 @@
-"""Fifth-generation tensor-core path (tcgen05 MMA, tensor memory) of the TF32 / BF16 expansion (GPU).
+"""Fifth-generation tensor-core path (tcgen05 MMA, tensor memory) of the TF32 / BF16 / 3xTF32 /
+split-FP16 expansion (GPU).
 
 First the operand layouts in isolation: one M=128, N=32 MMA on integer-valued operands, whose products
 and sums are exact in FP32, must equal numpy's matrix product bit for bit.  Then the expansion kernel
@@ -33,7 +34,7 @@ def test_umma_layout_selftest(bf16):
     assert np.array_equal(D, A @ B.T), np.argwhere(D != A @ B.T)[:10]
 
 
-@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("mode", ["tf32", "bf16", "3xtf32", "split_fp16"])
 @pytest.mark.parametrize("grid,periodic,numax,cube,nbands", [
     ((40, 36, 44), True, 7, 32, 200),    # 128 + 72 bands: a partial band tile
     ((34, 40, 36), True, 5, 32, 64),     # periodic grid barely wider than the cube: wrapped tiles
