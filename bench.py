@@ -598,7 +598,21 @@ def same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream):
                                  "ms_per_step": round(msb, 4),
                                  "note": f"{B} complex128 bands, k = {kvec}: Bloch projection + expansion (4 DFMA "
                                          "per complex FMA)"}
-    del zc, cz, oz, hz
+    ozf = torch.empty_like(cz)
+    hzf = torch.zeros_like(zc)
+
+    def bloch_ff_step():
+        api.project_bloch(zc, kvec, pos, sig, w.numax, w.cube, w.h, out=ozf, handle=handle, stream=stream,
+                          prec="ff64")
+        api.add_bloch(hzf, cz, kvec, pos, sig, w.numax, w.cube, w.h, handle=handle, stream=stream, prec="ff64")
+
+    msf = _time_steps(stream, bloch_ff_step, warmup=2, steps=10)
+    err_b = float(torch.linalg.vector_norm(torch.view_as_real(ozf - oz)) / torch.linalg.vector_norm(torch.view_as_real(oz)))
+    out["bloch_complex_ff64"] = {"value": round(bytes_b / (msf * 1e-3) / 1e9, 3), "unit": "GB/s",
+                                 "ms_per_step": round(msf, 4), "project_rel_diff_vs_fp64_form": err_b,
+                                 "note": f"same {B} complex bands and k: the FP64-accurate form (float-float passes "
+                                         "over the (re, im) pairs, phases turned per run)"}
+    del zc, cz, oz, hz, ozf, hzf
     torch.cuda.empty_cache()
     return out
 

@@ -263,24 +263,32 @@ int sho_apply_nonlocal(sho_handle* handle, const sho_grid* grid, const void* psi
                        const void* D, void* hpsi, void* stream);
 
 /* ----------------------------------------------------------------------------------------------
- * Bloch (complex) wave functions on a periodic grid, FP64.  The SHO states span functions R^3 -> C
+ * Bloch (complex) wave functions on a periodic grid.  The SHO states span functions R^3 -> C
  * (Sec. 2.5); for psi(r + T) = e^{i k.T} psi(r) a cube point i outside the cell maps to grid point
  * j(i) = r_i - T_i with the lattice translation T_i = (o + i - j(i)) h (per axis), and
  *     sho_project_bloch   coeff[a][k][b] = h^3 sum_i Psi_k(u_i) e^{+i k.T_i} psi[j(i)][b]
  *     sho_add_bloch       psi[j][b] += sum_a sum_{i: j(i)=j} sum_k coeff[a][k][b] Psi_k(u_i) e^{-i k.T_i}
  * (adjoint in the h^3-weighted complex inner product; k = 0 is the real transform of the real and
- * imaginary parts).  The phase rides on the 1D tables, so the three-pass form is kept.
- *   grid   periodic (SHO_ERR_ARG otherwise); sho_add_bloch needs n[0] <= 448
+ * imaginary parts).  The three-pass form is kept: the phase is a product over the axes and, along each
+ * axis, constant on the (at most two) runs of a cube on either side of the cell boundary.
+ *   grid   periodic (SHO_ERR_ARG otherwise); sho_add_bloch with SHO_P_FP64 needs n[0] <= 448
  *   kvec   host double[3], the Bloch vector in inverse length units
  *   psi    device complex double [n[2]][n[1]][n[0]][nbands] as (re, im) pairs
+ *   prec   SHO_P_FP64: complex 1D tables (phase included), complex FMAs on the FP64 pipe;
+ *          SHO_P_FF64: the real FP64-accurate kernels (float-float x- and y-passes, FP64 z-pass) over
+ *          the (re, im) pairs as 2 nbands real bands, each x-pass sum turned by its run's phase in
+ *          float pairs -- same accuracy class and input range as SHO_P_FF64 of sho_project (an input
+ *          outside it latches SHO_ERR_DEVICE), and the same workspace for 2 nbands bands;
+ *          any other value: SHO_ERR_DTYPE
  *   coeff  device complex double [natoms][sho_nstates(numax)][nbands] as (re, im) pairs
  * numax <= 7 (SHO_ERR_NUMAX).  Deterministic (fixed summation order, no atomics).
  */
 int sho_project_bloch(sho_handle* handle, const sho_grid* grid, const double* kvec, const void* psi, int nbands,
-                      int natoms, const double* pos, const double* sigma, int numax, int cube, void* coeff,
-                      void* stream);
+                      int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                      void* coeff, void* stream);
 int sho_add_bloch(sho_handle* handle, const sho_grid* grid, const double* kvec, const void* coeff, int nbands,
-                  int natoms, const double* pos, const double* sigma, int numax, int cube, void* psi, void* stream);
+                  int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
+                  void* stream);
 
 /* ----------------------------------------------------------------------------------------------
  * Cartesian <-> radial SHO coefficients -- eq. SHO-transform-Cartesian-to-radial (Sec. 2.4): within an

@@ -69,8 +69,8 @@ SIGNATURES = {
     "sho_last_cuda_error": (ctypes.c_char_p, [_VP]),
     "sho_project_path": (_I, [_GP, _VP, _I, _I, _I, _I, _I, _I]),
     "sho_plane_plan_check": (_I, [_GP, _I, _DP, _DP, _I, _IP, _IP]),
-    "sho_project_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP]),
-    "sho_add_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _VP, _VP]),
+    "sho_project_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _I, _VP, _VP]),
+    "sho_add_bloch": (_I, [_VP, _GP, _DP, _VP, _I, _I, _DP, _DP, _I, _I, _I, _VP, _VP]),
     "sho_radial_labels": (_I, [_I, _IP, _IP, _IP]),
     "sho_radial_matrix": (_I, [_I, _DP]),
     "sho_radial_transform": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _I, _VP]),

@@ -171,8 +171,9 @@ def _check_complex(t: torch.Tensor, what: str, dims: int):
 
 
 def project_bloch(psi: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h: float, out: torch.Tensor = None,
-                  handle: Handle = None, stream=None) -> torch.Tensor:
-    """sho_project_bloch: complex Bloch psi [Nz][Ny][Nx][B] (periodic grid) -> complex [A][N][B]."""
+                  handle: Handle = None, stream=None, prec: str = "fp64") -> torch.Tensor:
+    """sho_project_bloch: complex Bloch psi [Nz][Ny][Nx][B] (periodic grid) -> complex [A][N][B].
+    prec "fp64" (complex FMAs on the FP64 pipe) or "ff64" (float-float passes, FP64-accurate)."""
     _check_complex(psi, "psi", 4)
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
@@ -184,15 +185,16 @@ def project_bloch(psi: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h:
     hd = handle or default_handle(psi.device.index or 0)
     g = _grid_complex(psi, h)
     st = N.lib().sho_project_bloch(hd.ptr, ctypes.byref(g), _dp(k), ctypes.c_void_p(psi.data_ptr()), B, A,
-                                   _dp(pos_h), _dp(sig_h), int(numax), int(cube), ctypes.c_void_p(out.data_ptr()),
-                                   _stream_ptr(psi, stream))
+                                   _dp(pos_h), _dp(sig_h), int(numax), int(cube), N.PRECS[prec],
+                                   ctypes.c_void_p(out.data_ptr()), _stream_ptr(psi, stream))
     N.check(st, "sho_project_bloch")
     return out
 
 
 def add_bloch(psi: torch.Tensor, coeff: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h: float,
-              handle: Handle = None, stream=None) -> torch.Tensor:
-    """sho_add_bloch (in place): psi += sum_a sum_k c Psi_k e^{-i k.T} for complex Bloch psi."""
+              handle: Handle = None, stream=None, prec: str = "fp64") -> torch.Tensor:
+    """sho_add_bloch (in place): psi += sum_a sum_k c Psi_k e^{-i k.T} for complex Bloch psi.
+    prec "fp64" or "ff64" as for project_bloch."""
     _check_complex(psi, "psi", 4)
     _check_complex(coeff, "coeff", 3)
     pos_h = _host_f64(pos, 3)
@@ -204,7 +206,7 @@ def add_bloch(psi: torch.Tensor, coeff: torch.Tensor, kvec, pos, sigma, numax: i
     hd = handle or default_handle(psi.device.index or 0)
     g = _grid_complex(psi, h)
     st = N.lib().sho_add_bloch(hd.ptr, ctypes.byref(g), _dp(k), ctypes.c_void_p(coeff.data_ptr()), B, A, _dp(pos_h),
-                               _dp(sig_h), int(numax), int(cube), ctypes.c_void_p(psi.data_ptr()),
+                               _dp(sig_h), int(numax), int(cube), N.PRECS[prec], ctypes.c_void_p(psi.data_ptr()),
                                _stream_ptr(psi, stream))
     N.check(st, "sho_add_bloch")
     return psi

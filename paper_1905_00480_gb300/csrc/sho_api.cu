@@ -1,5 +1,6 @@
 // sho_api.cu -- host side of the C ABI declared in include/sho.h: argument validation, the per-call
 // plan (cube origins, per-plane atom lists), workspace management and kernel launches.
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -699,19 +700,74 @@ int sho_radial_transform(sho_handle* h, int natoms, int numax, int nbands, const
   return end_call(h, s);
 }
 
+static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
+                        int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                        void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2,
+                        const std::vector<BlochPh>* bloch = nullptr);
+static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
+                    sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
+                    int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream,
+                    const NonlocalIn* nl = nullptr, const std::vector<BlochPh>* bloch = nullptr);
+
+// Phases of the FP64-accurate Bloch kernels (BlochPh): per atom and axis the cube point w where the
+// cube crosses the cell boundary (floor((o + i) / n) steps from f0 to f0 + 1 there) and the eight
+// e^{sgn i k.T} of the translations T_d = (f0_d + b_d) n_d h, as float pairs.
+static std::vector<BlochPh> bloch_phases(const sho_grid* grid, const std::vector<AtomDev>& at, const double* k,
+                                         double sgn) {
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  std::vector<BlochPh> out(at.size());
+  for (size_t a = 0; a < at.size(); a++) {
+    BlochPh& b = out[a];
+    long long f0[3];
+    for (int d = 0; d < 3; d++) {
+      const long long n = grid->n[d], o = at[a].o[d];
+      f0[d] = o >= 0 ? o / n : -((-o + n - 1) / n);  // floor(o / n)
+      b.w[d] = (int)((f0[d] + 1) * n - o);             // in [1, n]
+    }
+    b.w[3] = 0;
+    for (int bits = 0; bits < 8; bits++) {
+      double ang = 0.0;
+      for (int d = 0; d < 3; d++)
+        ang += k[d] * (double)(f0[d] + ((bits >> d) & 1)) * grid->n[d] * grid->h;
+      float4& ph = b.ph[bits];
+      split(std::cos(sgn * ang), ph.x, ph.y);
+      split(std::sin(sgn * ang), ph.z, ph.w);
+    }
+    const double ax = -sgn * k[0] * grid->n[0] * grid->h;
+    split(std::cos(ax), b.xstep.x, b.xstep.y);
+    split(std::sin(ax), b.xstep.z, b.xstep.w);
+  }
+  return out;
+}
+
 static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, int op, const void* src, void* dst,
                       int nbands, int natoms, const double* pos, const double* sigma, int numax, int cube,
-                      void* stream) {
+                      sho_prec prec, void* stream) {
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, kTcMaxNumax));
   if (!grid->periodic || !kvec) return SHO_ERR_ARG;
+  if (prec != SHO_P_FP64 && prec != SHO_P_FF64) return SHO_ERR_DTYPE;
   if (h->rprj > 0.0) return SHO_ERR_DTYPE;  // spherical support: FP64 / FP64-accurate real forms only
   for (int d = 0; d < 3; d++)
     if (!std::isfinite(kvec[d])) return SHO_ERR_ARG;
-  if (op == 1 && grid->n[0] > kBlochMaxNx) return SHO_ERR_ARG;
+  if (op == 1 && prec == SHO_P_FP64 && grid->n[0] > kBlochMaxNx) return SHO_ERR_ARG;
+  if (nbands > INT_MAX / 2) return SHO_ERR_ARG;
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!src || !dst) return SHO_ERR_ARG;
+  if (prec == SHO_P_FF64) {
+    // the real FP64-accurate kernels over the (re, im) pairs as 2 nbands real bands, with the phases
+    const std::vector<BlochPh> ph =
+        bloch_phases(grid, make_atoms(grid, natoms, pos, sigma, cube), kvec, op == 0 ? 1.0 : -1.0);
+    if (op == 0)
+      return project_impl(h, grid, src, SHO_F64, 2 * nbands, natoms, pos, sigma, numax, cube, SHO_P_FF64, dst,
+                          SHO_F64, stream, nullptr, nullptr, &ph);
+    return add_impl(h, grid, 1.0, 0, src, SHO_F64, 2 * nbands, natoms, pos, sigma, numax, cube, SHO_P_FF64, dst,
+                    SHO_F64, stream, nullptr, &ph);
+  }
   DeviceGuard guard(h->device);
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -757,14 +813,15 @@ static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, i
 }
 
 int sho_project_bloch(sho_handle* h, const sho_grid* grid, const double* kvec, const void* psi, int nbands,
-                      int natoms, const double* pos, const double* sigma, int numax, int cube, void* coeff,
-                      void* stream) {
-  return bloch_call(h, grid, kvec, 0, psi, coeff, nbands, natoms, pos, sigma, numax, cube, stream);
+                      int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
+                      void* coeff, void* stream) {
+  return bloch_call(h, grid, kvec, 0, psi, coeff, nbands, natoms, pos, sigma, numax, cube, prec, stream);
 }
 
 int sho_add_bloch(sho_handle* h, const sho_grid* grid, const double* kvec, const void* coeff, int nbands, int natoms,
-                  const double* pos, const double* sigma, int numax, int cube, void* psi, void* stream) {
-  return bloch_call(h, grid, kvec, 1, coeff, psi, nbands, natoms, pos, sigma, numax, cube, stream);
+                  const double* pos, const double* sigma, int numax, int cube, sho_prec prec, void* psi,
+                  void* stream) {
+  return bloch_call(h, grid, kvec, 1, coeff, psi, nbands, natoms, pos, sigma, numax, cube, prec, stream);
 }
 
 int sho_plane_plan_check(const sho_grid* grid, int natoms, const double* pos, const double* sigma, int cube,
@@ -789,9 +846,12 @@ int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype,
 // t2_out != nullptr (fused non-local action): where the path has a separate z-pass (FP64-accurate form,
 // plane sweep) stop after the per-plane y-pass sums, leave them in t2_out ([A][cube][P][B], compute type)
 // and set *at_t2; other paths write coeff as usual.
+// bloch != nullptr: the FP64-accurate Bloch projection (complex psi and coeff as 2 real bands per band,
+// nbands counting both), its per-atom phases uploaded behind the per-plane sums.
 static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                         int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
-                        void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2) {
+                        void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2,
+                        const std::vector<BlochPh>* bloch) {
   if (at_t2) *at_t2 = false;
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
@@ -812,7 +872,10 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   }
   SHO_TRY(begin_call(h, s));
   const bool ff_t2 = prec == SHO_P_FF64 && t2_out;
-  if (prec == SHO_P_FF64 && !ff_t2) SHO_TRY(ensure_workspace(h, ff_t2_bytes(natoms, cube, numax, nbands)));
+  const size_t o_bloch = (ff_t2_bytes(natoms, cube, numax, nbands) + 255) & ~(size_t)255;
+  if (prec == SHO_P_FF64 && !ff_t2)
+    SHO_TRY(ensure_workspace(h, o_bloch + (bloch ? bloch->size() * sizeof(BlochPh) : 0)));
+  if (bloch) SHO_TRY(upload(h, o_bloch, bloch->data(), bloch->size() * sizeof(BlochPh), s));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[0].key != key) {
     std::vector<int> order = spatial_order(grid, at);
@@ -835,6 +898,10 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   L.t2_only = ff_t2;
   L.status = h->dstatus;
   L.chk = make_check(h, grid, nbands, natoms, numax, cube);
+  if (bloch) {
+    L.chk = DevCheck{};  // the Bloch kernels run unchecked
+    L.bloch = reinterpret_cast<const BlochPh*>(static_cast<char*>(h->ws) + o_bloch);
+  }
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
                         : prec == SHO_P_FF64 ? launch_project_ff(L)
@@ -860,7 +927,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
 static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
                     sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
                     int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream,
-                    const NonlocalIn* nl = nullptr) {
+                    const NonlocalIn* nl, const std::vector<BlochPh>* bloch) {
   if (!h) return SHO_ERR_ARG;
   if (!std::isfinite(alpha)) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
@@ -894,6 +961,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   const size_t o_t2 = cv.take(t2_bytes(natoms, cube, numax, nbands, tc));
   const size_t o_txm = cv.take((size_t)natoms * cube * txm_bytes_per_point(numax));
   const size_t o_oz = prec == SHO_P_FF64 ? cv.take(oz_layout(natoms, cube, nbands).total) : 0;
+  const size_t o_bloch = bloch ? cv.take(bloch->size() * sizeof(BlochPh)) : 0;
   SHO_TRY(begin_call(h, s));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[1].key != key) {
@@ -909,6 +977,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
     h->geo[1].extra = max_plane;
   }
   SHO_TRY(ensure_workspace(h, cv.off));
+  if (bloch) SHO_TRY(upload(h, o_bloch, bloch->data(), bloch->size() * sizeof(BlochPh), s));
   char* ws = static_cast<char*>(h->ws);
   const char* gm = static_cast<const char*>(h->geo[1].mem);
   ExpandLaunch L;
@@ -929,6 +998,10 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   if (prec == SHO_P_FF64) L.oz = ws + o_oz;
   L.stop_stage = h->stop_rows;
   L.chk = make_check(h, grid, nbands, natoms, numax, cube);
+  if (bloch) {
+    L.chk = DevCheck{};  // the Bloch kernels run unchecked
+    L.bloch = reinterpret_cast<const BlochPh*>(ws + o_bloch);
+  }
   L.scale = alpha;
   if (nl) L.nl = *nl;
   L.kernel = h->expand_kernel;

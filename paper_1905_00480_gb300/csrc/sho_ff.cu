@@ -50,11 +50,14 @@ struct FfProjectSmem {
 // the slab, converted from its float pair to FP64, goes to a workspace; the z-pass is k_project_ff_zpass.
 // Without z-pass accumulators a lane holds about 130 registers, and the ring two rows.
 // CHK: device checks of every psi and workspace index (sho_set_device_checks), a separate instantiation.
-template <int NU, bool CHK = false>
+// BLOCH: complex psi of a Bloch wave (Sec. 2.5), its (re, im) pairs as two real bands in neighbouring
+// lanes; the x-pass sum turns by the x translation's phase where the cube row crosses the cell boundary,
+// and each row's x-pass result by the phase of its translation, so that the y- and z-passes stay real.
+template <int NU, bool CHK = false, bool BLOCH = false>
 __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* __restrict__ psi,
                                                       const AtomDev* __restrict__ atoms, int zsplit,
                                                       double* __restrict__ t2g, int* __restrict__ status,
-                                                      DevCheck dc) {
+                                                      DevCheck dc, const BlochPh* __restrict__ bph) {
   using BS = Basis<NU>;
   using SM = FfProjectSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -166,22 +169,50 @@ __global__ void __launch_bounds__(kWarp) k_project_ff(GridDev g, const double* _
       float S[NP], E[NP];
 #pragma unroll
       for (int n = 0; n < NP; n++) S[n] = E[n] = 0.0f;
+      auto xpass = [&](int x0, int x1) {
 #pragma unroll 4
-      for (int ix = xlo; ix < xhi; ix++) {
-        const double pd = st[ix * 32 + lane];
-        range_bad |= ff_out_of_range(pd);
-        const ff pv = ff_from_double(pd);
-        const float4* f4 = reinterpret_cast<const float4*>(phx + (size_t)ix * NPX);
+        for (int ix = x0; ix < x1; ix++) {
+          const double pd = st[ix * 32 + lane];
+          range_bad |= ff_out_of_range(pd);
+          const ff pv = ff_from_double(pd);
+          const float4* f4 = reinterpret_cast<const float4*>(phx + (size_t)ix * NPX);
 #pragma unroll
-        for (int q = 0; q < NPX / 2; q++) {
-          const float4 f = f4[q];
-          if (2 * q < NP) ff_dot_step(S[2 * q], E[2 * q], pv, ff{f.x, f.y});
-          if (2 * q + 1 < NP) ff_dot_step(S[2 * q + 1], E[2 * q + 1], pv, ff{f.z, f.w});
+          for (int q = 0; q < NPX / 2; q++) {
+            const float4 f = f4[q];
+            if (2 * q < NP) ff_dot_step(S[2 * q], E[2 * q], pv, ff{f.x, f.y});
+            if (2 * q + 1 < NP) ff_dot_step(S[2 * q + 1], E[2 * q + 1], pv, ff{f.z, f.w});
+          }
         }
-      }
+      };
       ff t1[NP];
+      if constexpr (BLOCH) {
+        // points before the crossing w, the sum turned by ph(before) / ph(after), the points after it, and
+        // the row's sum turned by the phase of the last run (y and z bits of this row and plane)
+        const BlochPh& bp = bph[a];
+        const int wx = bp.w[0];
+        xpass(xlo, min(xhi, wx));
+        const float4 xst = bp.xstep;
+        if (wx > xlo && wx < xhi && !ff_is_one(xst)) {
 #pragma unroll
-      for (int n = 0; n < NP; n++) t1[n] = ff_norm(S[n], E[n]);
+          for (int n = 0; n < NP; n++) {
+            const ff v = ff_rotate(ff_norm(S[n], E[n]), xst, lane);
+            S[n] = v.hi;
+            E[n] = v.lo;
+          }
+        }
+        xpass(max(xlo, wx), xhi);
+        const float4 ph = bp.ph[(xhi > wx ? 1 : 0) + (iy >= bp.w[1] ? 2 : 0) + (iz >= bp.w[2] ? 4 : 0)];
+        const bool one = ff_is_one(ph);
+#pragma unroll
+        for (int n = 0; n < NP; n++) {
+          t1[n] = ff_norm(S[n], E[n]);
+          if (!one) t1[n] = ff_rotate(t1[n], ph, lane);
+        }
+      } else {
+        xpass(xlo, xhi);
+#pragma unroll
+        for (int n = 0; n < NP; n++) t1[n] = ff_norm(S[n], E[n]);
+      }
       // y-pass (a4) as float-float dot steps
 #pragma unroll
       for (int ny = 0; ny < NP; ny++) {
@@ -340,14 +371,18 @@ struct FfBlkSmem {
 };
 
 // CHK: device checks of every psi and z-pass-result index (sho_set_device_checks), a separate instantiation.
-template <int NU, bool CHK = false>
+// BLOCH: complex coefficients and psi of a Bloch wave (Sec. 2.5), (re, im) pairs as two real bands in
+// neighbouring lanes; the y-pass result of each (atom, row) turns by the phase of the translation of the
+// tile points it updates (one per run of the tile row), so that the z-, y- and x-passes stay real.
+template <int NU, bool CHK = false, bool BLOCH = false>
 __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, const AtomDev* __restrict__ atoms,
                                                                    const int* __restrict__ plane_ptr,
                                                                    const int* __restrict__ plane_atoms,
                                                                    const float2* __restrict__ tyff,
                                                                    const float2* __restrict__ txff,
                                                                    const float2* __restrict__ t2,
-                                                                   double* __restrict__ psi, DevCheck dc) {
+                                                                   double* __restrict__ psi, DevCheck dc,
+                                                                   const BlochPh* __restrict__ bph) {
   using BS = Basis<NU>;
   using SM = FfBlkSmem<NU>;
   constexpr int NP = BS::NP, P = BS::P, NPX = SM::NPX;
@@ -505,6 +540,21 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
         const int shift = run ? dx - Nx : dx;
         // tile points of this run whose cube index ix = x + shift lies in the row's support
         const int xa = max(run ? max(r1a, r0b) : r0a, slo - shift), xb = min(run ? r1b : r0b, shi - shift);
+        ff t1r[NP];
+#pragma unroll
+        for (int n = 0; n < NP; n++) t1r[n] = t1f[n];
+        if constexpr (BLOCH) {
+          // the run's points share one translation: its phase from the bits of cube point xa + shift,
+          // cube row iy and cube plane r.w
+          if (xa < xb) {
+            const BlochPh& bp = bph[r.x];
+            const float4 ph = bp.ph[(xa + shift >= bp.w[0] ? 1 : 0) + (iy >= bp.w[1] ? 2 : 0) + (r.w >= bp.w[2] ? 4 : 0)];
+            if (!ff_is_one(ph)) {
+#pragma unroll
+              for (int n = 0; n < NP; n++) t1r[n] = ff_rotate(t1f[n], ph, lane);
+            }
+          }
+        }
 #pragma unroll 2
         for (int x = xa; x < xb; x++) {
           const int ix = x + shift;
@@ -514,8 +564,8 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
 #pragma unroll
           for (int qn = 0; qn < NPX / 2; qn++) {
             const float4 f = f4[qn];
-            if (2 * qn < NP) ff_dot_step(v.x, v.y, t1f[2 * qn], ff{f.x, f.y});
-            if (2 * qn + 1 < NP) ff_dot_step(v.x, v.y, t1f[2 * qn + 1], ff{f.z, f.w});
+            if (2 * qn < NP) ff_dot_step(v.x, v.y, t1r[2 * qn], ff{f.x, f.y});
+            if (2 * qn + 1 < NP) ff_dot_step(v.x, v.y, t1r[2 * qn + 1], ff{f.z, f.w});
           }
           accw[x * kWarp + lane] = v;
         }
@@ -552,11 +602,17 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   if (!p.t2) return cudaErrorInvalidValue;
   const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
   auto kern = p.chk.flag ? k_project_ff<NU, true> : k_project_ff<NU, false>;
+  if constexpr (NU <= kBlochFfMaxNumax) {
+    if (p.bloch) kern = k_project_ff<NU, false, true>;
+  } else if (p.bloch) {
+    return cudaErrorInvalidValue;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned nbt = (unsigned)((p.g.nbands + kWarp - 1) / kWarp);
   kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
-      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status, p.chk);
+      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status, p.chk,
+      p.bloch);
   e = cudaGetLastError();
   if (e != cudaSuccess || p.t2_only) return e;
   const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
@@ -579,15 +635,20 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   if (e != cudaSuccess) return e;
   // the x-pass on the tensor cores when chosen (kernel choice 2) and where it applies; by default the
   // float-float block gather, which measures as fast on GB300 at a tenth of the error
-  if (p.kernel == 2 && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
+  if (p.kernel == 2 && !p.bloch && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
   auto kern = p.chk.flag ? k_expand_blk_ff<NU, true> : k_expand_blk_ff<NU, false>;
+  if constexpr (NU <= kBlochFfMaxNumax) {
+    if (p.bloch) kern = k_expand_blk_ff<NU, false, true>;
+  } else if (p.bloch) {
+    return cudaErrorInvalidValue;
+  }
   const size_t smem = FfBlkSmem<NU>::bytes(p.g.cube, p.max_plane);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nseg = (p.g.n[0] + kFfXSeg - 1) / kFfXSeg, nyb = (p.g.n[1] + kFfRows - 1) / kFfRows;
   kern<<<dim3((unsigned)nseg * nyb * p.g.n[2], (p.g.nbands + kWarp - 1) / kWarp), kFfRows * kWarp, smem, p.stream>>>(
       p.g, p.atoms, p.plane_ptr, p.plane_atoms, tyff, txff, static_cast<const float2*>(p.t2),
-      static_cast<double*>(p.psi), p.chk);
+      static_cast<double*>(p.psi), p.chk, p.bloch);
   return cudaGetLastError();
 }
 

@@ -99,4 +99,24 @@ __device__ __forceinline__ ff ff_norm(float s, float c) {
   return r;
 }
 
+// v times the unit complex number ph = (re.hi, re.lo, im.hi, im.lo) for complex data held by lane pairs,
+// the real part in the even lane and the imaginary part in the odd one (every lane of the warp calls it):
+// even lane re c - im s, odd lane im c + re s, as two float-float products and a TwoSum (the products may
+// cancel, so no ordering of the pair is assumed).
+__device__ __forceinline__ ff ff_rotate(ff v, const float4 ph, int lane) {
+  const ff u{__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1)};
+  const float sg = (lane & 1) ? 1.0f : -1.0f;
+  float s = 0.0f, c = 0.0f;
+  ff_dot_step(s, c, v, ff{ph.x, ph.y});
+  ff_dot_step(s, c, u, ff{sg * ph.z, sg * ph.w});
+  const float t = s + c;
+  const float bb = t - s;
+  return ff{t, (s - (t - bb)) + (c - bb)};
+}
+
+// True when ph is exactly 1 (no turn needed).
+__device__ __forceinline__ bool ff_is_one(const float4 ph) {
+  return ph.x == 1.0f && ph.y == 0.0f && ph.z == 0.0f && ph.w == 0.0f;
+}
+
 }  // namespace sho

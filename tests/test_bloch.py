@@ -1,4 +1,5 @@
-"""Bloch (complex) projection and expansion on the GPU against the oracle (FP64, 1e-12)."""
+"""Bloch (complex) projection and expansion on the GPU against the oracle (FP64 and FP64-accurate forms,
+1e-12)."""
 import numpy as np
 import pytest
 
@@ -19,8 +20,9 @@ def _case(seed, grid, h, natoms, nbands):
     return rng, pos, sig, psi
 
 
+@pytest.mark.parametrize("prec", ["fp64", "ff64"])
 @pytest.mark.parametrize("numax,nbands", [(3, 5), (5, 40), (7, 33)])
-def test_bloch_project_and_add(numax, nbands):
+def test_bloch_project_and_add(numax, nbands, prec):
     require_gpu()
     import torch
     from paper_1905_00480_gb300 import api
@@ -28,14 +30,92 @@ def test_bloch_project_and_add(numax, nbands):
     rng, pos, sig, psi = _case(910 + numax, grid, h, 5, nbands)
     k = np.array([0.9, -0.35, 1.7])
     psi_d = torch.from_numpy(psi).cuda()
-    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h).cpu().numpy()
+    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec=prec).cpu().numpy()
     ref = oracle.project_bloch(grid, h, k, psi, pos, sig, numax, cube)
     assert_coeff_close(got.view(np.float64), ref.view(np.float64), TOL_FP64)
     coef = rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)
     out = psi_d.clone()
-    api.add_bloch(out, torch.from_numpy(coef).cuda(), k, pos, sig, numax, cube, h)
+    api.add_bloch(out, torch.from_numpy(coef).cuda(), k, pos, sig, numax, cube, h, prec=prec)
     ref2 = oracle.add_bloch(grid, h, k, psi, pos, sig, numax, cube, coef)
     assert rel_norm((out.cpu().numpy() - psi).view(np.float64), (ref2 - psi).view(np.float64)) <= TOL_FP64
+
+
+def test_bloch_ff64_cubes_across_every_cell_face():
+    """Atoms on both sides of every face and in the corners, so that cube rows cross the boundary at
+    their start and at their end along each axis, and tile segments meet both runs; a grid wider than
+    the FP64 expansion's row limit."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, cube, numax, nbands = (456, 40, 36), 0.2, 16, 4, 6
+    L = np.array(grid) * h
+    rng = np.random.default_rng(941)
+    pos = np.array([[0.05 * h, 0.3 * h, 0.2 * h], [L[0] - 0.3 * h, L[1] - 0.1 * h, L[2] - 0.45 * h],
+                    [L[0] / 2, 0.4 * h, L[2] - 0.2 * h], [0.6 * h, L[1] / 2, L[2] / 2],
+                    [L[0] - 2.3 * h, 2.7 * h, 1.1 * h]])
+    sig = np.full(len(pos), 0.75)
+    psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands)) + 1j * rng.standard_normal(
+        (grid[2], grid[1], grid[0], nbands))
+    k = np.array([-1.3, 0.8, 2.1])
+    psi_d = torch.from_numpy(psi).cuda()
+    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec="ff64").cpu().numpy()
+    ref = oracle.project_bloch(grid, h, k, psi, pos, sig, numax, cube)
+    assert_coeff_close(got.view(np.float64), ref.view(np.float64), TOL_FP64)
+    coef = rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)
+    out = torch.zeros_like(psi_d)
+    api.add_bloch(out, torch.from_numpy(coef).cuda(), k, pos, sig, numax, cube, h, prec="ff64")
+    ref2 = oracle.add_bloch(grid, h, k, np.zeros_like(psi), pos, sig, numax, cube, coef)
+    assert rel_norm(out.cpu().numpy().view(np.float64), ref2.view(np.float64)) <= TOL_FP64
+
+
+def test_bloch_ff64_zero_k_is_the_real_form_on_each_part():
+    """k = 0: every phase is 1 and the FP64-accurate Bloch kernels are the real ones over the (re, im)
+    pairs, so each part matches the real FP64-accurate projection and expansion bit for bit."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, numax, cube = (40, 36, 34), 0.2, 5, 32
+    rng, pos, sig, psi = _case(925, grid, h, 4, 12)
+    psi_d = torch.from_numpy(psi).cuda()
+    c0 = api.project_bloch(psi_d, [0, 0, 0], pos, sig, numax, cube, h, prec="ff64")
+    cr = api.project(psi_d.real.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
+    ci = api.project(psi_d.imag.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
+    assert torch.equal(c0.real.contiguous(), cr) and torch.equal(c0.imag.contiguous(), ci)
+    coef = torch.from_numpy(rng.standard_normal(c0.shape) + 1j * rng.standard_normal(c0.shape)).cuda()
+    out = psi_d.clone()
+    api.add_bloch(out, coef, [0, 0, 0], pos, sig, numax, cube, h, prec="ff64")
+    re, im = psi_d.real.contiguous(), psi_d.imag.contiguous()
+    api.add(re, coef.real.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
+    api.add(im, coef.imag.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
+    assert torch.equal(out.real.contiguous(), re) and torch.equal(out.imag.contiguous(), im)
+
+
+def test_bloch_ff64_adjoint_and_fp64_agreement():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, numax, cube = (40, 36, 34), 0.2, 6, 32
+    rng, pos, sig, psi = _case(935, grid, h, 4, 7)
+    psi_d = torch.from_numpy(psi).cuda()
+    k = [1.1, 0.4, -0.8]
+    c = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec="ff64")
+    c64 = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec="fp64")
+    assert rel_norm(torch.view_as_real(c).cpu().numpy(), torch.view_as_real(c64).cpu().numpy()) <= TOL_FP64
+    coef = torch.from_numpy(rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).cuda()
+    ec = api.add_bloch(torch.zeros_like(psi_d), coef, k, pos, sig, numax, cube, h, prec="ff64")
+    lhs = torch.vdot(c.flatten(), coef.flatten()).item()
+    rhs = h ** 3 * torch.vdot(psi_d.flatten(), ec.flatten()).item()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_bloch_rejects_other_precisions():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api, ShoError
+    psi = torch.zeros((16, 16, 16, 2), dtype=torch.complex128, device="cuda")
+    for prec in ("fp32", "tf32", "bf16"):
+        with pytest.raises(ShoError):
+            api.project_bloch(psi, [0.1, 0, 0], np.array([[2.0, 2.0, 2.0]]), [1.0], 1, 16, 0.25, prec=prec)
 
 
 def test_bloch_zero_k_matches_real_path_and_adjoint():
@@ -76,5 +156,6 @@ def test_bloch_rejects_open_grid():
     sig = np.array([1.0])
     st = N.lib().sho_project_bloch(api.default_handle(0).ptr, ctypes.byref(g), k.ctypes.data_as(N._DP),
                                    ctypes.c_void_p(psi.data_ptr()), 2, 1, pos.ctypes.data_as(N._DP),
-                                   sig.ctypes.data_as(N._DP), 1, 16, ctypes.c_void_p(out.data_ptr()), None)
+                                   sig.ctypes.data_as(N._DP), 1, 16, N.PRECS["fp64"], ctypes.c_void_p(out.data_ptr()),
+                                   None)
     assert st != 0
