@@ -703,45 +703,11 @@ int sho_radial_transform(sho_handle* h, int natoms, int numax, int nbands, const
 static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                         int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                         void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2,
-                        const std::vector<BlochPh>* bloch = nullptr);
+                        const BlochArg* bloch = nullptr);
 static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
                     sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
                     int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream,
-                    const NonlocalIn* nl = nullptr, const std::vector<BlochPh>* bloch = nullptr);
-
-// Phases of the FP64-accurate Bloch kernels (BlochPh): per atom and axis the cube point w where the
-// cube crosses the cell boundary (floor((o + i) / n) steps from f0 to f0 + 1 there) and the eight
-// e^{sgn i k.T} of the translations T_d = (f0_d + b_d) n_d h, as float pairs.
-static std::vector<BlochPh> bloch_phases(const sho_grid* grid, const std::vector<AtomDev>& at, const double* k,
-                                         double sgn) {
-  auto split = [](double v, float& hi, float& lo) {
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-  };
-  std::vector<BlochPh> out(at.size());
-  for (size_t a = 0; a < at.size(); a++) {
-    BlochPh& b = out[a];
-    long long f0[3];
-    for (int d = 0; d < 3; d++) {
-      const long long n = grid->n[d], o = at[a].o[d];
-      f0[d] = o >= 0 ? o / n : -((-o + n - 1) / n);  // floor(o / n)
-      b.w[d] = (int)((f0[d] + 1) * n - o);             // in [1, n]
-    }
-    b.w[3] = 0;
-    for (int bits = 0; bits < 8; bits++) {
-      double ang = 0.0;
-      for (int d = 0; d < 3; d++)
-        ang += k[d] * (double)(f0[d] + ((bits >> d) & 1)) * grid->n[d] * grid->h;
-      float4& ph = b.ph[bits];
-      split(std::cos(sgn * ang), ph.x, ph.y);
-      split(std::sin(sgn * ang), ph.z, ph.w);
-    }
-    const double ax = -sgn * k[0] * grid->n[0] * grid->h;
-    split(std::cos(ax), b.xstep.x, b.xstep.y);
-    split(std::sin(ax), b.xstep.z, b.xstep.w);
-  }
-  return out;
-}
+                    const NonlocalIn* nl = nullptr, const BlochArg* bloch = nullptr);
 
 static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, int op, const void* src, void* dst,
                       int nbands, int natoms, const double* pos, const double* sigma, int numax, int cube,
@@ -760,13 +726,12 @@ static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, i
   if (!src || !dst) return SHO_ERR_ARG;
   if (prec == SHO_P_FF64) {
     // the real FP64-accurate kernels over the (re, im) pairs as 2 nbands real bands, with the phases
-    const std::vector<BlochPh> ph =
-        bloch_phases(grid, make_atoms(grid, natoms, pos, sigma, cube), kvec, op == 0 ? 1.0 : -1.0);
+    const BlochArg bl{{kvec[0], kvec[1], kvec[2]}, op == 0 ? 1.0 : -1.0};
     if (op == 0)
       return project_impl(h, grid, src, SHO_F64, 2 * nbands, natoms, pos, sigma, numax, cube, SHO_P_FF64, dst,
-                          SHO_F64, stream, nullptr, nullptr, &ph);
+                          SHO_F64, stream, nullptr, nullptr, &bl);
     return add_impl(h, grid, 1.0, 0, src, SHO_F64, 2 * nbands, natoms, pos, sigma, numax, cube, SHO_P_FF64, dst,
-                    SHO_F64, stream, nullptr, &ph);
+                    SHO_F64, stream, nullptr, &bl);
   }
   DeviceGuard guard(h->device);
   if (!guard.ok) return SHO_ERR_CUDA;
@@ -851,7 +816,7 @@ int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype,
 static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                         int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                         void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2,
-                        const std::vector<BlochPh>* bloch) {
+                        const BlochArg* bloch) {
   if (at_t2) *at_t2 = false;
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
@@ -873,9 +838,7 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   SHO_TRY(begin_call(h, s));
   const bool ff_t2 = prec == SHO_P_FF64 && t2_out;
   const size_t o_bloch = (ff_t2_bytes(natoms, cube, numax, nbands) + 255) & ~(size_t)255;
-  if (prec == SHO_P_FF64 && !ff_t2)
-    SHO_TRY(ensure_workspace(h, o_bloch + (bloch ? bloch->size() * sizeof(BlochPh) : 0)));
-  if (bloch) SHO_TRY(upload(h, o_bloch, bloch->data(), bloch->size() * sizeof(BlochPh), s));
+  if (prec == SHO_P_FF64 && !ff_t2) SHO_TRY(ensure_workspace(h, o_bloch + (bloch ? natoms * sizeof(BlochPh) : 0)));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[0].key != key) {
     std::vector<int> order = spatial_order(grid, at);
@@ -900,7 +863,14 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   L.chk = make_check(h, grid, nbands, natoms, numax, cube);
   if (bloch) {
     L.chk = DevCheck{};  // the Bloch kernels run unchecked
-    L.bloch = reinterpret_cast<const BlochPh*>(static_cast<char*>(h->ws) + o_bloch);
+    BlochPh* ph = reinterpret_cast<BlochPh*>(static_cast<char*>(h->ws) + o_bloch);
+    L.bloch = ph;
+    const cudaError_t e = launch_bloch_phases(L.g, L.atoms, natoms, *bloch, ph, s);
+    if (e != cudaSuccess) {
+      h->last_cuda = e;
+      h->last_where = "Bloch phases";
+      return SHO_ERR_CUDA;
+    }
   }
   L.stream = s;
   const cudaError_t e = prec == SHO_P_FP64 ? launch_project(L)
@@ -927,7 +897,7 @@ int sho_project(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype 
 static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overwrite, const void* coeff,
                     sho_dtype coeff_dtype, int nbands, int natoms, const double* pos, const double* sigma, int numax,
                     int cube, sho_prec prec, void* psi, sho_dtype psi_dtype, void* stream,
-                    const NonlocalIn* nl, const std::vector<BlochPh>* bloch) {
+                    const NonlocalIn* nl, const BlochArg* bloch) {
   if (!h) return SHO_ERR_ARG;
   if (!std::isfinite(alpha)) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, SHO_MAX_NUMAX));
@@ -961,7 +931,7 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   const size_t o_t2 = cv.take(t2_bytes(natoms, cube, numax, nbands, tc));
   const size_t o_txm = cv.take((size_t)natoms * cube * txm_bytes_per_point(numax));
   const size_t o_oz = prec == SHO_P_FF64 ? cv.take(oz_layout(natoms, cube, nbands).total) : 0;
-  const size_t o_bloch = bloch ? cv.take(bloch->size() * sizeof(BlochPh)) : 0;
+  const size_t o_bloch = bloch ? cv.take((size_t)natoms * sizeof(BlochPh)) : 0;
   SHO_TRY(begin_call(h, s));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[1].key != key) {
@@ -977,7 +947,6 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
     h->geo[1].extra = max_plane;
   }
   SHO_TRY(ensure_workspace(h, cv.off));
-  if (bloch) SHO_TRY(upload(h, o_bloch, bloch->data(), bloch->size() * sizeof(BlochPh), s));
   char* ws = static_cast<char*>(h->ws);
   const char* gm = static_cast<const char*>(h->geo[1].mem);
   ExpandLaunch L;
@@ -1000,7 +969,14 @@ static int add_impl(sho_handle* h, const sho_grid* grid, double alpha, int overw
   L.chk = make_check(h, grid, nbands, natoms, numax, cube);
   if (bloch) {
     L.chk = DevCheck{};  // the Bloch kernels run unchecked
-    L.bloch = reinterpret_cast<const BlochPh*>(ws + o_bloch);
+    BlochPh* ph = reinterpret_cast<BlochPh*>(ws + o_bloch);
+    L.bloch = ph;
+    const cudaError_t e = launch_bloch_phases(L.g, L.atoms, natoms, *bloch, ph, s);
+    if (e != cudaSuccess) {
+      h->last_cuda = e;
+      h->last_where = "Bloch phases";
+      return SHO_ERR_CUDA;
+    }
   }
   L.scale = alpha;
   if (nl) L.nl = *nl;

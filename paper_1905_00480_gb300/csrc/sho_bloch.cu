@@ -243,6 +243,50 @@ __global__ void __launch_bounds__(kWarp) k_bloch_rows(GridDev g, const AtomDev* 
   }
 }
 
+// Phases of the FP64-accurate Bloch kernels (BlochPh), one thread per atom: per axis the cube point w where
+// floor((o + i) / n) steps from f0 to f0 + 1 (the cube crosses the cell boundary), and the eight
+// e^{sgn i k.T} of the translations T_d = (f0_d + b_d) n_d h, split into float pairs.
+__global__ void k_bloch_phases(GridDev g, const AtomDev* __restrict__ atoms, int natoms, double3 kv, double sgn,
+                               BlochPh* __restrict__ out) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= natoms) return;
+  const AtomDev at = atoms[a];
+  const double kd[3] = {kv.x, kv.y, kv.z};
+  BlochPh b;
+  long long f0[3];
+  for (int d = 0; d < 3; d++) {
+    const long long n = g.n[d], o = at.o[d];
+    f0[d] = o >= 0 ? o / n : -((-o + n - 1) / n);  // floor(o / n)
+    b.w[d] = (int)((f0[d] + 1) * n - o);             // in [1, n]
+  }
+  b.w[3] = 0;
+  auto put = [](double v, float& hi, float& lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+  };
+  for (int bits = 0; bits < 8; bits++) {
+    double ang = 0.0;
+    for (int d = 0; d < 3; d++) ang += kd[d] * (double)(f0[d] + ((bits >> d) & 1)) * (double)g.n[d] * g.h;
+    double sn, cs;
+    sincos(sgn * ang, &sn, &cs);
+    put(cs, b.ph[bits].x, b.ph[bits].y);
+    put(sn, b.ph[bits].z, b.ph[bits].w);
+  }
+  double sn, cs;
+  sincos(-sgn * kd[0] * (double)g.n[0] * g.h, &sn, &cs);
+  put(cs, b.xstep.x, b.xstep.y);
+  put(sn, b.xstep.z, b.xstep.w);
+  out[a] = b;
+}
+
+cudaError_t launch_bloch_phases(const GridDev& g, const AtomDev* atoms, int natoms, const BlochArg& arg, BlochPh* ph,
+                                cudaStream_t s) {
+  if (natoms <= 0) return cudaSuccess;
+  k_bloch_phases<<<(natoms + 63) / 64, 64, 0, s>>>(g, atoms, natoms, make_double3(arg.k[0], arg.k[1], arg.k[2]),
+                                                  arg.sgn, ph);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------- launchers
 template <int NU>
 static cudaError_t bloch_nu(const BlochLaunch& p) {

@@ -65,6 +65,13 @@ struct BlochPh {
 };
 static_assert(sizeof(BlochPh) == 160, "BlochPh layout");
 constexpr int kBlochFfMaxNumax = 7;  // the FP64-accurate Bloch kernels are built for numax 0..7
+struct BlochArg {
+  double k[3];  // Bloch vector
+  double sgn;   // +1 projection, -1 expansion
+};
+// ph[a] for every atom from its cube origin (one thread per atom, FP64 sincos)
+cudaError_t launch_bloch_phases(const GridDev& g, const AtomDev* atoms, int natoms, const BlochArg& arg, BlochPh* ph,
+                                cudaStream_t s);
 
 // Bounded waits of the device pipelines give up after this many SM clock cycles (~2 s at 2.07 GHz)
 // unless a handle's fault-injection setting (include/sho_fault.h) shortens it.
