@@ -23,21 +23,24 @@
 //   * the point's update is F (D_2 + D_3 + D_4 + D_5..8), summed as a float pair and added to psi in FP64.
 // The operands are TF32 (digits of at most 9 significant bits are exact in TF32), K = 8 states.
 //
-// A CTA owns a tile of one z plane: 2 grid rows x 32 x points x 128 bands, thread = (row, band).  Its
-// four level accumulators per row live in tensor memory (2 x 4 x 32 = 256 columns) for the whole atom
-// loop.  The y functions of the listed atoms at the tile's two rows are gathered into shared memory once.
-// For each atom whose cube meets the tile (ascending order), with two operand slots used by atom parity:
-//   * once the MMAs of atom li - 2 are done, one thread stages the atom's x digit window for the tile's
-//     32 points (six digits x two chunks of four states) into the slot by bulk copies;
-//   * each thread runs the float-float y-pass of its (row, band) on its band's T2 slice (float pairs,
-//     loaded from global memory one atom ahead), cuts T1 into six digit slices and writes them into the
-//     slot as the A operands;
-//   * after one block barrier, one thread issues 2 rows x 26 digit-pair MMAs (M = 128 bands, N = 32
-//     points, K = 8) from the slot and commits them to the slot's barrier.
-// At the end each thread reads its row's four accumulators for its band, and adds the 32 points to psi.
-// Deterministic: fixed atom order, exact integer sums in the leading levels.  Every wait is bounded; on
-// expiry the kernel records kStatusTimeout, waits (bounded) for its own copies and MMAs, frees tensor
-// memory and returns without touching psi.
+// A CTA owns a tile of one z plane: 2 grid rows x 32 x points x 128 bands, with 256 compute threads,
+// thread = (row, band), and one more warp whose first thread stages and issues.  The four level
+// accumulators per row live in tensor memory (2 x 4 x 32 = 256 columns) for the whole atom loop.  The y
+// functions of the listed atoms at the tile's two rows are gathered into shared memory once.  For each
+// atom whose cube meets the tile (ascending order), with two operand slots used by atom parity:
+//   * the compute threads, once the MMAs of atom li - 2 are done, run the float-float y-pass of their
+//     (row, band) on the band's T2 slice (float pairs, loaded from global memory one atom ahead), cut T1
+//     into six digit slices, write them into the slot as the A operands and arrive on the slot's operand
+//     barrier;
+//   * the issuing thread, once the MMAs of atom li - 2 are done, stages the atom's x digit window for the
+//     tile's 32 points (six digits x two chunks of four states) into the slot by bulk copies, waits for
+//     the A operands and the window, issues 2 rows x 26 digit-pair MMAs (M = 128 bands, N = 32 points,
+//     K = 8) and commits them to the slot's barrier.
+// No block barrier per atom: the two sides meet on the slot barriers only.  At the end each compute thread
+// reads its row's four accumulators for its band and adds the 32 points to psi.
+// Deterministic: fixed atom order, exact integer sums in the leading levels.  Every wait is bounded; the
+// first one that runs out stops every thread's loop (a shared flag), the kernel records kStatusTimeout,
+// waits (bounded) for its own copies and MMAs, frees tensor memory and returns without touching psi.
 #include "sho_device.cuh"
 #include "sho_ff.cuh"
 #include "sho_umma.cuh"
@@ -47,7 +50,9 @@ namespace sho {
 constexpr int kOzRows = 2;                           // grid rows per tile
 constexpr int kOzX = 32;                             // x points per tile (the MMA N)
 constexpr int kOzBands = 128;                        // bands per tile (the MMA M)
-constexpr int kOzThreads = kOzRows * kOzBands;       // thread = (row, band)
+constexpr int kOzThreads = kOzRows * kOzBands;       // compute threads: thread = (row, band)
+constexpr int kOzComputeWarps = kOzThreads / 32;
+constexpr int kOzAllThreads = kOzThreads + 32;       // and one warp that stages and issues the MMAs
 constexpr int kOzDigits = 6;                         // digits per operand value
 constexpr int kOzMaxLevel = 8;                       // digit pairs (i, j) with i + j <= 8 are multiplied
 constexpr int kOzGroups = 4;                         // accumulators: levels 2, 3, 4 and 5..8
@@ -175,7 +180,7 @@ __global__ void __launch_bounds__(128) k_oz_tables(int natoms, int cube, int nba
 
 // ------------------------------------------------------------------------------------- expansion
 template <int NU>
-__global__ void __launch_bounds__(kOzThreads, 2)
+__global__ void __launch_bounds__(kOzAllThreads, 2)
     k_expand_ozaki(GridDev g, const AtomDev* __restrict__ atoms, const int* __restrict__ plane_ptr,
                    const int* __restrict__ plane_atoms, int max_plane, const float2* __restrict__ tyff,
                    const float2* __restrict__ t2, const float* __restrict__ dtab, const float* __restrict__ gpow,
@@ -196,9 +201,14 @@ __global__ void __launch_bounds__(kOzThreads, 2)
   const uint32_t bbar0 = cbar0 + 16;     // digit-window staging of slots 0 and 1
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 32);
   int* s_misc = reinterpret_cast<int*>(barp + 48);  // [0] list length, [1..8] warp counts (bytes 48..83)
+  // bytes 88..103: the A-operand barriers of the two slots; 104: abort flag; 108: atoms issued
   int4* slist = reinterpret_cast<int4*>(barp + 128);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rr = tid >> 7, bl = tid & 127;  // this thread's tile row and band
+  const bool mma_warp = warp == kOzComputeWarps;  // the warp that stages digit windows and issues the MMAs
+  const int rr = (tid >> 7) & 1, bl = tid & 127;  // a compute thread's tile row and band
+  const uint32_t fbar0 = cbar0 + 88;  // A operands of slots 0 and 1 written (every compute thread arrives)
+  volatile int* s_abort = reinterpret_cast<volatile int*>(barp + 104);  // a bounded wait ran out
+  int* s_issued = reinterpret_cast<int*>(barp + 108);                   // atoms whose MMAs were issued
 
   const int nseg = (Nx + kOzX - 1) / kOzX, nyb = (Ny + kOzRows - 1) / kOzRows;
   int bid = blockIdx.x;
@@ -210,19 +220,23 @@ __global__ void __launch_bounds__(kOzThreads, 2)
   const int b0 = blockIdx.y * kOzBands;
   const int nb = min(kOzBands, B - b0);  // bands of this tile (an even count)
   const int b = b0 + bl;
-  const bool bvalid = bl < nb;
+  const bool bvalid = !mma_warp && bl < nb;
   const int y = yb * kOzRows + rr;
   const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
 
   // atoms of the plane whose cube meets the tile, ascending: (atom, cube row of the tile's first row,
-  // cube-relative x offset, cube plane)
-  if (tid == 0) s_misc[0] = 0;
+  // cube-relative x offset, cube plane); the compute threads scan, every thread takes the barriers
+  if (tid == 0) {
+    s_misc[0] = 0;
+    *s_abort = 0;
+    *s_issued = 0;
+  }
   __syncthreads();
   for (int base = q0; base < q1; base += kOzThreads) {
     const int q = base + tid;
     int4 r = make_int4(-1, 0, 0, 0);
     bool m = false;
-    if (q < q1) {
+    if (!mma_warp && q < q1) {
       const int a = plane_atoms[q];
       const AtomDev at = atoms[a];
       int dy = yb * kOzRows - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
@@ -241,14 +255,14 @@ __global__ void __launch_bounds__(kOzThreads, 2)
       r = make_int4(a, dy, dx, dz);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, m);
-    if (lane == 0) s_misc[1 + warp] = __popc(bal);
+    if (lane == 0 && !mma_warp) s_misc[1 + warp] = __popc(bal);
     __syncthreads();
     int off = s_misc[0];
-    for (int w = 0; w < warp; w++) off += s_misc[1 + w];
+    for (int w = 0; w < warp && w < kOzComputeWarps; w++) off += s_misc[1 + w];
     if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = r;
     __syncthreads();
     if (tid == 0)
-      for (int w = 0; w < kOzThreads / 32; w++) s_misc[0] += s_misc[1 + w];
+      for (int w = 0; w < kOzComputeWarps; w++) s_misc[0] += s_misc[1 + w];
     __syncthreads();
   }
   const int nlist = s_misc[0];
@@ -261,12 +275,12 @@ __global__ void __launch_bounds__(kOzThreads, 2)
     return (yb * kOzRows + row < Ny && iy >= 0 && iy < C) ? iy : -1;
   };
   // the y functions of every listed atom at the tile's two rows (float pairs), and the tile's psi to L2
-  for (int i = tid; i < nlist * kOzRows * NP; i += kOzThreads) {
+  for (int i = tid; i < nlist * kOzRows * NP; i += kOzAllThreads) {
     const int li = i / (kOzRows * NP), row = (i / NP) % kOzRows, n = i % NP;
     const int iy = cube_row(li, row);
     ylist[i] = iy >= 0 ? tyff[((size_t)slist[li].x * NP + n) * C + iy] : make_float2(0.0f, 0.0f);
   }
-  for (int li = tid; li < nlist; li += kOzThreads)
+  for (int li = tid; li < nlist; li += kOzAllThreads)
     gexp[li] = (int)((__float_as_uint(gpow[slist[li].x]) >> 23) & 0xffu) - 127;
   if (tid < kOzRows * kOzX) {
     const int row = tid >> 5, x = tid & 31, yy = yb * kOzRows + row;
@@ -276,21 +290,22 @@ __global__ void __launch_bounds__(kOzThreads, 2)
     }
   }
 
-  // the frame F of this (row, band): a power of two above every covering atom's bound |T1_a| G_a
+  // the frame F of this (row, band): a power of two above every covering atom's bound |T1_a| G_a; the
+  // bounds of up to 8 atoms are loaded together
   float xb = 0.0f;
   if (bvalid && y < Ny) {
-    for (int l0 = 0; l0 < nlist; l0 += 4) {
-      float tv4[4], gv4[4];
+    for (int l0 = 0; l0 < nlist; l0 += 8) {
+      float tv8[8], gv8[8];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
+      for (int u = 0; u < 8; u++) {
         const int li = l0 + u;
         const bool in = li < nlist && cube_row(li, rr) >= 0;
         const int4 r = slist[min(li, nlist - 1)];
-        tv4[u] = in ? tmax[((size_t)r.x * C + r.w) * B + b] : 0.0f;
-        gv4[u] = in ? gpow[r.x] : 0.0f;
+        tv8[u] = in ? tmax[((size_t)r.x * C + r.w) * B + b] : 0.0f;
+        gv8[u] = in ? gpow[r.x] : 0.0f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; u++) xb = fmaxf(xb, tv4[u] * gv4[u]);
+      for (int u = 0; u < 8; u++) xb = fmaxf(xb, tv8[u] * gv8[u]);
     }
   }
   int eF = 0;
@@ -306,6 +321,8 @@ __global__ void __launch_bounds__(kOzThreads, 2)
     um_mbar_init(cbar0 + 8);
     um_mbar_init(bbar0);
     um_mbar_init(bbar0 + 8);
+    um_mbar_init_n(fbar0, kOzThreads);
+    um_mbar_init_n(fbar0 + 8, kOzThreads);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   tc05_fence_before();
@@ -313,138 +330,156 @@ __global__ void __launch_bounds__(kOzThreads, 2)
   tc05_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // lanes of this warp's bands
+  if (!mma_warp) {
 #pragma unroll
-  for (int c = 0; c < 4; c++) tmem_zero32(tlane + (uint32_t)(rr * kOzGroups * kOzX + 32 * c));
-
-  // digit window of atom li for the tile's 32 points into operand slot `slot` (one thread, bulk copies)
-  auto stage_b = [&](int li, int slot) {
-    const int4 r = slist[li];
-    const uint32_t dst = sB + (uint32_t)(slot * SM::kBs), bar = bbar0 + 8 * slot;
-    const float* src = dtab + (size_t)r.x * kOzTabFloats + (size_t)(r.z + 32) * 4;  // rows r.z + 32 ..
-    fence_async_smem();  // the slot's earlier use (by the tensor core, completed) comes before the copies
-    um_expect_tx(bar, (uint32_t)SM::kBs);
-#pragma unroll
-    for (int jc = 0; jc < 2 * kOzDigits; jc++)
-      um_bulk(dst + (uint32_t)(jc * kOzBChunk), src + (size_t)jc * kOzTabRows * 4, kOzBChunk, bar);
-  };
-
-  constexpr uint32_t idesc = umma_idesc(kUmmaTF32, kOzBands, kOzX);
-  // MMAs of atom li from operand slot `slot`: both rows, digit pairs (i, j) with i + j <= kOzMaxLevel
-  auto issue = [&](int slot) {
-    const uint32_t abase = sbase + (uint32_t)(slot * SM::kA), bbase = sB + (uint32_t)(slot * SM::kBs);
-    tc05_fence_after();
-#pragma unroll
-    for (int row = 0; row < kOzRows; row++)
-#pragma unroll
-      for (int i = 1; i <= kOzDigits; i++)
-#pragma unroll
-        for (int j = 1; j <= kOzDigits; j++) {
-          if (i + j > kOzMaxLevel) continue;
-          const int grp = (i + j < 5 ? i + j : 5) - 2;
-          const uint64_t ad = umma_desc(abase + (uint32_t)((row * kOzDigits + i - 1) * kOzA), kOzAChunk, 128);
-          const uint64_t bd = umma_desc(bbase + (uint32_t)((j - 1) * kOzB), kOzBChunk, 128);
-          umma_tf32(tmem + (uint32_t)((row * kOzGroups + grp) * kOzX), ad, bd, idesc, true);
-        }
-    umma_commit(cbar0 + 8 * slot);
-  };
-
-  // T2 of the current atom for this thread's band (float pairs), loaded one step ahead
-  float2 tv[P];
-  auto load_t2 = [&](int li) {
-    if (!bvalid || cube_row(li, rr) < 0) return;
-    const int4 r = slist[li];
-    const float2* src = t2 + ((size_t)r.x * C + r.w) * P * B + b;
-#pragma unroll
-    for (int p = 0; p < P; p++) tv[p] = src[(size_t)p * B];
-  };
-
-  bool ok = true;
-  int issued = 0;  // atoms whose MMAs are issued (uniform)
-  // digit windows staged (uniform); stop_stage < nlist only under fault injection: the windows from atom
-  // stop_stage on are never staged, so the waits for them run out
-  int bn = 0, loop_end = nlist;
-  load_t2(0);
-  for (int li = 0; li < nlist; li++) {
-    const int slot = li & 1;
-    // operand slot free: the MMAs of atom li - 2 are done; then stage this atom's digit window into it
-    if (li >= 2 && !um_mbar_wait(cbar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1), wait_cycles)) ok = false;
-    if (li < stop_stage) {
-      if (tid == 0) stage_b(li, slot);
-      bn = li + 1;
-    }
-    // y-pass of this (row, band) as float-float dot steps
-    const int iyr = cube_row(li, rr);
-    const bool yin = bvalid && iyr >= 0;
-    float ys[NP], yc[NP];
-#pragma unroll
-    for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
-    if (yin) {
-      const float2* yv = ylist + (li * kOzRows + rr) * NP;
-#pragma unroll
-      for (int ny = 0; ny < NP; ny++) {
-        const float2 w = yv[ny];
-#pragma unroll
-        for (int nx = 0; nx + ny <= NU; nx++)
-          ff_dot_step(ys[nx], yc[nx], ff{tv[BS::pair(nx, ny)].x, tv[BS::pair(nx, ny)].y}, ff{w.x, w.y});
-      }
-    }
-    if (li + 1 < nlist) load_t2(li + 1);  // in flight during the digits, the barrier and the next waits
-    // six digit slices of T1 G_a / F, written as the A operands of this row (two chunks of four states)
-    const int k = gexp[li] - eF;  // G_a / F = 2^k
-    const float sa = (k < -126 || !yin) ? 0.0f : oz_pow2(min(k, 127));
-    unsigned char* arow = smem_raw + (size_t)slot * SM::kA + (size_t)rr * kOzDigits * kOzA + (size_t)bl * 16;
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-      float dg[kOzDigits][4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int n = 4 * c + q;
-        if (n < NP) {
-          const ff tt = ff_norm(ys[n], yc[n]);
-          float rem = __fmul_rn(tt.hi, sa);  // |rem| < 1
-          const float lo = __fmul_rn(tt.lo, sa);
-          dg[0][q] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
-          dg[1][q] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
-          dg[2][q] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
-          rem = __fadd_rn(rem, lo);
-          dg[3][q] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
-          dg[4][q] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
-          dg[5][q] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
-        } else {
-#pragma unroll
-          for (int i = 0; i < kOzDigits; i++) dg[i][q] = 0.0f;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < kOzDigits; i++)
-        *reinterpret_cast<float4*>(arow + i * kOzA + c * kOzAChunk) = make_float4(dg[i][0], dg[i][1], dg[i][2], dg[i][3]);
-    }
-    fence_async_smem();  // the A slices become visible to the tensor core
-    // this atom's digit window has landed
-    if (!um_mbar_wait(bbar0 + 8 * slot, (uint32_t)((li >> 1) & 1), wait_cycles)) ok = false;
-    tc05_fence_before();
-    // a wait that ran out in any thread ends the loop for all
-    if (!__syncthreads_and(ok)) {
-      loop_end = li;
-      break;
-    }
-    if (tid == 0) issue(slot);
-    issued = li + 1;
+    for (int c = 0; c < 4; c++) tmem_zero32(tlane + (uint32_t)(rr * kOzGroups * kOzX + 32 * c));
   }
-  const int last = issued - 1;  // the last commit covers every MMA issued before it
-  bool done = loop_end == nlist && last >= 0 &&
-              um_mbar_wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), wait_cycles);
-  done = __syncthreads_and(done);
-  // copies issued and not yet seen complete (at most the last fill of each slot) complete whatever else
-  // happens: wait for them with the default limit before the CTA's shared memory is released
-  for (int q = max(0, bn - 2); q < bn; q++)
-    (void)um_mbar_wait(bbar0 + 8 * (q & 1), (uint32_t)((q >> 1) & 1), kDefaultWaitCycles);
-  if (!done) {
-    if (tid == 0 && status) atomicOr(status, kStatusTimeout);
-    if (last >= 0) (void)um_mbar_wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), kDefaultWaitCycles);
-  }
+  tc05_fence_before();
+  __syncthreads();  // accumulators zeroed before the first MMA
   tc05_fence_after();
-  if (done) {
+
+  // a wait that gives up when another thread's wait ran out, or after `limit` cycles (then it says so)
+  auto wait = [&](uint32_t bar, uint32_t parity) {
+    if (um_mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!um_mbar_try(bar, parity)) {
+      if (*s_abort) return false;
+      if (clock64() - t0 > wait_cycles) {
+        *s_abort = 1;
+        return false;
+      }
+    }
+    return true;
+  };
+
+  int bn = 0;  // digit windows staged (the MMA thread's count)
+  if (mma_warp) {
+    // ---- MMA thread: stage each atom's digit window once its slot is free, then issue its MMAs once the
+    // compute threads have written the A operands; stop_stage < nlist only under fault injection (the
+    // windows from atom stop_stage on are never staged, so the wait for them runs out)
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc(kUmmaTF32, kOzBands, kOzX);
+      const uint64_t ad0 = umma_desc(sbase, kOzAChunk, 128), bd0 = umma_desc(sB, kOzBChunk, 128);
+      int issued = 0;
+      for (int li = 0; li < nlist; li++) {
+        const int slot = li & 1;
+        if (li >= 2 && !wait(cbar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1))) break;
+        if (li < stop_stage) {
+          const int4 r = slist[li];
+          const uint32_t dst = sB + (uint32_t)(slot * SM::kBs), bar = bbar0 + 8 * slot;
+          const float* src = dtab + (size_t)r.x * kOzTabFloats + (size_t)(r.z + 32) * 4;  // rows r.z + 32 ..
+          fence_async_smem();  // the slot's earlier use (by the tensor core, completed) comes before the copies
+          um_expect_tx(bar, (uint32_t)SM::kBs);
+#pragma unroll
+          for (int jc = 0; jc < 2 * kOzDigits; jc++)
+            um_bulk(dst + (uint32_t)(jc * kOzBChunk), src + (size_t)jc * kOzTabRows * 4, kOzBChunk, bar);
+          bn = li + 1;
+        }
+        if (!wait(fbar0 + 8 * slot, (uint32_t)((li >> 1) & 1))) break;
+        if (!wait(bbar0 + 8 * slot, (uint32_t)((li >> 1) & 1))) break;
+        tc05_fence_after();
+        // descriptors: the slot's base plus constant offsets (16-byte units)
+        const uint64_t ad = ad0 + (uint64_t)((slot * SM::kA) >> 4), bd = bd0 + (uint64_t)((slot * SM::kBs) >> 4);
+#pragma unroll
+        for (int row = 0; row < kOzRows; row++)
+#pragma unroll
+          for (int i = 1; i <= kOzDigits; i++)
+#pragma unroll
+            for (int j = 1; j <= kOzDigits; j++) {
+              if (i + j > kOzMaxLevel) continue;
+              const int grp = (i + j < 5 ? i + j : 5) - 2;
+              umma_tf32(tmem + (uint32_t)((row * kOzGroups + grp) * kOzX),
+                        ad + (uint64_t)(((row * kOzDigits + i - 1) * kOzA) >> 4), bd + (uint64_t)(((j - 1) * kOzB) >> 4),
+                        idesc, true);
+            }
+        umma_commit(cbar0 + 8 * slot);
+        issued = li + 1;
+      }
+      *s_issued = issued;
+    }
+    __syncwarp();
+  } else {
+    // ---- compute threads: per atom the float-float y-pass of this (row, band) and its six digit slices
+    // as the A operands of the atom's slot, once the slot's MMAs of atom li - 2 are done
+    float2 tv[P];  // T2 of the current atom for this thread's band (float pairs), loaded one atom ahead
+    auto load_t2 = [&](int li) {
+      if (!bvalid || cube_row(li, rr) < 0) return;
+      const int4 r = slist[li];
+      const float2* src = t2 + ((size_t)r.x * C + r.w) * P * B + b;
+#pragma unroll
+      for (int p = 0; p < P; p++) tv[p] = src[(size_t)p * B];
+    };
+    load_t2(0);
+    for (int li = 0; li < nlist; li++) {
+      const int slot = li & 1;
+      if (li >= 2 && !wait(cbar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1))) break;
+      const int iyr = cube_row(li, rr);
+      const bool yin = bvalid && iyr >= 0;
+      float ys[NP], yc[NP];
+#pragma unroll
+      for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
+      if (yin) {
+        const float2* yv = ylist + (li * kOzRows + rr) * NP;
+#pragma unroll
+        for (int ny = 0; ny < NP; ny++) {
+          const float2 w = yv[ny];
+#pragma unroll
+          for (int nx = 0; nx + ny <= NU; nx++)
+            ff_dot_step(ys[nx], yc[nx], ff{tv[BS::pair(nx, ny)].x, tv[BS::pair(nx, ny)].y}, ff{w.x, w.y});
+        }
+      }
+      if (li + 1 < nlist) load_t2(li + 1);  // in flight during the digits and the next wait
+      // six digit slices of T1 G_a / F, written as the A operands of this row (two chunks of four states)
+      const int k = gexp[li] - eF;  // G_a / F = 2^k
+      const float sa = (k < -126 || !yin) ? 0.0f : oz_pow2(min(k, 127));
+      unsigned char* arow = smem_raw + (size_t)slot * SM::kA + (size_t)rr * kOzDigits * kOzA + (size_t)bl * 16;
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        float dg[kOzDigits][4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int n = 4 * c + q;
+          if (n < NP) {
+            const ff tt = ff_norm(ys[n], yc[n]);
+            float rem = __fmul_rn(tt.hi, sa);  // |rem| < 1
+            const float lo = __fmul_rn(tt.lo, sa);
+            dg[0][q] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
+            dg[1][q] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
+            dg[2][q] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
+            rem = __fadd_rn(rem, lo);
+            dg[3][q] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
+            dg[4][q] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
+            dg[5][q] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
+          } else {
+#pragma unroll
+            for (int i = 0; i < kOzDigits; i++) dg[i][q] = 0.0f;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kOzDigits; i++)
+          *reinterpret_cast<float4*>(arow + i * kOzA + c * kOzAChunk) = make_float4(dg[i][0], dg[i][1], dg[i][2], dg[i][3]);
+      }
+      fence_async_smem();  // the A slices become visible to the tensor core
+      um_mbar_arrive(fbar0 + 8 * slot);
+    }
+  }
+  __syncthreads();
+  const int last = *s_issued - 1;  // the last commit covers every MMA issued before it
+  bool done = !*s_abort && last == nlist - 1 && wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1));
+  done = __syncthreads_and(done);
+  if (mma_warp && lane == 0) {
+    // copies issued and not yet seen complete (at most the last fill of each slot) complete whatever else
+    // happens: wait for them with the default limit before the CTA's shared memory is released
+    for (int q = max(0, bn - 2); q < bn; q++)
+      (void)um_mbar_wait(bbar0 + 8 * (q & 1), (uint32_t)((q >> 1) & 1), kDefaultWaitCycles);
+    if (!done) {
+      if (status) atomicOr(status, kStatusTimeout);
+      if (last >= 0) (void)um_mbar_wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), kDefaultWaitCycles);
+    }
+  }
+  __syncthreads();
+  tc05_fence_after();
+  if (done && !mma_warp) {
     const bool wr = bvalid && y < Ny;
     const int xend = min(kOzX, Nx - xs);
     double* rowp = psi + (((size_t)z * Ny + (wr ? y : 0)) * Nx + xs) * (size_t)B + b;
@@ -476,6 +511,7 @@ __global__ void __launch_bounds__(kOzThreads, 2)
   if (warp == 0) tmem_dealloc(tmem, kOzCols);
   if (range_bad && status) atomicOr(status, kStatusRange);
 }
+
 
 // The kernel's MMA schedule on host digits: A [6][128][8] and B [6][32][8] (digit values), D [4][128][32]
 // the four level accumulators (test of the operand layouts and of the exactness of the level sums).
@@ -559,7 +595,7 @@ static cudaError_t ozaki_nu(const ExpandLaunch& p, const void* tyff) {
     if (e != cudaSuccess) return e;
     const int nseg = (p.g.n[0] + kOzX - 1) / kOzX, nyb = (p.g.n[1] + kOzRows - 1) / kOzRows;
     const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
-    kern<<<dim3(nblk, (p.g.nbands + kOzBands - 1) / kOzBands), kOzThreads, smem, p.stream>>>(
+    kern<<<dim3(nblk, (p.g.nbands + kOzBands - 1) / kOzBands), kOzAllThreads, smem, p.stream>>>(
         p.g, p.atoms, p.plane_ptr, p.plane_atoms, p.max_plane, static_cast<const float2*>(tyff),
         static_cast<const float2*>(p.t2),
         dtab, gpow, tmax, static_cast<double*>(p.psi), p.status, p.wait_cycles, p.stop_stage);

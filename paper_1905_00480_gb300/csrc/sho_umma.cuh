@@ -152,6 +152,14 @@ __device__ __forceinline__ void um_expect_tx(uint32_t bar, uint32_t bytes) {
 __device__ __forceinline__ void um_mbar_init(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
 }
+// A barrier whose phase completes after `count` arrivals.
+__device__ __forceinline__ void um_mbar_init_n(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+// One arrival of this thread (release: its earlier shared-memory writes come before the phase completes).
+__device__ __forceinline__ void um_mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ bool um_mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
