@@ -408,6 +408,13 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
   const int b0 = blockIdx.y * kWarp;
   const bool bok = b0 + lane < B;
   const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+  // the tile's psi (this warp's row, this lane's x point, the band tile's 256 bytes) to L2 for the final
+  // read-modify-write
+  if (yok && xs + lane < Nx) {
+    const double* pp = psi + (((size_t)z * Ny + y) * Nx + xs + lane) * (size_t)B + b0;
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pp));
+    if (B - b0 > 16) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pp + 16));
+  }
   // Offsets of atom a's cube against this tile, wrapped into [0, N) on a periodic grid: r.y = cube
   // row of the tile's first row, r.z = cube point of its first x point, r.w = cube plane of z.  True
   // when the cube meets the tile's rows and x segment.  Computed once per (tile, atom) here, so the
