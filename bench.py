@@ -38,9 +38,12 @@ def _peaks():
         return {}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the dominant kernel of the default bench
-# step (k_expand_blk_ff<5>, 96^3 / 64 atoms / 128 bands); valid only while that kernel is unchanged.
-NCU_TRAFFIC = {"k_expand": 950.974208e6 + 844.720640e6}
+# DRAM bytes (read + write) of one call, summed over its kernels' launches, from one ncu capture of the
+# default FF64 bench step (96^3 / 64 atoms / 128 bands), by (call, expansion engine); valid only while
+# those kernels are unchanged (None otherwise).
+NCU_TRAFFIC = {
+    ("k_project", e): 1983526400 + 43296000 + 44086016 for e in ("auto", "tcgen05")}  # x/y-pass + z-pass
+NCU_TRAFFIC.update({("k_expand", e): 3759104 + 44259328 + 952110336 + 841459712 for e in ("auto", "tcgen05")})
 
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
 # 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.
@@ -164,7 +167,7 @@ def max_over_ranks(ws, value):
 def launches_per_step(api, psi, w, prec, expand_kernel="auto"):
     """Kernels of this library that one project + expand step launches (mirrors the library's dispatch)."""
     if prec == "ff64":
-        oz = (expand_kernel == "tcgen05" and w.numax <= 7 and w.cube <= 32 and w.cube % 2 == 0
+        oz = (expand_kernel in ("auto", "tcgen05") and w.numax <= 7 and w.cube <= 32 and w.cube % 2 == 0
               and w.nbands % 2 == 0 and (not w.periodic or w.grid[0] >= w.cube + 32))
         # x/y-pass + z-pass kernels; the float-pair z-pass (with the tables), then the block gather, or the
         # digit tables and the tensor-core x-pass
@@ -383,7 +386,8 @@ def run_ours(args, ws, rank, local):
             bytes_dom = alg["bytes_prj"] if dom == "k_project" else alg["bytes_add"]
             achieved = bytes_dom / (t_dom * 1e-3) / 1e9
             hbm = peaks.get("hbm_gbs", 6793.4)
-            traffic = NCU_TRAFFIC.get(dom) if (prec == "ff64" and args.workload == WORKLOAD and not args.bands) else None
+            traffic = (NCU_TRAFFIC.get((dom, args.expand_kernel))
+                       if (prec == "ff64" and args.workload == WORKLOAD and not args.bands) else None)
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"}
@@ -402,7 +406,7 @@ def run_ours(args, ws, rank, local):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64": "f64", "ff64": "f64 (float-float x/y-passes)", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
+            "dtype": {"fp64": "f64", "ff64": "f64 (float-float passes; the expansion's x-pass as exact digit slices on TF32 tensor cores)", "fp32": "f32", "tf32": "tf32", "3xtf32": "3xtf32", "bf16": "bf16",
                       "split_fp16": "split-f16"}[prec],
             "data": "synthetic (seeded N(0,1) psi and coefficients, uniform atoms with min separation 2.0)",
             "config": {
@@ -1262,8 +1266,8 @@ def main():
     ap.add_argument("--table-reps", type=int, default=10)
     ap.add_argument("--table-runs", type=int, default=3)
     ap.add_argument("--expand-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
-                    help="x-pass engine of the expansion (sho_set_expand_kernel); tcgen05 also selects the "
-                         "digit-sliced tensor-core x-pass of the FF64 form")
+                    help="x-pass engine of the expansion (sho_set_expand_kernel); for the FF64 form auto and "
+                         "tcgen05 take the digit-sliced tensor-core x-pass, mma_sync the float-float block gather")
     ap.add_argument("--table-sphere", type=float, default=3.55,
                     help="projection sphere radius in Angstrom for --paper-table1 (0: whole cube)")
     args = ap.parse_args()

@@ -640,9 +640,10 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   float2* tyff = txff + (size_t)p.natoms * p.g.cube * NPX;
   cudaError_t e = launch_expand_zpass_ff(p, txff, tyff);
   if (e != cudaSuccess) return e;
-  // the x-pass on the tensor cores when chosen (kernel choice 2) and where it applies; by default the
-  // float-float block gather, which measures as fast on GB300 at a tenth of the error
-  if (p.kernel == 2 && !p.bloch && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
+  // the x-pass on the tensor cores by exact digit slicing where it applies (kernel choice automatic or
+  // tcgen05); the float-float block gather when chosen (kernel choice 1), for Bloch data, under device
+  // checks, and where the tensor-core form does not apply
+  if (p.kernel != 1 && !p.bloch && !p.chk.flag && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
   auto kern = p.chk.flag ? k_expand_blk_ff<NU, true> : k_expand_blk_ff<NU, false>;
   if constexpr (NU <= kBlochFfMaxNumax) {
     if (p.bloch) kern = k_expand_blk_ff<NU, false, true>;

@@ -23,46 +23,50 @@
 //   * the point's update is F (D_2 + D_3 + D_4 + D_5..8), summed as a float pair and added to psi in FP64.
 // The operands are TF32 (digits of at most 9 significant bits are exact in TF32), K = 8 states.
 //
-// A CTA owns a tile of one z plane: 2 grid rows x 32 x points x 128 bands, with 256 compute threads,
-// thread = (row, band), and one more warp whose first thread stages and issues.  The four level
-// accumulators per row live in tensor memory (2 x 4 x 32 = 256 columns) for the whole atom loop.  The y
-// functions of the listed atoms at the tile's two rows are gathered into shared memory once.  For each
-// atom whose cube meets the tile (ascending order), with two operand slots used by atom parity:
-//   * the compute threads, once the MMAs of atom li - 2 are done, run the float-float y-pass of their
-//     (row, band) on the band's T2 slice (float pairs, loaded from global memory one atom ahead), cut T1
-//     into six digit slices, write them into the slot as the A operands and arrive on the slot's operand
-//     barrier;
-//   * the issuing thread, once the MMAs of atom li - 2 are done, stages the atom's x digit window for the
-//     tile's 32 points (six digits x two chunks of four states) into the slot by bulk copies, waits for
-//     the A operands and the window, issues 2 rows x 26 digit-pair MMAs (M = 128 bands, N = 32 points,
-//     K = 8) and commits them to the slot's barrier.
-// No block barrier per atom: the two sides meet on the slot barriers only.  At the end each compute thread
-// reads its row's four accumulators for its band and adds the 32 points to psi.
-// Deterministic: fixed atom order, exact integer sums in the leading levels.  Every wait is bounded; the
-// first one that runs out stops every thread's loop (a shared flag), the kernel records kStatusTimeout,
-// waits (bounded) for its own copies and MMAs, frees tensor memory and returns without touching psi.
+// Persistent kernel, two CTAs per SM walking the tiles (one grid row x 32 x points x 128 bands) in a
+// fixed stride, with the work of a tile split over four warp roles that meet on mbarriers only:
+//   * a list warp writes each tile's record two tiles ahead: the plane's atoms whose cube meets the tile
+//     (ascending), their y function values at the row and G_a exponents, the frame exponent of every band,
+//     and the tile's psi prefetched to L2;
+//   * four digit warps, one thread per band: per atom the float-float y-pass on the band's T2 slice (float
+//     pairs, loaded one atom ahead), T1 cut into six digit slices written as the A operands of the atom's
+//     slot (two slots by atom parity), then an arrival on the slot's operand barrier;
+//   * one MMA thread: per atom the next atom's x digit window staged by bulk copies into a ring of three
+//     (one atom ahead), then, once the A operands and the window are in, 26 digit-pair MMAs (M = 128 bands,
+//     N = 32 points, K = 8) into the tile's four level accumulators in tensor memory, committed to the
+//     slot's barrier; after the tile's last atom a commit marks its accumulators complete;
+//   * four read-back warps, one thread per band: the tile's accumulators read from tensor memory, summed
+//     as a float pair, scaled by the frame and added to psi in FP64.
+// Two accumulator sets (2 x 4 x 32 = 256 columns) let the read-back of tile k run while the MMAs of tile
+// k + 1 accumulate.  Deterministic: fixed atom order, exact integer sums in the leading levels, each tile
+// computed by one CTA whatever the schedule.  Every wait is bounded; the first one that runs out stops
+// every role (a shared flag), the kernel records kStatusTimeout, waits (bounded) for its own copies and
+// MMAs, frees tensor memory and returns; tiles read back before that hold their update, the others none.
+#include <algorithm>
+
 #include "sho_device.cuh"
 #include "sho_ff.cuh"
 #include "sho_umma.cuh"
 
 namespace sho {
 
-constexpr int kOzRows = 2;                           // grid rows per tile
 constexpr int kOzX = 32;                             // x points per tile (the MMA N)
-constexpr int kOzBands = 128;                        // bands per tile (the MMA M)
-constexpr int kOzThreads = kOzRows * kOzBands;       // compute threads: thread = (row, band)
-constexpr int kOzComputeWarps = kOzThreads / 32;
-constexpr int kOzAllThreads = kOzThreads + 32;       // and one warp that stages and issues the MMAs
+constexpr int kOzBands = 128;                        // bands per tile (the MMA M), one thread each
+constexpr int kOzWarps = 10;                         // 4 digit warps, 4 read-back warps, a list warp, an MMA warp
+constexpr int kOzAllThreads = kOzWarps * 32;
+constexpr int kOzListWarp = 8, kOzMmaWarp = 9;
 constexpr int kOzDigits = 6;                         // digits per operand value
 constexpr int kOzMaxLevel = 8;                       // digit pairs (i, j) with i + j <= 8 are multiplied
 constexpr int kOzGroups = 4;                         // accumulators: levels 2, 3, 4 and 5..8
-constexpr int kOzCols = kOzRows * kOzGroups * kOzX;  // tensor-memory columns: 256
+constexpr int kOzBufCols = kOzGroups * kOzX;         // tensor-memory columns of one tile's accumulators: 128
+constexpr int kOzCols = 2 * kOzBufCols;              // two tiles in flight: 256
 constexpr int kOzTabRows = 96;                       // rows of a digit table: cube point ix = row - 32
 constexpr uint32_t kOzA = kOzBands * 8 * 4;          // one A digit slice [128 bands][8 states] TF32: 4 KB
 constexpr uint32_t kOzAChunk = kOzBands * 16;        // its states 4..7 (the second core matrix along K)
 constexpr uint32_t kOzB = kOzX * 8 * 4;              // one B digit slice [32 points][8 states]: 1 KB
 constexpr uint32_t kOzBChunk = kOzX * 16;            // its states 4..7
 constexpr int kOzTabFloats = kOzDigits * 2 * kOzTabRows * 4;  // digit table of one atom
+constexpr int kOzBBuf = 3;                           // digit-window buffers (staged one atom ahead)
 
 // Atoms per tile that keep the levels 2..4 exact: the level-4 products (first digits up to 256, the others
 // up to 128) are at most 2 * 2^15 + 2^14 per state and atom, so (numax + 1) states x atoms x 2.5 * 2^15 <= 2^24.
@@ -71,17 +75,19 @@ __host__ __device__ constexpr int oz_max_atoms(int numax) { return 2048 / (10 * 
 template <int NU>
 struct OzSmem {
   static constexpr int NP = NU + 1, P = Basis<NU>::P;
-  static constexpr size_t kA = (size_t)kOzRows * kOzDigits * kOzA;  // A slices of both rows, one slot: 48 KB
-  static constexpr size_t kBs = (size_t)kOzDigits * kOzB;           // one digit window: 6 KB
-  // two operand slots (A, then B), the y values of the tile's atoms [atom][row][NP] float pairs, the
-  // exponents of their G_a [atom], barriers
-  __host__ __device__ static size_t off_b() { return 2 * kA; }
-  __host__ __device__ static size_t off_y() { return 2 * kA + 2 * kBs; }
-  __host__ __device__ static size_t off_e(int max_plane) { return off_y() + (size_t)max_plane * kOzRows * NP * 8; }
-  __host__ __device__ static size_t off_bar(int max_plane) {
-    return (off_e(max_plane) + (size_t)max_plane * 4 + 127) & ~(size_t)127;
+  static constexpr size_t kA = (size_t)kOzDigits * kOzA;  // A slices of one operand slot: 24 KB
+  static constexpr size_t kBs = (size_t)kOzDigits * kOzB;  // one digit window: 6 KB
+  // Per-tile list record (two, by tile parity): header (atom count, or -1 after the last tile; z, y, x0 of
+  // the tile; first band), the frame exponent of each band [128], the listed atoms (atom, cube row, cube x
+  // offset, cube plane) [max_plane], their y function values [max_plane][NP] float pairs and the exponents
+  // of their G_a [max_plane].
+  __host__ __device__ static size_t rec_bytes(int mp) {
+    return ((size_t)32 + 4 * kOzBands + 16 * (size_t)mp + 8 * (size_t)NP * mp + 4 * (size_t)mp + 15) & ~(size_t)15;
   }
-  static size_t bytes(int max_plane) { return off_bar(max_plane) + 128 + (size_t)(max_plane + 1) * sizeof(int4); }
+  __host__ __device__ static size_t off_b() { return 2 * kA; }
+  __host__ __device__ static size_t off_rec(int mp, int u) { return 2 * kA + kOzBBuf * kBs + (size_t)u * rec_bytes(mp); }
+  __host__ __device__ static size_t off_bar(int mp) { return (off_rec(mp, 2) + 127) & ~(size_t)127; }
+  static size_t bytes(int mp) { return off_bar(mp) + 256; }  // barriers, tensor-memory slot, abort flag
 };
 
 // float 2^e for e in [-126, 127]
@@ -192,153 +198,54 @@ __global__ void __launch_bounds__(kOzAllThreads, 2)
   static_assert(NP <= 8, "a digit slice holds at most 8 states");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int C = g.cube, Nx = g.n[0], Ny = g.n[1], Nz = g.n[2], B = g.nbands;
+  const int mp = max_plane;
   const uint32_t sbase = um_smem(smem_raw);
   const uint32_t sB = sbase + (uint32_t)SM::off_b();
-  float2* ylist = reinterpret_cast<float2*>(smem_raw + SM::off_y());  // [atom][row][NP]
-  int* gexp = reinterpret_cast<int*>(smem_raw + SM::off_e(max_plane));  // [atom] exponent of G_a
-  unsigned char* barp = smem_raw + SM::off_bar(max_plane);
-  const uint32_t cbar0 = um_smem(barp);  // MMA commits of operand slots 0 and 1
-  const uint32_t bbar0 = cbar0 + 16;     // digit-window staging of slots 0 and 1
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 32);
-  int* s_misc = reinterpret_cast<int*>(barp + 48);  // [0] list length, [1..8] warp counts (bytes 48..83)
-  // bytes 88..103: the A-operand barriers of the two slots; 104: abort flag; 108: atoms issued
-  int4* slist = reinterpret_cast<int4*>(barp + 128);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool mma_warp = warp == kOzComputeWarps;  // the warp that stages digit windows and issues the MMAs
-  const int rr = (tid >> 7) & 1, bl = tid & 127;  // a compute thread's tile row and band
-  const uint32_t fbar0 = cbar0 + 88;  // A operands of slots 0 and 1 written (every compute thread arrives)
-  volatile int* s_abort = reinterpret_cast<volatile int*>(barp + 104);  // a bounded wait ran out
-  int* s_issued = reinterpret_cast<int*>(barp + 108);                   // atoms whose MMAs were issued
-
-  const int nseg = (Nx + kOzX - 1) / kOzX, nyb = (Ny + kOzRows - 1) / kOzRows;
-  int bid = blockIdx.x;
-  const int seg = bid % nseg;
-  bid /= nseg;
-  const int yb = bid % nyb;
-  const int z = bid / nyb;
-  const int xs = seg * kOzX;
-  const int b0 = blockIdx.y * kOzBands;
-  const int nb = min(kOzBands, B - b0);  // bands of this tile (an even count)
-  const int b = b0 + bl;
-  const bool bvalid = !mma_warp && bl < nb;
-  const int y = yb * kOzRows + rr;
-  const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
-
-  // atoms of the plane whose cube meets the tile, ascending: (atom, cube row of the tile's first row,
-  // cube-relative x offset, cube plane); the compute threads scan, every thread takes the barriers
-  if (tid == 0) {
-    s_misc[0] = 0;
-    *s_abort = 0;
-    *s_issued = 0;
-  }
-  __syncthreads();
-  for (int base = q0; base < q1; base += kOzThreads) {
-    const int q = base + tid;
-    int4 r = make_int4(-1, 0, 0, 0);
-    bool m = false;
-    if (!mma_warp && q < q1) {
-      const int a = plane_atoms[q];
-      const AtomDev at = atoms[a];
-      int dy = yb * kOzRows - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
-      if (g.periodic) {
-        dy %= Ny;
-        if (dy < 0) dy += Ny;
-        dx %= Nx;
-        if (dx < 0) dx += Nx;
-        dz %= Nz;
-        if (dz < 0) dz += Nz;
-        m = (dy < C || dy + kOzRows > Ny) && (dx < C || dx + kOzX > Nx);
-        if (dx >= C) dx -= Nx;  // the cube starts inside the tile (one run: Nx >= C + 32)
-      } else {
-        m = dy < C && dy + kOzRows > 0 && dx < C && dx + kOzX > 0;
-      }
-      r = make_int4(a, dy, dx, dz);
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, m);
-    if (lane == 0 && !mma_warp) s_misc[1 + warp] = __popc(bal);
-    __syncthreads();
-    int off = s_misc[0];
-    for (int w = 0; w < warp && w < kOzComputeWarps; w++) off += s_misc[1 + w];
-    if (m) slist[off + __popc(bal & ((1u << lane) - 1u))] = r;
-    __syncthreads();
-    if (tid == 0)
-      for (int w = 0; w < kOzComputeWarps; w++) s_misc[0] += s_misc[1 + w];
-    __syncthreads();
-  }
-  const int nlist = s_misc[0];
-  if (nlist == 0) return;  // no cube meets the tile: psi is unchanged
-
-  // cube row of tile row `row` for list entry li, or -1 outside the cube or the grid
-  auto cube_row = [&](int li, int row) {
-    int iy = slist[li].y + row;
-    if (g.periodic && iy >= Ny) iy -= Ny;
-    return (yb * kOzRows + row < Ny && iy >= 0 && iy < C) ? iy : -1;
+  unsigned char* barp = smem_raw + SM::off_bar(mp);
+  const uint32_t bar0 = um_smem(barp);
+  auto mf = [&](int u) { return bar0 + 8 * u; };        // list record u written (32 arrivals)
+  auto me = [&](int u) { return bar0 + 16 + 8 * u; };   // list record u read by the read-back threads (128)
+  auto af = [&](int u) { return bar0 + 32 + 8 * u; };   // accumulators u complete (MMA commit)
+  auto ae = [&](int u) { return bar0 + 48 + 8 * u; };   // accumulators u read back (128 arrivals)
+  auto fb = [&](int s) { return bar0 + 64 + 8 * s; };   // A operands of slot s written (128 arrivals)
+  auto cb = [&](int s) { return bar0 + 80 + 8 * s; };   // MMAs from slot s done (MMA commit)
+  auto bb = [&](int q) { return bar0 + 96 + 8 * q; };   // digit window q staged (bulk copies)
+  const uint32_t dr = bar0 + 120;                       // drain: every MMA of this CTA done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 128);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(barp + 132);
+  auto rec = [&](int u) { return smem_raw + SM::off_rec(mp, u); };
+  auto rec_hdr = [&](int u) { return reinterpret_cast<int*>(rec(u)); };
+  auto rec_ef = [&](int u) { return reinterpret_cast<int*>(rec(u) + 32); };
+  auto rec_list = [&](int u) { return reinterpret_cast<int4*>(rec(u) + 32 + 4 * kOzBands); };
+  auto rec_y = [&](int u) { return reinterpret_cast<float2*>(rec(u) + 32 + 4 * kOzBands + 16 * (size_t)mp); };
+  auto rec_gexp = [&](int u) {
+    return reinterpret_cast<int*>(rec(u) + 32 + 4 * kOzBands + 16 * (size_t)mp + 8 * (size_t)NP * mp);
   };
-  // the y functions of every listed atom at the tile's two rows (float pairs), and the tile's psi to L2
-  for (int i = tid; i < nlist * kOzRows * NP; i += kOzAllThreads) {
-    const int li = i / (kOzRows * NP), row = (i / NP) % kOzRows, n = i % NP;
-    const int iy = cube_row(li, row);
-    ylist[i] = iy >= 0 ? tyff[((size_t)slist[li].x * NP + n) * C + iy] : make_float2(0.0f, 0.0f);
-  }
-  for (int li = tid; li < nlist; li += kOzAllThreads)
-    gexp[li] = (int)((__float_as_uint(gpow[slist[li].x]) >> 23) & 0xffu) - 127;
-  if (tid < kOzRows * kOzX) {
-    const int row = tid >> 5, x = tid & 31, yy = yb * kOzRows + row;
-    if (yy < Ny && xs + x < Nx) {
-      const double* pp = psi + (((size_t)z * Ny + yy) * Nx + xs + x) * (size_t)B + b0;
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(pp), "r"((uint32_t)(nb * 8)) : "memory");
-    }
-  }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nseg = (Nx + kOzX - 1) / kOzX, nbt = (B + kOzBands - 1) / kOzBands;
+  const int ntiles = nseg * Ny * Nz;  // one grid row x 32 x points each, for every band tile
 
-  // the frame F of this (row, band): a power of two above every covering atom's bound |T1_a| G_a; the
-  // bounds of up to 8 atoms are loaded together
-  float xb = 0.0f;
-  if (bvalid && y < Ny) {
-    for (int l0 = 0; l0 < nlist; l0 += 8) {
-      float tv8[8], gv8[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int li = l0 + u;
-        const bool in = li < nlist && cube_row(li, rr) >= 0;
-        const int4 r = slist[min(li, nlist - 1)];
-        tv8[u] = in ? tmax[((size_t)r.x * C + r.w) * B + b] : 0.0f;
-        gv8[u] = in ? gpow[r.x] : 0.0f;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; u++) xb = fmaxf(xb, tv8[u] * gv8[u]);
-    }
-  }
-  int eF = 0;
-  if (xb > 0.0f) eF = (int)((__float_as_uint(xb * (1.0f + 0x1p-20f)) >> 23) & 0xffu) - 127 + 1;  // xb < 2^eF
-  const bool range_bad = eF > 127;  // the bound overflowed the float range
-  eF = max(-124, min(eF, 127));
-  const float F = oz_pow2(eF);
-
-  // tensor memory (zeroed), barriers
-  if (warp == 0) tmem_alloc(um_smem(tmem_slot), kOzCols);
   if (tid == 0) {
-    um_mbar_init(cbar0);
-    um_mbar_init(cbar0 + 8);
-    um_mbar_init(bbar0);
-    um_mbar_init(bbar0 + 8);
-    um_mbar_init_n(fbar0, kOzThreads);
-    um_mbar_init_n(fbar0 + 8, kOzThreads);
+    *s_abort = 0;
+    for (int u = 0; u < 2; u++) {
+      um_mbar_init_n(mf(u), 32);
+      um_mbar_init_n(me(u), kOzBands);
+      um_mbar_init(af(u));
+      um_mbar_init_n(ae(u), kOzBands);
+      um_mbar_init_n(fb(u), kOzBands);
+      um_mbar_init(cb(u));
+    }
+    for (int q = 0; q < kOzBBuf; q++) um_mbar_init(bb(q));
+    um_mbar_init(dr);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  if (warp == 0) tmem_alloc(um_smem(tmem_slot), kOzCols);
   tc05_fence_before();
   __syncthreads();
   tc05_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // lanes of this warp's bands
-  if (!mma_warp) {
-#pragma unroll
-    for (int c = 0; c < 4; c++) tmem_zero32(tlane + (uint32_t)(rr * kOzGroups * kOzX + 32 * c));
-  }
-  tc05_fence_before();
-  __syncthreads();  // accumulators zeroed before the first MMA
-  tc05_fence_after();
 
-  // a wait that gives up when another thread's wait ran out, or after `limit` cycles (then it says so)
+  // a wait that gives up when another thread's wait ran out, or after `wait_cycles` (then it says so)
   auto wait = [&](uint32_t bar, uint32_t parity) {
     if (um_mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
@@ -352,166 +259,320 @@ __global__ void __launch_bounds__(kOzAllThreads, 2)
     return true;
   };
 
-  int bn = 0;  // digit windows staged (the MMA thread's count)
-  if (mma_warp) {
-    // ---- MMA thread: stage each atom's digit window once its slot is free, then issue its MMAs once the
-    // compute threads have written the A operands; stop_stage < nlist only under fault injection (the
-    // windows from atom stop_stage on are never staged, so the wait for them runs out)
+  if (warp == kOzListWarp) {
+    // ---- list warp: the record of each of this CTA's tiles that a cube meets, two tiles ahead of the
+    // read-back: its atoms (ascending), their y values at the tile's row and G_a exponents, the frame
+    // exponent of every band, and the tile's psi to L2
+    int cursor = blockIdx.x;
+    for (int k = 0;; k++) {
+      const int u = k & 1;
+      // record u is free once the read-back of tile k - 2 has taken what it needs
+      const bool ok = k < 2 || wait(me(u), (uint32_t)(((k - 2) >> 1) & 1));
+      if (!__all_sync(0xffffffffu, ok)) break;
+      int4* sl = rec_list(u);
+      int nl = 0, z = 0, y = 0, xs = 0, bt = 0;
+      while (cursor < ntiles * nbt) {
+        const int t = cursor % ntiles;
+        bt = cursor / ntiles;
+        cursor += gridDim.x;
+        const int seg = t % nseg, yz = t / nseg;
+        y = yz % Ny;
+        z = yz / Ny;
+        xs = seg * kOzX;
+        const int q0 = plane_ptr[z], q1 = plane_ptr[z + 1];
+        nl = 0;
+        for (int base = q0; base < q1; base += 32) {
+          const int q = base + lane;
+          int4 r = make_int4(-1, 0, 0, 0);
+          bool m = false;
+          if (q < q1) {
+            const int a = plane_atoms[q];
+            const AtomDev at = atoms[a];
+            int dy = y - at.o[1], dx = xs - at.o[0], dz = z - at.o[2];
+            if (g.periodic) {
+              dy %= Ny;
+              if (dy < 0) dy += Ny;
+              dx %= Nx;
+              if (dx < 0) dx += Nx;
+              dz %= Nz;
+              if (dz < 0) dz += Nz;
+              m = dy < C && (dx < C || dx + kOzX > Nx);
+              if (dx >= C) dx -= Nx;  // the cube starts inside the tile (one run: Nx >= C + 32)
+            } else {
+              m = dy >= 0 && dy < C && dx < C && dx + kOzX > 0;
+            }
+            r = make_int4(a, dy, dx, dz);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, m);
+          if (m) sl[nl + __popc(bal & ((1u << lane) - 1u))] = r;
+          nl += __popc(bal);
+        }
+        if (nl > 0) break;
+      }
+      int* hdr = rec_hdr(u);
+      if (nl == 0) {  // no tile left: the end marker
+        if (lane == 0) hdr[0] = -1;
+        __syncwarp();
+        um_mbar_arrive(mf(u));
+        break;
+      }
+      const int b0 = bt * kOzBands, nb = min(kOzBands, B - b0);
+      __syncwarp();  // the list entries written above are read by every lane below
+      float2* yl = rec_y(u);
+      for (int i = lane; i < nl * NP; i += 32) {
+        const int li = i / NP, n = i - li * NP;
+        const int4 r = sl[li];
+        yl[i] = tyff[((size_t)r.x * NP + n) * C + r.y];
+      }
+      int* ge = rec_gexp(u);
+      for (int li = lane; li < nl; li += 32) ge[li] = (int)((__float_as_uint(gpow[sl[li].x]) >> 23) & 0xffu) - 127;
+      {
+        const double* pp = psi + (((size_t)z * Ny + y) * Nx + xs + lane) * (size_t)B + b0;
+        if (xs + lane < Nx) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(pp), "r"((uint32_t)(nb * 8)) : "memory");
+      }
+      // the frame of each band: a power of two above every listed atom's bound |T1_a| G_a
+      float xb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 2
+      for (int li = 0; li < nl; li++) {
+        const int4 r = sl[li];
+        const float ga = gpow[r.x];
+        const float* tm = tmax + ((size_t)r.x * C + r.w) * B + b0;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const int bi = lane + 32 * c;
+          if (bi < nb) xb[c] = fmaxf(xb[c], tm[bi] * ga);
+        }
+      }
+      int* ef = rec_ef(u);
+      bool range_bad = false;
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        int eF = 0;
+        if (xb[c] > 0.0f) eF = (int)((__float_as_uint(xb[c] * (1.0f + 0x1p-20f)) >> 23) & 0xffu) - 127 + 1;  // xb < 2^eF
+        range_bad |= eF > 127;  // the bound overflowed the float range
+        ef[lane + 32 * c] = max(-124, min(eF, 127));
+      }
+      if (range_bad && status) atomicOr(status, kStatusRange);
+      if (lane == 0) {
+        hdr[0] = nl;
+        hdr[1] = z;
+        hdr[2] = y;
+        hdr[3] = xs;
+        hdr[4] = b0;
+        hdr[5] = nb;
+      }
+      __syncwarp();
+      um_mbar_arrive(mf(u));
+    }
+  } else if (warp == kOzMmaWarp) {
+    // ---- MMA thread: per tile, once its accumulators are free (read back two tiles ago), per atom: the
+    // next atom's digit window staged into the ring (one atom ahead; stop_stage < the tile's atom count
+    // only under fault injection: windows from that atom on are never staged, so the wait runs out), the
+    // A operands and this atom's window awaited, 26 digit-pair MMAs issued and committed to the slot
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc(kUmmaTF32, kOzBands, kOzX);
       const uint64_t ad0 = umma_desc(sbase, kOzAChunk, 128), bd0 = umma_desc(sB, kOzBChunk, 128);
-      int issued = 0;
-      for (int li = 0; li < nlist; li++) {
-        const int slot = li & 1;
-        if (li >= 2 && !wait(cbar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1))) break;
-        if (li < stop_stage) {
-          const int4 r = slist[li];
-          const uint32_t dst = sB + (uint32_t)(slot * SM::kBs), bar = bbar0 + 8 * slot;
-          const float* src = dtab + (size_t)r.x * kOzTabFloats + (size_t)(r.z + 32) * 4;  // rows r.z + 32 ..
-          fence_async_smem();  // the slot's earlier use (by the tensor core, completed) comes before the copies
-          um_expect_tx(bar, (uint32_t)SM::kBs);
+      int gi = 0;          // atoms of this CTA so far: slot gi & 1, window buffer gi % 3
+      int staged = 0;      // windows staged (by CTA atom index)
+      int consumed = 0;    // windows waited for
+      bool any = false;    // an MMA was issued
+      auto stage = [&](const int4 r, int ga) {
+        const int q = ga % kOzBBuf;
+        const uint32_t dst = sB + (uint32_t)(q * SM::kBs);
+        const float* src = dtab + (size_t)r.x * kOzTabFloats + (size_t)(r.z + 32) * 4;  // rows r.z + 32 ..
+        fence_async_smem();  // the buffer's earlier use (by the tensor core, completed) comes before the copies
+        um_expect_tx(bb(q), (uint32_t)SM::kBs);
 #pragma unroll
-          for (int jc = 0; jc < 2 * kOzDigits; jc++)
-            um_bulk(dst + (uint32_t)(jc * kOzBChunk), src + (size_t)jc * kOzTabRows * 4, kOzBChunk, bar);
-          bn = li + 1;
-        }
-        if (!wait(fbar0 + 8 * slot, (uint32_t)((li >> 1) & 1))) break;
-        if (!wait(bbar0 + 8 * slot, (uint32_t)((li >> 1) & 1))) break;
+        for (int jc = 0; jc < 2 * kOzDigits; jc++)
+          um_bulk(dst + (uint32_t)(jc * kOzBChunk), src + (size_t)jc * kOzTabRows * 4, kOzBChunk, bb(q));
+        staged = ga + 1;
+      };
+      for (int k = 0;; k++) {
+        const int u = k & 1;
+        if (!wait(mf(u), (uint32_t)((k >> 1) & 1))) break;
+        const int nl = rec_hdr(u)[0];
+        if (nl < 0) break;
+        if (k >= 2 && !wait(ae(u), (uint32_t)(((k - 2) >> 1) & 1))) break;
         tc05_fence_after();
-        // descriptors: the slot's base plus constant offsets (16-byte units)
-        const uint64_t ad = ad0 + (uint64_t)((slot * SM::kA) >> 4), bd = bd0 + (uint64_t)((slot * SM::kBs) >> 4);
-#pragma unroll
-        for (int row = 0; row < kOzRows; row++)
+        const int4* sl = rec_list(u);
+        const uint32_t dacc = tmem + (uint32_t)(u * kOzBufCols);
+        if (stop_stage > 0) stage(sl[0], gi);
+        bool ok = true;
+        for (int li = 0; li < nl && ok; li++) {
+          const int ga = gi + li, slot = ga & 1, q = ga % kOzBBuf;
+          // slot ga & 1 and window buffer (ga + 1) % 3 free: the MMAs of atom ga - 2 are done
+          if (ga >= 2 && !wait(cb(slot), (uint32_t)(((ga - 2) >> 1) & 1))) { ok = false; break; }
+          if (li + 1 < nl && li + 1 < stop_stage) stage(sl[li + 1], ga + 1);
+          if (!wait(fb(slot), (uint32_t)((ga >> 1) & 1))) { ok = false; break; }
+          if (!wait(bb(q), (uint32_t)((ga / kOzBBuf) & 1))) { ok = false; break; }
+          consumed = ga + 1;
+          tc05_fence_after();
+          const uint64_t ad = ad0 + (uint64_t)((slot * SM::kA) >> 4), bd = bd0 + (uint64_t)((q * SM::kBs) >> 4);
 #pragma unroll
           for (int i = 1; i <= kOzDigits; i++)
 #pragma unroll
             for (int j = 1; j <= kOzDigits; j++) {
               if (i + j > kOzMaxLevel) continue;
               const int grp = (i + j < 5 ? i + j : 5) - 2;
-              umma_tf32(tmem + (uint32_t)((row * kOzGroups + grp) * kOzX),
-                        ad + (uint64_t)(((row * kOzDigits + i - 1) * kOzA) >> 4), bd + (uint64_t)(((j - 1) * kOzB) >> 4),
-                        idesc, true);
+              // the first product of each level group in the tile starts its accumulator
+              const bool acc = li > 0 || !(i == 1 && j <= 4);
+              umma_tf32(dacc + (uint32_t)(grp * kOzX), ad + (uint64_t)(((i - 1) * kOzA) >> 4),
+                        bd + (uint64_t)(((j - 1) * kOzB) >> 4), idesc, acc);
             }
-        umma_commit(cbar0 + 8 * slot);
-        issued = li + 1;
+          umma_commit(cb(slot));
+          any = true;
+        }
+        if (!ok) break;
+        umma_commit(af(u));  // the tile's accumulators are complete once its MMAs are
+        gi += nl;
       }
-      *s_issued = issued;
+      // windows staged and not waited for (at most two) complete whatever else happens; every MMA issued
+      // completes before the tensor memory is released
+      for (int q = consumed; q < staged; q++)
+        (void)um_mbar_wait(bb(q % kOzBBuf), (uint32_t)((q / kOzBBuf) & 1), kDefaultWaitCycles);
+      if (any) {
+        umma_commit(dr);
+        (void)um_mbar_wait(dr, 0, kDefaultWaitCycles);
+      }
     }
     __syncwarp();
-  } else {
-    // ---- compute threads: per atom the float-float y-pass of this (row, band) and its six digit slices
-    // as the A operands of the atom's slot, once the slot's MMAs of atom li - 2 are done
+  } else if (warp < 4) {
+    // ---- digit threads, one per band: per atom the float-float y-pass of the tile row and its six digit
+    // slices as the A operands of the atom's slot, once the slot's MMAs of atom gi - 2 are done
+    const int bl = tid;
+    int gi = 0;
     float2 tv[P];  // T2 of the current atom for this thread's band (float pairs), loaded one atom ahead
-    auto load_t2 = [&](int li) {
-      if (!bvalid || cube_row(li, rr) < 0) return;
-      const int4 r = slist[li];
-      const float2* src = t2 + ((size_t)r.x * C + r.w) * P * B + b;
+    for (int k = 0;; k++) {
+      const int u = k & 1;
+      if (!wait(mf(u), (uint32_t)((k >> 1) & 1))) break;
+      const int* hdr = rec_hdr(u);
+      const int nl = hdr[0];
+      if (nl < 0) break;
+      const int b0 = hdr[4], nb = hdr[5];
+      const bool bvalid = bl < nb;
+      const int b = b0 + bl;
+      const int eF = rec_ef(u)[bl];
+      const int4* sl = rec_list(u);
+      const float2* yl = rec_y(u);
+      const int* ge = rec_gexp(u);
+      auto load_t2 = [&](int li) {
+        if (!bvalid) return;
+        const int4 r = sl[li];
+        const float2* src = t2 + ((size_t)r.x * C + r.w) * P * B + b;
 #pragma unroll
-      for (int p = 0; p < P; p++) tv[p] = src[(size_t)p * B];
-    };
-    load_t2(0);
-    for (int li = 0; li < nlist; li++) {
-      const int slot = li & 1;
-      if (li >= 2 && !wait(cbar0 + 8 * slot, (uint32_t)(((li - 2) >> 1) & 1))) break;
-      const int iyr = cube_row(li, rr);
-      const bool yin = bvalid && iyr >= 0;
-      float ys[NP], yc[NP];
+        for (int p = 0; p < P; p++) tv[p] = src[(size_t)p * B];
+      };
+      load_t2(0);
+      bool ok = true;
+      for (int li = 0; li < nl; li++) {
+        const int ga = gi + li, slot = ga & 1;
+        if (ga >= 2 && !wait(cb(slot), (uint32_t)(((ga - 2) >> 1) & 1))) { ok = false; break; }
+        float ys[NP], yc[NP];
 #pragma unroll
-      for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
-      if (yin) {
-        const float2* yv = ylist + (li * kOzRows + rr) * NP;
+        for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
+        if (bvalid) {
+          const float2* yv = yl + li * NP;
 #pragma unroll
-        for (int ny = 0; ny < NP; ny++) {
-          const float2 w = yv[ny];
+          for (int ny = 0; ny < NP; ny++) {
+            const float2 w = yv[ny];
 #pragma unroll
-          for (int nx = 0; nx + ny <= NU; nx++)
-            ff_dot_step(ys[nx], yc[nx], ff{tv[BS::pair(nx, ny)].x, tv[BS::pair(nx, ny)].y}, ff{w.x, w.y});
-        }
-      }
-      if (li + 1 < nlist) load_t2(li + 1);  // in flight during the digits and the next wait
-      // six digit slices of T1 G_a / F, written as the A operands of this row (two chunks of four states)
-      const int k = gexp[li] - eF;  // G_a / F = 2^k
-      const float sa = (k < -126 || !yin) ? 0.0f : oz_pow2(min(k, 127));
-      unsigned char* arow = smem_raw + (size_t)slot * SM::kA + (size_t)rr * kOzDigits * kOzA + (size_t)bl * 16;
-#pragma unroll
-      for (int c = 0; c < 2; c++) {
-        float dg[kOzDigits][4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int n = 4 * c + q;
-          if (n < NP) {
-            const ff tt = ff_norm(ys[n], yc[n]);
-            float rem = __fmul_rn(tt.hi, sa);  // |rem| < 1
-            const float lo = __fmul_rn(tt.lo, sa);
-            dg[0][q] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
-            dg[1][q] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
-            dg[2][q] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
-            rem = __fadd_rn(rem, lo);
-            dg[3][q] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
-            dg[4][q] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
-            dg[5][q] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
-          } else {
-#pragma unroll
-            for (int i = 0; i < kOzDigits; i++) dg[i][q] = 0.0f;
+            for (int nx = 0; nx + ny <= NU; nx++)
+              ff_dot_step(ys[nx], yc[nx], ff{tv[BS::pair(nx, ny)].x, tv[BS::pair(nx, ny)].y}, ff{w.x, w.y});
           }
         }
+        if (li + 1 < nl) load_t2(li + 1);  // in flight during the digits and the next wait
+        // six digit slices of T1 G_a / F, written as the A operands (two chunks of four states)
+        const int kk = ge[li] - eF;  // G_a / F = 2^kk
+        const float sa = (kk < -126 || !bvalid) ? 0.0f : oz_pow2(min(kk, 127));
+        unsigned char* arow = smem_raw + (size_t)slot * SM::kA + (size_t)bl * 16;
 #pragma unroll
-        for (int i = 0; i < kOzDigits; i++)
-          *reinterpret_cast<float4*>(arow + i * kOzA + c * kOzAChunk) = make_float4(dg[i][0], dg[i][1], dg[i][2], dg[i][3]);
+        for (int c = 0; c < 2; c++) {
+          float dg[kOzDigits][4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int n = 4 * c + q;
+            if (n < NP) {
+              const ff tt = ff_norm(ys[n], yc[n]);
+              float rem = __fmul_rn(tt.hi, sa);  // |rem| < 1
+              const float lo = __fmul_rn(tt.lo, sa);
+              dg[0][q] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
+              dg[1][q] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
+              dg[2][q] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
+              rem = __fadd_rn(rem, lo);
+              dg[3][q] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
+              dg[4][q] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
+              dg[5][q] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
+            } else {
+#pragma unroll
+              for (int i = 0; i < kOzDigits; i++) dg[i][q] = 0.0f;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kOzDigits; i++)
+            *reinterpret_cast<float4*>(arow + i * kOzA + c * kOzAChunk) = make_float4(dg[i][0], dg[i][1], dg[i][2], dg[i][3]);
+        }
+        fence_async_smem();  // the A slices become visible to the tensor core
+        um_mbar_arrive(fb(slot));
       }
-      fence_async_smem();  // the A slices become visible to the tensor core
-      um_mbar_arrive(fbar0 + 8 * slot);
+      if (!ok) break;
+      gi += nl;
     }
-  }
-  __syncthreads();
-  const int last = *s_issued - 1;  // the last commit covers every MMA issued before it
-  bool done = !*s_abort && last == nlist - 1 && wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1));
-  done = __syncthreads_and(done);
-  if (mma_warp && lane == 0) {
-    // copies issued and not yet seen complete (at most the last fill of each slot) complete whatever else
-    // happens: wait for them with the default limit before the CTA's shared memory is released
-    for (int q = max(0, bn - 2); q < bn; q++)
-      (void)um_mbar_wait(bbar0 + 8 * (q & 1), (uint32_t)((q >> 1) & 1), kDefaultWaitCycles);
-    if (!done) {
-      if (status) atomicOr(status, kStatusTimeout);
-      if (last >= 0) (void)um_mbar_wait(cbar0 + 8 * (last & 1), (uint32_t)((last >> 1) & 1), kDefaultWaitCycles);
-    }
-  }
-  __syncthreads();
-  tc05_fence_after();
-  if (done && !mma_warp) {
-    const bool wr = bvalid && y < Ny;
-    const int xend = min(kOzX, Nx - xs);
-    double* rowp = psi + (((size_t)z * Ny + (wr ? y : 0)) * Nx + xs) * (size_t)B + b;
-    const uint32_t tcol = tlane + (uint32_t)(rr * kOzGroups * kOzX);
+  } else {
+    // ---- read-back threads, one per band (tensor-memory lanes 32 (warp - 4) ..): per tile, the four
+    // level accumulators of the 32 points summed as a float pair, scaled by the frame and added to psi in
+    // FP64; then the accumulators are free for tile k + 2
+    const int bl = tid - 128;
+    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int k = 0;; k++) {
+      const int u = k & 1;
+      if (!wait(mf(u), (uint32_t)((k >> 1) & 1))) break;
+      const int* hdr = rec_hdr(u);
+      const int nl = hdr[0];
+      if (nl < 0) break;
+      const int z = hdr[1], y = hdr[2], xs = hdr[3], b0 = hdr[4], nb = hdr[5];
+      const float F = oz_pow2(rec_ef(u)[bl]);
+      const bool wr = bl < nb;
+      const int xend = min(kOzX, Nx - xs);
+      double* rowp = psi + (((size_t)z * Ny + y) * Nx + xs) * (size_t)B + b0 + bl;
+      double pv[8];  // the current batch of 8 points, the next batch's loads issued before its adds
+#pragma unroll
+      for (int x = 0; x < 8; x++) pv[x] = (wr && x < xend) ? rowp[(size_t)x * B] : 0.0;
+      if (!wait(af(u), (uint32_t)((k >> 1) & 1))) break;
+      um_mbar_arrive(me(u));  // the record is no longer needed: the list warp may refill it
+      tc05_fence_after();
+      const uint32_t tcol = tlane + (uint32_t)(u * kOzBufCols);
 #pragma unroll 1
-    for (int x0 = 0; x0 < kOzX; x0 += 8) {
-      float d[32];  // d[8 g + k]: level accumulator g of point x0 + k
-      tmem_ld8x4(tcol + (uint32_t)x0, tcol + (uint32_t)(kOzX + x0), tcol + (uint32_t)(2 * kOzX + x0),
-                 tcol + (uint32_t)(3 * kOzX + x0), d);
-      if (wr) {
-        double pv[8];
+      for (int x0 = 0; x0 < kOzX; x0 += 8) {
+        float d[32];  // d[8 g + x]: level accumulator g of point x0 + x
+        tmem_ld8x4(tcol + (uint32_t)x0, tcol + (uint32_t)(kOzX + x0), tcol + (uint32_t)(2 * kOzX + x0),
+                   tcol + (uint32_t)(3 * kOzX + x0), d);
+        double pn[8];
 #pragma unroll
-        for (int k = 0; k < 8; k++) pv[k] = x0 + k < xend ? rowp[(size_t)(x0 + k) * B] : 0.0;
+        for (int x = 0; x < 8; x++) pn[x] = (wr && x0 + 8 + x < xend) ? rowp[(size_t)(x0 + 8 + x) * B] : 0.0;
+        if (wr) {
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-          if (x0 + k < xend) {
-            float s, e1, e2;
-            oz_two_sum(d[k], d[8 + k], s, e1);
-            oz_two_sum(s, d[16 + k], s, e2);
-            const float c = __fadd_rn(__fadd_rn(e1, e2), d[24 + k]);
-            rowp[(size_t)(x0 + k) * B] = pv[k] + ff_to_double(__fmul_rn(s, F), __fmul_rn(c, F));
+          for (int x = 0; x < 8; x++) {
+            if (x0 + x < xend) {
+              float s, e1, e2;
+              oz_two_sum(d[x], d[8 + x], s, e1);
+              oz_two_sum(s, d[16 + x], s, e2);
+              const float c = __fadd_rn(__fadd_rn(e1, e2), d[24 + x]);
+              rowp[(size_t)(x0 + x) * B] = pv[x] + ff_to_double(__fmul_rn(s, F), __fmul_rn(c, F));
+            }
           }
         }
+#pragma unroll
+        for (int x = 0; x < 8; x++) pv[x] = pn[x];
       }
+      tc05_fence_before();
+      um_mbar_arrive(ae(u));
     }
   }
-  tc05_fence_before();
   __syncthreads();
+  if (tid == 0 && *s_abort && status) atomicOr(status, kStatusTimeout);
+  tc05_fence_after();
   if (warp == 0) tmem_dealloc(tmem, kOzCols);
-  if (range_bad && status) atomicOr(status, kStatusRange);
 }
-
 
 // The kernel's MMA schedule on host digits: A [6][128][8] and B [6][32][8] (digit values), D [4][128][32]
 // the four level accumulators (test of the operand layouts and of the exactness of the level sums).
@@ -593,9 +654,15 @@ static cudaError_t ozaki_nu(const ExpandLaunch& p, const void* tyff) {
     auto kern = k_expand_ozaki<NU>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int nseg = (p.g.n[0] + kOzX - 1) / kOzX, nyb = (p.g.n[1] + kOzRows - 1) / kOzRows;
-    const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
-    kern<<<dim3(nblk, (p.g.nbands + kOzBands - 1) / kOzBands), kOzAllThreads, smem, p.stream>>>(
+    // persistent: two CTAs per SM walk the tiles (grid row x 32 points x 128 bands) in a fixed stride
+    const long long ntiles = (long long)((p.g.n[0] + kOzX - 1) / kOzX) * p.g.n[1] * p.g.n[2] *
+                             ((p.g.nbands + kOzBands - 1) / kOzBands);
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const unsigned nblk = (unsigned)std::min<long long>(ntiles, 2LL * sms);
+    kern<<<nblk, kOzAllThreads, smem, p.stream>>>(
         p.g, p.atoms, p.plane_ptr, p.plane_atoms, p.max_plane, static_cast<const float2*>(tyff),
         static_cast<const float2*>(p.t2),
         dtab, gpow, tmax, static_cast<double*>(p.psi), p.status, p.wait_cycles, p.stop_stage);

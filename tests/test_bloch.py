@@ -85,8 +85,11 @@ def test_bloch_ff64_zero_k_is_the_real_form_on_each_part():
     out = psi_d.clone()
     api.add_bloch(out, coef, [0, 0, 0], pos, sig, numax, cube, h, prec="ff64")
     re, im = psi_d.real.contiguous(), psi_d.imag.contiguous()
-    api.add(re, coef.real.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
-    api.add(im, coef.imag.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
+    hd = api.Handle(0)
+    hd.set_expand_kernel("mma_sync")  # the float-float block gather, the engine of the Bloch form
+    api.add(re, coef.real.contiguous(), pos, sig, numax, cube, h, True, prec="ff64", handle=hd)
+    api.add(im, coef.imag.contiguous(), pos, sig, numax, cube, h, True, prec="ff64", handle=hd)
+    hd.close()
     assert torch.equal(out.real.contiguous(), re) and torch.equal(out.imag.contiguous(), im)
 
 

@@ -46,6 +46,7 @@ def test_checked_kernels_match_unchecked_bit_for_bit(prec):
     from paper_1905_00480_gb300 import api
     grid, pos, sig, psi, c, numax = _case()
     plain = api.Handle(0)
+    plain.set_expand_kernel("mma_sync")  # the float-float block gather, the kernel the checked mode runs
     ref = _run(api, plain, grid, pos, sig, psi, c, numax, prec)
     assert N.lib().sho_sync(plain.ptr) == 0
     plain.close()

@@ -58,10 +58,11 @@ def _t(x):
 
 
 def _expand_both(grid, h, periodic, pos, sig, psi, c, numax, cube):
-    """FF64 expansion with the tensor-core x-pass and with the float-float kernel (the default)."""
+    """FF64 expansion with the tensor-core x-pass (chosen, and the default where it applies) and with the
+    float-float kernel; the default and the chosen tensor-core engine agree bit for bit."""
     from paper_1905_00480_gb300 import api
     outs = {}
-    for kernel in ("tcgen05", "auto"):
+    for kernel in ("tcgen05", "auto", "mma_sync"):
         hd = api.Handle(0)
         hd.set_expand_kernel(kernel)
         out = _t(psi)
@@ -69,7 +70,8 @@ def _expand_both(grid, h, periodic, pos, sig, psi, c, numax, cube):
         hd.sync()
         outs[kernel] = out.cpu().numpy()
         hd.close()
-    return outs["tcgen05"], outs["auto"]
+    assert np.array_equal(outs["tcgen05"], outs["auto"])
+    return outs["tcgen05"], outs["mma_sync"]
 
 
 @pytest.mark.parametrize("grid,periodic,numax,cube,nbands,natoms", [
