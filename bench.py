@@ -41,8 +41,7 @@ def _peaks():
 # DRAM bytes (read + write) of one call, summed over its kernels' launches, from one ncu capture of the
 # default FF64 bench step (96^3 / 64 atoms / 128 bands), by (call, expansion engine); valid only while
 # those kernels are unchanged (None otherwise).
-NCU_TRAFFIC = {
-    ("k_project", e): 1983526400 + 43296000 + 44086016 for e in ("auto", "tcgen05")}  # x/y-pass + z-pass
+NCU_TRAFFIC = {("k_project", e): 1983526400 + 43296000 + 44086016 for e in ("auto", "mma_sync")}  # x/y + z-pass
 NCU_TRAFFIC.update({("k_expand", e): 3759104 + 44259328 + 952110336 + 841459712 for e in ("auto", "tcgen05")})
 
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
@@ -164,14 +163,16 @@ def max_over_ranks(ws, value):
     return float(t.item())
 
 
-def launches_per_step(api, psi, w, prec, expand_kernel="auto"):
+def launches_per_step(api, psi, w, prec, expand_kernel="auto", project_kernel="auto"):
     """Kernels of this library that one project + expand step launches (mirrors the library's dispatch)."""
     if prec == "ff64":
         oz = (expand_kernel in ("auto", "tcgen05") and w.numax <= 7 and w.cube <= 32 and w.cube % 2 == 0
               and w.nbands % 2 == 0 and (not w.periodic or w.grid[0] >= w.cube + 32))
-        # x/y-pass + z-pass kernels; the float-pair z-pass (with the tables), then the block gather, or the
-        # digit tables and the tensor-core x-pass
-        return 2 + (3 if oz else 2)
+        # projection: the digit tables, the tensor-core x-pass and the z-pass (or the float-float x/y-pass
+        # and the z-pass); expansion: the float-pair z-pass (with the tables), then the digit tables and
+        # the tensor-core x-pass (or the block gather)
+        ozp = project_kernel == "tcgen05" and w.numax <= 7 and w.cube <= 32
+        return (3 if ozp else 2) + (3 if oz else 2)
     if prec == "fp64":
         return 1 + 2  # cluster projection; z-pass + row gather
     tc = prec in ("tf32", "3xtf32", "bf16", "split_fp16")
@@ -210,6 +211,8 @@ def run_ours(args, ws, rank, local):
     handle = api.Handle(local)
     if args.expand_kernel != "auto":
         handle.set_expand_kernel(args.expand_kernel)
+    if args.project_kernel != "auto":
+        handle.set_project_kernel(args.project_kernel)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -386,7 +389,7 @@ def run_ours(args, ws, rank, local):
             bytes_dom = alg["bytes_prj"] if dom == "k_project" else alg["bytes_add"]
             achieved = bytes_dom / (t_dom * 1e-3) / 1e9
             hbm = peaks.get("hbm_gbs", 6793.4)
-            traffic = (NCU_TRAFFIC.get((dom, args.expand_kernel))
+            traffic = (NCU_TRAFFIC.get((dom, args.project_kernel if dom == "k_project" else args.expand_kernel))
                        if (prec == "ff64" and args.workload == WORKLOAD and not args.bands) else None)
             roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic,
@@ -417,6 +420,7 @@ def run_ours(args, ws, rank, local):
                 "l2": f"inputs larger than L2 (psi {psi.numel() * psi.element_size() / 1e6:.0f} MB per buffer), "
                       "no flush",
                 **({"expand_kernel": args.expand_kernel} if args.expand_kernel != "auto" else {}),
+                **({"project_kernel": args.project_kernel} if args.project_kernel != "auto" else {}),
                 "union_cube_points": alg["union_points"],
                 "algorithmic_bytes_per_step": bytes_step,
             },
@@ -431,7 +435,7 @@ def run_ours(args, ws, rank, local):
                     "ms_per_step_windows": [round(v, 4) for v in e2e_runs],
                     "copy_floor_ms_per_step": round(ms_copy, 4),
                     "copy_floor_note": "the same host<->device copies on the same streams without kernels"},
-            "gpu_launches": launches_per_step(api, psi, w, prec, args.expand_kernel) * K,
+            "gpu_launches": launches_per_step(api, psi, w, prec, args.expand_kernel, args.project_kernel) * K,
             "clocks": clk,
             "paper_protocol": {"ms_per_step": round(ms_paper, 4),
                                "value": round(ws * bytes_step / (ms_paper * 1e-3) / 1e9, 3), "unit": "GB/s",
@@ -1268,6 +1272,9 @@ def main():
     ap.add_argument("--expand-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
                     help="x-pass engine of the expansion (sho_set_expand_kernel); for the FF64 form auto and "
                          "tcgen05 take the digit-sliced tensor-core x-pass, mma_sync the float-float block gather")
+    ap.add_argument("--project-kernel", default="auto", choices=["auto", "mma_sync", "tcgen05"],
+                    help="x-pass engine of the FF64 projection (sho_set_project_kernel): auto and mma_sync take "
+                         "the float-float kernel, tcgen05 the digit-sliced tensor-core x-pass")
     ap.add_argument("--table-sphere", type=float, default=3.55,
                     help="projection sphere radius in Angstrom for --paper-table1 (0: whole cube)")
     args = ap.parse_args()

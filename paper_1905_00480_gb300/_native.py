@@ -59,6 +59,7 @@ SIGNATURES = {
     "sho_set_strict": (_I, [_VP, _I]),
     "sho_set_support_radius": (_I, [_VP, ctypes.c_double]),
     "sho_set_expand_kernel": (_I, [_VP, _I]),
+    "sho_set_project_kernel": (_I, [_VP, _I]),
     "sho_set_device_checks": (_I, [_VP, _I]),
     # include/sho_selftest.h
     "sho_selftest_umma": (_I, [_I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),

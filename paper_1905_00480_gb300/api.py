@@ -52,6 +52,12 @@ class Handle:
         N.check(N.lib().sho_set_expand_kernel(self._h, {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]),
                 "sho_set_expand_kernel")
 
+    def set_project_kernel(self, kernel: str):
+        """sho_set_project_kernel: "auto" / "mma_sync" (the float-float CUDA-core kernel of the FF64
+        projection) or "tcgen05" (its digit-sliced tensor-core x-pass, where it applies)."""
+        N.check(N.lib().sho_set_project_kernel(self._h, {"auto": 0, "mma_sync": 1, "tcgen05": 2}[kernel]),
+                "sho_set_project_kernel")
+
     def set_device_checks(self, on: bool = True):
         """sho_set_device_checks: the FP64 / FF64 kernels check every psi, coefficient and intermediate index."""
         N.check(N.lib().sho_set_device_checks(self._h, 1 if on else 0), "sho_set_device_checks")

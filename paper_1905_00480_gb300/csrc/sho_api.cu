@@ -26,7 +26,8 @@ struct sho_handle {
   long long wait_cycles = sho::kDefaultWaitCycles;  // fault injection: limit of the bounded device waits
   int stop_rows = 0x7fffffff;                       // fault injection: rows a plane-sweep producer issues
   double rprj = 0.0;                                // spherical support radius (0: the whole cube)
-  int expand_kernel = SHO_KERNEL_AUTO;              // x-pass engine of the FP32-class expansion
+  int expand_kernel = SHO_KERNEL_AUTO;              // x-pass engine of the FP32-class / FF64 expansion
+  int project_kernel = SHO_KERNEL_AUTO;             // x-pass engine of the FF64 projection
   bool dev_checks = false;                          // device checks of the FP64 / FF64 kernels' indices
   long long check_psi_cap = -1;                     // fault injection: psi extent the checks assume (-1: real)
   // device CSR of the radial transform per (numax, direction): rowp | col | val F64 | val F32
@@ -463,7 +464,10 @@ size_t workspace_bytes(sho_op op, const sho_grid* grid, int natoms, int numax, i
   cv.take((size_t)natoms * sizeof(AtomDev));
   if (op == SHO_OP_PROJECT) {
     cv.take((size_t)natoms * sizeof(int));
-    if (coeff_dtype == SHO_F64) cv.take(ff_t2_bytes(natoms, cube, numax, nbands));  // FP64-accurate form
+    if (coeff_dtype == SHO_F64) {  // FP64-accurate form: per-plane sums, tensor-core tables
+      cv.take(ff_t2_bytes(natoms, cube, numax, nbands));
+      cv.take(op_layout(natoms, cube, numax).total);
+    }
     if (coeff_dtype == SHO_F32 && numax <= kTcMaxNumax) {
       // plane-sweep path (an upper bound: every (atom, plane) split into two row segments)
       const size_t segs = 2 * (size_t)natoms * cube + 1;
@@ -837,8 +841,12 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   }
   SHO_TRY(begin_call(h, s));
   const bool ff_t2 = prec == SHO_P_FF64 && t2_out;
-  const size_t o_bloch = (ff_t2_bytes(natoms, cube, numax, nbands) + 255) & ~(size_t)255;
-  if (prec == SHO_P_FF64 && !ff_t2) SHO_TRY(ensure_workspace(h, o_bloch + (bloch ? natoms * sizeof(BlochPh) : 0)));
+  // FP64-accurate form: per-plane sums (unless the caller provides them), Bloch phases, tensor-core tables
+  Carve fcv;
+  if (!ff_t2) fcv.take(ff_t2_bytes(natoms, cube, numax, nbands));
+  const size_t o_bloch = bloch ? fcv.take((size_t)natoms * sizeof(BlochPh)) : 0;
+  const size_t o_op = fcv.take(op_layout(natoms, cube, numax).total);
+  if (prec == SHO_P_FF64) SHO_TRY(ensure_workspace(h, fcv.off));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[0].key != key) {
     std::vector<int> order = spatial_order(grid, at);
@@ -860,6 +868,9 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   L.t2 = ff_t2 ? t2_out : h->ws;
   L.t2_only = ff_t2;
   L.status = h->dstatus;
+  if (prec == SHO_P_FF64) L.op = static_cast<char*>(h->ws) + o_op;
+  L.kernel = h->project_kernel;
+  L.wait_cycles = h->wait_cycles;
   L.chk = make_check(h, grid, nbands, natoms, numax, cube);
   if (bloch) {
     L.chk = DevCheck{};  // the Bloch kernels run unchecked
@@ -1237,6 +1248,12 @@ int sho_usu_add(sho_handle* h, const sho_grid* grid, const void* coeff, int nban
 int sho_set_expand_kernel(sho_handle* h, int kernel) {
   if (!h || kernel < SHO_KERNEL_AUTO || kernel > SHO_KERNEL_TCGEN05) return SHO_ERR_ARG;
   h->expand_kernel = kernel;
+  return SHO_OK;
+}
+
+int sho_set_project_kernel(sho_handle* h, int kernel) {
+  if (!h || kernel < SHO_KERNEL_AUTO || kernel > SHO_KERNEL_TCGEN05) return SHO_ERR_ARG;
+  h->project_kernel = kernel;
   return SHO_OK;
 }
 

@@ -607,20 +607,27 @@ __global__ void __launch_bounds__(kFfRows * kWarp) k_expand_blk_ff(GridDev g, co
 template <int NU>
 static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   if (!p.t2) return cudaErrorInvalidValue;
-  const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
-  auto kern = p.chk.flag ? k_project_ff<NU, true> : k_project_ff<NU, false>;
-  if constexpr (NU <= kBlochFfMaxNumax) {
-    if (p.bloch) kern = k_project_ff<NU, false, true>;
-  } else if (p.bloch) {
-    return cudaErrorInvalidValue;
-  }
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const unsigned nbt = (unsigned)((p.g.nbands + kWarp - 1) / kWarp);
-  kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
-      p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status, p.chk,
-      p.bloch);
-  e = cudaGetLastError();
+  cudaError_t e;
+  if (p.kernel == 2 && !p.bloch && !p.chk.flag && ozaki_project_ok(p)) {
+    // the x-pass on the tensor cores by exact digit slicing when chosen (kernel choice tcgen05): correct,
+    // but its 104 M128 N16 K8 MMAs per cube row take about 75 cycles each, twice the float-float kernel
+    e = launch_project_ozaki(p);
+  } else {
+    const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
+    auto kern = p.chk.flag ? k_project_ff<NU, true> : k_project_ff<NU, false>;
+    if constexpr (NU <= kBlochFfMaxNumax) {
+      if (p.bloch) kern = k_project_ff<NU, false, true>;
+    } else if (p.bloch) {
+      return cudaErrorInvalidValue;
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)p.zsplit, nbt, (unsigned)p.natoms), kWarp, smem, p.stream>>>(
+        p.g, static_cast<const double*>(p.psi), p.atoms, p.zsplit, static_cast<double*>(p.t2), p.status, p.chk,
+        p.bloch);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || p.t2_only) return e;
   const size_t zsmem = FfZpassSmem<NU>::bytes(p.g.cube);
   auto zk = k_project_ff_zpass<NU>;

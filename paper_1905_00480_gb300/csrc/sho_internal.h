@@ -94,8 +94,29 @@ struct ProjectLaunch {
   DevCheck chk;             // device checks (FP64 and FP64-accurate kernels), off by default
   const BlochPh* bloch = nullptr;  // FP64-accurate Bloch projection: device [A] phases; psi and coeff
                                    // are complex, their (re, im) pairs counted as 2 real bands (g.nbands)
+  void* op = nullptr;       // FP64-accurate form on the tensor cores: op_layout() workspace, may be null
+  int kernel = 0;           // FP64-accurate x-pass engine: 0 automatic, 1 float-float, 2 tcgen05
+  long long wait_cycles = kDefaultWaitCycles;  // limit of the bounded waits (tensor-core kernel)
   cudaStream_t stream;
 };
+
+// Workspace of the FP64-accurate projection on the tensor cores (sho_ozaki_project.cu), offsets in bytes
+// from ProjectLaunch::op, each region 256-byte aligned: the digit tables of the x functions [A][6][8][16][4]
+// floats, the per-atom power of two G_a [A] and the y functions as float pairs [A][numax+1][cube].
+struct OpLayout {
+  size_t btab, gpow, tyff, total;
+};
+inline OpLayout op_layout(int natoms, int cube, int numax) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  OpLayout L;
+  L.btab = 0;
+  L.gpow = up((size_t)natoms * 6 * 8 * 16 * 4 * sizeof(float));
+  L.tyff = L.gpow + up((size_t)natoms * sizeof(float));
+  L.total = L.tyff + up((size_t)natoms * (numax + 1) * cube * 2 * sizeof(float));
+  return L;
+}
+bool ozaki_project_ok(const ProjectLaunch& p);
+cudaError_t launch_project_ozaki(const ProjectLaunch& p);
 
 // Inputs of the fused non-local action (Sec. 3.2 steps 1-3) taken by the expansion's z-pass kernel: the
 // projection coefficients c of each (atom, band) -- from the projection's per-plane y-pass sums t2p

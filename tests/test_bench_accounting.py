@@ -69,6 +69,7 @@ def test_separable_flops_per_atom_band(cube, numax, flops):
 
 def test_launches_per_step_of_the_fp64_forms():
     w = workloads.WORKLOADS["c96"]
-    assert bench.launches_per_step(None, None, w, "ff64") == 5           # digit tables + tensor-core x-pass
-    assert bench.launches_per_step(None, None, w, "ff64", "mma_sync") == 4  # float-float block gather
+    assert bench.launches_per_step(None, None, w, "ff64") == 5   # float-float projection, tensor-core expansion
+    assert bench.launches_per_step(None, None, w, "ff64", "mma_sync", "mma_sync") == 4  # float-float kernels
+    assert bench.launches_per_step(None, None, w, "ff64", "tcgen05", "tcgen05") == 6    # tensor-core x-passes
     assert bench.launches_per_step(None, None, w, "fp64") == 3

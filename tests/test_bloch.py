@@ -78,8 +78,11 @@ def test_bloch_ff64_zero_k_is_the_real_form_on_each_part():
     rng, pos, sig, psi = _case(925, grid, h, 4, 12)
     psi_d = torch.from_numpy(psi).cuda()
     c0 = api.project_bloch(psi_d, [0, 0, 0], pos, sig, numax, cube, h, prec="ff64")
-    cr = api.project(psi_d.real.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
-    ci = api.project(psi_d.imag.contiguous(), pos, sig, numax, cube, h, True, prec="ff64")
+    hf = api.Handle(0)
+    hf.set_project_kernel("mma_sync")  # the float-float projection, the engine of the Bloch form
+    cr = api.project(psi_d.real.contiguous(), pos, sig, numax, cube, h, True, prec="ff64", handle=hf)
+    ci = api.project(psi_d.imag.contiguous(), pos, sig, numax, cube, h, True, prec="ff64", handle=hf)
+    hf.close()
     assert torch.equal(c0.real.contiguous(), cr) and torch.equal(c0.imag.contiguous(), ci)
     coef = torch.from_numpy(rng.standard_normal(c0.shape) + 1j * rng.standard_normal(c0.shape)).cuda()
     out = psi_d.clone()

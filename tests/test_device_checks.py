@@ -46,7 +46,8 @@ def test_checked_kernels_match_unchecked_bit_for_bit(prec):
     from paper_1905_00480_gb300 import api
     grid, pos, sig, psi, c, numax = _case()
     plain = api.Handle(0)
-    plain.set_expand_kernel("mma_sync")  # the float-float block gather, the kernel the checked mode runs
+    plain.set_expand_kernel("mma_sync")  # the float-float kernels, the ones the checked mode runs
+    plain.set_project_kernel("mma_sync")
     ref = _run(api, plain, grid, pos, sig, psi, c, numax, prec)
     assert N.lib().sho_sync(plain.ptr) == 0
     plain.close()
