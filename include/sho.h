@@ -156,12 +156,12 @@ int sho_set_expand_kernel(sho_handle* handle, int kernel);
  * sho_apply_nonlocal): SHO_KERNEL_AUTO (default) and SHO_KERNEL_MMA_SYNC take the float-float CUDA-core
  * kernel; SHO_KERNEL_TCGEN05 takes the fifth-generation tensor cores by exact digit slicing -- psi cut into
  * six 8-bit digits on a power-of-two frame per (cube row, band, half row of 16 points), the x functions on
- * a frame per atom, TF32 MMAs (M = 128 bands, N = 16 states, K = 8 points) whose leading level sums are
- * exact integers, in a persistent kernel with digit, MMA and read-back warps -- where it applies (numax
- * <= 7, cube <= 32, no spherical support, real data, device checks off).  The tensor-core form is correct
- * to the FP64 tolerance (its error about 2^-48 of each half row's frame times sum |phi|) but measured at
- * half the float-float kernel's speed: the narrow MMAs it issues are its bound.  Forces and served
- * requests always use the float-float kernel.  SHO_ERR_ARG for an unknown value or a null handle. */
+ * a frame per atom, BF16 MMAs (M = 128 bands, N = 64 = 7 levels x 8 states, K = 16 points) whose level
+ * sums are exact integers, in a persistent kernel with digit, MMA and read-back warps -- where it applies
+ * (numax <= 7, cube <= 32, no spherical support, real data, device checks off).  The tensor-core form is
+ * correct to the FP64 tolerance (its error about 2^-48 of each half row's frame times sum |phi|) but
+ * measured about 20 % slower than the float-float kernel on GB300.  Forces and served requests always use
+ * the float-float kernel.  SHO_ERR_ARG for an unknown value or a null handle. */
 int sho_set_project_kernel(sho_handle* handle, int kernel);
 
 /* Debug mode (on != 0; off by default): the handle's SHO_P_FP64 and SHO_P_FF64 projection, expansion and

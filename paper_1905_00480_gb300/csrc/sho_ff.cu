@@ -611,7 +611,7 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   cudaError_t e;
   if (p.kernel == 2 && !p.bloch && !p.chk.flag && ozaki_project_ok(p)) {
     // the x-pass on the tensor cores by exact digit slicing when chosen (kernel choice tcgen05): correct,
-    // but its 104 M128 N16 K8 MMAs per cube row take about 75 cycles each, twice the float-float kernel
+    // but measured about 20 % slower than the float-float kernel (its digit warps are the bound)
     e = launch_project_ozaki(p);
   } else {
     const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);

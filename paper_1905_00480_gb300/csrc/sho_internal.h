@@ -101,8 +101,9 @@ struct ProjectLaunch {
 };
 
 // Workspace of the FP64-accurate projection on the tensor cores (sho_ozaki_project.cu), offsets in bytes
-// from ProjectLaunch::op, each region 256-byte aligned: the digit tables of the x functions [A][6][8][16][4]
-// floats, the per-atom power of two G_a [A] and the y functions as float pairs [A][numax+1][cube].
+// from ProjectLaunch::op, each region 256-byte aligned: the stacked digit tables of the x functions
+// [A][6][4][64][8] BF16, the per-atom power of two G_a [A] and the y functions as float pairs
+// [A][numax+1][cube].
 struct OpLayout {
   size_t btab, gpow, tyff, total;
 };
@@ -110,7 +111,7 @@ inline OpLayout op_layout(int natoms, int cube, int numax) {
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   OpLayout L;
   L.btab = 0;
-  L.gpow = up((size_t)natoms * 6 * 8 * 16 * 4 * sizeof(float));
+  L.gpow = up((size_t)natoms * 6 * 4 * 64 * 8 * 2);
   L.tyff = L.gpow + up((size_t)natoms * sizeof(float));
   L.total = L.tyff + up((size_t)natoms * (numax + 1) * cube * 2 * sizeof(float));
   return L;

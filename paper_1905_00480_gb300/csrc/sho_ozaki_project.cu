@@ -10,33 +10,40 @@
 //     atom a power of two G_a above max |phi^a|;
 //   * psi / F = sum_{i=1..6} d_i and phi^a_nx(ix) / G_a = sum_{j=1..6} e_j, signed integers times 2^(-8 i),
 //     2^(-8 j) (round-to-nearest digits from the float pair of psi; at most 256 in magnitude);
-//   * the products d_i e_j of level L = i + j = 2, 3, 4 go to one accumulator per level, where the sums
-//     over the 16 points stay integers below 2^24 and so are exact; levels 5 .. 8 share a fourth one;
-//     levels above 8 are dropped (below 2^-56 F G_a per product);
+//   * the products d_i e_j of each level L = i + j = 2 .. 8 go to one accumulator per level, where the
+//     sums over the digit pairs and the 16 points stay integers below 2^24 and so are exact; levels above
+//     8 are dropped (below 2^-56 F G_a per product);
 //   * T1[nx] = G_a (F_0 S_0[nx] + F_1 S_1[nx]) with S_h the half row's level sums, summed as float pairs;
 //     the y-pass then runs as float-float dot steps and each finished plane's sums go to the FP64
 //     workspace of the z-pass kernel (k_project_ff_zpass), exactly as in the float-float projection.
-// The operands are TF32 (digits of at most 9 significant bits are exact in TF32), M = 128 bands, N = 16
-// (the numax + 1 <= 8 states, zero-padded), K = 8 points per MMA, two K steps per half row.
+// The operands are BF16 (digits of at most 8 significant bits -- integers up to 256 -- are exact in
+// BF16).  The MMA sums over the psi digits as well as the points: for psi digit i the B operand stacks
+// the x functions' digit j = L - i of every level L = 2..8 (64 rows: level x state, zero where L - i is
+// not a digit), so that
+//   D[band][(L, n)] += sum_k d_i[band][k] e_{L-i}[n][k]
+// gathers the level-L products of all digit pairs in one accumulator column (at most 6 x 16 products of
+// at most 2^16 per level: exact integers); M = 128 bands, N = 64, K = 16 points: 6 MMAs per half row.
+// Opt-in (sho_set_project_kernel): measured about 20 % slower than the float-float kernel on GB300, its
+// digit warps the bound.
 //
 // Persistent kernel, one CTA per SM over work items (atom, 128-band tile, cube plane) in contiguous
 // ranges, 32 rows per item, with three warp roles that meet on mbarriers only:
 //   * eight digit warps, thread = (band, half row): the row's 16 psi values (the next row's loaded ahead),
-//     the frame, six digit slices written as the A operands of the row's slot (two slots by row parity,
-//     free once the MMAs of row gr - 2 are done), then arrivals on the slot's operand barrier and on the
-//     frame barrier of the row (four frame and accumulator slots, free once row gr - 4 is read back);
-//   * one MMA thread: the atom's digit table staged once per atom by a bulk copy (after every MMA reading
-//     the previous one is done), then per row 2 halves x 26 digit pairs x 2 K steps of M128 N16 K8 MMAs into
-//     the row's level accumulators in tensor memory (four rows in flight, 512 columns), committed to
-//     the row's barrier;
-//   * four read-back warps, one thread per band: the row's accumulators and frames, T1 as float pairs,
-//     the y-pass, and at each plane's end its sums to the workspace.
-// Opt-in (sho_set_project_kernel): measured at twice the float-float kernel's time on GB300, bound by its
-// MMA thread -- the 104 narrow MMAs of a row take about 75 cycles each while the digit warps wait.
+//     the frame, six digit slices written as the A operands of the half row's stage (three stages, free
+//     once their MMAs are done), then arrivals on the stage's operand barrier and on the row's frame
+//     barrier (four frame and accumulator slots, free once row gr - 4 is read back);
+//   * one MMA thread: the atom's stacked digit table staged once per atom by a bulk copy (after every MMA
+//     reading the previous one is done), then per half row 12 MMAs into the row's level accumulators in
+//     tensor memory (four rows in flight, 512 columns), committed to the stage's barrier and, after the
+//     row, to the row's barrier;
+//   * four read-back warps, one thread per band: the row's level sums and frames, T1 as float pairs, the
+//     y-pass, and at each plane's end its sums to the workspace.
 // Deterministic: fixed order, exact leading levels, each item computed by one CTA.  Every wait is bounded;
 // the first one that runs out stops every role (a shared flag), the kernel records kStatusTimeout, waits
 // (bounded) for its own copies and MMAs, frees tensor memory and returns.
 #include <algorithm>
+
+#include <cuda_bf16.h>
 
 #include "sho_device.cuh"
 #include "sho_ff.cuh"
@@ -46,26 +53,25 @@
 namespace sho {
 
 constexpr int kOpBands = 128;                          // bands per item (the MMA M), one read-back thread each
-constexpr int kOpN = 16;                               // MMA N: the states, zero-padded
+constexpr int kOpN = 64;                               // MMA N: 7 levels x 8 states (levels 2..8)
 constexpr int kOpHalf = 16;                            // cube points per half row (the K of one operand set)
 constexpr int kOpDigits = 6;                           // digits per operand value
-constexpr int kOpMaxLevel = 8;                         // digit pairs (i, j) with i + j <= 8 are multiplied
-constexpr int kOpGroups = 4;                           // accumulators: levels 2, 3, 4 and 5..8
 constexpr int kOpDigitThreads = 2 * kOpBands;          // thread = (band, half row)
 constexpr int kOpThreads = kOpDigitThreads + kOpBands + 32;  // + read-back warps + MMA warp: 416
 constexpr int kOpMmaWarp = (kOpDigitThreads + kOpBands) / 32;  // 12
-constexpr uint32_t kOpAKc = kOpBands * 16;             // one K column of A (128 bands x 4 points, TF32): 2 KB
-constexpr uint32_t kOpASlice = 4 * kOpAKc;             // one digit of one half row: 8 KB
-constexpr uint32_t kOpASlot = 2 * kOpDigits * kOpASlice;  // both halves, six digits: 96 KB
-constexpr uint32_t kOpBKc = kOpN * 16;                 // one K column of B (16 states x 4 points): 256 B
-constexpr uint32_t kOpBSlice = 8 * kOpBKc;             // one digit, 32 points: 2 KB
-constexpr uint32_t kOpBBytes = kOpDigits * kOpBSlice;  // digit table of one atom: 12 KB
-constexpr int kOpSlotCols = 2 * kOpGroups * kOpN;      // tensor-memory columns of one row: 128
+constexpr uint32_t kOpAKc = kOpBands * 16;             // one K column of A (128 bands x 8 points, BF16): 2 KB
+constexpr uint32_t kOpASlice = 2 * kOpAKc;             // one digit of one half row: 4 KB
+constexpr uint32_t kOpAStage = kOpDigits * kOpASlice;  // the six digit slices of one half row: 24 KB
+constexpr int kOpStages = 4;                            // half-row operand stages in flight
+constexpr uint32_t kOpBKc = kOpN * 16;                 // one K column of B (64 rows x 8 points): 1 KB
+constexpr uint32_t kOpBSlice = 4 * kOpBKc;             // one psi digit's stacked table, 32 points: 4 KB
+constexpr uint32_t kOpBBytes = kOpDigits * kOpBSlice;  // stacked digit table of one atom: 24 KB
+constexpr int kOpSlotCols = 2 * kOpN;                  // one row: an accumulator set per half row: 128
 constexpr int kOpRows = 4;                             // rows whose accumulators and frames are in flight
 constexpr int kOpCols = kOpRows * kOpSlotCols;         // 512
 
 struct OpSmem {
-  static constexpr size_t off_b = 2 * (size_t)kOpASlot;                     // after two A slots (192 KB)
+  static constexpr size_t off_b = kOpStages * (size_t)kOpAStage;           // after four A stages (96 KB)
   static constexpr size_t off_e = off_b + kOpBBytes;                        // frames [4 rows][2 halves][128]
   static constexpr size_t off_bar = (off_e + kOpRows * 2 * kOpBands * 4 + 127) & ~(size_t)127;
   static constexpr size_t bytes = off_bar + 256;  // barriers, tensor-memory slot, abort flag
@@ -73,15 +79,17 @@ struct OpSmem {
 static_assert(OpSmem::bytes <= 227 * 1024, "one CTA per SM");
 
 // ------------------------------------------------------------------------------------- tables
-// Block a (128 threads): G_a = 2^e with max |phi_x| < 2^e, the digit table of phi_x / G_a in the B layout
-// [6 digits][8 point columns][16 states][4 points] (zero above numax and beyond the cube), and the y
-// functions as float pairs [NP][C].  Every digit step is exact in FP64.
+// Block a (128 threads): G_a = 2^e with max |phi_x| < 2^e; the digits e_j (j = 1..6) of phi_x / G_a; for
+// each psi digit i the stacked B operand [8 point columns][64 rows (L - 2) 8 + n][4 points] holding e_{L-i}
+// of state n (zero where L - i is not in 1..6, above numax and beyond the cube); and the y functions as
+// float pairs [NP][C].  Every digit step is exact in FP64.
 template <int NU>
 __global__ void __launch_bounds__(128) k_op_tables(GridDev g, const AtomDev* __restrict__ atoms,
-                                                   float* __restrict__ btab, float* __restrict__ gpow,
+                                                   __nv_bfloat16* __restrict__ btab, float* __restrict__ gpow,
                                                    float2* __restrict__ tyff) {
   constexpr int NP = NU + 1;
   __shared__ double px[NP][32];
+  __shared__ float dg[kOpDigits][8][32];  // e_j [digit][state][point]
   __shared__ double red[4];
   const int a = blockIdx.x, tid = threadIdx.x, C = g.cube;
   const AtomDev at = atoms[a];
@@ -118,8 +126,7 @@ __global__ void __launch_bounds__(128) k_op_tables(GridDev g, const AtomDev* __r
   const double G = m > 0.0 ? ldexp(1.0, e) : 1.0;
   if (tid == 0) gpow[a] = (float)G;
   const double ginv = 1.0 / G;
-  float* dst = btab + (size_t)a * (kOpBBytes / 4);
-  for (int idx = tid; idx < kOpN * 32; idx += 128) {
+  for (int idx = tid; idx < 8 * 32; idx += 128) {
     const int n = idx / 32, i = idx % 32;
     double v = n < NP ? px[n][i] * ginv : 0.0;  // |v| < 1
     double sc = 1.0, isc = 1.0;
@@ -129,20 +136,30 @@ __global__ void __launch_bounds__(128) k_op_tables(GridDev g, const AtomDev* __r
       isc *= 0.00390625;
       const double d = rint(v * sc) * isc;
       v -= d;
-      dst[j * (kOpBSlice / 4) + (i / 4) * (kOpBKc / 4) + n * 4 + (i % 4)] = (float)d;
+      dg[j][n][i] = (float)d;  // at most 256 (then 128) times 2^(-8 (j + 1))
     }
+  }
+  __syncthreads();
+  __nv_bfloat16* dst = btab + (size_t)a * (kOpBBytes / 2);
+  for (int idx = tid; idx < kOpDigits * kOpN * 32; idx += 128) {
+    const int di = idx / (kOpN * 32), r = (idx / 32) % kOpN, k = idx % 32;  // psi digit i = di + 1
+    const int L = r / 8 + 2, n = r % 8, j = L - (di + 1);                    // x digit j (1-based)
+    const float v = (r < 56 && j >= 1 && j <= kOpDigits) ? dg[j - 1][n][k] : 0.0f;
+    // digits of at most 8 significant bits: exact in BF16
+    dst[di * (kOpBSlice / 2) + (k / 8) * (kOpBKc / 2) + r * 8 + (k % 8)] = __float2bfloat16_rn(v);
   }
 }
 
 // ------------------------------------------------------------------------------------- projection
 template <int NU>
-__global__ void __launch_bounds__(kOpThreads, 1)
+__global__ void __launch_bounds__(kOpThreads, 1)  // 13 warps: at most 128 registers (16 K per SM sub-partition)
     k_project_ozaki(GridDev g, const double* __restrict__ psi, const AtomDev* __restrict__ atoms, int natoms,
-                    const float* __restrict__ btab, const float* __restrict__ gpow, const float2* __restrict__ tyff,
-                    double* __restrict__ t2g, int* __restrict__ status, long long wait_cycles) {
+                    const __nv_bfloat16* __restrict__ btab, const float* __restrict__ gpow,
+                    const float2* __restrict__ tyff, double* __restrict__ t2g, int* __restrict__ status,
+                    long long wait_cycles) {
   using BS = Basis<NU>;
   constexpr int NP = BS::NP, P = BS::P;
-  static_assert(NP <= 8, "the states fit one 8-column read-back");
+  static_assert(NP <= 8, "8 states per level column group");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const int C = g.cube, Nx = g.n[0], Ny = g.n[1], Nz = g.n[2], B = g.nbands;
   const int nbt = (B + kOpBands - 1) / kOpBands;
@@ -151,23 +168,30 @@ __global__ void __launch_bounds__(kOpThreads, 1)
   const int nhalf = C > kOpHalf ? 2 : 1;
   const uint32_t sbase = um_smem(smem_raw);
   const uint32_t sB = sbase + (uint32_t)OpSmem::off_b;
-  int* sexp = reinterpret_cast<int*>(smem_raw + OpSmem::off_e);  // [slot][half][band]
+  int* sexp = reinterpret_cast<int*>(smem_raw + OpSmem::off_e);  // [row slot][half][band]
   unsigned char* barp = smem_raw + OpSmem::off_bar;
   const uint32_t bar0 = um_smem(barp);
-  // A operand slots by row parity; accumulators and frames by row modulo 4
-  auto fb = [&](int s) { return bar0 + 8 * s; };        // A operands of slot s written (256 arrivals)
-  auto xf = [&](int r) { return bar0 + 16 + 8 * r; };   // frames of row slot r written (256)
-  auto rd = [&](int r) { return bar0 + 48 + 8 * r; };   // MMAs of row slot r done (MMA commit)
-  auto ae = [&](int r) { return bar0 + 80 + 8 * r; };   // accumulators and frames of row slot r read (128)
-  const uint32_t bb = bar0 + 112;                       // digit table staged (bulk copy)
-  const uint32_t dr = bar0 + 120;                       // drain: every MMA issued so far done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + 128);
-  volatile int* s_abort = reinterpret_cast<volatile int*>(barp + 132);
+  // operand stages by half-row count modulo 3; accumulators and frames by row modulo 4
+  constexpr uint32_t kFa = 0, kCa = kFa + 8 * kOpStages, kXf = kCa + 8 * kOpStages, kRd = kXf + 8 * kOpRows,
+                     kAe = kRd + 8 * kOpRows, kBb = kAe + 8 * kOpRows, kDr = kBb + 8, kSlot = kDr + 8;
+  static_assert(kSlot + 8 <= OpSmem::bytes - OpSmem::off_bar, "barrier area");
+  auto fa = [&](int q) { return bar0 + kFa + 8 * q; };  // A operands of stage q written (128 arrivals)
+  auto ca = [&](int q) { return bar0 + kCa + 8 * q; };  // MMAs reading stage q done (MMA commit)
+  auto xf = [&](int r) { return bar0 + kXf + 8 * r; };  // frames of row slot r written (256)
+  auto rd = [&](int r) { return bar0 + kRd + 8 * r; };  // MMAs of row slot r done (MMA commit)
+  auto ae = [&](int r) { return bar0 + kAe + 8 * r; };  // accumulators and frames of row slot r read (128)
+  const uint32_t bb = bar0 + kBb;                       // digit table staged (bulk copy)
+  const uint32_t dr = bar0 + kDr;                       // drain: every MMA issued so far done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(barp + kSlot);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(barp + kSlot + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     *s_abort = 0;
-    for (int s = 0; s < 2; s++) um_mbar_init_n(fb(s), kOpDigitThreads);
+    for (int q = 0; q < kOpStages; q++) {
+      um_mbar_init_n(fa(q), kOpBands);
+      um_mbar_init(ca(q));
+    }
     for (int r = 0; r < kOpRows; r++) {
       um_mbar_init_n(xf(r), kOpDigitThreads);
       um_mbar_init(rd(r));
@@ -207,7 +231,7 @@ __global__ void __launch_bounds__(kOpThreads, 1)
   if (warp == kOpMmaWarp) {
     // ---- MMA thread
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc(kUmmaTF32, kOpBands, kOpN);
+      constexpr uint32_t idesc = umma_idesc(kUmmaBF16, kOpBands, kOpN);
       const uint64_t ad0 = umma_desc(sbase, kOpAKc, 128), bd0 = umma_desc(sB, kOpBKc, 128);
       int gr = 0, cur = -1;
       uint32_t bbp = 0, drp = 0;
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(kOpThreads, 1)
           }
           fence_async_smem();
           um_expect_tx(bb, kOpBBytes);
-          um_bulk(sB, btab + (size_t)a * (kOpBBytes / 4), kOpBBytes, bb);
+          um_bulk(sB, btab + (size_t)a * (kOpBBytes / 2), kOpBBytes, bb);
           if (!wait(bb, bbp)) {
             (void)um_mbar_wait(bb, bbp, kDefaultWaitCycles);  // the copy completes before the CTA exits
             break;
@@ -232,31 +256,33 @@ __global__ void __launch_bounds__(kOpThreads, 1)
           bbp ^= 1u;
           cur = a;
         }
-        for (int iy = 0; iy < C; iy++, gr++) {
-          const int slot = gr & 1, rs = gr & (kOpRows - 1);
-          // the row slot's accumulators read back (row gr - 4), the A operands of row gr written
-          if (gr >= kOpRows && !wait(ae(rs), (uint32_t)(((gr - kOpRows) >> 2) & 1))) { ok = false; break; }
-          if (!wait(fb(slot), (uint32_t)((gr >> 1) & 1))) { ok = false; break; }
-          tc05_fence_after();
-          const uint64_t ad = ad0 + (uint64_t)((slot * kOpASlot) >> 4);
-          for (int h = 0; h < nhalf; h++) {
-            // consecutive MMAs share their A operand (one digit slice, one K step): pairs j for each (i, ks)
-#pragma unroll
-            for (int i = 1; i <= kOpDigits; i++)
-#pragma unroll
-              for (int ks = 0; ks < 2; ks++)
-#pragma unroll
-                for (int j = 1; j <= kOpDigits; j++) {
-                  if (i + j > kOpMaxLevel) continue;
-                  const int grp = (i + j < 5 ? i + j : 5) - 2;
-                  const uint32_t dacc = tmem + (uint32_t)(rs * kOpSlotCols + (h * kOpGroups + grp) * kOpN);
-                  // the first product of each level group in the row starts its accumulator
-                  const bool acc = ks > 0 || !(i == 1 && j <= 4);
-                  umma_tf32(dacc,
-                            ad + (uint64_t)(((h * kOpDigits + i - 1) * kOpASlice + 2 * ks * kOpAKc) >> 4),
-                            bd0 + (uint64_t)(((j - 1) * kOpBSlice + (4 * h + 2 * ks) * kOpBKc) >> 4), idesc, acc);
-                }
+        for (int iy = 0; iy < C && ok; iy++, gr++) {
+          const int rs = gr & (kOpRows - 1);
+          // the row slot's accumulators read back (row gr - 4)
+          if (gr >= kOpRows && !wait(ae(rs), (uint32_t)(((gr - kOpRows) / kOpRows) & 1))) { ok = false; break; }
+          // both half rows' operands written, then the row's MMAs, the two halves' accumulator sets
+          // interleaved
+          for (int h = 0; h < nhalf && ok; h++) {
+            const int st = gr * nhalf + h;
+            if (!wait(fa(st % kOpStages), (uint32_t)((st / kOpStages) & 1))) ok = false;
           }
+          if (!ok) break;
+          tc05_fence_after();
+          const int st0 = gr * nhalf;
+          const uint64_t ad_0 = ad0 + (uint64_t)(((st0 % kOpStages) * kOpAStage) >> 4);
+          const uint64_t ad_1 = ad0 + (uint64_t)((((st0 + 1) % kOpStages) * kOpAStage) >> 4);
+          const uint32_t drow = tmem + (uint32_t)(rs * kOpSlotCols);
+#pragma unroll
+          for (int i = 0; i < kOpDigits; i++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              if (h >= nhalf) continue;
+              umma_f16(drow + (uint32_t)(h * kOpN), (h ? ad_1 : ad_0) + (uint64_t)((i * kOpASlice) >> 4),
+                       bd0 + (uint64_t)((i * kOpBSlice + 2 * h * kOpBKc) >> 4), idesc,
+                       i > 0);  // the first digit starts each accumulator set
+            }
+          for (int h = 0; h < nhalf; h++) umma_commit(ca((st0 + h) % kOpStages));
+          if (!ok) break;
           umma_commit(rd(rs));
           any = true;
         }
@@ -269,8 +295,10 @@ __global__ void __launch_bounds__(kOpThreads, 1)
     __syncwarp();
   } else if (tid < kOpDigitThreads) {
     // ---- digit threads, thread = (band, half row): per row the 16 psi values, their frame and six digit
-    // slices as the A operands of the row's slot, once the slot's MMAs and read-back of row gr - 2 are done
+    // slices as the A operands of the half row's stage, once the stage's earlier MMAs are done and the
+    // row slot's frames (row gr - 4) are read back
     const int bl = tid & (kOpBands - 1), hh = tid >> 7;
+    const bool active = hh < nhalf;  // a second half row exists
     int gr = 0, cur = -1;
     int jx[kOpHalf];
     bool range_bad = false;
@@ -288,7 +316,7 @@ __global__ void __launch_bounds__(kOpThreads, 1)
         cur = a;
       }
       const int b = bt * kOpBands + bl;
-      const bool bvalid = b < B;
+      const bool bvalid = b < B && active;
       const int jz = cube_index(at.o[2], iz, Nz, g.periodic);
       auto load_row = [&](int iy, double (&v)[kOpHalf]) {
         const int jy = cube_index(at.o[1], iy, Ny, g.periodic);
@@ -300,11 +328,12 @@ __global__ void __launch_bounds__(kOpThreads, 1)
       load_row(0, pv);
       bool ok = true;
       for (int iy = 0; iy < C; iy++, gr++) {
-        const int slot = gr & 1, rs = gr & (kOpRows - 1);
+        const int rs = gr & (kOpRows - 1);
+        const int st = gr * nhalf + hh, q = st % kOpStages;
         if (iy + 1 < C) load_row(iy + 1, pn);  // in flight during this row
-        // A slot free: the MMAs of row gr - 2 done; frame slot free: row gr - 4 read back
-        if ((gr >= 2 && !wait(rd((gr - 2) & (kOpRows - 1)), (uint32_t)(((gr - 2) >> 2) & 1))) ||
-            (gr >= kOpRows && !wait(ae(rs), (uint32_t)(((gr - kOpRows) >> 2) & 1)))) {
+        // stage free: the MMAs of half row st - 3 done; frame slot free: row gr - 4 read back
+        if ((active && st >= kOpStages && !wait(ca(q), (uint32_t)(((st - kOpStages) / kOpStages) & 1))) ||
+            (gr >= kOpRows && !wait(ae(rs), (uint32_t)(((gr - kOpRows) / kOpRows) & 1)))) {
           ok = false;
           break;
         }
@@ -319,31 +348,36 @@ __global__ void __launch_bounds__(kOpThreads, 1)
         int e = (int)(mh >> 20) - 1023 + 1;  // |psi| < 2^e
         e = max(-124, min(e, 127));
         sexp[(rs * 2 + hh) * kOpBands + bl] = e;
-        const float s1 = oz_pow2(-(e >> 1)), s2 = oz_pow2(-(e - (e >> 1)));  // 2^-e in two factors
-        unsigned char* arow = smem_raw + (size_t)slot * kOpASlot + (size_t)hh * kOpDigits * kOpASlice + (size_t)bl * 16;
+        if (active) {
+          const float s1 = oz_pow2(-(e >> 1)), s2 = oz_pow2(-(e - (e >> 1)));  // 2^-e in two factors
+          unsigned char* arow = smem_raw + (size_t)q * kOpAStage + (size_t)bl * 16;
 #pragma unroll
-        for (int kc = 0; kc < 4; kc++) {
-          float dg[kOpDigits][4];
+          for (int kc = 0; kc < 4; kc++) {  // groups of 4 points: half of an 8-point BF16 core-matrix row
+            float dg[kOpDigits][4];
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const ff v = ff_from_double(pv[4 * kc + q]);
-            float rem = __fmul_rn(__fmul_rn(v.hi, s1), s2);  // |rem| < 1
-            const float lo = __fmul_rn(__fmul_rn(v.lo, s1), s2);
-            dg[0][q] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
-            dg[1][q] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
-            dg[2][q] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
-            rem = __fadd_rn(rem, lo);
-            dg[3][q] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
-            dg[4][q] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
-            dg[5][q] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
+            for (int k4 = 0; k4 < 4; k4++) {
+              const ff v = ff_from_double(pv[4 * kc + k4]);
+              float rem = __fmul_rn(__fmul_rn(v.hi, s1), s2);  // |rem| < 1
+              const float lo = __fmul_rn(__fmul_rn(v.lo, s1), s2);
+              dg[0][k4] = oz_digit(rem, 0x1.8p+15f);  // grid 2^-8
+              dg[1][k4] = oz_digit(rem, 0x1.8p+7f);   // grid 2^-16
+              dg[2][k4] = oz_digit(rem, 0x1.8p-1f);   // grid 2^-24: what is left of hi lies below it
+              rem = __fadd_rn(rem, lo);
+              dg[3][k4] = oz_digit(rem, 0x1.8p-9f);   // grid 2^-32
+              dg[4][k4] = oz_digit(rem, 0x1.8p-17f);  // grid 2^-40
+              dg[5][k4] = oz_digit(rem, 0x1.8p-25f);  // grid 2^-48
+            }
+#pragma unroll
+            for (int i = 0; i < kOpDigits; i++) {
+              const __nv_bfloat162 lo2 = __floats2bfloat162_rn(dg[i][0], dg[i][1]);  // exact: 8-bit digits
+              const __nv_bfloat162 hi2 = __floats2bfloat162_rn(dg[i][2], dg[i][3]);
+              *reinterpret_cast<uint2*>(arow + i * kOpASlice + (kc >> 1) * kOpAKc + (kc & 1) * 8) =
+                  make_uint2(*reinterpret_cast<const uint32_t*>(&lo2), *reinterpret_cast<const uint32_t*>(&hi2));
+            }
           }
-#pragma unroll
-          for (int i = 0; i < kOpDigits; i++)
-            *reinterpret_cast<float4*>(arow + i * kOpASlice + kc * kOpAKc) =
-                make_float4(dg[i][0], dg[i][1], dg[i][2], dg[i][3]);
+          fence_async_smem();  // the A slices become visible to the tensor core
+          um_mbar_arrive(fa(q));
         }
-        fence_async_smem();  // the A slices become visible to the tensor core
-        um_mbar_arrive(fb(slot));
         um_mbar_arrive(xf(rs));
 #pragma unroll
         for (int k = 0; k < kOpHalf; k++) pv[k] = pn[k];
@@ -353,7 +387,7 @@ __global__ void __launch_bounds__(kOpThreads, 1)
     if (__any_sync(0xffffffffu, range_bad) && lane == 0 && status) atomicOr(status, kStatusRange);
   } else {
     // ---- read-back threads, one per band (tensor-memory lanes 32 (warp - 8) ..): per row T1 from the
-    // level accumulators and frames as float pairs, the float-float y-pass, and each plane's sums in FP64
+    // level sums and frames as float pairs, the float-float y-pass, and each plane's sums in FP64
     const int bl = tid - kOpDigitThreads;
     const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     int gr = 0;
@@ -370,51 +404,57 @@ __global__ void __launch_bounds__(kOpThreads, 1)
       bool ok = true;
       for (int iy = 0; iy < C; iy++, gr++) {
         const int rs = gr & (kOpRows - 1);
-        if (!wait(xf(rs), (uint32_t)((gr >> 2) & 1)) || !wait(rd(rs), (uint32_t)((gr >> 2) & 1))) {
+        if (!wait(xf(rs), (uint32_t)((gr / kOpRows) & 1)) || !wait(rd(rs), (uint32_t)((gr / kOpRows) & 1))) {
           ok = false;
           break;
         }
         tc05_fence_after();
         const uint32_t tcol = tlane + (uint32_t)(rs * kOpSlotCols);
-        const int e0 = sexp[(rs * 2 + 0) * kOpBands + bl], e1 = sexp[(rs * 2 + 1) * kOpBands + bl];
-        // T1[n] = G (2^e0 S0[n] + 2^e1 S1[n]), the half rows read one after the other; each scale applied
-        // in two power-of-two factors
-        float th[NP], tl[NP];  // half row 0, scaled, as float pairs
-        {
-          float d[32];  // d[8 g + n]: level accumulator g of state n
-          tmem_ld8x4(tcol, tcol + kOpN, tcol + 2 * kOpN, tcol + 3 * kOpN, d);
-          const float ga = G * oz_pow2(e0 >> 1), gb = oz_pow2(e0 - (e0 >> 1));
-#pragma unroll
-          for (int n = 0; n < NP; n++) {
-            float sh, c0, c1;
-            oz_two_sum(d[n], d[8 + n], sh, c0);
-            oz_two_sum(sh, d[16 + n], sh, c1);
-            th[n] = __fmul_rn(__fmul_rn(sh, ga), gb);
-            tl[n] = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn(c0, c1), d[24 + n]), ga), gb);
-          }
-        }
+        // T1[n] = G (2^e0 S0[n] + 2^e1 S1[n]) with S_h[n] = sum over levels 2..8 of column (L - 2) 8 + n,
+        // the half rows read one after the other; each scale applied in two power-of-two factors
+        float th[NP], tl[NP];
         ff t1[NP];
-        if (nhalf > 1) {
-          float d[32];
-          tmem_ld8x4(tcol + 4 * kOpN, tcol + 5 * kOpN, tcol + 6 * kOpN, tcol + 7 * kOpN, d);
-          const float ga = G * oz_pow2(e1 >> 1), gb = oz_pow2(e1 - (e1 >> 1));
+        for (int h = 0; h < nhalf; h++) {
+          float sh[NP], sl[NP];  // levels 2..4 as a float pair, then the smaller levels added to the low part
+          const uint32_t s0 = tcol + (uint32_t)(h * kOpN);
+          {
+            float v[32];  // levels 2..5
+            tmem_ld8x4(s0, s0 + 8, s0 + 16, s0 + 24, v);
+#pragma unroll
+            for (int n = 0; n < NP; n++) {
+              float c0, c1;
+              oz_two_sum(v[n], v[8 + n], sh[n], c0);   // levels 2 and 3 (exact integers)
+              oz_two_sum(sh[n], v[16 + n], sh[n], c1);  // level 4
+              sl[n] = __fadd_rn(__fadd_rn(c0, c1), v[24 + n]);
+            }
+          }
+          {
+            float v[32];  // levels 6..8 and the zero columns
+            tmem_ld8x4(s0 + 32, s0 + 40, s0 + 48, s0 + 56, v);
+#pragma unroll
+            for (int n = 0; n < NP; n++) sl[n] = __fadd_rn(sl[n], __fadd_rn(v[n], __fadd_rn(v[8 + n], v[16 + n])));
+          }
+          const int eh = sexp[(rs * 2 + h) * kOpBands + bl];
+          const float ga = G * oz_pow2(eh >> 1), gb = oz_pow2(eh - (eh >> 1));
 #pragma unroll
           for (int n = 0; n < NP; n++) {
-            float sh, c0, c1;
-            oz_two_sum(d[n], d[8 + n], sh, c0);
-            oz_two_sum(sh, d[16 + n], sh, c1);
-            const float h1 = __fmul_rn(__fmul_rn(sh, ga), gb);
-            const float l1 = __fmul_rn(__fmul_rn(__fadd_rn(__fadd_rn(c0, c1), d[24 + n]), ga), gb);
-            float hi, lo;
-            oz_two_sum(th[n], h1, hi, lo);
-            oz_two_sum(hi, __fadd_rn(lo, __fadd_rn(tl[n], l1)), t1[n].hi, t1[n].lo);  // the halves may cancel
+            const float hs = __fmul_rn(__fmul_rn(sh[n], ga), gb);
+            const float ls = __fmul_rn(__fmul_rn(sl[n], ga), gb);
+            if (h == 0) {
+              th[n] = hs;
+              tl[n] = ls;
+            } else {
+              float hi, lo;
+              oz_two_sum(th[n], hs, hi, lo);
+              th[n] = hi;
+              tl[n] = __fadd_rn(lo, __fadd_rn(tl[n], ls));
+            }
           }
-        } else {
-#pragma unroll
-          for (int n = 0; n < NP; n++) oz_two_sum(th[n], tl[n], t1[n].hi, t1[n].lo);
         }
         tc05_fence_before();
         um_mbar_arrive(ae(rs));  // the row slot's accumulators and frames may be refilled
+#pragma unroll
+        for (int n = 0; n < NP; n++) oz_two_sum(th[n], tl[n], t1[n].hi, t1[n].lo);  // the halves may cancel
         // y-pass (a4) as float-float dot steps
 #pragma unroll
         for (int ny = 0; ny < NP; ny++) {
@@ -453,7 +493,7 @@ static cudaError_t op_nu(const ProjectLaunch& p) {
   } else {
     const OpLayout L = op_layout(p.natoms, p.g.cube, p.numax);
     char* ws = static_cast<char*>(p.op);
-    float* btab = reinterpret_cast<float*>(ws + L.btab);
+    __nv_bfloat16* btab = reinterpret_cast<__nv_bfloat16*>(ws + L.btab);
     float* gpow = reinterpret_cast<float*>(ws + L.gpow);
     float2* tyff = reinterpret_cast<float2*>(ws + L.tyff);
     k_op_tables<NU><<<(unsigned)p.natoms, 128, 0, p.stream>>>(p.g, p.atoms, btab, gpow, tyff);
@@ -462,6 +502,10 @@ static cudaError_t op_nu(const ProjectLaunch& p) {
     auto kern = k_project_ozaki<NU>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OpSmem::bytes);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if (fa.maxThreadsPerBlock < kOpThreads) return cudaErrorLaunchOutOfResources;  // registers of the build
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
