@@ -442,7 +442,7 @@ int sho_server_reset_stats(sho_server* server);
  *             s = 8 for SHO_P_FP64 and 4 for SHO_P_FP32; larger problems return SHO_ERR_CAPACITY before
  *             anything is enqueued.
  *   set-up    the first call on a device looks up the array's device address once (the device must be
- *             current, which it is for that call); make that first call before any stream capture.
+ *             current, which it is for that call).
  *   sharing   all calls on a device share the array and it keeps the last call's contents; each call
  *             writes every scratch element before reading it, so nothing needs clearing.  Calls whose
  *             GPU work overlaps (different streams with no ordering between them) race on the array:
