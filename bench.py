@@ -166,8 +166,9 @@ def max_over_ranks(ws, value):
 def launches_per_step(api, psi, w, prec, expand_kernel="auto", project_kernel="auto"):
     """Kernels of this library that one project + expand step launches (mirrors the library's dispatch)."""
     if prec == "ff64":
-        oz = (expand_kernel in ("auto", "tcgen05") and w.numax <= 7 and w.cube <= 32 and w.cube % 2 == 0
-              and w.nbands % 2 == 0 and (not w.periodic or w.grid[0] >= w.cube + 32))
+        full = 4 * w.nbands >= 3 * 128 * ((w.nbands + 127) // 128)  # the automatic choice wants full tiles
+        oz = ((expand_kernel == "tcgen05" or (expand_kernel == "auto" and full)) and w.numax <= 7 and w.cube <= 32
+              and w.cube % 2 == 0 and w.nbands % 2 == 0 and (not w.periodic or w.grid[0] >= w.cube + 32))
         # projection: the digit tables, the tensor-core x-pass and the z-pass (or the float-float x/y-pass
         # and the z-pass); expansion: the float-pair z-pass (with the tables), then the digit tables and
         # the tensor-core x-pass (or the block gather)

@@ -139,13 +139,14 @@ int sho_set_support_radius(sho_handle* handle, double rprj);
  * memory across the atoms, one M=128 N=32 MMA per row and atom; SHO_KERNEL_MMA_SYNC takes the warp-level
  * MMA kernel (tiles of 8 rows x 32 points x 32 bands, accumulators in registers).  Both add the same
  * products in the same atom order; the FP32 sums of the tensor cores may round differently.
- * For SHO_P_FF64 expansions SHO_KERNEL_AUTO (default) and SHO_KERNEL_TCGEN05 take the x-pass to the tensor
- * cores by exact digit slicing (Ozaki scheme: six 8-bit digits of T1 and of the x functions on fixed
+ * For SHO_P_FF64 expansions SHO_KERNEL_TCGEN05, and SHO_KERNEL_AUTO (default) when the band count fills
+ * its 128-band tiles at least three quarters (real bands; a complex band counts two), take the x-pass to
+ * the tensor cores by exact digit slicing (Ozaki scheme: six 8-bit digits of T1 and of the x functions on fixed
  * power-of-two frames, TF32 MMAs whose leading level sums are exact integers; a persistent kernel with
  * list, digit, MMA and read-back warps) where it applies -- numax <= 7, cube <= 32 and even, an even band
  * count, a periodic grid at least cube + 32 points wide along x, at most 204 / (numax + 1) atoms per z
- * plane, no spherical support, real data, device checks off; SHO_KERNEL_MMA_SYNC, and every other case,
- * takes the float-float CUDA-core block gather.  The tensor-core form's error is about 2^-44 of each
+ * plane, no spherical support, device checks off; real or Bloch data); SHO_KERNEL_MMA_SYNC, and every
+ * other case, takes the float-float CUDA-core block gather.  The tensor-core form's error is about 2^-44 of each
  * point's frame (a power of two above the largest single-atom contribution there), against 2^-48 of the
  * point's own terms for the float-float kernel; both are far inside the FP64 tolerance of 1e-12.
  * Other calls ignore the setting.  SHO_ERR_ARG for an unknown value. */

@@ -647,10 +647,14 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   float2* tyff = txff + (size_t)p.natoms * p.g.cube * NPX;
   cudaError_t e = launch_expand_zpass_ff(p, txff, tyff);
   if (e != cudaSuccess) return e;
-  // the x-pass on the tensor cores by exact digit slicing where it applies (kernel choice automatic or
-  // tcgen05); the float-float block gather when chosen (kernel choice 1), for Bloch data, under device
-  // checks, and where the tensor-core form does not apply
-  if (p.kernel != 1 && !p.bloch && !p.chk.flag && ozaki_expand_ok(p)) return launch_expand_ozaki(p, tyff);
+  // the x-pass on the tensor cores by exact digit slicing where it applies (kernel choice tcgen05; or
+  // automatic when its 128-band tiles are at least three quarters full, since a tile costs the same
+  // whatever its band count); the float-float block gather when chosen (kernel choice 1), under device
+  // checks, and in the other cases
+  const int obt = (p.g.nbands + 127) / 128;
+  const bool full_tiles = 4 * p.g.nbands >= 3 * 128 * obt;
+  if ((p.kernel == 2 || (p.kernel == 0 && full_tiles)) && !p.chk.flag && ozaki_expand_ok(p))
+    return launch_expand_ozaki(p, tyff);
   auto kern = p.chk.flag ? k_expand_blk_ff<NU, true> : k_expand_blk_ff<NU, false>;
   if constexpr (NU <= kBlochFfMaxNumax) {
     if (p.bloch) kern = k_expand_blk_ff<NU, false, true>;

@@ -169,13 +169,17 @@ __global__ void __launch_bounds__(128) k_oz_tables(int natoms, int cube, int nba
 }
 
 // ------------------------------------------------------------------------------------- expansion
-template <int NU>
+// BLOCH: complex coefficients and psi of a Bloch wave (Sec. 2.5), (re, im) pairs as two real bands in
+// neighbouring lanes; each (atom, tile) T1 turns by the phase of the translation of the tile's points
+// (one run: the tile segment does not cross the cell boundary) before its digit slicing, and the frames
+// bound the turned values (the sum of the pair's bounds).
+template <int NU, bool BLOCH = false>
 __global__ void __launch_bounds__(kOzAllThreads, 2)
     k_expand_ozaki(GridDev g, const AtomDev* __restrict__ atoms, const int* __restrict__ plane_ptr,
                    const int* __restrict__ plane_atoms, int max_plane, const float2* __restrict__ tyff,
                    const float2* __restrict__ t2, const float* __restrict__ dtab, const float* __restrict__ gpow,
                    const float* __restrict__ tmax, double* __restrict__ psi, int* __restrict__ status,
-                   long long wait_cycles, int stop_stage) {
+                   long long wait_cycles, int stop_stage, const BlochPh* __restrict__ bph) {
   using BS = Basis<NU>;
   using SM = OzSmem<NU>;
   constexpr int NP = SM::NP, P = SM::P;
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(kOzAllThreads, 2)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
           const int bi = lane + 32 * c;
-          if (bi < nb) xb[c] = fmaxf(xb[c], tm[bi] * ga);
+          if (bi < nb) xb[c] = fmaxf(xb[c], (BLOCH ? tm[bi] + tm[bi ^ 1] : tm[bi]) * ga);
         }
       }
       int* ef = rec_ef(u);
@@ -450,7 +454,12 @@ __global__ void __launch_bounds__(kOzAllThreads, 2)
       bool ok = true;
       for (int li = 0; li < nl; li++) {
         const int ga = gi + li, slot = ga & 1;
-        if (ga >= 2 && !wait(cb(slot), (uint32_t)(((ga - 2) >> 1) & 1))) { ok = false; break; }
+        // the whole warp leaves together (the Bloch turn below exchanges values between lanes)
+        const bool free_slot = ga < 2 || wait(cb(slot), (uint32_t)(((ga - 2) >> 1) & 1));
+        if (!__all_sync(0xffffffffu, free_slot)) {
+          ok = false;
+          break;
+        }
         float ys[NP], yc[NP];
 #pragma unroll
         for (int n = 0; n < NP; n++) ys[n] = yc[n] = 0.0f;
@@ -465,6 +474,20 @@ __global__ void __launch_bounds__(kOzAllThreads, 2)
           }
         }
         if (li + 1 < nl) load_t2(li + 1);  // in flight during the digits and the next wait
+        if constexpr (BLOCH) {
+          // T1 turned by the phase of the translation of the tile's points (every lane of the warp)
+          const int4 r = sl[li];
+          const BlochPh& bp = bph[r.x];
+          const float4 ph = bp.ph[(max(r.z, 0) >= bp.w[0] ? 1 : 0) + (r.y >= bp.w[1] ? 2 : 0) + (r.w >= bp.w[2] ? 4 : 0)];
+          if (!ff_is_one(ph)) {
+#pragma unroll
+            for (int n = 0; n < NP; n++) {
+              const ff v = ff_rotate(ff_norm(ys[n], yc[n]), ph, lane);
+              ys[n] = v.hi;
+              yc[n] = v.lo;
+            }
+          }
+        }
         // six digit slices of T1 G_a / F, written as the A operands (two chunks of four states)
         const int kk = ge[li] - eF;  // G_a / F = 2^kk
         const float sa = (kk < -126 || !bvalid) ? 0.0f : oz_pow2(min(kk, 127));
@@ -635,7 +658,7 @@ static cudaError_t ozaki_nu(const ExpandLaunch& p, const void* tyff) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = OzSmem<NU>::bytes(p.max_plane);
-    auto kern = k_expand_ozaki<NU>;
+    auto kern = p.bloch ? k_expand_ozaki<NU, true> : k_expand_ozaki<NU, false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // persistent: two CTAs per SM walk the tiles (grid row x 32 points x 128 bands) in a fixed stride
@@ -649,7 +672,7 @@ static cudaError_t ozaki_nu(const ExpandLaunch& p, const void* tyff) {
     kern<<<nblk, kOzAllThreads, smem, p.stream>>>(
         p.g, p.atoms, p.plane_ptr, p.plane_atoms, p.max_plane, static_cast<const float2*>(tyff),
         static_cast<const float2*>(p.t2),
-        dtab, gpow, tmax, static_cast<double*>(p.psi), p.status, p.wait_cycles, p.stop_stage);
+        dtab, gpow, tmax, static_cast<double*>(p.psi), p.status, p.wait_cycles, p.stop_stage, p.bloch);
     return cudaGetLastError();
   }
 }

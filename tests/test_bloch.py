@@ -165,3 +165,32 @@ def test_bloch_rejects_open_grid():
                                    sig.ctypes.data_as(N._DP), 1, 16, N.PRECS["fp64"], ctypes.c_void_p(out.data_ptr()),
                                    None)
     assert st != 0
+
+
+def test_bloch_ff64_tensor_core_expansion():
+    """On a grid at least cube + 32 points wide the FF64 Bloch expansion can take the tensor-core x-pass
+    (T1 turned by its tile's phase before the digit slicing): against the oracle with cubes that wrap on
+    every axis, and against the float-float block gather (close, not bit for bit); with 20 complex bands
+    (40 real, a third of a 128-band tile) the automatic choice is the block gather."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, cube, numax, nbands = (72, 40, 36), 0.2, 32, 5, 20
+    rng, pos, sig, psi = _case(945, grid, h, 5, nbands)
+    k = np.array([0.7, -1.2, 0.45])
+    coef = rng.standard_normal((len(pos), oracle.nstates(numax), nbands)) + 1j * rng.standard_normal(
+        (len(pos), oracle.nstates(numax), nbands))
+    outs = {}
+    for engine in ("tcgen05", "mma_sync", "auto"):
+        hd = api.Handle(0)
+        hd.set_expand_kernel(engine)
+        out = torch.zeros((grid[2], grid[1], grid[0], nbands), dtype=torch.complex128, device="cuda")
+        api.add_bloch(out, torch.from_numpy(coef).cuda(), k, pos, sig, numax, cube, h, handle=hd, prec="ff64")
+        hd.sync()
+        outs[engine] = out.cpu().numpy()
+        hd.close()
+    ref = oracle.add_bloch(grid, h, k, np.zeros_like(psi), pos, sig, numax, cube, coef)
+    for engine, got in outs.items():
+        assert rel_norm(got.view(np.float64), ref.view(np.float64)) <= TOL_FP64, engine
+    assert not np.array_equal(outs["tcgen05"], outs["mma_sync"])  # the tensor-core path ran
+    assert np.array_equal(outs["auto"], outs["mma_sync"])

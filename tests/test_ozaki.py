@@ -58,8 +58,9 @@ def _t(x):
 
 
 def _expand_both(grid, h, periodic, pos, sig, psi, c, numax, cube):
-    """FF64 expansion with the tensor-core x-pass (chosen, and the default where it applies) and with the
-    float-float kernel; the default and the chosen tensor-core engine agree bit for bit."""
+    """FF64 expansion with the tensor-core x-pass (chosen) and with the float-float kernel; the default
+    engine is the tensor-core one when the bands fill its 128-band tiles at least three quarters, the
+    float-float one otherwise, bit for bit."""
     from paper_1905_00480_gb300 import api
     outs = {}
     for kernel in ("tcgen05", "auto", "mma_sync"):
@@ -70,7 +71,9 @@ def _expand_both(grid, h, periodic, pos, sig, psi, c, numax, cube):
         hd.sync()
         outs[kernel] = out.cpu().numpy()
         hd.close()
-    assert np.array_equal(outs["tcgen05"], outs["auto"])
+    nb = psi.shape[3]
+    full = 4 * nb >= 3 * 128 * ((nb + 127) // 128)
+    assert np.array_equal(outs["auto"], outs["tcgen05" if full else "mma_sync"])
     return outs["tcgen05"], outs["mma_sync"]
 
 
