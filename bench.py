@@ -41,8 +41,8 @@ def _peaks():
 # DRAM bytes (read + write) of one call, summed over its kernels' launches, from one ncu capture of the
 # default FF64 bench step (96^3 / 64 atoms / 128 bands), by (call, expansion engine); valid only while
 # those kernels are unchanged (None otherwise).
-NCU_TRAFFIC = {("k_project", e): 1983526400 + 43296000 + 44086016 for e in ("auto", "mma_sync")}  # x/y + z-pass
-NCU_TRAFFIC.update({("k_expand", e): 3759104 + 44259328 + 952110336 + 841459712 for e in ("auto", "tcgen05")})
+NCU_TRAFFIC = {("k_project", e): 1985944576 + 43182592 + 44085248 for e in ("auto", "mma_sync")}  # x/y + z-pass
+NCU_TRAFFIC.update({("k_expand", e): 3760128 + 44259584 + 951985408 + 841280512 for e in ("auto", "tcgen05")})
 
 # FP64 FMA peak of the GB300 measured by a DFMA throughput loop (152 SMs x 2 DFMA/clk/SM x 2 flop,
 # 1.19 TFLOP/s at the clocks seen under load); the kernels of the FP64 form are bound by this pipe.
