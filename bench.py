@@ -621,7 +621,23 @@ def same_gpu_baselines(w, pos, sig, psi, cin, alg, api, handle, stream):
                                  "ms_per_step": round(msf, 4), "project_rel_diff_vs_fp64_form": err_b,
                                  "note": f"same {B} complex bands and k: the FP64-accurate form (float-float passes "
                                          "over the (re, im) pairs, phases turned per run)"}
-    del zc, cz, oz, hz, ozf, hzf
+    zc32, cz32 = zc.to(torch.complex64), cz.to(torch.complex64)
+    oz32 = torch.empty_like(cz32)
+    hz32 = torch.zeros_like(zc32)
+
+    def bloch_fp32_step():
+        api.project_bloch(zc32, kvec, pos, sig, w.numax, w.cube, w.h, out=oz32, handle=handle, stream=stream,
+                          prec="fp32")
+        api.add_bloch(hz32, cz32, kvec, pos, sig, w.numax, w.cube, w.h, handle=handle, stream=stream, prec="fp32")
+
+    ms32b = _time_steps(stream, bloch_fp32_step, warmup=2, steps=10)
+    err_32 = float(torch.linalg.vector_norm(torch.view_as_real(oz32.to(torch.complex128) - oz))
+                   / torch.linalg.vector_norm(torch.view_as_real(oz)))
+    out["bloch_complex_fp32"] = {"value": round(bytes_b // 2 / (ms32b * 1e-3) / 1e9, 3), "unit": "GB/s",
+                                 "ms_per_step": round(ms32b, 4), "project_rel_diff_vs_fp64_form": err_32,
+                                 "note": f"same {B} bands and k as complex64: the FP32 CUDA-core kernels over the "
+                                         "(re, im) pairs, phases turned per run in FP32"}
+    del zc, cz, oz, hz, ozf, hzf, zc32, cz32, oz32, hz32
     torch.cuda.empty_cache()
     return out
 

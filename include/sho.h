@@ -289,14 +289,19 @@ int sho_apply_nonlocal(sho_handle* handle, const sho_grid* grid, const void* psi
  * axis, constant on the (at most two) runs of a cube on either side of the cell boundary.
  *   grid   periodic (SHO_ERR_ARG otherwise); sho_add_bloch with SHO_P_FP64 needs n[0] <= 448
  *   kvec   host double[3], the Bloch vector in inverse length units
- *   psi    device complex double [n[2]][n[1]][n[0]][nbands] as (re, im) pairs
+ *   psi    device complex [n[2]][n[1]][n[0]][nbands] as (re, im) pairs: double for SHO_P_FP64 and
+ *          SHO_P_FF64, float for SHO_P_FP32
  *   prec   SHO_P_FP64: complex 1D tables (phase included), complex FMAs on the FP64 pipe;
  *          SHO_P_FF64: the real FP64-accurate kernels (float-float x- and y-passes, FP64 z-pass) over
  *          the (re, im) pairs as 2 nbands real bands, each x-pass sum turned by its run's phase in
  *          float pairs -- same accuracy class and input range as SHO_P_FF64 of sho_project (an input
  *          outside it latches SHO_ERR_DEVICE), and the same workspace for 2 nbands bands;
+ *          SHO_P_FP32: the real FP32 CUDA-core kernels (streaming projection, block gather) over the
+ *          (re, im) pairs as 2 nbands real bands, each x-pass sum (projection) or y-pass result
+ *          (expansion) turned by its run's phase in FP32; psi 16-byte aligned and nbands even
+ *          (SHO_ERR_ARG otherwise); the FP32 accuracy class of sho_project with SHO_P_FP32;
  *          any other value: SHO_ERR_DTYPE
- *   coeff  device complex double [natoms][sho_nstates(numax)][nbands] as (re, im) pairs
+ *   coeff  device complex [natoms][sho_nstates(numax)][nbands] as (re, im) pairs, of psi's type
  * numax <= 7 (SHO_ERR_NUMAX).  Deterministic (fixed summation order, no atomics).
  */
 int sho_project_bloch(sho_handle* handle, const sho_grid* grid, const double* kvec, const void* psi, int nbands,

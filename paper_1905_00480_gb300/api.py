@@ -171,23 +171,26 @@ def _grid_complex(psi: torch.Tensor, h: float):
     return g
 
 
-def _check_complex(t: torch.Tensor, what: str, dims: int):
-    if not t.is_cuda or not t.is_contiguous() or t.dtype != torch.complex128 or t.dim() != dims:
-        raise ValueError(f"{what} must be a contiguous CUDA complex128 tensor with {dims} dimensions")
+def _check_complex(t: torch.Tensor, what: str, dims: int, prec: str = "fp64"):
+    want = torch.complex64 if prec == "fp32" else torch.complex128
+    if not t.is_cuda or not t.is_contiguous() or t.dtype != want or t.dim() != dims:
+        raise ValueError(f"{what} must be a contiguous CUDA {str(want)[6:]} tensor with {dims} dimensions "
+                         f"for prec {prec!r}")
 
 
 def project_bloch(psi: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h: float, out: torch.Tensor = None,
                   handle: Handle = None, stream=None, prec: str = "fp64") -> torch.Tensor:
     """sho_project_bloch: complex Bloch psi [Nz][Ny][Nx][B] (periodic grid) -> complex [A][N][B].
-    prec "fp64" (complex FMAs on the FP64 pipe) or "ff64" (float-float passes, FP64-accurate)."""
-    _check_complex(psi, "psi", 4)
+    prec "fp64" (complex FMAs on the FP64 pipe) or "ff64" (float-float passes, FP64-accurate), both on
+    complex128 data, or "fp32" (the FP32 CUDA-core kernels) on complex64 data."""
+    _check_complex(psi, "psi", 4, prec)
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
     k = _host_f64(kvec).reshape(3)
     A, B = pos_h.shape[0], psi.shape[3]
     if out is None:
-        out = torch.empty((A, nstates(numax), B), dtype=torch.complex128, device=psi.device)
-    _check_complex(out, "out", 3)
+        out = torch.empty((A, nstates(numax), B), dtype=psi.dtype, device=psi.device)
+    _check_complex(out, "out", 3, prec)
     hd = handle or default_handle(psi.device.index or 0)
     g = _grid_complex(psi, h)
     st = N.lib().sho_project_bloch(hd.ptr, ctypes.byref(g), _dp(k), ctypes.c_void_p(psi.data_ptr()), B, A,
@@ -200,9 +203,9 @@ def project_bloch(psi: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h:
 def add_bloch(psi: torch.Tensor, coeff: torch.Tensor, kvec, pos, sigma, numax: int, cube: int, h: float,
               handle: Handle = None, stream=None, prec: str = "fp64") -> torch.Tensor:
     """sho_add_bloch (in place): psi += sum_a sum_k c Psi_k e^{-i k.T} for complex Bloch psi.
-    prec "fp64" or "ff64" as for project_bloch."""
-    _check_complex(psi, "psi", 4)
-    _check_complex(coeff, "coeff", 3)
+    prec "fp64", "ff64" or "fp32" as for project_bloch."""
+    _check_complex(psi, "psi", 4, prec)
+    _check_complex(coeff, "coeff", 3, prec)
     pos_h = _host_f64(pos, 3)
     sig_h = _host_f64(sigma).reshape(-1)
     k = _host_f64(kvec).reshape(3)

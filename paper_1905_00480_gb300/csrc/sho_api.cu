@@ -719,8 +719,8 @@ static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, i
   if (!h) return SHO_ERR_ARG;
   SHO_TRY(check_common(grid, nbands, natoms, pos, sigma, numax, cube, kTcMaxNumax));
   if (!grid->periodic || !kvec) return SHO_ERR_ARG;
-  if (prec != SHO_P_FP64 && prec != SHO_P_FF64) return SHO_ERR_DTYPE;
-  if (h->rprj > 0.0) return SHO_ERR_DTYPE;  // spherical support: FP64 / FP64-accurate real forms only
+  if (prec != SHO_P_FP64 && prec != SHO_P_FF64 && prec != SHO_P_FP32) return SHO_ERR_DTYPE;
+  if (h->rprj > 0.0) return SHO_ERR_DTYPE;  // spherical support: the real forms only
   for (int d = 0; d < 3; d++)
     if (!std::isfinite(kvec[d])) return SHO_ERR_ARG;
   if (op == 1 && prec == SHO_P_FP64 && grid->n[0] > kBlochMaxNx) return SHO_ERR_ARG;
@@ -728,14 +728,17 @@ static int bloch_call(sho_handle* h, const sho_grid* grid, const double* kvec, i
   SHO_TRY(check_spacing(h, grid, natoms, sigma, numax));
   if (natoms == 0 || nbands == 0) return SHO_OK;
   if (!src || !dst) return SHO_ERR_ARG;
-  if (prec == SHO_P_FF64) {
-    // the real FP64-accurate kernels over the (re, im) pairs as 2 nbands real bands, with the phases
+  // FP32: the streaming CUDA-core kernels, which want 16-byte aligned psi rows
+  if (prec == SHO_P_FP32 && !fp32_stream_ok(op == 0 ? src : dst, SHO_F32, 2 * nbands)) return SHO_ERR_ARG;
+  if (prec != SHO_P_FP64) {
+    // the real FP64-accurate or FP32 kernels over the (re, im) pairs as 2 nbands real bands, with the phases
     const BlochArg bl{{kvec[0], kvec[1], kvec[2]}, op == 0 ? 1.0 : -1.0};
+    const sho_dtype dt = prec == SHO_P_FF64 ? SHO_F64 : SHO_F32;
     if (op == 0)
-      return project_impl(h, grid, src, SHO_F64, 2 * nbands, natoms, pos, sigma, numax, cube, SHO_P_FF64, dst,
-                          SHO_F64, stream, nullptr, nullptr, &bl);
-    return add_impl(h, grid, 1.0, 0, src, SHO_F64, 2 * nbands, natoms, pos, sigma, numax, cube, SHO_P_FF64, dst,
-                    SHO_F64, stream, nullptr, &bl);
+      return project_impl(h, grid, src, dt, 2 * nbands, natoms, pos, sigma, numax, cube, prec, dst, dt, stream,
+                          nullptr, nullptr, &bl);
+    return add_impl(h, grid, 1.0, 0, src, dt, 2 * nbands, natoms, pos, sigma, numax, cube, prec, dst, dt, stream,
+                    nullptr, &bl);
   }
   DeviceGuard guard(h->device);
   if (!guard.ok) return SHO_ERR_CUDA;
@@ -815,8 +818,9 @@ int sho_project_path(const sho_grid* grid, const void* psi, sho_dtype psi_dtype,
 // t2_out != nullptr (fused non-local action): where the path has a separate z-pass (FP64-accurate form,
 // plane sweep) stop after the per-plane y-pass sums, leave them in t2_out ([A][cube][P][B], compute type)
 // and set *at_t2; other paths write coeff as usual.
-// bloch != nullptr: the FP64-accurate Bloch projection (complex psi and coeff as 2 real bands per band,
-// nbands counting both), its per-atom phases uploaded behind the per-plane sums.
+// bloch != nullptr: the FP64-accurate or FP32 Bloch projection (complex psi and coeff as 2 real bands per
+// band, nbands counting both), its per-atom phases computed into the workspace (behind the per-plane sums
+// of the FP64-accurate form).
 static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sho_dtype psi_dtype, int nbands,
                         int natoms, const double* pos, const double* sigma, int numax, int cube, sho_prec prec,
                         void* coeff, sho_dtype coeff_dtype, void* stream, void* t2_out, bool* at_t2,
@@ -834,7 +838,7 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   if (!guard.ok) return SHO_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<AtomDev> at = make_atoms(grid, natoms, pos, sigma, cube);
-  if (coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec)) {
+  if (!bloch && coeff_dtype == SHO_F32 && plane_ok(grid, psi, psi_dtype, nbands, numax, cube, prec)) {
     if (t2_out && at_t2) *at_t2 = true;
     return project_planes(h, grid, at, psi, psi_dtype, nbands, numax, cube, prec, static_cast<float*>(coeff), s,
                           static_cast<float*>(t2_out));
@@ -842,11 +846,12 @@ static int project_impl(sho_handle* h, const sho_grid* grid, const void* psi, sh
   SHO_TRY(begin_call(h, s));
   const bool ff_t2 = prec == SHO_P_FF64 && t2_out;
   // FP64-accurate form: per-plane sums (unless the caller provides them), Bloch phases, tensor-core tables
+  const bool ff = prec == SHO_P_FF64;
   Carve fcv;
-  if (!ff_t2) fcv.take(ff_t2_bytes(natoms, cube, numax, nbands));
+  if (ff && !ff_t2) fcv.take(ff_t2_bytes(natoms, cube, numax, nbands));
   const size_t o_bloch = bloch ? fcv.take((size_t)natoms * sizeof(BlochPh)) : 0;
-  const size_t o_op = fcv.take(op_layout(natoms, cube, numax).total);
-  if (prec == SHO_P_FF64) SHO_TRY(ensure_workspace(h, fcv.off));
+  const size_t o_op = ff ? fcv.take(op_layout(natoms, cube, numax).total) : 0;
+  if (ff || bloch) SHO_TRY(ensure_workspace(h, fcv.off));
   const uint64_t key = geometry_key(grid, at, cube);
   if (h->geo[0].key != key) {
     std::vector<int> order = spatial_order(grid, at);

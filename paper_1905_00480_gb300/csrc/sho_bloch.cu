@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kWarp) k_bloch_rows(GridDev g, const AtomDev* 
   }
 }
 
-// Phases of the FP64-accurate Bloch kernels (BlochPh), one thread per atom: per axis the cube point w where
+// Phases of the real-kernel Bloch forms (BlochPh; FP64-accurate and FP32), one thread per atom: per axis the cube point w where
 // floor((o + i) / n) steps from f0 to f0 + 1 (the cube crosses the cell boundary), and the eight
 // e^{sgn i k.T} of the translations T_d = (f0_d + b_d) n_d h, split into float pairs.
 __global__ void k_bloch_phases(GridDev g, const AtomDev* __restrict__ atoms, int natoms, double3 kv, double sgn,

@@ -616,7 +616,7 @@ static cudaError_t ff_project_nu(const ProjectLaunch& p) {
   } else {
     const size_t smem = FfProjectSmem<NU>::bytes(p.g.cube);
     auto kern = p.chk.flag ? k_project_ff<NU, true> : k_project_ff<NU, false>;
-    if constexpr (NU <= kBlochFfMaxNumax) {
+    if constexpr (NU <= kBlochRealMaxNumax) {
       if (p.bloch) kern = k_project_ff<NU, false, true>;
     } else if (p.bloch) {
       return cudaErrorInvalidValue;
@@ -656,7 +656,7 @@ static cudaError_t ff_expand_nu(const ExpandLaunch& p) {
   if ((p.kernel == 2 || (p.kernel == 0 && full_tiles)) && !p.chk.flag && ozaki_expand_ok(p))
     return launch_expand_ozaki(p, tyff);
   auto kern = p.chk.flag ? k_expand_blk_ff<NU, true> : k_expand_blk_ff<NU, false>;
-  if constexpr (NU <= kBlochFfMaxNumax) {
+  if constexpr (NU <= kBlochRealMaxNumax) {
     if (p.bloch) kern = k_expand_blk_ff<NU, false, true>;
   } else if (p.bloch) {
     return cudaErrorInvalidValue;

@@ -70,11 +70,22 @@ struct PipeSmem {
   }
 };
 
-template <int NU, typename TP, int MODE>
+// v times the unit complex number ph (leading floats of its float pairs) for complex data held by lane
+// pairs, the real part in the even lane and the imaginary part in the odd one (every lane calls it).
+__device__ __forceinline__ float f32_rotate(float v, const float4 ph, int lane) {
+  const float u = __shfl_xor_sync(0xffffffffu, v, 1);
+  return fmaf(v, ph.x, ((lane & 1) ? u : -u) * ph.z);
+}
+
+// BLOCH (SIMT form, float psi): complex psi of a Bloch wave (Sec. 2.5), its (re, im) pairs as two real
+// bands in neighbouring lanes; the x-pass sum turns by the x translation's phase where the cube row
+// crosses the cell boundary, and each row's x-pass result by the phase of its translation, so that the
+// y- and z-passes stay real (as in the FP64-accurate form).
+template <int NU, typename TP, int MODE, bool BLOCH = false>
 __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __restrict__ psi,
                                                         const AtomDev* __restrict__ atoms,
                                                         const int* __restrict__ order, int zsplit,
-                                                        float* __restrict__ coeff) {
+                                                        float* __restrict__ coeff, const BlochPh* __restrict__ bph) {
   using BS = Basis<NU>;
   using SM = PipeSmem<NU, TP, MODE>;
   constexpr int NP = BS::NP, P = BS::P, N = BS::N, NPX = SM::NPX;
@@ -200,17 +211,36 @@ __global__ void __launch_bounds__(kWarp) k_project_pipe(GridDev g, const TP* __r
       if constexpr (!TC) {
 #pragma unroll
         for (int n = 0; n < NP; n++) t1[n] = 0.0f;
-        for (int ix = 0; ix < C; ix++) {
-          const float v = to_real(st[ix * RSE + lane], 0.0f);
-          const float4* f4 = reinterpret_cast<const float4*>(phx + ix * NPX);
+        auto xpass = [&](int x0, int x1) {
+          for (int ix = x0; ix < x1; ix++) {
+            const float v = to_real(st[ix * RSE + lane], 0.0f);
+            const float4* f4 = reinterpret_cast<const float4*>(phx + ix * NPX);
 #pragma unroll
-          for (int q = 0; q < NPX / 4; q++) {
-            const float4 f = f4[q];
-            if (4 * q + 0 < NP) t1[4 * q + 0] = fmaf(v, f.x, t1[4 * q + 0]);
-            if (4 * q + 1 < NP) t1[4 * q + 1] = fmaf(v, f.y, t1[4 * q + 1]);
-            if (4 * q + 2 < NP) t1[4 * q + 2] = fmaf(v, f.z, t1[4 * q + 2]);
-            if (4 * q + 3 < NP) t1[4 * q + 3] = fmaf(v, f.w, t1[4 * q + 3]);
+            for (int q = 0; q < NPX / 4; q++) {
+              const float4 f = f4[q];
+              if (4 * q + 0 < NP) t1[4 * q + 0] = fmaf(v, f.x, t1[4 * q + 0]);
+              if (4 * q + 1 < NP) t1[4 * q + 1] = fmaf(v, f.y, t1[4 * q + 1]);
+              if (4 * q + 2 < NP) t1[4 * q + 2] = fmaf(v, f.z, t1[4 * q + 2]);
+              if (4 * q + 3 < NP) t1[4 * q + 3] = fmaf(v, f.w, t1[4 * q + 3]);
+            }
           }
+        };
+        if constexpr (BLOCH) {
+          // points before the crossing w, the sum turned by ph(before) / ph(after), the points after it,
+          // and the row's sum turned by the phase of its last run (y and z bits of this row and plane)
+          const BlochPh& bp = bph[a];
+          const int wx = min(bp.w[0], C);
+          xpass(0, wx);
+          if (wx < C) {
+#pragma unroll
+            for (int n = 0; n < NP; n++) t1[n] = f32_rotate(t1[n], bp.xstep, lane);
+          }
+          xpass(wx, C);
+          const float4 ph = bp.ph[(wx < C ? 1 : 0) + (iy >= bp.w[1] ? 2 : 0) + (iz >= bp.w[2] ? 4 : 0)];
+#pragma unroll
+          for (int n = 0; n < NP; n++) t1[n] = f32_rotate(t1[n], ph, lane);
+        } else {
+          xpass(0, C);
         }
       } else {
         float d[2][4], dl[2][4];
@@ -368,7 +398,11 @@ __global__ void k_expand_xfrag(int cube, const float* __restrict__ txm, uint32_t
 
 // Tensor forms: at most 128 registers, two blocks of 8 warps per SM; the CUDA-core form on FP32 psi at
 // most 64 (four blocks); on BF16 psi the compiler's choice (about 80 registers, three blocks).
-template <int NU, typename TP, int MODE>
+// BLOCH (SIMT form, float psi): complex coefficients and psi of a Bloch wave, (re, im) pairs as two real
+// bands in neighbouring lanes; each (atom, row) y-pass result turns by the phase of the translation of
+// each tile point it updates (the point's cube index before or after the crossing w), so that the z-, y-
+// and x-passes stay real.
+template <int NU, typename TP, int MODE, bool BLOCH = false>
 __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeof(TP) == 4 ? 4 : 0) k_expand_blk(GridDev g, const AtomDev* __restrict__ atoms,
                                                                     const int* __restrict__ plane_ptr,
                                                                     const int* __restrict__ plane_atoms,
@@ -376,7 +410,8 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
                                                                     const float* __restrict__ txm,
                                                                     const uint32_t* __restrict__ xf,
                                                                     const float* __restrict__ t2,
-                                                                    TP* __restrict__ psi) {
+                                                                    TP* __restrict__ psi,
+                                                                    const BlochPh* __restrict__ bph) {
   using BS = Basis<NU>;
   using SM = BlkSmem<NU, MODE>;
   constexpr bool TC = MODE != kSimt;
@@ -557,6 +592,21 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
           }
         const int dx = r.z;  // cube index of tile point x is dx + x (mod Nx when periodic)
         if constexpr (!TC) {
+          // Bloch data: the y-pass result turned by the phases of both runs of the cube row (before and
+          // after the crossing w); each point takes the one of its cube index
+          float t1b[BLOCH ? NP : 1];
+          int wx = C;
+          if constexpr (BLOCH) {
+            const BlochPh& bp = bph[r.x];
+            wx = bp.w[0];
+            const int yz = (iy >= bp.w[1] ? 2 : 0) + (r.w >= bp.w[2] ? 4 : 0);
+            const float4 ph0 = bp.ph[yz], ph1 = bp.ph[1 + yz];
+#pragma unroll
+            for (int n = 0; n < NP; n++) {
+              t1b[n] = f32_rotate(t1[n], ph1, lane);
+              t1[n] = f32_rotate(t1[n], ph0, lane);
+            }
+          }
 #pragma unroll
           for (int x = 0; x < kXSeg; x++) {
             int ix = dx + x;
@@ -564,13 +614,21 @@ __global__ void __launch_bounds__(kRowsPerBlk * kWarp, MODE != kSimt ? 2 : sizeo
             if (ix >= 0 && ix < C) {
               float s = accr[x];
               const float4* f4 = reinterpret_cast<const float4*>(txs + ix * NPX);
+              float tt[NP];
+#pragma unroll
+              for (int n = 0; n < NP; n++) {
+                if constexpr (BLOCH)
+                  tt[n] = ix >= wx ? t1b[n] : t1[n];
+                else
+                  tt[n] = t1[n];
+              }
 #pragma unroll
               for (int q = 0; q < NPX / 4; q++) {
                 const float4 f = f4[q];
-                if (4 * q + 0 < NP) s = fmaf(t1[4 * q + 0], f.x, s);
-                if (4 * q + 1 < NP) s = fmaf(t1[4 * q + 1], f.y, s);
-                if (4 * q + 2 < NP) s = fmaf(t1[4 * q + 2], f.z, s);
-                if (4 * q + 3 < NP) s = fmaf(t1[4 * q + 3], f.w, s);
+                if (4 * q + 0 < NP) s = fmaf(tt[4 * q + 0], f.x, s);
+                if (4 * q + 1 < NP) s = fmaf(tt[4 * q + 1], f.y, s);
+                if (4 * q + 2 < NP) s = fmaf(tt[4 * q + 2], f.z, s);
+                if (4 * q + 3 < NP) s = fmaf(tt[4 * q + 3], f.w, s);
               }
               accr[x] = s;
             }
@@ -655,6 +713,11 @@ template <int NU, typename TP, int MODE>
 static cudaError_t pipe_project_t(const ProjectLaunch& p) {
   const size_t smem = PipeSmem<NU, TP, MODE>::bytes(p.g.cube);
   auto kern = k_project_pipe<NU, TP, MODE>;
+  if constexpr (MODE == kSimt && sizeof(TP) == 4 && NU <= kBlochRealMaxNumax) {
+    if (p.bloch) kern = k_project_pipe<NU, TP, MODE, true>;
+  } else if (p.bloch) {
+    return cudaErrorInvalidValue;  // Bloch data: the FP32 CUDA-core form with float psi only
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -670,7 +733,7 @@ static cudaError_t pipe_project_t(const ProjectLaunch& p) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, p.g, static_cast<const TP*>(p.psi), p.atoms, p.order, p.zsplit,
-                            static_cast<float*>(p.coeff));
+                            static_cast<float*>(p.coeff), p.bloch);
 }
 
 template <int NU, typename TP, int MODE>
@@ -689,13 +752,18 @@ static cudaError_t blk_expand_t(const ExpandLaunch& p) {
   }
   const size_t smem = BlkSmem<NU, MODE>::bytes(p.g.cube, p.max_plane);
   auto kern = k_expand_blk<NU, TP, MODE>;
+  if constexpr (MODE == kSimt && sizeof(TP) == 4 && NU <= kBlochRealMaxNumax) {
+    if (p.bloch) kern = k_expand_blk<NU, TP, MODE, true>;
+  } else if (p.bloch) {
+    return cudaErrorInvalidValue;  // Bloch data: the FP32 CUDA-core form with float psi only
+  }
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nseg = (p.g.n[0] + kXSeg - 1) / kXSeg, nyb = (p.g.n[1] + kRowsPerBlk - 1) / kRowsPerBlk;
   const unsigned nblk = (unsigned)nseg * nyb * p.g.n[2];
   kern<<<dim3(nblk, (p.g.nbands + kWarp - 1) / kWarp), kRowsPerBlk * kWarp, smem, p.stream>>>(
       p.g, p.atoms, p.plane_ptr, p.plane_atoms, static_cast<const float*>(p.tables),
-      static_cast<const float*>(p.tables_xmajor), xf, static_cast<const float*>(p.t2), static_cast<TP*>(p.psi));
+      static_cast<const float*>(p.tables_xmajor), xf, static_cast<const float*>(p.t2), static_cast<TP*>(p.psi), p.bloch);
   return cudaGetLastError();
 }
 

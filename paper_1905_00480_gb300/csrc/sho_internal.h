@@ -53,8 +53,9 @@ struct DevCheck {
   int* flag = nullptr;
 };
 
-// FP64-accurate form of the Bloch transforms (Sec. 2.5; periodic grid): per atom the phase factors of its
-// cube's lattice translations as float pairs (re.hi, re.lo, im.hi, im.lo).  Along axis d the cube points
+// Bloch transforms on the real kernels (Sec. 2.5; periodic grid; FP64-accurate and FP32 forms): per atom
+// the phase factors of its cube's lattice translations as float pairs (re.hi, re.lo, im.hi, im.lo; the
+// FP32 form reads the leading floats).  Along axis d the cube points
 // i < w[d] map into the cell with translation T_d = f0_d n_d h and those from w[d] on with (f0_d + 1) n_d h
 // (w[d] >= cube: no crossing); ph[bx + 2 by + 4 bz] = e^{s i k.T} for the translation with bits b_d =
 // (i_d >= w[d]), s = +1 for the projection and -1 for the expansion; xstep = ph[0] / ph[1] = e^{-s i k_x n_x h}.
@@ -64,7 +65,7 @@ struct BlochPh {
   int w[4];
 };
 static_assert(sizeof(BlochPh) == 160, "BlochPh layout");
-constexpr int kBlochFfMaxNumax = 7;  // the FP64-accurate Bloch kernels are built for numax 0..7
+constexpr int kBlochRealMaxNumax = 7;  // Bloch variants of the real kernels (FP64-accurate, FP32): numax 0..7
 struct BlochArg {
   double k[3];  // Bloch vector
   double sgn;   // +1 projection, -1 expansion
@@ -92,7 +93,7 @@ struct ProjectLaunch {
   int* status = nullptr;    // FP64-accurate form: device status word (kStatusRange), may be null
   bool t2_only = false;     // FP64-accurate form: stop after the per-plane sums (the z-pass runs fused later)
   DevCheck chk;             // device checks (FP64 and FP64-accurate kernels), off by default
-  const BlochPh* bloch = nullptr;  // FP64-accurate Bloch projection: device [A] phases; psi and coeff
+  const BlochPh* bloch = nullptr;  // Bloch projection (FP64-accurate, FP32): device [A] phases; psi and coeff
                                    // are complex, their (re, im) pairs counted as 2 real bands (g.nbands)
   void* op = nullptr;       // FP64-accurate form on the tensor cores: op_layout() workspace, may be null
   int kernel = 0;           // FP64-accurate x-pass engine: 0 automatic, 1 float-float, 2 tcgen05
@@ -158,7 +159,7 @@ struct ExpandLaunch {
   void* oz = nullptr;       // FP64-accurate form on the tensor cores: oz_layout() workspace, may be null
   int stop_stage = 0x7fffffff;  // fault injection: that kernel stages the z-pass slices of this many atoms
   DevCheck chk;             // device checks (FP64 and FP64-accurate kernels), off by default
-  const BlochPh* bloch = nullptr;  // FP64-accurate Bloch expansion: device [A] phases (complex data as
+  const BlochPh* bloch = nullptr;  // Bloch expansion (FP64-accurate, FP32): device [A] phases (complex data as
                                    // 2 real bands per band, as for the projection)
   cudaStream_t stream;
 };

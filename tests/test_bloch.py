@@ -1,11 +1,11 @@
 """Bloch (complex) projection and expansion on the GPU against the oracle (FP64 and FP64-accurate forms,
-1e-12)."""
+1e-12; FP32 form on complex64 data against the oracle run on the same rounded input, the FP32 bound)."""
 import numpy as np
 import pytest
 
 import oracle
 import workloads
-from helpers import TOL_FP64, assert_coeff_close, rel_norm, require_gpu
+from helpers import TOL_FP32, TOL_FP64, assert_coeff_close, rel_norm, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,52 @@ def test_bloch_project_and_add(numax, nbands, prec):
     assert rel_norm((out.cpu().numpy() - psi).view(np.float64), (ref2 - psi).view(np.float64)) <= TOL_FP64
 
 
-def test_bloch_ff64_cubes_across_every_cell_face():
+@pytest.mark.parametrize("numax,nbands,k", [(3, 6, (0.0, 0.0, 0.0)), (5, 40, (0.9, -0.35, 1.7)),
+                                            (7, 34, (-2.2, 1.3, 0.6))])
+def test_bloch_fp32_project_and_add(numax, nbands, k):
+    """FP32 form on complex64 data (the real FP32 CUDA-core kernels over the (re, im) pairs, the phases
+    applied in FP32): 2 nbands real bands over full and ragged 32-band tiles, cubes that wrap on every
+    axis, k = 0 included."""
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, cube = (40, 36, 34), 0.2, 32
+    rng, pos, sig, psi = _case(950 + numax, grid, h, 5, nbands)
+    psi_d = torch.from_numpy(psi.astype(np.complex64)).cuda()
+    psi_r = psi_d.cpu().numpy().astype(np.complex128)   # the rounded input the kernels see
+    k = np.array(k)
+    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec="fp32")
+    assert got.dtype == torch.complex64
+    ref = oracle.project_bloch(grid, h, k, psi_r, pos, sig, numax, cube)
+    assert_coeff_close(got.cpu().numpy().astype(np.complex128).view(np.float64), ref.view(np.float64), TOL_FP32)
+    coef_d = torch.from_numpy((rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)).astype(
+        np.complex64)).cuda()
+    out = psi_d.clone()
+    api.add_bloch(out, coef_d, k, pos, sig, numax, cube, h, prec="fp32")
+    ref2 = oracle.add_bloch(grid, h, k, psi_r, pos, sig, numax, cube, coef_d.cpu().numpy().astype(np.complex128))
+    d = out.cpu().numpy().astype(np.complex128) - psi_r
+    assert rel_norm(d.view(np.float64), (ref2 - psi_r).view(np.float64)) <= TOL_FP32
+
+
+def test_bloch_fp32_adjoint():
+    require_gpu()
+    import torch
+    from paper_1905_00480_gb300 import api
+    grid, h, numax, cube = (40, 36, 34), 0.2, 6, 32
+    rng, pos, sig, psi = _case(955, grid, h, 4, 8)
+    psi_d = torch.from_numpy(psi.astype(np.complex64)).cuda()
+    k = [1.1, 0.4, -0.8]
+    c = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec="fp32")
+    coef = torch.from_numpy((rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).astype(
+        np.complex64)).cuda()
+    ec = api.add_bloch(torch.zeros_like(psi_d), coef, k, pos, sig, numax, cube, h, prec="fp32")
+    lhs = torch.vdot(c.flatten().cdouble(), coef.flatten().cdouble()).item()
+    rhs = h ** 3 * torch.vdot(psi_d.flatten().cdouble(), ec.flatten().cdouble()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("prec", ["ff64", "fp32"])
+def test_bloch_cubes_across_every_cell_face(prec):
     """Atoms on both sides of every face and in the corners, so that cube rows cross the boundary at
     their start and at their end along each axis, and tile segments meet both runs; a grid wider than
     the FP64 expansion's row limit."""
@@ -48,6 +93,7 @@ def test_bloch_ff64_cubes_across_every_cell_face():
     import torch
     from paper_1905_00480_gb300 import api
     grid, h, cube, numax, nbands = (456, 40, 36), 0.2, 16, 4, 6
+    cdt, tol = (np.complex128, TOL_FP64) if prec == "ff64" else (np.complex64, TOL_FP32)
     L = np.array(grid) * h
     rng = np.random.default_rng(941)
     pos = np.array([[0.05 * h, 0.3 * h, 0.2 * h], [L[0] - 0.3 * h, L[1] - 0.1 * h, L[2] - 0.45 * h],
@@ -57,15 +103,17 @@ def test_bloch_ff64_cubes_across_every_cell_face():
     psi = rng.standard_normal((grid[2], grid[1], grid[0], nbands)) + 1j * rng.standard_normal(
         (grid[2], grid[1], grid[0], nbands))
     k = np.array([-1.3, 0.8, 2.1])
-    psi_d = torch.from_numpy(psi).cuda()
-    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec="ff64").cpu().numpy()
+    psi = psi.astype(cdt).astype(np.complex128)
+    psi_d = torch.from_numpy(psi.astype(cdt)).cuda()
+    got = api.project_bloch(psi_d, k, pos, sig, numax, cube, h, prec=prec).cpu().numpy().astype(np.complex128)
     ref = oracle.project_bloch(grid, h, k, psi, pos, sig, numax, cube)
-    assert_coeff_close(got.view(np.float64), ref.view(np.float64), TOL_FP64)
-    coef = rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)
+    assert_coeff_close(got.view(np.float64), ref.view(np.float64), tol)
+    coef = (rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)).astype(cdt).astype(np.complex128)
     out = torch.zeros_like(psi_d)
-    api.add_bloch(out, torch.from_numpy(coef).cuda(), k, pos, sig, numax, cube, h, prec="ff64")
+    api.add_bloch(out, torch.from_numpy(coef.astype(cdt)).cuda(), k, pos, sig, numax, cube, h, prec=prec)
     ref2 = oracle.add_bloch(grid, h, k, np.zeros_like(psi), pos, sig, numax, cube, coef)
-    assert rel_norm(out.cpu().numpy().view(np.float64), ref2.view(np.float64)) <= TOL_FP64
+    got2 = out.cpu().numpy().astype(np.complex128)
+    assert rel_norm(got2.view(np.float64), ref2.view(np.float64)) <= tol
 
 
 def test_bloch_ff64_zero_k_is_the_real_form_on_each_part():
@@ -118,10 +166,16 @@ def test_bloch_rejects_other_precisions():
     require_gpu()
     import torch
     from paper_1905_00480_gb300 import api, ShoError
+    pos = np.array([[2.0, 2.0, 2.0]])
     psi = torch.zeros((16, 16, 16, 2), dtype=torch.complex128, device="cuda")
-    for prec in ("fp32", "tf32", "bf16"):
+    for prec in ("tf32", "bf16", "3xtf32"):
         with pytest.raises(ShoError):
-            api.project_bloch(psi, [0.1, 0, 0], np.array([[2.0, 2.0, 2.0]]), [1.0], 1, 16, 0.25, prec=prec)
+            api.project_bloch(psi, [0.1, 0, 0], pos, [1.0], 1, 16, 0.25, prec=prec)
+    with pytest.raises(ValueError):   # FP32 form: complex64 data
+        api.project_bloch(psi, [0.1, 0, 0], pos, [1.0], 1, 16, 0.25, prec="fp32")
+    odd = torch.zeros((16, 16, 16, 3), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ShoError):     # FP32 form: 2 nbands real bands in 16-byte rows
+        api.project_bloch(odd, [0.1, 0, 0], pos, [1.0], 1, 16, 0.25, prec="fp32")
 
 
 def test_bloch_zero_k_matches_real_path_and_adjoint():
