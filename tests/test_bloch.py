@@ -176,6 +176,17 @@ def test_bloch_rejects_other_precisions():
     odd = torch.zeros((16, 16, 16, 3), dtype=torch.complex64, device="cuda")
     with pytest.raises(ShoError):     # FP32 form: 2 nbands real bands in 16-byte rows
         api.project_bloch(odd, [0.1, 0, 0], pos, [1.0], 1, 16, 0.25, prec="fp32")
+    flat = torch.zeros(16 * 16 * 16 * 2 + 1, dtype=torch.complex64, device="cuda")
+    shifted = flat[1:].view(16, 16, 16, 2)   # contiguous, 8 bytes past a 16-byte boundary
+    assert shifted.data_ptr() % 16 == 8
+    with pytest.raises(ShoError):
+        api.project_bloch(shifted, [0.1, 0, 0], pos, [1.0], 1, 16, 0.25, prec="fp32")
+    c = torch.zeros((1, oracle.nstates(1), 2), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ShoError):
+        api.add_bloch(shifted, c, [0.1, 0, 0], pos, [1.0], 1, 16, 0.25, prec="fp32")
+    ok = torch.zeros((16, 16, 16, 2), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ShoError):     # numax above 7
+        api.project_bloch(ok, [0.1, 0, 0], pos, [1.0], 8, 16, 0.25, prec="fp32")
 
 
 def test_bloch_zero_k_matches_real_path_and_adjoint():
